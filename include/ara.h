@@ -1,0 +1,159 @@
+/*
+ * ara.h -- C ABI of libara: aggregate risk analysis with secondary uncertainty on one B300 GPU.
+ *
+ * Method: Varghese & Rau-Chaplin, "Accounting for Secondary Uncertainty: Efficient Computation of
+ * Portfolio Risk Measures on Multi and Many Core Architectures" (WHPCF'13), Algorithm 1 with the
+ * secondary-uncertainty model of its §3.  For every trial of a Year Event Table and every event
+ * in timestamp order, each ELT of a layer is looked up; a hit draws a loss
+ * max_l * InvCDF_beta(u; alpha, beta) from the moment-matched beta distribution; the losses of an
+ * event are summed, the occurrence terms applied, the results summed over the year and the
+ * aggregate terms applied, giving one Year Loss Table entry per trial.  PML and TVaR follow
+ * from the ordered YLT.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an ara_status; outputs are written only on ARA_OK unless a call says
+ *     otherwise.  ara_last_error_detail() gives a one-line reason for the last failure.
+ *   - Handles (YET, ELT, layer) are small non-negative integers owned by the context; they stay
+ *     valid until freed or until ara_destroy().
+ *   - Input arrays may be host or device pointers (the library tells them apart through unified
+ *     addressing) and are copied: the caller keeps ownership and may free them on return.
+ *   - The library never frees caller memory; ara_destroy() frees everything it allocated.
+ *   - A context is used by one host thread at a time.
+ *   - Device work runs on the context's own stream unless a call takes a stream argument.
+ *   - Nothing in the library traps, spins without bound or aborts the process: device-side
+ *     iteration caps are reported as ARA_ERR_NOT_CONVERGED with the results still written.
+ */
+#ifndef ARA_H
+#define ARA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ARA_API __attribute__((visibility("default")))
+
+typedef struct ara_ctx ara_ctx;
+
+typedef enum {
+  ARA_OK = 0,
+  ARA_ERR_INVALID_ARG = 1,   /* a size, pointer, value or ordering rule was broken      */
+  ARA_ERR_BAD_HANDLE = 2,    /* unknown or freed YET / ELT / layer handle                */
+  ARA_ERR_OOM = 3,           /* device or host allocation failed                         */
+  ARA_ERR_CUDA = 4,          /* a CUDA runtime call failed (detail holds its message)    */
+  ARA_ERR_NOT_CONVERGED = 5, /* some inversions hit the iteration cap; results written    */
+  ARA_ERR_BUSY = 6,          /* the serving queue is full                                */
+  ARA_ERR_NO_DEVICE = 7      /* no usable CUDA device                                    */
+} ara_status;
+
+/* Per-trial accumulation of occurrence losses into the year's aggregate (paper §2.3):
+ * ARA_ACC_FP64 sums in binary64; ARA_ACC_KAHAN32 sums in binary32 with Kahan compensation.
+ * Sampling, event sums and occurrence terms are binary32 in both; PML/TVaR tails are binary64. */
+#define ARA_ACC_FP64 0
+#define ARA_ACC_KAHAN32 1
+
+typedef struct {
+  uint64_t seed;       /* Philox key for the secondary-uncertainty uniforms (42 by convention) */
+  int32_t precision;   /* ARA_ACC_FP64 or ARA_ACC_KAHAN32                                      */
+  int32_t use_surrogate; /* 0 = exact inversion everywhere; 1 = learned surrogate with fallback */
+  int32_t device;      /* CUDA device ordinal                                                   */
+  int32_t reserved;
+} ara_config;
+
+/* Context ------------------------------------------------------------------------------------- */
+ARA_API ara_status ara_create(const ara_config* cfg, ara_ctx** out);
+ARA_API void ara_destroy(ara_ctx* ctx); /* NULL-safe; waits for the context's device work */
+ARA_API const char* ara_status_string(ara_status s);
+/* Copies the detail of the last failed call on ctx (NUL-terminated, truncated to n bytes). */
+ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n);
+/* Options settable after creation: ARA_OPT_PRECISION (value ARA_ACC_*), ARA_OPT_SEED,
+ * ARA_OPT_SURROGATE (0/1). */
+#define ARA_OPT_PRECISION 1
+#define ARA_OPT_SEED 2
+#define ARA_OPT_SURROGATE 3
+ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
+
+/* Year Event Table (paper §2.1) ------------------------------------------------------------------
+ * Trial i owns occurrences trial_offsets[i] .. trial_offsets[i+1]-1 of event_ids/timestamps, in
+ * ascending timestamp order (ties keep the stored order).  trial_offsets[0] = 0 and offsets are
+ * nondecreasing (an empty trial is allowed).  Event ids must lie in [0, catalog_size).
+ * Rejected with ARA_ERR_INVALID_ARG: n_trials < 0, catalog_size <= 0, bad offsets, an id out of
+ * range, a timestamp below its predecessor in the same trial, a NaN timestamp.
+ * Device copy: int32 ids and float32 timestamps, trial-major; 8 bytes per occurrence. */
+ARA_API ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_offsets,
+                                  const int32_t* event_ids, const float* timestamps,
+                                  int32_t catalog_size, int32_t* yet_out);
+ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
+
+/* Extended Event Loss Table (paper §2.1, §3.1, §3.3) ----------------------------------------------
+ * n records (n >= 0) with distinct event ids in the YET's catalogue: mean loss mu_l > 0,
+ * standard deviation sigma >= 0 and maximum exposure max_l > mu_l when sigma > 0.  Events absent
+ * from the table have zero loss (paper §4.1).  A record with sigma = 0 contributes its mean
+ * (primary uncertainty only).  Values are staged in FP64 once: alpha, beta (moment matching with
+ * the sigma_beta_max clamp of §3.3, sigma_beta set to sigma_beta_max (1 - 2^-20) when above it)
+ * and the constants of the inversion, then stored as binary32 (32 bytes per record).
+ * The handle number keys the record's uniforms: Philox4x32-10 counter (k, i_lo, elt/4, i_hi),
+ * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i. */
+ARA_API ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
+                               const double* mean, const double* sd, const double* max_exposure,
+                               int32_t* elt_out);
+ARA_API ara_status ara_free_elt(ara_ctx* ctx, int32_t elt);
+
+/* Layer (paper §2.1: XELT set plus terms (OccR, OccL, AggR, AggL)) ----------------------------
+ * elts[n_elts] (1 <= n_elts <= 64, distinct, same YET): the order fixes the order in which one
+ * event's ELT losses are summed.  All terms must be finite and >= 0.  Builds the layer's lookup
+ * structure on the device: per catalogue event an 8- (n_elts <= 32) or 16-byte entry (base,
+ * ELT bit mask) plus the event's records packed in layer order, sized to stay L2-resident. */
+ARA_API ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
+                                 double occ_ret, double occ_lim, double agg_ret, double agg_lim,
+                                 int32_t* layer_out);
+ARA_API ara_status ara_free_layer(ara_ctx* ctx, int32_t layer);
+
+/* Algorithm 1 -------------------------------------------------------------------------------------
+ * Year losses of trials [t0, t0+n) of yet under layer -> ylt[0..n-1] (binary64):
+ *   Y_i = min(max(S_i - AggR, 0), AggL),  S_i = sum_k min(max(l_ik - OccR, 0), OccL),
+ *   l_ik = sum over the layer's ELTs holding event e_ik of max_l * InvCDF_beta(u; alpha, beta).
+ * ylt may be host or device memory.  stream == NULL: blocking, on the context's stream, and
+ * ARA_ERR_NOT_CONVERGED is returned (with ylt written) if any inversion hit its cap.
+ * stream != NULL (a cudaStream_t): asynchronous on that stream, ylt must be device memory, and
+ * the convergence count is read later with ara_not_converged(). */
+ARA_API ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                           double* ylt, void* stream);
+/* Inversions that hit the iteration cap since the context was created (blocks on its work). */
+ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
+
+/* Risk measures (paper §2.4) ---------------------------------------------------------------------
+ * ylt[n] (host or device, n >= 1, no NaN), rps[m] return periods (> 1, host).  With
+ * k = n/rp (rounded up when not an integer; 1 <= k <= n) and the trials ordered by year loss
+ * descending, ties by ascending trial index:  pml[q] = the loss at rank k,
+ * tvar[q] = the mean of ranks 1..k (binary64 sums).  pml/tvar are host arrays of m values.
+ * Ordering by a device LSD radix sort (stable) of the losses' order-preserving bit patterns. */
+ARA_API ara_status ara_risk_measures(ara_ctx* ctx, const double* ylt, int64_t n,
+                                     const double* rps, int32_t m, double* pml, double* tvar);
+/* The same ordering exposed: order[r] = index of the r-th largest entry of ylt[n]; order may be
+ * host or device memory (int64). */
+ARA_API ara_status ara_rank_ylt(ara_ctx* ctx, const double* ylt, int64_t n, int64_t* order);
+
+/* Verification ------------------------------------------------------------------------------------
+ * Re-runs trials [t0, t0+n) with the same device code as ara_run, additionally listing every
+ * (trial, event, ELT) hit in event order, then layer order: the trial offset from t0, the event
+ * position k within its trial, the layer slot j, the record index in the caller's ELT order, the
+ * uniform u, the beta quantile x (NaN for a sigma = 0 record) and the loss.  Host arrays of
+ * max_hits entries; *n_hits receives the total (entries beyond max_hits are dropped).  Sized for
+ * small runs: the device buffer holds n * (longest trial) * n_elts hits. */
+ARA_API ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0,
+                                  int64_t n, int64_t max_hits, int32_t* hit_trial,
+                                  int32_t* hit_k, int32_t* hit_j, int32_t* hit_rec,
+                                  float* hit_u, float* hit_x, float* hit_loss, double* ylt,
+                                  int64_t* n_hits);
+
+/* Synchronises the context's stream. */
+ARA_API ara_status ara_synchronize(ara_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARA_H */

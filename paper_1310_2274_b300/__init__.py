@@ -1,0 +1,260 @@
+"""B300-native aggregate risk analysis with secondary uncertainty (arXiv 1310.2274).
+
+Thin Python binding of the C-ABI library libara.so (declared in include/ara.h): argument
+marshalling only.  Every step of the method runs in the library's CUDA kernels; there is no CPU
+fallback, and importing the binding fails loudly when the library has not been built.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); PyTorch provides device
+memory and streams, nothing else.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["lib", "Context", "AraError", "ACC_FP64", "ACC_KAHAN32", "LIB_PATH"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libara.so")
+ACC_FP64 = 0
+ACC_KAHAN32 = 1
+OPT_PRECISION, OPT_SEED, OPT_SURROGATE = 1, 2, 3
+STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",
+          5: "inversion did not converge", 6: "busy", 7: "no CUDA device"}
+
+_lib = None
+
+
+class AraError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {detail}" if detail else
+                         STATUS.get(status, str(status)))
+
+
+class _Config(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("precision", C.c_int32), ("use_surrogate", C.c_int32),
+                ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+_P = C.c_void_p
+_I32, _I64, _D = C.c_int32, C.c_int64, C.c_double
+
+_SIGNATURES = {
+    "ara_create": ([C.POINTER(_Config), C.POINTER(_P)], C.c_int),
+    "ara_destroy": ([_P], None),
+    "ara_status_string": ([C.c_int], C.c_char_p),
+    "ara_last_error_detail": ([_P, C.c_char_p, C.c_size_t], C.c_int),
+    "ara_set_option": ([_P, _I32, _I64], C.c_int),
+    "ara_create_yet": ([_P, _I64, _P, _P, _P, _I32, C.POINTER(_I32)], C.c_int),
+    "ara_free_yet": ([_P, _I32], C.c_int),
+    "ara_add_elt": ([_P, _I32, _I64, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
+    "ara_free_elt": ([_P, _I32], C.c_int),
+    "ara_add_layer": ([_P, _P, _I32, _D, _D, _D, _D, C.POINTER(_I32)], C.c_int),
+    "ara_free_layer": ([_P, _I32], C.c_int),
+    "ara_run": ([_P, _I32, _I32, _I64, _I64, _P, _P], C.c_int),
+    "ara_not_converged": ([_P, C.POINTER(_I64)], C.c_int),
+    "ara_risk_measures": ([_P, _P, _I64, _P, _I32, _P, _P], C.c_int),
+    "ara_rank_ylt": ([_P, _P, _I64, _P], C.c_int),
+    "ara_trace_hits": ([_P, _I32, _I32, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P,
+                        C.POINTER(_I64)], C.c_int),
+    "ara_synchronize": ([_P], C.c_int),
+}
+
+
+def lib():
+    """The loaded libara.so.  Raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libara.so not built at {LIB_PATH}: run "
+                              "`python -m paper_1310_2274_b300.build` (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    # torch tensor
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _np(a, dtype):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=dtype)
+    try:
+        import torch
+
+        if isinstance(a, torch.Tensor):
+            td = {np.int32: torch.int32, np.int64: torch.int64, np.float32: torch.float32,
+                  np.float64: torch.float64}[np.dtype(dtype).type]
+            return a.to(td).contiguous()
+    except ImportError:
+        pass
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Context:
+    """One ara_ctx: owns the device copies of YETs, ELTs and layers."""
+
+    def __init__(self, seed: int = 42, precision: int = ACC_FP64, device: int = 0,
+                 use_surrogate: bool = False):
+        cfg = _Config(seed, precision, int(use_surrogate), device, 0)
+        h = _P()
+        st = lib().ara_create(C.byref(cfg), C.byref(h))
+        if st != 0:
+            raise AraError(st, "ara_create")
+        self._h = h
+
+    # -- plumbing ------------------------------------------------------------------------------
+    @property
+    def handle(self):
+        return self._h
+
+    def _detail(self) -> str:
+        buf = C.create_string_buffer(512)
+        lib().ara_last_error_detail(self._h, buf, 512)
+        return buf.value.decode(errors="replace")
+
+    def _check(self, st: int, allow_not_converged: bool = False):
+        if st == 0 or (allow_not_converged and st == 5):
+            return st
+        raise AraError(st, self._detail())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ara_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, option: int, value: int):
+        self._check(lib().ara_set_option(self._h, option, int(value)))
+
+    def synchronize(self):
+        self._check(lib().ara_synchronize(self._h))
+
+    def not_converged(self) -> int:
+        v = _I64(0)
+        self._check(lib().ara_not_converged(self._h, C.byref(v)))
+        return v.value
+
+    # -- staging -------------------------------------------------------------------------------
+    def create_yet(self, offsets, event_ids, timestamps, catalog_size: int) -> int:
+        off = _np(offsets, np.int64)
+        ids = _np(event_ids, np.int32)
+        ts = _np(timestamps, np.float32)
+        n_trials = int(off.shape[0]) - 1
+        out = _I32(-1)
+        self._check(lib().ara_create_yet(self._h, n_trials, _ptr(off), _ptr(ids), _ptr(ts),
+                                         int(catalog_size), C.byref(out)))
+        return out.value
+
+    def add_elt(self, yet: int, event_ids, mean, sd, max_exposure) -> int:
+        ids = _np(event_ids, np.int32)
+        mu = _np(mean, np.float64)
+        s = _np(sd, np.float64)
+        mx = _np(max_exposure, np.float64)
+        out = _I32(-1)
+        self._check(lib().ara_add_elt(self._h, yet, int(ids.shape[0]), _ptr(ids), _ptr(mu),
+                                      _ptr(s), _ptr(mx), C.byref(out)))
+        return out.value
+
+    def add_layer(self, elts, occ_ret: float, occ_lim: float, agg_ret: float,
+                  agg_lim: float) -> int:
+        e = np.ascontiguousarray(elts, dtype=np.int32)
+        out = _I32(-1)
+        self._check(lib().ara_add_layer(self._h, _ptr(e), int(e.shape[0]), occ_ret, occ_lim,
+                                        agg_ret, agg_lim, C.byref(out)))
+        return out.value
+
+    def free_yet(self, yet: int):
+        self._check(lib().ara_free_yet(self._h, yet))
+
+    def free_elt(self, elt: int):
+        self._check(lib().ara_free_elt(self._h, elt))
+
+    def free_layer(self, layer: int):
+        self._check(lib().ara_free_layer(self._h, layer))
+
+    # -- Algorithm 1 ---------------------------------------------------------------------------
+    def run(self, yet: int, layer: int, t0: int, n: int, out=None, stream=None,
+            allow_not_converged: bool = False):
+        """Year losses of trials [t0, t0+n).  out: float64 numpy array or torch tensor (host or
+        CUDA); stream: a torch.cuda.Stream or raw cudaStream_t (asynchronous, CUDA out only)."""
+        if out is None:
+            out = np.zeros(n, dtype=np.float64)
+        s = None
+        if stream is not None:
+            s = getattr(stream, "cuda_stream", stream)
+        st = lib().ara_run(self._h, yet, layer, int(t0), int(n), _ptr(out), s)
+        self._check(st, allow_not_converged)
+        return out
+
+    # -- risk measures -------------------------------------------------------------------------
+    def risk_measures(self, ylt, rps):
+        y = ylt if _is_cuda(ylt) else _np(ylt, np.float64)
+        r = np.ascontiguousarray(rps, dtype=np.float64)
+        pml = np.zeros(r.shape[0])
+        tvar = np.zeros(r.shape[0])
+        self._check(lib().ara_risk_measures(self._h, _ptr(y), int(y.shape[0]), _ptr(r),
+                                            int(r.shape[0]), _ptr(pml), _ptr(tvar)))
+        return pml, tvar
+
+    def rank(self, ylt, out=None):
+        y = ylt if _is_cuda(ylt) else _np(ylt, np.float64)
+        if out is None:
+            out = np.zeros(int(y.shape[0]), dtype=np.int64)
+        self._check(lib().ara_rank_ylt(self._h, _ptr(y), int(y.shape[0]), _ptr(out)))
+        return out
+
+    def trace(self, yet: int, layer: int, t0: int, n: int, max_hits: int = 1 << 22):
+        bufs = dict(trial=np.zeros(max_hits, np.int32), k=np.zeros(max_hits, np.int32),
+                    j=np.zeros(max_hits, np.int32), rec=np.zeros(max_hits, np.int32),
+                    u=np.zeros(max_hits, np.float32), x=np.zeros(max_hits, np.float32),
+                    loss=np.zeros(max_hits, np.float32))
+        ylt = np.zeros(n, dtype=np.float64)
+        nh = _I64(0)
+        self._check(lib().ara_trace_hits(
+            self._h, yet, layer, int(t0), int(n), int(max_hits), _ptr(bufs["trial"]),
+            _ptr(bufs["k"]), _ptr(bufs["j"]), _ptr(bufs["rec"]), _ptr(bufs["u"]),
+            _ptr(bufs["x"]), _ptr(bufs["loss"]), _ptr(ylt), C.byref(nh)))
+        m = min(nh.value, max_hits)
+        return {k: v[:m] for k, v in bufs.items()}, ylt
+
+    # -- convenience for synthetic workloads ---------------------------------------------------
+    def stage_workload(self, w):
+        """Stage a synth.Workload: returns (yet, [elt handles], layer)."""
+        yet = self.create_yet(w.yet.offsets, w.yet.event_ids, w.yet.timestamps,
+                              w.yet.catalog_size)
+        elts = [self.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in w.elts]
+        t = w.terms
+        layer = self.add_layer(elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+        return yet, elts, layer

@@ -1,0 +1,773 @@
+// ara_api.cu -- the C ABI of libara (include/ara.h): contexts, handles, validation, launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ara.h"
+#include "ara_internal.h"
+
+using namespace ara;
+
+struct ara_ctx {
+  ara_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string detail;
+  std::vector<YetDev> yets;
+  std::vector<EltDev> elts;
+  std::vector<LayerDev> layers;
+  unsigned long long* d_not_conv = nullptr;
+  unsigned int* d_flags = nullptr;
+  // grow-only scratch
+  SortScratch sort;
+  double* d_ylt_tmp = nullptr;
+  int64_t ylt_tmp_cap = 0;
+  void* d_misc = nullptr;  // small staging area for tail sums
+};
+
+namespace {
+
+ara_status fail(ara_ctx* c, ara_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->detail = buf;
+  }
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess) {                                                                  \
+      cudaGetLastError();                                                                     \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA, "%s: %s", \
+                  #call, cudaGetErrorString(_e));                                             \
+    }                                                                                         \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dev_alloc(T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)n);
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Copies n elements from a host or device pointer into device memory on the stream.
+template <class T>
+cudaError_t copy_in(T* dst, const T* src, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, st);
+}
+
+void free_yet(YetDev& y) {
+  dev_free(y.ids);
+  dev_free(y.ts);
+  dev_free(y.offsets);
+  y = YetDev();
+}
+void free_elt(EltDev& e) {
+  dev_free(e.ids);
+  dev_free(e.recs);
+  e = EltDev();
+}
+void free_layer(LayerDev& l) {
+  dev_free(l.evt);
+  dev_free(l.packed);
+  dev_free(l.packed_rec);
+  l = LayerDev();
+}
+
+ara_status set_device(ara_ctx* c) {
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  return ARA_OK;
+}
+
+ara_status ensure_ylt_tmp(ara_ctx* c, int64_t n) {
+  if (n <= c->ylt_tmp_cap) return ARA_OK;
+  dev_free(c->d_ylt_tmp);
+  c->d_ylt_tmp = nullptr;
+  c->ylt_tmp_cap = 0;
+  CUDA_TRY(c, dev_alloc(&c->d_ylt_tmp, n));
+  c->ylt_tmp_cap = n;
+  return ARA_OK;
+}
+
+ara_status ensure_sort(ara_ctx* c, int64_t n) {
+  SortScratch& s = c->sort;
+  const int64_t tiles = sort_tiles(n);
+  const int64_t hist_n = 256 * tiles;
+  if (n > s.cap) {
+    for (int b = 0; b < 2; ++b) {
+      dev_free(s.keys[b]);
+      dev_free(s.vals[b]);
+      s.keys[b] = nullptr;
+      s.vals[b] = nullptr;
+    }
+    s.cap = 0;
+    for (int b = 0; b < 2; ++b) {
+      CUDA_TRY(c, dev_alloc(&s.keys[b], n));
+      CUDA_TRY(c, dev_alloc(&s.vals[b], n));
+    }
+    s.cap = n;
+  }
+  if (hist_n > s.hist_cap) {
+    dev_free(s.hist);
+    dev_free(s.scan_tmp);
+    s.hist = nullptr;
+    s.scan_tmp = nullptr;
+    s.hist_cap = 0;
+    CUDA_TRY(c, dev_alloc(&s.hist, hist_n));
+    s.scan_cap = scan_tmp_words(hist_n);
+    CUDA_TRY(c, dev_alloc(&s.scan_tmp, s.scan_cap));
+    s.hist_cap = hist_n;
+  }
+  if (!s.digit_flags) CUDA_TRY(c, dev_alloc(&s.digit_flags, 4));
+  return ARA_OK;
+}
+
+int64_t tail_count(int64_t n, double rp) {
+  const double q = (double)n / rp;
+  const double r = nearbyint(q);
+  int64_t k = (fabs(q - r) <= 1e-9 * fmax(1.0, q)) ? (int64_t)r : (int64_t)ceil(q);
+  if (k < 1) k = 1;
+  if (k > n) k = n;
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ara_status_string(ara_status s) {
+  switch (s) {
+    case ARA_OK: return "ok";
+    case ARA_ERR_INVALID_ARG: return "invalid argument";
+    case ARA_ERR_BAD_HANDLE: return "bad handle";
+    case ARA_ERR_OOM: return "out of memory";
+    case ARA_ERR_CUDA: return "CUDA error";
+    case ARA_ERR_NOT_CONVERGED: return "inversion did not converge";
+    case ARA_ERR_BUSY: return "busy";
+    case ARA_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
+  if (!out) return ARA_ERR_INVALID_ARG;
+  *out = nullptr;
+  ara_config c{};
+  c.seed = 42;
+  if (cfg) c = *cfg;
+  if (c.precision != ARA_ACC_FP64 && c.precision != ARA_ACC_KAHAN32) return ARA_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return ARA_ERR_NO_DEVICE;
+  }
+  if (c.device < 0 || c.device >= ndev) return ARA_ERR_INVALID_ARG;
+  ara_ctx* ctx = new (std::nothrow) ara_ctx();
+  if (!ctx) return ARA_ERR_OOM;
+  ctx->cfg = c;
+  ctx->device = c.device;
+  if (cudaSetDevice(ctx->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      dev_alloc(&ctx->d_not_conv, 1) != cudaSuccess || dev_alloc(&ctx->d_flags, 4) != cudaSuccess ||
+      cudaMalloc(&ctx->d_misc, 4096) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_not_conv, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ara_destroy(ctx);
+    return ARA_ERR_CUDA;
+  }
+  *out = ctx;
+  return ARA_OK;
+}
+
+void ara_destroy(ara_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& y : ctx->yets) free_yet(y);
+  for (auto& e : ctx->elts) free_elt(e);
+  for (auto& l : ctx->layers) free_layer(l);
+  for (int b = 0; b < 2; ++b) {
+    dev_free(ctx->sort.keys[b]);
+    dev_free(ctx->sort.vals[b]);
+  }
+  dev_free(ctx->sort.hist);
+  dev_free(ctx->sort.scan_tmp);
+  dev_free(ctx->sort.digit_flags);
+  dev_free(ctx->d_ylt_tmp);
+  dev_free(ctx->d_not_conv);
+  dev_free(ctx->d_flags);
+  dev_free(ctx->d_misc);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaGetLastError();
+  delete ctx;
+}
+
+ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return ARA_ERR_INVALID_ARG;
+  snprintf(buf, n, "%s", ctx->detail.c_str());
+  return ARA_OK;
+}
+
+ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  switch (option) {
+    case ARA_OPT_PRECISION:
+      if (value != ARA_ACC_FP64 && value != ARA_ACC_KAHAN32)
+        return fail(ctx, ARA_ERR_INVALID_ARG, "precision must be ARA_ACC_FP64 or ARA_ACC_KAHAN32");
+      ctx->cfg.precision = (int32_t)value;
+      return ARA_OK;
+    case ARA_OPT_SEED:
+      ctx->cfg.seed = (uint64_t)value;
+      return ARA_OK;
+    case ARA_OPT_SURROGATE:
+      if (value != 0 && value != 1) return fail(ctx, ARA_ERR_INVALID_ARG, "surrogate is 0 or 1");
+      ctx->cfg.use_surrogate = (int32_t)value;
+      return ARA_OK;
+  }
+  return fail(ctx, ARA_ERR_INVALID_ARG, "unknown option %d", option);
+}
+
+ara_status ara_synchronize(ara_ctx* ctx) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return ARA_OK;
+}
+
+// ---- YET ------------------------------------------------------------------------------------
+ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_offsets,
+                          const int32_t* event_ids, const float* timestamps,
+                          int32_t catalog_size, int32_t* yet_out) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!yet_out) return fail(ctx, ARA_ERR_INVALID_ARG, "yet_out is NULL");
+  if (n_trials < 0) return fail(ctx, ARA_ERR_INVALID_ARG, "n_trials < 0");
+  if (catalog_size <= 0) return fail(ctx, ARA_ERR_INVALID_ARG, "catalog_size <= 0");
+  if (!trial_offsets) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets is NULL");
+  ara_status s = set_device(ctx);
+  if (s != ARA_OK) return s;
+  // offsets are validated on the host (n_trials + 1 values)
+  std::vector<int64_t> off((size_t)n_trials + 1);
+  CUDA_TRY(ctx, cudaMemcpy(off.data(), trial_offsets, sizeof(int64_t) * off.size(),
+                           cudaMemcpyDefault));
+  if (off[0] != 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets[0] != 0");
+  int64_t max_len = 0;
+  for (int64_t i = 0; i < n_trials; ++i) {
+    const int64_t len = off[(size_t)i + 1] - off[(size_t)i];
+    if (len < 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets decrease at trial %lld",
+                             (long long)i);
+    if (len > max_len) max_len = len;
+  }
+  const int64_t n_occ = off[(size_t)n_trials];
+  if (n_occ > 0 && (!event_ids || !timestamps))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "event_ids or timestamps is NULL");
+  if (n_occ >= ((int64_t)1 << 40)) return fail(ctx, ARA_ERR_INVALID_ARG, "YET too large");
+  YetDev y;
+  y.n_trials = n_trials;
+  y.n_occ = n_occ;
+  y.catalog = catalog_size;
+  y.max_len = max_len;
+  cudaError_t e;
+  if ((e = dev_alloc(&y.ids, n_occ)) != cudaSuccess || (e = dev_alloc(&y.ts, n_occ)) != cudaSuccess ||
+      (e = dev_alloc(&y.offsets, n_trials + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    free_yet(y);
+    return fail(ctx, ARA_ERR_OOM, "YET of %lld occurrences: %s", (long long)n_occ,
+                cudaGetErrorString(e));
+  }
+  if ((e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess ||
+      (e = copy_in(y.ts, timestamps, n_occ, ctx->stream)) != cudaSuccess ||
+      (e = copy_in(y.offsets, off.data(), n_trials + 1, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
+      (e = launch_validate_yet(y, ctx->d_flags, ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    free_yet(y);
+    return fail(ctx, ARA_ERR_CUDA, "staging YET: %s", cudaGetErrorString(e));
+  }
+  unsigned int flags = 0;
+  if ((e = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
+                           ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    free_yet(y);
+    return fail(ctx, ARA_ERR_CUDA, "staging YET: %s", cudaGetErrorString(e));
+  }
+  if (flags) {
+    free_yet(y);
+    return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
+                (flags & 1) ? " event id outside [0, catalog_size)" : "",
+                (flags & 2) ? " timestamps decrease within a trial" : "",
+                (flags & 4) ? " NaN timestamp" : "");
+  }
+  y.live = true;
+  ctx->yets.push_back(y);
+  *yet_out = (int32_t)ctx->yets.size() - 1;
+  return ARA_OK;
+}
+
+ara_status ara_free_yet(ara_ctx* ctx, int32_t yet) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (yet < 0 || yet >= (int32_t)ctx->yets.size() || !ctx->yets[yet].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad YET handle %d", yet);
+  for (auto& e : ctx->elts)
+    if (e.live && e.yet == yet) return fail(ctx, ARA_ERR_INVALID_ARG, "YET still has ELTs");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  free_yet(ctx->yets[yet]);
+  return ARA_OK;
+}
+
+// ---- ELT ------------------------------------------------------------------------------------
+ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
+                       const double* mean, const double* sd, const double* max_exposure,
+                       int32_t* elt_out) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!elt_out) return fail(ctx, ARA_ERR_INVALID_ARG, "elt_out is NULL");
+  if (yet < 0 || yet >= (int32_t)ctx->yets.size() || !ctx->yets[yet].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad YET handle %d", yet);
+  if (n < 0 || n >= ((int64_t)1 << 31)) return fail(ctx, ARA_ERR_INVALID_ARG, "bad record count");
+  if (n > 0 && (!event_ids || !mean || !sd || !max_exposure))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "NULL ELT array");
+  ara_status s = set_device(ctx);
+  if (s != ARA_OK) return s;
+  const YetDev& y = ctx->yets[yet];
+  EltDev e;
+  e.yet = yet;
+  e.n = n;
+  double *d_mean = nullptr, *d_sd = nullptr, *d_mx = nullptr;
+  unsigned int* d_dup = nullptr;
+  cudaError_t err;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(d_mean);
+    dev_free(d_sd);
+    dev_free(d_mx);
+    dev_free(d_dup);
+  };
+  if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
+      (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
+      (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    free_elt(e);
+    return fail(ctx, ARA_ERR_OOM, "ELT of %lld records: %s", (long long)n, cudaGetErrorString(err));
+  }
+  unsigned int flags = 0;
+  if ((err = copy_in(e.ids, event_ids, n, ctx->stream)) != cudaSuccess ||
+      (err = copy_in(d_mean, mean, n, ctx->stream)) != cudaSuccess ||
+      (err = copy_in(d_sd, sd, n, ctx->stream)) != cudaSuccess ||
+      (err = copy_in(d_mx, max_exposure, n, ctx->stream)) != cudaSuccess ||
+      (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog, ctx->stream)) != cudaSuccess ||
+      (err = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
+      (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_mx, y.catalog, e.recs, d_dup,
+                                ctx->d_flags, ctx->stream)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess ||
+      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    free_elt(e);
+    return fail(ctx, ARA_ERR_CUDA, "staging ELT: %s", cudaGetErrorString(err));
+  }
+  cleanup();
+  if (flags) {
+    free_elt(e);
+    return fail(ctx, ARA_ERR_INVALID_ARG, "ELT rejected:%s%s%s%s",
+                (flags & 8) ? " event id outside the catalogue" : "",
+                (flags & 16) ? " mean <= 0, sd < 0 or non-finite value" : "",
+                (flags & 32) ? " max_exposure <= mean with sd > 0" : "",
+                (flags & 64) ? " duplicate event id" : "");
+  }
+  e.live = true;
+  ctx->elts.push_back(e);
+  *elt_out = (int32_t)ctx->elts.size() - 1;
+  return ARA_OK;
+}
+
+ara_status ara_free_elt(ara_ctx* ctx, int32_t elt) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (elt < 0 || elt >= (int32_t)ctx->elts.size() || !ctx->elts[elt].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad ELT handle %d", elt);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  free_elt(ctx->elts[elt]);
+  return ARA_OK;
+}
+
+// ---- layer ------------------------------------------------------------------------------------
+ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
+                         double occ_lim, double agg_ret, double agg_lim, int32_t* layer_out) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!layer_out || !elts) return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
+  if (n_elts < 1 || n_elts > kMaxLayerElts)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "a layer covers 1..%d ELTs", kMaxLayerElts);
+  const double terms[4] = {occ_ret, occ_lim, agg_ret, agg_lim};
+  for (double t : terms)
+    if (!(t >= 0.0) || !isfinite(t))
+      return fail(ctx, ARA_ERR_INVALID_ARG, "layer terms must be finite and >= 0");
+  int32_t yet = -1;
+  for (int j = 0; j < n_elts; ++j) {
+    const int32_t h = elts[j];
+    if (h < 0 || h >= (int32_t)ctx->elts.size() || !ctx->elts[h].live)
+      return fail(ctx, ARA_ERR_BAD_HANDLE, "bad ELT handle %d", h);
+    for (int j2 = 0; j2 < j; ++j2)
+      if (elts[j2] == h) return fail(ctx, ARA_ERR_INVALID_ARG, "ELT %d listed twice", h);
+    if (yet < 0) yet = ctx->elts[h].yet;
+    if (ctx->elts[h].yet != yet)
+      return fail(ctx, ARA_ERR_INVALID_ARG, "ELTs of a layer must share one YET");
+  }
+  ara_status s = set_device(ctx);
+  if (s != ARA_OK) return s;
+  const int64_t C = ctx->yets[yet].catalog;
+  LayerDev L;
+  L.yet = yet;
+  L.n_slots = n_elts;
+  L.mask_words = n_elts <= 32 ? 1 : 2;
+  for (int j = 0; j < kMaxLayerElts; ++j) L.handles[j] = j < n_elts ? elts[j] : 0;
+  L.occ_ret = occ_ret;
+  L.occ_lim = occ_lim;
+  L.agg_ret = agg_ret;
+  L.agg_lim = agg_lim;
+  const int MW = L.mask_words;
+  uint32_t *d_mask = nullptr, *d_cnt = nullptr, *d_base = nullptr, *d_tmp = nullptr;
+  const int64_t tmp_words = scan_tmp_words(C);
+  cudaError_t err;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(d_mask);
+    dev_free(d_cnt);
+    dev_free(d_base);
+    dev_free(d_tmp);
+  };
+  const int64_t evt_words = C * (MW == 1 ? 2 : 4);
+  if ((err = dev_alloc(&d_mask, C * MW)) != cudaSuccess || (err = dev_alloc(&d_cnt, C)) != cudaSuccess ||
+      (err = dev_alloc(&d_base, C)) != cudaSuccess || (err = dev_alloc(&d_tmp, tmp_words)) != cudaSuccess ||
+      (err = dev_alloc(&L.evt, evt_words)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    free_layer(L);
+    return fail(ctx, ARA_ERR_OOM, "layer index: %s", cudaGetErrorString(err));
+  }
+  uint32_t last[2] = {0, 0};
+  err = cudaMemsetAsync(d_mask, 0, sizeof(uint32_t) * (size_t)(C * MW), ctx->stream);
+  for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
+    err = launch_layer_mask(ctx->elts[elts[j]], j, MW, d_mask, ctx->stream);
+  if (err == cudaSuccess) err = launch_layer_counts(d_mask, MW, C, d_cnt, ctx->stream);
+  if (err == cudaSuccess) err = launch_exclusive_scan_u32(d_cnt, d_base, C, d_tmp, tmp_words, ctx->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&last[0], d_base + (C - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&last[1], d_cnt + (C - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = launch_layer_index(d_mask, d_base, MW, C, L.evt, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    free_layer(L);
+    return fail(ctx, ARA_ERR_CUDA, "layer index: %s", cudaGetErrorString(err));
+  }
+  L.n_packed = (int64_t)last[0] + (int64_t)last[1];
+  if ((err = dev_alloc(&L.packed, L.n_packed)) != cudaSuccess ||
+      (err = dev_alloc(&L.packed_rec, L.n_packed)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    free_layer(L);
+    return fail(ctx, ARA_ERR_OOM, "layer records: %s", cudaGetErrorString(err));
+  }
+  for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
+    err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, L.packed_rec, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    free_layer(L);
+    return fail(ctx, ARA_ERR_CUDA, "layer records: %s", cudaGetErrorString(err));
+  }
+  L.live = true;
+  ctx->layers.push_back(L);
+  *layer_out = (int32_t)ctx->layers.size() - 1;
+  return ARA_OK;
+}
+
+ara_status ara_free_layer(ara_ctx* ctx, int32_t layer) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (layer < 0 || layer >= (int32_t)ctx->layers.size() || !ctx->layers[layer].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad layer handle %d", layer);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  free_layer(ctx->layers[layer]);
+  return ARA_OK;
+}
+
+// ---- run ------------------------------------------------------------------------------------
+static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n) {
+  if (yet < 0 || yet >= (int32_t)ctx->yets.size() || !ctx->yets[yet].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad YET handle %d", yet);
+  if (layer < 0 || layer >= (int32_t)ctx->layers.size() || !ctx->layers[layer].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad layer handle %d", layer);
+  const LayerDev& L = ctx->layers[layer];
+  if (L.yet != yet) return fail(ctx, ARA_ERR_INVALID_ARG, "layer belongs to another YET");
+  for (int j = 0; j < L.n_slots; ++j)
+    if (!ctx->elts[L.handles[j]].live)
+      return fail(ctx, ARA_ERR_BAD_HANDLE, "layer uses freed ELT %d", L.handles[j]);
+  if (t0 < 0 || n < 0 || t0 + n > ctx->yets[yet].n_trials)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "trial range [%lld, %lld) outside the YET",
+                (long long)t0, (long long)(t0 + n));
+  return ARA_OK;
+}
+
+static TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
+                               int64_t n, double* d_ylt) {
+  TrialParams p;
+  memset(&p, 0, sizeof p);
+  p.ids = Y.ids;
+  p.offsets = Y.offsets;
+  p.evt = L.evt;
+  p.recs = L.packed;
+  p.rec_idx = L.packed_rec;
+  for (int j = 0; j < kMaxLayerElts; ++j) p.handles[j] = L.handles[j];
+  p.n_slots = L.n_slots;
+  p.occ_ret = (float)L.occ_ret;
+  p.occ_lim = (float)L.occ_lim;
+  p.agg_ret = L.agg_ret;
+  p.agg_lim = L.agg_lim;
+  p.seed = ctx->cfg.seed;
+  p.t0 = t0;
+  p.n = n;
+  p.ylt = d_ylt;
+  p.not_conv = ctx->d_not_conv;
+  return p;
+}
+
+ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n, double* ylt,
+                   void* stream) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  ara_status s = check_run_args(ctx, yet, layer, t0, n);
+  if (s != ARA_OK) return s;
+  if (n > 0 && !ylt) return fail(ctx, ARA_ERR_INVALID_ARG, "ylt is NULL");
+  if (n == 0) return ARA_OK;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const bool dev_out = is_device_ptr(ylt);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  if (stream && !dev_out)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need a device ylt");
+  double* d_ylt = ylt;
+  if (!dev_out) {
+    s = ensure_ylt_tmp(ctx, n);
+    if (s != ARA_OK) return s;
+    d_ylt = ctx->d_ylt_tmp;
+  }
+  unsigned long long nc_before = 0;
+  if (!stream)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
+                                  cudaMemcpyDeviceToHost, st));
+  const TrialParams p = make_params(ctx, ctx->yets[yet], ctx->layers[layer], t0, n, d_ylt);
+  CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision, false, st));
+  if (stream) return ARA_OK;
+  if (!dev_out)
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  unsigned long long nc_after = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
+                                cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (nc_after != nc_before)
+    return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
+                nc_after - nc_before);
+  return ARA_OK;
+}
+
+ara_status ara_not_converged(ara_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaDeviceSynchronize());
+  unsigned long long v = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&v, ctx->d_not_conv, sizeof v, cudaMemcpyDeviceToHost));
+  *count = (int64_t)v;
+  return ARA_OK;
+}
+
+// ---- ordering and risk measures -------------------------------------------------------------
+static ara_status stage_and_sort(ara_ctx* ctx, const double* ylt, int64_t n, const double** d_y,
+                                 const uint32_t** d_order) {
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (n >= ((int64_t)1 << 32)) return fail(ctx, ARA_ERR_INVALID_ARG, "YLT too long");
+  ara_status s = ensure_sort(ctx, n);
+  if (s != ARA_OK) return s;
+  const double* dy = ylt;
+  if (!is_device_ptr(ylt)) {
+    s = ensure_ylt_tmp(ctx, n);
+    if (s != ARA_OK) return s;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_ylt_tmp, ylt, sizeof(double) * (size_t)n,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    dy = ctx->d_ylt_tmp;
+  }
+  int which = 0;
+  cudaError_t e = sort_ylt_desc(dy, n, ctx->sort, &which, ctx->stream);
+  if (e == cudaErrorInvalidValue) return fail(ctx, ARA_ERR_INVALID_ARG, "NaN in the YLT");
+  CUDA_TRY(ctx, e);
+  *d_y = dy;
+  *d_order = ctx->sort.vals[which];
+  return ARA_OK;
+}
+
+ara_status ara_risk_measures(ara_ctx* ctx, const double* ylt, int64_t n, const double* rps,
+                             int32_t m, double* pml, double* tvar) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (n < 1 || !ylt) return fail(ctx, ARA_ERR_INVALID_ARG, "empty YLT");
+  if (m < 0 || m > 128 || (m > 0 && (!rps || !pml || !tvar)))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "bad return-period list");
+  for (int q = 0; q < m; ++q)
+    if (!(rps[q] > 1.0) || !isfinite(rps[q]))
+      return fail(ctx, ARA_ERR_INVALID_ARG, "return periods must be finite and > 1");
+  const double* dy;
+  const uint32_t* order;
+  ara_status s = stage_and_sort(ctx, ylt, n, &dy, &order);
+  if (s != ARA_OK) return s;
+  if (m == 0) return ARA_OK;
+  int64_t ks[128];
+  for (int q = 0; q < m; ++q) ks[q] = tail_count(n, rps[q]);
+  int64_t* d_k = reinterpret_cast<int64_t*>(ctx->d_misc);
+  double* d_pml = reinterpret_cast<double*>(d_k + 128);
+  double* d_tvar = d_pml + 128;
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_k, ks, sizeof(int64_t) * m, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, launch_tail_sums(dy, order, n, d_k, m, d_pml, d_tvar, ctx->stream));
+  std::vector<double> hp(m), ht(m);
+  CUDA_TRY(ctx, cudaMemcpyAsync(hp.data(), d_pml, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(ht.data(), d_tvar, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < m; ++q) {
+    pml[q] = hp[q];
+    tvar[q] = ht[q];
+  }
+  return ARA_OK;
+}
+
+ara_status ara_rank_ylt(ara_ctx* ctx, const double* ylt, int64_t n, int64_t* order) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (n < 1 || !ylt || !order) return fail(ctx, ARA_ERR_INVALID_ARG, "empty YLT or NULL order");
+  const double* dy;
+  const uint32_t* d_order;
+  ara_status s = stage_and_sort(ctx, ylt, n, &dy, &d_order);
+  if (s != ARA_OK) return s;
+  if (is_device_ptr(order)) {
+    CUDA_TRY(ctx, launch_order_to_i64(d_order, n, order, ctx->stream));
+  } else {
+    // stage through the key buffer the sort is not holding its result in (n * 8 bytes)
+    int64_t* tmp = reinterpret_cast<int64_t*>(d_order == ctx->sort.vals[0] ? ctx->sort.keys[1]
+                                                                            : ctx->sort.keys[0]);
+    CUDA_TRY(ctx, launch_order_to_i64(d_order, n, tmp, ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(order, tmp, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return ARA_OK;
+}
+
+// ---- verification trace ------------------------------------------------------------------------
+ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                          int64_t max_hits, int32_t* hit_trial, int32_t* hit_k, int32_t* hit_j,
+                          int32_t* hit_rec, float* hit_u, float* hit_x, float* hit_loss,
+                          double* ylt, int64_t* n_hits) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  ara_status s = check_run_args(ctx, yet, layer, t0, n);
+  if (s != ARA_OK) return s;
+  if (!n_hits || max_hits < 0 || (max_hits > 0 && (!hit_trial || !hit_k || !hit_j || !hit_rec ||
+                                                     !hit_u || !hit_x || !hit_loss)) || !ylt)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "NULL trace buffer");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const YetDev& Y = ctx->yets[yet];
+  const LayerDev& L = ctx->layers[layer];
+  const int64_t cap = std::max<int64_t>(1, Y.max_len * L.n_slots);
+  const int64_t total = n * cap;
+  if (total > ((int64_t)1 << 27)) return fail(ctx, ARA_ERR_INVALID_ARG, "trace too large");
+  if (n == 0) {
+    *n_hits = 0;
+    return ARA_OK;
+  }
+  int32_t *d_k = nullptr, *d_j = nullptr, *d_rec = nullptr, *d_cnt = nullptr;
+  float *d_u = nullptr, *d_x = nullptr, *d_loss = nullptr;
+  double* d_ylt = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(d_k); dev_free(d_j); dev_free(d_rec); dev_free(d_cnt);
+    dev_free(d_u); dev_free(d_x); dev_free(d_loss); dev_free(d_ylt);
+  };
+  cudaError_t e;
+  if ((e = dev_alloc(&d_k, total)) != cudaSuccess || (e = dev_alloc(&d_j, total)) != cudaSuccess ||
+      (e = dev_alloc(&d_rec, total)) != cudaSuccess || (e = dev_alloc(&d_cnt, n)) != cudaSuccess ||
+      (e = dev_alloc(&d_u, total)) != cudaSuccess || (e = dev_alloc(&d_x, total)) != cudaSuccess ||
+      (e = dev_alloc(&d_loss, total)) != cudaSuccess || (e = dev_alloc(&d_ylt, n)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, ARA_ERR_OOM, "trace buffers: %s", cudaGetErrorString(e));
+  }
+  TrialParams p = make_params(ctx, Y, L, t0, n, d_ylt);
+  p.trace_cap = cap;
+  p.tr_k = d_k; p.tr_j = d_j; p.tr_rec = d_rec; p.tr_u = d_u; p.tr_x = d_x; p.tr_loss = d_loss;
+  p.tr_count = d_cnt;
+  std::vector<int32_t> cnt(n), k(total), j(total), rec(total);
+  std::vector<float> u(total), x(total), loss(total);
+  e = launch_trial(p, L.mask_words, ARA_ACC_FP64, true, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(k.data(), d_k, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(j.data(), d_j, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rec.data(), d_rec, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u.data(), d_u, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x.data(), d_x, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loss.data(), d_loss, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, ARA_ERR_CUDA, "trace: %s", cudaGetErrorString(e));
+  }
+  int64_t h = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    for (int32_t q = 0; q < cnt[t] && q < cap; ++q) {
+      if (h < max_hits) {
+        const int64_t o = t * cap + q;
+        hit_trial[h] = (int32_t)t;
+        hit_k[h] = k[o];
+        hit_j[h] = j[o];
+        hit_rec[h] = rec[o];
+        hit_u[h] = u[o];
+        hit_x[h] = x[o];
+        hit_loss[h] = loss[o];
+      }
+      ++h;
+    }
+  }
+  *n_hits = h;
+  return ARA_OK;
+}
+
+}  // extern "C"

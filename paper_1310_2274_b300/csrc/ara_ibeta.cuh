@@ -1,0 +1,211 @@
+// ara_ibeta.cuh -- FP32 inverse of the regularised incomplete beta function, for one lane.
+//
+// Paper §3.3: Loss = max_l * InvCDF_beta(z; alpha, beta), where InvCDF_beta is the functional
+// inverse of I_x(alpha, beta) = B(x; alpha, beta) / B(alpha, beta).  This is the time sink of
+// the method (paper §5.1: most of the secondary-uncertainty time is spent in it).
+//
+// Formulation (chosen for SIMT execution in binary32):
+//   * Per-record constants are computed once, in FP64, when an ELT is staged: alpha, beta and
+//       L0 = alpha ln x0 + beta ln y0 - ln B(alpha, beta),   x0 = alpha/(alpha+beta), y0 = 1-x0.
+//     With them the beta prefactor x^a y^b / B(a,b) = exp(L0 + a ln(x/x0) + b ln(y/y0)), whose
+//     exponent is O(1) near the bulk of the distribution, so binary32 keeps it accurate without
+//     any per-hit lgamma (the cancellation of large log-gamma values happens once, in FP64).
+//   * I_x(a,b) = prefactor * K / a with K the continued fraction of DLMF 8.17.22, evaluated
+//     back-to-front-free by the forward (Wallis) three-term recurrence after an equivalence
+//     transformation that clears every division: partial numerators
+//       alpha_1 = -(a+b) x,  alpha_{2m+1} = -(a+m)(a+b+m) x,  alpha_{2m} = m(b-m) x,
+//     partial denominators a+n.  Numerator and denominator are rescaled by exact powers of two.
+//     Past x = (a+1)/(a+b+2) the symmetric fraction for I_{1-x}(b,a) is used (DLMF 8.17.4).
+//   * The root of I_x = p is found by Newton's method in t = ln x from a start given by the
+//     small-x limit of DLMF 8.17.22 or, for a, b > 1, by the normal approximation of
+//     Abramowitz & Stegun 26.5.22 with the normal quantile of A&S 26.2.23.  The tail below the
+//     mean is always the one solved (the other through 1 - u, exact on the uniform grid).
+//   * Iterations are capped; a lane that reaches the cap reports it (no trap, no spin).
+#pragma once
+
+#ifndef ARA_HD
+#ifdef __CUDACC__
+#define ARA_HD __host__ __device__ __forceinline__
+#else
+#include <cmath>
+#define ARA_HD inline
+#endif
+#endif
+
+#include <stdint.h>
+
+namespace ara {
+
+struct IbetaResult {
+  float x;        // quantile in [0,1]
+  int iters;      // Newton iterations used
+  int cf_terms;   // continued-fraction terms summed
+  bool converged;
+};
+
+constexpr int kIbetaMaxIter = 12;
+constexpr int kCfMaxTerms = 160;
+
+// Multiply by 2^-e exactly, e taken from the exponent field of s (s finite, nonzero).
+ARA_HD float ara_pow2_scale_of(float s) {
+#ifdef __CUDA_ARCH__
+  int bits = __float_as_int(s);
+#else
+  int bits;
+  memcpy(&bits, &s, 4);
+#endif
+  int e = ((bits >> 23) & 0xFF) - 127;
+  int sb = (127 - e) << 23;  // 2^-e as binary32 (e in [-126, 127])
+  float r;
+#ifdef __CUDA_ARCH__
+  r = __int_as_float(sb);
+#else
+  memcpy(&r, &sb, 4);
+#endif
+  return r;
+}
+
+// K(a,b,x) = 1/(1 + d1/(1 + d2/(...))) of DLMF 8.17.22 by the Wallis recurrence on the
+// division-free equivalent fraction T = 1 + alpha_1/(beta_1 + alpha_2/(beta_2 + ...)), K = 1/T.
+// Converges quickly for x < (a+1)/(a+b+2).  Returns K; *terms counts recurrence steps.
+ARA_HD float ara_beta_cf(float a, float b, float x, int* terms) {
+  const float apb = a + b;
+  // T_n = A_n / B_n.  A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1.
+  float Am2 = 1.0f, Am1 = 1.0f, Bm2 = 0.0f, Bm1 = 1.0f;
+  float prev = 1.0f;
+  float res = 1.0f;
+  int n = 1;
+  for (; n <= kCfMaxTerms; n += 2) {
+    // odd step n = 2m+1: alpha = -(a+m)(a+b+m) x  (alpha_1 = -(a+b) x: the a cancels)
+    const float m = 0.5f * (float)(n - 1);
+    const float al_odd = (n == 1) ? -apb * x : -(a + m) * (apb + m) * x;
+    const float be_odd = a + (float)n;
+    float A = be_odd * Am1 + al_odd * Am2;
+    float B = be_odd * Bm1 + al_odd * Bm2;
+    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
+    // even step n+1 = 2(m+1): alpha = (m+1)(b-m-1) x
+    const float m2 = m + 1.0f;
+    const float al_even = m2 * (b - m2) * x;
+    const float be_even = a + (float)(n + 1);
+    A = be_even * Am1 + al_even * Am2;
+    B = be_even * Bm1 + al_even * Bm2;
+    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
+    // exact power-of-two rescale keeps the recurrence inside binary32 range
+    const float sc = ara_pow2_scale_of(Am1);
+    Am1 *= sc; Am2 *= sc; Bm1 *= sc; Bm2 *= sc;
+    if (((n + 1) & 3) == 0 || n + 2 > kCfMaxTerms) {
+      res = Bm1 / Am1;
+      if (fabsf(res - prev) <= 1.2e-7f * fabsf(res)) { n += 2; break; }
+      prev = res;
+    }
+  }
+  if (terms) *terms += n - 1;
+  return res;
+}
+
+// Normal quantile for the upper tail probability q in (0, 1/2]: the deviate t with
+// Q(t) = q, by the rational approximation A&S 26.2.23 (|error| < 4.5e-4).  Used only for a start.
+ARA_HD float ara_norm_upper_quantile(float q) {
+  const float t = sqrtf(-2.0f * logf(q));
+  const float num = 2.515517f + t * (0.802853f + t * 0.010328f);
+  const float den = 1.0f + t * (1.432788f + t * (0.189269f + t * 0.001308f));
+  return t - num / den;
+}
+
+// One ELT record as the device uses it (32 bytes, one L2 sector).  All fields are derived once
+// per record, in FP64, from (mean, sd, max) when an ELT is staged (paper §3.3):
+//   a, b   alpha and beta of the moment-matched beta distribution (sd clamped as in §3.3);
+//          a = 0 marks a record with sd = 0, whose loss is the mean (primary uncertainty only);
+//   mx     max_l, the scale of the loss (for a = 0: the mean itself);
+//   L0     a ln x0 + b ln y0 - ln B(a,b), x0 = a/(a+b), y0 = b/(a+b) (symmetric in a, b);
+//   p0     I_{x0}(a,b), the probability below the mean: u <= p0 puts the root below x0;
+//   lnx0, lny0, lns   ln x0, ln y0, ln(a+b).
+struct BetaRec {
+  float a, b, mx, L0;
+  float p0, lnx0, lny0, lns;
+};
+
+// Solve I_x(a,b) = u for x, x in [0,1].
+//
+// Newton's method on G(t) = ln I_{e^t}(a,b) - ln p in t = ln x.  Below the threshold
+// x = (a+1)/(a+b+2), I_x = P K / a with P the prefactor, so G = E + ln(K/a) - ln p and
+// G'(t) = x f(x) / I_x = a / ((1-x) K): no exponential is needed.  In the lower tail G is nearly
+// linear in t (I_x ~ x^a), which is where Newton in x fails for a < 1.
+//
+// The tail is chosen per record: if u > p0 the root lies above the mean, and the symmetric
+// problem I_y(b,a) = 1 - u (exact on the uniform grid) is solved for y = 1 - x instead, so the
+// unknown solved for is always below the mean of its distribution.
+ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
+  IbetaResult r;
+  r.iters = 0;
+  r.cf_terms = 0;
+  r.converged = true;
+  const bool flip = u > rec.p0;
+  const float p = flip ? 1.0f - u : u;
+  const float a = flip ? rec.b : rec.a;
+  const float b = flip ? rec.a : rec.b;
+  const float lnx0 = flip ? rec.lny0 : rec.lnx0;
+  const float lny0 = flip ? rec.lnx0 : rec.lny0;
+  const float L0 = rec.L0;
+  const float s = a + b;
+  const float lna = lnx0 + rec.lns;
+  const float lnp = logf(p);
+
+  // ---- start --------------------------------------------------------------------------------
+  // small-x limit of DLMF 8.17.22 (K -> 1, y -> 1): ln p = L0 + a ln(x/x0) - b ln y0 - ln a
+  float t = lnx0 + (lnp + lna - L0 + b * lny0) / a;
+  if (a > 1.0f && b > 1.0f) {
+    // A&S 26.5.22: x ~ a / (a + b e^{2w}), with yp the upper-tail normal deviate of p.
+    const float yp = ara_norm_upper_quantile(fminf(p, 0.5f));
+    const float ypl = p > 0.5f ? -ara_norm_upper_quantile(1.0f - p) : yp;
+    const float lam = (ypl * ypl - 3.0f) / 6.0f;
+    const float h = 2.0f / (1.0f / (2.0f * a - 1.0f) + 1.0f / (2.0f * b - 1.0f));
+    const float w = ypl * sqrtf(fmaxf(h + lam, 0.0f)) / h -
+                    (1.0f / (2.0f * b - 1.0f) - 1.0f / (2.0f * a - 1.0f)) *
+                        (lam + 5.0f / 6.0f - 2.0f / (3.0f * h));
+    t = lna - logf(a + b * expf(2.0f * w));
+  }
+  t = fminf(t, lnx0);  // the root is below the mean
+  // Below e^-69 ~ 1e-30 the loss max_l * x is far under every term of a year loss.
+  if (!(t > -69.0f)) { r.x = flip ? 1.0f : 0.0f; return r; }
+
+  // ---- Newton iterations in t ---------------------------------------------------------------
+  const float thr = (a + 1.0f) / (s + 2.0f);
+  bool done = false;
+  int it = 0;
+  float x = expf(t);
+  for (; it < kIbetaMaxIter; ++it) {
+    const float y = 1.0f - x;
+    // E = ln(x^a y^b / B(a,b)) = L0 + a ln(x/x0) + b ln(y/y0), w = (x - x0)(a + b)
+    const float w = fmaf(x, s, -a);
+    const float rx = w / a;   // x/x0 - 1
+    const float ry = -w / b;  // y/y0 - 1
+    const float lnrx = rx > -0.5f ? log1pf(rx) : t - lnx0;
+    const float lnry = ry > -0.5f ? log1pf(ry) : logf(y) - lny0;
+    const float E = L0 + a * lnrx + b * lnry;
+    float G, dG;
+    if (x < thr) {
+      const float K = ara_beta_cf(a, b, x, &r.cf_terms);
+      G = E + logf(K) - lna - lnp;
+      dG = a / (y * K);
+    } else {
+      const float P = expf(E);
+      const float J = P * ara_beta_cf(b, a, y, &r.cf_terms) / b;  // I_{1-x}(b,a)
+      G = log1pf(-J) - lnp;
+      dG = P / (y * (1.0f - J));
+    }
+    float tn = t - G / dG;
+    if (!(tn < 0.0f)) tn = 0.5f * t;  // a step past x = 1 is halved toward it
+    const float step = fabsf(tn - t);
+    t = tn;
+    x = expf(t);
+    if (step <= 3.0e-5f) { done = true; ++it; break; }
+    if (!(t > -69.0f)) { done = true; ++it; x = 0.0f; break; }
+  }
+  r.iters = it;
+  r.converged = done;
+  r.x = flip ? 1.0f - x : x;
+  return r;
+}
+
+}  // namespace ara

@@ -1,0 +1,124 @@
+// ara_internal.h -- device data structures and kernel launchers shared by libara's sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ara_ibeta.cuh"
+
+namespace ara {
+
+constexpr int kMaxLayerElts = 64;
+
+// Year Event Table on the device: trial-major event ids and timestamps (paper §2.1).
+struct YetDev {
+  bool live = false;
+  int64_t n_trials = 0;
+  int64_t n_occ = 0;
+  int32_t catalog = 0;
+  int64_t max_len = 0;       // longest trial
+  int32_t* ids = nullptr;    // [n_occ]
+  float* ts = nullptr;       // [n_occ]
+  int64_t* offsets = nullptr;  // [n_trials + 1]
+};
+
+// One staged ELT: event ids and the derived per-record constants, in the caller's order.
+struct EltDev {
+  bool live = false;
+  int32_t yet = -1;
+  int64_t n = 0;
+  int32_t* ids = nullptr;    // [n]
+  BetaRec* recs = nullptr;   // [n]
+};
+
+// A layer: lookup structure over the YET's catalogue plus its terms (paper §2.1, §2.3).
+// evt[e] holds (base, mask words...): the records of event e in the layer's ELTs are
+// packed[base + r], r = rank of the ELT's slot bit among the set bits of the mask.
+struct LayerDev {
+  bool live = false;
+  int32_t yet = -1;
+  int32_t n_slots = 0;
+  int32_t mask_words = 1;          // 1 (<= 32 ELTs) or 2 (<= 64)
+  int32_t handles[kMaxLayerElts];  // global ELT handle per slot (keys the uniforms)
+  double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
+  uint32_t* evt = nullptr;         // [catalog * (1 + mask_words)] entries, padded to 2 or 4 words
+  BetaRec* packed = nullptr;       // [n_packed]
+  uint32_t* packed_rec = nullptr;  // [n_packed] caller record index (verification)
+  int64_t n_packed = 0;
+};
+
+// Parameters of one trial-kernel launch.
+struct TrialParams {
+  const int32_t* ids;
+  const int64_t* offsets;
+  const uint32_t* evt;
+  const BetaRec* recs;
+  const uint32_t* rec_idx;
+  int32_t handles[kMaxLayerElts];
+  int32_t n_slots;
+  float occ_ret, occ_lim;
+  double agg_ret, agg_lim;
+  uint64_t seed;
+  int64_t t0, n;
+  double* ylt;
+  unsigned long long* not_conv;
+  // verification trace (TRACE instantiation only)
+  int64_t trace_cap;  // hits per trial slot in the trace buffers
+  int32_t* tr_k;
+  int32_t* tr_j;
+  int32_t* tr_rec;
+  float* tr_u;
+  float* tr_x;
+  float* tr_loss;
+  int32_t* tr_count;  // [n]
+};
+
+// ---- launchers (each returns the launch's cudaError_t) ---------------------------------------
+cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st);
+cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
+                               const double* sd, const double* mx, int32_t catalog,
+                               BetaRec* recs, unsigned int* d_dup, unsigned int* d_flags,
+                               cudaStream_t st);
+cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
+                              cudaStream_t st);
+cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,
+                                uint32_t* d_cnt, cudaStream_t st);
+cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n,
+                                      uint32_t* d_tmp, int64_t tmp_words, cudaStream_t st);
+int64_t scan_tmp_words(int64_t n);
+cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, int mask_words,
+                               int64_t catalog, uint32_t* d_evt, cudaStream_t st);
+cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
+                                 const uint32_t* d_evt, BetaRec* packed, uint32_t* packed_rec,
+                                 cudaStream_t st);
+cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, bool trace,
+                         cudaStream_t st);
+
+// Radix sort of binary64 year losses (descending, ties by index) and tail sums.
+struct SortScratch {
+  uint64_t* keys[2] = {nullptr, nullptr};
+  uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* hist = nullptr;       // [256 * tiles]
+  uint32_t* scan_tmp = nullptr;
+  uint32_t* digit_flags = nullptr;  // [8 passes * 2]
+  int64_t cap = 0;                // elements
+  int64_t hist_cap = 0;
+  int64_t scan_cap = 0;
+};
+int64_t sort_tiles(int64_t n);
+// Sorts ylt[n] (device) -> the permutation is left in vals[result_buf]; returns that index via
+// *which.  Uses the scratch buffers only.
+cudaError_t sort_ylt_desc(const double* d_ylt, int64_t n, SortScratch& s, int* which,
+                          cudaStream_t st);
+cudaError_t launch_tail_sums(const double* d_ylt, const uint32_t* d_order, int64_t n,
+                             const int64_t* d_k, int32_t m, double* d_pml, double* d_tvar,
+                             cudaStream_t st);
+cudaError_t launch_order_to_i64(const uint32_t* d_order, int64_t n, int64_t* d_out,
+                                cudaStream_t st);
+cudaError_t launch_check_nan(const double* d_ylt, int64_t n, unsigned int* d_flag,
+                             cudaStream_t st);
+
+}  // namespace ara

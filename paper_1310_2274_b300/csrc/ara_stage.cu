@@ -1,0 +1,345 @@
+// ara_stage.cu -- staging kernels: YET validation, ELT record preparation, layer lookup build.
+//
+// The paper's preprocessing stage (§2.2) loads YET, XELTs and portfolio into memory; its §4.1
+// chooses a direct-access table over compact forms for lookup speed.  A dense direct-access
+// table of 16 ELTs over a 2,000,000-event catalogue would be 16x larger than the L2 cache, so
+// here each layer gets one compact direct-access entry per catalogue event (record base + ELT bit
+// mask, 8 or 16 bytes) and the event's records packed contiguously in layer order: one random
+// read per occurrence plus one 32-byte sector per hit, all L2-resident at paper scale.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ara_internal.h"
+
+namespace ara {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int per_block = kThreads) {
+  int64_t g = (n + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > 0x7FFFFFFF) g = 0x7FFFFFFF;
+  return (unsigned)g;
+}
+
+// ---- YET validation (warp per trial) ----------------------------------------------------------
+// flags bit 0: id out of range; bit 1: timestamp decreases within a trial; bit 2: NaN timestamp.
+__global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float* __restrict__ ts,
+                                    const int64_t* __restrict__ off, int64_t n_trials,
+                                    int32_t catalog, unsigned int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned int f = 0;
+  for (int64_t i = warp; i < n_trials; i += nwarps) {
+    const int64_t beg = off[i], end = off[i + 1];
+    for (int64_t q = beg + lane; q < end; q += 32) {
+      const int32_t e = ids[q];
+      if (e < 0 || e >= catalog) f |= 1u;
+      const float t = ts[q];
+      if (t != t) f |= 4u;
+      if (q > beg && t < ts[q - 1]) f |= 2u;
+    }
+  }
+  f = __reduce_or_sync(0xFFFFFFFFu, f);
+  if (lane == 0 && f) atomicOr(flags, f);
+}
+
+// ---- ELT record preparation (FP64, once per record) --------------------------------------------
+
+// K = 1/(1 + d1/(1 + ...)) of DLMF 8.17.22 in binary64 by the Wallis recurrence of the
+// division-free equivalent fraction (partial numerators -(a+b)x, -(a+m)(a+b+m)x, m(b-m)x;
+// denominators a+n), rescaled by powers of two.
+__device__ double beta_cf_f64(double a, double b, double x) {
+  const double apb = a + b;
+  double Am2 = 1.0, Am1 = 1.0, Bm2 = 0.0, Bm1 = 1.0, prev = 1.0, res = 1.0;
+  for (int n = 1; n < 4000; n += 2) {
+    const double m = 0.5 * (double)(n - 1);
+    const double al_odd = (n == 1) ? -apb * x : -(a + m) * (apb + m) * x;
+    const double be_odd = a + (double)n;
+    double A = be_odd * Am1 + al_odd * Am2;
+    double B = be_odd * Bm1 + al_odd * Bm2;
+    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
+    const double m2 = m + 1.0;
+    const double al_even = m2 * (b - m2) * x;
+    const double be_even = a + (double)(n + 1);
+    A = be_even * Am1 + al_even * Am2;
+    B = be_even * Bm1 + al_even * Bm2;
+    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
+    int e;
+    frexp(Am1, &e);
+    Am1 = ldexp(Am1, -e); Am2 = ldexp(Am2, -e); Bm1 = ldexp(Bm1, -e); Bm2 = ldexp(Bm2, -e);
+    res = Bm1 / Am1;
+    if (fabs(res - prev) <= 1e-15 * fabs(res)) break;
+    prev = res;
+  }
+  return res;
+}
+
+// I_x(a,b) in binary64 (DLMF 8.17.22, with the symmetry DLMF 8.17.4 past (a+1)/(a+b+2)).
+__device__ double betainc_f64(double a, double b, double x) {
+  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
+  if (x < (a + 1.0) / (a + b + 2.0)) {
+    return exp(a * log(x) + b * log1p(-x) - lnB) * beta_cf_f64(a, b, x) / a;
+  }
+  const double y = 1.0 - x;
+  return 1.0 - exp(b * log(y) + a * log1p(-y) - lnB) * beta_cf_f64(b, a, y) / b;
+}
+
+// flags bit 3: id out of range; bit 4: mean <= 0 or sd < 0 or non-finite; bit 5: max <= mean
+// with sd > 0; dup[e] counts records per event (a count above one is a duplicate, bit 6).
+__global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
+                                   const double* __restrict__ mean, const double* __restrict__ sd,
+                                   const double* __restrict__ mx, int32_t catalog,
+                                   BetaRec* __restrict__ recs, unsigned int* dup,
+                                   unsigned int* flags) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  unsigned int f = 0;
+  const int32_t e = ids[r];
+  if (e < 0 || e >= catalog) {
+    f |= 8u;
+  } else if (atomicAdd(&dup[e], 1u) != 0u) {
+    f |= 64u;
+  }
+  const double mu = mean[r], sigma = sd[r], m = mx[r];
+  BetaRec rec;
+  rec.a = 0.f; rec.b = 0.f; rec.mx = (float)mu; rec.L0 = 0.f;
+  rec.p0 = 0.5f; rec.lnx0 = 0.f; rec.lny0 = 0.f; rec.lns = 0.f;
+  if (!(mu > 0.0) || !(sigma >= 0.0) || !isfinite(mu) || !isfinite(sigma)) {
+    f |= 16u;
+  } else if (sigma > 0.0) {
+    if (!(m > mu) || !isfinite(m)) {
+      f |= 32u;
+    } else {
+      // paper §3.3: sigma_beta = sigma/max, mu_beta = mu/max, clamp, alpha, beta
+      const double mu_b = mu / m;
+      double sig_b = sigma / m;
+      const double sig_max = sqrt(mu_b * (1.0 - mu_b));
+      if (sig_b > sig_max) sig_b = sig_max * (1.0 - 0x1p-20);
+      const double rr = sig_max / sig_b;
+      const double k = rr * rr - 1.0;
+      const double a = mu_b * k, b = (1.0 - mu_b) * k;
+      const double s = a + b;
+      const double lnx0 = log(a / s), lny0 = log(b / s);
+      const double lnB = lgamma(a) + lgamma(b) - lgamma(s);
+      rec.a = (float)a;
+      rec.b = (float)b;
+      rec.mx = (float)m;
+      rec.L0 = (float)(a * lnx0 + b * lny0 - lnB);
+      rec.p0 = (float)betainc_f64(a, b, a / s);
+      rec.lnx0 = (float)lnx0;
+      rec.lny0 = (float)lny0;
+      rec.lns = (float)log(s);
+      if (!(rec.a > 0.f) || !(rec.b > 0.f)) f |= 16u;  // alpha or beta outside binary32 range
+    }
+  }
+  recs[r] = rec;
+  if (f) atomicOr(flags, f);
+}
+
+// ---- layer lookup structure ----------------------------------------------------------------------
+__global__ void layer_mask_kernel(int64_t n, const int32_t* __restrict__ ids, int slot,
+                                  int mask_words, uint32_t* mask) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int32_t e = ids[r];
+  atomicOr(&mask[(int64_t)e * mask_words + (slot >> 5)], 1u << (slot & 31));
+}
+
+__global__ void layer_counts_kernel(const uint32_t* __restrict__ mask, int mask_words,
+                                    int64_t catalog, uint32_t* cnt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= catalog) return;
+  uint32_t c = __popc(mask[e * mask_words]);
+  if (mask_words == 2) c += __popc(mask[e * mask_words + 1]);
+  cnt[e] = c;
+}
+
+// Entry layout: mask_words == 1 -> (base, mask) 8 bytes; == 2 -> (base, mask_lo, mask_hi, 0).
+__global__ void layer_index_kernel(const uint32_t* __restrict__ mask,
+                                   const uint32_t* __restrict__ base, int mask_words,
+                                   int64_t catalog, uint32_t* evt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= catalog) return;
+  if (mask_words == 1) {
+    reinterpret_cast<uint2*>(evt)[e] = make_uint2(base[e], mask[e]);
+  } else {
+    reinterpret_cast<uint4*>(evt)[e] = make_uint4(base[e], mask[2 * e], mask[2 * e + 1], 0u);
+  }
+}
+
+__global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
+                                     const BetaRec* __restrict__ recs, int slot, int mask_words,
+                                     const uint32_t* __restrict__ evt, BetaRec* packed,
+                                     uint32_t* packed_rec) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int64_t e = ids[r];
+  uint32_t base, rank;
+  if (mask_words == 1) {
+    const uint2 v = reinterpret_cast<const uint2*>(evt)[e];
+    base = v.x;
+    rank = __popc(v.y & ((1u << slot) - 1u));
+  } else {
+    const uint4 v = reinterpret_cast<const uint4*>(evt)[e];
+    base = v.x;
+    const uint64_t m = ((uint64_t)v.z << 32) | v.y;
+    rank = __popcll(m & ((1ull << slot) - 1ull));
+  }
+  packed[base + rank] = recs[r];
+  packed_rec[base + rank] = (uint32_t)r;
+}
+
+// ---- exclusive scan of uint32 (three passes: block sums, scan of sums, block scans) ----------
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 8;  // per thread
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive prefix, *total = sum.
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_incl_scan(v);
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t s = lane < nw ? warp_sums[lane] : 0u;
+    s = warp_incl_scan(s);
+    if (lane < nw) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t warp_excl = warp == 0 ? 0u : warp_sums[warp - 1];
+  *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_excl + incl - v;
+}
+
+__global__ void scan_tile_sums_kernel(const uint32_t* __restrict__ in, int64_t n,
+                                      uint32_t* sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t q = base + (int64_t)k * kScanBlock + threadIdx.x;
+    if (q < n) s += in[q];
+  }
+  uint32_t total;
+  block_excl_scan(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_kernel(uint32_t* sums, int64_t n_tiles) {
+  // one block: exclusive scan of the tile sums in chunks of blockDim
+  uint32_t carry = 0;
+  for (int64_t c = 0; c < n_tiles; c += blockDim.x) {
+    const int64_t q = c + threadIdx.x;
+    const uint32_t v = q < n_tiles ? sums[q] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(v, &total);
+    if (q < n_tiles) sums[q] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void scan_tiles_kernel(const uint32_t* __restrict__ in, int64_t n,
+                                  const uint32_t* __restrict__ sums, uint32_t* out) {
+  // each thread owns kScanItems consecutive elements of the tile
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t q = base + k;
+    v[k] = q < n ? in[q] : 0u;
+    s += v[k];
+  }
+  uint32_t total;
+  uint32_t ex = block_excl_scan(s, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t q = base + k;
+    if (q < n) out[q] = ex;
+    ex += v[k];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st) {
+  if (y.n_trials == 0) return cudaSuccess;
+  int64_t warps = y.n_trials;
+  int64_t blocks = (warps * 32 + kThreads - 1) / kThreads;
+  if (blocks > 148 * 64) blocks = 148 * 64;
+  validate_yet_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(y.ids, y.ts, y.offsets, y.n_trials,
+                                                              y.catalog, d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
+                               const double* sd, const double* mx, int32_t catalog,
+                               BetaRec* recs, unsigned int* d_dup, unsigned int* d_flags,
+                               cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, mx, catalog, recs,
+                                                       d_dup, d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
+                              cudaStream_t st) {
+  if (e.n == 0) return cudaSuccess;
+  layer_mask_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, slot, mask_words, d_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,
+                                uint32_t* d_cnt, cudaStream_t st) {
+  layer_counts_kernel<<<grid_for(catalog), kThreads, 0, st>>>(d_mask, mask_words, catalog, d_cnt);
+  return cudaGetLastError();
+}
+
+int64_t scan_tmp_words(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n,
+                                      uint32_t* d_tmp, int64_t tmp_words, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles > tmp_words) return cudaErrorInvalidValue;
+  scan_tile_sums_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, n, d_tmp);
+  scan_sums_kernel<<<1, kScanBlock, 0, st>>>(d_tmp, tiles);
+  scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, n, d_tmp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, int mask_words,
+                               int64_t catalog, uint32_t* d_evt, cudaStream_t st) {
+  layer_index_kernel<<<grid_for(catalog), kThreads, 0, st>>>(d_mask, d_base, mask_words, catalog,
+                                                             d_evt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
+                                 const uint32_t* d_evt, BetaRec* packed, uint32_t* packed_rec,
+                                 cudaStream_t st) {
+  if (e.n == 0) return cudaSuccess;
+  layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, slot, mask_words,
+                                                           d_evt, packed, packed_rec);
+  return cudaGetLastError();
+}
+
+}  // namespace ara

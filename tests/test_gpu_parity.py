@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same inputs.
+
+Bars (from the method's statement of the hot path):
+  * event lookups, uniforms and the YLT ordering: bit-exact;
+  * year losses: |gpu - oracle| <= 1e-5 * max(|oracle|, AggR, 1)  (relative error 1e-5, measured
+    against the aggregate retention where the year loss is a small difference near it);
+  * PML / TVaR: relative error 1e-6.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1310_2274_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+YLT_TOL = 1e-5
+RISK_TOL = 1e-6
+
+
+def ylt_close(g, o, terms):
+    scale = np.maximum(np.maximum(np.abs(o), terms.agg_ret), 1.0)
+    err = np.abs(g - o) / scale
+    return err.max(initial=0.0), err
+
+
+@pytest.fixture(scope="module")
+def ctx(ara):
+    c = ara.Context(seed=42)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tiny(ctx):
+    w = synth.tiny()
+    yet, elts, layer = ctx.stage_workload(w)
+    return w, yet, elts, layer
+
+
+def test_tiny_ylt_matches_oracle(ctx, oracle, tiny):
+    w, yet, elts, layer = tiny
+    g = ctx.run(yet, layer, 0, w.yet.n_trials)
+    o, nc = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
+    assert nc == 0
+    worst, _ = ylt_close(g, o, w.terms)
+    assert worst <= YLT_TOL, worst
+    assert np.all(g >= 0) and np.all(g <= w.terms.agg_lim)
+    assert np.count_nonzero(o) > 100  # the terms leave a non-trivial YLT
+
+
+def test_tiny_trace_bit_exact_lookups_and_uniforms(ctx, oracle, tiny):
+    w, yet, elts, layer = tiny
+    trials = np.arange(200)
+    gh, gy = ctx.trace(yet, layer, 0, 200)
+    oh, oy = oracle.trace(w.yet, w.elts, w.terms, 42, trials, elt_handles=elts)
+    assert gh["trial"].shape == oh["trial"].shape and gh["trial"].size > 1000
+    np.testing.assert_array_equal(gh["trial"], oh["trial"])
+    np.testing.assert_array_equal(gh["k"], oh["k"])
+    np.testing.assert_array_equal(gh["j"], oh["j"])
+    np.testing.assert_array_equal(gh["rec"], oh["rec"])
+    # uniforms: binary32 on the device, binary64 in the oracle, identical values
+    np.testing.assert_array_equal(gh["u"].astype(np.float64), oh["u"])
+    # beta quantiles: FP32 inversion against the FP64 oracle
+    dx = np.abs(gh["x"].astype(np.float64) - oh["x"])
+    assert dx.max() <= 1e-5
+    big = oh["x"] > 1e-6
+    assert (dx[big] / oh["x"][big]).max() <= 1e-4
+    # the trace run is the production kernel: same year losses as ara_run
+    np.testing.assert_array_equal(gy, ctx.run(yet, layer, 0, 200))
+
+
+def test_tiny_risk_measures_end_to_end(ctx, oracle, tiny):
+    w, yet, elts, layer = tiny
+    g = ctx.run(yet, layer, 0, w.yet.n_trials)
+    o, _ = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
+    gp, gt = ctx.risk_measures(g, w.rps)
+    op, ot = oracle.risk(o, w.rps)
+    np.testing.assert_allclose(gp, op, rtol=RISK_TOL)
+    np.testing.assert_allclose(gt, ot, rtol=RISK_TOL)
+
+
+@pytest.mark.parametrize("kind", ["oracle_ylt", "ties", "random_1e5", "constant", "single"])
+def test_rank_and_risk_on_identical_ylt(ctx, oracle, kind):
+    rng = np.random.default_rng(4)
+    if kind == "oracle_ylt":
+        w = synth.tiny(600)
+        y, _ = oracle.run(w.yet, w.elts, w.terms, 42)
+    elif kind == "ties":
+        y = rng.choice([0.0, 5e7, 1.25e6, 3.0], size=5000)
+    elif kind == "random_1e5":
+        y = np.maximum(rng.lognormal(17, 1.3, 100_000) - 3e7, 0.0)
+    elif kind == "constant":
+        y = np.full(777, 2.5)
+    else:
+        y = np.array([42.0])
+    order_g = ctx.rank(y)
+    order_o = oracle.rank(y)
+    np.testing.assert_array_equal(order_g, order_o)
+    rps = [1.5, 10.0, 100.0, 250.0, 500.0, 1000.0]
+    gp, gt = ctx.risk_measures(y, rps)
+    op, ot = oracle.risk(y, rps)
+    np.testing.assert_array_equal(gp, op)
+    np.testing.assert_allclose(gt, ot, rtol=1e-13)
+
+
+def test_rank_from_device_memory(ctx, oracle):
+    import torch
+
+    y = np.random.default_rng(8).uniform(0, 1e6, 70_001)
+    yd = torch.from_numpy(y).cuda()
+    out = torch.empty(y.size, dtype=torch.int64, device="cuda")
+    ctx.rank(yd, out=out)
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.rank(y))
+
+
+def test_ragged_multi_elt_and_zero_sigma(ctx, oracle):
+    yet_h = synth.make_ragged_yet(400, 0, 300, 3000, seed=12)
+    elts_h = [synth.make_elt(n, 3000, seed=40 + s) for s, n in enumerate([900, 50, 1400])]
+    elts_h[1].sd[:] = 0.0  # primary uncertainty only for one ELT
+    elts_h[2].sd[::3] = 0.0
+    terms = synth.Terms(2e4, 5e6, 1e5, 3e7)
+    yet = ctx.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 3000)
+    elts = [ctx.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
+    layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+    g = ctx.run(yet, layer, 0, 400)
+    o, _ = oracle.run(yet_h, elts_h, terms, 42, elt_handles=elts)
+    worst, _ = ylt_close(g, o, terms)
+    assert worst <= YLT_TOL, worst
+    empty = np.diff(yet_h.offsets) == 0
+    assert empty.any() and np.all(g[empty] == 0.0)
+    gh, _ = ctx.trace(yet, layer, 0, 400)
+    oh, _ = oracle.trace(yet_h, elts_h, terms, 42, np.arange(400), elt_handles=elts)
+    for f in ("trial", "k", "j", "rec"):
+        np.testing.assert_array_equal(gh[f], oh[f])
+    sig0 = np.isnan(oh["x"])
+    assert sig0.any()
+    # sigma = 0 hits contribute the mean exactly (binary32 of a binary32-representable mean)
+    np.testing.assert_array_equal(gh["loss"][sig0].astype(np.float64), oh["loss"][sig0])
+
+
+def test_wide_layer_uses_two_mask_words(ctx, oracle):
+    yet_h = synth.make_yet(150, 120, 4000, seed=21)
+    elts_h = [synth.make_elt(150 + 7 * s, 4000, seed=100 + s) for s in range(40)]
+    terms = synth.Terms(1e5, 1e7, 5e5, 5e8)
+    yet = ctx.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 4000)
+    elts = [ctx.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
+    layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+    g = ctx.run(yet, layer, 0, 150)
+    o, _ = oracle.run(yet_h, elts_h, terms, 42, elt_handles=elts)
+    worst, _ = ylt_close(g, o, terms)
+    assert worst <= YLT_TOL, worst
+    gh, _ = ctx.trace(yet, layer, 0, 40)
+    oh, _ = oracle.trace(yet_h, elts_h, terms, 42, np.arange(40), elt_handles=elts)
+    for f in ("trial", "k", "j", "rec"):
+        np.testing.assert_array_equal(gh[f], oh[f])
+    assert gh["j"].max() >= 32
+
+
+def test_subranges_and_launch_independence(ctx, tiny):
+    w, yet, elts, layer = tiny
+    full = ctx.run(yet, layer, 0, w.yet.n_trials)
+    for t0, n in [(0, 1), (1, 7), (333, 100), (999, 1), (17, 983)]:
+        np.testing.assert_array_equal(ctx.run(yet, layer, t0, n), full[t0:t0 + n])
+
+
+def test_async_stream_into_device_tensor(ctx, tiny):
+    import torch
+
+    w, yet, elts, layer = tiny
+    ref = ctx.run(yet, layer, 0, w.yet.n_trials)
+    out = torch.zeros(w.yet.n_trials, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    ctx.run(yet, layer, 0, w.yet.n_trials, out=out, stream=s)
+    s.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    assert ctx.not_converged() == 0
+
+
+def test_seed_option_changes_draws(ara, tiny):
+    w = tiny[0]
+    with ara.Context(seed=7) as c7:
+        yet, elts, layer = c7.stage_workload(w)
+        a = c7.run(yet, layer, 0, 300)
+        c7.set_option(ara.OPT_SEED, 42)
+        b = c7.run(yet, layer, 0, 300)
+    with ara.Context(seed=42) as c42:
+        yet, elts, layer = c42.stage_workload(w)
+        np.testing.assert_array_equal(b, c42.run(yet, layer, 0, 300))
+    assert not np.array_equal(a, b)
+
+
+def test_kahan_accumulation_matches_fp64(ara, ctx, oracle, tiny):
+    w, yet, elts, layer = tiny
+    g64 = ctx.run(yet, layer, 0, w.yet.n_trials)
+    ctx.set_option(ara.OPT_PRECISION, ara.ACC_KAHAN32)
+    try:
+        gk = ctx.run(yet, layer, 0, w.yet.n_trials)
+    finally:
+        ctx.set_option(ara.OPT_PRECISION, ara.ACC_FP64)
+    o, _ = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
+    worst, _ = ylt_close(gk, o, w.terms)
+    assert worst <= YLT_TOL
+    assert np.max(np.abs(gk - g64) / np.maximum(g64, w.terms.agg_ret)) < 1e-6
+
+
+@pytest.mark.parametrize("bad", ["id_range", "ts_order", "ts_nan", "offsets"])
+def test_yet_validation(ara, ctx, bad):
+    yet = synth.make_yet(10, 20, 100, seed=3)
+    off, ids, ts = yet.offsets.copy(), yet.event_ids.copy(), yet.timestamps.copy()
+    if bad == "id_range":
+        ids[57] = 100
+    elif bad == "ts_order":
+        ts[45], ts[46] = ts[46] + 1.0, ts[45]
+    elif bad == "ts_nan":
+        ts[3] = np.nan
+    else:
+        off[4] = off[5] + 1
+    with pytest.raises(ara.AraError) as ei:
+        ctx.create_yet(off, ids, ts, 100)
+    assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("bad", ["dup", "range", "max_le_mean", "neg_mean"])
+def test_elt_validation(ara, ctx, bad):
+    y = synth.make_yet(4, 10, 50, seed=3)
+    yet = ctx.create_yet(y.offsets, y.event_ids, y.timestamps, y.catalog_size)
+    ids = np.arange(10, dtype=np.int32)
+    mean = np.full(10, 100.0)
+    sd = np.full(10, 30.0)
+    mx = np.full(10, 500.0)
+    if bad == "dup":
+        ids[3] = ids[4]
+    elif bad == "range":
+        ids[0] = 50
+    elif bad == "max_le_mean":
+        mx[2] = 100.0
+    else:
+        mean[1] = -1.0
+    with pytest.raises(ara.AraError) as ei:
+        ctx.add_elt(yet, ids, mean, sd, mx)
+    assert ei.value.status == 1
+
+
+def test_handle_and_range_errors(ara, ctx, tiny):
+    w, yet, elts, layer = tiny
+    with pytest.raises(ara.AraError) as ei:
+        ctx.run(yet, 999, 0, 10)
+    assert ei.value.status == 2
+    with pytest.raises(ara.AraError) as ei:
+        ctx.run(yet, layer, 990, 20)
+    assert ei.value.status == 1
+    with pytest.raises(ara.AraError):
+        ctx.add_layer([elts[0], elts[0]], 0, 1, 0, 1)
+    with pytest.raises(ara.AraError):
+        ctx.add_layer(elts, -1.0, 1, 0, 1)
+    with pytest.raises(ara.AraError):
+        ctx.risk_measures(np.array([1.0, np.nan]), [10.0])
+    with pytest.raises(ara.AraError):
+        ctx.risk_measures(np.array([1.0, 2.0]), [1.0])
