@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark: aggregate risk analysis with secondary uncertainty, paper-scale layer on B300.
+
+A step is one pass of the whole hot path over the workload resident in HBM: Algorithm 1 for
+800,000 trials x 1,000 events x 16 ELTs (ara_run -> YLT) followed by PML/TVaR at 1-in-100/250/
+500/1000 (ara_risk_measures).  The metric is trial-event-ELT evaluations per second,
+N * K * J / step time.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the paper's method written plainly) on bounded
+trial samples of the same workload, on this machine's host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_2274_b300 import synth  # noqa: E402
+
+METRIC = "trial-event-ELT evals/s"
+UNIT = "evals/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+FALLBACK_SM_MHZ = 2032.0
+
+# Algorithmic FP32 work of one launch, from the device algorithm's own trip counts (counted by
+# the kernel) and its per-block operation counts (+ - * / = 1 flop, fma = 2, each call of a
+# math-library function = 1):
+#   continued-fraction term (Wallis step, numerator/denominator, power-of-two rescale, every
+#     fourth term a convergence test)                                      14.25 flops
+#   Newton iteration in ln x (prefactor exponent, ln K, G, G', update)      17 flops + 4 calls
+#   per inversion (tail choice, small-x start, quantile to loss)            14 flops + 2 calls
+# The normal-approximation start used for alpha, beta > 1 is not counted (a lower bound).
+FLOP_PER_CF_TERM = 14.25
+FLOP_PER_NEWTON = 17.0 + 4.0
+FLOP_PER_INVERSION = 14.0 + 2.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--trials", type=int, default=800_000)
+    p.add_argument("--events", type=int, default=1000)
+    p.add_argument("--elts", type=int, default=16)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(a, world, l2_note=True):
+    return {
+        "workload": f"paper-scale layer {a.trials}x{a.events}x{a.elts} per GPU",
+        "trials": a.trials, "events_per_trial": a.events, "elts": a.elts,
+        "catalog": 2_000_000, "elt_records": "U{20000..200000} each",
+        "terms": [synth.TERMS_PAPER.occ_ret, synth.TERMS_PAPER.occ_lim,
+                  synth.TERMS_PAPER.agg_ret, synth.TERMS_PAPER.agg_lim],
+        "return_periods": list(synth.RPS_PAPER), "philox_seed": 42,
+        "parallelism": f"trial batches, {world} independent GPU(s)",
+        "l2": "inputs larger than L2 (3.2 GB event-id stream per step); the per-layer lookup "
+              "tables (~72 MB) stay L2-resident by design",
+    }
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_rate(a, seconds: float, elts=None, sample_seed: int = 7):
+    """evals/s of the FP64 oracle on a seeded sample of the workload's trials (all host cores)."""
+    import oracle
+
+    yet = synth.make_yet(min(a.trials, synth.YET_BLOCK), a.events, 2_000_000, seed=1)
+    elts = elts if elts is not None else synth.paper_elts(a.elts)
+    cores = oracle.n_threads()
+    # grow the sample until one timed run lasts about `seconds` (the first call also pays for
+    # building the oracle's search index, so it only sizes the next one)
+    n, dt = 64, 0.0
+    for _ in range(4):
+        pick = synth.subset_trials(yet.n_trials, n, seed=sample_seed)
+        t = time.perf_counter()
+        oracle.run(yet, elts, synth.TERMS_PAPER, 42, trials=pick, threads=cores)
+        dt = time.perf_counter() - t
+        if dt >= 0.6 * seconds or n >= yet.n_trials:
+            break
+        n = int(min(yet.n_trials, max(2 * n, n * 1.1 * seconds / max(dt, 1e-3))))
+    evals = n * a.events * a.elts
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded trials of the first 65,536 of the workload's YET "
+                      f"({a.events} events, {a.elts} ELTs), FP64 oracle, {dt:.1f} s wall"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401
+
+    elts = synth.paper_elts(a.elts)
+    times, rates = [], []
+    per_step = max(2.0, min(10.0, 120.0 / max(1, a.steps + a.warmup)))
+    cb = None
+    for s in range(a.warmup + a.steps):
+        r = oracle_sample_rate(a, per_step, elts=elts, sample_seed=100 + s)
+        if s >= a.warmup:
+            rates.append(r["value"])
+            cb = r
+    value = statistics.median(rates)
+    ms = a.trials * a.events * a.elts / value * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a, 1), "impl": "reference",
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "note": "reference arm = the FP64 CPU oracle on host cores; ms_per_step is the "
+                    "full workload's time extrapolated linearly from the sampled rate"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def traffic_for_current_kernel():
+    """DRAM bytes per launch of the trial kernel from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "trial_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in ("ara_trial.cu", "ara_ibeta.cuh", "ara_philox.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1310_2274_b300", "csrc", f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1310_2274_b300 as ara
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # each GPU processes its own batch of trials (independent YET seed): weak scaling
+    yet_h = synth.make_yet(a.trials, a.events, 2_000_000, seed=1 + rank)
+    elts_h = synth.paper_elts(a.elts)
+    terms = synth.TERMS_PAPER
+    rps = list(synth.RPS_PAPER)
+    n = a.trials
+
+    stream = torch.cuda.current_stream(dev)
+    ctx = ara.Context(seed=42, device=local)
+    ctx.set_stream(stream)
+    yet = ctx.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 2_000_000)
+    elts = [ctx.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
+    layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+    ylt = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+        return ctx.risk_measures(ylt, rps)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    s0 = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    k_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(a.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    for i in range(a.steps):
+        k_ev[i][0].record(stream)
+        ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+        k_ev[i][1].record(stream)
+        pml, tvar = ctx.risk_measures(ylt, rps)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    s1 = ctx.stats()
+
+    step_ms = t_start.elapsed_time(t_end) / a.steps
+    kern_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in k_ev)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    evals = n * a.events * a.elts
+    value = world * evals / (step_ms * 1e-3)
+
+    d = {k: (s1[k] - s0[k]) / a.steps for k in s0}
+    flops = (FLOP_PER_CF_TERM * d["cf_terms"] + FLOP_PER_NEWTON * d["newton"] +
+             FLOP_PER_INVERSION * d["inversions"])
+    sm_mhz = FALLBACK_SM_MHZ
+    peak_src = "recipe unit counts at the maximum SM clock 2032 MHz (MEASURED_PEAKS sm_max_mhz)"
+    if os.path.exists(PEAKS):
+        sm_mhz = float(json.load(open(PEAKS)).get("sm_max_mhz", FALLBACK_SM_MHZ))
+    peak = 2.0 * SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s FP32
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    traffic = traffic_for_current_kernel()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; shapes and value laws of the paper's workload)",
+        "config": workload_config(a, world),
+        "gpu_launches": int(s1["launches"] - s0["launches"]),
+        "clocks": clk,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "trial_kernel (Algorithm 1, one warp per trial)",
+                     "kernel_ms": kern_ms, "flops_per_launch": flops,
+                     "per_launch": {k: d[k] for k in ("inversions", "newton", "cf_terms",
+                                                      "hits")},
+                     "peak_source": f"FP32 FMA peak: 2 x {SM_COUNT} SMs x {FP32_LANES_PER_SM} "
+                                    f"lanes x {sm_mhz:.0f} MHz ({peak_src})"},
+        "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
+                          "tvar": [float(v) for v in tvar]},
+        "seconds_per_run": step_ms * 1e-3,
+    }
+
+    # ---- end to end through the public API with host buffers ---------------------------------
+    if not a.no_e2e:
+        result["e2e"] = e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream)
+    ctx.close()
+
+    # ---- CPU baseline (rank 0, one GPU only) --------------------------------------------------
+    if rank == 0 and world == 1 and not a.no_cpu:
+        result["cpu_baseline"] = oracle_sample_rate(a, a.cpu_seconds, elts=elts_h)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream):
+    import torch
+
+    def pinned(x):
+        t = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        return t, t.numpy()
+
+    off_t, off = pinned(yet_h.offsets)
+    ids_t, ids = pinned(yet_h.event_ids)
+    ts_t, ts = pinned(yet_h.timestamps)
+    elt_p = [tuple(pinned(v) for v in (e.event_ids, e.mean, e.sd, e.max_exposure))
+             for e in elts_h]
+    ylt_t, ylt = pinned(np.zeros(a.trials))
+    h2d = ids.nbytes + ts.nbytes + off.nbytes + ylt.nbytes + \
+        sum(v[1].nbytes for p in elt_p for v in p)
+    d2h = ylt.nbytes + 2 * 8 * len(rps)
+
+    def step():
+        yet = ctx.create_yet(off, ids, ts, 2_000_000)
+        elts = [ctx.add_elt(yet, *(v[1] for v in p)) for p in elt_p]
+        layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+        ctx.run(yet, layer, 0, a.trials, out=ylt)
+        pml, tvar = ctx.risk_measures(ylt, rps)
+        ctx.free_layer(layer)
+        for e in elts:
+            ctx.free_elt(e)
+        ctx.free_yet(yet)
+        return pml
+
+    steps = max(1, min(a.steps, 5))
+    for _ in range(min(a.warmup, 2)):
+        step()
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t) / steps
+    _, world = dist_env()[:2]
+    evals = a.trials * a.events * a.elts
+    return {"value": world * evals / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": steps,
+            "path": "ara_create_yet + 16 x ara_add_elt + ara_add_layer from pinned host memory, "
+                    "ara_run into a host YLT, ara_risk_measures, frees"}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

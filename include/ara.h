@@ -123,6 +123,12 @@ ARA_API ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0,
                            double* ylt, void* stream);
 /* Inversions that hit the iteration cap since the context was created (blocks on its work). */
 ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
+/* Work counters accumulated by every ara_run since the context was created (blocks on its work):
+ * out[0] beta inversions, out[1] Newton iterations, out[2] continued-fraction terms,
+ * out[3] inversions that hit the iteration cap, out[4] hits (ELT records met, sigma = 0 ones
+ * included); out[5] kernel launches issued by the library in this process (all contexts).
+ * They state the algorithmic work of a launch. */
+ARA_API ara_status ara_get_stats(ara_ctx* ctx, int64_t out[6]);
 
 /* Risk measures (paper §2.4) ---------------------------------------------------------------------
  * ylt[n] (host or device, n >= 1, no NaN), rps[m] return periods (> 1, host).  With
@@ -151,6 +157,9 @@ ARA_API ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int6
 
 /* Synchronises the context's stream. */
 ARA_API ara_status ara_synchronize(ara_ctx* ctx);
+/* Issues all later device work of the context on stream (a cudaStream_t of the context's device;
+ * NULL restores the context's own stream).  Blocking calls then synchronise that stream. */
+ARA_API ara_status ara_set_stream(ara_ctx* ctx, void* stream);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,8 @@ _SIGNATURES = {
     "ara_trace_hits": ([_P, _I32, _I32, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P,
                         C.POINTER(_I64)], C.c_int),
     "ara_synchronize": ([_P], C.c_int),
+    "ara_get_stats": ([_P, _P], C.c_int),
+    "ara_set_stream": ([_P, _P], C.c_int),
 }
 
 
@@ -160,6 +162,18 @@ class Context:
 
     def synchronize(self):
         self._check(lib().ara_synchronize(self._h))
+
+    def stats(self) -> dict:
+        """Cumulative work counters of every ara_run on this context."""
+        v = np.zeros(6, dtype=np.int64)
+        self._check(lib().ara_get_stats(self._h, _ptr(v)))
+        return dict(inversions=int(v[0]), newton=int(v[1]), cf_terms=int(v[2]),
+                    not_converged=int(v[3]), hits=int(v[4]), launches=int(v[5]))
+
+    def set_stream(self, stream=None):
+        """Issue the context's device work on stream (torch.cuda.Stream or cudaStream_t)."""
+        s = None if stream is None else getattr(stream, "cuda_stream", stream)
+        self._check(lib().ara_set_stream(self._h, s))
 
     def not_converged(self) -> int:
         v = _I64(0)

@@ -24,7 +24,9 @@ struct ara_ctx {
   std::vector<EltDev> elts;
   std::vector<LayerDev> layers;
   unsigned long long* d_not_conv = nullptr;
+  unsigned long long* d_stats = nullptr;  // [4]
   unsigned int* d_flags = nullptr;
+  cudaStream_t own_stream = nullptr;
   // grow-only scratch
   SortScratch sort;
   double* d_ylt_tmp = nullptr;
@@ -195,8 +197,11 @@ ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
   ctx->cfg = c;
   ctx->device = c.device;
   if (cudaSetDevice(ctx->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      (ctx->stream = ctx->own_stream, false) ||
       dev_alloc(&ctx->d_not_conv, 1) != cudaSuccess || dev_alloc(&ctx->d_flags, 4) != cudaSuccess ||
+      dev_alloc(&ctx->d_stats, 4) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
       cudaMalloc(&ctx->d_misc, 4096) != cudaSuccess ||
       cudaMemsetAsync(ctx->d_not_conv, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -224,9 +229,10 @@ void ara_destroy(ara_ctx* ctx) {
   dev_free(ctx->sort.digit_flags);
   dev_free(ctx->d_ylt_tmp);
   dev_free(ctx->d_not_conv);
+  dev_free(ctx->d_stats);
   dev_free(ctx->d_flags);
   dev_free(ctx->d_misc);
-  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   cudaGetLastError();
   delete ctx;
 }
@@ -564,6 +570,7 @@ static TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L,
   p.n = n;
   p.ylt = d_ylt;
   p.not_conv = ctx->d_not_conv;
+  p.stats = ctx->d_stats;
   return p;
 }
 
@@ -601,6 +608,30 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
   if (nc_after != nc_before)
     return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
                 nc_after - nc_before);
+  return ARA_OK;
+}
+
+ara_status ara_get_stats(ara_ctx* ctx, int64_t out[6]) {
+  if (!ctx || !out) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaDeviceSynchronize());
+  unsigned long long v[4], nc = 0;
+  CUDA_TRY(ctx, cudaMemcpy(v, ctx->d_stats, sizeof v, cudaMemcpyDeviceToHost));
+  CUDA_TRY(ctx, cudaMemcpy(&nc, ctx->d_not_conv, sizeof nc, cudaMemcpyDeviceToHost));
+  out[0] = (int64_t)v[0];
+  out[1] = (int64_t)v[1];
+  out[2] = (int64_t)v[2];
+  out[3] = (int64_t)nc;
+  out[4] = (int64_t)v[3];
+  out[5] = launches_so_far();
+  return ARA_OK;
+}
+
+ara_status ara_set_stream(ara_ctx* ctx, void* stream) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
   return ARA_OK;
 }
 

@@ -65,6 +65,7 @@ struct TrialParams {
   int64_t t0, n;
   double* ylt;
   unsigned long long* not_conv;
+  unsigned long long* stats;  // [4]: inversions, Newton iterations, CF terms, hits
   // verification trace (TRACE instantiation only)
   int64_t trace_cap;  // hits per trial slot in the trace buffers
   int32_t* tr_k;
@@ -75,6 +76,10 @@ struct TrialParams {
   float* tr_loss;
   int32_t* tr_count;  // [n]
 };
+
+// Kernel launches issued by this library since load (every launcher adds its launches).
+void count_launches(int64_t n);
+int64_t launches_so_far();
 
 // ---- launchers (each returns the launch's cudaError_t) ---------------------------------------
 cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st);

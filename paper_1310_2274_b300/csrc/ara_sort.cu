@@ -22,7 +22,6 @@ namespace {
 constexpr int kSortWarps = 8;
 constexpr int kSortItems = 16;                 // rounds of 32 keys per warp tile
 constexpr int kTile = 32 * kSortItems;         // keys per warp tile
-constexpr int kBlockKeys = kTile * kSortWarps; // keys per block
 
 __device__ __forceinline__ uint64_t desc_key(double y) {
   if (y == 0.0) y = 0.0;  // one zero: -0 and +0 are the same loss
@@ -148,6 +147,7 @@ cudaError_t sort_ylt_desc(const double* d_ylt, int64_t n, SortScratch& s, int* w
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   make_keys_kernel<<<blocks, 256, 0, st>>>(d_ylt, n, s.keys[0], s.vals[0], varying, nan_flag);
+  count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   uint32_t flags[4];
   if ((e = cudaMemcpyAsync(flags, s.digit_flags, sizeof flags, cudaMemcpyDeviceToHost, st)) !=
@@ -164,11 +164,13 @@ cudaError_t sort_ylt_desc(const double* d_ylt, int64_t n, SortScratch& s, int* w
     const int shift = 8 * pass;
     if (((var >> shift) & 255ull) == 0ull) continue;  // the same digit everywhere
     hist_kernel<<<grid, kSortWarps * 32, 0, st>>>(s.keys[cur], n, shift, n_tiles, s.hist);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_exclusive_scan_u32(s.hist, s.hist, hist_n, s.scan_tmp, s.scan_cap, st);
     if (e != cudaSuccess) return e;
     scatter_kernel<<<grid, kSortWarps * 32, 0, st>>>(s.keys[cur], s.vals[cur], n, shift, n_tiles,
                                                      s.hist, s.keys[1 - cur], s.vals[1 - cur]);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     cur = 1 - cur;
   }
@@ -182,12 +184,14 @@ cudaError_t launch_tail_sums(const double* d_ylt, const uint32_t* d_order, int64
   (void)n;
   if (m == 0) return cudaSuccess;
   tail_kernel<<<m, 256, 0, st>>>(d_ylt, d_order, d_k, d_pml, d_tvar);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_order_to_i64(const uint32_t* d_order, int64_t n, int64_t* d_out,
                                 cudaStream_t st) {
   order_to_i64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_order, n, d_out);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "ara_internal.h"
 
 namespace ara {
@@ -280,6 +282,12 @@ __global__ void scan_tiles_kernel(const uint32_t* __restrict__ in, int64_t n,
 
 }  // namespace
 
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
 cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st) {
   if (y.n_trials == 0) return cudaSuccess;
   int64_t warps = y.n_trials;
@@ -287,6 +295,7 @@ cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStre
   if (blocks > 148 * 64) blocks = 148 * 64;
   validate_yet_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(y.ids, y.ts, y.offsets, y.n_trials,
                                                               y.catalog, d_flags);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -297,6 +306,7 @@ cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean
   if (n == 0) return cudaSuccess;
   prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, mx, catalog, recs,
                                                        d_dup, d_flags);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -304,12 +314,14 @@ cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_
                               cudaStream_t st) {
   if (e.n == 0) return cudaSuccess;
   layer_mask_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, slot, mask_words, d_mask);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,
                                 uint32_t* d_cnt, cudaStream_t st) {
   layer_counts_kernel<<<grid_for(catalog), kThreads, 0, st>>>(d_mask, mask_words, catalog, d_cnt);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -323,6 +335,7 @@ cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t
   scan_tile_sums_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, n, d_tmp);
   scan_sums_kernel<<<1, kScanBlock, 0, st>>>(d_tmp, tiles);
   scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, n, d_tmp, out);
+  count_launches(3);
   return cudaGetLastError();
 }
 
@@ -330,6 +343,7 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
                                int64_t catalog, uint32_t* d_evt, cudaStream_t st) {
   layer_index_kernel<<<grid_for(catalog), kThreads, 0, st>>>(d_mask, d_base, mask_words, catalog,
                                                              d_evt);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -339,6 +353,7 @@ cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
   if (e.n == 0) return cudaSuccess;
   layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, slot, mask_words,
                                                            d_evt, packed, packed_rec);
+  count_launches(1);
   return cudaGetLastError();
 }
 

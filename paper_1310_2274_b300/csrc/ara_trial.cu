@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   Acc acc;
   int32_t trace_n = 0;
   unsigned int nc = 0;
+  unsigned int n_inv = 0, n_it = 0, n_cf = 0, n_hit = 0;
 
   for (int64_t c = beg; c < end; c += kChunk) {
     // ---- stream ids, look up entries, lay out the chunk's hits in event order ---------------
@@ -197,6 +198,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           const IbetaResult ib = ara_inv_beta(rec, u);
           x = ib.x;
           nc += ib.converged ? 0u : 1u;
+          n_inv += 1u;
+          n_it += (unsigned)ib.iters;
+          n_cf += (unsigned)ib.cf_terms;
           loss = rec.mx * x;
         } else {
           loss = rec.mx;  // sd = 0: the mean (primary uncertainty only)
@@ -230,6 +234,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       __syncwarp();
     }
     if constexpr (TRACE) trace_n += run;
+    n_hit += (lane == 0) ? (unsigned)run : 0u;
 
     // ---- occurrence terms and the year's running sum -----------------------------------------
 #pragma unroll
@@ -246,10 +251,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
   acc.warp_reduce();
   nc = __reduce_add_sync(0xFFFFFFFFu, nc);
+  n_inv = __reduce_add_sync(0xFFFFFFFFu, n_inv);
+  n_it = __reduce_add_sync(0xFFFFFFFFu, n_it);
+  n_cf = __reduce_add_sync(0xFFFFFFFFu, n_cf);
   if (lane == 0) {
     const double S = acc.value();
     P.ylt[w] = fmin(fmax(S - P.agg_ret, 0.0), P.agg_lim);
     if (nc) atomicAdd(P.not_conv, (unsigned long long)nc);
+    atomicAdd(P.stats + 0, (unsigned long long)n_inv);
+    atomicAdd(P.stats + 1, (unsigned long long)n_it);
+    atomicAdd(P.stats + 2, (unsigned long long)n_cf);
+    atomicAdd(P.stats + 3, (unsigned long long)n_hit);
     if constexpr (TRACE) P.tr_count[w] = trace_n;
   }
 }
@@ -259,6 +271,7 @@ cudaError_t launch_one(const TrialParams& p, cudaStream_t st) {
   const int64_t blocks = (p.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks == 0) return cudaSuccess;
   trial_kernel<MW, Acc, TRACE><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(p);
+  count_launches(1);
   return cudaGetLastError();
 }
 
