@@ -155,6 +155,29 @@ ARA_API ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int6
                                   float* hit_u, float* hit_x, float* hit_loss, double* ylt,
                                   int64_t* n_hits);
 
+/* Risk measures without any allocation ---------------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory when they need PML/TVaR (code running inside a pre-sized pool or another allocator that
+ * owns the device's memory, real-time loops that must not meet cudaMalloc's implicit
+ * synchronisation or its failure under memory pressure, callers holding no ara_ctx).  It computes
+ * what ara_risk_measures computes, with the same kernels, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   ylt[n]       device memory of the current device, 1 <= n <= ARA_NOALLOC_MAX_TRIALS;
+ *   rps[m]       host array, 0 <= m <= 16, each finite and > 1;
+ *   pml, tvar    device memory of the current device, m values each (caller-owned);
+ *   stream       cudaStream_t (NULL = the legacy default stream); the call is asynchronous and
+ *                the outputs are valid once the stream has passed it.
+ * Scratch is a fixed device array inside the library (about 29 MB, held by every GPU that loads
+ * the library until the process exits).  The first call on a device looks up that array's device
+ * address (make it before any stream capture).  Calls share the array: calls whose work overlaps
+ * on the GPU race and must not be made.  A YLT holding NaN yields NaN outputs.
+ * Returns ARA_ERR_INVALID_ARG for a size above the maximum, host pointers or a bad return
+ * period; ARA_ERR_CUDA if a launch fails; ARA_ERR_NO_DEVICE without a current device. */
+#define ARA_NOALLOC_MAX_TRIALS (1 << 20)
+ARA_API ara_status ara_risk_measures_noalloc(const double* ylt, int64_t n, const double* rps,
+                                             int32_t m, double* pml, double* tvar,
+                                             void* stream);
+
 /* Synchronises the context's stream. */
 ARA_API ara_status ara_synchronize(ara_ctx* ctx);
 /* Issues all later device work of the context on stream (a cudaStream_t of the context's device;

@@ -126,4 +126,21 @@ cudaError_t launch_order_to_i64(const uint32_t* d_order, int64_t n, int64_t* d_o
 cudaError_t launch_check_nan(const double* d_ylt, int64_t n, unsigned int* d_flag,
                              cudaStream_t st);
 
+// Tail counts passed by value to a kernel (no device buffer needed).
+constexpr int kMaxTailCounts = 16;
+struct TailCounts {
+  int64_t k[kMaxTailCounts];
+};
+// Same ordering as sort_ylt_desc on caller-provided buffers, with every radix pass run and no
+// host round trip; *order receives the buffer holding the permutation.  flags4 is cleared here
+// and flags4[2] is raised if the YLT holds a NaN.
+cudaError_t sort_ylt_desc_no_sync(const double* d_ylt, int64_t n, uint64_t* keys0,
+                                  uint64_t* keys1, uint32_t* vals0, uint32_t* vals1,
+                                  uint32_t* hist, uint32_t* scan_tmp, int64_t scan_cap,
+                                  uint32_t* flags4, const uint32_t** order, cudaStream_t st);
+cudaError_t launch_tail_sums_flagged(const double* d_ylt, const uint32_t* d_order,
+                                     const TailCounts& ks, int32_t m,
+                                     const unsigned int* d_nan_flag, double* d_pml,
+                                     double* d_tvar, cudaStream_t st);
+
 }  // namespace ara

@@ -129,6 +129,30 @@ __global__ void tail_kernel(const double* __restrict__ ylt, const uint32_t* __re
   }
 }
 
+// As tail_kernel, with the tail counts passed by value and a NaN flag raised by the key pass:
+// when it is set every output is NaN (the ordering of a YLT holding NaN is undefined).
+__global__ void tail_kernel_flagged(const double* __restrict__ ylt,
+                                   const uint32_t* __restrict__ order, const TailCounts ks,
+                                   const unsigned int* __restrict__ nan_flag, double* pml,
+                                   double* tvar) {
+  __shared__ double part[256];
+  const int q = blockIdx.x;
+  const int64_t k = ks.k[q];
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < k; r += blockDim.x) s += ylt[order[r]];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h >= 1; h >>= 1) {
+    if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const bool bad = *nan_flag != 0u;
+    pml[q] = bad ? __longlong_as_double(0x7FF8000000000000ll) : ylt[order[k - 1]];
+    tvar[q] = bad ? __longlong_as_double(0x7FF8000000000000ll) : part[0] / (double)k;
+  }
+}
+
 __global__ void order_to_i64_kernel(const uint32_t* __restrict__ o, int64_t n, int64_t* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (int64_t)o[i];
@@ -184,6 +208,50 @@ cudaError_t launch_tail_sums(const double* d_ylt, const uint32_t* d_order, int64
   (void)n;
   if (m == 0) return cudaSuccess;
   tail_kernel<<<m, 256, 0, st>>>(d_ylt, d_order, d_k, d_pml, d_tvar);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_ylt_desc_no_sync(const double* d_ylt, int64_t n, uint64_t* keys0,
+                                  uint64_t* keys1, uint32_t* vals0, uint32_t* vals1,
+                                  uint32_t* hist, uint32_t* scan_tmp, int64_t scan_cap,
+                                  uint32_t* flags4, const uint32_t** order, cudaStream_t st) {
+  // flags4: [0..1] varying-bit mask (unused here), [2] NaN flag; all cleared first
+  cudaError_t e = cudaMemsetAsync(flags4, 0, 4 * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  uint64_t* keys[2] = {keys0, keys1};
+  uint32_t* vals[2] = {vals0, vals1};
+  make_keys_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      d_ylt, n, keys[0], vals[0], reinterpret_cast<unsigned long long*>(flags4), flags4 + 2);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int64_t n_tiles = sort_tiles(n);
+  const int64_t hist_n = 256 * n_tiles;
+  const unsigned grid = (unsigned)((n_tiles + kSortWarps - 1) / kSortWarps);
+  int cur = 0;
+  for (int pass = 0; pass < 8; ++pass) {  // every pass: no host round trip to skip any
+    const int shift = 8 * pass;
+    hist_kernel<<<grid, kSortWarps * 32, 0, st>>>(keys[cur], n, shift, n_tiles, hist);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_exclusive_scan_u32(hist, hist, hist_n, scan_tmp, scan_cap, st);
+    if (e != cudaSuccess) return e;
+    scatter_kernel<<<grid, kSortWarps * 32, 0, st>>>(keys[cur], vals[cur], n, shift, n_tiles,
+                                                     hist, keys[1 - cur], vals[1 - cur]);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cur = 1 - cur;
+  }
+  *order = vals[cur];
+  return cudaSuccess;
+}
+
+cudaError_t launch_tail_sums_flagged(const double* d_ylt, const uint32_t* d_order,
+                                     const TailCounts& ks, int32_t m,
+                                     const unsigned int* d_nan_flag, double* d_pml,
+                                     double* d_tvar, cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  tail_kernel_flagged<<<m, 256, 0, st>>>(d_ylt, d_order, ks, d_nan_flag, d_pml, d_tvar);
   count_launches(1);
   return cudaGetLastError();
 }
