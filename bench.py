@@ -37,9 +37,17 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 FALLBACK_SM_MHZ = 2032.0
 
-# Algorithmic FP32 work of one launch, from the device algorithm's own trip counts (counted by
-# the kernel) and its per-block operation counts (+ - * / = 1 flop, fma = 2, each call of a
-# math-library function = 1):
+# Dominant kernel, certified-table inversion (default): HBM-bound.  Algorithmic DRAM bytes of one
+# launch = the event-id stream (4 B per occurrence) + one 32-byte table piece per table
+# evaluation (a random read of a 32-byte sector from the multi-GB tables) + the YLT (8 B per
+# trial).  The lookup index and per-record headers (~73 MB) are L2-resident by design.
+BYTES_PER_OCCURRENCE = 4.0
+BYTES_PER_TABLE_EVAL = 32.0
+BYTES_PER_TRIAL = 8.0
+
+# Newton inversion (reported beside it): FP32-ALU bound.  Algorithmic FP32 work of one launch,
+# from the device algorithm's own trip counts (counted by the kernel) and its per-block
+# operation counts (+ - * / = 1 flop, fma = 2, each call of a math-library function = 1):
 #   continued-fraction term (Wallis step, numerator/denominator, power-of-two rescale, every
 #     fourth term a convergence test)                                      14.25 flops
 #   Newton iteration in ln x (prefactor exponent, ln K, G, G', update)      17 flops + 4 calls
@@ -283,15 +291,38 @@ def run_ours(a):
     value = world * evals / (step_ms * 1e-3)
 
     d = {k: (s1[k] - s0[k]) / a.steps for k in s0}
-    flops = (FLOP_PER_CF_TERM * d["cf_terms"] + FLOP_PER_NEWTON * d["newton"] +
-             FLOP_PER_INVERSION * d["inversions"])
+    hbm_peak = 6442.9
+    if os.path.exists(PEAKS):
+        hbm_peak = float(json.load(open(PEAKS)).get("hbm_gbs", hbm_peak))
+    bytes_launch = (BYTES_PER_OCCURRENCE * n * a.events + BYTES_PER_TABLE_EVAL * d["table_evals"]
+                    + BYTES_PER_TRIAL * n)
+    achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
+    traffic = traffic_for_current_kernel()
+
+    # ---- the Newton inversion on the same data (secondary figure) -----------------------------
+    ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+    ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+    torch.cuda.synchronize(dev)
+    sn0 = ctx.stats()
+    nsteps = max(1, min(3, a.steps))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(nsteps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sn1 = ctx.stats()
+    ctx.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+    newton_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    dn = {k: (sn1[k] - sn0[k]) / nsteps for k in sn0}
+    flops = (FLOP_PER_CF_TERM * dn["cf_terms"] + FLOP_PER_NEWTON * dn["newton"] +
+             FLOP_PER_INVERSION * dn["inversions"])
     sm_mhz = FALLBACK_SM_MHZ
-    peak_src = "recipe unit counts at the maximum SM clock 2032 MHz (MEASURED_PEAKS sm_max_mhz)"
     if os.path.exists(PEAKS):
         sm_mhz = float(json.load(open(PEAKS)).get("sm_max_mhz", FALLBACK_SM_MHZ))
-    peak = 2.0 * SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s FP32
-    achieved = flops / (kern_ms * 1e-3) / 1e12
-    traffic = traffic_for_current_kernel()
+    alu_peak = 2.0 * SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s FP32
+    alu_achieved = flops / (newton_ms * 1e-3) / 1e12
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -301,14 +332,22 @@ def run_ours(a):
         "config": workload_config(a, world),
         "gpu_launches": int(s1["launches"] - s0["launches"]),
         "clocks": clk,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "trial_kernel (Algorithm 1, one warp per trial)",
-                     "kernel_ms": kern_ms, "flops_per_launch": flops,
-                     "per_launch": {k: d[k] for k in ("inversions", "newton", "cf_terms",
-                                                      "hits")},
-                     "peak_source": f"FP32 FMA peak: 2 x {SM_COUNT} SMs x {FP32_LANES_PER_SM} "
-                                    f"lanes x {sm_mhz:.0f} MHz ({peak_src})"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "kernel": "trial_kernel, certified-table inversion (one warp per trial)",
+                     "kernel_ms": kern_ms, "bytes_per_launch": bytes_launch,
+                     "per_launch": {k: d[k] for k in ("hits", "table_evals", "inversions")},
+                     "peak_source": "measured hbm_gbs in MEASURED_PEAKS.json (burst copy)"},
+        "newton_path": {"kernel_ms": newton_ms,
+                        "value": world * evals / (newton_ms * 1e-3),
+                        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                                     "unit": "TFLOP/s", "frac": alu_achieved / alu_peak,
+                                     "flops_per_launch": flops,
+                                     "per_launch": {k: dn[k] for k in ("inversions", "newton",
+                                                                        "cf_terms")},
+                                     "peak_source": f"FP32 FMA peak 2 x {SM_COUNT} SMs x "
+                                                    f"{FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"}},
+        "uncertified_records": s1["uncertified"],
         "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
                           "tvar": [float(v) for v in tvar]},
         "seconds_per_run": step_ms * 1e-3,

@@ -69,10 +69,18 @@ ARA_API const char* ara_status_string(ara_status s);
 /* Copies the detail of the last failed call on ctx (NUL-terminated, truncated to n bytes). */
 ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n);
 /* Options settable after creation: ARA_OPT_PRECISION (value ARA_ACC_*), ARA_OPT_SEED,
- * ARA_OPT_SURROGATE (0/1). */
+ * ARA_OPT_SURROGATE (0/1), ARA_OPT_INVERSION (value ARA_INV_*).
+ * Inversion of the beta CDF (paper §3.3, InvCDF_beta):
+ *   ARA_INV_TABLE (default): each record's quantile function, tabulated when its ELT is staged
+ *     (32 quintic pieces per tail in t = sqrt(-2 ln u), certified at every piece's midpoint to
+ *     1e-6 relative in x against the Newton inversion); records failing certification use Newton;
+ *   ARA_INV_NEWTON: Newton's method in ln x on the continued fraction for every hit. */
 #define ARA_OPT_PRECISION 1
 #define ARA_OPT_SEED 2
 #define ARA_OPT_SURROGATE 3
+#define ARA_OPT_INVERSION 4
+#define ARA_INV_TABLE 0
+#define ARA_INV_NEWTON 1
 ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
 
 /* Year Event Table (paper §2.1) ------------------------------------------------------------------
@@ -93,7 +101,8 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
  * from the table have zero loss (paper §4.1).  A record with sigma = 0 contributes its mean
  * (primary uncertainty only).  Values are staged in FP64 once: alpha, beta (moment matching with
  * the sigma_beta_max clamp of §3.3, sigma_beta set to sigma_beta_max (1 - 2^-20) when above it)
- * and the constants of the inversion, then stored as binary32 (32 bytes per record).
+ * and the constants of the inversion, then stored as binary32 (32 bytes per record); the record's
+ * certified quantile table is built at the same time (2 KB per record, see ARA_OPT_INVERSION).
  * The handle number keys the record's uniforms: Philox4x32-10 counter (k, i_lo, elt/4, i_hi),
  * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i. */
 ARA_API ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
@@ -124,11 +133,12 @@ ARA_API ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0,
 /* Inversions that hit the iteration cap since the context was created (blocks on its work). */
 ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
 /* Work counters accumulated by every ara_run since the context was created (blocks on its work):
- * out[0] beta inversions, out[1] Newton iterations, out[2] continued-fraction terms,
+ * out[0] Newton inversions, out[1] Newton iterations, out[2] continued-fraction terms,
  * out[3] inversions that hit the iteration cap, out[4] hits (ELT records met, sigma = 0 ones
- * included); out[5] kernel launches issued by the library in this process (all contexts).
- * They state the algorithmic work of a launch. */
-ARA_API ara_status ara_get_stats(ara_ctx* ctx, int64_t out[6]);
+ * included), out[5] kernel launches issued by the library in this process (all contexts),
+ * out[6] table evaluations, out[7] records of live ELTs whose table failed certification,
+ * out[8] surrogate evaluations.  They state the algorithmic work of a launch. */
+ARA_API ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]);
 
 /* Risk measures (paper §2.4) ---------------------------------------------------------------------
  * ylt[n] (host or device, n >= 1, no NaN), rps[m] return periods (> 1, host).  With
@@ -141,6 +151,50 @@ ARA_API ara_status ara_risk_measures(ara_ctx* ctx, const double* ylt, int64_t n,
 /* The same ordering exposed: order[r] = index of the r-th largest entry of ylt[n]; order may be
  * host or device memory (int64). */
 ARA_API ara_status ara_rank_ylt(ara_ctx* ctx, const double* ylt, int64_t n, int64_t* order);
+
+/* Learned surrogate of InvCDF_beta ----------------------------------------------------------------
+ * A 3 -> 64 -> 64 -> 64 -> 1 SiLU network (BF16 weights, FP32 accumulation, tensor-core MMA) maps
+ * (ln alpha, ln beta, logit u), normalised over the box alpha, beta in [0.1, 50], to logit x.
+ * Trained on the GPU by this library's own forward/backward/Adam kernels on (alpha, beta, u, x)
+ * tuples generated by the exact inversion (polished in binary64); then certified: on a 32 x 32 x 64
+ * grid of cells over the normalised inputs, each cell's largest |x_net - x| over its corners and
+ * cert_samples - 8 further points is recorded.  With ARA_OPT_SURROGATE = 1, ara_run uses the
+ * network for a hit only inside the box and where its cell's recorded error is <= eps; every other
+ * hit falls back to the exact Newton inversion. */
+typedef struct {
+  int64_t n_samples;    /* training tuples generated (e.g. 50,000,000)                       */
+  int64_t steps;        /* Adam steps                                                          */
+  int32_t batch;        /* rows per step, a multiple of 128                                    */
+  int32_t cert_samples; /* points per certification cell (>= 8)                                */
+  float lr, lr_final;   /* cosine schedule from lr to lr_final                                 */
+  float eps;            /* accepted absolute error in x per cell                               */
+  float reserved;
+  uint64_t seed;        /* stream of the training tuples and of the initial weights            */
+} ara_surrogate_config;
+typedef struct {
+  double loss_first, loss_last;   /* mean loss of the first and last 1% of steps                */
+  double gen_ms, train_ms, cert_ms;
+  double cells_accepted;          /* fraction of certification cells with error <= eps          */
+  double err_median, err_p99;     /* over cells: recorded |x_net - x|                            */
+  int64_t bad_targets;            /* tuples whose exact inversion reported non-convergence       */
+} ara_surrogate_report;
+ARA_API ara_status ara_train_surrogate(ara_ctx* ctx, const ara_surrogate_config* cfg,
+                                       ara_surrogate_report* report);
+/* Serialised surrogate: header, 8,641 FP32 parameters, 65,536 FP32 cell errors.  save writes at
+ * most cap bytes (*bytes receives the size needed); load replaces the context's surrogate. */
+ARA_API ara_status ara_save_surrogate(ara_ctx* ctx, void* blob, size_t cap, size_t* bytes);
+ARA_API ara_status ara_load_surrogate(ara_ctx* ctx, const void* blob, size_t bytes);
+/* Sets the accepted error eps of the loaded surrogate (the cell table is kept). */
+ARA_API ara_status ara_set_surrogate_eps(ara_ctx* ctx, float eps);
+/* Network evaluation and gradient with caller parameters (host FP32 vector of 8,641 in the order
+ * W1[64,3], b1, W2[64,64], b2, W3[64,64], b3, W4[64], b4; NULL = the context's trained network):
+ * z[n][3] normalised inputs (host), y[n] outputs (host).  ara_mlp_grad also takes x[n] and the
+ * clipped logit targets t[n] (both host) and returns the loss of one training step and its
+ * gradient (host, 8,641 values) as the training kernels compute them. */
+ARA_API ara_status ara_mlp_eval(ara_ctx* ctx, const float* params, const float* z, int64_t n,
+                                float* y);
+ARA_API ara_status ara_mlp_grad(ara_ctx* ctx, const float* params, const float* z, const float* x,
+                                const float* t, int64_t n, float* grad, double* loss);
 
 /* Verification ------------------------------------------------------------------------------------
  * Re-runs trials [t0, t0+n) with the same device code as ara_run, additionally listing every
@@ -177,6 +231,79 @@ ARA_API ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int6
 ARA_API ara_status ara_risk_measures_noalloc(const double* ylt, int64_t n, const double* rps,
                                              int32_t m, double* pml, double* tvar,
                                              void* stream);
+
+/* Continuous-batching service (paper §1: re-pricing layers while the client waits) ------------
+ * A server owns one context and one YET staged in it; the ELTs referenced by requests must be
+ * staged in the same context before the server is created, and while a server exists the context
+ * is used only through it (a worker thread issues all of the context's device work on the
+ * server's streams).  A request names a layer (ELT handles in summation order and the four terms,
+ * as ara_add_layer), trials [t0, t0 + n_trials) of the YET and up to ARA_MAX_RPS return periods;
+ * its result is the YLT of those trials and the PML/TVaR of that YLT, identical to ara_run +
+ * ara_risk_measures on the same inputs whatever else is in flight.
+ * Scheduling: a pending request is admitted, in arrival order, when fewer than max_inflight
+ * requests are running and the device memory it needs (its layer's lookup structure, 16 bytes per
+ * catalogue event, its packed records and its YLT) fits hbm_budget; its layer is built then.  Each
+ * kernel launch takes the next slice (up to slice_trials trials) of every running request, up to
+ * max_batch_trials trials in all, so a request arriving while others run joins the next launch.
+ * A finished request's memory is released at once; its results stay in host memory until
+ * ara_server_release.  Requests that fail (allocation, invalid layer) are marked FAILED with the
+ * status; the server keeps running. */
+#define ARA_MAX_RPS 16
+#define ARA_REQ_PENDING 0
+#define ARA_REQ_RUNNING 1
+#define ARA_REQ_DONE 2
+#define ARA_REQ_FAILED 3
+typedef struct ara_server ara_server;
+typedef struct {
+  int32_t yet;              /* YET handle of the context                                         */
+  int32_t max_inflight;     /* requests running at once (>= 1)                                  */
+  int64_t slice_trials;     /* trials of one request per launch (>= 1)                           */
+  int64_t max_batch_trials; /* trials per launch over all requests (>= slice_trials)             */
+  int64_t max_queue;        /* pending requests beyond which submit returns ARA_ERR_BUSY         */
+  int64_t hbm_budget;       /* bytes of device memory requests may hold; 0 = free memory - 4 GiB */
+  int32_t use_surrogate;    /* 1: the context's learned surrogate with exact fallback           */
+  int32_t inversion;        /* ARA_INV_TABLE or ARA_INV_NEWTON when use_surrogate = 0           */
+} ara_server_config;
+typedef struct {
+  int32_t elts[64];         /* ELT handles, n_elts of them                                       */
+  int32_t n_elts;
+  int32_t n_rps;            /* 0 .. ARA_MAX_RPS                                                  */
+  double occ_ret, occ_lim, agg_ret, agg_lim;
+  int64_t t0, n_trials;     /* trial range of the server's YET                                   */
+  double rps[ARA_MAX_RPS];  /* return periods, each > 1                                          */
+} ara_request;
+typedef struct {
+  int32_t state;            /* ARA_REQ_*                                                         */
+  int32_t error;            /* ara_status of a FAILED request                                    */
+  double submit_s, admit_s, done_s; /* seconds since the server was created                      */
+  int64_t n_trials;
+  double pml[ARA_MAX_RPS], tvar[ARA_MAX_RPS];
+} ara_request_status;
+typedef struct {
+  int64_t completed, failed, launches, pending, active;
+  double mean_items_per_launch;   /* requests sharing one launch, averaged                     */
+  int64_t hbm_budget, hbm_used;
+  double latency_p50_s, latency_p99_s, latency_max_s; /* submit -> done of completed requests */
+  double requests_per_s;          /* completed / (last completion - first submission)          */
+} ara_server_stats;
+ARA_API ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg,
+                                     ara_server** out);
+/* Queues a request (copied); *ticket identifies it.  ARA_ERR_BUSY when max_queue requests are
+ * pending; ARA_ERR_INVALID_ARG / ARA_ERR_BAD_HANDLE for a request that could never run. */
+ARA_API ara_status ara_server_submit(ara_server* s, const ara_request* req, int64_t* ticket);
+/* Blocks until the request is DONE (ARA_OK) or FAILED (its status), or timeout_s passes
+ * (ARA_ERR_BUSY). */
+ARA_API ara_status ara_server_wait(ara_server* s, int64_t ticket, double timeout_s);
+/* State, timings and risk measures of a request; with ylt != NULL (host, ylt_len >= n_trials) the
+ * YLT of a DONE request is copied out. */
+ARA_API ara_status ara_server_result(ara_server* s, int64_t ticket, ara_request_status* st,
+                                     double* ylt, int64_t ylt_len);
+/* Drops a finished request's host results (ARA_ERR_BUSY while it is pending or running). */
+ARA_API ara_status ara_server_release(ara_server* s, int64_t ticket);
+ARA_API ara_status ara_server_get_stats(ara_server* s, ara_server_stats* out);
+/* Stops the worker after the launches in flight, frees the server's memory and gives the context
+ * back its own stream.  Requests not yet finished are dropped.  NULL-safe. */
+ARA_API void ara_server_destroy(ara_server* s);
 
 /* Synchronises the context's stream. */
 ARA_API ara_status ara_synchronize(ara_ctx* ctx);

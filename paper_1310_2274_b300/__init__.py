@@ -15,12 +15,13 @@ import os
 
 import numpy as np
 
-__all__ = ["lib", "Context", "AraError", "ACC_FP64", "ACC_KAHAN32", "LIB_PATH"]
+__all__ = ["lib", "Context", "Server", "AraError", "ACC_FP64", "ACC_KAHAN32", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libara.so")
 ACC_FP64 = 0
 ACC_KAHAN32 = 1
-OPT_PRECISION, OPT_SEED, OPT_SURROGATE = 1, 2, 3
+OPT_PRECISION, OPT_SEED, OPT_SURROGATE, OPT_INVERSION = 1, 2, 3, 4
+INV_TABLE, INV_NEWTON = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",
           5: "inversion did not converge", 6: "busy", 7: "no CUDA device"}
 
@@ -32,6 +33,52 @@ class AraError(RuntimeError):
         self.status = status
         super().__init__(f"{STATUS.get(status, status)}: {detail}" if detail else
                          STATUS.get(status, str(status)))
+
+
+class SurrogateConfig(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("steps", C.c_int64), ("batch", C.c_int32),
+                ("cert_samples", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
+                ("eps", C.c_float), ("reserved", C.c_float), ("seed", C.c_uint64)]
+
+
+class SurrogateReport(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("gen_ms", C.c_double),
+                ("train_ms", C.c_double), ("cert_ms", C.c_double),
+                ("cells_accepted", C.c_double), ("err_median", C.c_double),
+                ("err_p99", C.c_double), ("bad_targets", C.c_int64)]
+
+
+MAX_RPS = 16
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("yet", C.c_int32), ("max_inflight", C.c_int32), ("slice_trials", C.c_int64),
+                ("max_batch_trials", C.c_int64), ("max_queue", C.c_int64),
+                ("hbm_budget", C.c_int64), ("use_surrogate", C.c_int32),
+                ("inversion", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("elts", C.c_int32 * 64), ("n_elts", C.c_int32), ("n_rps", C.c_int32),
+                ("occ_ret", C.c_double), ("occ_lim", C.c_double), ("agg_ret", C.c_double),
+                ("agg_lim", C.c_double), ("t0", C.c_int64), ("n_trials", C.c_int64),
+                ("rps", C.c_double * MAX_RPS)]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double), ("n_trials", C.c_int64),
+                ("pml", C.c_double * MAX_RPS), ("tvar", C.c_double * MAX_RPS)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("launches", C.c_int64),
+                ("pending", C.c_int64), ("active", C.c_int64),
+                ("mean_items_per_launch", C.c_double), ("hbm_budget", C.c_int64),
+                ("hbm_used", C.c_int64), ("latency_p50_s", C.c_double),
+                ("latency_p99_s", C.c_double), ("latency_max_s", C.c_double),
+                ("requests_per_s", C.c_double)]
 
 
 class _Config(C.Structure):
@@ -63,6 +110,19 @@ _SIGNATURES = {
     "ara_synchronize": ([_P], C.c_int),
     "ara_get_stats": ([_P, _P], C.c_int),
     "ara_set_stream": ([_P, _P], C.c_int),
+    "ara_train_surrogate": ([_P, C.POINTER(SurrogateConfig), C.POINTER(SurrogateReport)], C.c_int),
+    "ara_save_surrogate": ([_P, _P, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+    "ara_load_surrogate": ([_P, _P, C.c_size_t], C.c_int),
+    "ara_set_surrogate_eps": ([_P, C.c_float], C.c_int),
+    "ara_mlp_eval": ([_P, _P, _P, _I64, _P], C.c_int),
+    "ara_mlp_grad": ([_P, _P, _P, _P, _P, _I64, _P, C.POINTER(C.c_double)], C.c_int),
+    "ara_server_create": ([_P, C.POINTER(ServerConfig), C.POINTER(_P)], C.c_int),
+    "ara_server_submit": ([_P, C.POINTER(Request), C.POINTER(_I64)], C.c_int),
+    "ara_server_wait": ([_P, _I64, C.c_double], C.c_int),
+    "ara_server_result": ([_P, _I64, C.POINTER(RequestStatus), _P, _I64], C.c_int),
+    "ara_server_release": ([_P, _I64], C.c_int),
+    "ara_server_get_stats": ([_P, C.POINTER(ServerStats)], C.c_int),
+    "ara_server_destroy": ([_P], None),
 }
 
 
@@ -165,10 +225,11 @@ class Context:
 
     def stats(self) -> dict:
         """Cumulative work counters of every ara_run on this context."""
-        v = np.zeros(6, dtype=np.int64)
+        v = np.zeros(9, dtype=np.int64)
         self._check(lib().ara_get_stats(self._h, _ptr(v)))
         return dict(inversions=int(v[0]), newton=int(v[1]), cf_terms=int(v[2]),
-                    not_converged=int(v[3]), hits=int(v[4]), launches=int(v[5]))
+                    not_converged=int(v[3]), hits=int(v[4]), launches=int(v[5]),
+                    table_evals=int(v[6]), uncertified=int(v[7]), surrogate_evals=int(v[8]))
 
     def set_stream(self, stream=None):
         """Issue the context's device work on stream (torch.cuda.Stream or cudaStream_t)."""
@@ -263,6 +324,46 @@ class Context:
         m = min(nh.value, max_hits)
         return {k: v[:m] for k, v in bufs.items()}, ylt
 
+    # -- learned surrogate ---------------------------------------------------------------------
+    def train_surrogate(self, n_samples=50_000_000, steps=20_000, batch=8192, lr=3e-3,
+                        lr_final=3e-5, eps=2e-3, cert_samples=24, seed=3) -> dict:
+        cfg = SurrogateConfig(int(n_samples), int(steps), int(batch), int(cert_samples),
+                              float(lr), float(lr_final), float(eps), 0.0, int(seed))
+        rep = SurrogateReport()
+        self._check(lib().ara_train_surrogate(self._h, C.byref(cfg), C.byref(rep)))
+        return {f: getattr(rep, f) for f, _ in SurrogateReport._fields_}
+
+    def save_surrogate(self) -> bytes:
+        need = C.c_size_t(0)
+        self._check(lib().ara_save_surrogate(self._h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        self._check(lib().ara_save_surrogate(self._h, buf, need.value, C.byref(need)))
+        return buf.raw
+
+    def load_surrogate(self, blob: bytes):
+        self._check(lib().ara_load_surrogate(self._h, blob, len(blob)))
+
+    def set_surrogate_eps(self, eps: float):
+        self._check(lib().ara_set_surrogate_eps(self._h, float(eps)))
+
+    def mlp_eval(self, z, params=None):
+        z = np.ascontiguousarray(z, dtype=np.float32)
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        y = np.zeros(z.shape[0], dtype=np.float32)
+        self._check(lib().ara_mlp_eval(self._h, _ptr(p), _ptr(z), z.shape[0], _ptr(y)))
+        return y
+
+    def mlp_grad(self, params, z, x, t):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        z = np.ascontiguousarray(z, dtype=np.float32)
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(p.shape[0], dtype=np.float32)
+        loss = C.c_double(0)
+        self._check(lib().ara_mlp_grad(self._h, _ptr(p), _ptr(z), _ptr(x), _ptr(t), z.shape[0],
+                                       _ptr(g), C.byref(loss)))
+        return loss.value, g
+
     # -- convenience for synthetic workloads ---------------------------------------------------
     def stage_workload(self, w):
         """Stage a synth.Workload: returns (yet, [elt handles], layer)."""
@@ -272,3 +373,90 @@ class Context:
         t = w.terms
         layer = self.add_layer(elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
         return yet, elts, layer
+
+
+class Server:
+    """Continuous-batching service over one context and one staged YET (ara_server_*).
+
+    While a Server exists its context is driven only through it."""
+
+    def __init__(self, ctx: Context, yet: int, max_inflight: int = 32,
+                 slice_trials: int = 65536, max_batch_trials: int = 1 << 20,
+                 max_queue: int = 1 << 16, hbm_budget: int = 0, use_surrogate: bool = False,
+                 inversion: int = INV_TABLE):
+        cfg = ServerConfig(yet, max_inflight, slice_trials, max_batch_trials, max_queue,
+                           hbm_budget, int(use_surrogate), inversion)
+        h = _P()
+        st = lib().ara_server_create(ctx.handle, C.byref(cfg), C.byref(h))
+        if st != 0:
+            raise AraError(st, "ara_server_create")
+        self._h = h
+        self._ctx = ctx
+
+    def submit(self, elts, occ_ret, occ_lim, agg_ret, agg_lim, t0, n_trials, rps=()) -> int:
+        r = Request()
+        elts = list(elts)
+        rps = list(rps)
+        if len(elts) > 64 or len(rps) > MAX_RPS:
+            raise AraError(1, "too many ELTs or return periods")
+        for i, e in enumerate(elts):
+            r.elts[i] = int(e)
+        for i, v in enumerate(rps):
+            r.rps[i] = float(v)
+        r.n_elts, r.n_rps = len(elts), len(rps)
+        r.occ_ret, r.occ_lim, r.agg_ret, r.agg_lim = occ_ret, occ_lim, agg_ret, agg_lim
+        r.t0, r.n_trials = int(t0), int(n_trials)
+        tk = _I64(0)
+        st = lib().ara_server_submit(self._h, C.byref(r), C.byref(tk))
+        if st != 0:
+            raise AraError(st, "ara_server_submit")
+        return tk.value
+
+    def wait(self, ticket: int, timeout: float = 60.0) -> int:
+        """Status of the wait: 0 done, 6 timed out, else the failed request's status."""
+        return lib().ara_server_wait(self._h, ticket, timeout)
+
+    def result(self, ticket: int, ylt: bool = True) -> dict:
+        s = RequestStatus()
+        st = lib().ara_server_result(self._h, ticket, C.byref(s), None, 0)
+        if st != 0:
+            raise AraError(st, "ara_server_result")
+        out = dict(state=s.state, error=s.error, submit_s=s.submit_s, admit_s=s.admit_s,
+                   done_s=s.done_s, n_trials=s.n_trials, pml=np.array(s.pml[:]),
+                   tvar=np.array(s.tvar[:]))
+        if ylt and s.state == REQ_DONE:
+            y = np.empty(s.n_trials, dtype=np.float64)
+            st = lib().ara_server_result(self._h, ticket, C.byref(s), _ptr(y), y.shape[0])
+            if st != 0:
+                raise AraError(st, "ara_server_result")
+            out["ylt"] = y
+        return out
+
+    def release(self, ticket: int):
+        st = lib().ara_server_release(self._h, ticket)
+        if st != 0:
+            raise AraError(st, "ara_server_release")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        st = lib().ara_server_get_stats(self._h, C.byref(s))
+        if st != 0:
+            raise AraError(st, "ara_server_get_stats")
+        return {name: getattr(s, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ara_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -6,33 +6,18 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
+#include <random>
 #include <string>
 #include <vector>
 
 #include "../../include/ara.h"
 #include "ara_internal.h"
+#include "ara_ctx.h"
 
 using namespace ara;
 
-struct ara_ctx {
-  ara_config cfg{};
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  std::string detail;
-  std::vector<YetDev> yets;
-  std::vector<EltDev> elts;
-  std::vector<LayerDev> layers;
-  unsigned long long* d_not_conv = nullptr;
-  unsigned long long* d_stats = nullptr;  // [4]
-  unsigned int* d_flags = nullptr;
-  cudaStream_t own_stream = nullptr;
-  // grow-only scratch
-  SortScratch sort;
-  double* d_ylt_tmp = nullptr;
-  int64_t ylt_tmp_cap = 0;
-  void* d_misc = nullptr;  // small staging area for tail sums
-};
 
 namespace {
 
@@ -95,10 +80,17 @@ void free_yet(YetDev& y) {
 void free_elt(EltDev& e) {
   dev_free(e.ids);
   dev_free(e.recs);
+  dev_free(e.trecs);
+  dev_free(e.ivals);
   e = EltDev();
 }
 void free_layer(LayerDev& l) {
-  dev_free(l.evt);
+  if (l.hot) {
+    dev_free(l.hot);  // evt and tpacked live inside it
+  } else {
+    dev_free(l.evt);
+    dev_free(l.tpacked);
+  }
   dev_free(l.packed);
   dev_free(l.packed_rec);
   l = LayerDev();
@@ -200,8 +192,8 @@ ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
       cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       (ctx->stream = ctx->own_stream, false) ||
       dev_alloc(&ctx->d_not_conv, 1) != cudaSuccess || dev_alloc(&ctx->d_flags, 4) != cudaSuccess ||
-      dev_alloc(&ctx->d_stats, 4) != cudaSuccess ||
-      cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+      dev_alloc(&ctx->d_stats, 6) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_stats, 0, 6 * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
       cudaMalloc(&ctx->d_misc, 4096) != cudaSuccess ||
       cudaMemsetAsync(ctx->d_not_conv, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -232,6 +224,12 @@ void ara_destroy(ara_ctx* ctx) {
   dev_free(ctx->d_stats);
   dev_free(ctx->d_flags);
   dev_free(ctx->d_misc);
+  dev_free(ctx->mlp_P);
+  dev_free(ctx->mlp_M);
+  dev_free(ctx->mlp_V);
+  dev_free(ctx->mlp_G);
+  dev_free(ctx->mlp_W);
+  dev_free(ctx->mlp_bound);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   cudaGetLastError();
   delete ctx;
@@ -254,8 +252,15 @@ ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value) {
     case ARA_OPT_SEED:
       ctx->cfg.seed = (uint64_t)value;
       return ARA_OK;
+    case ARA_OPT_INVERSION:
+      if (value != ARA_INV_TABLE && value != ARA_INV_NEWTON)
+        return fail(ctx, ARA_ERR_INVALID_ARG, "inversion must be ARA_INV_TABLE or ARA_INV_NEWTON");
+      ctx->inversion = (int32_t)value;
+      return ARA_OK;
     case ARA_OPT_SURROGATE:
       if (value != 0 && value != 1) return fail(ctx, ARA_ERR_INVALID_ARG, "surrogate is 0 or 1");
+      if (value == 1 && !ctx->mlp_ready)
+        return fail(ctx, ARA_ERR_INVALID_ARG, "no surrogate trained or loaded");
       ctx->cfg.use_surrogate = (int32_t)value;
       return ARA_OK;
   }
@@ -370,6 +375,9 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
   e.n = n;
   double *d_mean = nullptr, *d_sd = nullptr, *d_mx = nullptr;
   unsigned int* d_dup = nullptr;
+  unsigned long long* d_uncert = nullptr;
+  double2* d_ab64 = nullptr;
+  unsigned long long uncert = 0;
   cudaError_t err;
   auto cleanup = [&]() {
     cudaStreamSynchronize(ctx->stream);
@@ -377,10 +385,15 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
     dev_free(d_sd);
     dev_free(d_mx);
     dev_free(d_dup);
+    dev_free(d_uncert);
+    dev_free(d_ab64);
   };
   if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
+      (err = dev_alloc(&e.trecs, n)) != cudaSuccess ||
+      (err = dev_alloc(&e.ivals, n * 4 * kTableIntervals)) != cudaSuccess ||
       (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
-      (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess) {
+      (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess ||
+      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess || (err = dev_alloc(&d_ab64, n)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     free_elt(e);
@@ -393,8 +406,12 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
       (err = copy_in(d_mx, max_exposure, n, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
-      (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_mx, y.catalog, e.recs, d_dup,
+      (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_mx, y.catalog, e.recs, d_ab64, d_dup,
                                 ctx->d_flags, ctx->stream)) != cudaSuccess ||
+      (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
+      (err = launch_build_tables(n, e.recs, d_ab64, e.trecs, e.ivals, d_uncert, ctx->stream)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess ||
       (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
@@ -412,6 +429,7 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
                 (flags & 32) ? " max_exposure <= mean with sd > 0" : "",
                 (flags & 64) ? " duplicate event id" : "");
   }
+  e.n_uncertified = (int64_t)uncert;
   e.live = true;
   ctx->elts.push_back(e);
   *elt_out = (int32_t)ctx->elts.size() - 1;
@@ -429,8 +447,13 @@ ara_status ara_free_elt(ara_ctx* ctx, int32_t elt) {
 }
 
 // ---- layer ------------------------------------------------------------------------------------
-ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
-                         double occ_lim, double agg_ret, double agg_lim, int32_t* layer_out) {
+}  // extern "C"
+
+// Builds a layer; wide = true forces 16-byte index entries (two mask words) whatever the ELT
+// count, the form the batched serving kernel takes.
+ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
+                              double occ_lim, double agg_ret, double agg_lim, bool wide,
+                              int32_t* layer_out) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
   if (!layer_out || !elts) return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
   if (n_elts < 1 || n_elts > kMaxLayerElts)
@@ -456,7 +479,7 @@ ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, doub
   LayerDev L;
   L.yet = yet;
   L.n_slots = n_elts;
-  L.mask_words = n_elts <= 32 ? 1 : 2;
+  L.mask_words = (n_elts <= 32 && !wide) ? 1 : 2;
   for (int j = 0; j < kMaxLayerElts; ++j) L.handles[j] = j < n_elts ? elts[j] : 0;
   L.occ_ret = occ_ret;
   L.occ_lim = occ_lim;
@@ -501,6 +524,23 @@ ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, doub
     return fail(ctx, ARA_ERR_CUDA, "layer index: %s", cudaGetErrorString(err));
   }
   L.n_packed = (int64_t)last[0] + (int64_t)last[1];
+  // the lookup index and the record headers share one allocation
+  const size_t evt_bytes = ((size_t)evt_words * sizeof(uint32_t) + 255) & ~(size_t)255;
+  L.hot_bytes = evt_bytes + sizeof(TableRec) * (size_t)(L.n_packed > 0 ? L.n_packed : 1);
+  if ((err = cudaMalloc(&L.hot, L.hot_bytes)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(L.hot, L.evt, (size_t)evt_words * sizeof(uint32_t),
+                             cudaMemcpyDeviceToDevice, ctx->stream)) != cudaSuccess ||
+      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    dev_free(L.hot);  // the index still lives in its first allocation
+    L.hot = nullptr;
+    free_layer(L);
+    return fail(ctx, ARA_ERR_OOM, "layer index: %s", cudaGetErrorString(err));
+  }
+  dev_free(L.evt);
+  L.evt = static_cast<uint32_t*>(L.hot);
+  L.tpacked = reinterpret_cast<TableRec*>(static_cast<char*>(L.hot) + evt_bytes);
   if ((err = dev_alloc(&L.packed, L.n_packed)) != cudaSuccess ||
       (err = dev_alloc(&L.packed_rec, L.n_packed)) != cudaSuccess) {
     cudaGetLastError();
@@ -509,7 +549,8 @@ ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, doub
     return fail(ctx, ARA_ERR_OOM, "layer records: %s", cudaGetErrorString(err));
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
-    err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, L.packed_rec, ctx->stream);
+    err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, L.tpacked, L.packed_rec,
+                               ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   cleanup();
   if (err != cudaSuccess) {
@@ -521,6 +562,14 @@ ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, doub
   ctx->layers.push_back(L);
   *layer_out = (int32_t)ctx->layers.size() - 1;
   return ARA_OK;
+}
+
+extern "C" {
+
+ara_status ara_add_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
+                         double occ_lim, double agg_ret, double agg_lim, int32_t* layer_out) {
+  return ara_add_layer_impl(ctx, elts, n_elts, occ_ret, occ_lim, agg_ret, agg_lim, false,
+                            layer_out);
 }
 
 ara_status ara_free_layer(ara_ctx* ctx, int32_t layer) {
@@ -550,14 +599,22 @@ static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64
   return ARA_OK;
 }
 
-static TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
-                               int64_t n, double* d_ylt) {
+}  // extern "C"
+
+int inversion_mode(const ara_ctx* ctx) {
+  if (ctx->cfg.use_surrogate && ctx->mlp_ready) return 2;
+  return ctx->inversion;
+}
+
+TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
+                        int64_t n, double* d_ylt) {
   TrialParams p;
   memset(&p, 0, sizeof p);
   p.ids = Y.ids;
   p.offsets = Y.offsets;
   p.evt = L.evt;
   p.recs = L.packed;
+  p.trecs = L.tpacked;
   p.rec_idx = L.packed_rec;
   for (int j = 0; j < kMaxLayerElts; ++j) p.handles[j] = L.handles[j];
   p.n_slots = L.n_slots;
@@ -571,8 +628,15 @@ static TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L,
   p.ylt = d_ylt;
   p.not_conv = ctx->d_not_conv;
   p.stats = ctx->d_stats;
+  if (ctx->cfg.use_surrogate && ctx->mlp_ready) {
+    p.mlp = &ctx->mlp_W->fwd;
+    p.mlp_bound = ctx->mlp_bound;
+    p.mlp_eps = ctx->mlp_eps;
+  }
   return p;
 }
+
+extern "C" {
 
 ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n, double* ylt,
                    void* stream) {
@@ -597,7 +661,8 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
     CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
                                   cudaMemcpyDeviceToHost, st));
   const TrialParams p = make_params(ctx, ctx->yets[yet], ctx->layers[layer], t0, n, d_ylt);
-  CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision, false, st));
+  CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
+                             inversion_mode(ctx), false, st));
   if (stream) return ARA_OK;
   if (!dev_out)
     CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
@@ -611,11 +676,11 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
   return ARA_OK;
 }
 
-ara_status ara_get_stats(ara_ctx* ctx, int64_t out[6]) {
+ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {
   if (!ctx || !out) return ARA_ERR_INVALID_ARG;
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   CUDA_TRY(ctx, cudaDeviceSynchronize());
-  unsigned long long v[4], nc = 0;
+  unsigned long long v[6], nc = 0;
   CUDA_TRY(ctx, cudaMemcpy(v, ctx->d_stats, sizeof v, cudaMemcpyDeviceToHost));
   CUDA_TRY(ctx, cudaMemcpy(&nc, ctx->d_not_conv, sizeof nc, cudaMemcpyDeviceToHost));
   out[0] = (int64_t)v[0];
@@ -624,6 +689,12 @@ ara_status ara_get_stats(ara_ctx* ctx, int64_t out[6]) {
   out[3] = (int64_t)nc;
   out[4] = (int64_t)v[3];
   out[5] = launches_so_far();
+  out[6] = (int64_t)v[4];
+  int64_t unc = 0;
+  for (const auto& e : ctx->elts)
+    if (e.live) unc += e.n_uncertified;
+  out[7] = unc;
+  out[8] = (int64_t)v[5];
   return ARA_OK;
 }
 
@@ -766,7 +837,7 @@ ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   p.tr_count = d_cnt;
   std::vector<int32_t> cnt(n), k(total), j(total), rec(total);
   std::vector<float> u(total), x(total), loss(total);
-  e = launch_trial(p, L.mask_words, ARA_ACC_FP64, true, ctx->stream);
+  e = launch_trial(p, L.mask_words, ARA_ACC_FP64, inversion_mode(ctx), true, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(k.data(), d_k, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(j.data(), d_j, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
@@ -799,6 +870,356 @@ ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   }
   *n_hits = h;
   return ARA_OK;
+}
+
+}  // extern "C"
+
+// ---- learned surrogate ----------------------------------------------------------------------------
+namespace {
+
+ara_status mlp_alloc(ara_ctx* ctx) {
+  if (ctx->mlp_P) return ARA_OK;
+  CUDA_TRY(ctx, dev_alloc(&ctx->mlp_P, kMlpParams));
+  CUDA_TRY(ctx, dev_alloc(&ctx->mlp_M, kMlpParams));
+  CUDA_TRY(ctx, dev_alloc(&ctx->mlp_V, kMlpParams));
+  CUDA_TRY(ctx, dev_alloc(&ctx->mlp_G, kMlpParams));
+  CUDA_TRY(ctx, cudaMalloc(&ctx->mlp_W, sizeof(MlpDevWeights)));
+  CUDA_TRY(ctx, dev_alloc(&ctx->mlp_bound, kCertCells));
+  return ARA_OK;
+}
+
+// Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases, seeded.
+void init_params(std::vector<float>& p, uint64_t seed) {
+  std::mt19937_64 rng(seed ^ 0x9E3779B97F4A7C15ull);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  p.assign(kMlpParams, 0.0f);
+  const int fans[4][2] = {{kH, 3}, {kH, kH}, {kH, kH}, {1, kH}};
+  int o = 0;
+  for (auto& f : fans) {
+    const double bnd = 1.0 / std::sqrt((double)f[1]);
+    for (int i = 0; i < f[0] * f[1] + f[0]; ++i) p[o++] = (float)(bnd * U(rng));
+  }
+}
+
+struct MlpBuffers {
+  MlpScratch s;
+  void free_all() {
+    dev_free(s.HT0); dev_free(s.HT1); dev_free(s.HT2); dev_free(s.HT3);
+    dev_free(s.DZT1); dev_free(s.DZT2); dev_free(s.DZT3);
+    s = MlpScratch();
+  }
+};
+
+cudaError_t mlp_scratch(MlpBuffers& b, int64_t B, cudaStream_t st) {
+  b.s.B = B;
+  cudaError_t e;
+  if ((e = dev_alloc(&b.s.HT0, 8 * B)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.s.HT0, 0, sizeof(__nv_bfloat16) * 8 * B, st)) != cudaSuccess) return e;
+  __nv_bfloat16** big[] = {&b.s.HT1, &b.s.HT2, &b.s.HT3, &b.s.DZT1, &b.s.DZT2, &b.s.DZT3};
+  for (auto p : big)
+    if ((e = dev_alloc(p, (int64_t)kH * B)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+float percentile(std::vector<float> v, double q) {
+  if (v.empty()) return 0.0f;
+  const size_t k = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1)));
+  std::nth_element(v.begin(), v.begin() + k, v.end());
+  return v[k];
+}
+
+// Certifies the network held in ctx->mlp_W: fills ctx->mlp_bound.
+ara_status mlp_certify(ara_ctx* ctx, int samples, uint64_t seed, ara_surrogate_report* rep,
+                       float eps) {
+  const int64_t n = kCertCells * samples;
+  float *Z = nullptr, *X = nullptr, *Y = nullptr;
+  unsigned int* bad = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(Z); dev_free(X); dev_free(Y); dev_free(bad);
+  };
+  cudaError_t e;
+  if ((e = dev_alloc(&Z, 3 * n)) != cudaSuccess || (e = dev_alloc(&X, n)) != cudaSuccess ||
+      (e = dev_alloc(&Y, n)) != cudaSuccess || (e = dev_alloc(&bad, 1)) != cudaSuccess ||
+      (e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
+      (e = launch_mlp_cert_points(kCertCells, samples, seed, Z, X, bad, ctx->stream)) != cudaSuccess ||
+      (e = launch_mlp_eval(ctx->mlp_W, Z, n, Y, ctx->stream)) != cudaSuccess ||
+      (e = launch_mlp_cert_reduce(kCertCells, samples, X, Y, ctx->mlp_bound, ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, ARA_ERR_CUDA, "surrogate certification: %s", cudaGetErrorString(e));
+  }
+  std::vector<float> b(kCertCells);
+  e = cudaMemcpyAsync(b.data(), ctx->mlp_bound, sizeof(float) * kCertCells, cudaMemcpyDeviceToHost,
+                      ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (e != cudaSuccess) return fail(ctx, ARA_ERR_CUDA, "surrogate certification: %s", cudaGetErrorString(e));
+  if (rep) {
+    int64_t acc = 0;
+    for (float v : b) acc += v <= eps;
+    rep->cells_accepted = (double)acc / (double)kCertCells;
+    rep->err_median = percentile(b, 0.5);
+    rep->err_p99 = percentile(b, 0.99);
+  }
+  return ARA_OK;
+}
+
+// Parameters into a BF16 image: the context's own (params == NULL) or caller values.
+ara_status mlp_image(ara_ctx* ctx, const float* params, MlpDevWeights** out, float** tmpP) {
+  *tmpP = nullptr;
+  if (!params) {
+    if (!ctx->mlp_ready) return fail(ctx, ARA_ERR_INVALID_ARG, "no surrogate trained or loaded");
+    *out = ctx->mlp_W;
+    return ARA_OK;
+  }
+  MlpDevWeights* w = nullptr;
+  CUDA_TRY(ctx, dev_alloc(tmpP, kMlpParams));
+  CUDA_TRY(ctx, cudaMalloc(&w, sizeof(MlpDevWeights)));
+  CUDA_TRY(ctx, cudaMemcpyAsync(*tmpP, params, sizeof(float) * kMlpParams, cudaMemcpyDefault, ctx->stream));
+  CUDA_TRY(ctx, launch_mlp_pack(*tmpP, w, ctx->stream));
+  *out = w;
+  return ARA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ara_status ara_train_surrogate(ara_ctx* ctx, const ara_surrogate_config* cfg,
+                               ara_surrogate_report* report) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!cfg || cfg->n_samples < cfg->batch || cfg->batch < 128 || cfg->batch % 128 != 0 ||
+      cfg->steps < 1 || cfg->cert_samples < 8 || !(cfg->lr > 0.0f) || !(cfg->lr_final > 0.0f) ||
+      !(cfg->eps > 0.0f))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "bad surrogate training configuration");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ara_status s = mlp_alloc(ctx);
+  if (s != ARA_OK) return s;
+  ara_surrogate_report rep{};
+  const int64_t N = cfg->n_samples / cfg->batch * cfg->batch;
+  float *Z = nullptr, *X = nullptr, *T = nullptr, *loss = nullptr;
+  unsigned int* bad = nullptr;
+  MlpBuffers buf;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(Z); dev_free(X); dev_free(T); dev_free(loss); dev_free(bad);
+    buf.free_all();
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  const int64_t n_loss = cfg->steps + 1;
+  if (e == cudaSuccess) e = dev_alloc(&Z, 3 * N);
+  if (e == cudaSuccess) e = dev_alloc(&X, N);
+  if (e == cudaSuccess) e = dev_alloc(&T, N);
+  if (e == cudaSuccess) e = dev_alloc(&loss, n_loss);
+  if (e == cudaSuccess) e = dev_alloc(&bad, 1);
+  if (e == cudaSuccess) e = mlp_scratch(buf, cfg->batch, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, ARA_ERR_OOM, "surrogate training buffers: %s", cudaGetErrorString(e));
+  }
+  std::vector<float> p0;
+  init_params(p0, cfg->seed);
+  e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float) * n_loss, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], ctx->stream);
+  const int64_t gen_chunk = 1 << 24;
+  for (int64_t f = 0; f < N && e == cudaSuccess; f += gen_chunk)
+    e = launch_mlp_gen(std::min(gen_chunk, N - f), cfg->seed, f, Z + 3 * f, X + f, T + f, bad,
+                       ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->mlp_P, p0.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice,
+                        ctx->stream);
+  for (float* q : {ctx->mlp_M, ctx->mlp_V, ctx->mlp_G})
+    if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, sizeof(float) * kMlpParams, ctx->stream);
+  if (e == cudaSuccess) e = launch_mlp_pack(ctx->mlp_P, ctx->mlp_W, ctx->stream);
+  const int64_t per_epoch = N / cfg->batch;
+  const double pi = 3.14159265358979323846;
+  for (int64_t step = 1; step <= cfg->steps && e == cudaSuccess; ++step) {
+    const int64_t b = (step - 1) % per_epoch;
+    e = launch_mlp_step(ctx->mlp_W, Z + 3 * b * cfg->batch, X + b * cfg->batch,
+                        T + b * cfg->batch, cfg->batch, buf.s, ctx->mlp_G, loss + step,
+                        ctx->stream);
+    const double frac = (double)(step - 1) / (double)std::max<int64_t>(1, cfg->steps - 1);
+    const float lr = (float)(cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + std::cos(pi * frac)));
+    if (e == cudaSuccess)
+      e = launch_mlp_adam(ctx->mlp_P, ctx->mlp_M, ctx->mlp_V, ctx->mlp_G, lr, step, ctx->stream);
+    if (e == cudaSuccess) e = launch_mlp_pack(ctx->mlp_P, ctx->mlp_W, ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], ctx->stream);
+  std::vector<float> hl(n_loss);
+  unsigned int hbad = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hl.data(), loss, sizeof(float) * n_loss, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, ARA_ERR_CUDA, "surrogate training: %s", cudaGetErrorString(e));
+  }
+  ctx->mlp_ready = true;
+  ctx->mlp_eps = cfg->eps;
+  s = mlp_certify(ctx, cfg->cert_samples, cfg->seed + 1, &rep, cfg->eps);
+  if (s != ARA_OK) {
+    ctx->mlp_ready = false;
+    cleanup();
+    return s;
+  }
+  cudaEventRecord(ev[3], ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  rep.gen_ms = ms;
+  cudaEventElapsedTime(&ms, ev[1], ev[2]);
+  rep.train_ms = ms;
+  cudaEventElapsedTime(&ms, ev[2], ev[3]);
+  rep.cert_ms = ms;
+  const int64_t w = std::max<int64_t>(1, cfg->steps / 100);
+  double a = 0, z = 0;
+  for (int64_t i = 1; i <= w; ++i) {
+    a += hl[i];
+    z += hl[cfg->steps + 1 - i];
+  }
+  rep.loss_first = a / w;
+  rep.loss_last = z / w;
+  rep.bad_targets = hbad;
+  cleanup();
+  if (report) *report = rep;
+  return ARA_OK;
+}
+
+ara_status ara_set_surrogate_eps(ara_ctx* ctx, float eps) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!(eps > 0.0f)) return fail(ctx, ARA_ERR_INVALID_ARG, "eps must be > 0");
+  ctx->mlp_eps = eps;
+  return ARA_OK;
+}
+
+static const uint32_t kBlobMagic = 0x53524741u;  // "AGRS"
+struct BlobHeader {
+  uint32_t magic, version;
+  int32_t n_params, n_cells;
+  float eps;
+  uint32_t pad[3];
+};
+
+ara_status ara_save_surrogate(ara_ctx* ctx, void* blob, size_t cap, size_t* bytes) {
+  if (!ctx || !bytes) return ARA_ERR_INVALID_ARG;
+  const size_t need = sizeof(BlobHeader) + sizeof(float) * (kMlpParams + kCertCells);
+  *bytes = need;
+  if (!ctx->mlp_ready) return fail(ctx, ARA_ERR_INVALID_ARG, "no surrogate trained or loaded");
+  if (!blob) return ARA_OK;
+  if (cap < need) return fail(ctx, ARA_ERR_INVALID_ARG, "blob needs %zu bytes", need);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  BlobHeader h{kBlobMagic, 1, kMlpParams, (int32_t)kCertCells, ctx->mlp_eps, {0, 0, 0}};
+  char* o = static_cast<char*>(blob);
+  memcpy(o, &h, sizeof h);
+  CUDA_TRY(ctx, cudaMemcpyAsync(o + sizeof h, ctx->mlp_P, sizeof(float) * kMlpParams,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(o + sizeof h + sizeof(float) * kMlpParams, ctx->mlp_bound,
+                                sizeof(float) * kCertCells, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return ARA_OK;
+}
+
+ara_status ara_load_surrogate(ara_ctx* ctx, const void* blob, size_t bytes) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  const size_t need = sizeof(BlobHeader) + sizeof(float) * (kMlpParams + kCertCells);
+  if (!blob || bytes < need) return fail(ctx, ARA_ERR_INVALID_ARG, "surrogate blob too short");
+  BlobHeader h;
+  memcpy(&h, blob, sizeof h);
+  if (h.magic != kBlobMagic || h.version != 1 || h.n_params != kMlpParams ||
+      h.n_cells != (int32_t)kCertCells || !(h.eps > 0.0f))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "not a surrogate blob of this library");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ara_status s = mlp_alloc(ctx);
+  if (s != ARA_OK) return s;
+  const char* in = static_cast<const char*>(blob);
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mlp_P, in + sizeof h, sizeof(float) * kMlpParams,
+                                cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mlp_bound, in + sizeof h + sizeof(float) * kMlpParams,
+                                sizeof(float) * kCertCells, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, launch_mlp_pack(ctx->mlp_P, ctx->mlp_W, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->mlp_eps = h.eps;
+  ctx->mlp_ready = true;
+  return ARA_OK;
+}
+
+ara_status ara_mlp_eval(ara_ctx* ctx, const float* params, const float* z, int64_t n, float* y) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!z || !y))) return fail(ctx, ARA_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return ARA_OK;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  MlpDevWeights* w = nullptr;
+  float* tmpP = nullptr;
+  ara_status s = mlp_image(ctx, params, &w, &tmpP);
+  const int64_t np = (n + 15) / 16 * 16;
+  float *dz = nullptr, *dy = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (s == ARA_OK) {
+    if ((e = dev_alloc(&dz, 3 * np)) == cudaSuccess && (e = dev_alloc(&dy, np)) == cudaSuccess &&
+        (e = cudaMemsetAsync(dz, 0, sizeof(float) * 3 * np, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(dz, z, sizeof(float) * 3 * n, cudaMemcpyDefault, ctx->stream)) == cudaSuccess &&
+        (e = launch_mlp_eval(w, dz, np, dy, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(y, dy, sizeof(float) * n, cudaMemcpyDefault, ctx->stream)) == cudaSuccess)
+      e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) s = fail(ctx, ARA_ERR_CUDA, "mlp eval: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(ctx->stream);
+  cudaGetLastError();
+  dev_free(dz);
+  dev_free(dy);
+  dev_free(tmpP);
+  if (w && w != ctx->mlp_W) dev_free(w);
+  return s;
+}
+
+ara_status ara_mlp_grad(ara_ctx* ctx, const float* params, const float* z, const float* x,
+                        const float* t, int64_t n, float* grad, double* loss) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (n < 16 || n % 16 != 0 || !z || !x || !t || !grad || !loss)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "n must be a positive multiple of 16");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  MlpDevWeights* w = nullptr;
+  float* tmpP = nullptr;
+  ara_status s = mlp_image(ctx, params, &w, &tmpP);
+  float *dz = nullptr, *dx = nullptr, *dt = nullptr, *dg = nullptr, *dl = nullptr;
+  MlpBuffers buf;
+  cudaError_t e = cudaSuccess;
+  float hl = 0.0f;
+  if (s == ARA_OK) {
+    if ((e = dev_alloc(&dz, 3 * n)) == cudaSuccess && (e = dev_alloc(&dx, n)) == cudaSuccess &&
+        (e = dev_alloc(&dt, n)) == cudaSuccess && (e = dev_alloc(&dg, kMlpParams)) == cudaSuccess &&
+        (e = dev_alloc(&dl, 1)) == cudaSuccess && (e = mlp_scratch(buf, n, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(dz, z, sizeof(float) * 3 * n, cudaMemcpyDefault, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(dx, x, sizeof(float) * n, cudaMemcpyDefault, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(dt, t, sizeof(float) * n, cudaMemcpyDefault, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemsetAsync(dg, 0, sizeof(float) * kMlpParams, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemsetAsync(dl, 0, sizeof(float), ctx->stream)) == cudaSuccess &&
+        (e = launch_mlp_step(w, dz, dx, dt, n, buf.s, dg, dl, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(grad, dg, sizeof(float) * kMlpParams, cudaMemcpyDefault, ctx->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(&hl, dl, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream)) == cudaSuccess)
+      e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) s = fail(ctx, ARA_ERR_CUDA, "mlp grad: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(ctx->stream);
+  cudaGetLastError();
+  for (float* q : {dz, dx, dt, dg, dl}) dev_free(q);
+  buf.free_all();
+  dev_free(tmpP);
+  if (w && w != ctx->mlp_W) dev_free(w);
+  *loss = hl;
+  return s;
 }
 
 }  // extern "C"

@@ -1,0 +1,53 @@
+// ara_ctx.h -- the context object behind the opaque ara_ctx handle (shared by libara's host
+// sources).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ara.h"
+#include "ara_internal.h"
+
+using ara::BetaRec;
+using ara::EltDev;
+using ara::LayerDev;
+using ara::MlpDevWeights;
+using ara::SortScratch;
+using ara::TrialParams;
+using ara::YetDev;
+
+struct ara_ctx {
+  ara_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string detail;
+  std::vector<YetDev> yets;
+  std::vector<EltDev> elts;
+  std::vector<LayerDev> layers;
+  unsigned long long* d_not_conv = nullptr;
+  unsigned long long* d_stats = nullptr;  // [6]
+  int32_t inversion = 0;                   // 0 certified tables + Newton fallback, 1 Newton
+  // learned surrogate: FP32 master parameters, Adam moments, gradient, BF16 image, cell errors
+  float *mlp_P = nullptr, *mlp_M = nullptr, *mlp_V = nullptr, *mlp_G = nullptr;
+  MlpDevWeights* mlp_W = nullptr;
+  float* mlp_bound = nullptr;
+  float mlp_eps = 0.0f;
+  bool mlp_ready = false;
+  unsigned int* d_flags = nullptr;
+  cudaStream_t own_stream = nullptr;
+  // grow-only scratch
+  SortScratch sort;
+  double* d_ylt_tmp = nullptr;
+  int64_t ylt_tmp_cap = 0;
+  void* d_misc = nullptr;  // small staging area for tail sums
+};
+
+// Internal entry points shared between the API and the serving loop.
+ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
+                              double occ_lim, double agg_ret, double agg_lim, bool wide,
+                              int32_t* layer_out);
+int inversion_mode(const ara_ctx* ctx);
+TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,
+                        double* d_ylt);

@@ -34,10 +34,29 @@
 
 #include <stdint.h>
 
+#ifndef __CUDACC__
+#include <cmath>
+#include <cstring>
+using std::isfinite;
+struct float4 {
+  float x, y, z, w;
+};
+#endif
+
+namespace ara {
+ARA_HD float4 ara_make_float4(float x, float y, float z, float w) {
+  float4 v;
+  v.x = x; v.y = y; v.z = z; v.w = w;
+  return v;
+}
+}  // namespace ara
+
 namespace ara {
 
 struct IbetaResult {
   float x;        // quantile in [0,1]
+  float t;        // ln of the unknown actually solved for (x, or 1-x when the tail flipped);
+                  // finite even where that unknown underflows binary32
   int iters;      // Newton iterations used
   int cf_terms;   // continued-fraction terms summed
   bool converged;
@@ -140,6 +159,7 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
   r.iters = 0;
   r.cf_terms = 0;
   r.converged = true;
+  r.t = 0.0f;
   const bool flip = u > rec.p0;
   const float p = flip ? 1.0f - u : u;
   const float a = flip ? rec.b : rec.a;
@@ -167,7 +187,7 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
   }
   t = fminf(t, lnx0);  // the root is below the mean
   // Below e^-69 ~ 1e-30 the loss max_l * x is far under every term of a year loss.
-  if (!(t > -69.0f)) { r.x = flip ? 1.0f : 0.0f; return r; }
+  if (!(t > -69.0f)) { r.x = flip ? 1.0f : 0.0f; r.t = t; return r; }
 
   // ---- Newton iterations in t ---------------------------------------------------------------
   const float thr = (a + 1.0f) / (s + 2.0f);
@@ -204,8 +224,68 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
   }
   r.iters = it;
   r.converged = done;
+  r.t = t;
   r.x = flip ? 1.0f - x : x;
   return r;
+}
+
+// ---- certified per-record quantile tables ---------------------------------------------------------
+//
+// Each record's (alpha, beta) is fixed and is met hundreds of times per run, so its quantile
+// function is tabulated once, when the ELT is staged.  The two tails are tabulated separately:
+// below the mean (u <= p0) the table maps t = sqrt(-2 ln u) to r = ln x; above it, t =
+// sqrt(-2 ln(1-u)) to r = ln(1-x).  In t the quantile's log is smooth and nearly quadratic in the
+// tails (ln x ~ (ln u)/a), so kTableIntervals quintic Hermite pieces per tail, built from r and its
+// first two derivatives at uniformly spaced knots, reproduce it to ~1e-8; every piece is checked
+// at its midpoint when the table is built, and a record whose table misses the bound keeps the
+// Newton inversion.  One piece is 6 binary32 coefficients of a polynomial in the local coordinate
+// tau in [0,1], padded to 32 bytes (one sector); the record header is 16 bytes.
+constexpr int kTableIntervals = 32;
+// t at the smallest uniform on the grid, 2^-24: sqrt(48 ln 2)
+constexpr float kTableTHi = 5.76832104f;
+
+struct TableRec {
+  float mx;          // loss scale (the mean itself for a sd = 0 record)
+  float p0;          // I_{x0}(a,b); negative marks a sd = 0 record
+  const float4* iv;  // 2 * kTableIntervals pieces (lower then upper), 2 float4 each; NULL: no table
+};
+
+// Start of a tail's table in t and its inverse piece width, from the tail's mean probability
+// pe (p0 for the lower tail, 1 - p0 for the upper).  The builder and the evaluation both use
+// this binary32 computation, so they agree on the piece boundaries exactly.
+ARA_HD void ara_table_span(float pe, float* tlo, float* invh) {
+  *tlo = sqrtf(-2.0f * logf(pe));
+  *invh = (float)kTableIntervals / (kTableTHi - *tlo);
+}
+
+// Quantile from a certified table (iv != NULL, p0 >= 0).
+ARA_HD float ara_table_quantile(const TableRec& tr, float u) {
+  const bool lower = u <= tr.p0;
+  const float q = lower ? u : 1.0f - u;  // exact on the uniform grid
+  const float t = sqrtf(-2.0f * logf(q));
+  float tlo, ih;
+  ara_table_span(lower ? tr.p0 : 1.0f - tr.p0, &tlo, &ih);
+  float pos = fminf(fmaxf((t - tlo) * ih, 0.0f), (float)kTableIntervals);
+  const int k = pos < (float)(kTableIntervals - 1) ? (int)pos : kTableIntervals - 1;
+  const float tau = pos - (float)k;
+  const float4* c = tr.iv + 2 * ((lower ? 0 : kTableIntervals) + k);
+#ifdef __CUDA_ARCH__
+  // one 32-byte load, streamed: a piece is read once per hit from tables far larger than L2, so
+  // it bypasses L1 and is first in line for eviction from L2
+  float4 c0, c1;
+  asm volatile(
+      "ld.global.nc.L1::no_allocate.L2::evict_first.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(c0.x), "=f"(c0.y), "=f"(c0.z), "=f"(c0.w), "=f"(c1.x), "=f"(c1.y), "=f"(c1.z),
+        "=f"(c1.w)
+      : "l"(c));
+#else
+  const float4 c0 = c[0];
+  const float4 c1 = c[1];
+#endif
+  const float r = fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, c1.y, c1.x), c0.w), c0.z), c0.y),
+                       c0.x);
+  const float v = expf(r);
+  return lower ? v : 1.0f - v;
 }
 
 }  // namespace ara

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "ara_ibeta.cuh"
+#include "ara_mlp.cuh"
 
 namespace ara {
 
@@ -32,6 +33,9 @@ struct EltDev {
   int64_t n = 0;
   int32_t* ids = nullptr;    // [n]
   BetaRec* recs = nullptr;   // [n]
+  TableRec* trecs = nullptr; // [n] certified quantile tables (iv NULL: Newton inversion)
+  float4* ivals = nullptr;   // [n * 4 * kTableIntervals] table pieces
+  int64_t n_uncertified = 0; // records whose table failed certification
 };
 
 // A layer: lookup structure over the YET's catalogue plus its terms (paper §2.1, §2.3).
@@ -46,8 +50,11 @@ struct LayerDev {
   double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
   uint32_t* evt = nullptr;         // [catalog * (1 + mask_words)] entries, padded to 2 or 4 words
   BetaRec* packed = nullptr;       // [n_packed]
+  TableRec* tpacked = nullptr;     // [n_packed] table records, same order
   uint32_t* packed_rec = nullptr;  // [n_packed] caller record index (verification)
   int64_t n_packed = 0;
+  void* hot = nullptr;             // one allocation holding evt then tpacked
+  size_t hot_bytes = 0;
 };
 
 // Parameters of one trial-kernel launch.
@@ -56,6 +63,7 @@ struct TrialParams {
   const int64_t* offsets;
   const uint32_t* evt;
   const BetaRec* recs;
+  const TableRec* trecs;
   const uint32_t* rec_idx;
   int32_t handles[kMaxLayerElts];
   int32_t n_slots;
@@ -65,7 +73,11 @@ struct TrialParams {
   int64_t t0, n;
   double* ylt;
   unsigned long long* not_conv;
-  unsigned long long* stats;  // [4]: inversions, Newton iterations, CF terms, hits
+  unsigned long long* stats;  // [6]: inversions, Newton iterations, CF terms, hits, table evals,
+                              //      surrogate evaluations
+  const MlpSmem* mlp;         // surrogate weights (inversion 2)
+  const float* mlp_bound;     // certified error per cell
+  float mlp_eps;
   // verification trace (TRACE instantiation only)
   int64_t trace_cap;  // hits per trial slot in the trace buffers
   int32_t* tr_k;
@@ -85,8 +97,8 @@ int64_t launches_so_far();
 cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st);
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
                                const double* sd, const double* mx, int32_t catalog,
-                               BetaRec* recs, unsigned int* d_dup, unsigned int* d_flags,
-                               cudaStream_t st);
+                               BetaRec* recs, double2* ab64, unsigned int* d_dup,
+                               unsigned int* d_flags, cudaStream_t st);
 cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
                               cudaStream_t st);
 cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,
@@ -97,10 +109,21 @@ int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, int mask_words,
                                int64_t catalog, uint32_t* d_evt, cudaStream_t st);
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
-                                 const uint32_t* d_evt, BetaRec* packed, uint32_t* packed_rec,
-                                 cudaStream_t st);
-cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, bool trace,
-                         cudaStream_t st);
+                                 const uint32_t* d_evt, BetaRec* packed, TableRec* tpacked,
+                                 uint32_t* packed_rec, cudaStream_t st);
+// ab64[n]: each record's (alpha, beta) in binary64, as written by launch_prepare_elt.
+cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
+                                TableRec* trecs, float4* ivals,
+                                unsigned long long* d_uncertified, cudaStream_t st);
+// inversion: 0 = certified tables with Newton fallback, 1 = Newton everywhere, 2 = learned
+// surrogate with Newton fallback
+cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, int inversion,
+                         bool trace, cudaStream_t st);
+// One launch over n_items work items (device array of TrialParams whose layers all use 16-byte
+// index entries, i.e. mask_words = 2); warp_begin[i] = first warp of item i (device, ascending).
+cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp_begin,
+                               int n_items, int64_t total_warps, int precision, int inversion,
+                               cudaStream_t st);
 
 // Radix sort of binary64 year losses (descending, ties by index) and tail sums.
 struct SortScratch {
@@ -108,7 +131,7 @@ struct SortScratch {
   uint32_t* vals[2] = {nullptr, nullptr};
   uint32_t* hist = nullptr;       // [256 * tiles]
   uint32_t* scan_tmp = nullptr;
-  uint32_t* digit_flags = nullptr;  // [8 passes * 2]
+  uint32_t* digit_flags = nullptr;  // [4]: varying-bit mask (2 words), NaN flag, spare
   int64_t cap = 0;                // elements
   int64_t hist_cap = 0;
   int64_t scan_cap = 0;
@@ -142,5 +165,29 @@ cudaError_t launch_tail_sums_flagged(const double* d_ylt, const uint32_t* d_orde
                                      const TailCounts& ks, int32_t m,
                                      const unsigned int* d_nan_flag, double* d_pml,
                                      double* d_tvar, cudaStream_t st);
+
+// ---- learned surrogate (ara_mlp.cu) -------------------------------------------------------------
+constexpr int kCert0 = 32, kCert1 = 32, kCert2 = 64;  // certification grid over the inputs
+constexpr int64_t kCertCells = (int64_t)kCert0 * kCert1 * kCert2;
+
+struct MlpScratch {  // per-step buffers of a training batch of B rows (transposed, BF16)
+  __nv_bfloat16 *HT0 = nullptr, *HT1 = nullptr, *HT2 = nullptr, *HT3 = nullptr;
+  __nv_bfloat16 *DZT1 = nullptr, *DZT2 = nullptr, *DZT3 = nullptr;
+  int64_t B = 0;
+};
+cudaError_t launch_mlp_gen(int64_t n, uint64_t seed, int64_t first, float* Z, float* X, float* T,
+                           unsigned int* bad, cudaStream_t st);
+cudaError_t launch_mlp_pack(const float* P, MlpDevWeights* Wd, cudaStream_t st);
+cudaError_t launch_mlp_step(const MlpDevWeights* Wd, const float* Z, const float* X,
+                            const float* T, int64_t B, MlpScratch& s, float* grad, float* loss_acc,
+                            cudaStream_t st);
+cudaError_t launch_mlp_adam(float* P, float* M, float* V, float* G, float lr, int64_t step,
+                            cudaStream_t st);
+cudaError_t launch_mlp_eval(const MlpDevWeights* Wd, const float* Z, int64_t n, float* Y,
+                            cudaStream_t st);
+cudaError_t launch_mlp_cert_points(int64_t n_cells, int samples, uint64_t seed, float* Z, float* X,
+                                   unsigned int* bad, cudaStream_t st);
+cudaError_t launch_mlp_cert_reduce(int64_t n_cells, int samples, const float* X, const float* Y,
+                                   float* bound, cudaStream_t st);
 
 }  // namespace ara

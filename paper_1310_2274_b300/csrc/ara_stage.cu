@@ -13,6 +13,7 @@
 #include <atomic>
 
 #include "ara_internal.h"
+#include "ara_table.cuh"
 
 namespace ara {
 
@@ -52,43 +53,10 @@ __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float
 
 // ---- ELT record preparation (FP64, once per record) --------------------------------------------
 
-// K = 1/(1 + d1/(1 + ...)) of DLMF 8.17.22 in binary64 by the Wallis recurrence of the
-// division-free equivalent fraction (partial numerators -(a+b)x, -(a+m)(a+b+m)x, m(b-m)x;
-// denominators a+n), rescaled by powers of two.
-__device__ double beta_cf_f64(double a, double b, double x) {
-  const double apb = a + b;
-  double Am2 = 1.0, Am1 = 1.0, Bm2 = 0.0, Bm1 = 1.0, prev = 1.0, res = 1.0;
-  for (int n = 1; n < 4000; n += 2) {
-    const double m = 0.5 * (double)(n - 1);
-    const double al_odd = (n == 1) ? -apb * x : -(a + m) * (apb + m) * x;
-    const double be_odd = a + (double)n;
-    double A = be_odd * Am1 + al_odd * Am2;
-    double B = be_odd * Bm1 + al_odd * Bm2;
-    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
-    const double m2 = m + 1.0;
-    const double al_even = m2 * (b - m2) * x;
-    const double be_even = a + (double)(n + 1);
-    A = be_even * Am1 + al_even * Am2;
-    B = be_even * Bm1 + al_even * Bm2;
-    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
-    int e;
-    frexp(Am1, &e);
-    Am1 = ldexp(Am1, -e); Am2 = ldexp(Am2, -e); Bm1 = ldexp(Bm1, -e); Bm2 = ldexp(Bm2, -e);
-    res = Bm1 / Am1;
-    if (fabs(res - prev) <= 1e-15 * fabs(res)) break;
-    prev = res;
-  }
-  return res;
-}
-
 // I_x(a,b) in binary64 (DLMF 8.17.22, with the symmetry DLMF 8.17.4 past (a+1)/(a+b+2)).
 __device__ double betainc_f64(double a, double b, double x) {
   const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
-  if (x < (a + 1.0) / (a + b + 2.0)) {
-    return exp(a * log(x) + b * log1p(-x) - lnB) * beta_cf_f64(a, b, x) / a;
-  }
-  const double y = 1.0 - x;
-  return 1.0 - exp(b * log(y) + a * log1p(-y) - lnB) * beta_cf_f64(b, a, y) / b;
+  return exp(ara_ln_betainc_f64(a, b, log(x), lnB));
 }
 
 // flags bit 3: id out of range; bit 4: mean <= 0 or sd < 0 or non-finite; bit 5: max <= mean
@@ -96,8 +64,8 @@ __device__ double betainc_f64(double a, double b, double x) {
 __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
                                    const double* __restrict__ mean, const double* __restrict__ sd,
                                    const double* __restrict__ mx, int32_t catalog,
-                                   BetaRec* __restrict__ recs, unsigned int* dup,
-                                   unsigned int* flags) {
+                                   BetaRec* __restrict__ recs, double2* __restrict__ ab64,
+                                   unsigned int* dup, unsigned int* flags) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   unsigned int f = 0;
@@ -111,6 +79,7 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
   BetaRec rec;
   rec.a = 0.f; rec.b = 0.f; rec.mx = (float)mu; rec.L0 = 0.f;
   rec.p0 = 0.5f; rec.lnx0 = 0.f; rec.lny0 = 0.f; rec.lns = 0.f;
+  double2 ab = make_double2(0.0, 0.0);
   if (!(mu > 0.0) || !(sigma >= 0.0) || !isfinite(mu) || !isfinite(sigma)) {
     f |= 16u;
   } else if (sigma > 0.0) {
@@ -136,10 +105,12 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
       rec.lnx0 = (float)lnx0;
       rec.lny0 = (float)lny0;
       rec.lns = (float)log(s);
+      ab = make_double2(a, b);
       if (!(rec.a > 0.f) || !(rec.b > 0.f)) f |= 16u;  // alpha or beta outside binary32 range
     }
   }
   recs[r] = rec;
+  ab64[r] = ab;
   if (f) atomicOr(flags, f);
 }
 
@@ -175,9 +146,10 @@ __global__ void layer_index_kernel(const uint32_t* __restrict__ mask,
 }
 
 __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
-                                     const BetaRec* __restrict__ recs, int slot, int mask_words,
+                                     const BetaRec* __restrict__ recs,
+                                     const TableRec* __restrict__ trecs, int slot, int mask_words,
                                      const uint32_t* __restrict__ evt, BetaRec* packed,
-                                     uint32_t* packed_rec) {
+                                     TableRec* tpacked, uint32_t* packed_rec) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t e = ids[r];
@@ -193,6 +165,7 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
     rank = __popcll(m & ((1ull << slot) - 1ull));
   }
   packed[base + rank] = recs[r];
+  tpacked[base + rank] = trecs[r];
   packed_rec[base + rank] = (uint32_t)r;
 }
 
@@ -301,10 +274,10 @@ cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStre
 
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
                                const double* sd, const double* mx, int32_t catalog,
-                               BetaRec* recs, unsigned int* d_dup, unsigned int* d_flags,
-                               cudaStream_t st) {
+                               BetaRec* recs, double2* ab64, unsigned int* d_dup,
+                               unsigned int* d_flags, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, mx, catalog, recs,
+  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, mx, catalog, recs, ab64,
                                                        d_dup, d_flags);
   count_launches(1);
   return cudaGetLastError();
@@ -348,11 +321,12 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
 }
 
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
-                                 const uint32_t* d_evt, BetaRec* packed, uint32_t* packed_rec,
-                                 cudaStream_t st) {
+                                 const uint32_t* d_evt, BetaRec* packed, TableRec* tpacked,
+                                 uint32_t* packed_rec, cudaStream_t st) {
   if (e.n == 0) return cudaSuccess;
-  layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, slot, mask_words,
-                                                           d_evt, packed, packed_rec);
+  layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, e.trecs, slot,
+                                                           mask_words, d_evt, packed, tpacked,
+                                                           packed_rec);
   count_launches(1);
   return cudaGetLastError();
 }

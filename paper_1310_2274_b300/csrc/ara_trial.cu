@@ -25,6 +25,7 @@
 
 #include "ara_ibeta.cuh"
 #include "ara_internal.h"
+#include "ara_mlp.cuh"
 #include "ara_philox.cuh"
 
 namespace ara {
@@ -70,14 +71,48 @@ struct AccKahan {
   __device__ double value() const { return (double)s - (double)c; }
 };
 
+// L2 residency (sm_100+ cache policies).  Per launch the kernel streams the 3.2 GB event-id
+// stream and, on the table path, one random 32-byte table piece per hit from tables of several
+// GB; both are read once and marked evict-first.  The lookup index and the record headers
+// (~45 MB, reused every few microseconds) are marked evict-last so the stream does not push them
+// out of the 126 MB L2.
+struct L2Policies {
+  unsigned long long keep, stream;
+  __device__ static L2Policies make() {
+    L2Policies p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.stream));
+    return p;
+  }
+};
+
+__device__ __forceinline__ int32_t ld_stream_s32(const int32_t* p, unsigned long long pol) {
+  int32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+               : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_keep_u2(const uint2* p, unsigned long long pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_keep_u4(const uint4* p, unsigned long long pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+
 template <int MW>
 struct Entry;
 template <>
 struct Entry<1> {
   uint32_t base;
   uint32_t m0;
-  __device__ static Entry load(const uint32_t* evt, int32_t e) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(evt) + e);
+  __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
+    const uint2 v = ld_keep_u2(reinterpret_cast<const uint2*>(evt) + e, pol);
     Entry r;
     r.base = v.x;
     r.m0 = v.y;
@@ -89,8 +124,8 @@ template <>
 struct Entry<2> {
   uint32_t base;
   uint32_t m0, m1;
-  __device__ static Entry load(const uint32_t* evt, int32_t e) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(evt) + e);
+  __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
+    const uint4 v = ld_keep_u4(reinterpret_cast<const uint4*>(evt) + e, pol);
     Entry r;
     r.base = v.x;
     r.m0 = v.y;
@@ -116,30 +151,67 @@ __device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
   return r;
 }
 
-template <int MW, class Acc, bool TRACE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    trial_kernel(const __grid_constant__ TrialParams P) {
-  __shared__ int32_t s_excl[kWarpsPerBlock][kChunk];
-  __shared__ uint32_t s_base[kWarpsPerBlock][kChunk];
-  __shared__ uint32_t s_mask[kWarpsPerBlock][MW][kChunk];
-  __shared__ float s_lsum[kWarpsPerBlock][kChunk];
+__device__ __forceinline__ TableRec load_trec(const TableRec* p, unsigned long long pol) {
+  const uint4 u = ld_keep_u4(reinterpret_cast<const uint4*>(p), pol);
+  TableRec r;
+  r.mx = __uint_as_float(u.x);
+  r.p0 = __uint_as_float(u.y);
+  const unsigned long long ptr = ((unsigned long long)u.w << 32) | (unsigned long long)u.z;
+  r.iv = reinterpret_cast<const float4*>(ptr);
+  return r;
+}
 
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
-  if (w >= P.n) return;  // whole warp leaves together; no block-wide barrier follows
+// The Newton inversion for the rare record whose table failed certification, kept out of line
+// so that its registers do not weigh on the table path.
+__device__ __noinline__ IbetaResult newton_fallback(const BetaRec* p, float u) {
+  return ara_inv_beta(load_rec(p), u);
+}
+
+// The table path is latency bound on its two dependent loads per hit (record header, then table
+// piece), so it is held to 64 registers for 4 blocks (32 warps) per SM; the Newton path keeps its
+// registers.
+// Surrogate inference for the round's hits: lanes with want set get the network's x (logit x =
+// kOutScale * y); the warp's 32 hits are two 16-row MMA tiles (lane 16 m + r is row r of tile m).
+__device__ __forceinline__ float surrogate_round(const MlpSmem& W, const float (&z)[3], int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  float y_t[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    float zr0[3], zr8[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zr0[c] = __shfl_sync(0xFFFFFFFFu, z[c], mt * 16 + g);
+      zr8[c] = __shfl_sync(0xFFFFFFFFu, z[c], mt * 16 + g + 8);
+    }
+    mlp_tile_forward(W, zr0, zr8, g, t, &y_t[mt][0], &y_t[mt][1]);
+  }
+  // row r of tile m sits in lanes 4 (r mod 8) .. 4 (r mod 8) + 3, component r >= 8
+  const int r = lane & 15, src = 4 * (r & 7);
+  const float a0 = __shfl_sync(0xFFFFFFFFu, y_t[0][0], src);
+  const float a8 = __shfl_sync(0xFFFFFFFFu, y_t[0][1], src);
+  const float b0 = __shfl_sync(0xFFFFFFFFu, y_t[1][0], src);
+  const float b8 = __shfl_sync(0xFFFFFFFFu, y_t[1][1], src);
+  const float y = lane < 16 ? (r < 8 ? a0 : a8) : (r < 8 ? b0 : b8);
+  return 1.0f / (1.0f + __expf(-kOutScale * y));
+}
+
+// The whole of Algorithm 1 for one trial (w-th of the launch item P), run by one warp.
+template <int MW, class Acc, bool TRACE, int INV>
+__device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, int lane, int wib,
+                                              int32_t* excl, uint32_t* sbase,
+                                              uint32_t (*s_maskw)[kChunk], float* lsum,
+                                              const MlpSmem* s_mlp) {
+  constexpr bool TABLE = INV == 0;
+  constexpr bool SURR = INV == 2;
   const int64_t trial = P.t0 + w;
   const int64_t beg = P.offsets[trial];
   const int64_t end = P.offsets[trial + 1];
 
-  int32_t* excl = s_excl[wib];
-  uint32_t* sbase = s_base[wib];
-  float* lsum = s_lsum[wib];
-
+  const L2Policies pol = L2Policies::make();
   Acc acc;
   int32_t trace_n = 0;
   unsigned int nc = 0;
-  unsigned int n_inv = 0, n_it = 0, n_cf = 0, n_hit = 0;
+  unsigned int n_inv = 0, n_it = 0, n_cf = 0, n_hit = 0, n_tab = 0, n_net = 0;
 
   for (int64_t c = beg; c < end; c += kChunk) {
     // ---- stream ids, look up entries, lay out the chunk's hits in event order ---------------
@@ -151,7 +223,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       en.base = 0;
       en.m0 = 0;
       if constexpr (MW == 2) en.m1 = 0;
-      if (q < end) en = Entry<MW>::load(P.evt, __ldg(P.ids + q));
+      if (q < end) en = Entry<MW>::load(P.evt, ld_stream_s32(P.ids + q, pol.stream), pol.keep);
       const int cnt = en.count();
       int incl = cnt;
 #pragma unroll
@@ -162,8 +234,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const int idx = v * 32 + lane;
       excl[idx] = run + incl - cnt;
       sbase[idx] = en.base;
-      s_mask[wib][0][idx] = en.m0;
-      if constexpr (MW == 2) s_mask[wib][1][idx] = en.m1;
+      s_maskw[0][idx] = en.m0;
+      if constexpr (MW == 2) s_maskw[1][idx] = en.m1;
       lsum[idx] = 0.f;
       run += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
@@ -173,50 +245,94 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     for (int32_t r0 = 0; r0 < run; r0 += 32) {
       const int32_t g = r0 + lane;
       const bool has = g < run;
-      int ev = 0;
-      float loss = 0.f;
+      int ev = 0, slot = 0;
+      uint32_t pos = 0, k = 0;
+      float loss = 0.f, u = 0.f, x = __int_as_float(0x7FC00000), mx = 0.f;
+      float surr_z[3] = {0.f, 0.f, 0.f};
+      bool net = false;
       if (has) {
         // largest event index whose exclusive prefix is <= g
 #pragma unroll
         for (int step = kChunk / 2; step >= 1; step >>= 1)
           if (excl[ev + step] <= g) ev += step;
         const int nth = g - excl[ev];
-        int slot;
         if constexpr (MW == 1) {
-          slot = nth_set_bit(s_mask[wib][0][ev], nth);
+          slot = nth_set_bit(s_maskw[0][ev], nth);
         } else {
-          const uint32_t m0 = s_mask[wib][0][ev];
+          const uint32_t m0 = s_maskw[0][ev];
           const int c0 = __popc(m0);
-          slot = nth < c0 ? nth_set_bit(m0, nth) : 32 + nth_set_bit(s_mask[wib][1][ev], nth - c0);
+          slot = nth < c0 ? nth_set_bit(m0, nth) : 32 + nth_set_bit(s_maskw[1][ev], nth - c0);
         }
-        const uint32_t pos = sbase[ev] + (uint32_t)nth;
-        const BetaRec rec = load_rec(P.recs + pos);
-        const uint32_t k = (uint32_t)(c - beg) + (uint32_t)ev;
-        float u = 0.f, x = __int_as_float(0x7FC00000);
-        if (rec.a > 0.f) {
-          u = su_uniform(P.seed, trial, k, P.handles[slot]);
-          const IbetaResult ib = ara_inv_beta(rec, u);
-          x = ib.x;
-          nc += ib.converged ? 0u : 1u;
-          n_inv += 1u;
-          n_it += (unsigned)ib.iters;
-          n_cf += (unsigned)ib.cf_terms;
-          loss = rec.mx * x;
+        pos = sbase[ev] + (uint32_t)nth;
+        k = (uint32_t)(c - beg) + (uint32_t)ev;
+        bool sd0 = false, use_table = false;
+        TableRec tr;
+        if constexpr (TABLE) {
+          tr = load_trec(P.trecs + pos, pol.keep);
+          sd0 = tr.p0 < 0.f;
+          mx = tr.mx;
+          use_table = tr.iv != nullptr;
         } else {
-          loss = rec.mx;  // sd = 0: the mean (primary uncertainty only)
-          if (TRACE) u = su_uniform(P.seed, trial, k, P.handles[slot]);
+          tr.iv = nullptr;
         }
-        if constexpr (TRACE) {
-          const int32_t th = trace_n + g;
-          if (th < P.trace_cap) {
-            const int64_t o = w * P.trace_cap + th;
-            P.tr_k[o] = (int32_t)k;
-            P.tr_j[o] = slot;
-            P.tr_rec[o] = (int32_t)P.rec_idx[pos];
-            P.tr_u[o] = u;
-            P.tr_x[o] = x;
-            P.tr_loss[o] = loss;
+        BetaRec rec;
+        if (!TABLE) {
+          rec = load_rec(P.recs + pos);
+          sd0 = !(rec.a > 0.f);
+          mx = rec.mx;
+        }
+        if (!sd0 || TRACE) u = su_uniform(P.seed, trial, k, P.handles[slot]);
+        if constexpr (SURR) {
+          // the network serves this hit if (alpha, beta) lies in its box and the certified error
+          // of the hit's cell is within eps; all lanes then evaluate it together below
+          if (!sd0 && rec.a >= kBoxLo && rec.a <= kBoxHi && rec.b >= kBoxLo && rec.b <= kBoxHi) {
+            surr_z[0] = (logf(rec.a) - kLnCenter) / kLnHalf;
+            surr_z[1] = (logf(rec.b) - kLnCenter) / kLnHalf;
+            surr_z[2] = (logf(u) - log1pf(-u)) / kLogitScale;
+            const int i0 = min(max((int)((surr_z[0] + 1.0f) * (0.5f * kCert0)), 0), kCert0 - 1);
+            const int i1 = min(max((int)((surr_z[1] + 1.0f) * (0.5f * kCert1)), 0), kCert1 - 1);
+            const int i2 = min(max((int)((surr_z[2] + 1.0f) * (0.5f * kCert2)), 0), kCert2 - 1);
+            net = __ldg(P.mlp_bound + ((i0 * kCert1) + i1) * kCert2 + i2) <= P.mlp_eps;
           }
+        }
+        if (sd0) {
+          loss = mx;  // sd = 0: the mean (primary uncertainty only)
+        } else if (!net) {
+          if (TABLE && use_table) {
+            x = ara_table_quantile(tr, u);
+            n_tab += 1u;
+          } else {
+            const IbetaResult ib =
+                INV == 1 ? ara_inv_beta(rec, u) : newton_fallback(P.recs + pos, u);
+            x = ib.x;
+            nc += ib.converged ? 0u : 1u;
+            n_inv += 1u;
+            n_it += (unsigned)ib.iters;
+            n_cf += (unsigned)ib.cf_terms;
+          }
+          loss = mx * x;
+        }
+      }
+      if constexpr (SURR) {
+        if (__any_sync(0xFFFFFFFFu, net)) {
+          const float xs = surrogate_round(*s_mlp, surr_z, lane);
+          if (net) {
+            x = xs;
+            loss = mx * x;
+            n_net += 1u;
+          }
+        }
+      }
+      if constexpr (TRACE) {
+        const int32_t th = trace_n + g;
+        if (has && th < P.trace_cap) {
+          const int64_t o = w * P.trace_cap + th;
+          P.tr_k[o] = (int32_t)k;
+          P.tr_j[o] = slot;
+          P.tr_rec[o] = (int32_t)P.rec_idx[pos];
+          P.tr_u[o] = u;
+          P.tr_x[o] = x;
+          P.tr_loss[o] = loss;
         }
       }
       // segmented inclusive scan over lanes: segments are the runs of equal ev
@@ -254,6 +370,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   n_inv = __reduce_add_sync(0xFFFFFFFFu, n_inv);
   n_it = __reduce_add_sync(0xFFFFFFFFu, n_it);
   n_cf = __reduce_add_sync(0xFFFFFFFFu, n_cf);
+  n_tab = __reduce_add_sync(0xFFFFFFFFu, n_tab);
+  n_net = __reduce_add_sync(0xFFFFFFFFu, n_net);
   if (lane == 0) {
     const double S = acc.value();
     P.ylt[w] = fmin(fmax(S - P.agg_ret, 0.0), P.agg_lim);
@@ -262,33 +380,128 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     atomicAdd(P.stats + 1, (unsigned long long)n_it);
     atomicAdd(P.stats + 2, (unsigned long long)n_cf);
     atomicAdd(P.stats + 3, (unsigned long long)n_hit);
+    if (n_tab) atomicAdd(P.stats + 4, (unsigned long long)n_tab);
+    if (n_net) atomicAdd(P.stats + 5, (unsigned long long)n_net);
     if constexpr (TRACE) P.tr_count[w] = trace_n;
   }
 }
 
-template <int MW, class Acc, bool TRACE>
+// INV: 0 certified tables (Newton fallback), 1 Newton, 2 learned surrogate (Newton fallback).
+// The table path is latency bound on its two dependent loads per hit (record header, then table
+// piece), so it is held to 64 registers for 4 blocks (32 warps) per SM.
+template <int MW, class Acc, bool TRACE, int INV>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 ? 3 : 1))
+    trial_kernel(const __grid_constant__ TrialParams P) {
+  __shared__ int32_t s_excl[kWarpsPerBlock][kChunk];
+  __shared__ uint32_t s_base[kWarpsPerBlock][kChunk];
+  __shared__ uint32_t s_mask[kWarpsPerBlock][MW][kChunk];
+  __shared__ float s_lsum[kWarpsPerBlock][kChunk];
+  __shared__ __align__(16) MlpSmem s_mlp[1];
+  if constexpr (INV == 2) {  // network weights, once per block, before any warp may leave
+    const uint4* src = reinterpret_cast<const uint4*>(P.mlp);
+    uint4* dst = reinterpret_cast<uint4*>(&s_mlp[0]);
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+  if (w >= P.n) return;  // whole warp leaves together; no block-wide barrier follows
+  process_trial<MW, Acc, TRACE, INV>(P, w, lane, wib, s_excl[wib], s_base[wib], s_mask[wib],
+                                     s_lsum[wib], &s_mlp[0]);
+}
+
+// One launch over many work items (serving: slices of different requests, each with its own
+// layer and YLT): warp w runs trial w - warp_begin[i] of the item i with warp_begin[i] <= w.
+template <int MW, class Acc, int INV>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 ? 3 : 1))
+    batch_kernel(const TrialParams* __restrict__ items, const int64_t* __restrict__ warp_begin,
+                 int n_items, int64_t total_warps) {
+  __shared__ int32_t s_excl[kWarpsPerBlock][kChunk];
+  __shared__ uint32_t s_base[kWarpsPerBlock][kChunk];
+  __shared__ uint32_t s_mask[kWarpsPerBlock][MW][kChunk];
+  __shared__ float s_lsum[kWarpsPerBlock][kChunk];
+  __shared__ __align__(16) MlpSmem s_mlp[1];
+  if constexpr (INV == 2) {
+    const uint4* src = reinterpret_cast<const uint4*>(items[0].mlp);
+    uint4* dst = reinterpret_cast<uint4*>(&s_mlp[0]);
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+  if (w >= total_warps) return;
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {  // largest item whose first warp is <= w
+    const int mid = (lo + hi + 1) >> 1;
+    if (warp_begin[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  process_trial<MW, Acc, false, INV>(items[lo], w - warp_begin[lo], lane, wib, s_excl[wib],
+                                     s_base[wib], s_mask[wib], s_lsum[wib], &s_mlp[0]);
+}
+
+template <int MW, class Acc, bool TRACE, int INV>
 cudaError_t launch_one(const TrialParams& p, cudaStream_t st) {
   const int64_t blocks = (p.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks == 0) return cudaSuccess;
-  trial_kernel<MW, Acc, TRACE><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(p);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kWarpsPerBlock * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, trial_kernel<MW, Acc, TRACE, INV>, p);
+  count_launches(1);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int INV>
+cudaError_t launch_mode(const TrialParams& p, int mask_words, int precision, bool trace,
+                        cudaStream_t st) {
+  if (trace) {
+    return mask_words == 1 ? launch_one<1, AccF64, true, INV>(p, st)
+                           : launch_one<2, AccF64, true, INV>(p, st);
+  }
+  if (precision == 1) {
+    return mask_words == 1 ? launch_one<1, AccKahan, false, INV>(p, st)
+                           : launch_one<2, AccKahan, false, INV>(p, st);
+  }
+  return mask_words == 1 ? launch_one<1, AccF64, false, INV>(p, st)
+                         : launch_one<2, AccF64, false, INV>(p, st);
+}
+
+template <class Acc, int INV>
+cudaError_t launch_batch_mode(const TrialParams* d_items, const int64_t* d_warp_begin,
+                              int n_items, int64_t total_warps, cudaStream_t st) {
+  const int64_t blocks = (total_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks == 0) return cudaSuccess;
+  batch_kernel<2, Acc, INV><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
+      d_items, d_warp_begin, n_items, total_warps);
   count_launches(1);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, bool trace,
-                         cudaStream_t st) {
-  if (trace) {
-    return mask_words == 1 ? launch_one<1, AccF64, true>(p, st)
-                           : launch_one<2, AccF64, true>(p, st);
-  }
+cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp_begin,
+                               int n_items, int64_t total_warps, int precision, int inversion,
+                               cudaStream_t st) {
   if (precision == 1) {
-    return mask_words == 1 ? launch_one<1, AccKahan, false>(p, st)
-                           : launch_one<2, AccKahan, false>(p, st);
+    if (inversion == 2) return launch_batch_mode<AccKahan, 2>(d_items, d_warp_begin, n_items, total_warps, st);
+    if (inversion == 1) return launch_batch_mode<AccKahan, 1>(d_items, d_warp_begin, n_items, total_warps, st);
+    return launch_batch_mode<AccKahan, 0>(d_items, d_warp_begin, n_items, total_warps, st);
   }
-  return mask_words == 1 ? launch_one<1, AccF64, false>(p, st)
-                         : launch_one<2, AccF64, false>(p, st);
+  if (inversion == 2) return launch_batch_mode<AccF64, 2>(d_items, d_warp_begin, n_items, total_warps, st);
+  if (inversion == 1) return launch_batch_mode<AccF64, 1>(d_items, d_warp_begin, n_items, total_warps, st);
+  return launch_batch_mode<AccF64, 0>(d_items, d_warp_begin, n_items, total_warps, st);
+}
+
+cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, int inversion,
+                         bool trace, cudaStream_t st) {
+  if (inversion == 2) return launch_mode<2>(p, mask_words, precision, trace, st);
+  return inversion == 0 ? launch_mode<0>(p, mask_words, precision, trace, st)
+                        : launch_mode<1>(p, mask_words, precision, trace, st);
 }
 
 }  // namespace ara

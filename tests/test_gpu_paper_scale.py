@@ -39,6 +39,24 @@ def test_paper_scale_sampled_trials(oracle, paper):
     assert np.count_nonzero(o) >= len(pick) // 2
 
 
+def test_paper_scale_newton_path_sampled(ara, oracle, paper):
+    w, c, (yet, elts, layer), ylt_table = paper
+    c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+    try:
+        ylt = c.run(yet, layer, 0, w.yet.n_trials)
+    finally:
+        c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+    pick = synth.subset_trials(w.yet.n_trials, 24, seed=11)
+    o, _ = oracle.run(w.yet, w.elts, w.terms, 42, trials=pick, elt_handles=elts)
+    scale = np.maximum(np.maximum(np.abs(o), w.terms.agg_ret), 1.0)
+    assert np.max(np.abs(ylt[pick] - o) / scale) <= YLT_TOL
+    # the two inversions agree everywhere to well inside the tolerance
+    scale_all = np.maximum(ylt, w.terms.agg_ret)
+    assert np.max(np.abs(ylt - ylt_table) / scale_all) <= 2e-6
+    st = c.stats()
+    assert st["uncertified"] <= 0.005 * sum(e.n for e in w.elts)
+
+
 def test_paper_scale_properties(paper):
     w, c, _, ylt = paper
     assert ylt.shape == (800_000,)

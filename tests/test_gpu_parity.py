@@ -38,7 +38,15 @@ def tiny(ctx):
     return w, yet, elts, layer
 
 
-def test_tiny_ylt_matches_oracle(ctx, oracle, tiny):
+@pytest.fixture(params=["table", "newton"])
+def inversion(request, ara, ctx):
+    mode = {"table": ara.INV_TABLE, "newton": ara.INV_NEWTON}[request.param]
+    ctx.set_option(ara.OPT_INVERSION, mode)
+    yield request.param
+    ctx.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+
+
+def test_tiny_ylt_matches_oracle(ctx, oracle, tiny, inversion):
     w, yet, elts, layer = tiny
     g = ctx.run(yet, layer, 0, w.yet.n_trials)
     o, nc = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
@@ -49,7 +57,7 @@ def test_tiny_ylt_matches_oracle(ctx, oracle, tiny):
     assert np.count_nonzero(o) > 100  # the terms leave a non-trivial YLT
 
 
-def test_tiny_trace_bit_exact_lookups_and_uniforms(ctx, oracle, tiny):
+def test_tiny_trace_bit_exact_lookups_and_uniforms(ctx, oracle, tiny, inversion):
     w, yet, elts, layer = tiny
     trials = np.arange(200)
     gh, gy = ctx.trace(yet, layer, 0, 200)
@@ -70,7 +78,7 @@ def test_tiny_trace_bit_exact_lookups_and_uniforms(ctx, oracle, tiny):
     np.testing.assert_array_equal(gy, ctx.run(yet, layer, 0, 200))
 
 
-def test_tiny_risk_measures_end_to_end(ctx, oracle, tiny):
+def test_tiny_risk_measures_end_to_end(ctx, oracle, tiny, inversion):
     w, yet, elts, layer = tiny
     g = ctx.run(yet, layer, 0, w.yet.n_trials)
     o, _ = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
@@ -114,7 +122,7 @@ def test_rank_from_device_memory(ctx, oracle):
     np.testing.assert_array_equal(out.cpu().numpy(), oracle.rank(y))
 
 
-def test_ragged_multi_elt_and_zero_sigma(ctx, oracle):
+def test_ragged_multi_elt_and_zero_sigma(ctx, oracle, inversion):
     yet_h = synth.make_ragged_yet(400, 0, 300, 3000, seed=12)
     elts_h = [synth.make_elt(n, 3000, seed=40 + s) for s, n in enumerate([900, 50, 1400])]
     elts_h[1].sd[:] = 0.0  # primary uncertainty only for one ELT
@@ -139,7 +147,7 @@ def test_ragged_multi_elt_and_zero_sigma(ctx, oracle):
     np.testing.assert_array_equal(gh["loss"][sig0].astype(np.float64), oh["loss"][sig0])
 
 
-def test_wide_layer_uses_two_mask_words(ctx, oracle):
+def test_wide_layer_uses_two_mask_words(ctx, oracle, inversion):
     yet_h = synth.make_yet(150, 120, 4000, seed=21)
     elts_h = [synth.make_elt(150 + 7 * s, 4000, seed=100 + s) for s in range(40)]
     terms = synth.Terms(1e5, 1e7, 5e5, 5e8)
@@ -190,7 +198,7 @@ def test_seed_option_changes_draws(ara, tiny):
     assert not np.array_equal(a, b)
 
 
-def test_kahan_accumulation_matches_fp64(ara, ctx, oracle, tiny):
+def test_kahan_accumulation_matches_fp64(ara, ctx, oracle, tiny, inversion):
     w, yet, elts, layer = tiny
     g64 = ctx.run(yet, layer, 0, w.yet.n_trials)
     ctx.set_option(ara.OPT_PRECISION, ara.ACC_KAHAN32)
@@ -258,3 +266,48 @@ def test_handle_and_range_errors(ara, ctx, tiny):
         ctx.risk_measures(np.array([1.0, np.nan]), [10.0])
     with pytest.raises(ara.AraError):
         ctx.risk_measures(np.array([1.0, 2.0]), [1.0])
+
+
+def test_tables_are_certified_and_used(ara, ctx, tiny):
+    w, yet, elts, layer = tiny
+    s0 = ctx.stats()
+    ctx.run(yet, layer, 0, w.yet.n_trials)
+    s1 = ctx.stats()
+    hits = s1["hits"] - s0["hits"]
+    tab = s1["table_evals"] - s0["table_evals"]
+    newton = s1["inversions"] - s0["inversions"]
+    assert hits > 10_000 and tab + newton == hits  # every hit of this ELT has sd > 0
+    assert newton <= 0.005 * hits  # records whose table failed certification fall back
+    assert s1["uncertified"] <= 0.005 * sum(e.n for e in w.elts) + 5
+
+
+def test_extreme_shapes_tables_match_newton(ara, oracle):
+    # beta parameters spread over [0.1, 100]^2 (far wider than the workload's), one event each
+    rng = np.random.default_rng(17)
+    n = 3000
+    a = np.exp(rng.uniform(np.log(0.1), np.log(100.0), n))
+    b = np.exp(rng.uniform(np.log(0.1), np.log(100.0), n))
+    mx = np.full(n, 1.0e6)
+    mean = mx * a / (a + b)
+    sd = mx * np.sqrt(a * b / ((a + b) ** 2 * (a + b + 1)))
+    f32 = lambda v: v.astype(np.float32).astype(np.float64)
+    mean, sd = f32(mean), f32(sd)
+    elt = synth.Elt(np.arange(n, dtype=np.int32), mean, sd, mx)
+    yet_h = synth.make_yet(40, n, n, seed=23)
+    yet_h.event_ids = np.tile(np.arange(n, dtype=np.int32), 40)
+    terms = synth.Terms(0.0, 1e12, 0.0, 1e15)
+    with ara.Context(seed=42) as c:
+        yet = c.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, n)
+        e = c.add_elt(yet, elt.event_ids, elt.mean, elt.sd, elt.max_exposure)
+        layer = c.add_layer([e], *terms.__dict__.values())
+        assert c.stats()["uncertified"] <= 0.05 * n
+        gt, _ = c.trace(yet, layer, 0, 4)
+        c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+        gn, _ = c.trace(yet, layer, 0, 4)
+    oh, _ = oracle.trace(yet_h, [elt], terms, 42, np.arange(4), elt_handles=[e])
+    for g in (gt, gn):
+        np.testing.assert_array_equal(g["rec"], oh["rec"])
+        dx = np.abs(g["x"].astype(np.float64) - oh["x"])
+        assert dx.max() <= 2e-6
+        # loss-weighted relative error
+        assert dx.sum() / oh["x"].sum() <= 1e-6
