@@ -61,7 +61,7 @@ FLOP_PER_INVERSION = 14.0 + 2.0
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--trials", type=int, default=800_000)
@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=100)
     return p.parse_args()
 
 
@@ -113,7 +115,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -206,21 +208,26 @@ def run_reference(a):
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
-def traffic_for_current_kernel():
-    """DRAM bytes per launch of the trial kernel from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def traffic_for_current_kernel(name="trial_kernel_table_50000x1000x16.md",
+                               files=("ara_trial.cu", "ara_ibeta.cuh", "ara_philox.cuh")):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if that
+    capture was taken on the current kernel source (else None)."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "trial_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ")):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("ara_trial.cu", "ara_ibeta.cuh", "ara_philox.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1310_2274_b300", "csrc", f), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("source_sha256") != h.hexdigest() or "dram_bytes_per_launch" not in rec:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return float(rec["dram_bytes_per_launch"])
 
 
 def run_ours(a):
@@ -298,6 +305,8 @@ def run_ours(a):
                     + BYTES_PER_TRIAL * n)
     achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
     traffic = traffic_for_current_kernel()
+    if traffic is not None:
+        traffic *= n / 800_000  # the summary states bytes for an 800,000-trial launch
 
     # ---- the Newton inversion on the same data (secondary figure) -----------------------------
     ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
@@ -353,6 +362,10 @@ def run_ours(a):
         "seconds_per_run": step_ms * 1e-3,
     }
 
+    # ---- continuous-batching service on the resident YET (64 ELTs) ---------------------------
+    if not a.no_serve and rank == 0:
+        result["serving"] = serving(a, ara, ctx, yet, elts, dev)
+
     # ---- end to end through the public API with host buffers ---------------------------------
     if not a.no_e2e:
         result["e2e"] = e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream)
@@ -366,6 +379,54 @@ def run_ours(a):
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
+
+
+def serving(a, ara, ctx, yet, elts16, dev):
+    """Poisson arrivals (20 requests/s, seed 11) of layer requests against the resident YET and
+    64 ELTs (seeds 2..65): ELT count U{1..64}, trials U{10,000..N} (prefix ranges), terms
+    log-uniform around the paper-scale layer's.  Reports latency percentiles and throughput."""
+    import torch
+
+    more = synth.paper_elts(64 - len(elts16), first_seed=2 + len(elts16))
+    elts = list(elts16) + [ctx.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure)
+                           for e in more]
+    torch.cuda.synchronize(dev)
+    rng = np.random.default_rng(11)
+    n_req = a.serve_requests
+    gaps = rng.exponential(1.0 / 20.0, size=n_req)
+    reqs = []
+    for _ in range(n_req):
+        k = int(rng.integers(1, 65))
+        pick = [elts[i] for i in np.sort(rng.choice(64, size=k, replace=False))]
+        lu = lambda lo, hi: float(np.exp(rng.uniform(np.log(lo), np.log(hi))))  # noqa: E731
+        scale = k / 16.0
+        reqs.append(dict(elts=pick, occ_ret=lu(3e4, 3e5), occ_lim=lu(3e6, 3e7),
+                         agg_ret=scale * lu(1.25e8, 5e8), agg_lim=scale * lu(1.25e8, 5e8),
+                         t0=0, n_trials=int(rng.integers(10_000, a.trials + 1)),
+                         rps=synth.RPS_PAPER))
+    evals = sum(r["n_trials"] * a.events * len(r["elts"]) for r in reqs)
+    with ara.Server(ctx, yet, max_inflight=16, slice_trials=65536,
+                    max_batch_trials=1 << 20) as srv:
+        t = time.perf_counter()
+        tickets = []
+        for r, g in zip(reqs, gaps):
+            time.sleep(g)
+            tickets.append(srv.submit(**r))
+        for tk in tickets:
+            if srv.wait(tk, 300.0) != 0:
+                raise RuntimeError(f"serving request {tk} failed")
+        wall = time.perf_counter() - t
+        st = srv.stats()
+    for h in elts[len(elts16):]:
+        ctx.free_elt(h)
+    return {"requests": n_req, "arrival_rate_per_s": 20.0, "wall_s": wall,
+            "latency_p50_ms": st["latency_p50_s"] * 1e3, "latency_p99_ms": st["latency_p99_s"] * 1e3,
+            "latency_max_ms": st["latency_max_s"] * 1e3,
+            "requests_per_s": st["requests_per_s"], "evals_per_s": evals / wall,
+            "mean_requests_per_launch": st["mean_items_per_launch"],
+            "launches": st["launches"], "failed": st["failed"],
+            "workload": "resident YET + 64 paper-scale ELTs; Poisson 20/s, seed 11; ELTs "
+                        "U{1..64}, trials U{10000..N} prefixes"}
 
 
 def e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream):
