@@ -71,6 +71,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--schedule", choices=["band", "trial"], default="band")
     p.add_argument("--serve-requests", type=int, default=100)
     return p.parse_args()
 
@@ -251,6 +252,8 @@ def run_ours(a):
 
     stream = torch.cuda.current_stream(dev)
     ctx = ara.Context(seed=42, device=local)
+    SCHEDULE = ara.SCHED_BAND if a.schedule == "band" else ara.SCHED_TRIAL
+    ctx.set_option(ara.OPT_SCHEDULE, SCHEDULE)
     ctx.set_stream(stream)
     yet = ctx.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 2_000_000)
     elts = [ctx.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
@@ -308,6 +311,25 @@ def run_ours(a):
     if traffic is not None:
         traffic *= n / 800_000  # the summary states bytes for an 800,000-trial launch
 
+    # ---- the other schedule of the table path on the same data --------------------------------
+    def time_runs(k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+    other = ara.SCHED_TRIAL if SCHEDULE == ara.SCHED_BAND else ara.SCHED_BAND
+    ctx.set_option(ara.OPT_SCHEDULE, other)
+    ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+    other_ms = time_runs(max(3, min(10, a.steps)))
+    ctx.set_option(ara.OPT_SCHEDULE, SCHEDULE)
+    sched_ms = {("band" if SCHEDULE == ara.SCHED_BAND else "trial"): kern_ms,
+                ("band" if other == ara.SCHED_BAND else "trial"): other_ms}
+
     # ---- the Newton inversion on the same data (secondary figure) -----------------------------
     ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
     ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
@@ -343,7 +365,9 @@ def run_ours(a):
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "trial_kernel, certified-table inversion (one warp per trial)",
+                     "kernel": ("band_kernel + band_finalize_kernel, certified-table inversion "
+                                "(catalogue bands in L2)" if a.schedule == "band" else
+                                "trial_kernel, certified-table inversion (one warp per trial)"),
                      "kernel_ms": kern_ms, "bytes_per_launch": bytes_launch,
                      "per_launch": {k: d[k] for k in ("hits", "table_evals", "inversions")},
                      "peak_source": "measured hbm_gbs in MEASURED_PEAKS.json (burst copy)"},
@@ -356,6 +380,7 @@ def run_ours(a):
                                                                         "cf_terms")},
                                      "peak_source": f"FP32 FMA peak 2 x {SM_COUNT} SMs x "
                                                     f"{FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"}},
+        "schedules_ms": sched_ms,
         "uncertified_records": s1["uncertified"],
         "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
                           "tvar": [float(v) for v in tvar]},

@@ -69,7 +69,7 @@ ARA_API const char* ara_status_string(ara_status s);
 /* Copies the detail of the last failed call on ctx (NUL-terminated, truncated to n bytes). */
 ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n);
 /* Options settable after creation: ARA_OPT_PRECISION (value ARA_ACC_*), ARA_OPT_SEED,
- * ARA_OPT_SURROGATE (0/1), ARA_OPT_INVERSION (value ARA_INV_*).
+ * ARA_OPT_SURROGATE (0/1), ARA_OPT_INVERSION (value ARA_INV_*), ARA_OPT_SCHEDULE (ARA_SCHED_*).
  * Inversion of the beta CDF (paper §3.3, InvCDF_beta):
  *   ARA_INV_TABLE (default): each record's quantile function, tabulated when its ELT is staged
  *     (32 quintic pieces per tail in t = sqrt(-2 ln u), certified at every piece's midpoint to
@@ -81,6 +81,22 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_OPT_INVERSION 4
 #define ARA_INV_TABLE 0
 #define ARA_INV_NEWTON 1
+/* ARA_OPT_SCHEDULE (value ARA_SCHED_*), for the table inversion:
+ *   ARA_SCHED_BAND (default): the catalogue is cut into bands of 2^w events (w chosen per layer
+ *     so that one band's lookup entries, record headers and tables fit in L2); ara_add_layer
+ *     builds a band-major copy of the YET's event ids for that w once (4 bytes per occurrence
+ *     plus 4 per (band, trial)), and ara_run visits the work band by band, each band's year sums
+ *     kept apart and combined in band order;
+ *   ARA_SCHED_TRIAL: one warp per trial over its events in order (also used by the Newton and
+ *     surrogate inversions, and by layers whose YET cannot be banded: more than 2^32
+ *     occurrences, trials longer than 2^(32-w) events, or more than 512 bands).
+ * Both give the same hits, uniforms and losses; year sums differ only in summation order. */
+#define ARA_OPT_SCHEDULE 5
+#define ARA_SCHED_BAND 0
+#define ARA_SCHED_TRIAL 1
+/* ARA_OPT_BAND_WIDTH: the band width 2^w (value w in 10..20) of layers created afterwards;
+ * 0 (default) chooses w per layer from its record count.  Results do not depend on w. */
+#define ARA_OPT_BAND_WIDTH 6
 ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
 
 /* Year Event Table (paper §2.1) ------------------------------------------------------------------

@@ -22,6 +22,9 @@ ACC_FP64 = 0
 ACC_KAHAN32 = 1
 OPT_PRECISION, OPT_SEED, OPT_SURROGATE, OPT_INVERSION = 1, 2, 3, 4
 INV_TABLE, INV_NEWTON = 0, 1
+OPT_SCHEDULE = 5
+OPT_BAND_WIDTH = 6
+SCHED_BAND, SCHED_TRIAL = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",
           5: "inversion did not converge", 6: "busy", 7: "no CUDA device"}
 

@@ -15,6 +15,7 @@
 #include "../../include/ara.h"
 #include "ara_internal.h"
 #include "ara_ctx.h"
+#include "ara_philox.cuh"
 
 using namespace ara;
 
@@ -72,6 +73,7 @@ cudaError_t copy_in(T* dst, const T* src, int64_t n, cudaStream_t st) {
 }
 
 void free_yet(YetDev& y) {
+  for (auto& v : y.bands) free_band_variant(v);
   dev_free(y.ids);
   dev_free(y.ts);
   dev_free(y.offsets);
@@ -108,6 +110,16 @@ ara_status ensure_ylt_tmp(ara_ctx* c, int64_t n) {
   c->ylt_tmp_cap = 0;
   CUDA_TRY(c, dev_alloc(&c->d_ylt_tmp, n));
   c->ylt_tmp_cap = n;
+  return ARA_OK;
+}
+
+ara_status ensure_ysum(ara_ctx* c, int64_t n) {
+  if (n <= c->ysum_cap) return ARA_OK;
+  dev_free(c->d_ysum);
+  c->d_ysum = nullptr;
+  c->ysum_cap = 0;
+  CUDA_TRY(c, dev_alloc(&c->d_ysum, n));
+  c->ysum_cap = n;
   return ARA_OK;
 }
 
@@ -192,8 +204,9 @@ ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
       cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       (ctx->stream = ctx->own_stream, false) ||
       dev_alloc(&ctx->d_not_conv, 1) != cudaSuccess || dev_alloc(&ctx->d_flags, 4) != cudaSuccess ||
-      dev_alloc(&ctx->d_stats, 6) != cudaSuccess ||
-      cudaMemsetAsync(ctx->d_stats, 0, 6 * sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+      dev_alloc(&ctx->d_stats, kStatCounters * kStatStripes) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_stats, 0, sizeof(unsigned long long) * kStatCounters * kStatStripes,
+                      ctx->stream) != cudaSuccess ||
       cudaMalloc(&ctx->d_misc, 4096) != cudaSuccess ||
       cudaMemsetAsync(ctx->d_not_conv, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -220,6 +233,7 @@ void ara_destroy(ara_ctx* ctx) {
   dev_free(ctx->sort.scan_tmp);
   dev_free(ctx->sort.digit_flags);
   dev_free(ctx->d_ylt_tmp);
+  dev_free(ctx->d_ysum);
   dev_free(ctx->d_not_conv);
   dev_free(ctx->d_stats);
   dev_free(ctx->d_flags);
@@ -262,6 +276,16 @@ ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value) {
       if (value == 1 && !ctx->mlp_ready)
         return fail(ctx, ARA_ERR_INVALID_ARG, "no surrogate trained or loaded");
       ctx->cfg.use_surrogate = (int32_t)value;
+      return ARA_OK;
+    case ARA_OPT_BAND_WIDTH:
+      if (value != 0 && (value < 10 || value > 20))
+        return fail(ctx, ARA_ERR_INVALID_ARG, "band width exponent must be 0 or 10..20");
+      ctx->band_log2w = (int32_t)value;
+      return ARA_OK;
+    case ARA_OPT_SCHEDULE:
+      if (value != ARA_SCHED_BAND && value != ARA_SCHED_TRIAL)
+        return fail(ctx, ARA_ERR_INVALID_ARG, "schedule must be ARA_SCHED_BAND or ARA_SCHED_TRIAL");
+      ctx->schedule = (int32_t)value;
       return ARA_OK;
   }
   return fail(ctx, ARA_ERR_INVALID_ARG, "unknown option %d", option);
@@ -558,6 +582,26 @@ ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
     free_layer(L);
     return fail(ctx, ARA_ERR_CUDA, "layer records: %s", cudaGetErrorString(err));
   }
+  // band-major copy of the YET at this layer's band width (built once per width)
+  const int log2w = ctx->band_log2w > 0 ? ctx->band_log2w : choose_band_log2w(C, L.n_packed);
+  YetDev& Y = ctx->yets[yet];
+  if (band_layout_fits(Y, log2w)) {
+    int slot = -1;
+    for (int v = 0; v < kMaxBandVariants && slot < 0; ++v)
+      if (Y.bands[v].log2w == log2w) slot = v;
+    for (int v = 0; v < kMaxBandVariants && slot < 0; ++v)
+      if (Y.bands[v].log2w == 0) {
+        err = build_band_variant(Y, log2w, Y.bands[v], ctx->stream);
+        if (err != cudaSuccess) {
+          cudaGetLastError();
+          free_layer(L);
+          return fail(ctx, err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA,
+                      "band-major YET copy: %s", cudaGetErrorString(err));
+        }
+        slot = v;
+      }
+    if (slot >= 0) L.band_log2w = log2w;
+  }
   L.live = true;
   ctx->layers.push_back(L);
   *layer_out = (int32_t)ctx->layers.size() - 1;
@@ -601,6 +645,11 @@ static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64
 
 }  // extern "C"
 
+bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
+  return inversion_mode(ctx) == 0 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
+         ctx->cfg.precision == ARA_ACC_FP64;
+}
+
 int inversion_mode(const ara_ctx* ctx) {
   if (ctx->cfg.use_surrogate && ctx->mlp_ready) return 2;
   return ctx->inversion;
@@ -623,11 +672,26 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   p.agg_ret = L.agg_ret;
   p.agg_lim = L.agg_lim;
   p.seed = ctx->cfg.seed;
+  ara::philox_round_keys(p.seed, p.rk0, p.rk1);
   p.t0 = t0;
   p.n = n;
   p.ylt = d_ylt;
   p.not_conv = ctx->d_not_conv;
   p.stats = ctx->d_stats;
+  p.yet_n = Y.n_trials;
+  const int qe = year_grid_exponent((float)L.occ_lim, Y.max_len);
+  p.q_scale = std::ldexp(1.0f, -qe);
+  p.q_unit = std::ldexp(1.0, qe);
+  if (L.band_log2w > 0) {
+    for (const auto& v : Y.bands)
+      if (v.log2w == L.band_log2w) {
+        p.bocc = v.occ;
+        p.boff = v.off;
+        p.log2w = v.log2w;
+        p.kbits = v.kbits;
+        p.n_bands = v.n_bands;
+      }
+  }
   if (ctx->cfg.use_surrogate && ctx->mlp_ready) {
     p.mlp = &ctx->mlp_W->fwd;
     p.mlp_bound = ctx->mlp_bound;
@@ -660,9 +724,16 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
   if (!stream)
     CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
                                   cudaMemcpyDeviceToHost, st));
-  const TrialParams p = make_params(ctx, ctx->yets[yet], ctx->layers[layer], t0, n, d_ylt);
-  CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
-                             inversion_mode(ctx), false, st));
+  TrialParams p = make_params(ctx, ctx->yets[yet], ctx->layers[layer], t0, n, d_ylt);
+  if (uses_band_schedule(ctx, ctx->layers[layer])) {
+    s = ensure_ysum(ctx, n);
+    if (s != ARA_OK) return s;
+    p.ysum = ctx->d_ysum;
+    CUDA_TRY(ctx, launch_band(p, ctx->layers[layer].mask_words, ctx->cfg.precision, st));
+  } else {
+    CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
+                               inversion_mode(ctx), false, st));
+  }
   if (stream) return ARA_OK;
   if (!dev_out)
     CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
@@ -680,8 +751,10 @@ ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {
   if (!ctx || !out) return ARA_ERR_INVALID_ARG;
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   CUDA_TRY(ctx, cudaDeviceSynchronize());
-  unsigned long long v[6], nc = 0;
-  CUDA_TRY(ctx, cudaMemcpy(v, ctx->d_stats, sizeof v, cudaMemcpyDeviceToHost));
+  unsigned long long raw[kStatCounters * kStatStripes], v[kStatCounters] = {}, nc = 0;
+  CUDA_TRY(ctx, cudaMemcpy(raw, ctx->d_stats, sizeof raw, cudaMemcpyDeviceToHost));
+  for (int c = 0; c < kStatCounters; ++c)
+    for (int s = 0; s < kStatStripes; ++s) v[c] += raw[c * kStatStripes + s];
   CUDA_TRY(ctx, cudaMemcpy(&nc, ctx->d_not_conv, sizeof nc, cudaMemcpyDeviceToHost));
   out[0] = (int64_t)v[0];
   out[1] = (int64_t)v[1];

@@ -27,7 +27,7 @@ struct ara_ctx {
   std::vector<EltDev> elts;
   std::vector<LayerDev> layers;
   unsigned long long* d_not_conv = nullptr;
-  unsigned long long* d_stats = nullptr;  // [6]
+  unsigned long long* d_stats = nullptr;  // [kStatCounters * kStatStripes]
   int32_t inversion = 0;                   // 0 certified tables + Newton fallback, 1 Newton
   // learned surrogate: FP32 master parameters, Adam moments, gradient, BF16 image, cell errors
   float *mlp_P = nullptr, *mlp_M = nullptr, *mlp_V = nullptr, *mlp_G = nullptr;
@@ -41,6 +41,10 @@ struct ara_ctx {
   SortScratch sort;
   double* d_ylt_tmp = nullptr;
   int64_t ylt_tmp_cap = 0;
+  unsigned long long* d_ysum = nullptr;  // year sums in grid units (band-major runs)
+  int64_t ysum_cap = 0;
+  int32_t schedule = 0;                  // ARA_SCHED_BAND or ARA_SCHED_TRIAL
+  int32_t band_log2w = 0;                // band width exponent for new layers (0: automatic)
   void* d_misc = nullptr;  // small staging area for tail sums
 };
 
@@ -49,5 +53,6 @@ ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
                               double occ_lim, double agg_ret, double agg_lim, bool wide,
                               int32_t* layer_out);
 int inversion_mode(const ara_ctx* ctx);
+bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L);
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,
                         double* d_ylt);

@@ -244,47 +244,74 @@ constexpr int kTableIntervals = 32;
 // t at the smallest uniform on the grid, 2^-24: sqrt(48 ln 2)
 constexpr float kTableTHi = 5.76832104f;
 
+// A record's table header: 32 bytes, one L2 sector.  The spans of both tails are computed once
+// when the table is built, by the same binary32 code (ara_table_span) the builder used, so the
+// evaluation and the builder agree on the piece boundaries exactly.
 struct TableRec {
   float mx;          // loss scale (the mean itself for a sd = 0 record)
   float p0;          // I_{x0}(a,b); negative marks a sd = 0 record
+  float tlo[2];      // table start in t of the lower and the upper tail
+  float ih[2];       // inverse piece widths of the two tails
   const float4* iv;  // 2 * kTableIntervals pieces (lower then upper), 2 float4 each; NULL: no table
 };
+static_assert(sizeof(TableRec) == 32, "a table header is one 32-byte sector");
 
 // Start of a tail's table in t and its inverse piece width, from the tail's mean probability
-// pe (p0 for the lower tail, 1 - p0 for the upper).  The builder and the evaluation both use
-// this binary32 computation, so they agree on the piece boundaries exactly.
+// pe (p0 for the lower tail, 1 - p0 for the upper).
 ARA_HD void ara_table_span(float pe, float* tlo, float* invh) {
   *tlo = sqrtf(-2.0f * logf(pe));
   *invh = (float)kTableIntervals / (kTableTHi - *tlo);
 }
 
-// Quantile from a certified table (iv != NULL, p0 >= 0).
+ARA_HD float ara_exp2_fast(float r) {
+#ifdef __CUDA_ARCH__
+  float v;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(r));  // relative error about 2^-22
+  return v;
+#else
+  return exp2f(r);
+#endif
+}
+
+// Quantile from a certified table (iv != NULL, p0 >= 0).  Pieces hold log2 x as quintics in
+// tau, the position inside the piece.  KEEP chooses the piece load's L2 policy: evict-last when
+// the pieces are reused while they are cached (band-major schedule), evict-first when the tables
+// are swept at random and a piece is rarely met twice before eviction (trial-major schedule).
+template <bool KEEP = false>
 ARA_HD float ara_table_quantile(const TableRec& tr, float u) {
   const bool lower = u <= tr.p0;
   const float q = lower ? u : 1.0f - u;  // exact on the uniform grid
   const float t = sqrtf(-2.0f * logf(q));
-  float tlo, ih;
-  ara_table_span(lower ? tr.p0 : 1.0f - tr.p0, &tlo, &ih);
+  const float tlo = lower ? tr.tlo[0] : tr.tlo[1];
+  const float ih = lower ? tr.ih[0] : tr.ih[1];
   float pos = fminf(fmaxf((t - tlo) * ih, 0.0f), (float)kTableIntervals);
   const int k = pos < (float)(kTableIntervals - 1) ? (int)pos : kTableIntervals - 1;
   const float tau = pos - (float)k;
   const float4* c = tr.iv + 2 * ((lower ? 0 : kTableIntervals) + k);
 #ifdef __CUDA_ARCH__
-  // one 32-byte load, streamed: a piece is read once per hit from tables far larger than L2, so
-  // it bypasses L1 and is first in line for eviction from L2
+  // one 32-byte load, streamed: bypasses L1 and is first in line for eviction from L2
   float4 c0, c1;
-  asm volatile(
-      "ld.global.nc.L1::no_allocate.L2::evict_first.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=f"(c0.x), "=f"(c0.y), "=f"(c0.z), "=f"(c0.w), "=f"(c1.x), "=f"(c1.y), "=f"(c1.z),
-        "=f"(c1.w)
-      : "l"(c));
+  if constexpr (KEEP) {
+    asm volatile(
+        "ld.global.nc.L1::no_allocate.L2::evict_last.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(c0.x), "=f"(c0.y), "=f"(c0.z), "=f"(c0.w), "=f"(c1.x), "=f"(c1.y), "=f"(c1.z),
+          "=f"(c1.w)
+        : "l"(c));
+  } else {
+    asm volatile(
+        "ld.global.nc.L1::no_allocate.L2::evict_first.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(c0.x), "=f"(c0.y), "=f"(c0.z), "=f"(c0.w), "=f"(c1.x), "=f"(c1.y), "=f"(c1.z),
+          "=f"(c1.w)
+        : "l"(c));
+  }
 #else
   const float4 c0 = c[0];
   const float4 c1 = c[1];
 #endif
-  const float r = fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, c1.y, c1.x), c0.w), c0.z), c0.y),
-                       c0.x);
-  const float v = expf(r);
+  const float r2 = fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, c1.y, c1.x), c0.w), c0.z),
+                                  c0.y),
+                        c0.x);
+  const float v = ara_exp2_fast(r2);
   return lower ? v : 1.0f - v;
 }
 

@@ -14,6 +14,21 @@ namespace ara {
 
 constexpr int kMaxLayerElts = 64;
 
+// A YET bucketed by catalogue band for the band-major schedule of the table path.  Band b holds
+// the catalogue events [b W, (b + 1) W), W = 2^log2w.  The occurrences of band b are stored
+// together, trial by trial, each trial's in its own occurrence order, as the 32-bit word
+// (e - b W) << kbits | k with k the occurrence's position in its trial.  The occurrences of
+// (band b, trial i) are occ[off[b N + i] .. off[b N + i + 1]) (N = trials; off[P N] = total).
+struct BandedYet {
+  int32_t log2w = 0;         // 0: not built
+  int32_t n_bands = 0;       // P = ceil(catalog / W)
+  int32_t kbits = 0;         // 32 - log2w
+  uint32_t* occ = nullptr;   // [n_occ]
+  uint32_t* off = nullptr;   // [P N + 1]
+};
+constexpr int kMaxBandVariants = 6;
+constexpr int kMaxBands = 512;
+
 // Year Event Table on the device: trial-major event ids and timestamps (paper §2.1).
 struct YetDev {
   bool live = false;
@@ -24,6 +39,7 @@ struct YetDev {
   int32_t* ids = nullptr;    // [n_occ]
   float* ts = nullptr;       // [n_occ]
   int64_t* offsets = nullptr;  // [n_trials + 1]
+  BandedYet bands[kMaxBandVariants];  // band-major copies, built on demand per band width
 };
 
 // One staged ELT: event ids and the derived per-record constants, in the caller's order.
@@ -55,6 +71,7 @@ struct LayerDev {
   int64_t n_packed = 0;
   void* hot = nullptr;             // one allocation holding evt then tpacked
   size_t hot_bytes = 0;
+  int32_t band_log2w = 0;          // band width of the band-major schedule (0: trial-major only)
 };
 
 // Parameters of one trial-kernel launch.
@@ -70,11 +87,12 @@ struct TrialParams {
   float occ_ret, occ_lim;
   double agg_ret, agg_lim;
   uint64_t seed;
+  uint32_t rk0[10], rk1[10];  // Philox round keys of seed
   int64_t t0, n;
   double* ylt;
   unsigned long long* not_conv;
-  unsigned long long* stats;  // [6]: inversions, Newton iterations, CF terms, hits, table evals,
-                              //      surrogate evaluations
+  unsigned long long* stats;  // [6 x kStatStripes]: inversions, Newton iterations, CF terms,
+                              //      hits, table evals, surrogate evaluations
   const MlpSmem* mlp;         // surrogate weights (inversion 2)
   const float* mlp_bound;     // certified error per cell
   float mlp_eps;
@@ -87,7 +105,21 @@ struct TrialParams {
   float* tr_x;
   float* tr_loss;
   int32_t* tr_count;  // [n]
+  // band-major schedule
+  const uint32_t* bocc;  // BandedYet::occ
+  const uint32_t* boff;  // BandedYet::off
+  int64_t yet_n;         // trials of the YET (row length of boff)
+  int32_t log2w, kbits, n_bands, tiles;
+  unsigned long long* ysum;  // [n] year sums in grid units (band-major schedule; zeroed first)
+  // grid of the exact year sums: occurrence results are rounded to multiples of q_unit = 2^e
+  float q_scale;             // 2^-e
+  double q_unit;             // 2^e
 };
+
+// Work counters are striped over kStatStripes copies (counter c of stripe s at
+// stats[c * kStatStripes + s]) so that blocks do not contend on one address.
+constexpr int kStatCounters = 6;
+constexpr int kStatStripes = 64;
 
 // Kernel launches issued by this library since load (every launcher adds its launches).
 void count_launches(int64_t n);
@@ -121,6 +153,22 @@ cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, in
                          bool trace, cudaStream_t st);
 // One launch over n_items work items (device array of TrialParams whose layers all use 16-byte
 // index entries, i.e. mask_words = 2); warp_begin[i] = first warp of item i (device, ascending).
+// Band-major schedule (certified-table inversion).
+int choose_band_log2w(int64_t catalog, int64_t n_packed);
+bool band_layout_fits(const YetDev& y, int log2w);
+cudaError_t build_band_variant(const YetDev& y, int log2w, BandedYet& out, cudaStream_t st);
+void free_band_variant(BandedYet& v);
+int64_t band_tiles(int64_t n);
+// exponent e of the year-sum grid for trials of at most max_len occurrences under OccL
+int year_grid_exponent(float occ_lim, int64_t max_len);
+// band kernel + per-trial finalisation over p.t0 .. p.t0 + p.n; p.ysum holds n words (zeroed here)
+cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cudaStream_t st);
+// serving: items with their band fields set (tiles = band_tiles(n), ysum zeroed); block_begin[i]
+// = first block of item i (n_bands * tiles blocks each), trial_begin[i] = its first trial
+cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block_begin,
+                              const int64_t* d_trial_begin, int n_items, int64_t total_blocks,
+                              int64_t total_trials, int precision, cudaStream_t st);
+
 cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp_begin,
                                int n_items, int64_t total_warps, int precision, int inversion,
                                cudaStream_t st);

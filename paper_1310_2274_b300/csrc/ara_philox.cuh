@@ -37,6 +37,36 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The same generator with the round keys given (rk0[r], rk1[r] = key words of round r), so that
+// a kernel can take them from its launch parameters instead of advancing the key per call.
+__device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t* rk0, const uint32_t* rk1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    U4 n;
+    n.x = hi1 ^ c.y ^ rk0[r];
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ rk1[r];
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
+// Round keys of the key (seed_lo, seed_hi), as philox4x32_10 advances them.
+inline void philox_round_keys(uint64_t seed, uint32_t* rk0, uint32_t* rk1) {
+  uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk0[r] = k0;
+    rk1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 // Upper 23 bits j of w -> (2j+1) 2^-24: exact in binary32, in [2^-24, 1 - 2^-24], and the grid is
 // symmetric so 1 - u is exact as well.
 __device__ __forceinline__ float word_to_uniform(uint32_t w) {
@@ -52,6 +82,20 @@ __device__ __forceinline__ float su_uniform(uint64_t seed, int64_t trial, uint32
   c.z = (uint32_t)elt >> 2;
   c.w = (uint32_t)((uint64_t)trial >> 32);
   const U4 o = philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+  const int q = elt & 3;
+  const uint32_t w = q == 0 ? o.x : (q == 1 ? o.y : (q == 2 ? o.z : o.w));
+  return word_to_uniform(w);
+}
+
+// su_uniform with precomputed round keys.
+__device__ __forceinline__ float su_uniform_rk(const uint32_t* rk0, const uint32_t* rk1,
+                                               int64_t trial, uint32_t k, int32_t elt) {
+  U4 c;
+  c.x = k;
+  c.y = (uint32_t)((uint64_t)trial & 0xFFFFFFFFu);
+  c.z = (uint32_t)elt >> 2;
+  c.w = (uint32_t)((uint64_t)trial >> 32);
+  const U4 o = philox4x32_10_rk(c, rk0, rk1);
   const int q = elt & 3;
   const uint32_t w = q == 0 ? o.x : (q == 1 ? o.y : (q == 2 ? o.z : o.w));
   return word_to_uniform(w);

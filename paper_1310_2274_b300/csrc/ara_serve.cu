@@ -44,6 +44,8 @@ struct Request {
   double submit_s = 0, admit_s = 0, done_s = 0;
   int32_t layer = -1;
   double* d_ylt = nullptr;
+  unsigned long long* d_ysum = nullptr;  // year sums in grid units (band-major schedule)
+  bool band = false;
   int64_t next = 0;        // next trial offset to schedule
   int64_t finished = 0;    // trials whose launch has completed
   int64_t bytes = 0;       // device memory held
@@ -56,7 +58,7 @@ struct Launch {
   cudaEvent_t done = nullptr;
   std::vector<std::pair<int64_t, int64_t>> parts;  // (ticket, trials)
   TrialParams* h_items = nullptr;  // pinned staging
-  int64_t* h_begin = nullptr;
+  int64_t* h_begin = nullptr;  // [3 cap]: trial-major warp_begin, band block_begin, trial_begin
   TrialParams* d_items = nullptr;
   int64_t* d_begin = nullptr;
   int cap = 0;
@@ -104,14 +106,15 @@ int64_t tail_count_rp(int64_t n, double rp) {
 }
 
 // Device bytes a request holds: 16-byte index entries over the catalogue, its records in three
-// packed arrays (BetaRec, TableRec, record index), and the YLT.
+// packed arrays (BetaRec, TableRec, record index), its YLT and its exact year sums.
 int64_t request_bytes(const ara_server* s, const ara_request& r) {
   const ara_ctx* c = s->ctx;
-  const int64_t C = c->yets[s->cfg.yet].catalog;
+  const YetDev& Y = c->yets[s->cfg.yet];
+  const int64_t C = Y.catalog;
   int64_t recs = 0;
   for (int j = 0; j < r.n_elts; ++j) recs += c->elts[r.elts[j]].n;
-  return C * 16 + recs * (int64_t)(sizeof(BetaRec) + sizeof(ara::TableRec) + 4) + r.n_trials * 8 +
-         (1 << 20);
+  return C * 16 + recs * (int64_t)(sizeof(BetaRec) + sizeof(ara::TableRec) + 4) +
+         r.n_trials * 16 + (1 << 20);
 }
 
 bool ensure_launch_capacity(Launch& L, int n) {
@@ -122,9 +125,9 @@ bool ensure_launch_capacity(Launch& L, int n) {
   if (L.d_begin) cudaFree(L.d_begin);
   L.h_items = nullptr; L.h_begin = nullptr; L.d_items = nullptr; L.d_begin = nullptr; L.cap = 0;
   if (cudaMallocHost(&L.h_items, sizeof(TrialParams) * n) != cudaSuccess ||
-      cudaMallocHost(&L.h_begin, sizeof(int64_t) * n) != cudaSuccess ||
+      cudaMallocHost(&L.h_begin, sizeof(int64_t) * 3 * n) != cudaSuccess ||
       cudaMalloc(&L.d_items, sizeof(TrialParams) * n) != cudaSuccess ||
-      cudaMalloc(&L.d_begin, sizeof(int64_t) * n) != cudaSuccess) {
+      cudaMalloc(&L.d_begin, sizeof(int64_t) * 3 * n) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -135,8 +138,10 @@ bool ensure_launch_capacity(Launch& L, int n) {
 void release(ara_server* s, Request& r) {
   if (r.layer >= 0) ara_free_layer(s->ctx, r.layer);
   if (r.d_ylt) cudaFree(r.d_ylt);
+  if (r.d_ysum) cudaFree(r.d_ysum);
   r.layer = -1;
   r.d_ylt = nullptr;
+  r.d_ysum = nullptr;
   s->used -= r.bytes;
   r.bytes = 0;
 }
@@ -212,6 +217,16 @@ void admit(ara_server* s) {
       fail_request(s, r, ARA_ERR_OOM);
       continue;
     }
+    r.band = uses_band_schedule(s->ctx, s->ctx->layers[layer]);
+    if (r.band) {
+      const size_t bytes = sizeof(unsigned long long) * (size_t)r.req.n_trials;
+      if (cudaMalloc(&r.d_ysum, bytes) != cudaSuccess ||
+          cudaMemsetAsync(r.d_ysum, 0, bytes, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        fail_request(s, r, ARA_ERR_OOM);
+        continue;
+      }
+    }
     r.state = ARA_REQ_RUNNING;
     r.admit_s = now_s(s);
     s->active.push_back(r.ticket);
@@ -273,26 +288,45 @@ bool issue(ara_server* s) {
     s->pool.push_back(L);
     return false;
   }
-  int64_t warp = 0;
+  // band-major items first (items [0, kb)), then trial-major ones (items [kb, k))
+  std::stable_partition(take.begin(), take.end(),
+                        [](const std::pair<Request*, int64_t>& t) { return t.first->band; });
   const YetDev& Y = s->ctx->yets[s->cfg.yet];
-  for (size_t i = 0; i < take.size(); ++i) {
+  const int k = (int)take.size();
+  const int cap = L.cap;
+  int kb = 0;
+  int64_t warp = 0, blocks = 0, trials = 0;
+  for (int i = 0; i < k; ++i) {
     Request& r = *take[i].first;
     const int64_t n = take[i].second;
     const LayerDev& Ld = s->ctx->layers[r.layer];
-    L.h_items[i] = make_params(s->ctx, Y, Ld, r.req.t0 + r.next, n, r.d_ylt + r.next);
-    L.h_begin[i] = warp;
-    warp += n;
+    TrialParams p = make_params(s->ctx, Y, Ld, r.req.t0 + r.next, n, r.d_ylt + r.next);
+    if (r.band) {
+      p.tiles = (int32_t)ara::band_tiles(n);
+      p.ysum = r.d_ysum + r.next;
+      L.h_begin[cap + kb] = blocks;
+      L.h_begin[2 * cap + kb] = trials;
+      blocks += (int64_t)p.n_bands * p.tiles;
+      trials += n;
+      ++kb;
+    } else {
+      L.h_begin[i - kb] = warp;
+      warp += n;
+    }
+    L.h_items[i] = p;
     r.next += n;
     L.parts.emplace_back(r.ticket, n);
   }
-  const int k = (int)take.size();
   cudaError_t e = cudaMemcpyAsync(L.d_items, L.h_items, sizeof(TrialParams) * k,
                                   cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(L.d_begin, L.h_begin, sizeof(int64_t) * k, cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(L.d_begin, L.h_begin, sizeof(int64_t) * 3 * cap, cudaMemcpyHostToDevice,
                         s->stream);
-  if (e == cudaSuccess)
-    e = ara::launch_trial_batch(L.d_items, L.d_begin, k, warp, s->ctx->cfg.precision,
+  if (e == cudaSuccess && kb > 0)
+    e = ara::launch_band_batch(L.d_items, L.d_begin + cap, L.d_begin + 2 * cap, kb, blocks,
+                               trials, s->ctx->cfg.precision, s->stream);
+  if (e == cudaSuccess && k > kb)
+    e = ara::launch_trial_batch(L.d_items + kb, L.d_begin, k - kb, warp, s->ctx->cfg.precision,
                                 inversion_mode(s->ctx), s->stream);
   if (e == cudaSuccess) e = cudaEventRecord(L.done, s->stream);
   if (e != cudaSuccess) {

@@ -154,10 +154,16 @@ ARA_HD double piece_eval(const double* c, double tau) {
   return c[0] + tau * (c[1] + tau * (c[2] + tau * (c[3] + tau * (c[4] + tau * c[5]))));
 }
 
-// Builds one tail: writes kTableIntervals pieces to iv, returns false if certification fails.
-ARA_HD bool build_tail(const BetaRec& br, const TailParams& tp, float p_end, float4* iv) {
+// Builds one tail: writes kTableIntervals pieces to iv and the span to *tlo_out, *ih_out;
+// returns false if certification fails.  Pieces hold log2 x (the evaluation's exponential is
+// base 2).
+ARA_HD bool build_tail(const BetaRec& br, const TailParams& tp, float p_end, float4* iv,
+                       float* tlo_out, float* ih_out) {
   float tlo_f, invh_f;
   ara_table_span(p_end, &tlo_f, &invh_f);
+  *tlo_out = tlo_f;
+  *ih_out = invh_f;
+  const double kLog2e = 1.4426950408889634;
   const double tlo = tlo_f;
   const double h = 1.0 / (double)invh_f;  // the evaluation's own piece width
   bool ok = h > 0.0 && isfinite(h);
@@ -177,12 +183,14 @@ ARA_HD bool build_tail(const BetaRec& br, const TailParams& tp, float p_end, flo
     c[3] = 10.0 * A - 4.0 * B + 0.5 * C;
     c[4] = -15.0 * A + 7.0 * B - C;
     c[5] = 6.0 * A - 3.0 * B + 0.5 * C;
-    iv[2 * i] = ara_make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
-    iv[2 * i + 1] = ara_make_float4((float)c[4], (float)c[5], 0.0f, 0.0f);
+    float c2[6];  // log2 x coefficients as stored
+    for (int j = 0; j < 6; ++j) c2[j] = (float)(c[j] * kLog2e);
+    iv[2 * i] = ara_make_float4(c2[0], c2[1], c2[2], c2[3]);
+    iv[2 * i + 1] = ara_make_float4(c2[4], c2[5], 0.0f, 0.0f);
     // certify at the midpoint against the Newton inversion (binary32 coefficients as stored)
     const Knot km = knot_at(br, tp, tlo + (i + 0.5) * h);
-    double cf[6] = {(double)(float)c[0], (double)(float)c[1], (double)(float)c[2],
-                    (double)(float)c[3], (double)(float)c[4], (double)(float)c[5]};
+    double cf[6];
+    for (int j = 0; j < 6; ++j) cf[j] = (double)c2[j] / kLog2e;
     const double rp = piece_eval(cf, 0.5);
     if (km.r > -69.0) {
       // allowed: kTableTol plus the binary32 rounding of r itself (4 ulp of |r|), which
@@ -203,6 +211,7 @@ ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, fl
   TableRec tr;
   tr.mx = br.mx;
   tr.iv = nullptr;
+  tr.tlo[0] = tr.tlo[1] = tr.ih[0] = tr.ih[1] = 0.0f;
   *ok_out = true;
   if (!(br.a > 0.0f)) {  // sd = 0: the loss is the mean
     tr.p0 = -1.0f;
@@ -212,12 +221,12 @@ ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, fl
   tr.p0 = br.p0;
   const double lnB = lgamma(a64) + lgamma(b64) - lgamma(a64 + b64);
   const TailParams lo = {a64, b64, lnB}, up = {b64, a64, lnB};
-  bool ok = build_tail(br, lo, br.p0, iv);
+  bool ok = build_tail(br, lo, br.p0, iv, &tr.tlo[0], &tr.ih[0]);
   // upper tail: y = 1 - x solves I_y(b, a) = 1 - u, whose own mean probability is 1 - p0
   BetaRec sw;
   sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
   sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
-  ok = ok && build_tail(sw, up, 1.0f - br.p0, iv + 2 * kTableIntervals);
+  ok = ok && build_tail(sw, up, 1.0f - br.p0, iv + 2 * kTableIntervals, &tr.tlo[1], &tr.ih[1]);
   if (ok) tr.iv = iv;
   *ok_out = ok;
   *out = tr;

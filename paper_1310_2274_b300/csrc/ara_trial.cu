@@ -11,15 +11,16 @@
 //     c + 32v + l (v = 0..3), so each of the four id loads is one coalesced 128-byte line.
 //   * Each occurrence reads its 8/16-byte lookup entry (record base + ELT mask); hits are counted
 //     with popc and laid out in event order by a warp scan, giving the chunk's hit list.
-//   * The hit list is processed 32 hits per round, one hit per lane, so the inversion (the time
-//     sink) runs with every lane busy however sparse the hits are.  A lane finds its hit's event
+//   * The hit list is processed in rounds of up to 32 hits, one hit per lane, so the inversion
+//     (the time sink) runs with nearly every lane busy however sparse the hits are; a round ends
+//     on an event boundary, so an event's ELT losses are summed the same way in every schedule.  A lane finds its hit's event
 //     by binary search of the chunk's hit prefix in shared memory and its ELT by the n-th set bit
 //     of the mask.
 //   * An event's losses (contiguous in the hit list) are summed by a segmented warp scan; the
 //     tail lane adds the segment to the event's shared accumulator.  The order is fixed by the
 //     data, so results do not depend on the launch configuration.
-//   * Occurrence terms are applied per event in FP32; the year sum S is carried per lane in FP64
-//     (or Kahan-compensated FP32) and reduced across the warp at the end.
+//   * Occurrence terms are applied per event in FP32; the year sum S is carried per lane exactly
+//     in integer grid units (or Kahan-compensated FP32) and reduced across the warp at the end.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,6 +28,7 @@
 #include "ara_internal.h"
 #include "ara_mlp.cuh"
 #include "ara_philox.cuh"
+#include "ara_trial_common.cuh"
 
 namespace ara {
 
@@ -36,140 +38,6 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kV = 4;             // occurrences per lane per chunk
 constexpr int kChunk = 32 * kV;   // occurrences per chunk
 
-struct AccF64 {
-  double s = 0.0;
-  __device__ void add(float o) { s += (double)o; }
-  __device__ void warp_reduce() {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
-  }
-  __device__ double value() const { return s; }
-};
-
-// Kahan-compensated binary32: the running sum is s - c.
-struct AccKahan {
-  float s = 0.f, c = 0.f;
-  __device__ void add(float o) {
-    const float y = __fsub_rn(o, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-  }
-  __device__ void warp_reduce() {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-      const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, d);
-      const float c2 = __shfl_xor_sync(0xFFFFFFFFu, c, d);
-      // TwoSum(s, s2) = t + e exactly; the combined sum is t + e - c - c2.
-      const float t = __fadd_rn(s, s2);
-      const float bb = __fsub_rn(t, s);
-      const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
-      c = __fsub_rn(__fadd_rn(c, c2), e);
-      s = t;
-    }
-  }
-  __device__ double value() const { return (double)s - (double)c; }
-};
-
-// L2 residency (sm_100+ cache policies).  Per launch the kernel streams the 3.2 GB event-id
-// stream and, on the table path, one random 32-byte table piece per hit from tables of several
-// GB; both are read once and marked evict-first.  The lookup index and the record headers
-// (~45 MB, reused every few microseconds) are marked evict-last so the stream does not push them
-// out of the 126 MB L2.
-struct L2Policies {
-  unsigned long long keep, stream;
-  __device__ static L2Policies make() {
-    L2Policies p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.stream));
-    return p;
-  }
-};
-
-__device__ __forceinline__ int32_t ld_stream_s32(const int32_t* p, unsigned long long pol) {
-  int32_t v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
-               : "=r"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ uint2 ld_keep_u2(const uint2* p, unsigned long long pol) {
-  uint2 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
-               : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ uint4 ld_keep_u4(const uint4* p, unsigned long long pol) {
-  uint4 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
-  return v;
-}
-
-template <int MW>
-struct Entry;
-template <>
-struct Entry<1> {
-  uint32_t base;
-  uint32_t m0;
-  __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
-    const uint2 v = ld_keep_u2(reinterpret_cast<const uint2*>(evt) + e, pol);
-    Entry r;
-    r.base = v.x;
-    r.m0 = v.y;
-    return r;
-  }
-  __device__ int count() const { return __popc(m0); }
-};
-template <>
-struct Entry<2> {
-  uint32_t base;
-  uint32_t m0, m1;
-  __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
-    const uint4 v = ld_keep_u4(reinterpret_cast<const uint4*>(evt) + e, pol);
-    Entry r;
-    r.base = v.x;
-    r.m0 = v.y;
-    r.m1 = v.z;
-    return r;
-  }
-  __device__ int count() const { return __popc(m0) + __popc(m1); }
-};
-
-// Bit position of the n-th (0-based) set bit of m (n < popc(m)): clear the n lowest set bits.
-__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
-  for (int i = 0; i < n; ++i) m &= m - 1u;
-  return __ffs(m) - 1;
-}
-
-__device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-  const float4 u = __ldg(q);
-  const float4 v = __ldg(q + 1);
-  BetaRec r;
-  r.a = u.x; r.b = u.y; r.mx = u.z; r.L0 = u.w;
-  r.p0 = v.x; r.lnx0 = v.y; r.lny0 = v.z; r.lns = v.w;
-  return r;
-}
-
-__device__ __forceinline__ TableRec load_trec(const TableRec* p, unsigned long long pol) {
-  const uint4 u = ld_keep_u4(reinterpret_cast<const uint4*>(p), pol);
-  TableRec r;
-  r.mx = __uint_as_float(u.x);
-  r.p0 = __uint_as_float(u.y);
-  const unsigned long long ptr = ((unsigned long long)u.w << 32) | (unsigned long long)u.z;
-  r.iv = reinterpret_cast<const float4*>(ptr);
-  return r;
-}
-
-// The Newton inversion for the rare record whose table failed certification, kept out of line
-// so that its registers do not weigh on the table path.
-__device__ __noinline__ IbetaResult newton_fallback(const BetaRec* p, float u) {
-  return ara_inv_beta(load_rec(p), u);
-}
-
-// The table path is latency bound on its two dependent loads per hit (record header, then table
-// piece), so it is held to 64 registers for 4 blocks (32 warps) per SM; the Newton path keeps its
-// registers.
 // Surrogate inference for the round's hits: lanes with want set get the network's x (logit x =
 // kOutScale * y); the warp's 32 hits are two 16-row MMA tiles (lane 16 m + r is row r of tile m).
 __device__ __forceinline__ float surrogate_round(const MlpSmem& W, const float (&z)[3], int lane) {
@@ -208,7 +76,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
   const int64_t end = P.offsets[trial + 1];
 
   const L2Policies pol = L2Policies::make();
-  Acc acc;
+  Acc acc = Acc::make(P);
   int32_t trace_n = 0;
   unsigned int nc = 0;
   unsigned int n_inv = 0, n_it = 0, n_cf = 0, n_hit = 0, n_tab = 0, n_net = 0;
@@ -241,20 +109,35 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
     }
     __syncwarp();
 
-    // ---- 32 hits per round: uniform draw, inverse beta, per-event segmented sum ------------
-    for (int32_t r0 = 0; r0 < run; r0 += 32) {
+    // ---- rounds of up to 32 hits ending on an event boundary (an event with more than 32
+    // hits left is split 32 hits from its first): uniform draw, inverse beta, per-event
+    // segmented sum.  Rounds depend on the event's hits alone, so the FP32 event sums do too.
+    for (int32_t r0 = 0; r0 < run;) {
       const int32_t g = r0 + lane;
-      const bool has = g < run;
-      int ev = 0, slot = 0;
+      int ev = 0;  // event of hit g: the last position whose exclusive prefix is <= g
+      if (g < run) {
+#pragma unroll
+        for (int step = kChunk / 2; step >= 1; step >>= 1)
+          if (excl[ev + step] <= g) ev += step;
+      }
+      // the round ends at r0 + 32 unless the event of hit r0 + 31 continues past it: then at that
+      // event's first hit, or at r0 + 32 if it began at or before r0 (more than 32 hits left)
+      int32_t r1 = min(run, r0 + 32);
+      if (run > r0 + 32) {
+        const int ev31 = __shfl_sync(0xFFFFFFFFu, ev, 31);
+        const int32_t end31 = ev31 + 1 < kChunk ? excl[ev31 + 1] : run;
+        if (end31 > r0 + 32) {
+          const int32_t s31 = excl[ev31];
+          r1 = s31 > r0 ? s31 : r0 + 32;
+        }
+      }
+      const bool has = g < r1;
+      int slot = 0;
       uint32_t pos = 0, k = 0;
       float loss = 0.f, u = 0.f, x = __int_as_float(0x7FC00000), mx = 0.f;
       float surr_z[3] = {0.f, 0.f, 0.f};
       bool net = false;
       if (has) {
-        // largest event index whose exclusive prefix is <= g
-#pragma unroll
-        for (int step = kChunk / 2; step >= 1; step >>= 1)
-          if (excl[ev + step] <= g) ev += step;
         const int nth = g - excl[ev];
         if constexpr (MW == 1) {
           slot = nth_set_bit(s_maskw[0][ev], nth);
@@ -281,7 +164,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
           sd0 = !(rec.a > 0.f);
           mx = rec.mx;
         }
-        if (!sd0 || TRACE) u = su_uniform(P.seed, trial, k, P.handles[slot]);
+        if (!sd0 || TRACE) u = su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]);
         if constexpr (SURR) {
           // the network serves this hit if (alpha, beta) lies in its box and the certified error
           // of the hit's cell is within eps; all lanes then evaluate it together below
@@ -348,6 +231,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
       const bool tail = has && (lane == 31 || next_seg != seg);
       if (tail) lsum[ev] += val;
       __syncwarp();
+      r0 = r1;
     }
     if constexpr (TRACE) trace_n += run;
     n_hit += (lane == 0) ? (unsigned)run : 0u;
@@ -376,12 +260,13 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
     const double S = acc.value();
     P.ylt[w] = fmin(fmax(S - P.agg_ret, 0.0), P.agg_lim);
     if (nc) atomicAdd(P.not_conv, (unsigned long long)nc);
-    atomicAdd(P.stats + 0, (unsigned long long)n_inv);
-    atomicAdd(P.stats + 1, (unsigned long long)n_it);
-    atomicAdd(P.stats + 2, (unsigned long long)n_cf);
-    atomicAdd(P.stats + 3, (unsigned long long)n_hit);
-    if (n_tab) atomicAdd(P.stats + 4, (unsigned long long)n_tab);
-    if (n_net) atomicAdd(P.stats + 5, (unsigned long long)n_net);
+    unsigned long long* st = P.stats + (blockIdx.x & (kStatStripes - 1));
+    if (n_inv) atomicAdd(st + 0 * kStatStripes, (unsigned long long)n_inv);
+    if (n_it) atomicAdd(st + 1 * kStatStripes, (unsigned long long)n_it);
+    if (n_cf) atomicAdd(st + 2 * kStatStripes, (unsigned long long)n_cf);
+    if (n_hit) atomicAdd(st + 3 * kStatStripes, (unsigned long long)n_hit);
+    if (n_tab) atomicAdd(st + 4 * kStatStripes, (unsigned long long)n_tab);
+    if (n_net) atomicAdd(st + 5 * kStatStripes, (unsigned long long)n_net);
     if constexpr (TRACE) P.tr_count[w] = trace_n;
   }
 }
@@ -460,15 +345,15 @@ template <int INV>
 cudaError_t launch_mode(const TrialParams& p, int mask_words, int precision, bool trace,
                         cudaStream_t st) {
   if (trace) {
-    return mask_words == 1 ? launch_one<1, AccF64, true, INV>(p, st)
-                           : launch_one<2, AccF64, true, INV>(p, st);
+    return mask_words == 1 ? launch_one<1, AccExact, true, INV>(p, st)
+                           : launch_one<2, AccExact, true, INV>(p, st);
   }
   if (precision == 1) {
     return mask_words == 1 ? launch_one<1, AccKahan, false, INV>(p, st)
                            : launch_one<2, AccKahan, false, INV>(p, st);
   }
-  return mask_words == 1 ? launch_one<1, AccF64, false, INV>(p, st)
-                         : launch_one<2, AccF64, false, INV>(p, st);
+  return mask_words == 1 ? launch_one<1, AccExact, false, INV>(p, st)
+                         : launch_one<2, AccExact, false, INV>(p, st);
 }
 
 template <class Acc, int INV>
@@ -492,9 +377,9 @@ cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp
     if (inversion == 1) return launch_batch_mode<AccKahan, 1>(d_items, d_warp_begin, n_items, total_warps, st);
     return launch_batch_mode<AccKahan, 0>(d_items, d_warp_begin, n_items, total_warps, st);
   }
-  if (inversion == 2) return launch_batch_mode<AccF64, 2>(d_items, d_warp_begin, n_items, total_warps, st);
-  if (inversion == 1) return launch_batch_mode<AccF64, 1>(d_items, d_warp_begin, n_items, total_warps, st);
-  return launch_batch_mode<AccF64, 0>(d_items, d_warp_begin, n_items, total_warps, st);
+  if (inversion == 2) return launch_batch_mode<AccExact, 2>(d_items, d_warp_begin, n_items, total_warps, st);
+  if (inversion == 1) return launch_batch_mode<AccExact, 1>(d_items, d_warp_begin, n_items, total_warps, st);
+  return launch_batch_mode<AccExact, 0>(d_items, d_warp_begin, n_items, total_warps, st);
 }
 
 cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, int inversion,

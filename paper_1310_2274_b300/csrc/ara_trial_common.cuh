@@ -1,0 +1,172 @@
+// ara_trial_common.cuh -- device pieces shared by the trial-major and the band-major kernels of
+// Algorithm 1: year-sum accumulators, L2 cache policies, lookup-entry loads, record loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ara_ibeta.cuh"
+#include "ara_internal.h"
+
+namespace ara {
+namespace {
+
+// Year-sum accumulators.  make() starts a sum for the launch item P; add() takes one
+// occurrence's result; warp_reduce() combines the 32 lanes; value() is the year sum S.
+//
+// AccExact (ARA_ACC_FP64): each binary32 occurrence result is rounded to a multiple of the
+// item's grid unit 2^e (e chosen per launch so that max trial length x OccL fits in 2^52 units)
+// and summed exactly in 64-bit integers; S = units x 2^e is then exact in binary64.  The sum is
+// independent of the order and grouping of the additions, so every schedule gives the same S.
+struct AccExact {
+  unsigned long long s = 0;
+  float qs = 1.0f;    // 2^-e
+  double unit = 1.0;  // 2^e
+  __device__ static AccExact make(const TrialParams& P) {
+    AccExact a;
+    a.qs = P.q_scale;
+    a.unit = P.q_unit;
+    return a;
+  }
+  __device__ static unsigned long long units(float o, float qs) {
+    return __float2ull_rn(o * qs);  // o >= 0; the scaling by 2^-e is exact
+  }
+  __device__ void add(float o) { s += units(o, qs); }
+  __device__ void warp_reduce() {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
+  }
+  __device__ double value() const { return (double)s * unit; }
+};
+
+// ARA_ACC_KAHAN32: Kahan-compensated binary32 in occurrence order per lane, lanes combined by
+// TwoSum; the running sum is s - c.
+struct AccKahan {
+  float s = 0.f, c = 0.f;
+  __device__ static AccKahan make(const TrialParams&) { return AccKahan(); }
+  __device__ void add(float o) {
+    const float y = __fsub_rn(o, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  // TwoSum(s, o.s) = t + e exactly; the combined sum is t + e - c - o.c.
+  __device__ void merge(const AccKahan& o) {
+    const float t = __fadd_rn(s, o.s);
+    const float bb = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(o.s, bb));
+    c = __fsub_rn(__fadd_rn(c, o.c), e);
+    s = t;
+  }
+  __device__ void warp_reduce() {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      AccKahan o;
+      o.s = __shfl_xor_sync(0xFFFFFFFFu, s, d);
+      o.c = __shfl_xor_sync(0xFFFFFFFFu, c, d);
+      merge(o);
+    }
+  }
+  __device__ double value() const { return (double)s - (double)c; }
+};
+
+// L2 residency (sm_100+ cache policies).  Per launch the kernel streams the 3.2 GB event-id
+// stream and, on the table path, one random 32-byte table piece per hit from tables of several
+// GB; both are read once and marked evict-first.  The lookup index and the record headers
+// (~45 MB, reused every few microseconds) are marked evict-last so the stream does not push them
+// out of the 126 MB L2.
+struct L2Policies {
+  unsigned long long keep, stream;
+  __device__ static L2Policies make() {
+    L2Policies p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.stream));
+    return p;
+  }
+};
+
+__device__ __forceinline__ int32_t ld_stream_s32(const int32_t* p, unsigned long long pol) {
+  int32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+               : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_keep_u2(const uint2* p, unsigned long long pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_keep_u4(const uint4* p, unsigned long long pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+
+template <int MW>
+struct Entry;
+template <>
+struct Entry<1> {
+  uint32_t base;
+  uint32_t m0;
+  __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
+    const uint2 v = ld_keep_u2(reinterpret_cast<const uint2*>(evt) + e, pol);
+    Entry r;
+    r.base = v.x;
+    r.m0 = v.y;
+    return r;
+  }
+  __device__ int count() const { return __popc(m0); }
+};
+template <>
+struct Entry<2> {
+  uint32_t base;
+  uint32_t m0, m1;
+  __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
+    const uint4 v = ld_keep_u4(reinterpret_cast<const uint4*>(evt) + e, pol);
+    Entry r;
+    r.base = v.x;
+    r.m0 = v.y;
+    r.m1 = v.z;
+    return r;
+  }
+  __device__ int count() const { return __popc(m0) + __popc(m1); }
+};
+
+// Bit position of the n-th (0-based) set bit of m (n < popc(m)).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) { return (int)__fns(m, 0u, n + 1); }
+
+__device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 u = __ldg(q);
+  const float4 v = __ldg(q + 1);
+  BetaRec r;
+  r.a = u.x; r.b = u.y; r.mx = u.z; r.L0 = u.w;
+  r.p0 = v.x; r.lnx0 = v.y; r.lny0 = v.z; r.lns = v.w;
+  return r;
+}
+
+__device__ __forceinline__ TableRec load_trec(const TableRec* p, unsigned long long pol) {
+  const uint4 u = ld_keep_u4(reinterpret_cast<const uint4*>(p), pol);
+  const uint4 v = ld_keep_u4(reinterpret_cast<const uint4*>(p) + 1, pol);
+  TableRec r;
+  r.mx = __uint_as_float(u.x);
+  r.p0 = __uint_as_float(u.y);
+  r.tlo[0] = __uint_as_float(u.z);
+  r.tlo[1] = __uint_as_float(u.w);
+  r.ih[0] = __uint_as_float(v.x);
+  r.ih[1] = __uint_as_float(v.y);
+  const unsigned long long ptr = ((unsigned long long)v.w << 32) | (unsigned long long)v.z;
+  r.iv = reinterpret_cast<const float4*>(ptr);
+  return r;
+}
+
+// The Newton inversion for the rare record whose table failed certification, kept out of line
+// so that its registers do not weigh on the table path.
+__device__ __noinline__ IbetaResult newton_fallback(const BetaRec* p, float u) {
+  return ara_inv_beta(load_rec(p), u);
+}
+
+}  // namespace
+}  // namespace ara

@@ -115,13 +115,16 @@ def _f32(x: np.ndarray) -> np.ndarray:
 
 
 def make_elt(n: int, catalog: int, seed: int, *, mu: float = 12.0, sigma: float = 1.5,
-             sd_range=(0.3, 1.2), max_range=(3.0, 10.0)) -> Elt:
-    """ELT of n distinct events with the lognormal / beta parameterisation above."""
+             sd_range=(0.3, 1.2), max_range=(3.0, 10.0), round32: bool = True) -> Elt:
+    """ELT of n distinct events with the lognormal / beta parameterisation above.  Values are
+    rounded once to binary32 (both sides then see the same numbers); round32=False keeps the
+    binary64 draws of the same stream (the precision study's unrounded inputs)."""
+    rnd = _f32 if round32 else (lambda x: x)
     rng = np.random.default_rng(seed)
     ids = rng.choice(catalog, size=n, replace=False).astype(np.int32)
-    mean = _f32(rng.lognormal(mu, sigma, size=n))
-    sd = _f32(mean * rng.uniform(sd_range[0], sd_range[1], size=n))
-    mx = _f32(mean * rng.uniform(max_range[0], max_range[1], size=n))
+    mean = rnd(rng.lognormal(mu, sigma, size=n))
+    sd = rnd(mean * rng.uniform(sd_range[0], sd_range[1], size=n))
+    mx = rnd(mean * rng.uniform(max_range[0], max_range[1], size=n))
     return Elt(ids, mean, sd, mx)
 
 

@@ -1,0 +1,115 @@
+"""Band-major schedule of the table path against the trial-major one and the FP64 oracle.
+
+The workload has the paper's 2,000,000-event catalogue and 16 ELTs, so a layer is cut into 62
+bands of 32,768 events, on 3,000 trials (oracle-checkable).  Both schedules make the same hits,
+uniforms and table evaluations, sum each event's ELT losses the same way and sum years exactly
+(integer grid units), so their year losses are identical bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1310_2274_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+YLT_TOL = 1e-5
+N = 3000
+
+
+@pytest.fixture(scope="module")
+def staged(ara):
+    w = synth.paper(n_trials=N)
+    c = ara.Context(seed=42)
+    yet, elts, layer = c.stage_workload(w)
+    yield c, w, yet, elts, layer
+    c.close()
+
+
+def run_sched(ara, c, yet, layer, sched, t0=0, n=N):
+    c.set_option(ara.OPT_SCHEDULE, sched)
+    try:
+        s0 = c.stats()
+        y = c.run(yet, layer, t0, n)
+        s1 = c.stats()
+    finally:
+        c.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND)
+    return y, {k: s1[k] - s0[k] for k in s0}
+
+
+def scale_of(o, terms):
+    return np.maximum(np.maximum(np.abs(o), terms.agg_ret), 1.0)
+
+
+def test_band_schedule_matches_oracle(ara, oracle, staged):
+    c, w, yet, elts, layer = staged
+    g, d = run_sched(ara, c, yet, layer, ara.SCHED_BAND)
+    o, nc = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
+    assert nc == 0
+    err = np.abs(g - o) / scale_of(o, w.terms)
+    assert err.max() <= YLT_TOL, err.max()
+    assert d["launches"] == 2  # band kernel + band-order finalisation
+    assert d["table_evals"] > 0.99 * d["hits"]
+
+
+def test_band_and_trial_schedules_agree(ara, staged):
+    c, w, yet, elts, layer = staged
+    gb, db = run_sched(ara, c, yet, layer, ara.SCHED_BAND)
+    gt, dt = run_sched(ara, c, yet, layer, ara.SCHED_TRIAL)
+    # identical work
+    for k in ("hits", "table_evals", "inversions", "newton", "cf_terms"):
+        assert db[k] == dt[k], k
+    # the same binary32 occurrence results, summed exactly
+    np.testing.assert_array_equal(gb, gt)
+    assert np.count_nonzero(gb) > N // 2
+
+
+def test_kahan_precision_runs_trial_major(ara, oracle, staged):
+    # the Kahan-compensated binary32 year sum depends on the order of additions, so it keeps the
+    # trial-major schedule (one launch) whatever the schedule option says
+    c, w, yet, elts, layer = staged
+    c.set_option(ara.OPT_PRECISION, ara.ACC_KAHAN32)
+    try:
+        g, d = run_sched(ara, c, yet, layer, ara.SCHED_BAND, 0, 500)
+    finally:
+        c.set_option(ara.OPT_PRECISION, ara.ACC_FP64)
+    assert d["launches"] == 1
+    o, _ = oracle.run(w.yet, w.elts, w.terms, 42, trials=np.arange(500), elt_handles=elts)
+    assert np.max(np.abs(g - o) / scale_of(o, w.terms)) <= YLT_TOL
+
+
+def test_band_results_do_not_depend_on_the_trial_range(ara, staged):
+    c, w, yet, elts, layer = staged
+    full, _ = run_sched(ara, c, yet, layer, ara.SCHED_BAND)
+    # ranges that start inside a block's and a warp's trial tile, single trials, the last trial
+    for t0, n in [(0, 1), (1, 15), (5, 129), (127, 300), (N - 1, 1), (1000, N - 1000)]:
+        part, _ = run_sched(ara, c, yet, layer, ara.SCHED_BAND, t0, n)
+        np.testing.assert_array_equal(part, full[t0:t0 + n])
+
+
+def test_band_schedule_ragged_yet(ara, oracle):
+    # empty trials, trials of one event and long trials over the paper catalogue
+    rng = np.random.default_rng(9)
+    lens = rng.choice([0, 0, 1, 2, 15, 16, 17, 33, 900, 2500], size=700)
+    offsets = np.zeros(701, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    ids = rng.integers(0, 2_000_000, size=int(offsets[-1]), dtype=np.int32)
+    ts = np.concatenate([np.sort(rng.uniform(0, 365, size=m)).astype(np.float32) for m in lens])
+    yet_h = synth.Yet(offsets, ids, ts, 2_000_000)
+    elts_h = synth.paper_elts(3)
+    terms = synth.TERMS_PAPER
+    with ara.Context(seed=42) as c:
+        yet = c.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 2_000_000)
+        elts = [c.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
+        layer = c.add_layer(elts, terms.occ_ret, terms.occ_lim, 1e7, terms.agg_lim)
+        g, d = run_sched(ara, c, yet, layer, ara.SCHED_BAND, 0, 700)
+        gt, _ = run_sched(ara, c, yet, layer, ara.SCHED_TRIAL, 0, 700)
+    o, _ = oracle.run(yet_h, elts_h, synth.Terms(terms.occ_ret, terms.occ_lim, 1e7, terms.agg_lim),
+                      42, elt_handles=elts)
+    lens = np.diff(yet_h.offsets)
+    assert (lens == 0).any()
+    assert d["launches"] == 2
+    scale = np.maximum(np.maximum(np.abs(o), 1e7), 1.0)
+    assert np.max(np.abs(g - o) / scale) <= YLT_TOL
+    np.testing.assert_array_equal(g, gt)
+    assert np.all(g[lens == 0] == 0.0)
