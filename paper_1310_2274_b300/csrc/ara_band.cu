@@ -34,6 +34,7 @@ constexpr int kT = 32;               // trials per warp
 constexpr int kV = 4;                // positions per lane per chunk
 constexpr int kCh = 32 * kV;         // positions per chunk
 constexpr int kTrialsPerBlock = kBW * kT;
+constexpr int kHitCap = 512;         // hits per chunk mapped to their positions in shared memory
 
 constexpr int kStageWarps = 8;       // warps per block of the bucketing kernels
 
@@ -98,6 +99,7 @@ struct BandWarpSmem {
   float lsum[kCh];            // the event's summed loss
   uint32_t k[kCh];            // occurrence position in its trial
   uint8_t t[kCh];             // warp-local trial of each position
+  uint8_t hitev[kHitCap];     // position of each of the chunk's hits (when they fit)
   uint32_t off[kT + 1];       // segment starts of the warp's trials in this band
   unsigned long long ys[kT];  // year-sum units gathered by the warp
 };
@@ -128,27 +130,42 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
   const float qs = P.q_scale;
   unsigned int nc = 0, n_inv = 0, n_it = 0, n_cf = 0, n_tab = 0, n_hit = 0;
 
+  // the band words are streamed one chunk ahead, so their DRAM latency overlaps a chunk's hits
+  uint32_t wn[kV];
+#pragma unroll
+  for (int v = 0; v < kV; ++v) {
+    const uint32_t q = beg + v * 32 + lane;
+    wn[v] = q < end ? ld_stream_u32(P.bocc + q, pol.stream) : 0u;
+  }
   for (uint32_t c = beg; c < end; c += kCh) {
-    // ---- stream the band words, look up entries, lay out the chunk's hits -------------------
+    // ---- look up the chunk's entries, lay out its hits ----------------------------------------
+    uint32_t w[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      w[v] = wn[v];
+      const uint32_t q = c + kCh + v * 32 + lane;
+      wn[v] = q < end ? ld_stream_u32(P.bocc + q, pol.stream) : 0u;
+    }
+    Entry<MW> en[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      en[v].base = 0;
+      en[v].m0 = 0;
+      if constexpr (MW == 2) en[v].m1 = 0;
+      if (c + v * 32 + lane < end)
+        en[v] = Entry<MW>::load(P.evt, ebase + (int32_t)(w[v] >> P.kbits), pol.keep);
+    }
     int32_t run = 0;
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const uint32_t q = c + v * 32 + lane;
-      Entry<MW> en;
-      en.base = 0;
-      en.m0 = 0;
-      if constexpr (MW == 2) en.m1 = 0;
-      uint32_t k = 0;
       int t = 0;
       if (q < end) {
-        const uint32_t word = ld_stream_u32(P.bocc + q, pol.stream);
-        k = word & kmask;
-        en = Entry<MW>::load(P.evt, ebase + (int32_t)(word >> P.kbits), pol.keep);
 #pragma unroll
         for (int step = kT / 2; step >= 1; step >>= 1)  // last trial whose segment starts <= q
           if (t + step < nt && sm.off[t + step] <= q) t += step;
       }
-      const int cnt = en.count();
+      const int cnt = en[v].count();
       int incl = cnt;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -156,25 +173,32 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
         if (lane >= d) incl += x;
       }
       const int idx = v * 32 + lane;
-      sm.excl[idx] = run + incl - cnt;
-      sm.base[idx] = en.base;
-      sm.mask[0][idx] = en.m0;
-      if constexpr (MW == 2) sm.mask[1][idx] = en.m1;
+      const int e0 = run + incl - cnt;
+      sm.excl[idx] = e0;
+      sm.base[idx] = en[v].base;
+      sm.mask[0][idx] = en[v].m0;
+      if constexpr (MW == 2) sm.mask[1][idx] = en[v].m1;
       sm.lsum[idx] = 0.f;
-      sm.k[idx] = k;
+      sm.k[idx] = w[v] & kmask;
       sm.t[idx] = (uint8_t)t;
+      for (int j = 0; j < cnt && e0 + j < kHitCap; ++j) sm.hitev[e0 + j] = (uint8_t)idx;
       run += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
     __syncwarp();
+    const bool mapped = run <= kHitCap;
 
     // ---- rounds of up to 32 hits that end on an event boundary -------------------------------
     for (int32_t r0 = 0; r0 < run;) {
       const int32_t g = r0 + lane;
       int ev = 0;  // event of hit g: the last position whose exclusive prefix is <= g
       if (g < run) {
+        if (mapped) {
+          ev = sm.hitev[g];
+        } else {
 #pragma unroll
-        for (int step = kCh / 2; step >= 1; step >>= 1)
-          if (sm.excl[ev + step] <= g) ev += step;
+          for (int step = kCh / 2; step >= 1; step >>= 1)
+            if (sm.excl[ev + step] <= g) ev += step;
+        }
       }
       // the round ends at r0 + 32 unless the event of hit r0 + 31 continues past it: then at that
       // event's first hit, or at r0 + 32 if it began at or before r0 (more than 32 hits left)
