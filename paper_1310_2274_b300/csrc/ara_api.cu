@@ -82,17 +82,12 @@ void free_yet(YetDev& y) {
 void free_elt(EltDev& e) {
   dev_free(e.ids);
   dev_free(e.recs);
-  dev_free(e.trecs);
-  dev_free(e.ivals);
+  dev_free(e.tables);
   e = EltDev();
 }
 void free_layer(LayerDev& l) {
-  if (l.hot) {
-    dev_free(l.hot);  // evt and tpacked live inside it
-  } else {
-    dev_free(l.evt);
-    dev_free(l.tpacked);
-  }
+  dev_free(l.evt);
+  dev_free(l.tables);
   dev_free(l.packed);
   dev_free(l.packed_rec);
   l = LayerDev();
@@ -413,8 +408,7 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
     dev_free(d_ab64);
   };
   if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
-      (err = dev_alloc(&e.trecs, n)) != cudaSuccess ||
-      (err = dev_alloc(&e.ivals, n * 4 * kTableIntervals)) != cudaSuccess ||
+      (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess ||
       (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
       (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess ||
       (err = dev_alloc(&d_uncert, 1)) != cudaSuccess || (err = dev_alloc(&d_ab64, n)) != cudaSuccess) {
@@ -433,7 +427,7 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
       (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_mx, y.catalog, e.recs, d_ab64, d_dup,
                                 ctx->d_flags, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-      (err = launch_build_tables(n, e.recs, d_ab64, e.trecs, e.ivals, d_uncert, ctx->stream)) != cudaSuccess ||
+      (err = launch_build_tables(n, e.recs, d_ab64, e.tables, d_uncert, ctx->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
@@ -548,35 +542,25 @@ ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
     return fail(ctx, ARA_ERR_CUDA, "layer index: %s", cudaGetErrorString(err));
   }
   L.n_packed = (int64_t)last[0] + (int64_t)last[1];
-  // the lookup index and the record headers share one allocation
-  const size_t evt_bytes = ((size_t)evt_words * sizeof(uint32_t) + 255) & ~(size_t)255;
-  L.hot_bytes = evt_bytes + sizeof(TableRec) * (size_t)(L.n_packed > 0 ? L.n_packed : 1);
-  if ((err = cudaMalloc(&L.hot, L.hot_bytes)) != cudaSuccess ||
-      (err = cudaMemcpyAsync(L.hot, L.evt, (size_t)evt_words * sizeof(uint32_t),
-                             cudaMemcpyDeviceToDevice, ctx->stream)) != cudaSuccess ||
-      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
-    cudaGetLastError();
-    cleanup();
-    dev_free(L.hot);  // the index still lives in its first allocation
-    L.hot = nullptr;
-    free_layer(L);
-    return fail(ctx, ARA_ERR_OOM, "layer index: %s", cudaGetErrorString(err));
-  }
-  dev_free(L.evt);
-  L.evt = static_cast<uint32_t*>(L.hot);
-  L.tpacked = reinterpret_cast<TableRec*>(static_cast<char*>(L.hot) + evt_bytes);
+  // packed records, then the records' tables copied into packed order (one gather per hit)
+  const TablePiece** d_src = nullptr;
   if ((err = dev_alloc(&L.packed, L.n_packed)) != cudaSuccess ||
-      (err = dev_alloc(&L.packed_rec, L.n_packed)) != cudaSuccess) {
+      (err = dev_alloc(&L.packed_rec, L.n_packed)) != cudaSuccess ||
+      (err = dev_alloc(&L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
+      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
+    dev_free(d_src);
     free_layer(L);
-    return fail(ctx, ARA_ERR_OOM, "layer records: %s", cudaGetErrorString(err));
+    return fail(ctx, ARA_ERR_OOM, "layer records and tables: %s", cudaGetErrorString(err));
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
-    err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, L.tpacked, L.packed_rec,
+    err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
                                ctx->stream);
+  if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   cleanup();
+  dev_free(d_src);
   if (err != cudaSuccess) {
     cudaGetLastError();
     free_layer(L);
@@ -663,7 +647,7 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   p.offsets = Y.offsets;
   p.evt = L.evt;
   p.recs = L.packed;
-  p.trecs = L.tpacked;
+  p.tables = L.tables;
   p.rec_idx = L.packed_rec;
   for (int j = 0; j < kMaxLayerElts; ++j) p.handles[j] = L.handles[j];
   p.n_slots = L.n_slots;

@@ -224,25 +224,23 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
           slot = nth < c0 ? nth_set_bit(m0, nth) : 32 + nth_set_bit(sm.mask[1][ev], nth - c0);
         }
         const uint32_t pos = sm.base[ev] + (uint32_t)nth;
-        const TableRec tr = load_trec(P.trecs + pos, pol.keep);
-        if (tr.p0 < 0.f) {
-          loss = tr.mx;  // sd = 0: the mean (primary uncertainty only)
+        const int64_t trial = P.t0 + i_rel0 + sm.t[ev];
+        const float u = su_uniform_rk(P.rk0, P.rk1, trial, sm.k[ev], P.handles[slot]);
+        float tau;
+        const int kp = ara_table_piece(u, &tau);
+        const TablePiece pc = ara_load_piece<true>(P.tables + (size_t)pos * kTablePieces, kp);
+        if (pc.flag == kPieceTable) {
+          loss = pc.mx * ara_piece_x(pc, tau);
+          n_tab += 1u;
+        } else if (pc.flag == kPieceMean) {
+          loss = pc.mx;  // sd = 0: the mean (primary uncertainty only)
         } else {
-          const int64_t trial = P.t0 + i_rel0 + sm.t[ev];
-          const float u = su_uniform_rk(P.rk0, P.rk1, trial, sm.k[ev], P.handles[slot]);
-          float x;
-          if (tr.iv != nullptr) {
-            x = ara_table_quantile<true>(tr, u);
-            n_tab += 1u;
-          } else {
-            const IbetaResult ib = newton_fallback(P.recs + pos, u);
-            x = ib.x;
-            nc += ib.converged ? 0u : 1u;
-            n_inv += 1u;
-            n_it += (unsigned)ib.iters;
-            n_cf += (unsigned)ib.cf_terms;
-          }
-          loss = tr.mx * x;
+          const IbetaResult ib = newton_fallback(P.recs + pos, u);
+          nc += ib.converged ? 0u : 1u;
+          n_inv += 1u;
+          n_it += (unsigned)ib.iters;
+          n_cf += (unsigned)ib.cf_terms;
+          loss = pc.mx * ib.x;
         }
       }
       // segmented inclusive scan: segments are the runs of equal ev

@@ -232,36 +232,33 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
 // ---- certified per-record quantile tables ---------------------------------------------------------
 //
 // Each record's (alpha, beta) is fixed and is met hundreds of times per run, so its quantile
-// function is tabulated once, when the ELT is staged.  The two tails are tabulated separately:
-// below the mean (u <= p0) the table maps t = sqrt(-2 ln u) to r = ln x; above it, t =
-// sqrt(-2 ln(1-u)) to r = ln(1-x).  In t the quantile's log is smooth and nearly quadratic in the
-// tails (ln x ~ (ln u)/a), so kTableIntervals quintic Hermite pieces per tail, built from r and its
-// first two derivatives at uniformly spaced knots, reproduce it to ~1e-8; every piece is checked
-// at its midpoint when the table is built, and a record whose table misses the bound keeps the
-// Newton inversion.  One piece is 6 binary32 coefficients of a polynomial in the local coordinate
-// tau in [0,1], padded to 32 bytes (one sector); the record header is 16 bytes.
-constexpr int kTableIntervals = 32;
-// t at the smallest uniform on the grid, 2^-24: sqrt(48 ln 2)
-constexpr float kTableTHi = 5.76832104f;
+// function is tabulated once, when the ELT is staged.  One coordinate serves every record and
+// both tails: with q = min(u, 1 - u) and t = sqrt(-2 ln q), the signed distance from the median
+//   z = t - t_m  (u < 1/2),   z = t_m - t  (u > 1/2),   t_m = sqrt(2 ln 2),
+// covers the whole uniform grid (u in [2^-24, 1 - 2^-24] gives |z| <= 4.591) and is cut into
+// kTablePieces pieces of width kTableH on [-kTableZ, kTableZ]; the median is a piece boundary.
+// In z the log-odds L = ln(x / (1 - x)) of the quantile is smooth and nearly quadratic in both
+// tails (ln x ~ (ln u)/alpha, ln(1-x) ~ (ln(1-u))/beta), so quintic Hermite pieces built from L
+// and its first two derivatives at the knots reproduce it to ~1e-8; every piece is checked at its
+// midpoint when the table is built, and a record whose table misses the bound keeps the Newton
+// inversion.  A piece is 32 bytes, one sector: 6 binary32 coefficients of log2-odds in the local
+// coordinate tau in [0,1), the record's loss scale max_l, and a flag.  Because the piece index
+// depends on u alone, a hit needs no record header: one 32-byte load gives everything.
+constexpr int kTablePieces = 64;
+constexpr float kTableTm = 1.17741002f;   // sqrt(2 ln 2): t at the median
+constexpr float kTableH = 0.14453125f;    // 37/256, exact: 32 pieces per side reach z = 4.625
+constexpr float kTableZ = 4.625f;         // 32 kTableH
+constexpr float kTableInvH = 6.91891892f; // 1 / kTableH
+constexpr uint32_t kPieceTable = 0;       // piece flags: evaluate the quintic
+constexpr uint32_t kPieceMean = 1;        //   sd = 0: the loss is max_l (the mean)
+constexpr uint32_t kPieceNewton = 2;      //   table not certified: invert by Newton
 
-// A record's table header: 32 bytes, one L2 sector.  The spans of both tails are computed once
-// when the table is built, by the same binary32 code (ara_table_span) the builder used, so the
-// evaluation and the builder agree on the piece boundaries exactly.
-struct TableRec {
-  float mx;          // loss scale (the mean itself for a sd = 0 record)
-  float p0;          // I_{x0}(a,b); negative marks a sd = 0 record
-  float tlo[2];      // table start in t of the lower and the upper tail
-  float ih[2];       // inverse piece widths of the two tails
-  const float4* iv;  // 2 * kTableIntervals pieces (lower then upper), 2 float4 each; NULL: no table
+struct TablePiece {
+  float c[6];     // log2-odds in tau, lowest order first
+  float mx;       // the record's loss scale (the mean itself for a sd = 0 record)
+  uint32_t flag;  // kPiece*
 };
-static_assert(sizeof(TableRec) == 32, "a table header is one 32-byte sector");
-
-// Start of a tail's table in t and its inverse piece width, from the tail's mean probability
-// pe (p0 for the lower tail, 1 - p0 for the upper).
-ARA_HD void ara_table_span(float pe, float* tlo, float* invh) {
-  *tlo = sqrtf(-2.0f * logf(pe));
-  *invh = (float)kTableIntervals / (kTableTHi - *tlo);
-}
+static_assert(sizeof(TablePiece) == 32, "a table piece is one 32-byte sector");
 
 ARA_HD float ara_exp2_fast(float r) {
 #ifdef __CUDA_ARCH__
@@ -273,46 +270,62 @@ ARA_HD float ara_exp2_fast(float r) {
 #endif
 }
 
-// Quantile from a certified table (iv != NULL, p0 >= 0).  Pieces hold log2 x as quintics in
-// tau, the position inside the piece.  KEEP chooses the piece load's L2 policy: evict-last when
-// the pieces are reused while they are cached (band-major schedule), evict-first when the tables
-// are swept at random and a piece is rarely met twice before eviction (trial-major schedule).
-template <bool KEEP = false>
-ARA_HD float ara_table_quantile(const TableRec& tr, float u) {
-  const bool lower = u <= tr.p0;
+// Piece index and local coordinate of uniform u.
+ARA_HD int ara_table_piece(float u, float* tau) {
+  const bool lower = u < 0.5f;
   const float q = lower ? u : 1.0f - u;  // exact on the uniform grid
   const float t = sqrtf(-2.0f * logf(q));
-  const float tlo = lower ? tr.tlo[0] : tr.tlo[1];
-  const float ih = lower ? tr.ih[0] : tr.ih[1];
-  float pos = fminf(fmaxf((t - tlo) * ih, 0.0f), (float)kTableIntervals);
-  const int k = pos < (float)(kTableIntervals - 1) ? (int)pos : kTableIntervals - 1;
-  const float tau = pos - (float)k;
-  const float4* c = tr.iv + 2 * ((lower ? 0 : kTableIntervals) + k);
+  const float z = lower ? t - kTableTm : kTableTm - t;
+  const float pos = fminf(fmaxf((z + kTableZ) * kTableInvH, 0.0f), (float)kTablePieces);
+  const int k = pos < (float)(kTablePieces - 1) ? (int)pos : kTablePieces - 1;
+  *tau = pos - (float)k;
+  return k;
+}
+
+// One 32-byte load of piece k of the record whose table starts at rec.  KEEP chooses the L2
+// policy: evict-last when pieces are reused while cached (band-major schedule), evict-first when
+// the tables are swept at random (trial-major schedule).
+template <bool KEEP>
+ARA_HD TablePiece ara_load_piece(const TablePiece* rec, int k) {
+  TablePiece pc;
 #ifdef __CUDA_ARCH__
-  // one 32-byte load, streamed: bypasses L1 and is first in line for eviction from L2
-  float4 c0, c1;
+  uint32_t w[8];
+  const TablePiece* p = rec + k;
   if constexpr (KEEP) {
     asm volatile(
-        "ld.global.nc.L1::no_allocate.L2::evict_last.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(c0.x), "=f"(c0.y), "=f"(c0.z), "=f"(c0.w), "=f"(c1.x), "=f"(c1.y), "=f"(c1.z),
-          "=f"(c1.w)
-        : "l"(c));
+        "ld.global.nc.L1::no_allocate.L2::evict_last.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7])
+        : "l"(p));
   } else {
     asm volatile(
-        "ld.global.nc.L1::no_allocate.L2::evict_first.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(c0.x), "=f"(c0.y), "=f"(c0.z), "=f"(c0.w), "=f"(c1.x), "=f"(c1.y), "=f"(c1.z),
-          "=f"(c1.w)
-        : "l"(c));
+        "ld.global.nc.L1::no_allocate.L2::evict_first.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7])
+        : "l"(p));
   }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) pc.c[i] = __uint_as_float(w[i]);
+  pc.mx = __uint_as_float(w[6]);
+  pc.flag = w[7];
 #else
-  const float4 c0 = c[0];
-  const float4 c1 = c[1];
+  pc = rec[k];
 #endif
-  const float r2 = fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, c1.y, c1.x), c0.w), c0.z),
-                                  c0.y),
-                        c0.x);
-  const float v = ara_exp2_fast(r2);
-  return lower ? v : 1.0f - v;
+  return pc;
+}
+
+// x from a table piece (flag kPieceTable): log2-odds by Horner, then x = 1 / (1 + 2^-L2).
+ARA_HD float ara_piece_x(const TablePiece& pc, float tau) {
+  const float l2 = fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, pc.c[5], pc.c[4]), pc.c[3]),
+                                            pc.c[2]),
+                                  pc.c[1]),
+                        pc.c[0]);
+  const float e = ara_exp2_fast(-l2);
+#ifdef __CUDA_ARCH__
+  return __fdividef(1.0f, 1.0f + e);  // e beyond 2^126 (x below ~1e-38) gives 0
+#else
+  return 1.0f / (1.0f + e);
+#endif
 }
 
 }  // namespace ara

@@ -49,8 +49,7 @@ struct EltDev {
   int64_t n = 0;
   int32_t* ids = nullptr;    // [n]
   BetaRec* recs = nullptr;   // [n]
-  TableRec* trecs = nullptr; // [n] certified quantile tables (iv NULL: Newton inversion)
-  float4* ivals = nullptr;   // [n * 4 * kTableIntervals] table pieces
+  TablePiece* tables = nullptr;  // [n * kTablePieces] certified quantile tables
   int64_t n_uncertified = 0; // records whose table failed certification
 };
 
@@ -66,11 +65,9 @@ struct LayerDev {
   double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
   uint32_t* evt = nullptr;         // [catalog * (1 + mask_words)] entries, padded to 2 or 4 words
   BetaRec* packed = nullptr;       // [n_packed]
-  TableRec* tpacked = nullptr;     // [n_packed] table records, same order
+  TablePiece* tables = nullptr;    // [n_packed * kTablePieces] the records' tables, same order
   uint32_t* packed_rec = nullptr;  // [n_packed] caller record index (verification)
   int64_t n_packed = 0;
-  void* hot = nullptr;             // one allocation holding evt then tpacked
-  size_t hot_bytes = 0;
   int32_t band_log2w = 0;          // band width of the band-major schedule (0: trial-major only)
 };
 
@@ -80,7 +77,7 @@ struct TrialParams {
   const int64_t* offsets;
   const uint32_t* evt;
   const BetaRec* recs;
-  const TableRec* trecs;
+  const TablePiece* tables;  // the layer's tables, kTablePieces per packed record
   const uint32_t* rec_idx;
   int32_t handles[kMaxLayerElts];
   int32_t n_slots;
@@ -141,12 +138,16 @@ int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, int mask_words,
                                int64_t catalog, uint32_t* d_evt, cudaStream_t st);
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
-                                 const uint32_t* d_evt, BetaRec* packed, TableRec* tpacked,
-                                 uint32_t* packed_rec, cudaStream_t st);
+                                 const uint32_t* d_evt, BetaRec* packed,
+                                 const TablePiece** table_src, uint32_t* packed_rec,
+                                 cudaStream_t st);
 // ab64[n]: each record's (alpha, beta) in binary64, as written by launch_prepare_elt.
 cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
-                                TableRec* trecs, float4* ivals,
-                                unsigned long long* d_uncertified, cudaStream_t st);
+                                TablePiece* tables, unsigned long long* d_uncertified,
+                                cudaStream_t st);
+// dst[i * kTablePieces ...] = the table at d_src[i], for the n packed records of a layer
+cudaError_t launch_gather_tables(int64_t n, const TablePiece* const* d_src, TablePiece* dst,
+                                 cudaStream_t st);
 // inversion: 0 = certified tables with Newton fallback, 1 = Newton everywhere, 2 = learned
 // surrogate with Newton fallback
 cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, int inversion,

@@ -105,15 +105,15 @@ int64_t tail_count_rp(int64_t n, double rp) {
   return std::min<int64_t>(std::max<int64_t>(k, 1), n);
 }
 
-// Device bytes a request holds: 16-byte index entries over the catalogue, its records in three
-// packed arrays (BetaRec, TableRec, record index), its YLT and its exact year sums.
+// Device bytes a request holds: 16-byte index entries over the catalogue, its packed records
+// (BetaRec, record index) with a copy of their tables, its YLT and its exact year sums.
 int64_t request_bytes(const ara_server* s, const ara_request& r) {
   const ara_ctx* c = s->ctx;
   const YetDev& Y = c->yets[s->cfg.yet];
   const int64_t C = Y.catalog;
   int64_t recs = 0;
   for (int j = 0; j < r.n_elts; ++j) recs += c->elts[r.elts[j]].n;
-  return C * 16 + recs * (int64_t)(sizeof(BetaRec) + sizeof(ara::TableRec) + 4) +
+  return C * 16 + recs * (int64_t)(sizeof(BetaRec) + 4 + ara::kTablePieces * sizeof(ara::TablePiece)) +
          r.n_trials * 16 + (1 << 20);
 }
 

@@ -147,9 +147,10 @@ __global__ void layer_index_kernel(const uint32_t* __restrict__ mask,
 
 __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
                                      const BetaRec* __restrict__ recs,
-                                     const TableRec* __restrict__ trecs, int slot, int mask_words,
-                                     const uint32_t* __restrict__ evt, BetaRec* packed,
-                                     TableRec* tpacked, uint32_t* packed_rec) {
+                                     const TablePiece* __restrict__ tables, int slot,
+                                     int mask_words, const uint32_t* __restrict__ evt,
+                                     BetaRec* packed, const TablePiece** table_src,
+                                     uint32_t* packed_rec) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t e = ids[r];
@@ -165,7 +166,7 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
     rank = __popcll(m & ((1ull << slot) - 1ull));
   }
   packed[base + rank] = recs[r];
-  tpacked[base + rank] = trecs[r];
+  table_src[base + rank] = tables + r * kTablePieces;
   packed_rec[base + rank] = (uint32_t)r;
 }
 
@@ -321,11 +322,12 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
 }
 
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
-                                 const uint32_t* d_evt, BetaRec* packed, TableRec* tpacked,
-                                 uint32_t* packed_rec, cudaStream_t st) {
+                                 const uint32_t* d_evt, BetaRec* packed,
+                                 const TablePiece** table_src, uint32_t* packed_rec,
+                                 cudaStream_t st) {
   if (e.n == 0) return cudaSuccess;
-  layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, e.trecs, slot,
-                                                           mask_words, d_evt, packed, tpacked,
+  layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, e.tables, slot,
+                                                           mask_words, d_evt, packed, table_src,
                                                            packed_rec);
   count_launches(1);
   return cudaGetLastError();

@@ -12,28 +12,49 @@ namespace ara {
 namespace {
 
 __global__ void build_tables_kernel(int64_t n, const BetaRec* __restrict__ recs,
-                                    const double2* __restrict__ ab64, TableRec* trecs,
-                                    float4* ivals, unsigned long long* n_uncertified) {
+                                    const double2* __restrict__ ab64, TablePiece* tables,
+                                    unsigned long long* n_uncertified) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const BetaRec br = recs[r];
   const double2 ab = ab64[r];
-  TableRec tr;
   bool ok;
-  ara_build_table_record(br, ab.x, ab.y, ivals + (int64_t)r * 4 * kTableIntervals, &tr, &ok);
+  ara_build_table_record(br, ab.x, ab.y, tables + r * kTablePieces, &ok);
   if (!ok) atomicAdd(n_uncertified, 1ull);
-  trecs[r] = tr;
+}
+
+// Layer copy of the tables in packed order: one warp per packed record, 2 KB each.
+__global__ void gather_tables_kernel(int64_t n, const TablePiece* const* __restrict__ src,
+                                     TablePiece* __restrict__ dst) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const uint4* s = reinterpret_cast<const uint4*>(src[w]);
+  uint4* d = reinterpret_cast<uint4*>(dst + w * kTablePieces);
+#pragma unroll
+  for (int i = 0; i < (int)(kTablePieces * sizeof(TablePiece) / 16 / 32); ++i)
+    d[i * 32 + lane] = s[i * 32 + lane];
 }
 
 }  // namespace
 
 cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
-                                TableRec* trecs, float4* ivals,
-                                unsigned long long* d_uncertified, cudaStream_t st) {
+                                TablePiece* tables, unsigned long long* d_uncertified,
+                                cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int threads = 128;
   build_tables_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
-      n, recs, ab64, trecs, ivals, d_uncertified);
+      n, recs, ab64, tables, d_uncertified);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_tables(int64_t n, const TablePiece* const* d_src, TablePiece* dst,
+                                 cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  gather_tables_kernel<<<(unsigned)((n * 32 + threads - 1) / threads), threads, 0, st>>>(
+      n, d_src, dst);
   count_launches(1);
   return cudaGetLastError();
 }

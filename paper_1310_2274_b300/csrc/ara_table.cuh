@@ -1,17 +1,18 @@
 // ara_table.cuh -- construction of the certified per-record quantile tables (host and device).
 //
-// For each tail, kTableIntervals + 1 knots are placed uniformly in t = sqrt(-2 ln q) between the
-// mean (q = p0, or 1 - p0 for the upper tail) and the smallest uniform 2^-24.  The quantile at a
-// knot comes from the binary32 Newton inversion (which works in ln x, so tails that underflow
-// binary32 are still tabulated); r = ln x and its first two derivatives in t follow from the beta
-// density; each piece's quintic Hermite coefficients are formed in binary64.  Each piece is then
-// checked at its midpoint against the polished inversion; a record keeps its table only if every
-// midpoint agrees to kTableTol in x plus the binary32 rounding of ln x (where x > 1e-30).
+// Knots are placed at z_i = -kTableZ + i kTableH (i = 0..kTablePieces), z the signed distance
+// from the median in t = sqrt(-2 ln q), q = min(u, 1 - u).  The quantile at a knot comes from
+// the binary32 Newton inversion on the record's own tail (u <= p0: x itself; u > p0: 1 - x of
+// the swapped record, so x near 1 keeps its precision), polished by one binary64 Newton step;
+// the log-odds L = ln x - ln(1-x) and its first two derivatives in z follow from the beta density;
+// each piece's quintic Hermite coefficients are formed in binary64.  Each piece is then checked at
+// its midpoint against a polished inversion; a record keeps its table only if every midpoint
+// agrees to kTableTol in L (so in x/(1-x) relatively) plus the binary32 rounding of L.
 //
-// Derivatives (s = ln u = -t^2/2, r = ln x, f the beta density):
-//   dr/ds = u / (x f(x)),  x f(x) = x^a y^b / (y B(a,b)) = exp(E) / y,
-//   d2r/ds2 = r_s (1 - r_s (a - (b-1) x / y)),
-//   dr/dt = -t r_s,  d2r/dt2 = t^2 r_ss - r_s.
+// Derivatives (g = dL/du = B(a,b) / (x^a (1-x)^b), t = t_m + |z|, u(z) with du/dz = -t q):
+//   L'  = -t q g,
+//   L'' = L'^2 (b x - a (1 - x)) - s (t^2 - 1) L' / t,   s = +1 for z > 0, -1 for z < 0;
+// L'' jumps at the median (z = 0), which is a piece boundary: each side uses its own value.
 #pragma once
 
 #include "ara_ibeta.cuh"
@@ -66,11 +67,6 @@ struct TailParams {
   double a, b, lnB;
 };
 
-struct Knot {
-  double r, rt, rtt;  // ln x and its derivatives in t at the knot
-  bool ok;
-};
-
 // ln of the quantile of the tail described by br (binary32 record, solved without flipping: u <=
 // br.p0) and tp (the same tail in binary64), at the uniform uf with su = ln u known exactly (or
 // ln uf): the binary32 Newton inversion gives the start and one binary64 Newton step in r = ln x
@@ -89,29 +85,6 @@ ARA_HD double ara_polish_ln_quantile(const BetaRec& br, const TailParams& tp, fl
   }
   *ok = res.converged && isfinite(r);
   return r;
-}
-
-// Quantile data at table coordinate t: r = ln x and its derivatives in t, in binary64.
-ARA_HD Knot knot_at(const BetaRec& br, const TailParams& tp, double t) {
-  Knot k;
-  const double su = -0.5 * t * t;  // ln u at the knot, exactly
-  float uf = (float)exp(su);
-  if (!(uf <= br.p0)) uf = br.p0;  // start on this tail
-  if (!(uf > 0.0f)) uf = 1.17549435e-38f;
-  bool ok;
-  const double r = ara_polish_ln_quantile(br, tp, uf, su, &ok);
-  const double a = tp.a, b = tp.b;
-  const double x = exp(r);
-  const double lny = log1p(-x);
-  // x f(x) = x^a y^b / (y B(a,b))
-  const double lnxf = a * r + (b - 1.0) * lny - tp.lnB;
-  const double rs = exp(su - lnxf);
-  const double rss = rs * (1.0 - rs * (a - (b - 1.0) * x / (1.0 - x)));
-  k.r = r;
-  k.rt = -t * rs;
-  k.rtt = t * t * rss - rs;
-  k.ok = ok && isfinite(k.rt) && isfinite(k.rtt);
-  return k;
 }
 
 // The binary32 record of Beta(a, b) (for the Newton start) and ln B(a,b), from binary64 a, b.
@@ -154,82 +127,109 @@ ARA_HD double piece_eval(const double* c, double tau) {
   return c[0] + tau * (c[1] + tau * (c[2] + tau * (c[3] + tau * (c[4] + tau * c[5]))));
 }
 
-// Builds one tail: writes kTableIntervals pieces to iv and the span to *tlo_out, *ih_out;
-// returns false if certification fails.  Pieces hold log2 x (the evaluation's exponential is
-// base 2).
-ARA_HD bool build_tail(const BetaRec& br, const TailParams& tp, float p_end, float4* iv,
-                       float* tlo_out, float* ih_out) {
-  float tlo_f, invh_f;
-  ara_table_span(p_end, &tlo_f, &invh_f);
-  *tlo_out = tlo_f;
-  *ih_out = invh_f;
+// Log-odds of the quantile at z and its first two derivatives in z (the second from the side s).
+struct LogitKnot {
+  double L, L1, L2;
+  bool ok;
+};
+
+ARA_HD LogitKnot logit_knot(const BetaRec& br, const BetaRec& sw, const TailParams& lo,
+                            const TailParams& up, double z, double s) {
+  LogitKnot k;
+  const double t = (double)kTableTm + fabs(z);
+  const double lnq = -0.5 * t * t;
+  const double q = exp(lnq);
+  // u = q below the median, 1 - q above it; ln u and ln(1 - u) without cancellation
+  const double lnu = z >= 0.0 ? lnq : log1p(-q);
+  const double ln1mu = z >= 0.0 ? log1p(-q) : lnq;
+  const double u = z >= 0.0 ? q : 1.0 - q;
+  bool ok;
+  double lnx, ln1mx;
+  if (u <= (double)br.p0) {
+    float uf = (float)u;
+    if (!(uf <= br.p0)) uf = br.p0;
+    if (!(uf > 0.0f)) uf = 1.17549435e-38f;
+    lnx = ara_polish_ln_quantile(br, lo, uf, lnu, &ok);
+    ln1mx = log1p(-exp(lnx));
+  } else {
+    float vf = (float)exp(ln1mu);
+    if (!(vf <= sw.p0)) vf = sw.p0;
+    if (!(vf > 0.0f)) vf = 1.17549435e-38f;
+    ln1mx = ara_polish_ln_quantile(sw, up, vf, ln1mu, &ok);
+    lnx = log1p(-exp(ln1mx));
+  }
+  const double a = lo.a, b = lo.b;
+  const double x = exp(lnx), y = exp(ln1mx);
+  k.L = lnx - ln1mx;
+  k.L1 = -t * exp(lnq + lo.lnB - a * lnx - b * ln1mx);
+  k.L2 = k.L1 * k.L1 * (b * x - a * y) - s * (t * t - 1.0) * k.L1 / t;
+  k.ok = ok && isfinite(k.L) && isfinite(k.L1) && isfinite(k.L2);
+  return k;
+}
+
+// Fills a record's kTablePieces pieces (pc) and reports whether every piece was certified.
+// br: the record in binary32; a64, b64: its beta parameters in binary64.
+ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, TablePiece* pc,
+                                   bool* ok_out) {
+  *ok_out = true;
+  if (!(br.a > 0.0f)) {  // sd = 0: the loss is the mean
+    for (int i = 0; i < kTablePieces; ++i) {
+      for (int j = 0; j < 6; ++j) pc[i].c[j] = 0.0f;
+      pc[i].mx = br.mx;
+      pc[i].flag = kPieceMean;
+    }
+    return;
+  }
+  const double lnB = lgamma(a64) + lgamma(b64) - lgamma(a64 + b64);
+  const TailParams lo = {a64, b64, lnB}, up = {b64, a64, lnB};
+  BetaRec sw;  // the swapped record: 1 - x ~ Beta(b, a), whose own mean probability is 1 - p0
+  sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
+  sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
+  const double h = (double)kTableH, z0 = -(double)kTableZ;
   const double kLog2e = 1.4426950408889634;
-  const double tlo = tlo_f;
-  const double h = 1.0 / (double)invh_f;  // the evaluation's own piece width
-  bool ok = h > 0.0 && isfinite(h);
-  Knot k0 = knot_at(br, tp, tlo);
+  bool ok = true;
+  const int half = kTablePieces / 2;
+  LogitKnot k0 = logit_knot(br, sw, lo, up, z0, -1.0);
   ok = ok && k0.ok;
-  for (int i = 0; i < kTableIntervals; ++i) {
-    const Knot k1 = knot_at(br, tp, tlo + (i + 1) * h);
-    ok = ok && k1.ok;
+  for (int i = 0; i < kTablePieces && ok; ++i) {
+    const double side = i < half ? -1.0 : 1.0;  // the median is the boundary of pieces half-1, half
+    if (i == half) k0 = logit_knot(br, sw, lo, up, 0.0, 1.0);
+    const LogitKnot k1 = logit_knot(br, sw, lo, up, z0 + (i + 1) * h, side);
+    ok = ok && k0.ok && k1.ok;
     // quintic Hermite on tau in [0,1]: values, h * first, h^2 * second derivatives at both ends
     double c[6];
-    c[0] = k0.r;
-    c[1] = h * k0.rt;
-    c[2] = 0.5 * h * h * k0.rtt;
-    const double A = k1.r - (c[0] + c[1] + c[2]);
-    const double B = h * k1.rt - (c[1] + 2.0 * c[2]);
-    const double C = h * h * k1.rtt - 2.0 * c[2];
+    c[0] = k0.L;
+    c[1] = h * k0.L1;
+    c[2] = 0.5 * h * h * k0.L2;
+    const double A = k1.L - (c[0] + c[1] + c[2]);
+    const double B = h * k1.L1 - (c[1] + 2.0 * c[2]);
+    const double C = h * h * k1.L2 - 2.0 * c[2];
     c[3] = 10.0 * A - 4.0 * B + 0.5 * C;
     c[4] = -15.0 * A + 7.0 * B - C;
     c[5] = 6.0 * A - 3.0 * B + 0.5 * C;
-    float c2[6];  // log2 x coefficients as stored
-    for (int j = 0; j < 6; ++j) c2[j] = (float)(c[j] * kLog2e);
-    iv[2 * i] = ara_make_float4(c2[0], c2[1], c2[2], c2[3]);
-    iv[2 * i + 1] = ara_make_float4(c2[4], c2[5], 0.0f, 0.0f);
-    // certify at the midpoint against the Newton inversion (binary32 coefficients as stored)
-    const Knot km = knot_at(br, tp, tlo + (i + 0.5) * h);
-    double cf[6];
-    for (int j = 0; j < 6; ++j) cf[j] = (double)c2[j] / kLog2e;
-    const double rp = piece_eval(cf, 0.5);
-    if (km.r > -69.0) {
-      // allowed: kTableTol plus the binary32 rounding of r itself (4 ulp of |r|), which
-      // dominates only for x < ~1e-12, far below any loss that reaches a year loss
-      const double err = fabs(expm1(rp - km.r));
-      const double tol = kTableTol + 2.384185791015625e-7 * fabs(km.r);
-      if (!(err <= tol) || !km.ok) ok = false;
+    double cf[6];  // the stored log2-odds coefficients, back in natural units
+    for (int j = 0; j < 6; ++j) {
+      pc[i].c[j] = (float)(c[j] * kLog2e);
+      cf[j] = (double)pc[i].c[j] / kLog2e;
     }
+    pc[i].mx = br.mx;
+    pc[i].flag = kPieceTable;
+    // certify at the midpoint against a polished inversion (coefficients as stored)
+    const LogitKnot km = logit_knot(br, sw, lo, up, z0 + (i + 0.5) * h, side);
+    const double err = fabs(piece_eval(cf, 0.5) - km.L);
+    // allowed: kTableTol plus the binary32 rounding of L (4 ulp of |L|), which dominates only for
+    // x or 1 - x below ~1e-12, far below any loss that reaches a year loss
+    const double tol = kTableTol + 2.384185791015625e-7 * fabs(km.L);
+    if (!(err <= tol) || !km.ok) ok = false;
     k0 = k1;
   }
-  return ok;
-}
-
-
-// br: the record in binary32; a64, b64: its beta parameters in binary64; p0 = I_{x0}(a,b).
-ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, float4* iv,
-                                   TableRec* out, bool* ok_out) {
-  TableRec tr;
-  tr.mx = br.mx;
-  tr.iv = nullptr;
-  tr.tlo[0] = tr.tlo[1] = tr.ih[0] = tr.ih[1] = 0.0f;
-  *ok_out = true;
-  if (!(br.a > 0.0f)) {  // sd = 0: the loss is the mean
-    tr.p0 = -1.0f;
-    *out = tr;
-    return;
+  if (!ok) {
+    for (int i = 0; i < kTablePieces; ++i) {
+      pc[i].mx = br.mx;
+      pc[i].flag = kPieceNewton;
+    }
   }
-  tr.p0 = br.p0;
-  const double lnB = lgamma(a64) + lgamma(b64) - lgamma(a64 + b64);
-  const TailParams lo = {a64, b64, lnB}, up = {b64, a64, lnB};
-  bool ok = build_tail(br, lo, br.p0, iv, &tr.tlo[0], &tr.ih[0]);
-  // upper tail: y = 1 - x solves I_y(b, a) = 1 - u, whose own mean probability is 1 - p0
-  BetaRec sw;
-  sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
-  sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
-  ok = ok && build_tail(sw, up, 1.0f - br.p0, iv + 2 * kTableIntervals, &tr.tlo[1], &tr.ih[1]);
-  if (ok) tr.iv = iv;
   *ok_out = ok;
-  *out = tr;
 }
 
 }  // namespace ara

@@ -149,22 +149,24 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
         pos = sbase[ev] + (uint32_t)nth;
         k = (uint32_t)(c - beg) + (uint32_t)ev;
         bool sd0 = false, use_table = false;
-        TableRec tr;
+        TablePiece pc;
+        float tau = 0.f;
         if constexpr (TABLE) {
-          tr = load_trec(P.trecs + pos, pol.keep);
-          sd0 = tr.p0 < 0.f;
-          mx = tr.mx;
-          use_table = tr.iv != nullptr;
-        } else {
-          tr.iv = nullptr;
+          // the piece index depends on u alone: draw first, then one 32-byte load
+          u = su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]);
+          const int kp = ara_table_piece(u, &tau);
+          pc = ara_load_piece<false>(P.tables + (size_t)pos * kTablePieces, kp);
+          sd0 = pc.flag == kPieceMean;
+          mx = pc.mx;
+          use_table = pc.flag == kPieceTable;
         }
         BetaRec rec;
         if (!TABLE) {
           rec = load_rec(P.recs + pos);
           sd0 = !(rec.a > 0.f);
           mx = rec.mx;
+          if (!sd0 || TRACE) u = su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]);
         }
-        if (!sd0 || TRACE) u = su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]);
         if constexpr (SURR) {
           // the network serves this hit if (alpha, beta) lies in its box and the certified error
           // of the hit's cell is within eps; all lanes then evaluate it together below
@@ -182,7 +184,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
           loss = mx;  // sd = 0: the mean (primary uncertainty only)
         } else if (!net) {
           if (TABLE && use_table) {
-            x = ara_table_quantile(tr, u);
+            x = ara_piece_x(pc, tau);
             n_tab += 1u;
           } else {
             const IbetaResult ib =

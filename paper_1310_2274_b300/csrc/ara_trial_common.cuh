@@ -147,25 +147,6 @@ __device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
   return r;
 }
 
-// One 32-byte load (a single L1 sector access) for the whole table header, kept in L2.
-__device__ __forceinline__ TableRec load_trec(const TableRec* p, unsigned long long) {
-  uint32_t w[8];
-  asm volatile(
-      "ld.global.nc.L1::no_allocate.L2::evict_last.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
-        "=r"(w[7])
-      : "l"(p));
-  TableRec r;
-  r.mx = __uint_as_float(w[0]);
-  r.p0 = __uint_as_float(w[1]);
-  r.tlo[0] = __uint_as_float(w[2]);
-  r.tlo[1] = __uint_as_float(w[3]);
-  r.ih[0] = __uint_as_float(w[4]);
-  r.ih[1] = __uint_as_float(w[5]);
-  const unsigned long long ptr = ((unsigned long long)w[7] << 32) | (unsigned long long)w[6];
-  r.iv = reinterpret_cast<const float4*>(ptr);
-  return r;
-}
 
 // The Newton inversion for the rare record whose table failed certification, kept out of line
 // so that its registers do not weigh on the table path.
