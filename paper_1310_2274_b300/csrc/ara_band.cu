@@ -137,6 +137,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
     const uint32_t q = beg + v * 32 + lane;
     wn[v] = q < end ? ld_stream_u32(P.bocc + q, pol.stream) : 0u;
   }
+  int t_row = 0;  // trial of the next row's first position (nondecreasing along the band words)
   for (uint32_t c = beg; c < end; c += kCh) {
     // ---- look up the chunk's entries, lay out its hits ----------------------------------------
     uint32_t w[kV];
@@ -159,11 +160,15 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const uint32_t q = c + v * 32 + lane;
-      int t = 0;
-      if (q < end) {
-#pragma unroll
-        for (int step = kT / 2; step >= 1; step >>= 1)  // last trial whose segment starts <= q
-          if (t + step < nt && sm.off[t + step] <= q) t += step;
+      // trial of position q: the last whose segment starts at or before q, found by advancing
+      // from the trial of the row's first position (segments are short, so a step or two)
+      int t = t_row;
+      if (q < end)
+        while (t + 1 < nt && sm.off[t + 1] <= q) ++t;
+      t_row = __shfl_sync(0xFFFFFFFFu, t, 31);
+      {
+        const uint32_t q31 = c + v * 32 + 31;  // the next row starts at the trial of lane 31
+        if (q31 >= end) t_row = nt - 1;
       }
       const int cnt = en[v].count();
       int incl = cnt;

@@ -270,11 +270,17 @@ ARA_HD float ara_exp2_fast(float r) {
 #endif
 }
 
-// Piece index and local coordinate of uniform u.
+// Piece index and local coordinate of uniform u.  ln q comes from the hardware base-2 logarithm
+// (relative error about 2^-22 for q <= 1/2), which moves z by at most ~3e-7: well inside a
+// piece, and the quantile's log-odds by L'(z) times that.
 ARA_HD int ara_table_piece(float u, float* tau) {
   const bool lower = u < 0.5f;
   const float q = lower ? u : 1.0f - u;  // exact on the uniform grid
+#ifdef __CUDA_ARCH__
+  const float t = sqrtf(-1.38629436f * __log2f(q));  // -2 ln q = -2 ln 2 log2 q
+#else
   const float t = sqrtf(-2.0f * logf(q));
+#endif
   const float z = lower ? t - kTableTm : kTableTm - t;
   const float pos = fminf(fmaxf((z + kTableZ) * kTableInvH, 0.0f), (float)kTablePieces);
   const int k = pos < (float)(kTablePieces - 1) ? (int)pos : kTablePieces - 1;

@@ -42,15 +42,13 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 __device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t* rk0, const uint32_t* rk1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;  // one 32x32 -> 64-bit product each
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
     U4 n;
-    n.x = hi1 ^ c.y ^ rk0[r];
-    n.y = lo1;
-    n.z = hi0 ^ c.w ^ rk1[r];
-    n.w = lo0;
+    n.x = (uint32_t)(p1 >> 32) ^ c.y ^ rk0[r];
+    n.y = (uint32_t)p1;
+    n.z = (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r];
+    n.w = (uint32_t)p0;
     c = n;
   }
   return c;
