@@ -568,24 +568,13 @@ ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
   }
   // band-major copy of the YET at this layer's band width (built once per width)
   const int log2w = ctx->band_log2w > 0 ? ctx->band_log2w : choose_band_log2w(C, L.n_packed);
-  YetDev& Y = ctx->yets[yet];
-  if (band_layout_fits(Y, log2w)) {
-    int slot = -1;
-    for (int v = 0; v < kMaxBandVariants && slot < 0; ++v)
-      if (Y.bands[v].log2w == log2w) slot = v;
-    for (int v = 0; v < kMaxBandVariants && slot < 0; ++v)
-      if (Y.bands[v].log2w == 0) {
-        err = build_band_variant(Y, log2w, Y.bands[v], ctx->stream);
-        if (err != cudaSuccess) {
-          cudaGetLastError();
-          free_layer(L);
-          return fail(ctx, err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA,
-                      "band-major YET copy: %s", cudaGetErrorString(err));
-        }
-        slot = v;
-      }
-    if (slot >= 0) L.band_log2w = log2w;
+  bool banded = false;
+  const ara_status bs = ensure_band_variant(ctx, yet, log2w, &banded);
+  if (bs != ARA_OK) {
+    free_layer(L);
+    return bs;
   }
+  if (banded) L.band_log2w = log2w;
   L.live = true;
   ctx->layers.push_back(L);
   *layer_out = (int32_t)ctx->layers.size() - 1;
@@ -632,6 +621,29 @@ static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64
 bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
   return inversion_mode(ctx) == 0 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
          ctx->cfg.precision == ARA_ACC_FP64;
+}
+
+ara_status ensure_band_variant(ara_ctx* ctx, int32_t yet, int log2w, bool* available) {
+  *available = false;
+  YetDev& Y = ctx->yets[yet];
+  if (!band_layout_fits(Y, log2w)) return ARA_OK;
+  for (int v = 0; v < kMaxBandVariants; ++v)
+    if (Y.bands[v].log2w == log2w) {
+      *available = true;
+      return ARA_OK;
+    }
+  for (int v = 0; v < kMaxBandVariants; ++v)
+    if (Y.bands[v].log2w == 0) {
+      const cudaError_t err = build_band_variant(Y, log2w, Y.bands[v], ctx->stream);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA,
+                    "band-major YET copy: %s", cudaGetErrorString(err));
+      }
+      *available = true;
+      return ARA_OK;
+    }
+  return ARA_OK;  // every slot taken: the layer runs trial-major
 }
 
 int inversion_mode(const ara_ctx* ctx) {

@@ -53,6 +53,8 @@ ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
                               double occ_lim, double agg_ret, double agg_lim, bool wide,
                               int32_t* layer_out);
 int inversion_mode(const ara_ctx* ctx);
+// Makes sure the YET has its band-major copy for band width 2^log2w (*available: it has).
+ara_status ensure_band_variant(ara_ctx* ctx, int32_t yet, int log2w, bool* available);
 bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L);
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,
                         double* d_ylt);

@@ -403,6 +403,27 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
     ara_set_option(ctx, ARA_OPT_SURROGATE, 0);
     ara_set_option(ctx, ARA_OPT_INVERSION, cfg->inversion);
   }
+  // band-major copies of the YET for every band width a request's layer can take (from all
+  // ELTs of the YET down to its smallest one), so that no request waits for one to be built
+  {
+    int64_t total = 0, smallest = -1;
+    for (const auto& e : ctx->elts)
+      if (e.live && e.yet == cfg->yet) {
+        total += e.n;
+        if (smallest < 0 || e.n < smallest) smallest = e.n;
+      }
+    if (total > 0 && !cfg->use_surrogate && cfg->inversion == ARA_INV_TABLE) {
+      const int64_t C = ctx->yets[cfg->yet].catalog;
+      const int lo = ara::choose_band_log2w(C, total), hi = ara::choose_band_log2w(C, smallest);
+      for (int w = lo; w <= hi; w += 2) {
+        bool ok = false;
+        if (ensure_band_variant(ctx, cfg->yet, w, &ok) != ARA_OK) {
+          ara_server_destroy(s);
+          return ARA_ERR_OOM;
+        }
+      }
+    }
+  }
   // ordering buffers sized for the whole YET
   const int64_t nmax = ctx->yets[cfg->yet].n_trials;
   SortScratch& so = s->sort;

@@ -26,7 +26,7 @@ constexpr double kTableTol = 1e-6;
 // a+n), rescaled by powers of two every step pair.
 ARA_HD double ara_beta_cf_f64(double a, double b, double x) {
   const double apb = a + b;
-  double Am2 = 1.0, Am1 = 1.0, Bm2 = 0.0, Bm1 = 1.0, prev = 1.0, res = 1.0;
+  double Am2 = 1.0, Am1 = 1.0, Bm2 = 0.0, Bm1 = 1.0, pA = 1.0, pB = 1.0;
   for (int n = 1; n < 4000; n += 2) {
     const double m = 0.5 * (double)(n - 1);
     const double al_odd = (n == 1) ? -apb * x : -(a + m) * (apb + m) * x;
@@ -40,14 +40,17 @@ ARA_HD double ara_beta_cf_f64(double a, double b, double x) {
     A = be_even * Am1 + al_even * Am2;
     B = be_even * Bm1 + al_even * Bm2;
     Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
+    // converged when B/A moved by at most 1e-15 relative since the previous pair, tested without
+    // a division: |B pA - pB A| <= 1e-15 |B pA| (pA, pB: the previous pair at the same scale)
+    const bool done = fabs(Bm1 * pA - pB * Am1) <= 1e-15 * fabs(Bm1 * pA);
     int e;
     frexp(Am1, &e);
     Am1 = ldexp(Am1, -e); Am2 = ldexp(Am2, -e); Bm1 = ldexp(Bm1, -e); Bm2 = ldexp(Bm2, -e);
-    res = Bm1 / Am1;
-    if (fabs(res - prev) <= 1e-15 * fabs(res)) break;
-    prev = res;
+    pA = Am1;
+    pB = Bm1;
+    if (done) break;
   }
-  return res;
+  return Bm1 / Am1;
 }
 
 // ln I_x(a,b) for x = e^r (DLMF 8.17.22; past (a+1)/(a+b+2) through DLMF 8.17.4).
@@ -76,10 +79,12 @@ ARA_HD double ara_polish_ln_quantile(const BetaRec& br, const TailParams& tp, fl
   const IbetaResult res = ara_inv_beta(br, uf);
   const double a = tp.a, b = tp.b;
   double r = res.t;
-  {  // one binary64 Newton step: the binary32 start is within ~1e-7, so the step lands ~1e-14
+  {  // one binary64 Newton step: the binary32 start is within ~1e-7, so the step lands ~1e-14;
+     // the slope G' only scales that small step, so binary32 accuracy is enough for it
     const double lnI = ara_ln_betainc_f64(a, b, r, tp.lnB);
-    const double x = exp(r);
-    const double dG = exp(a * r + (b - 1.0) * log1p(-x) - tp.lnB - lnI);
+    const float xf = expf((float)r);
+    const double lg = a * r - tp.lnB - lnI + (b - 1.0) * (double)log1pf(-xf);
+    const double dG = (double)expf((float)lg);
     const double step = (lnI - su) / dG;
     if (isfinite(step)) r -= step;
   }
@@ -159,9 +164,11 @@ ARA_HD LogitKnot logit_knot(const BetaRec& br, const BetaRec& sw, const TailPara
     lnx = log1p(-exp(ln1mx));
   }
   const double a = lo.a, b = lo.b;
-  const double x = exp(lnx), y = exp(ln1mx);
+  // the derivatives need ~1e-7 relative accuracy only (they enter the pieces multiplied by h and
+  // h^2): exponents in binary64, exponentials in binary32
+  const double x = (double)expf((float)lnx), y = (double)expf((float)ln1mx);
   k.L = lnx - ln1mx;
-  k.L1 = -t * exp(lnq + lo.lnB - a * lnx - b * ln1mx);
+  k.L1 = -t * (double)expf((float)(lnq + lo.lnB - a * lnx - b * ln1mx));
   k.L2 = k.L1 * k.L1 * (b * x - a * y) - s * (t * t - 1.0) * k.L1 / t;
   k.ok = ok && isfinite(k.L) && isfinite(k.L1) && isfinite(k.L2);
   return k;
