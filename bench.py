@@ -77,6 +77,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--schedule", choices=["band", "trial"], default="band")
+    p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--serve-requests", type=int, default=100)
     return p.parse_args()
 
@@ -355,6 +356,17 @@ def run_ours(a):
     sched_ms = {("band" if SCHEDULE == ara.SCHED_BAND else "trial"): kern_ms,
                 ("band" if other == ara.SCHED_BAND else "trial"): other_ms}
 
+    # ---- precision variant: Kahan-compensated FP32 year sums on the same data ------------------
+    ctx.set_option(ara.OPT_PRECISION, ara.ACC_KAHAN32)
+    ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
+    kahan_ms = time_runs(max(3, min(10, a.steps)))
+    kp, kt = ctx.risk_measures(ylt, rps)
+    ctx.set_option(ara.OPT_PRECISION, ara.ACC_FP64)
+    precision = {"fp64_exact_ms": kern_ms, "kahan32_ms": kahan_ms,
+                 "kahan32_schedule": "trial-major (order-dependent sums)",
+                 "pml_rel_diff": max(abs(float(x) / float(y) - 1.0) for x, y in zip(kp, pml)),
+                 "tvar_rel_diff": max(abs(float(x) / float(y) - 1.0) for x, y in zip(kt, tvar))}
+
     # ---- the Newton inversion on the same data (secondary figure) -----------------------------
     ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
     ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
@@ -418,11 +430,17 @@ def run_ours(a):
                                      "peak_source": f"FP32 FMA peak 2 x {SM_COUNT} SMs x "
                                                     f"{FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"}},
         "schedules_ms": sched_ms,
+        "precision": precision,
         "uncertified_records": s1["uncertified"],
         "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
                           "tvar": [float(v) for v in tvar]},
         "seconds_per_run": step_ms * 1e-3,
     }
+
+    # ---- learned surrogate of the inverse (trained here on the GPU), on the same data ----------
+    if not a.no_surrogate:
+        result["surrogate"] = surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, pml,
+                                            newton_ms)
 
     # ---- continuous-batching service on the resident YET (64 ELTs) ---------------------------
     if not a.no_serve and rank == 0:
@@ -441,6 +459,40 @@ def run_ours(a):
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
+
+
+def surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, pml_table, newton_ms):
+    """Trains the surrogate (the same settings as its tests), then times the paper-scale run with
+    it (network inside its certified cells, Newton elsewhere) against the Newton-only run."""
+    import torch
+
+    t = time.perf_counter()
+    rep = ctx.train_surrogate(n_samples=8_000_000, steps=30_000, batch=8192, lr=3e-3,
+                              lr_final=3e-5, eps=1e-3, cert_samples=16, seed=3)
+    train_s = time.perf_counter() - t
+    ctx.set_option(ara.OPT_SURROGATE, 1)
+    try:
+        ctx.run(yet, layer, 0, a.trials, out=ylt, stream=stream)
+        torch.cuda.synchronize(dev)
+        s0 = ctx.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run(yet, layer, 0, a.trials, out=ylt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        s1 = ctx.stats()
+        sp, _ = ctx.risk_measures(ylt, list(synth.RPS_PAPER))
+    finally:
+        ctx.set_option(ara.OPT_SURROGATE, 0)
+    net = s1["surrogate_evals"] - s0["surrogate_evals"]
+    fb = s1["inversions"] - s0["inversions"]
+    return {"kernel_ms": ms, "newton_only_ms": newton_ms, "speedup_vs_newton": newton_ms / ms,
+            "network_evals": net, "fallback_rate": fb / max(1, net + fb),
+            "pml_rel_diff_vs_table": max(abs(float(x) / float(y) - 1.0)
+                                         for x, y in zip(sp, pml_table)),
+            "cells_accepted": rep["cells_accepted"], "train_s": train_s,
+            "train": "8e6 tuples, 30,000 Adam steps of 8,192, eps 1e-3"}
 
 
 def serving(a, ara, ctx, yet, elts16, dev):
