@@ -65,6 +65,24 @@ void dev_free(void* p) {
   if (p) cudaFree(p);
 }
 
+// Allocation either plain (cudaMalloc/cudaFree, which waits for the device) or stream-ordered
+// on st (cudaMallocAsync/cudaFreeAsync from the device's memory pool, which never blocks the host:
+// the serving loop builds and frees layers while launches run).
+template <class T>
+cudaError_t mem_alloc(T** p, int64_t n, bool ordered, cudaStream_t st) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  const size_t bytes = sizeof(T) * (size_t)n;
+  return ordered ? cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st)
+                 : cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+void mem_free(const void* p, bool ordered, cudaStream_t st) {
+  if (!p) return;
+  if (ordered) cudaFreeAsync(const_cast<void*>(p), st);
+  else cudaFree(const_cast<void*>(p));
+}
+
 // Copies n elements from a host or device pointer into device memory on the stream.
 template <class T>
 cudaError_t copy_in(T* dst, const T* src, int64_t n, cudaStream_t st) {
@@ -84,13 +102,6 @@ void free_elt(EltDev& e) {
   dev_free(e.recs);
   dev_free(e.tables);
   e = EltDev();
-}
-void free_layer(LayerDev& l) {
-  dev_free(l.evt);
-  dev_free(l.tables);
-  dev_free(l.packed);
-  dev_free(l.packed_rec);
-  l = LayerDev();
 }
 
 ara_status set_device(ara_ctx* c) {
@@ -161,6 +172,16 @@ int64_t tail_count(int64_t n, double rp) {
 }
 
 }  // namespace
+
+void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st) {
+  mem_free(l.evt, ordered, st);
+  mem_free(l.tables, ordered, st);
+  mem_free(l.packed, ordered, st);
+  mem_free(l.packed_rec, ordered, st);
+  l = LayerDev();
+}
+
+void free_layer(LayerDev& l) { free_layer_on(l, false, nullptr); }
 
 extern "C" {
 
@@ -469,11 +490,12 @@ ara_status ara_free_elt(ara_ctx* ctx, int32_t elt) {
 
 // Builds a layer; wide = true forces 16-byte index entries (two mask words) whatever the ELT
 // count, the form the batched serving kernel takes.
-ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
-                              double occ_lim, double agg_ret, double agg_lim, bool wide,
-                              int32_t* layer_out) {
+ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
+                           double occ_lim, double agg_ret, double agg_lim, bool wide,
+                           cudaStream_t st, bool may_build_band, bool ordered,
+                           LayerDev* out) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
-  if (!layer_out || !elts) return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
+  if (!out || !elts) return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
   if (n_elts < 1 || n_elts > kMaxLayerElts)
     return fail(ctx, ARA_ERR_INVALID_ARG, "a layer covers 1..%d ELTs", kMaxLayerElts);
   const double terms[4] = {occ_ret, occ_lim, agg_ret, agg_lim};
@@ -508,74 +530,91 @@ ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts,
   const int64_t tmp_words = scan_tmp_words(C);
   cudaError_t err;
   auto cleanup = [&]() {
-    cudaStreamSynchronize(ctx->stream);
-    dev_free(d_mask);
-    dev_free(d_cnt);
-    dev_free(d_base);
-    dev_free(d_tmp);
+    if (!ordered) cudaStreamSynchronize(st);
+    mem_free(d_mask, ordered, st);
+    mem_free(d_cnt, ordered, st);
+    mem_free(d_base, ordered, st);
+    mem_free(d_tmp, ordered, st);
   };
   const int64_t evt_words = C * (MW == 1 ? 2 : 4);
-  if ((err = dev_alloc(&d_mask, C * MW)) != cudaSuccess || (err = dev_alloc(&d_cnt, C)) != cudaSuccess ||
-      (err = dev_alloc(&d_base, C)) != cudaSuccess || (err = dev_alloc(&d_tmp, tmp_words)) != cudaSuccess ||
-      (err = dev_alloc(&L.evt, evt_words)) != cudaSuccess) {
+  if ((err = mem_alloc(&d_mask, C * MW, ordered, st)) != cudaSuccess || (err = mem_alloc(&d_cnt, C, ordered, st)) != cudaSuccess ||
+      (err = mem_alloc(&d_base, C, ordered, st)) != cudaSuccess || (err = mem_alloc(&d_tmp, tmp_words, ordered, st)) != cudaSuccess ||
+      (err = mem_alloc(&L.evt, evt_words, ordered, st)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    free_layer(L);
+    free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_OOM, "layer index: %s", cudaGetErrorString(err));
   }
   uint32_t last[2] = {0, 0};
-  err = cudaMemsetAsync(d_mask, 0, sizeof(uint32_t) * (size_t)(C * MW), ctx->stream);
+  err = cudaMemsetAsync(d_mask, 0, sizeof(uint32_t) * (size_t)(C * MW), st);
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
-    err = launch_layer_mask(ctx->elts[elts[j]], j, MW, d_mask, ctx->stream);
-  if (err == cudaSuccess) err = launch_layer_counts(d_mask, MW, C, d_cnt, ctx->stream);
-  if (err == cudaSuccess) err = launch_exclusive_scan_u32(d_cnt, d_base, C, d_tmp, tmp_words, ctx->stream);
+    err = launch_layer_mask(ctx->elts[elts[j]], j, MW, d_mask, st);
+  if (err == cudaSuccess) err = launch_layer_counts(d_mask, MW, C, d_cnt, st);
+  if (err == cudaSuccess) err = launch_exclusive_scan_u32(d_cnt, d_base, C, d_tmp, tmp_words, st);
   if (err == cudaSuccess)
-    err = cudaMemcpyAsync(&last[0], d_base + (C - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    err = cudaMemcpyAsync(&last[0], d_base + (C - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (err == cudaSuccess)
-    err = cudaMemcpyAsync(&last[1], d_cnt + (C - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
-  if (err == cudaSuccess) err = launch_layer_index(d_mask, d_base, MW, C, L.evt, ctx->stream);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+    err = cudaMemcpyAsync(&last[1], d_cnt + (C - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = launch_layer_index(d_mask, d_base, MW, C, L.evt, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   if (err != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    free_layer(L);
+    free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_CUDA, "layer index: %s", cudaGetErrorString(err));
   }
   L.n_packed = (int64_t)last[0] + (int64_t)last[1];
   // packed records, then the records' tables copied into packed order (one gather per hit)
   const TablePiece** d_src = nullptr;
-  if ((err = dev_alloc(&L.packed, L.n_packed)) != cudaSuccess ||
-      (err = dev_alloc(&L.packed_rec, L.n_packed)) != cudaSuccess ||
-      (err = dev_alloc(&L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
-      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
+  if ((err = mem_alloc(&L.packed, L.n_packed, ordered, st)) != cudaSuccess ||
+      (err = mem_alloc(&L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
+      (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) != cudaSuccess ||
+      (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    dev_free(d_src);
-    free_layer(L);
+    mem_free(d_src, ordered, st);
+    free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_OOM, "layer records and tables: %s", cudaGetErrorString(err));
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
-                               ctx->stream);
-  if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, ctx->stream);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+                               st);
+  if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   cleanup();
-  dev_free(d_src);
+  mem_free(d_src, ordered, st);
   if (err != cudaSuccess) {
     cudaGetLastError();
-    free_layer(L);
+    free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_CUDA, "layer records: %s", cudaGetErrorString(err));
   }
   // band-major copy of the YET at this layer's band width (built once per width)
   const int log2w = ctx->band_log2w > 0 ? ctx->band_log2w : choose_band_log2w(C, L.n_packed);
   bool banded = false;
-  const ara_status bs = ensure_band_variant(ctx, yet, log2w, &banded);
-  if (bs != ARA_OK) {
-    free_layer(L);
-    return bs;
+  if (may_build_band) {
+    const ara_status bs = ensure_band_variant(ctx, yet, log2w, &banded);
+    if (bs != ARA_OK) {
+      free_layer_on(L, ordered, st);
+      return bs;
+    }
+  } else {
+    for (const auto& v : ctx->yets[yet].bands) banded = banded || v.log2w == log2w;
   }
   if (banded) L.band_log2w = log2w;
   L.live = true;
+  *out = L;
+  return ARA_OK;
+}
+
+ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
+                              double occ_lim, double agg_ret, double agg_lim, bool wide,
+                              int32_t* layer_out) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!layer_out) return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
+  LayerDev L;
+  const ara_status s = ara_build_layer(ctx, elts, n_elts, occ_ret, occ_lim, agg_ret, agg_lim,
+                                       wide, ctx->stream, true, false, &L);
+  if (s != ARA_OK) return s;
   ctx->layers.push_back(L);
   *layer_out = (int32_t)ctx->layers.size() - 1;
   return ARA_OK;

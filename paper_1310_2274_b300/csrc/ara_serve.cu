@@ -6,15 +6,17 @@
 // occurrence/aggregate terms), a trial range and return periods, and receives its YLT, PML and
 // TVaR.
 //
-// One worker thread runs the loop:
-//   admission  a pending request is admitted when a slot is free and its device memory (layer
-//              lookup structure + YLT) fits the HBM budget; its layer is built then;
-//   batching   each launch takes the next slice (up to slice_trials trials) of every admitted
+// Two host threads share the work:
+//   builder    admits a pending request when a slot is free and its device memory (layer lookup
+//              structure, packed records and tables, YLT, year sums) fits the HBM budget, and
+//              builds its layer on its own stream, so that launches in flight never wait for a
+//              build; it also frees the memory of finished requests (cudaFree waits for the
+//              device, so the launching thread never calls it);
+//   worker     each launch takes the next slice (up to slice_trials trials) of every running
 //              request, up to max_batch_trials in all, and runs them in one batched kernel launch
-//              (one warp per trial, each warp reading its own request's layer), so requests that
-//              arrive while others run join the very next launch and their work overlaps;
-//   completion a request whose last slice has finished gets its PML/TVaR on the device, its YLT
-//              copied out, and its memory released, which lets pending requests in.
+//              (each warp reading its own request's layer), so requests that arrive while others
+//              run join the very next launch; a request whose last slice has finished gets its
+//              PML/TVaR on the device and its YLT copied out, on a stream of its own.
 // Results do not depend on batching: a trial's year loss depends only on (trial, layer, seed).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -42,7 +44,8 @@ struct Request {
   ara_request req{};
   int32_t state = ARA_REQ_PENDING;
   double submit_s = 0, admit_s = 0, done_s = 0;
-  int32_t layer = -1;
+  LayerDev layer;          // the request's own layer (not registered in the context)
+  bool has_layer = false;
   double* d_ylt = nullptr;
   unsigned long long* d_ysum = nullptr;  // year sums in grid units (band-major schedule)
   bool band = false;
@@ -52,6 +55,15 @@ struct Request {
   std::vector<double> ylt; // host copy once done
   double pml[ARA_MAX_RPS] = {}, tvar[ARA_MAX_RPS] = {};
   ara_status error = ARA_OK;
+};
+
+// Device memory of a finished request, freed by the builder thread.
+struct Retired {
+  LayerDev layer;
+  bool has_layer = false;
+  double* d_ylt = nullptr;
+  unsigned long long* d_ysum = nullptr;
+  int64_t bytes = 0;
 };
 
 struct Launch {
@@ -71,9 +83,13 @@ struct ara_server {
   ara_server_config cfg{};
   cudaStream_t stream = nullptr;      // batched trial launches
   cudaStream_t fin_stream = nullptr;  // ordering, tail sums and copies of finished requests
+  cudaStream_t build_stream = nullptr;  // layer builds
   std::mutex mu;
-  std::condition_variable cv;
-  std::thread worker;
+  std::condition_variable cv;        // wakes the worker
+  std::condition_variable cv_build;  // wakes the builder
+  std::thread worker, builder;
+  int building = 0;                  // requests whose layer is being built
+  std::deque<Retired> retired;
   std::atomic<bool> stop{false};
   Clock::time_point t0;
   int64_t next_ticket = 1;
@@ -135,21 +151,27 @@ bool ensure_launch_capacity(Launch& L, int n) {
   return true;
 }
 
-void release(ara_server* s, Request& r) {
-  if (r.layer >= 0) ara_free_layer(s->ctx, r.layer);
-  if (r.d_ylt) cudaFree(r.d_ylt);
-  if (r.d_ysum) cudaFree(r.d_ysum);
-  r.layer = -1;
+// Hands a request's device memory to the builder thread for freeing (server lock held).
+void retire(ara_server* s, Request& r) {
+  Retired f;
+  f.layer = r.layer;
+  f.has_layer = r.has_layer;
+  f.d_ylt = r.d_ylt;
+  f.d_ysum = r.d_ysum;
+  f.bytes = r.bytes;
+  s->retired.push_back(f);
+  r.has_layer = false;
+  r.layer = LayerDev();
   r.d_ylt = nullptr;
   r.d_ysum = nullptr;
-  s->used -= r.bytes;
   r.bytes = 0;
+  s->cv_build.notify_one();
 }
 
 void fail_request(ara_server* s, Request& r, ara_status st) {
   cudaStreamSynchronize(s->stream);  // no launch in flight may still use its memory
   cudaGetLastError();
-  release(s, r);
+  retire(s, r);
   r.error = st;
   r.state = ARA_REQ_FAILED;
   r.done_s = now_s(s);
@@ -187,7 +209,7 @@ void finish(ara_server* s, Request& r) {
     fail_request(s, r, ARA_ERR_CUDA);
     return;
   }
-  release(s, r);
+  retire(s, r);
   r.state = ARA_REQ_DONE;
   r.done_s = now_s(s);
   s->n_done++;
@@ -195,41 +217,82 @@ void finish(ara_server* s, Request& r) {
   s->last_done = r.done_s;
 }
 
-// Admission of pending requests while slots and memory allow (server lock held).
-void admit(ara_server* s) {
-  while (!s->pending.empty() && (int)s->active.size() < s->cfg.max_inflight) {
-    Request& r = *s->reqs[s->pending.front()];
-    const int64_t need = request_bytes(s, r.req);
-    if (s->used + need > s->budget && !s->active.empty()) break;  // wait for memory to free
-    s->pending.pop_front();
-    r.bytes = need;
-    s->used += need;
-    int32_t layer = -1;
-    ara_status st = ara_add_layer_impl(s->ctx, r.req.elts, r.req.n_elts, r.req.occ_ret,
-                                       r.req.occ_lim, r.req.agg_ret, r.req.agg_lim, true, &layer);
-    if (st != ARA_OK) {
-      fail_request(s, r, st);
-      continue;
-    }
-    r.layer = layer;
-    if (cudaMalloc(&r.d_ylt, sizeof(double) * std::max<int64_t>(1, r.req.n_trials)) != cudaSuccess) {
+// Builder thread: frees retired memory, admits pending requests in arrival order while slots and
+// memory allow, and builds their layers on the build stream without holding the server lock.
+void builder_loop(ara_server* s) {
+  cudaSetDevice(s->ctx->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (!s->stop.load()) {
+    if (!s->retired.empty()) {
+      Retired f = s->retired.front();
+      s->retired.pop_front();
+      lk.unlock();
+      // the request's launches and copies are complete: stream-ordered frees, no host wait
+      if (f.has_layer) free_layer_on(f.layer, true, s->build_stream);
+      if (f.d_ylt) cudaFreeAsync(f.d_ylt, s->build_stream);
+      if (f.d_ysum) cudaFreeAsync(f.d_ysum, s->build_stream);
       cudaGetLastError();
-      fail_request(s, r, ARA_ERR_OOM);
+      lk.lock();
+      s->used -= f.bytes;
       continue;
     }
-    r.band = uses_band_schedule(s->ctx, s->ctx->layers[layer]);
-    if (r.band) {
-      const size_t bytes = sizeof(unsigned long long) * (size_t)r.req.n_trials;
-      if (cudaMalloc(&r.d_ysum, bytes) != cudaSuccess ||
-          cudaMemsetAsync(r.d_ysum, 0, bytes, s->stream) != cudaSuccess) {
+    if (s->pending.empty() || (int)s->active.size() + s->building >= s->cfg.max_inflight) {
+      s->cv_build.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    const int64_t tk = s->pending.front();
+    Request& r0 = *s->reqs[tk];
+    const int64_t need = request_bytes(s, r0.req);
+    if (s->used + need > s->budget && !(s->active.empty() && s->building == 0)) {
+      s->cv_build.wait_for(lk, std::chrono::milliseconds(2));  // wait for memory to free
+      continue;
+    }
+    s->pending.pop_front();
+    r0.bytes = need;
+    s->used += need;
+    s->building++;
+    const ara_request req = r0.req;
+    lk.unlock();
+    LayerDev L;
+    double* ylt = nullptr;
+    unsigned long long* ysum = nullptr;
+    bool band = false;
+    ara_status st = ara_build_layer(s->ctx, req.elts, req.n_elts, req.occ_ret, req.occ_lim,
+                                    req.agg_ret, req.agg_lim, true, s->build_stream, false, true,
+                                    &L);
+    if (st == ARA_OK) {
+      band = uses_band_schedule(s->ctx, L);
+      const size_t n = (size_t)std::max<int64_t>(1, req.n_trials);
+      if (cudaMallocAsync(&ylt, sizeof(double) * n, s->build_stream) != cudaSuccess ||
+          (band && (cudaMallocAsync(&ysum, sizeof(unsigned long long) * n, s->build_stream) !=
+                        cudaSuccess ||
+                    cudaMemsetAsync(ysum, 0, sizeof(unsigned long long) * n,
+                                    s->build_stream) != cudaSuccess)) ||
+          cudaStreamSynchronize(s->build_stream) != cudaSuccess) {
         cudaGetLastError();
-        fail_request(s, r, ARA_ERR_OOM);
-        continue;
+        st = ARA_ERR_OOM;
       }
     }
+    lk.lock();
+    s->building--;
+    Request& r = *s->reqs[tk];  // a request can be released only once done or failed
+    r.layer = L;
+    r.has_layer = st == ARA_OK || L.live;
+    r.d_ylt = ylt;
+    r.d_ysum = ysum;
+    if (st != ARA_OK) {
+      retire(s, r);
+      r.error = st;
+      r.state = ARA_REQ_FAILED;
+      r.done_s = now_s(s);
+      s->n_failed++;
+      continue;
+    }
+    r.band = band;
     r.state = ARA_REQ_RUNNING;
     r.admit_s = now_s(s);
-    s->active.push_back(r.ticket);
+    s->active.push_back(tk);
+    s->cv.notify_all();
   }
 }
 
@@ -299,7 +362,7 @@ bool issue(ara_server* s) {
   for (int i = 0; i < k; ++i) {
     Request& r = *take[i].first;
     const int64_t n = take[i].second;
-    const LayerDev& Ld = s->ctx->layers[r.layer];
+    const LayerDev& Ld = r.layer;
     TrialParams p = make_params(s->ctx, Y, Ld, r.req.t0 + r.next, n, r.d_ylt + r.next);
     if (r.band) {
       p.tiles = (int32_t)ara::band_tiles(n);
@@ -346,7 +409,6 @@ void worker_loop(ara_server* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop.load()) {
     reap(s, false);
-    admit(s);
     // keep two launches in flight: the next one is built while the previous runs
     bool issued = false;
     while (s->inflight.size() < 2 && issue(s)) issued = true;
@@ -380,8 +442,15 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
   s->cfg = *cfg;
   s->t0 = Clock::now();
   size_t free_b = 0, total_b = 0;
+  // layer builds and the finishing of requests are on the latency path: their streams have the
+  // greatest priority, so their few blocks are scheduled ahead of the batched launches' blocks
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->fin_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&s->fin_stream, cudaStreamNonBlocking, prio_greatest) !=
+          cudaSuccess ||
+      cudaStreamCreateWithPriority(&s->build_stream, cudaStreamNonBlocking, prio_greatest) !=
+          cudaSuccess ||
       cudaMemGetInfo(&free_b, &total_b) != cudaSuccess ||
       cudaMalloc(&s->d_k, sizeof(int64_t) * ARA_MAX_RPS) != cudaSuccess ||
       cudaMalloc(&s->d_pml, sizeof(double) * ARA_MAX_RPS) != cudaSuccess ||
@@ -389,6 +458,14 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
     cudaGetLastError();
     ara_server_destroy(s);
     return ARA_ERR_CUDA;
+  }
+  {  // freed request memory stays in the device's pool for the next request's layer
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
   }
   s->budget = cfg->hbm_budget > 0 ? cfg->hbm_budget
                                   : std::max<int64_t>(0, (int64_t)free_b - ((int64_t)4 << 30));
@@ -443,6 +520,7 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
   so.cap = nmax;
   so.hist_cap = hist_n;
   s->worker = std::thread(worker_loop, s);
+  s->builder = std::thread(builder_loop, s);
   *out = s;
   return ARA_OK;
 }
@@ -471,7 +549,7 @@ ara_status ara_server_submit(ara_server* s, const ara_request* req, int64_t* tic
   *ticket = r->ticket;
   s->pending.push_back(r->ticket);
   s->reqs[r->ticket] = std::move(r);
-  s->cv.notify_one();
+  s->cv_build.notify_one();
   return ARA_OK;
 }
 
@@ -557,8 +635,17 @@ void ara_server_destroy(ara_server* s) {
   if (!s) return;
   s->stop.store(true);
   s->cv.notify_all();
+  s->cv_build.notify_all();
   if (s->worker.joinable()) s->worker.join();
-  for (auto& kv : s->reqs) release(s, *kv.second);
+  if (s->builder.joinable()) s->builder.join();
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& kv : s->reqs) retire(s, *kv.second);
+  for (auto& f : s->retired) {
+    if (f.has_layer) free_layer_on(f.layer, true, s->build_stream);
+    if (f.d_ylt) cudaFreeAsync(f.d_ylt, s->build_stream);
+    if (f.d_ysum) cudaFreeAsync(f.d_ysum, s->build_stream);
+  }
+  s->retired.clear();
   auto drop = [](Launch& L) {
     if (L.done) cudaEventDestroy(L.done);
     if (L.h_items) cudaFreeHost(L.h_items);
@@ -579,10 +666,18 @@ void ara_server_destroy(ara_server* s) {
   if (s->d_pml) cudaFree(s->d_pml);
   if (s->d_tvar) cudaFree(s->d_tvar);
   if (s->ctx) ara_set_stream(s->ctx, nullptr);
-  for (cudaStream_t st : {s->stream, s->fin_stream}) {
+  for (cudaStream_t st : {s->stream, s->fin_stream, s->build_stream}) {
     if (!st) continue;
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
+  }
+  {  // hand the pooled request memory back and restore the pool's default release threshold
+    cudaMemPool_t pool;
+    if (s->ctx && cudaDeviceGetDefaultMemPool(&pool, s->ctx->device) == cudaSuccess) {
+      cudaMemPoolTrimTo(pool, 0);
+      uint64_t zero = 0;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &zero);
+    }
   }
   cudaGetLastError();
   delete s;
