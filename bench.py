@@ -97,7 +97,9 @@ def workload_config(a, world, l2_note=True):
         "terms": [synth.TERMS_PAPER.occ_ret, synth.TERMS_PAPER.occ_lim,
                   synth.TERMS_PAPER.agg_ret, synth.TERMS_PAPER.agg_lim],
         "return_periods": list(synth.RPS_PAPER), "philox_seed": 42,
-        "parallelism": f"trial batches, {world} independent GPU(s)",
+        "parallelism": (f"trial batches on {world} GPU(s); global PML/TVaR by one all-gather of "
+                        "each rank's k_max largest year losses" if world > 1 else
+                        "trial batch on one GPU"),
         "l2": "inputs larger than L2 (3.2 GB event-id stream per step); the per-layer lookup "
               "tables (~72 MB) stay L2-resident by design",
     }
@@ -279,9 +281,18 @@ def run_ours(a):
     layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
     ylt = torch.empty(n, dtype=torch.float64, device=dev)
 
+    from paper_1310_2274_b300 import shards
+
+    def risk():
+        # one rank: PML/TVaR of its YLT; several: the global tails of all ranks' trials through
+        # the one exchange of the trial-sharded path (each rank's k_max largest, gathered)
+        if world > 1:
+            return shards.global_risk(ctx, ylt, world * n, rps)
+        return ctx.risk_measures(ylt, rps)
+
     def step():
         ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
-        return ctx.risk_measures(ylt, rps)
+        return risk()
 
     for _ in range(a.warmup):
         step()
@@ -302,7 +313,7 @@ def run_ours(a):
         k_ev[i][0].record(stream)
         ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
         k_ev[i][1].record(stream)
-        pml, tvar = ctx.risk_measures(ylt, rps)
+        pml, tvar = risk()
     t_end.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:

@@ -168,6 +168,21 @@ ARA_API ara_status ara_risk_measures(ara_ctx* ctx, const double* ylt, int64_t n,
  * host or device memory (int64). */
 ARA_API ara_status ara_rank_ylt(ara_ctx* ctx, const double* ylt, int64_t n, int64_t* order);
 
+/* Trial shards (one process per GPU, trials split into contiguous ranges, one collective):
+ * the global PML/TVaR of N_total trials needs, for each return period, the k = N_total/RP
+ * largest year losses of all shards.  Each shard sends the k_max largest of its own (k_max for
+ * the smallest RP), in ascending trial order; concatenated in shard order they are in global trial
+ * order, so ordering them by (loss descending, position ascending) is the global ordering of
+ * §2.4 restricted to the candidates, which contain every trial a tail needs.
+ *   ara_top_k: out[k] = the k largest entries of ylt[n] (ties: lower index first), in ascending
+ *     index order (0 <= k <= n; ylt and out host or device).
+ *   ara_risk_measures_n: PML/TVaR as ara_risk_measures over values[n] with the tail counts of
+ *     n_total trials, k = n_total/RP; ARA_ERR_INVALID_ARG if some k exceeds n. */
+ARA_API ara_status ara_top_k(ara_ctx* ctx, const double* ylt, int64_t n, int64_t k, double* out);
+ARA_API ara_status ara_risk_measures_n(ara_ctx* ctx, const double* values, int64_t n,
+                                       int64_t n_total, const double* rps, int32_t m, double* pml,
+                                       double* tvar);
+
 /* Learned surrogate of InvCDF_beta ----------------------------------------------------------------
  * A 3 -> 64 -> 64 -> 64 -> 1 SiLU network (BF16 weights, FP32 accumulation, tensor-core MMA) maps
  * (ln alpha, ln beta, logit u), normalised over the box alpha, beta in [0.1, 50], to logit x.

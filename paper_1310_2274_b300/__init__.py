@@ -108,6 +108,8 @@ _SIGNATURES = {
     "ara_not_converged": ([_P, C.POINTER(_I64)], C.c_int),
     "ara_risk_measures": ([_P, _P, _I64, _P, _I32, _P, _P], C.c_int),
     "ara_rank_ylt": ([_P, _P, _I64, _P], C.c_int),
+    "ara_top_k": ([_P, _P, _I64, _I64, _P], C.c_int),
+    "ara_risk_measures_n": ([_P, _P, _I64, _I64, _P, _I32, _P, _P], C.c_int),
     "ara_trace_hits": ([_P, _I32, _I32, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P,
                         C.POINTER(_I64)], C.c_int),
     "ara_synchronize": ([_P], C.c_int),
@@ -305,6 +307,29 @@ class Context:
         self._check(lib().ara_risk_measures(self._h, _ptr(y), int(y.shape[0]), _ptr(r),
                                             int(r.shape[0]), _ptr(pml), _ptr(tvar)))
         return pml, tvar
+
+    def risk_measures_n(self, values, n_total, rps):
+        """PML/TVaR over candidate values with the tail counts of n_total trials."""
+        y = values if _is_cuda(values) else _np(values, np.float64)
+        r = np.ascontiguousarray(rps, dtype=np.float64)
+        pml = np.zeros(r.shape[0])
+        tvar = np.zeros(r.shape[0])
+        self._check(lib().ara_risk_measures_n(self._h, _ptr(y), int(y.shape[0]), int(n_total),
+                                              _ptr(r), int(r.shape[0]), _ptr(pml), _ptr(tvar)))
+        return pml, tvar
+
+    def top_k(self, ylt, k, out=None):
+        """The k largest year losses (ties: lower index first) in ascending trial order."""
+        y = ylt if _is_cuda(ylt) else _np(ylt, np.float64)
+        if out is None:
+            if _is_cuda(y):
+                import torch
+
+                out = torch.empty(int(k), dtype=torch.float64, device=y.device)
+            else:
+                out = np.zeros(int(k), dtype=np.float64)
+        self._check(lib().ara_top_k(self._h, _ptr(y), int(y.shape[0]), int(k), _ptr(out)))
+        return out
 
     def rank(self, ylt, out=None):
         y = ylt if _is_cuda(ylt) else _np(ylt, np.float64)

@@ -44,6 +44,8 @@ struct ara_ctx {
   unsigned long long* d_ysum = nullptr;  // year sums in grid units (band-major runs)
   int64_t ysum_cap = 0;
   int32_t schedule = 0;                  // ARA_SCHED_BAND or ARA_SCHED_TRIAL
+  uint32_t* d_sel = nullptr;             // top-k selection: flags, positions, scan scratch
+  int64_t sel_cap = 0;
   int32_t band_log2w = 0;                // band width exponent for new layers (0: automatic)
   void* d_misc = nullptr;  // small staging area for tail sums
 };

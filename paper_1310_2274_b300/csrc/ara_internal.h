@@ -195,6 +195,11 @@ cudaError_t launch_tail_sums(const double* d_ylt, const uint32_t* d_order, int64
                              cudaStream_t st);
 cudaError_t launch_order_to_i64(const uint32_t* d_order, int64_t n, int64_t* d_out,
                                 cudaStream_t st);
+// The first k entries of d_order (ranks), written to d_out in ascending index order; flags and
+// pos hold n words each, tmp the scan's scratch.
+cudaError_t launch_top_k_in_index_order(const double* d_y, const uint32_t* d_order, int64_t n,
+                                       int64_t k, uint32_t* flags, uint32_t* pos, uint32_t* tmp,
+                                       int64_t tmp_words, double* d_out, cudaStream_t st);
 cudaError_t launch_check_nan(const double* d_ylt, int64_t n, unsigned int* d_flag,
                              cudaStream_t st);
 

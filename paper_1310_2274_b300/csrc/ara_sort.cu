@@ -158,6 +158,19 @@ __global__ void order_to_i64_kernel(const uint32_t* __restrict__ o, int64_t n, i
   if (i < n) out[i] = (int64_t)o[i];
 }
 
+// flags[order[r]] = 1 for the first k ranks (flags zeroed before).
+__global__ void mark_top_kernel(const uint32_t* __restrict__ order, int64_t k, uint32_t* flags) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < k) flags[order[r]] = 1u;
+}
+
+// The marked entries in index order: out[pos[i]] = y[i] where flags[i] is set.
+__global__ void compact_marked_kernel(const double* __restrict__ y, const uint32_t* __restrict__ flags,
+                                      const uint32_t* __restrict__ pos, int64_t n, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flags[i]) out[pos[i]] = y[i];
+}
+
 }  // namespace
 
 int64_t sort_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
@@ -259,6 +272,22 @@ cudaError_t launch_tail_sums_flagged(const double* d_ylt, const uint32_t* d_orde
 cudaError_t launch_order_to_i64(const uint32_t* d_order, int64_t n, int64_t* d_out,
                                 cudaStream_t st) {
   order_to_i64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_order, n, d_out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_top_k_in_index_order(const double* d_y, const uint32_t* d_order, int64_t n,
+                                       int64_t k, uint32_t* flags, uint32_t* pos, uint32_t* tmp,
+                                       int64_t tmp_words, double* d_out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (size_t)n, st);
+  if (e != cudaSuccess) return e;
+  if (k > 0) {
+    mark_top_kernel<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(d_order, k, flags);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = launch_exclusive_scan_u32(flags, pos, n, tmp, tmp_words, st)) != cudaSuccess) return e;
+  compact_marked_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_y, flags, pos, n, d_out);
   count_launches(1);
   return cudaGetLastError();
 }

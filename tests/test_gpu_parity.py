@@ -311,3 +311,28 @@ def test_extreme_shapes_tables_match_newton(ara, oracle):
         assert dx.max() <= 2e-6
         # loss-weighted relative error
         assert dx.sum() / oh["x"].sum() <= 1e-6
+
+
+def test_top_k_and_shard_risk_measures(ctx, oracle):
+    # the device side of the trial-shard exchange: per-shard candidates and the global tails
+    rng = np.random.default_rng(29)
+    n = 20_011
+    y = np.round(rng.lognormal(10, 1.2, n), -3)  # many ties
+    k = 517
+    order = oracle.rank(y)
+    np.testing.assert_array_equal(ctx.top_k(y, k), y[np.sort(order[:k])])
+    import torch
+
+    yd = torch.from_numpy(y).cuda()
+    np.testing.assert_array_equal(ctx.top_k(yd, k).cpu().numpy(), y[np.sort(order[:k])])
+    assert ctx.top_k(y, 0).shape == (0,)
+    rps = (10.0, 100.0, 1000.5)
+    k_max = max(oracle.tail_count(n, rp) for rp in rps)
+    cuts = [0, 6_000, 13_337, n]
+    cand = np.concatenate([ctx.top_k(y[a:b], min(k_max, b - a)) for a, b in zip(cuts, cuts[1:])])
+    gp, gt = ctx.risk_measures_n(cand, n, rps)
+    op, ot = oracle.risk(y, rps)
+    np.testing.assert_array_equal(gp, op)
+    np.testing.assert_allclose(gt, ot, rtol=1e-12)
+    with pytest.raises(Exception):
+        ctx.risk_measures_n(cand[:10], n, rps)  # too few candidates for the 1-in-10 tail
