@@ -168,3 +168,28 @@ def test_poisson_arrivals_latency(ara, staged):
           f"p99 {st['latency_p99_s'] * 1e3:.2f} ms, {st['requests_per_s']:.1f} req/s, "
           f"{st['mean_items_per_launch']:.2f} requests per launch")
     assert st["completed"] == len(mix)
+
+
+@pytest.mark.parametrize("mode", ["newton", "kahan"])
+def test_trial_major_serving_equals_requests_run_alone(ara, staged, mode):
+    # the batched trial-major kernel: Newton inversion, or Kahan FP32 year sums (both keep the
+    # trial-major schedule); results again identical to the same requests run alone
+    c, yet, hs = staged
+    mix = [dict(r, n_trials=min(r["n_trials"], 3000)) for r in request_mix(hs, 4, seed=5)]
+    inversion = ara.INV_NEWTON if mode == "newton" else ara.INV_TABLE
+    c.set_option(ara.OPT_INVERSION, inversion)
+    if mode == "kahan":
+        c.set_option(ara.OPT_PRECISION, ara.ACC_KAHAN32)
+    try:
+        ref = [alone(c, yet, r) for r in mix]
+        with ara.Server(c, yet, max_inflight=4, slice_trials=700, inversion=inversion) as s:
+            tickets = [s.submit(**r) for r in mix]
+            for tk in tickets:
+                assert s.wait(tk, 120.0) == 0
+            for tk, (y, p, t) in zip(tickets, ref):
+                res = s.result(tk)
+                np.testing.assert_array_equal(res["ylt"], y)
+                np.testing.assert_array_equal(res["pml"][:3], p)
+    finally:
+        c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+        c.set_option(ara.OPT_PRECISION, ara.ACC_FP64)
