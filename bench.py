@@ -100,8 +100,9 @@ def workload_config(a, world, l2_note=True):
         "parallelism": (f"trial batches on {world} GPU(s); global PML/TVaR by one all-gather of "
                         "each rank's k_max largest year losses" if world > 1 else
                         "trial batch on one GPU"),
-        "l2": "inputs larger than L2 (3.2 GB event-id stream per step); the per-layer lookup "
-              "tables (~72 MB) stay L2-resident by design",
+        "l2": "inputs larger than L2 (3.2 GB of band-major event words per step, 3.7 GB of "
+              "quantile tables); one catalogue band's index and tables are L2-resident while "
+              "the band is processed",
     }
 
 
