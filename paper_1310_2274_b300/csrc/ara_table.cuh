@@ -43,9 +43,11 @@ ARA_HD double ara_beta_cf_f64(double a, double b, double x) {
     // converged when B/A moved by at most 1e-15 relative since the previous pair, tested without
     // a division: |B pA - pB A| <= 1e-15 |B pA| (pA, pB: the previous pair at the same scale)
     const bool done = fabs(Bm1 * pA - pB * Am1) <= 1e-15 * fabs(Bm1 * pA);
-    int e;
-    frexp(Am1, &e);
-    Am1 = ldexp(Am1, -e); Am2 = ldexp(Am2, -e); Bm1 = ldexp(Bm1, -e); Bm2 = ldexp(Bm2, -e);
+    if (((n >> 1) & 3) == 3) {  // a pair grows A, B by about (a+n)^2: rescale every 4th pair
+      int e;
+      frexp(Am1, &e);
+      Am1 = ldexp(Am1, -e); Am2 = ldexp(Am2, -e); Bm1 = ldexp(Bm1, -e); Bm2 = ldexp(Bm2, -e);
+    }
     pA = Am1;
     pB = Bm1;
     if (done) break;
@@ -53,21 +55,25 @@ ARA_HD double ara_beta_cf_f64(double a, double b, double x) {
   return Bm1 / Am1;
 }
 
-// ln I_x(a,b) for x = e^r (DLMF 8.17.22; past (a+1)/(a+b+2) through DLMF 8.17.4).
-ARA_HD double ara_ln_betainc_f64(double a, double b, double r, double lnB) {
+// ln I_x(a,b) for x = e^r (DLMF 8.17.22; past (a+1)/(a+b+2) through DLMF 8.17.4); lna = ln a.
+ARA_HD double ara_ln_betainc_f64(double a, double b, double r, double lnB, double lna) {
   const double x = exp(r);
   if (x < (a + 1.0) / (a + b + 2.0)) {
-    return a * r + b * log1p(-x) - lnB + log(ara_beta_cf_f64(a, b, x)) - log(a);
+    return a * r + b * log1p(-x) - lnB + log(ara_beta_cf_f64(a, b, x)) - lna;
   }
   const double y = 1.0 - x;
   const double Iy = exp(b * log(y) + a * r - lnB) * ara_beta_cf_f64(b, a, y) / b;
   return log1p(-Iy);
+}
+ARA_HD double ara_ln_betainc_f64(double a, double b, double r, double lnB) {
+  return ara_ln_betainc_f64(a, b, r, lnB, log(a));
 }
 
 // The tail's beta parameters in binary64 (as computed from mean, sd and max when the ELT was
 // staged) and ln B(a,b).
 struct TailParams {
   double a, b, lnB;
+  double lna;  // ln a (0: compute it)
 };
 
 // ln of the quantile of the tail described by br (binary32 record, solved without flipping: u <=
@@ -81,7 +87,7 @@ ARA_HD double ara_polish_ln_quantile(const BetaRec& br, const TailParams& tp, fl
   double r = res.t;
   {  // one binary64 Newton step: the binary32 start is within ~1e-7, so the step lands ~1e-14;
      // the slope G' only scales that small step, so binary32 accuracy is enough for it
-    const double lnI = ara_ln_betainc_f64(a, b, r, tp.lnB);
+    const double lnI = ara_ln_betainc_f64(a, b, r, tp.lnB, tp.lna != 0.0 ? tp.lna : log(a));
     const float xf = expf((float)r);
     const double lg = a * r - tp.lnB - lnI + (b - 1.0) * (double)log1pf(-xf);
     const double dG = (double)expf((float)lg);
@@ -143,25 +149,28 @@ ARA_HD LogitKnot logit_knot(const BetaRec& br, const BetaRec& sw, const TailPara
   LogitKnot k;
   const double t = (double)kTableTm + fabs(z);
   const double lnq = -0.5 * t * t;
-  const double q = exp(lnq);
-  // u = q below the median, 1 - q above it; ln u and ln(1 - u) without cancellation
-  const double lnu = z >= 0.0 ? lnq : log1p(-q);
-  const double ln1mu = z >= 0.0 ? log1p(-q) : lnq;
-  const double u = z >= 0.0 ? q : 1.0 - q;
+  const float qf = expf((float)lnq);
+  // u = q below the median, 1 - q above it; ln u or ln(1 - u) (whichever the solve needs) in
+  // binary64 without cancellation.  The complement ln(1 - v) of the solved v = x or 1 - x is
+  // well conditioned in binary32 while v <= 1/2 (it enters L at the 1e-7 level); above that it
+  // takes binary64
+  const bool below = z >= 0.0 ? (double)qf <= (double)br.p0 : (1.0 - (double)qf) <= (double)br.p0;
   bool ok;
   double lnx, ln1mx;
-  if (u <= (double)br.p0) {
-    float uf = (float)u;
+  if (below) {
+    const double lnu = z >= 0.0 ? lnq : log1p(-exp(lnq));
+    float uf = (float)exp(lnu);
     if (!(uf <= br.p0)) uf = br.p0;
     if (!(uf > 0.0f)) uf = 1.17549435e-38f;
     lnx = ara_polish_ln_quantile(br, lo, uf, lnu, &ok);
-    ln1mx = log1p(-exp(lnx));
+    ln1mx = lnx < -0.6931471805599453 ? (double)log1pf(-expf((float)lnx)) : log1p(-exp(lnx));
   } else {
+    const double ln1mu = z >= 0.0 ? log1p(-exp(lnq)) : lnq;
     float vf = (float)exp(ln1mu);
     if (!(vf <= sw.p0)) vf = sw.p0;
     if (!(vf > 0.0f)) vf = 1.17549435e-38f;
     ln1mx = ara_polish_ln_quantile(sw, up, vf, ln1mu, &ok);
-    lnx = log1p(-exp(ln1mx));
+    lnx = ln1mx < -0.6931471805599453 ? (double)log1pf(-expf((float)ln1mx)) : log1p(-exp(ln1mx));
   }
   const double a = lo.a, b = lo.b;
   // the derivatives need ~1e-7 relative accuracy only (they enter the pieces multiplied by h and
@@ -188,7 +197,7 @@ ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, Ta
     return;
   }
   const double lnB = lgamma(a64) + lgamma(b64) - lgamma(a64 + b64);
-  const TailParams lo = {a64, b64, lnB}, up = {b64, a64, lnB};
+  const TailParams lo = {a64, b64, lnB, log(a64)}, up = {b64, a64, lnB, log(b64)};
   BetaRec sw;  // the swapped record: 1 - x ~ Beta(b, a), whose own mean probability is 1 - p0
   sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
   sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
