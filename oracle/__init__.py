@@ -50,10 +50,18 @@ def _declare(L):
     L.ora_agg_terms.restype = C.c_double
     L.ora_su_loss.argtypes = [C.c_double] * 4 + [C.POINTER(C.c_int)]
     L.ora_su_loss.restype = C.c_double
-    L.ora_run.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
+    L.ora_su_uniform_corr.argtypes = [C.c_uint64, C.c_int64, C.c_int64]
+    L.ora_su_uniform_corr.restype = C.c_double
+    L.ora_norm_cdf.argtypes = [C.c_double]
+    L.ora_norm_cdf.restype = C.c_double
+    L.ora_norm_quantile.argtypes = [C.c_double]
+    L.ora_norm_quantile.restype = C.c_double
+    L.ora_su_combine.argtypes = [C.c_double] * 4
+    L.ora_su_combine.restype = C.c_double
+    L.ora_run.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
                           C.c_int64, _P, C.POINTER(C.c_int64), C.c_int]
     L.ora_run.restype = C.c_int
-    L.ora_trace.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
+    L.ora_trace.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
                             C.c_int64, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                             C.POINTER(C.c_int64)]
     L.ora_trace.restype = C.c_int
@@ -122,6 +130,22 @@ def agg_terms(s, r, lim):
     return lib().ora_agg_terms(s, r, lim)
 
 
+def su_uniform_corr(seed: int, trial: int, k: int) -> float:
+    return lib().ora_su_uniform_corr(seed, trial, k)
+
+
+def norm_cdf(x: float) -> float:
+    return lib().ora_norm_cdf(x)
+
+
+def norm_quantile(p: float) -> float:
+    return lib().ora_norm_quantile(p)
+
+
+def su_combine(zp: float, ze: float, sd_i: float, sd_c: float) -> float:
+    return lib().ora_su_combine(zp, ze, sd_i, sd_c)
+
+
 def su_loss(mean, sd, mx, u):
     st = C.c_int(0)
     v = lib().ora_su_loss(mean, sd, mx, u, C.byref(st))
@@ -137,15 +161,17 @@ def _layer_arrays(elts, elt_handles):
     ids = np.ascontiguousarray(cat(lambda e: e.event_ids), dtype=np.int32)
     mean = np.ascontiguousarray(cat(lambda e: e.mean), dtype=np.float64)
     sd = np.ascontiguousarray(cat(lambda e: e.sd), dtype=np.float64)
+    sdc = np.ascontiguousarray(cat(lambda e: e.sd_corr if getattr(e, "sd_corr", None) is not None
+                                   else np.zeros(e.n)), dtype=np.float64)
     mx = np.ascontiguousarray(cat(lambda e: e.max_exposure), dtype=np.float64)
     h = np.ascontiguousarray(elt_handles if elt_handles is not None else np.arange(len(elts)),
                              dtype=np.int32)
-    return off, ids, mean, sd, mx, h
+    return off, ids, mean, sd, sdc, mx, h
 
 
 def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0):
     """Year losses of the selected trials (all by default) -> (ylt float64, not_converged)."""
-    off, ids, mean, sd, mx, h = _layer_arrays(elts, elt_handles)
+    off, ids, mean, sd, sdc, mx, h = _layer_arrays(elts, elt_handles)
     t = np.ascontiguousarray(np.arange(yet.n_trials) if trials is None else trials,
                              dtype=np.int64)
     yo = np.ascontiguousarray(yet.offsets, dtype=np.int64)
@@ -154,7 +180,7 @@ def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0)
     ylt = np.zeros(t.shape[0], dtype=np.float64)
     nc = C.c_int64(0)
     rc = lib().ora_run(_ptr(yo), _ptr(yi), len(elts), _ptr(off), _ptr(ids), _ptr(mean),
-                       _ptr(sd), _ptr(mx), _ptr(h), _ptr(tr), seed, _ptr(t), t.shape[0],
+                       _ptr(sd), _ptr(sdc), _ptr(mx), _ptr(h), _ptr(tr), seed, _ptr(t), t.shape[0],
                        _ptr(ylt), C.byref(nc), int(threads))
     if rc != 0:
         raise ValueError(f"oracle run failed: {rc}")
@@ -163,7 +189,7 @@ def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0)
 
 def trace(yet, elts, terms, seed, trials, elt_handles=None, max_hits: int = 1 << 22):
     """Every hit of the selected trials in loop order, plus their year losses."""
-    off, ids, mean, sd, mx, h = _layer_arrays(elts, elt_handles)
+    off, ids, mean, sd, sdc, mx, h = _layer_arrays(elts, elt_handles)
     t = np.ascontiguousarray(trials, dtype=np.int64)
     yo = np.ascontiguousarray(yet.offsets, dtype=np.int64)
     yi = np.ascontiguousarray(yet.event_ids, dtype=np.int32)
@@ -175,7 +201,7 @@ def trace(yet, elts, terms, seed, trials, elt_handles=None, max_hits: int = 1 <<
                loss=np.zeros(max_hits, np.float64))
     nh = C.c_int64(0)
     rc = lib().ora_trace(_ptr(yo), _ptr(yi), len(elts), _ptr(off), _ptr(ids), _ptr(mean),
-                         _ptr(sd), _ptr(mx), _ptr(h), _ptr(tr), seed, _ptr(t), t.shape[0],
+                         _ptr(sd), _ptr(sdc), _ptr(mx), _ptr(h), _ptr(tr), seed, _ptr(t), t.shape[0],
                          _ptr(ylt), max_hits, _ptr(out["trial"]), _ptr(out["k"]),
                          _ptr(out["j"]), _ptr(out["rec"]), _ptr(out["u"]), _ptr(out["x"]),
                          _ptr(out["loss"]), C.byref(nh))

@@ -13,6 +13,10 @@
  *                       and Table 2 (Philox4x32 with R = 10 rounds). It stands in for the
  *                       pre-stored uniforms z_(Prog,E) and z_(E) of paper §3.1.
  *   ora_uniform         32-bit word -> U(0,1) on the dyadic grid (2j+1) 2^-24.
+ *   ora_su_uniform_corr the correlated (event-occurrence) uniform of an occurrence.
+ *   ora_norm_cdf        Phi of paper §3.2 step 5, (1/2) erfc(-x / sqrt 2).
+ *   ora_norm_quantile   Phi^-1 of paper §3.2 step 2 (reading G1): bracketed Newton on ln Phi.
+ *   ora_su_combine      paper §3.2 steps 1-5: the uniform fed to the beta inversion.
  *   ora_betainc         regularised incomplete beta I_x(a,b), the ratio B(x;a,b)/B(a,b) of
  *                       paper §3.3; continued fraction DLMF 8.17.22 by the modified Lentz method.
  *   ora_betaincinv      its functional inverse (paper §3.3, InvCDF_beta): safeguarded Newton.
@@ -33,6 +37,10 @@
  *   - with a single standard deviation per record (sigma_C = 0) the combination of paper §3.2
  *     returns the program/occurrence uniform unchanged, so that uniform is used directly; it is
  *     drawn by Philox keyed by (trial, event position, ELT handle);
+ *   - with sigma_C > 0 (paper §3.1-3.2): z_(Prog,E) is that per-(trial, event position, ELT)
+ *     uniform and z_(E), "the same across programs" for an event occurrence, is one uniform per
+ *     (trial, event position) shared by every ELT and layer; sigma = sigma_I + sigma_C feeds the
+ *     beta moments;
  *   - PML(RP) is the k-th largest year loss and TVaR(RP) the mean of the k largest, k = N/RP
  *     (ceil when N/RP is not an integer); ties are ordered by ascending trial index.
  */
@@ -113,6 +121,72 @@ ORA_API double ora_su_uniform(uint64_t seed, int64_t trial, int64_t k, int32_t e
   key[1] = (uint32_t)(seed >> 32);
   ora_philox4x32_10(ctr, key, out);
   return ora_uniform(out[elt & 3]);
+}
+
+/* The correlated (event-occurrence) uniform of occurrence k of trial i, shared by every ELT
+ * and every layer: counter (k, i_lo, 0xFFFFFFFF, i_hi), which no ELT handle's group reaches,
+ * key (seed_lo, seed_hi), output word 0. */
+ORA_API double ora_su_uniform_corr(uint64_t seed, int64_t trial, int64_t k) {
+  uint32_t ctr[4], key[2], out[4];
+  ctr[0] = (uint32_t)k;
+  ctr[1] = (uint32_t)((uint64_t)trial & 0xFFFFFFFFu);
+  ctr[2] = 0xFFFFFFFFu;
+  ctr[3] = (uint32_t)((uint64_t)trial >> 32);
+  key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
+  key[1] = (uint32_t)(seed >> 32);
+  ora_philox4x32_10(ctr, key, out);
+  return ora_uniform(out[0]);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Standard normal distribution, paper §3.2 (steps 2 and 5).                                  */
+/* ------------------------------------------------------------------------------------------ */
+/* Phi(x) = (1/2) erfc(-x / sqrt 2). */
+static const double kSqrtHalf = 0.70710678118654752440;  /* 1/sqrt(2) */
+static const double kSqrt2Pi = 2.50662827463100050242;   /* sqrt(2 pi) */
+ORA_API double ora_norm_cdf(double x) { return 0.5 * erfc(-x * kSqrtHalf); }
+
+/* Phi^-1(p): the x with Phi(x) = p (reading G1: step 2 maps a uniform to a normal).  The upper
+ * tail y > 0 with Phi(-y) = q = min(p, 1 - p) is solved by Newton's method on
+ * h(y) = ln Phi(-y) - ln q (h' = -phi(y) / Phi(-y)), kept inside a bracket [lo, hi] and replaced by
+ * bisection whenever a step would leave it; start y = sqrt(-2 ln q) - 1, clipped to the bracket. */
+ORA_API double ora_norm_quantile(double p) {
+  if (!(p > 0.0)) return -INFINITY;
+  if (!(p < 1.0)) return INFINITY;
+  if (p == 0.5) return 0.0;
+  const double q = p < 0.5 ? p : 1.0 - p;
+  const double lnq = log(q);
+  const double t = sqrt(-2.0 * lnq);
+  double lo = 0.0, hi = t + 1.0; /* Phi(-y) < phi(y)/y gives the root below sqrt(-2 ln q) + 1 */
+  double y = fmax(t - 1.0, 0.0);
+  for (int it = 0; it < 200; ++it) {
+    const double c = 0.5 * erfc(y * kSqrtHalf); /* Phi(-y) */
+    const double h = log(c) - lnq;
+    if (h > 0.0) lo = y; else hi = y;           /* h decreases in y */
+    const double dens = exp(-0.5 * y * y) / kSqrt2Pi;
+    double yn = y + h * c / dens;
+    if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+    if (fabs(yn - y) <= 4.0 * DBL_EPSILON * fmax(1.0, yn)) { y = yn; break; }
+    y = yn;
+  }
+  return p < 0.5 ? -y : y;
+}
+
+/* Paper §3.2: the uniform z that the beta inversion receives, from the independent (program-and-
+ * occurrence) uniform zp and the correlated (occurrence) uniform ze of a record with independent
+ * and correlated standard deviations sd_i, sd_c:
+ *   sigma = sd_i + sd_c (step 1); vp = Phi^-1(zp), ve = Phi^-1(ze) (step 2);
+ *   LC = vp sd_i/sigma + ve sd_c/sigma (step 3); v = LC / sqrt((sd_i/sigma)^2 + (sd_c/sigma)^2)
+ *   (step 4); z = Phi(v) (step 5).
+ * With sd_c = 0 the steps give Phi(Phi^-1(zp)) = zp, which is returned exactly. */
+ORA_API double ora_su_combine(double zp, double ze, double sd_i, double sd_c) {
+  if (sd_c == 0.0) return zp;
+  const double sigma = sd_i + sd_c;
+  const double wi = sd_i / sigma, wc = sd_c / sigma;
+  const double vp = ora_norm_quantile(zp), ve = ora_norm_quantile(ze);
+  const double lc = vp * wi + ve * wc;
+  const double v = lc / sqrt(wi * wi + wc * wc);
+  return ora_norm_cdf(v);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -349,7 +423,8 @@ typedef struct {
 
 static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t n_elts,
                     const int64_t *elt_off, const int32_t *ids, const double *mean,
-                    const double *sd, const double *mx, const int32_t *elt_handle,
+                    const double *sd, const double *sdc, const double *mx,
+                    const int32_t *elt_handle,
                     const double *terms, uint64_t seed, const int64_t *trials, int64_t n_sel,
                     double *ylt, ora_hit *hits, int64_t max_hits, int64_t *n_hits,
                     int64_t *not_conv, int n_threads) {
@@ -379,13 +454,16 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
           int64_t g = elt_off[j] + r;
           double u = ora_su_uniform(seed, i, k, elt_handle[j]);
           int st = 0;
-          double loss = ora_su_loss(mean[g], sd[g], mx[g], u, &st);
+          /* paper §3.2: independent SD sd, correlated SD sdc (0 when not given) */
+          const double sc = sdc ? sdc[g] : 0.0;
+          if (sc > 0.0) u = ora_su_combine(u, ora_su_uniform_corr(seed, i, k), sd[g], sc);
+          double loss = ora_su_loss(mean[g], sd[g] + sc, mx[g], u, &st);
           if (st == 1) nc += 1;
           l += loss;
           if (hits && nh < max_hits) {
             ora_hit *h = &hits[nh];
             h->trial = i; h->k = k; h->rec = r; h->j = j; h->u = u;
-            h->x = (sd[g] == 0.0) ? NAN : loss / mx[g];
+            h->x = (sd[g] + sc == 0.0) ? NAN : loss / mx[g];
             h->loss = loss;
           }
           if (hits) nh++;
@@ -404,19 +482,21 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
 
 ORA_API int ora_run(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t n_elts,
                     const int64_t *elt_off, const int32_t *ids, const double *mean,
-                    const double *sd, const double *mx, const int32_t *elt_handle,
-                    const double *terms, uint64_t seed, const int64_t *trials, int64_t n_sel,
-                    double *ylt, int64_t *not_conv, int n_threads) {
-  return run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, mx, elt_handle, terms,
-                  seed, trials, n_sel, ylt, NULL, 0, NULL, not_conv, n_threads);
+                    const double *sd, const double *sdc, const double *mx,
+                    const int32_t *elt_handle, const double *terms, uint64_t seed,
+                    const int64_t *trials, int64_t n_sel, double *ylt, int64_t *not_conv,
+                    int n_threads) {
+  return run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
+                  terms, seed, trials, n_sel, ylt, NULL, 0, NULL, not_conv, n_threads);
 }
 
 /* Same loop, single-threaded, additionally listing every hit (trial, event position k, layer
- * slot j, record index r in the caller's ELT order, uniform u, beta quantile x, loss) in loop
- * order; at most max_hits are written, the total is returned in *n_hits. */
+ * slot j, record index r in the caller's ELT order, the uniform z the inversion received, beta
+ * quantile x, loss) in loop order; at most max_hits are written, the total is in *n_hits. */
 ORA_API int ora_trace(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t n_elts,
                       const int64_t *elt_off, const int32_t *ids, const double *mean,
-                      const double *sd, const double *mx, const int32_t *elt_handle,
+                      const double *sd, const double *sdc, const double *mx,
+                      const int32_t *elt_handle,
                       const double *terms, uint64_t seed, const int64_t *trials, int64_t n_sel,
                       double *ylt, int64_t max_hits, int64_t *hit_trial, int64_t *hit_k,
                       int32_t *hit_j, int64_t *hit_rec, double *hit_u, double *hit_x,
@@ -424,8 +504,8 @@ ORA_API int ora_trace(const int64_t *yet_offsets, const int32_t *yet_ids, int32_
   ora_hit *hits = (ora_hit *)malloc(sizeof(ora_hit) * (size_t)(max_hits > 0 ? max_hits : 1));
   if (!hits) return -1;
   int64_t nh = 0, nc = 0;
-  int rc = run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, mx, elt_handle, terms,
-                    seed, trials, n_sel, ylt, hits, max_hits, &nh, &nc, 1);
+  int rc = run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
+                    terms, seed, trials, n_sel, ylt, hits, max_hits, &nh, &nc, 1);
   int64_t w = nh < max_hits ? nh : max_hits;
   for (int64_t h = 0; h < w; ++h) {
     hit_trial[h] = hits[h].trial; hit_k[h] = hits[h].k; hit_j[h] = hits[h].j;

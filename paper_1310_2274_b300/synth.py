@@ -52,8 +52,9 @@ class Elt:
 
     event_ids: np.ndarray  # int32 [n], distinct
     mean: np.ndarray  # float64 [n], values exactly representable in float32
-    sd: np.ndarray  # float64 [n]
+    sd: np.ndarray  # float64 [n]; the independent SD sigma_I when sd_corr is given
     max_exposure: np.ndarray  # float64 [n]
+    sd_corr: np.ndarray = None  # float64 [n], correlated SD sigma_C (paper §3.1); None: zero
 
     @property
     def n(self) -> int:
@@ -128,6 +129,16 @@ def make_elt(n: int, catalog: int, seed: int, *, mu: float = 12.0, sigma: float 
     return Elt(ids, mean, sd, mx)
 
 
+def split_sd(elt: Elt, seed: int, lo: float = 0.2, hi: float = 0.8) -> Elt:
+    """The same ELT with each record's SD split into independent and correlated parts (paper
+    §3.1): sigma_C = f32(sd U(1 - hi, 1 - lo)), sigma_I = f32(sd - sigma_C), so sigma_I + sigma_C
+    stays within rounding of the original SD."""
+    rng = np.random.default_rng([seed, 0xC0])
+    sdc = _f32(elt.sd * (1.0 - rng.uniform(lo, hi, size=elt.n)))
+    sdi = _f32(elt.sd - sdc)
+    return Elt(elt.event_ids, elt.mean, sdi, elt.max_exposure, sdc)
+
+
 def elt_size_for_seed(seed: int, lo: int = 20_000, hi: int = 200_000) -> int:
     """Record count of a paper-scale ELT: U{lo..hi} drawn from its own seed."""
     return int(np.random.default_rng([seed, 0x51E]).integers(lo, hi + 1))
@@ -165,6 +176,15 @@ def tiny(n_trials: int = 1000) -> Workload:
     yet = make_yet(n_trials, 100, 10_000, seed=1)
     elt = make_elt(2_000, 10_000, seed=2)
     return Workload("tiny-1000x100x1", yet, [elt], TERMS_TINY, RPS_TINY)
+
+
+def correlated(n_trials: int = 1000) -> Workload:
+    """Paper §3.1-3.2 with both standard deviations: 1,000 trials x 100 events over a 10,000-event
+    catalogue, three ELTs of 2,000 records whose SDs are split into independent and correlated
+    parts, so that one occurrence's losses in the three ELTs are correlated."""
+    yet = make_yet(n_trials, 100, 10_000, seed=1)
+    elts = [split_sd(make_elt(2_000, 10_000, seed=s), seed=s) for s in (2, 3, 4)]
+    return Workload(f"correlated-{n_trials}x100x3", yet, elts, Terms(1e5, 1e7, 1e6, 1e8), RPS_TINY)
 
 
 def paper_elts(n_elts: int = 16, catalog: int = 2_000_000, first_seed: int = 2) -> list:
