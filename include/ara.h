@@ -124,6 +124,17 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
 ARA_API ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
                                const double* mean, const double* sd, const double* max_exposure,
                                int32_t* elt_out);
+/* The same with the two standard deviations of paper §3.1: sd_indep (sigma_I) and sd_corr
+ * (sigma_C, NULL = all zero), both >= 0.  sigma = sigma_I + sigma_C feeds the moments (§3.2 step
+ * 1).  A hit's uniform follows §3.2 steps 2-5: the hit's own Philox uniform above plays
+ * z_(Prog,E); z_(E), the same for every ELT and every layer, is one Philox uniform per (trial,
+ * event position), counter (k, i_lo, 0xFFFFFFFF, i_hi), word 0; v = sqrt(1 - c^2) Phi^-1(z_P) +
+ * c Phi^-1(z_E) with c = (sigma_C/sigma) / |(sigma_I, sigma_C)/sigma|, and z = Phi(v) is inverted
+ * (Phi and Phi^-1 in binary32).  sigma_C = 0 gives z = z_P exactly, as ara_add_elt. */
+ARA_API ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
+                                    const double* mean, const double* sd_indep,
+                                    const double* sd_corr, const double* max_exposure,
+                                    int32_t* elt_out);
 ARA_API ara_status ara_free_elt(ara_ctx* ctx, int32_t elt);
 
 /* Layer (paper §2.1: XELT set plus terms (OccR, OccL, AggR, AggL)) ----------------------------

@@ -101,6 +101,7 @@ _SIGNATURES = {
     "ara_create_yet": ([_P, _I64, _P, _P, _P, _I32, C.POINTER(_I32)], C.c_int),
     "ara_free_yet": ([_P, _I32], C.c_int),
     "ara_add_elt": ([_P, _I32, _I64, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
+    "ara_add_elt_corr": ([_P, _I32, _I64, _P, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
     "ara_free_elt": ([_P, _I32], C.c_int),
     "ara_add_layer": ([_P, _P, _I32, _D, _D, _D, _D, C.POINTER(_I32)], C.c_int),
     "ara_free_layer": ([_P, _I32], C.c_int),
@@ -257,14 +258,22 @@ class Context:
                                          int(catalog_size), C.byref(out)))
         return out.value
 
-    def add_elt(self, yet: int, event_ids, mean, sd, max_exposure) -> int:
+    def add_elt(self, yet: int, event_ids, mean, sd, max_exposure, sd_corr=None) -> int:
+        """Stage an ELT; sd is the independent SD sigma_I and sd_corr (optional) the correlated
+        SD sigma_C of paper §3.1."""
         ids = _np(event_ids, np.int32)
         mu = _np(mean, np.float64)
         s = _np(sd, np.float64)
         mx = _np(max_exposure, np.float64)
         out = _I32(-1)
-        self._check(lib().ara_add_elt(self._h, yet, int(ids.shape[0]), _ptr(ids), _ptr(mu),
-                                      _ptr(s), _ptr(mx), C.byref(out)))
+        if sd_corr is None:
+            self._check(lib().ara_add_elt(self._h, yet, int(ids.shape[0]), _ptr(ids), _ptr(mu),
+                                          _ptr(s), _ptr(mx), C.byref(out)))
+        else:
+            sc = _np(sd_corr, np.float64)
+            self._check(lib().ara_add_elt_corr(self._h, yet, int(ids.shape[0]), _ptr(ids),
+                                               _ptr(mu), _ptr(s), _ptr(sc), _ptr(mx),
+                                               C.byref(out)))
         return out.value
 
     def add_layer(self, elts, occ_ret: float, occ_lim: float, agg_ret: float,
@@ -397,7 +406,8 @@ class Context:
         """Stage a synth.Workload: returns (yet, [elt handles], layer)."""
         yet = self.create_yet(w.yet.offsets, w.yet.event_ids, w.yet.timestamps,
                               w.yet.catalog_size)
-        elts = [self.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in w.elts]
+        elts = [self.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure,
+                             getattr(e, "sd_corr", None)) for e in w.elts]
         t = w.terms
         layer = self.add_layer(elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
         return yet, elts, layer

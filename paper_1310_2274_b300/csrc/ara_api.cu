@@ -101,6 +101,7 @@ void free_elt(EltDev& e) {
   dev_free(e.ids);
   dev_free(e.recs);
   dev_free(e.tables);
+  dev_free(e.corr);
   e = EltDev();
 }
 
@@ -178,6 +179,7 @@ void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st) {
   mem_free(l.tables, ordered, st);
   mem_free(l.packed, ordered, st);
   mem_free(l.packed_rec, ordered, st);
+  mem_free(l.corr, ordered, st);
   l = LayerDev();
 }
 
@@ -398,9 +400,10 @@ ara_status ara_free_yet(ara_ctx* ctx, int32_t yet) {
 }
 
 // ---- ELT ------------------------------------------------------------------------------------
-ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
-                       const double* mean, const double* sd, const double* max_exposure,
-                       int32_t* elt_out) {
+ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
+                            const double* mean, const double* sd_indep, const double* sd_corr,
+                            const double* max_exposure, int32_t* elt_out) {
+  const double* sd = sd_indep;
   if (!ctx) return ARA_ERR_INVALID_ARG;
   if (!elt_out) return fail(ctx, ARA_ERR_INVALID_ARG, "elt_out is NULL");
   if (yet < 0 || yet >= (int32_t)ctx->yets.size() || !ctx->yets[yet].live)
@@ -414,7 +417,7 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
   EltDev e;
   e.yet = yet;
   e.n = n;
-  double *d_mean = nullptr, *d_sd = nullptr, *d_mx = nullptr;
+  double *d_mean = nullptr, *d_sd = nullptr, *d_sdc = nullptr, *d_mx = nullptr;
   unsigned int* d_dup = nullptr;
   unsigned long long* d_uncert = nullptr;
   double2* d_ab64 = nullptr;
@@ -424,6 +427,7 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
     cudaStreamSynchronize(ctx->stream);
     dev_free(d_mean);
     dev_free(d_sd);
+    dev_free(d_sdc);
     dev_free(d_mx);
     dev_free(d_dup);
     dev_free(d_uncert);
@@ -433,7 +437,9 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
       (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess ||
       (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
       (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess ||
-      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess || (err = dev_alloc(&d_ab64, n)) != cudaSuccess) {
+      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess || (err = dev_alloc(&d_ab64, n)) != cudaSuccess ||
+      (sd_corr && ((err = dev_alloc(&d_sdc, n)) != cudaSuccess ||
+                   (err = dev_alloc(&e.corr, n)) != cudaSuccess))) {
     cudaGetLastError();
     cleanup();
     free_elt(e);
@@ -443,11 +449,12 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
   if ((err = copy_in(e.ids, event_ids, n, ctx->stream)) != cudaSuccess ||
       (err = copy_in(d_mean, mean, n, ctx->stream)) != cudaSuccess ||
       (err = copy_in(d_sd, sd, n, ctx->stream)) != cudaSuccess ||
+      (sd_corr && (err = copy_in(d_sdc, sd_corr, n, ctx->stream)) != cudaSuccess) ||
       (err = copy_in(d_mx, max_exposure, n, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
-      (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_mx, y.catalog, e.recs, d_ab64, d_dup,
-                                ctx->d_flags, ctx->stream)) != cudaSuccess ||
+      (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_sdc, d_mx, y.catalog, e.recs, d_ab64,
+                                e.corr, d_dup, ctx->d_flags, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
       (err = launch_build_tables(n, e.recs, d_ab64, e.tables, d_uncert, ctx->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
@@ -465,7 +472,7 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
     free_elt(e);
     return fail(ctx, ARA_ERR_INVALID_ARG, "ELT rejected:%s%s%s%s",
                 (flags & 8) ? " event id outside the catalogue" : "",
-                (flags & 16) ? " mean <= 0, sd < 0 or non-finite value" : "",
+                (flags & 16) ? " mean <= 0, an sd < 0 or non-finite value" : "",
                 (flags & 32) ? " max_exposure <= mean with sd > 0" : "",
                 (flags & 64) ? " duplicate event id" : "");
   }
@@ -474,6 +481,12 @@ ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* even
   ctx->elts.push_back(e);
   *elt_out = (int32_t)ctx->elts.size() - 1;
   return ARA_OK;
+}
+
+ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
+                       const double* mean, const double* sd, const double* max_exposure,
+                       int32_t* elt_out) {
+  return ara_add_elt_corr(ctx, yet, n, event_ids, mean, sd, nullptr, max_exposure, elt_out);
 }
 
 ara_status ara_free_elt(ara_ctx* ctx, int32_t elt) {
@@ -565,12 +578,16 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     return fail(ctx, ARA_ERR_CUDA, "layer index: %s", cudaGetErrorString(err));
   }
   L.n_packed = (int64_t)last[0] + (int64_t)last[1];
-  // packed records, then the records' tables copied into packed order (one gather per hit)
+  // packed records, then the records' tables copied into packed order (one gather per hit);
+  // correlated weights only when some ELT of the layer has a correlated SD
   const TablePiece** d_src = nullptr;
+  bool has_corr = false;
+  for (int j = 0; j < n_elts; ++j) has_corr = has_corr || ctx->elts[elts[j]].corr != nullptr;
   if ((err = mem_alloc(&L.packed, L.n_packed, ordered, st)) != cudaSuccess ||
       (err = mem_alloc(&L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
       (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) != cudaSuccess ||
-      (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess) {
+      (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess ||
+      (has_corr && (err = mem_alloc(&L.corr, L.n_packed, ordered, st)) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
     mem_free(d_src, ordered, st);
@@ -579,7 +596,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
-                               st);
+                               L.corr, st);
   if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   cleanup();
@@ -700,6 +717,7 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   p.evt = L.evt;
   p.recs = L.packed;
   p.tables = L.tables;
+  p.corr = L.corr;
   p.rec_idx = L.packed_rec;
   for (int j = 0; j < kMaxLayerElts; ++j) p.handles[j] = L.handles[j];
   p.n_slots = L.n_slots;

@@ -230,9 +230,13 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
         }
         const uint32_t pos = sm.base[ev] + (uint32_t)nth;
         const int64_t trial = P.t0 + i_rel0 + sm.t[ev];
-        const float u = su_uniform_rk(P.rk0, P.rk1, trial, sm.k[ev], P.handles[slot]);
+        const float u0 = su_uniform_rk(P.rk0, P.rk1, trial, sm.k[ev], P.handles[slot]);
+        const float cc = P.corr != nullptr ? __ldg(P.corr + pos) : 0.0f;
+        const SuDraw d =
+            su_draw(u0, cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, sm.k[ev]) : 0.5f, cc);
+        const float u = d.z;
         float tau;
-        const int kp = ara_table_piece(u, &tau);
+        const int kp = ara_table_piece_q(d.lower, d.q, &tau);
         const TablePiece pc = ara_load_piece<true>(P.tables + (size_t)pos * kTablePieces, kp);
         if (pc.flag == kPieceTable) {
           loss = pc.mx * ara_piece_x(pc, tau);

@@ -270,12 +270,11 @@ ARA_HD float ara_exp2_fast(float r) {
 #endif
 }
 
-// Piece index and local coordinate of uniform u.  ln q comes from the hardware base-2 logarithm
+// Piece index and local coordinate of the uniform whose tail side is `lower` and whose tail
+// probability is q = min(z, 1 - z).  ln q comes from the hardware base-2 logarithm
 // (relative error about 2^-22 for q <= 1/2), which moves z by at most ~3e-7: well inside a
 // piece, and the quantile's log-odds by L'(z) times that.
-ARA_HD int ara_table_piece(float u, float* tau) {
-  const bool lower = u < 0.5f;
-  const float q = lower ? u : 1.0f - u;  // exact on the uniform grid
+ARA_HD int ara_table_piece_q(bool lower, float q, float* tau) {
 #ifdef __CUDA_ARCH__
   const float t = sqrtf(-1.38629436f * __log2f(q));  // -2 ln q = -2 ln 2 log2 q
 #else
@@ -286,6 +285,12 @@ ARA_HD int ara_table_piece(float u, float* tau) {
   const int k = pos < (float)(kTablePieces - 1) ? (int)pos : kTablePieces - 1;
   *tau = pos - (float)k;
   return k;
+}
+
+// The same from the uniform u itself (q = min(u, 1 - u), exact on the uniform grid).
+ARA_HD int ara_table_piece(float u, float* tau) {
+  const bool lower = u < 0.5f;
+  return ara_table_piece_q(lower, lower ? u : 1.0f - u, tau);
 }
 
 // One 32-byte load of piece k of the record whose table starts at rec.  KEEP chooses the L2

@@ -50,6 +50,7 @@ struct EltDev {
   int32_t* ids = nullptr;    // [n]
   BetaRec* recs = nullptr;   // [n]
   TablePiece* tables = nullptr;  // [n * kTablePieces] certified quantile tables
+  float* corr = nullptr;     // [n] normalised correlated weights (NULL: every sigma_C = 0)
   int64_t n_uncertified = 0; // records whose table failed certification
 };
 
@@ -67,6 +68,7 @@ struct LayerDev {
   BetaRec* packed = nullptr;       // [n_packed]
   TablePiece* tables = nullptr;    // [n_packed * kTablePieces] the records' tables, same order
   uint32_t* packed_rec = nullptr;  // [n_packed] caller record index (verification)
+  float* corr = nullptr;           // [n_packed] correlated weights (NULL: none in the layer)
   int64_t n_packed = 0;
   int32_t band_log2w = 0;          // band width of the band-major schedule (0: trial-major only)
 };
@@ -78,6 +80,7 @@ struct TrialParams {
   const uint32_t* evt;
   const BetaRec* recs;
   const TablePiece* tables;  // the layer's tables, kTablePieces per packed record
+  const float* corr;         // packed correlated weights (paper §3.2), NULL when all are zero
   const uint32_t* rec_idx;
   int32_t handles[kMaxLayerElts];
   int32_t n_slots;
@@ -125,9 +128,9 @@ int64_t launches_so_far();
 // ---- launchers (each returns the launch's cudaError_t) ---------------------------------------
 cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st);
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
-                               const double* sd, const double* mx, int32_t catalog,
-                               BetaRec* recs, double2* ab64, unsigned int* d_dup,
-                               unsigned int* d_flags, cudaStream_t st);
+                               const double* sd, const double* sdc, const double* mx,
+                               int32_t catalog, BetaRec* recs, double2* ab64, float* corr,
+                               unsigned int* d_dup, unsigned int* d_flags, cudaStream_t st);
 cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
                               cudaStream_t st);
 cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,
@@ -140,7 +143,7 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
-                                 cudaStream_t st);
+                                 float* packed_corr, cudaStream_t st);
 // ab64[n]: each record's (alpha, beta) in binary64, as written by launch_prepare_elt.
 cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
                                 TablePiece* tables, unsigned long long* d_uncertified,

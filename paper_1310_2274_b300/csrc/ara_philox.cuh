@@ -99,4 +99,17 @@ __device__ __forceinline__ float su_uniform_rk(const uint32_t* rk0, const uint32
   return word_to_uniform(w);
 }
 
+// The correlated (event-occurrence) uniform of occurrence k of trial i, shared by every ELT and
+// layer (paper §3.1, z_(E)): counter (k, i_lo, 0xFFFFFFFF, i_hi), a group no ELT handle reaches,
+// output word 0.
+__device__ __forceinline__ float su_uniform_corr_rk(const uint32_t* rk0, const uint32_t* rk1,
+                                                    int64_t trial, uint32_t k) {
+  U4 c;
+  c.x = k;
+  c.y = (uint32_t)((uint64_t)trial & 0xFFFFFFFFu);
+  c.z = 0xFFFFFFFFu;
+  c.w = (uint32_t)((uint64_t)trial >> 32);
+  return word_to_uniform(philox4x32_10_rk(c, rk0, rk1).x);
+}
+
 }  // namespace ara

@@ -59,12 +59,15 @@ __device__ double betainc_f64(double a, double b, double x) {
   return exp(ara_ln_betainc_f64(a, b, log(x), lnB));
 }
 
-// flags bit 3: id out of range; bit 4: mean <= 0 or sd < 0 or non-finite; bit 5: max <= mean
+// flags bit 3: id out of range; bit 4: mean <= 0 or an SD < 0 or non-finite; bit 5: max <= mean
 // with sd > 0; dup[e] counts records per event (a count above one is a duplicate, bit 6).
+// sdc (NULL: zero) is the correlated SD of paper §3.1: sigma = sd + sdc feeds the moments and
+// corr[r] receives the normalised correlated weight of §3.2, (sdc/sigma) / |(sd, sdc)/sigma|.
 __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
                                    const double* __restrict__ mean, const double* __restrict__ sd,
-                                   const double* __restrict__ mx, int32_t catalog,
-                                   BetaRec* __restrict__ recs, double2* __restrict__ ab64,
+                                   const double* __restrict__ sdc, const double* __restrict__ mx,
+                                   int32_t catalog, BetaRec* __restrict__ recs,
+                                   double2* __restrict__ ab64, float* __restrict__ corr,
                                    unsigned int* dup, unsigned int* flags) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -75,7 +78,13 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
   } else if (atomicAdd(&dup[e], 1u) != 0u) {
     f |= 64u;
   }
-  const double mu = mean[r], sigma = sd[r], m = mx[r];
+  const double sd_i = sd[r], sd_c = sdc ? sdc[r] : 0.0;
+  const double mu = mean[r], sigma = sd_i + sd_c, m = mx[r];
+  if (corr) {  // paper §3.2 steps 3-4: weights sd_i/sigma, sd_c/sigma, normalised
+    const double wi = sigma > 0.0 ? sd_i / sigma : 1.0, wc = sigma > 0.0 ? sd_c / sigma : 0.0;
+    corr[r] = (float)(wc / sqrt(wi * wi + wc * wc));
+  }
+  if (!(sd_i >= 0.0) || !(sd_c >= 0.0)) f |= 16u;
   BetaRec rec;
   rec.a = 0.f; rec.b = 0.f; rec.mx = (float)mu; rec.L0 = 0.f;
   rec.p0 = 0.5f; rec.lnx0 = 0.f; rec.lny0 = 0.f; rec.lns = 0.f;
@@ -150,7 +159,8 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
                                      const TablePiece* __restrict__ tables, int slot,
                                      int mask_words, const uint32_t* __restrict__ evt,
                                      BetaRec* packed, const TablePiece** table_src,
-                                     uint32_t* packed_rec) {
+                                     uint32_t* packed_rec, const float* __restrict__ corr,
+                                     float* packed_corr) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t e = ids[r];
@@ -167,6 +177,7 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
   }
   packed[base + rank] = recs[r];
   table_src[base + rank] = tables + r * kTablePieces;
+  if (packed_corr) packed_corr[base + rank] = corr ? corr[r] : 0.0f;
   packed_rec[base + rank] = (uint32_t)r;
 }
 
@@ -274,12 +285,12 @@ cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStre
 }
 
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
-                               const double* sd, const double* mx, int32_t catalog,
-                               BetaRec* recs, double2* ab64, unsigned int* d_dup,
-                               unsigned int* d_flags, cudaStream_t st) {
+                               const double* sd, const double* sdc, const double* mx,
+                               int32_t catalog, BetaRec* recs, double2* ab64, float* corr,
+                               unsigned int* d_dup, unsigned int* d_flags, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, mx, catalog, recs, ab64,
-                                                       d_dup, d_flags);
+  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, sdc, mx, catalog, recs,
+                                                       ab64, corr, d_dup, d_flags);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -324,11 +335,11 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
-                                 cudaStream_t st) {
+                                 float* packed_corr, cudaStream_t st) {
   if (e.n == 0) return cudaSuccess;
   layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, e.tables, slot,
                                                            mask_words, d_evt, packed, table_src,
-                                                           packed_rec);
+                                                           packed_rec, e.corr, packed_corr);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -151,10 +151,14 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
         bool sd0 = false, use_table = false;
         TablePiece pc;
         float tau = 0.f;
+        const float cc = P.corr != nullptr ? __ldg(P.corr + pos) : 0.0f;
         if constexpr (TABLE) {
-          // the piece index depends on u alone: draw first, then one 32-byte load
-          u = su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]);
-          const int kp = ara_table_piece(u, &tau);
+          // the piece index depends on the draw alone: draw first, then one 32-byte load
+          const SuDraw d = su_draw(su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]),
+                                   cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, k) : 0.5f,
+                                   cc);
+          u = d.z;
+          const int kp = ara_table_piece_q(d.lower, d.q, &tau);
           pc = ara_load_piece<false>(P.tables + (size_t)pos * kTablePieces, kp);
           sd0 = pc.flag == kPieceMean;
           mx = pc.mx;
@@ -165,7 +169,9 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
           rec = load_rec(P.recs + pos);
           sd0 = !(rec.a > 0.f);
           mx = rec.mx;
-          if (!sd0 || TRACE) u = su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]);
+          if (!sd0 || TRACE)
+            u = su_draw(su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]),
+                        cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, k) : 0.5f, cc).z;
         }
         if constexpr (SURR) {
           // the network serves this hit if (alpha, beta) lies in its box and the certified error

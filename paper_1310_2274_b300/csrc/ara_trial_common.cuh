@@ -134,6 +134,30 @@ struct Entry<2> {
   __device__ int count() const { return __popc(m0) + __popc(m1); }
 };
 
+// The uniform a hit's inversion receives (paper §3.2).  u is the hit's own uniform (z_(Prog,E));
+// with a correlated weight cc > 0 the occurrence's shared uniform uc (z_(E)) enters through
+// v = sqrt(1 - cc^2) Phi^-1(u) + cc Phi^-1(uc), z = Phi(v); the table receives the tail side and
+// q = Phi(-|v|), which keeps its precision where z is close to 1.  cc = 0 returns u itself.
+struct SuDraw {
+  bool lower;  // z < 1/2
+  float q;     // min(z, 1 - z)
+  float z;
+};
+__device__ __forceinline__ SuDraw su_draw(float u, float uc, float cc) {
+  SuDraw d;
+  if (!(cc > 0.0f)) {
+    d.lower = u < 0.5f;
+    d.q = d.lower ? u : 1.0f - u;
+    d.z = u;
+    return d;
+  }
+  const float v = sqrtf(fmaxf(1.0f - cc * cc, 0.0f)) * normcdfinvf(u) + cc * normcdfinvf(uc);
+  d.lower = v < 0.0f;
+  d.q = normcdff(-fabsf(v));
+  d.z = d.lower ? d.q : 1.0f - d.q;
+  return d;
+}
+
 // Bit position of the n-th (0-based) set bit of m (n < popc(m)).
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int n) { return (int)__fns(m, 0u, n + 1); }
 
