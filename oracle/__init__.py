@@ -59,7 +59,7 @@ def _declare(L):
     L.ora_su_combine.argtypes = [C.c_double] * 4
     L.ora_su_combine.restype = C.c_double
     L.ora_run.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
-                          C.c_int64, _P, C.POINTER(C.c_int64), C.c_int]
+                          C.c_int64, _P, _P, C.POINTER(C.c_int64), C.c_int]
     L.ora_run.restype = C.c_int
     L.ora_trace.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
                             C.c_int64, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
@@ -169,8 +169,10 @@ def _layer_arrays(elts, elt_handles):
     return off, ids, mean, sd, sdc, mx, h
 
 
-def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0):
-    """Year losses of the selected trials (all by default) -> (ylt float64, not_converged)."""
+def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0,
+        with_oep: bool = False):
+    """Year losses of the selected trials (all by default) -> (ylt float64, not_converged), or
+    (ylt, oep, not_converged) with with_oep: oep = each year's largest occurrence loss."""
     off, ids, mean, sd, sdc, mx, h = _layer_arrays(elts, elt_handles)
     t = np.ascontiguousarray(np.arange(yet.n_trials) if trials is None else trials,
                              dtype=np.int64)
@@ -178,13 +180,14 @@ def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0)
     yi = np.ascontiguousarray(yet.event_ids, dtype=np.int32)
     tr = np.array([terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim], dtype=np.float64)
     ylt = np.zeros(t.shape[0], dtype=np.float64)
+    oep = np.zeros(t.shape[0], dtype=np.float64)
     nc = C.c_int64(0)
     rc = lib().ora_run(_ptr(yo), _ptr(yi), len(elts), _ptr(off), _ptr(ids), _ptr(mean),
                        _ptr(sd), _ptr(sdc), _ptr(mx), _ptr(h), _ptr(tr), seed, _ptr(t), t.shape[0],
-                       _ptr(ylt), C.byref(nc), int(threads))
+                       _ptr(ylt), _ptr(oep) if with_oep else None, C.byref(nc), int(threads))
     if rc != 0:
         raise ValueError(f"oracle run failed: {rc}")
-    return ylt, nc.value
+    return (ylt, oep, nc.value) if with_oep else (ylt, nc.value)
 
 
 def trace(yet, elts, terms, seed, trials, elt_handles=None, max_hits: int = 1 << 22):

@@ -23,7 +23,8 @@
  *   ora_beta_moments    paper §3.3: sigma_beta, mu_beta, the sigma_beta_max clamp, alpha, beta.
  *   ora_occ_terms       paper §2.3 occurrence terms  min(max(l - OccR, 0), OccL).
  *   ora_agg_terms       paper §2.3 aggregate terms   min(max(S - AggR, 0), AggL).
- *   ora_run             Algorithm 1 for one layer over a list of trials -> YLT entries.
+ *   ora_run             Algorithm 1 for one layer over a list of trials -> YLT entries, and
+ *                       optionally each year's largest occurrence loss (OEP year table).
  *   ora_trace           the same loop, reporting every (trial, event, ELT) hit.
  *   ora_rank / ora_risk YLT order and PML / TVaR (paper §2.4).
  *
@@ -426,7 +427,8 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
                     const double *sd, const double *sdc, const double *mx,
                     const int32_t *elt_handle,
                     const double *terms, uint64_t seed, const int64_t *trials, int64_t n_sel,
-                    double *ylt, ora_hit *hits, int64_t max_hits, int64_t *n_hits,
+                    double *ylt, double *oep, ora_hit *hits, int64_t max_hits,
+                    int64_t *n_hits,
                     int64_t *not_conv, int n_threads) {
   ora_index *ix = (ora_index *)calloc((size_t)(n_elts > 0 ? n_elts : 1), sizeof(ora_index));
   if (!ix) return -1;
@@ -443,7 +445,8 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : nc) if (hits == NULL)
     for (int64_t s = 0; s < n_sel; ++s) {
       int64_t i = trials[s];
-      double S = 0.0; /* cumulative occurrence loss, paper §2.3 */
+      double S = 0.0;    /* cumulative occurrence loss, paper §2.3 */
+      double omax = 0.0; /* the year's largest occurrence loss (event-level output) */
       for (int64_t q = yet_offsets[i]; q < yet_offsets[i + 1]; ++q) {
         int64_t k = q - yet_offsets[i];
         int32_t e = yet_ids[q];
@@ -468,9 +471,12 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
           }
           if (hits) nh++;
         }
-        S += ora_occ_terms(l, terms[0], terms[1]);
+        const double o = ora_occ_terms(l, terms[0], terms[1]);
+        S += o;
+        if (o > omax) omax = o;
       }
       ylt[s] = ora_agg_terms(S, terms[2], terms[3]);
+      if (oep) oep[s] = omax;
     }
   }
   for (int32_t j = 0; j < n_elts; ++j) free_index(&ix[j]);
@@ -484,10 +490,10 @@ ORA_API int ora_run(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
                     const int64_t *elt_off, const int32_t *ids, const double *mean,
                     const double *sd, const double *sdc, const double *mx,
                     const int32_t *elt_handle, const double *terms, uint64_t seed,
-                    const int64_t *trials, int64_t n_sel, double *ylt, int64_t *not_conv,
-                    int n_threads) {
+                    const int64_t *trials, int64_t n_sel, double *ylt, double *oep,
+                    int64_t *not_conv, int n_threads) {
   return run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
-                  terms, seed, trials, n_sel, ylt, NULL, 0, NULL, not_conv, n_threads);
+                  terms, seed, trials, n_sel, ylt, oep, NULL, 0, NULL, not_conv, n_threads);
 }
 
 /* Same loop, single-threaded, additionally listing every hit (trial, event position k, layer
@@ -505,7 +511,7 @@ ORA_API int ora_trace(const int64_t *yet_offsets, const int32_t *yet_ids, int32_
   if (!hits) return -1;
   int64_t nh = 0, nc = 0;
   int rc = run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
-                    terms, seed, trials, n_sel, ylt, hits, max_hits, &nh, &nc, 1);
+                    terms, seed, trials, n_sel, ylt, NULL, hits, max_hits, &nh, &nc, 1);
   int64_t w = nh < max_hits ? nh : max_hits;
   for (int64_t h = 0; h < w; ++h) {
     hit_trial[h] = hits[h].trial; hit_k[h] = hits[h].k; hit_j[h] = hits[h].j;

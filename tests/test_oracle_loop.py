@@ -130,3 +130,47 @@ def test_duplicate_ids_rejected(oracle):
     elt = synth.Elt(np.array([3, 3], np.int32), np.ones(2), np.zeros(2), np.full(2, 4.0))
     with pytest.raises(ValueError):
         oracle.run(yet, [elt], synth.TERMS_TINY, 42)
+
+
+def test_oep_is_the_largest_occurrence_loss():
+    # event-level output: the year's largest occurrence loss, checked against a hand-rolled loop
+    # over the oracle's own per-hit trace (occurrence sums, then terms, then the maximum)
+    import oracle
+    from paper_1310_2274_b300 import synth
+
+    w = synth.tiny(60)
+    ylt, oep, nc = oracle.run(w.yet, w.elts, w.terms, 42, with_oep=True)
+    assert nc == 0
+    hits, y2 = oracle.trace(w.yet, w.elts, w.terms, 42, np.arange(60))
+    np.testing.assert_array_equal(ylt, y2)
+    for i in range(60):
+        sel = hits["trial"] == i
+        ks = np.unique(hits["k"][sel])
+        o = [min(max(hits["loss"][sel & (hits["k"] == k)].sum() - w.terms.occ_ret, 0.0),
+                 w.terms.occ_lim) for k in ks]
+        assert oep[i] == (max(o) if o else 0.0)
+    # the OEP year never exceeds the occurrence-summed year before aggregate terms
+    assert np.all(oep >= 0) and np.all(oep <= w.terms.occ_lim)
+
+
+def test_oep_against_the_aggregate_year_in_special_cases():
+    # with identity aggregate terms the largest occurrence loss never exceeds the year's sum, and a
+    # trial of one event has OEP = AEP; the OEP does not move with the aggregate terms
+    import oracle
+    from paper_1310_2274_b300 import synth
+
+    w = synth.tiny(200)
+    rng = np.random.default_rng(4)
+    lens = rng.choice([0, 1, 1, 2, 7, 40], size=300)
+    offsets = np.zeros(301, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    ids = rng.integers(0, w.yet.catalog_size, size=int(offsets[-1]), dtype=np.int32)
+    yet = synth.Yet(offsets, ids, np.zeros(ids.shape[0], np.float32), w.yet.catalog_size)
+    ident = synth.Terms(w.terms.occ_ret, w.terms.occ_lim, 0.0, np.inf)
+    ylt, oep, _ = oracle.run(yet, w.elts, ident, 42, with_oep=True)
+    assert np.all(oep <= ylt) and np.count_nonzero(oep) > 100
+    np.testing.assert_array_equal(oep[lens == 1], ylt[lens == 1])
+    assert np.all(oep[lens == 0] == 0.0)
+    assert np.any(oep[lens > 2] < ylt[lens > 2])
+    _, oep2, _ = oracle.run(yet, w.elts, w.terms, 42, with_oep=True)
+    np.testing.assert_array_equal(oep, oep2)
