@@ -157,6 +157,15 @@ ARA_API ara_status ara_free_layer(ara_ctx* ctx, int32_t layer);
  * the convergence count is read later with ara_not_converged(). */
 ARA_API ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
                            double* ylt, void* stream);
+/* Event-level output beside the aggregate one, in the same pass: as ara_run, and when oep is not
+ * NULL also oep[i] = max_k min(max(l_ik - OccR, 0), OccL) (0 for a year without occurrences),
+ * the year's largest occurrence loss after occurrence terms (the OEP year table; paper §2.1's
+ * occurrence terms applied per event, before the aggregate terms).  The maximum is taken over
+ * the binary32 occurrence results, so it is one of them exactly and does not depend on the
+ * schedule or on the trial range.  oep (binary64, n entries) must be the same kind of memory as
+ * ylt (both host or both device); ARA_ERR_INVALID_ARG otherwise. */
+ARA_API ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                              double* ylt, double* oep, void* stream);
 /* Inversions that hit the iteration cap since the context was created (blocks on its work). */
 ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
 /* Work counters accumulated by every ara_run since the context was created (blocks on its work):

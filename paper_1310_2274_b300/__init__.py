@@ -106,6 +106,7 @@ _SIGNATURES = {
     "ara_add_layer": ([_P, _P, _I32, _D, _D, _D, _D, C.POINTER(_I32)], C.c_int),
     "ara_free_layer": ([_P, _I32], C.c_int),
     "ara_run": ([_P, _I32, _I32, _I64, _I64, _P, _P], C.c_int),
+    "ara_run_ep": ([_P, _I32, _I32, _I64, _I64, _P, _P, _P], C.c_int),
     "ara_not_converged": ([_P, C.POINTER(_I64)], C.c_int),
     "ara_risk_measures": ([_P, _P, _I64, _P, _I32, _P, _P], C.c_int),
     "ara_rank_ylt": ([_P, _P, _I64, _P], C.c_int),
@@ -306,6 +307,24 @@ class Context:
         st = lib().ara_run(self._h, yet, layer, int(t0), int(n), _ptr(out), s)
         self._check(st, allow_not_converged)
         return out
+
+    def run_ep(self, yet: int, layer: int, t0: int, n: int, out=None, oep=None, stream=None,
+               allow_not_converged: bool = False):
+        """Year losses (AEP year table) and each year's largest occurrence loss (OEP year table)
+        of trials [t0, t0+n) from one pass -> (ylt, oep); out and oep both host or both CUDA."""
+        if out is None:
+            out = np.zeros(n, dtype=np.float64)
+        if oep is None and _is_cuda(out):
+            import torch
+            oep = torch.zeros(n, dtype=torch.float64, device=out.device)
+        elif oep is None:
+            oep = np.zeros(n, dtype=np.float64)
+        s = None
+        if stream is not None:
+            s = getattr(stream, "cuda_stream", stream)
+        st = lib().ara_run_ep(self._h, yet, layer, int(t0), int(n), _ptr(out), _ptr(oep), s)
+        self._check(st, allow_not_converged)
+        return out, oep
 
     # -- risk measures -------------------------------------------------------------------------
     def risk_measures(self, ylt, rps):

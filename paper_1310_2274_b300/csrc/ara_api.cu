@@ -756,8 +756,8 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
 
 extern "C" {
 
-ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n, double* ylt,
-                   void* stream) {
+ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                      double* ylt, double* oep, void* stream) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
   ara_status s = check_run_args(ctx, yet, layer, t0, n);
   if (s != ARA_OK) return s;
@@ -765,24 +765,31 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
   if (n == 0) return ARA_OK;
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const bool dev_out = is_device_ptr(ylt);
+  if (oep && is_device_ptr(oep) != dev_out)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "ylt and oep must both be host or both device memory");
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
   if (stream && !dev_out)
     return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need a device ylt");
   double* d_ylt = ylt;
+  double* d_oep = oep;
   if (!dev_out) {
-    s = ensure_ylt_tmp(ctx, n);
+    s = ensure_ylt_tmp(ctx, oep ? 2 * n : n);
     if (s != ARA_OK) return s;
     d_ylt = ctx->d_ylt_tmp;
+    d_oep = oep ? ctx->d_ylt_tmp + n : nullptr;
   }
   unsigned long long nc_before = 0;
   if (!stream)
     CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
                                   cudaMemcpyDeviceToHost, st));
   TrialParams p = make_params(ctx, ctx->yets[yet], ctx->layers[layer], t0, n, d_ylt);
+  p.oep = d_oep;
   if (uses_band_schedule(ctx, ctx->layers[layer])) {
-    s = ensure_ysum(ctx, n);
+    // year sums (8 B per trial), then the OEP maxima (4 B per trial) in the same scratch
+    s = ensure_ysum(ctx, oep ? n + (n + 1) / 2 : n);
     if (s != ARA_OK) return s;
     p.ysum = ctx->d_ysum;
+    p.omax = oep ? reinterpret_cast<unsigned int*>(ctx->d_ysum + n) : nullptr;
     CUDA_TRY(ctx, launch_band(p, ctx->layers[layer].mask_words, ctx->cfg.precision, st));
   } else {
     CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
@@ -791,6 +798,8 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
   if (stream) return ARA_OK;
   if (!dev_out)
     CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  if (!dev_out && oep)
+    CUDA_TRY(ctx, cudaMemcpyAsync(oep, d_oep, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
   unsigned long long nc_after = 0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
                                 cudaMemcpyDeviceToHost, st));
@@ -799,6 +808,11 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
     return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
                 nc_after - nc_before);
   return ARA_OK;
+}
+
+ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n, double* ylt,
+                   void* stream) {
+  return ara_run_ep(ctx, yet, layer, t0, n, ylt, nullptr, stream);
 }
 
 ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {

@@ -102,6 +102,7 @@ struct BandWarpSmem {
   uint8_t hitev[kHitCap];     // position of each of the chunk's hits (when they fit)
   uint32_t off[kT + 1];       // segment starts of the warp's trials in this band
   unsigned long long ys[kT];  // year-sum units gathered by the warp
+  unsigned int om[kT];        // bit patterns of the trials' largest occurrence losses in the band
 };
 
 __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, unsigned long long pol) {
@@ -123,11 +124,13 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
   if (lane < nt) {
     sm.off[lane] = __ldg(P.boff + orow + lane);
     sm.ys[lane] = 0ull;
+    sm.om[lane] = 0u;
   }
   if (lane == 0) sm.off[nt] = __ldg(P.boff + orow + nt);
   __syncwarp();
   const uint32_t beg = sm.off[0], end = sm.off[nt];
   const float qs = P.q_scale;
+  const bool want_oep = P.omax != nullptr;
   unsigned int nc = 0, n_inv = 0, n_it = 0, n_cf = 0, n_tab = 0, n_hit = 0;
 
   // the band words are streamed one chunk ahead, so their DRAM latency overlaps a chunk's hits
@@ -271,6 +274,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
     // ---- occurrence terms; exact year-sum units gathered per trial ----------------------------
     // lane l takes the chunk's positions 4l .. 4l+3, which mostly belong to one trial
     unsigned long long acc = 0;
+    float om = 0.f;
     int tc = -1;
 #pragma unroll
     for (int j = 0; j < kV; ++j) {
@@ -279,18 +283,28 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
         const int t = sm.t[p];
         const float o = fminf(fmaxf(sm.lsum[p] - P.occ_ret, 0.f), P.occ_lim);
         if (t != tc) {
-          if (tc >= 0) atomicAdd(&sm.ys[tc], acc);
+          if (tc >= 0) {
+            atomicAdd(&sm.ys[tc], acc);
+            if (want_oep && om > 0.f) atomicMax(&sm.om[tc], __float_as_uint(om));
+          }
           acc = 0;
+          om = 0.f;
           tc = t;
         }
         acc += AccExact::units(o, qs);
+        om = fmaxf(om, o);
       }
     }
-    if (tc >= 0) atomicAdd(&sm.ys[tc], acc);
+    if (tc >= 0) {
+      atomicAdd(&sm.ys[tc], acc);
+      if (want_oep && om > 0.f) atomicMax(&sm.om[tc], __float_as_uint(om));
+    }
     __syncwarp();
   }
 
   if (lane < nt && sm.ys[lane] != 0ull) atomicAdd(P.ysum + i_rel0 + lane, sm.ys[lane]);
+  // the maximum over bands: an integer maximum of non-negative binary32 patterns, order-free
+  if (want_oep && lane < nt && sm.om[lane] != 0u) atomicMax(P.omax + i_rel0 + lane, sm.om[lane]);
   // work counters, one striped atomic each
   nc = __reduce_add_sync(0xFFFFFFFFu, nc);
   n_inv = __reduce_add_sync(0xFFFFFFFFu, n_inv);
@@ -347,6 +361,7 @@ __global__ void __launch_bounds__(kBW * 32, 4)
 __device__ __forceinline__ void finalize_one(const TrialParams& P, int64_t i) {
   const double S = (double)P.ysum[i] * P.q_unit;
   P.ylt[i] = fmin(fmax(S - P.agg_ret, 0.0), P.agg_lim);
+  if (P.oep) P.oep[i] = (double)__uint_as_float(P.omax[i]);
 }
 
 __global__ void band_finalize_kernel(const __grid_constant__ TrialParams P) {
@@ -374,8 +389,13 @@ cudaError_t launch_band_t(const TrialParams& p0, cudaStream_t st) {
   const int64_t blocks = (int64_t)p.n_bands * p.tiles;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7FFFFFFFll) return cudaErrorInvalidConfiguration;
+  if ((p.oep == nullptr) != (p.omax == nullptr)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(p.ysum, 0, sizeof(unsigned long long) * (size_t)p.n, st);
   if (e != cudaSuccess) return e;
+  if (p.omax) {
+    e = cudaMemsetAsync(p.omax, 0, sizeof(unsigned int) * (size_t)p.n, st);
+    if (e != cudaSuccess) return e;
+  }
   band_kernel<MW><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
   count_launches(1);
   e = cudaGetLastError();

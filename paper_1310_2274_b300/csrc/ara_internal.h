@@ -114,6 +114,10 @@ struct TrialParams {
   // grid of the exact year sums: occurrence results are rounded to multiples of q_unit = 2^e
   float q_scale;             // 2^-e
   double q_unit;             // 2^e
+  // event-level output (optional): each year's largest occurrence loss, after occurrence terms
+  double* oep;               // [n] or null
+  unsigned int* omax;        // [n] binary32 bit patterns of the running maxima (band-major;
+                             //     zeroed first; non-negative floats order like their bits)
 };
 
 // Work counters are striped over kStatStripes copies (counter c of stripe s at

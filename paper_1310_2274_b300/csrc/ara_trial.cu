@@ -77,6 +77,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
 
   const L2Policies pol = L2Policies::make();
   Acc acc = Acc::make(P);
+  float omax = 0.f;  // the year's largest occurrence loss (event-level output)
   int32_t trace_n = 0;
   unsigned int nc = 0;
   unsigned int n_inv = 0, n_it = 0, n_cf = 0, n_hit = 0, n_tab = 0, n_net = 0;
@@ -252,12 +253,15 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
         const float l = lsum[v * 32 + lane];
         const float o = fminf(fmaxf(l - P.occ_ret, 0.f), P.occ_lim);
         acc.add(o);
+        omax = fmaxf(omax, o);
       }
     }
     __syncwarp();
   }
 
   acc.warp_reduce();
+  // o >= +0 always, so the largest float is the largest bit pattern
+  const unsigned om_bits = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(omax));
   nc = __reduce_add_sync(0xFFFFFFFFu, nc);
   n_inv = __reduce_add_sync(0xFFFFFFFFu, n_inv);
   n_it = __reduce_add_sync(0xFFFFFFFFu, n_it);
@@ -267,6 +271,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
   if (lane == 0) {
     const double S = acc.value();
     P.ylt[w] = fmin(fmax(S - P.agg_ret, 0.0), P.agg_lim);
+    if (P.oep) P.oep[w] = (double)__uint_as_float(om_bits);
     if (nc) atomicAdd(P.not_conv, (unsigned long long)nc);
     unsigned long long* st = P.stats + (blockIdx.x & (kStatStripes - 1));
     if (n_inv) atomicAdd(st + 0 * kStatStripes, (unsigned long long)n_inv);

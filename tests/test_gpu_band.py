@@ -113,3 +113,88 @@ def test_band_schedule_ragged_yet(ara, oracle):
     assert np.max(np.abs(g - o) / scale) <= YLT_TOL
     np.testing.assert_array_equal(g, gt)
     assert np.all(g[lens == 0] == 0.0)
+
+
+def run_ep_sched(ara, c, yet, layer, sched, t0=0, n=N, device=False):
+    c.set_option(ara.OPT_SCHEDULE, sched)
+    try:
+        if device:
+            import torch
+            y = torch.zeros(n, dtype=torch.float64, device="cuda")
+            e = torch.zeros(n, dtype=torch.float64, device="cuda")
+            c.run_ep(yet, layer, t0, n, out=y, oep=e)
+            return y.cpu().numpy(), e.cpu().numpy()
+        return c.run_ep(yet, layer, t0, n)
+    finally:
+        c.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND)
+
+
+def test_oep_matches_oracle_and_both_schedules_agree(ara, oracle, staged):
+    # event-level output: each year's largest occurrence loss, from the same pass as the YLT
+    c, w, yet, elts, layer = staged
+    yb, eb = run_ep_sched(ara, c, yet, layer, ara.SCHED_BAND)
+    yt, et = run_ep_sched(ara, c, yet, layer, ara.SCHED_TRIAL)
+    o_y, o_e, nc = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts, with_oep=True)
+    assert nc == 0
+    scale = np.maximum(np.maximum(o_e, w.terms.occ_ret), 1.0)
+    assert np.max(np.abs(eb - o_e) / scale) <= YLT_TOL
+    np.testing.assert_array_equal(eb, et)  # a maximum of the same binary32 values
+    assert np.count_nonzero(eb) > N // 2
+    # the YLT of the same pass is the YLT of ara_run
+    y, _ = run_sched(ara, c, yet, layer, ara.SCHED_BAND)
+    np.testing.assert_array_equal(yb, y)
+    np.testing.assert_array_equal(yt, y)
+    # OEP values are binary32 occurrence results, capped by the occurrence limit
+    assert np.all(eb == eb.astype(np.float32)) and np.all(eb <= w.terms.occ_lim)
+
+
+def test_oep_device_output_and_trial_ranges(ara, staged):
+    c, w, yet, elts, layer = staged
+    y_full, e_full = run_ep_sched(ara, c, yet, layer, ara.SCHED_BAND)
+    y_dev, e_dev = run_ep_sched(ara, c, yet, layer, ara.SCHED_BAND, device=True)
+    np.testing.assert_array_equal(y_dev, y_full)
+    np.testing.assert_array_equal(e_dev, e_full)
+    for sched in (ara.SCHED_BAND, ara.SCHED_TRIAL):
+        for t0, n in [(0, 1), (5, 129), (N - 1, 1), (1000, N - 1000)]:
+            _, e = run_ep_sched(ara, c, yet, layer, sched, t0, n)
+            np.testing.assert_array_equal(e, e_full[t0:t0 + n])
+
+
+def test_oep_is_independent_of_the_year_accumulator(ara, staged):
+    # Kahan year sums (trial-major) change the YLT's rounding, never the per-event maximum
+    c, w, yet, elts, layer = staged
+    _, e_ref = run_ep_sched(ara, c, yet, layer, ara.SCHED_BAND, 0, 500)
+    c.set_option(ara.OPT_PRECISION, ara.ACC_KAHAN32)
+    try:
+        _, e_k = run_ep_sched(ara, c, yet, layer, ara.SCHED_BAND, 0, 500)
+    finally:
+        c.set_option(ara.OPT_PRECISION, ara.ACC_FP64)
+    np.testing.assert_array_equal(e_k, e_ref)
+
+
+def test_oep_ragged_yet_and_newton_path(ara, oracle):
+    rng = np.random.default_rng(11)
+    lens = rng.choice([0, 0, 1, 2, 31, 33, 600], size=500)
+    offsets = np.zeros(501, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    ids = rng.integers(0, 2_000_000, size=int(offsets[-1]), dtype=np.int32)
+    yet_h = synth.Yet(offsets, ids, np.zeros(ids.shape[0], np.float32), 2_000_000)
+    elts_h = synth.paper_elts(4)
+    terms = synth.Terms(2e5, 2e7, 1e7, 1e9)
+    o_y, o_e, _ = oracle.run(yet_h, elts_h, terms, 42, elt_handles=[0, 1, 2, 3], with_oep=True)
+    with ara.Context(seed=42) as c:
+        yet = c.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 2_000_000)
+        elts = [c.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
+        assert elts == [0, 1, 2, 3]
+        layer = c.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+        _, eb = run_ep_sched(ara, c, yet, layer, ara.SCHED_BAND, 0, 500)
+        c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+        try:
+            _, en = c.run_ep(yet, layer, 0, 500)
+        finally:
+            c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+    scale = np.maximum(np.maximum(o_e, terms.occ_ret), 1.0)
+    for e in (eb, en):
+        assert np.max(np.abs(e - o_e) / scale) <= YLT_TOL
+        assert np.all(e[lens == 0] == 0.0)
+    assert np.count_nonzero(o_e) > 100

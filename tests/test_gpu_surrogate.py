@@ -59,7 +59,7 @@ def test_gradient_matches_reference_network(ara, batch):
 def trained(ara):
     c = ara.Context(seed=42)
     rep = c.train_surrogate(n_samples=8_000_000, steps=30_000, batch=8192, lr=3e-3,
-                            lr_final=3e-5, eps=1e-3, cert_samples=16, seed=3)
+                            lr_final=3e-5, eps=5e-4, cert_samples=16, seed=3)
     yield c, rep
     c.close()
 
