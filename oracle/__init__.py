@@ -61,6 +61,9 @@ def _declare(L):
     L.ora_run.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
                           C.c_int64, _P, _P, C.POINTER(C.c_int64), C.c_int]
     L.ora_run.restype = C.c_int
+    L.ora_run_events.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64,
+                                 _P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64), C.c_int]
+    L.ora_run_events.restype = C.c_int
     L.ora_trace.argtypes = [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_uint64, _P,
                             C.c_int64, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                             C.POINTER(C.c_int64)]
@@ -188,6 +191,32 @@ def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0,
     if rc != 0:
         raise ValueError(f"oracle run failed: {rc}")
     return (ylt, oep, nc.value) if with_oep else (ylt, nc.value)
+
+
+def run_events(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0):
+    """Year losses plus the event-level outputs -> (ylt, oep, olt, inc, not_converged): oep = each
+    year's largest occurrence loss; olt / inc per occurrence of the selected trials (concatenated
+    in selection order) = occurrence loss after occurrence terms / increment of the year's net
+    aggregate loss at that occurrence."""
+    off, ids, mean, sd, sdc, mx, h = _layer_arrays(elts, elt_handles)
+    t = np.ascontiguousarray(np.arange(yet.n_trials) if trials is None else trials,
+                             dtype=np.int64)
+    yo = np.ascontiguousarray(yet.offsets, dtype=np.int64)
+    yi = np.ascontiguousarray(yet.event_ids, dtype=np.int32)
+    tr = np.array([terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim], dtype=np.float64)
+    n_occ = int(np.sum(yo[t + 1] - yo[t]))
+    ylt = np.zeros(t.shape[0])
+    oep = np.zeros(t.shape[0])
+    olt = np.zeros(n_occ)
+    inc = np.zeros(n_occ)
+    nc = C.c_int64(0)
+    rc = lib().ora_run_events(_ptr(yo), _ptr(yi), len(elts), _ptr(off), _ptr(ids), _ptr(mean),
+                              _ptr(sd), _ptr(sdc), _ptr(mx), _ptr(h), _ptr(tr), seed, _ptr(t),
+                              t.shape[0], _ptr(ylt), _ptr(oep), _ptr(olt), _ptr(inc),
+                              C.byref(nc), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle run failed: {rc}")
+    return ylt, oep, olt, inc, nc.value
 
 
 def trace(yet, elts, terms, seed, trials, elt_handles=None, max_hits: int = 1 << 22):

@@ -25,6 +25,8 @@
  *   ora_agg_terms       paper §2.3 aggregate terms   min(max(S - AggR, 0), AggL).
  *   ora_run             Algorithm 1 for one layer over a list of trials -> YLT entries, and
  *                       optionally each year's largest occurrence loss (OEP year table).
+ *   ora_run_events      The same with per-occurrence outputs: occurrence losses after
+ *                       occurrence terms and the increments of the net aggregate loss.
  *   ora_trace           the same loop, reporting every (trial, event, ELT) hit.
  *   ora_rank / ora_risk YLT order and PML / TVaR (paper §2.4).
  *
@@ -427,11 +429,22 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
                     const double *sd, const double *sdc, const double *mx,
                     const int32_t *elt_handle,
                     const double *terms, uint64_t seed, const int64_t *trials, int64_t n_sel,
-                    double *ylt, double *oep, ora_hit *hits, int64_t max_hits,
-                    int64_t *n_hits,
-                    int64_t *not_conv, int n_threads) {
+                    double *ylt, double *oep, double *olt, double *inc, ora_hit *hits,
+                    int64_t max_hits, int64_t *n_hits, int64_t *not_conv, int n_threads) {
+  /* per-occurrence outputs: the selected trials' occurrences, concatenated in selection order */
+  int64_t *out_off = NULL;
+  if (olt || inc) {
+    out_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_sel + 1));
+    if (!out_off) return -1;
+    out_off[0] = 0;
+    for (int64_t s = 0; s < n_sel; ++s)
+      out_off[s + 1] = out_off[s] + yet_offsets[trials[s] + 1] - yet_offsets[trials[s]];
+  }
   ora_index *ix = (ora_index *)calloc((size_t)(n_elts > 0 ? n_elts : 1), sizeof(ora_index));
-  if (!ix) return -1;
+  if (!ix) {
+    free(out_off);
+    return -1;
+  }
   int rc = 0;
   for (int32_t j = 0; j < n_elts && rc == 0; ++j)
     rc = build_index(&ix[j], ids + elt_off[j], elt_off[j + 1] - elt_off[j]);
@@ -472,8 +485,13 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
           if (hits) nh++;
         }
         const double o = ora_occ_terms(l, terms[0], terms[1]);
+        /* Algorithm 1 applies the aggregate terms after every event: the year's net loss so far
+         * before (A_prev) and after (A) this occurrence; the increment is its share of the YLT */
+        const double A_prev = ora_agg_terms(S, terms[2], terms[3]);
         S += o;
         if (o > omax) omax = o;
+        if (olt) olt[out_off[s] + k] = o;
+        if (inc) inc[out_off[s] + k] = ora_agg_terms(S, terms[2], terms[3]) - A_prev;
       }
       ylt[s] = ora_agg_terms(S, terms[2], terms[3]);
       if (oep) oep[s] = omax;
@@ -481,6 +499,7 @@ static int run_impl(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
   }
   for (int32_t j = 0; j < n_elts; ++j) free_index(&ix[j]);
   free(ix);
+  free(out_off);
   if (not_conv) *not_conv = nc;
   if (n_hits) *n_hits = nh;
   return rc;
@@ -493,7 +512,23 @@ ORA_API int ora_run(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t 
                     const int64_t *trials, int64_t n_sel, double *ylt, double *oep,
                     int64_t *not_conv, int n_threads) {
   return run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
-                  terms, seed, trials, n_sel, ylt, oep, NULL, 0, NULL, not_conv, n_threads);
+                  terms, seed, trials, n_sel, ylt, oep, NULL, NULL, NULL, 0, NULL, not_conv,
+                  n_threads);
+}
+
+/* As ora_run, with the per-occurrence outputs of the selected trials (their occurrences
+ * concatenated in selection order, sum of their lengths entries each): olt = the occurrence loss
+ * after occurrence terms, inc = the increment of the year's net loss (aggregate terms applied to
+ * the running sum) at that occurrence.  Any output may be NULL. */
+ORA_API int ora_run_events(const int64_t *yet_offsets, const int32_t *yet_ids, int32_t n_elts,
+                           const int64_t *elt_off, const int32_t *ids, const double *mean,
+                           const double *sd, const double *sdc, const double *mx,
+                           const int32_t *elt_handle, const double *terms, uint64_t seed,
+                           const int64_t *trials, int64_t n_sel, double *ylt, double *oep,
+                           double *olt, double *inc, int64_t *not_conv, int n_threads) {
+  return run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
+                  terms, seed, trials, n_sel, ylt, oep, olt, inc, NULL, 0, NULL, not_conv,
+                  n_threads);
 }
 
 /* Same loop, single-threaded, additionally listing every hit (trial, event position k, layer
@@ -511,7 +546,8 @@ ORA_API int ora_trace(const int64_t *yet_offsets, const int32_t *yet_ids, int32_
   if (!hits) return -1;
   int64_t nh = 0, nc = 0;
   int rc = run_impl(yet_offsets, yet_ids, n_elts, elt_off, ids, mean, sd, sdc, mx, elt_handle,
-                    terms, seed, trials, n_sel, ylt, NULL, hits, max_hits, &nh, &nc, 1);
+                    terms, seed, trials, n_sel, ylt, NULL, NULL, NULL, hits, max_hits, &nh, &nc,
+                    1);
   int64_t w = nh < max_hits ? nh : max_hits;
   for (int64_t h = 0; h < w; ++h) {
     hit_trial[h] = hits[h].trial; hit_k[h] = hits[h].k; hit_j[h] = hits[h].j;
