@@ -78,24 +78,31 @@ def test_identity_aggregate_terms_pass_occurrence_losses_through():
 
 
 def test_limit_crossing_pays_the_rest_of_the_limit():
-    # one trial whose occurrences overrun a small aggregate limit: the increments are 0 up to the
-    # retention, the partial occurrence that crosses it, full occurrences, then exactly the
-    # remainder of the limit and zeros
+    # one trial whose occurrences overrun a small aggregate layer: nothing before the retention,
+    # the part of the crossing occurrence above it, whole occurrences, the rest of the limit at
+    # the occurrence that exhausts it, then nothing
     yet, elts, terms, lens = ragged_workload(seed=6)
     _, _, olt0, _, _ = oracle.run_events(yet, elts, terms, 42)
     i = int(np.argmax(lens))
     a, b = yet.offsets[i], yet.offsets[i + 1]
-    cum = np.cumsum(olt0[a:b])
-    agg_ret, agg_lim = float(cum[len(cum) // 4]), float(cum[len(cum) // 2] - cum[len(cum) // 4])
-    assert agg_ret > 0 and agg_lim > 0
-    t2 = synth.Terms(terms.occ_ret, terms.occ_lim, agg_ret, agg_lim)
+    o = olt0[a:b]
+    nz = np.flatnonzero(o)
+    assert nz.size >= 6
+    cum = np.cumsum(o)
+    lo = float(cum[nz[1]] - 0.5 * o[nz[1]])   # retention: half-way through occurrence nz[1]
+    hi = float(cum[nz[4]] - 0.25 * o[nz[4]])  # retention + limit: 3/4 through occurrence nz[4]
+    t2 = synth.Terms(terms.occ_ret, terms.occ_lim, lo, hi - lo)
     ylt, _, olt, inc, _ = oracle.run_events(yet, elts, t2, 42, trials=np.array([i]))
-    np.testing.assert_array_equal(olt, olt0[a:b])
-    assert abs(ylt[0] - agg_lim) <= 1e-9 * agg_lim
-    assert abs(inc.sum() - agg_lim) <= 1e-9 * agg_lim
-    assert np.all(inc[:len(cum) // 4 + 1] == 0.0)
-    assert np.all(inc[len(cum) // 2 + 1:] == 0.0)
-    assert np.count_nonzero(inc) >= 2
+    np.testing.assert_array_equal(olt, o)
+    tol = 1e-12 * hi
+    assert abs(ylt[0] - (hi - lo)) <= tol
+    assert np.all(inc[:nz[1]] == 0.0)
+    assert abs(inc[nz[1]] - 0.5 * o[nz[1]]) <= tol
+    for k in (nz[2], nz[3]):
+        assert abs(inc[k] - o[k]) <= tol
+    assert abs(inc[nz[4]] - 0.75 * o[nz[4]]) <= tol
+    assert np.all(inc[nz[4] + 1:] == 0.0)
+    assert np.count_nonzero(inc) == 4
 
 
 def test_selected_trials_are_concatenated_in_selection_order():
