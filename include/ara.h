@@ -166,6 +166,21 @@ ARA_API ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0,
  * ylt (both host or both device); ARA_ERR_INVALID_ARG otherwise. */
 ARA_API ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
                               double* ylt, double* oep, void* stream);
+/* Per-occurrence outputs (Algorithm 1 applies the occurrence terms to every event and the
+ * aggregate terms to the running year sum after every event; §2.3): for the occurrences of
+ * trials [t0, t0+n), indexed by occurrence position - trial_offsets[t0] (so the caller sizes
+ * them trial_offsets[t0+n] - trial_offsets[t0]):
+ *   olt[q] (binary32) = min(max(l_q - OccR, 0), OccL), the occurrence loss the year sum takes;
+ *   inc[q] (binary64) = A(S_q) - A(S_q - o_q), A(S) = min(max(S - AggR, 0), AggL), S_q the
+ *     running year sum through occurrence q; A of the trial's last occurrence is its ylt entry
+ *     bit for bit, and the increments sum to it up to binary64 rounding.
+ * Any of oep, olt, inc may be NULL; all given outputs must be the same kind of memory as ylt.
+ * Per-occurrence outputs are written in trial order, so such a call runs the trial-major
+ * schedule; inc needs ARA_ACC_FP64 (ARA_ERR_INVALID_ARG otherwise).  With host outputs the
+ * library stages them in stream-ordered device memory for the call. */
+ARA_API ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                                  double* ylt, double* oep, float* olt, double* inc,
+                                  void* stream);
 /* Inversions that hit the iteration cap since the context was created (blocks on its work). */
 ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
 /* Work counters accumulated by every ara_run since the context was created (blocks on its work):

@@ -107,6 +107,7 @@ _SIGNATURES = {
     "ara_free_layer": ([_P, _I32], C.c_int),
     "ara_run": ([_P, _I32, _I32, _I64, _I64, _P, _P], C.c_int),
     "ara_run_ep": ([_P, _I32, _I32, _I64, _I64, _P, _P, _P], C.c_int),
+    "ara_run_events": ([_P, _I32, _I32, _I64, _I64, _P, _P, _P, _P, _P], C.c_int),
     "ara_not_converged": ([_P, C.POINTER(_I64)], C.c_int),
     "ara_risk_measures": ([_P, _P, _I64, _P, _I32, _P, _P], C.c_int),
     "ara_rank_ylt": ([_P, _P, _I64, _P], C.c_int),
@@ -325,6 +326,25 @@ class Context:
         st = lib().ara_run_ep(self._h, yet, layer, int(t0), int(n), _ptr(out), _ptr(oep), s)
         self._check(st, allow_not_converged)
         return out, oep
+
+    def run_events(self, yet: int, layer: int, t0: int, n: int, n_occ: int, device=False,
+                   increments: bool = True, allow_not_converged: bool = False):
+        """Year losses, OEP year table and the per-occurrence outputs of trials [t0, t0+n), whose
+        occurrences number n_occ -> (ylt, oep, olt float32, inc float64 or None); device=True
+        returns CUDA tensors (asynchronous-capable path), else numpy arrays."""
+        if device:
+            import torch
+            mk = lambda m, dt: torch.zeros(m, dtype=dt, device="cuda")  # noqa: E731
+            f64, f32 = torch.float64, torch.float32
+        else:
+            mk = lambda m, dt: np.zeros(m, dtype=dt)  # noqa: E731
+            f64, f32 = np.float64, np.float32
+        ylt, oep, olt = mk(n, f64), mk(n, f64), mk(max(n_occ, 1), f32)
+        inc = mk(max(n_occ, 1), f64) if increments else None
+        st = lib().ara_run_events(self._h, yet, layer, int(t0), int(n), _ptr(ylt), _ptr(oep),
+                                  _ptr(olt), _ptr(inc) if inc is not None else None, None)
+        self._check(st, allow_not_converged)
+        return ylt, oep, olt[:n_occ], (inc[:n_occ] if inc is not None else None)
 
     # -- risk measures -------------------------------------------------------------------------
     def risk_measures(self, ylt, rps):

@@ -83,6 +83,13 @@ void mem_free(const void* p, bool ordered, cudaStream_t st) {
   else cudaFree(const_cast<void*>(p));
 }
 
+// A stream-ordered temporary freed when the call returns, on whichever path.
+struct OrderedTemp {
+  void* p;
+  cudaStream_t st;
+  ~OrderedTemp() { mem_free(p, true, st); }
+};
+
 // Copies n elements from a host or device pointer into device memory on the stream.
 template <class T>
 cudaError_t copy_in(T* dst, const T* src, int64_t n, cudaStream_t st) {
@@ -756,8 +763,8 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
 
 extern "C" {
 
-ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
-                      double* ylt, double* oep, void* stream) {
+ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                          double* ylt, double* oep, float* olt, double* inc, void* stream) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
   ara_status s = check_run_args(ctx, yet, layer, t0, n);
   if (s != ARA_OK) return s;
@@ -765,26 +772,55 @@ ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int6
   if (n == 0) return ARA_OK;
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const bool dev_out = is_device_ptr(ylt);
-  if (oep && is_device_ptr(oep) != dev_out)
-    return fail(ctx, ARA_ERR_INVALID_ARG, "ylt and oep must both be host or both device memory");
+  if ((oep && is_device_ptr(oep) != dev_out) || (olt && is_device_ptr(olt) != dev_out) ||
+      (inc && is_device_ptr(inc) != dev_out))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "outputs must all be host or all device memory");
+  const bool per_occ = olt != nullptr || inc != nullptr;
+  if (inc && ctx->cfg.precision != ARA_ACC_FP64)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "occurrence increments need ARA_ACC_FP64 year sums");
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
   if (stream && !dev_out)
-    return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need a device ylt");
+    return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need device outputs");
+  const YetDev& Y = ctx->yets[yet];
   double* d_ylt = ylt;
   double* d_oep = oep;
+  float* d_olt = olt;
+  double* d_inc = inc;
+  int64_t n_occ = 0;
+  OrderedTemp tmp_olt{nullptr, st}, tmp_inc{nullptr, st};  // host outputs' device staging
   if (!dev_out) {
     s = ensure_ylt_tmp(ctx, oep ? 2 * n : n);
     if (s != ARA_OK) return s;
     d_ylt = ctx->d_ylt_tmp;
     d_oep = oep ? ctx->d_ylt_tmp + n : nullptr;
+    if (per_occ) {
+      int64_t ends[2];
+      CUDA_TRY(ctx, cudaMemcpyAsync(&ends[0], Y.offsets + t0, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(ctx, cudaMemcpyAsync(&ends[1], Y.offsets + t0 + n, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(ctx, cudaStreamSynchronize(st));
+      n_occ = ends[1] - ends[0];
+      if (olt) {
+        CUDA_TRY(ctx, mem_alloc(&d_olt, n_occ, true, st));
+        tmp_olt.p = d_olt;
+      }
+      if (inc) {
+        CUDA_TRY(ctx, mem_alloc(&d_inc, n_occ, true, st));
+        tmp_inc.p = d_inc;
+      }
+    }
   }
   unsigned long long nc_before = 0;
   if (!stream)
     CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
                                   cudaMemcpyDeviceToHost, st));
-  TrialParams p = make_params(ctx, ctx->yets[yet], ctx->layers[layer], t0, n, d_ylt);
+  TrialParams p = make_params(ctx, Y, ctx->layers[layer], t0, n, d_ylt);
   p.oep = d_oep;
-  if (uses_band_schedule(ctx, ctx->layers[layer])) {
+  p.olt = d_olt;
+  p.inc = d_inc;
+  // per-occurrence outputs are written in trial order, so they keep the trial-major schedule
+  if (!per_occ && uses_band_schedule(ctx, ctx->layers[layer])) {
     // year sums (8 B per trial), then the OEP maxima (4 B per trial) in the same scratch
     s = ensure_ysum(ctx, oep ? n + (n + 1) / 2 : n);
     if (s != ARA_OK) return s;
@@ -796,10 +832,19 @@ ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int6
                                inversion_mode(ctx), false, st));
   }
   if (stream) return ARA_OK;
-  if (!dev_out)
-    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
-  if (!dev_out && oep)
-    CUDA_TRY(ctx, cudaMemcpyAsync(oep, d_oep, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  if (!dev_out) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                                  st));
+    if (oep)
+      CUDA_TRY(ctx, cudaMemcpyAsync(oep, d_oep, sizeof(double) * (size_t)n,
+                                    cudaMemcpyDeviceToHost, st));
+    if (olt && n_occ > 0)
+      CUDA_TRY(ctx, cudaMemcpyAsync(olt, d_olt, sizeof(float) * (size_t)n_occ,
+                                    cudaMemcpyDeviceToHost, st));
+    if (inc && n_occ > 0)
+      CUDA_TRY(ctx, cudaMemcpyAsync(inc, d_inc, sizeof(double) * (size_t)n_occ,
+                                    cudaMemcpyDeviceToHost, st));
+  }
   unsigned long long nc_after = 0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
                                 cudaMemcpyDeviceToHost, st));
@@ -810,9 +855,14 @@ ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int6
   return ARA_OK;
 }
 
+ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                      double* ylt, double* oep, void* stream) {
+  return ara_run_events(ctx, yet, layer, t0, n, ylt, oep, nullptr, nullptr, stream);
+}
+
 ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n, double* ylt,
                    void* stream) {
-  return ara_run_ep(ctx, yet, layer, t0, n, ylt, nullptr, stream);
+  return ara_run_events(ctx, yet, layer, t0, n, ylt, nullptr, nullptr, nullptr, stream);
 }
 
 ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {

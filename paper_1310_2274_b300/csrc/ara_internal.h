@@ -118,6 +118,9 @@ struct TrialParams {
   double* oep;               // [n] or null
   unsigned int* omax;        // [n] binary32 bit patterns of the running maxima (band-major;
                              //     zeroed first; non-negative floats order like their bits)
+  // per-occurrence outputs (trial-major only), indexed by occurrence position - offsets[t0]
+  float* olt;                // occurrence loss after occurrence terms, or null
+  double* inc;               // increment of the year's net aggregate loss, or null
 };
 
 // Work counters are striped over kStatStripes copies (counter c of stripe s at

@@ -63,6 +63,31 @@ __device__ __forceinline__ float surrogate_round(const MlpSmem& W, const float (
   return 1.0f / (1.0f + __expf(-kOutScale * y));
 }
 
+// Per-occurrence outputs for 32 consecutive occurrences (lane l: position q), in trial order:
+// the occurrence loss o after occurrence terms, and the increment of the year's net loss
+// A(S) = min(max(S - AggR, 0), AggL) that o brings, Algorithm 1 applying the aggregate terms
+// after every event.  S is the running year sum in exact grid units (an inclusive warp scan plus
+// the carry of earlier groups), so the trial's last A is its YLT entry bit for bit.
+__device__ __forceinline__ void occurrence_outputs(const TrialParams& P, int64_t q, int64_t end,
+                                                   float o, int64_t q0,
+                                                   unsigned long long& carry, int lane) {
+  const bool in = q < end;
+  if (P.olt != nullptr && in) P.olt[q - q0] = o;
+  if (P.inc == nullptr) return;
+  const unsigned long long un = in ? AccExact::units(o, P.q_scale) : 0ull;
+  unsigned long long incl = un;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  const unsigned long long s1 = carry + incl;
+  const double a1 = fmin(fmax((double)s1 * P.q_unit - P.agg_ret, 0.0), P.agg_lim);
+  const double a0 = fmin(fmax((double)(s1 - un) * P.q_unit - P.agg_ret, 0.0), P.agg_lim);
+  if (in) P.inc[q - q0] = a1 - a0;
+  carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+}
+
 // The whole of Algorithm 1 for one trial (w-th of the launch item P), run by one warp.
 template <int MW, class Acc, bool TRACE, int INV>
 __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, int lane, int wib,
@@ -78,6 +103,11 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
   const L2Policies pol = L2Policies::make();
   Acc acc = Acc::make(P);
   float omax = 0.f;  // the year's largest occurrence loss (event-level output)
+  // per-occurrence outputs: exact running year sum (grid units) of the occurrences before the
+  // current group of 32, and the output index origin
+  const bool evt = P.olt != nullptr || P.inc != nullptr;
+  unsigned long long carry = 0ull;
+  const int64_t q0 = evt ? P.offsets[P.t0] : 0;
   int32_t trace_n = 0;
   unsigned int nc = 0;
   unsigned int n_inv = 0, n_it = 0, n_cf = 0, n_hit = 0, n_tab = 0, n_net = 0;
@@ -249,12 +279,14 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const int64_t q = c + v * 32 + lane;
+      float o = 0.f;
       if (q < end) {
         const float l = lsum[v * 32 + lane];
-        const float o = fminf(fmaxf(l - P.occ_ret, 0.f), P.occ_lim);
+        o = fminf(fmaxf(l - P.occ_ret, 0.f), P.occ_lim);
         acc.add(o);
         omax = fmaxf(omax, o);
       }
+      if (evt) occurrence_outputs(P, q, end, o, q0, carry, lane);
     }
     __syncwarp();
   }
