@@ -193,6 +193,23 @@ def run(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0,
     return (ylt, oep, nc.value) if with_oep else (ylt, nc.value)
 
 
+def run_portfolio(yet, elts, portfolio, seed, trials=None, threads: int = 0):
+    """Algorithm 1's outer loops: portfolio = list of programs, each a list of layers
+    (ELT indices into elts, Terms).  Every layer's YLT over the selected trials, in program then
+    layer order -> float64 array [layers, trials].  An ELT's draws are keyed by its index in elts
+    (its handle), so an ELT shared by several layers has the same losses in each."""
+    rows = []
+    for program in portfolio:
+        for idx, terms in program:
+            y, nc = run(yet, [elts[i] for i in idx], terms, seed, trials=trials,
+                        elt_handles=list(idx), threads=threads)
+            if nc:
+                raise ValueError(f"{nc} inversions did not converge")
+            rows.append(y)
+    n = yet.n_trials if trials is None else len(trials)
+    return np.array(rows).reshape(len(rows), n)
+
+
 def run_events(yet, elts, terms, seed, trials=None, elt_handles=None, threads: int = 0):
     """Year losses plus the event-level outputs -> (ylt, oep, olt, inc, not_converged): oep = each
     year's largest occurrence loss; olt / inc per occurrence of the selected trials (concatenated
