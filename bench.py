@@ -379,6 +379,32 @@ def run_ours(a):
                  "pml_rel_diff": max(abs(float(x) / float(y) - 1.0) for x, y in zip(kp, pml)),
                  "tvar_rel_diff": max(abs(float(x) / float(y) - 1.0) for x, y in zip(kt, tvar))}
 
+    # ---- event-level outputs: OEP year table, per-occurrence losses and net increments --------
+    # (one trial-major pass writing 4 + 8 bytes per occurrence beside the YLT; device buffers)
+    n_occ = int(yet_h.offsets[n] - yet_h.offsets[0])
+    ev_out = (torch.empty(n, dtype=torch.float64, device=dev),
+              torch.empty(n, dtype=torch.float64, device=dev),
+              torch.empty(n_occ, dtype=torch.float32, device=dev),
+              torch.empty(n_occ, dtype=torch.float64, device=dev))
+    ctx.run_events(yet, layer, 0, n, n_occ, out=ev_out, stream=stream)
+    k_ev = max(3, min(10, a.steps))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(k_ev)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.run_events(yet, layer, 0, n, n_occ, out=ev_out, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    events_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    oep_p, _ = ctx.risk_measures(ev_out[1], rps)
+    ctx.run(yet, layer, 0, n, out=ylt, stream=stream)  # the headline YLT again (exact sums)
+    ev_y_equal = bool(torch.equal(ev_out[0], ylt))
+    events = {"ms": events_ms, "schedule": "trial-major", "occurrences": n_occ,
+              "output_bytes": n_occ * 12 + n * 16,
+              "ylt_identical_to_headline": ev_y_equal,
+              "oep_pml": [float(x) for x in oep_p]}
+    del ev_out
+
     # ---- the Newton inversion on the same data (secondary figure) -----------------------------
     ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
     ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
@@ -443,6 +469,7 @@ def run_ours(a):
                                                     f"{FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"}},
         "schedules_ms": sched_ms,
         "precision": precision,
+        "event_outputs": events,
         "uncertified_records": s1["uncertified"],
         "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
                           "tvar": [float(v) for v in tvar]},

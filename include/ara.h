@@ -181,6 +181,16 @@ ARA_API ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t 
 ARA_API ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
                                   double* ylt, double* oep, float* olt, double* inc,
                                   void* stream);
+/* Portfolio (paper §2.1: a portfolio groups programs, a program groups layers; Algorithm 1 loops
+ * over programs, then layers, then trials): the YLTs of n_layers layers of one YET over trials
+ * [t0, t0+n) from one call, ylt[i*n + j] = the year loss of trial t0+j under layers[i], equal bit
+ * for bit to ara_run of that layer.  The caller lists the layers of its programs in any order
+ * (a layer may appear more than once).  Layers sharing a schedule and lookup-entry width share
+ * one batched launch, so a portfolio of many small layers fills the GPU as one large layer does.
+ * ylt: n_layers*n binary64, host or device (stream as for ara_run); layers: host array. */
+ARA_API ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers,
+                                     int32_t n_layers, int64_t t0, int64_t n, double* ylt,
+                                     void* stream);
 /* Inversions that hit the iteration cap since the context was created (blocks on its work). */
 ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
 /* Work counters accumulated by every ara_run since the context was created (blocks on its work):

@@ -108,6 +108,7 @@ _SIGNATURES = {
     "ara_run": ([_P, _I32, _I32, _I64, _I64, _P, _P], C.c_int),
     "ara_run_ep": ([_P, _I32, _I32, _I64, _I64, _P, _P, _P], C.c_int),
     "ara_run_events": ([_P, _I32, _I32, _I64, _I64, _P, _P, _P, _P, _P], C.c_int),
+    "ara_run_portfolio": ([_P, _I32, _P, _I32, _I64, _I64, _P, _P], C.c_int),
     "ara_not_converged": ([_P, C.POINTER(_I64)], C.c_int),
     "ara_risk_measures": ([_P, _P, _I64, _P, _I32, _P, _P], C.c_int),
     "ara_rank_ylt": ([_P, _P, _I64, _P], C.c_int),
@@ -327,22 +328,40 @@ class Context:
         self._check(st, allow_not_converged)
         return out, oep
 
+    def run_portfolio(self, yet: int, layers, t0: int, n: int, out=None, stream=None,
+                      allow_not_converged: bool = False):
+        """YLTs of several layers (a portfolio's programs' layers, flattened) over trials
+        [t0, t0+n) -> float64 [len(layers), n]; out: numpy array or CUDA tensor of that shape."""
+        ls = np.ascontiguousarray(layers, dtype=np.int32)
+        if out is None:
+            out = np.zeros((ls.shape[0], n), dtype=np.float64)
+        s = None if stream is None else getattr(stream, "cuda_stream", stream)
+        st = lib().ara_run_portfolio(self._h, yet, _ptr(ls), int(ls.shape[0]), int(t0), int(n),
+                                     _ptr(out), s)
+        self._check(st, allow_not_converged)
+        return out
+
     def run_events(self, yet: int, layer: int, t0: int, n: int, n_occ: int, device=False,
-                   increments: bool = True, allow_not_converged: bool = False):
+                   increments: bool = True, out=None, stream=None,
+                   allow_not_converged: bool = False):
         """Year losses, OEP year table and the per-occurrence outputs of trials [t0, t0+n), whose
-        occurrences number n_occ -> (ylt, oep, olt float32, inc float64 or None); device=True
-        returns CUDA tensors (asynchronous-capable path), else numpy arrays."""
-        if device:
-            import torch
-            mk = lambda m, dt: torch.zeros(m, dtype=dt, device="cuda")  # noqa: E731
-            f64, f32 = torch.float64, torch.float32
-        else:
-            mk = lambda m, dt: np.zeros(m, dtype=dt)  # noqa: E731
-            f64, f32 = np.float64, np.float32
-        ylt, oep, olt = mk(n, f64), mk(n, f64), mk(max(n_occ, 1), f32)
-        inc = mk(max(n_occ, 1), f64) if increments else None
+        occurrences number n_occ -> (ylt, oep, olt float32, inc float64 or None).  device=True
+        returns CUDA tensors, else numpy arrays; out = (ylt, oep, olt, inc) reuses caller buffers
+        (inc may be None); stream (CUDA outputs only) makes the call asynchronous."""
+        if out is None:
+            if device:
+                import torch
+                mk = lambda m, dt: torch.zeros(m, dtype=dt, device="cuda")  # noqa: E731
+                f64, f32 = torch.float64, torch.float32
+            else:
+                mk = lambda m, dt: np.zeros(m, dtype=dt)  # noqa: E731
+                f64, f32 = np.float64, np.float32
+            out = (mk(n, f64), mk(n, f64), mk(max(n_occ, 1), f32),
+                   mk(max(n_occ, 1), f64) if increments else None)
+        ylt, oep, olt, inc = out
+        s = None if stream is None else getattr(stream, "cuda_stream", stream)
         st = lib().ara_run_events(self._h, yet, layer, int(t0), int(n), _ptr(ylt), _ptr(oep),
-                                  _ptr(olt), _ptr(inc) if inc is not None else None, None)
+                                  _ptr(olt), _ptr(inc) if inc is not None else None, s)
         self._check(st, allow_not_converged)
         return ylt, oep, olt[:n_occ], (inc[:n_occ] if inc is not None else None)
 

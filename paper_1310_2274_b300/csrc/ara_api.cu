@@ -865,6 +865,114 @@ ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t
   return ara_run_events(ctx, yet, layer, t0, n, ylt, nullptr, nullptr, nullptr, stream);
 }
 
+ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, int32_t n_layers,
+                             int64_t t0, int64_t n, double* ylt, void* stream) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (n_layers < 0 || (n_layers > 0 && !layers))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "bad layer list");
+  for (int32_t i = 0; i < n_layers; ++i) {
+    const ara_status s = check_run_args(ctx, yet, layers[i], t0, n);
+    if (s != ARA_OK) return s;
+  }
+  if (n == 0 || n_layers == 0) return ARA_OK;
+  if (!ylt) return fail(ctx, ARA_ERR_INVALID_ARG, "ylt is NULL");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const bool dev_out = is_device_ptr(ylt);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  if (stream && !dev_out)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need a device ylt");
+  const int64_t total = (int64_t)n_layers * n;
+  double* d_ylt = ylt;
+  if (!dev_out) {
+    ara_status s = ensure_ylt_tmp(ctx, total);
+    if (s != ARA_OK) return s;
+    d_ylt = ctx->d_ylt_tmp;
+  }
+  // one launch item per layer, grouped by schedule and lookup-entry width (one batched launch
+  // per group): band-major items first, each with its own year-sum rows
+  const YetDev& Y = ctx->yets[yet];
+  std::vector<int32_t> order(n_layers);
+  for (int32_t i = 0; i < n_layers; ++i) order[i] = i;
+  auto group = [&](int32_t i) {
+    const LayerDev& L = ctx->layers[layers[i]];
+    return (uses_band_schedule(ctx, L) ? 0 : 2) + (L.mask_words == 1 ? 0 : 1);
+  };
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return group(a) < group(b); });
+  int32_t n_band = 0;
+  for (int32_t i = 0; i < n_layers; ++i) n_band += group(i) < 2 ? 1 : 0;
+  if (n_band > 0) {
+    ara_status s = ensure_ysum(ctx, (int64_t)n_band * n);
+    if (s != ARA_OK) return s;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ysum, 0,
+                                  sizeof(unsigned long long) * (size_t)n_band * (size_t)n, st));
+  }
+  std::vector<TrialParams> items(n_layers);
+  std::vector<int64_t> begin(3 * (size_t)n_layers, 0);  // warp / block / trial firsts per item
+  struct Group { int32_t first = 0, count = 0; int64_t units = 0, trials = 0; };
+  Group g[4];
+  int32_t band_row = 0;
+  for (int32_t k = 0; k < n_layers; ++k) {
+    const int32_t i = order[k];
+    const LayerDev& L = ctx->layers[layers[i]];
+    TrialParams p = make_params(ctx, Y, L, t0, n, d_ylt + (int64_t)i * n);
+    Group& G = g[group(i)];
+    if (G.count == 0) G.first = k;
+    if (group(i) < 2) {
+      p.tiles = (int32_t)band_tiles(n);
+      p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
+      begin[n_layers + k] = G.units;
+      begin[2 * (size_t)n_layers + k] = G.trials;
+      G.units += (int64_t)p.n_bands * p.tiles;
+      G.trials += n;
+    } else {
+      begin[k] = G.units;
+      G.units += n;
+    }
+    G.count++;
+    items[k] = p;
+  }
+  TrialParams* d_items = nullptr;
+  int64_t* d_begin = nullptr;
+  CUDA_TRY(ctx, mem_alloc(&d_items, n_layers, true, st));
+  OrderedTemp tmp_items{d_items, st};
+  CUDA_TRY(ctx, mem_alloc(&d_begin, 3 * (int64_t)n_layers, true, st));
+  OrderedTemp tmp_begin{d_begin, st};
+  // pageable sources: each copy has read its source when the call returns
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_items, items.data(), sizeof(TrialParams) * (size_t)n_layers,
+                                cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_begin, begin.data(), sizeof(int64_t) * begin.size(),
+                                cudaMemcpyHostToDevice, st));
+  unsigned long long nc_before = 0;
+  if (!stream)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
+                                  cudaMemcpyDeviceToHost, st));
+  for (int gi = 0; gi < 4; ++gi) {
+    const Group& G = g[gi];
+    if (G.count == 0) continue;
+    const int mw = (gi & 1) ? 2 : 1;
+    if (gi < 2)
+      CUDA_TRY(ctx, launch_band_batch(d_items + G.first, d_begin + n_layers + G.first,
+                                      d_begin + 2 * (int64_t)n_layers + G.first, G.count,
+                                      G.units, G.trials, mw, ctx->cfg.precision, st));
+    else
+      CUDA_TRY(ctx, launch_trial_batch(d_items + G.first, d_begin + G.first, G.count, G.units,
+                                       mw, ctx->cfg.precision, inversion_mode(ctx), st));
+  }
+  if (stream) return ARA_OK;
+  if (!dev_out)
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)total,
+                                  cudaMemcpyDeviceToHost, st));
+  unsigned long long nc_after = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
+                                cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (nc_after != nc_before)
+    return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
+                nc_after - nc_before);
+  return ARA_OK;
+}
+
 ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {
   if (!ctx || !out) return ARA_ERR_INVALID_ARG;
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));

@@ -499,12 +499,17 @@ cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cud
 
 cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block_begin,
                               const int64_t* d_trial_begin, int n_items, int64_t total_blocks,
-                              int64_t total_trials, int precision, cudaStream_t st) {
+                              int64_t total_trials, int mask_words, int precision,
+                              cudaStream_t st) {
   if (precision != 0) return cudaErrorInvalidValue;
   if (total_blocks <= 0) return cudaSuccess;
   if (total_blocks > 0x7FFFFFFFll) return cudaErrorInvalidConfiguration;
-  band_batch_kernel<2><<<(unsigned)total_blocks, kBW * 32, 0, st>>>(d_items, d_block_begin,
-                                                                   n_items);
+  if (mask_words == 1)
+    band_batch_kernel<1><<<(unsigned)total_blocks, kBW * 32, 0, st>>>(d_items, d_block_begin,
+                                                                     n_items);
+  else
+    band_batch_kernel<2><<<(unsigned)total_blocks, kBW * 32, 0, st>>>(d_items, d_block_begin,
+                                                                     n_items);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -174,15 +174,17 @@ int64_t band_tiles(int64_t n);
 int year_grid_exponent(float occ_lim, int64_t max_len);
 // band kernel + per-trial finalisation over p.t0 .. p.t0 + p.n; p.ysum holds n words (zeroed here)
 cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cudaStream_t st);
-// serving: items with their band fields set (tiles = band_tiles(n), ysum zeroed); block_begin[i]
+// many items in one launch (serving slices, portfolio layers), all with mask_words-word lookup
+// entries: items with their band fields set (tiles = band_tiles(n), ysum zeroed); block_begin[i]
 // = first block of item i (n_bands * tiles blocks each), trial_begin[i] = its first trial
 cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block_begin,
                               const int64_t* d_trial_begin, int n_items, int64_t total_blocks,
-                              int64_t total_trials, int precision, cudaStream_t st);
-
+                              int64_t total_trials, int mask_words, int precision,
+                              cudaStream_t st);
+// warp_begin[i] = first warp of item i (one warp per trial)
 cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp_begin,
-                               int n_items, int64_t total_warps, int precision, int inversion,
-                               cudaStream_t st);
+                               int n_items, int64_t total_warps, int mask_words, int precision,
+                               int inversion, cudaStream_t st);
 
 // Radix sort of binary64 year losses (descending, ties by index) and tail sums.
 struct SortScratch {

@@ -387,10 +387,10 @@ bool issue(ara_server* s) {
                         s->stream);
   if (e == cudaSuccess && kb > 0)
     e = ara::launch_band_batch(L.d_items, L.d_begin + cap, L.d_begin + 2 * cap, kb, blocks,
-                               trials, s->ctx->cfg.precision, s->stream);
+                               trials, 2, s->ctx->cfg.precision, s->stream);
   if (e == cudaSuccess && k > kb)
-    e = ara::launch_trial_batch(L.d_items + kb, L.d_begin, k - kb, warp, s->ctx->cfg.precision,
-                                inversion_mode(s->ctx), s->stream);
+    e = ara::launch_trial_batch(L.d_items + kb, L.d_begin, k - kb, warp, 2,
+                                s->ctx->cfg.precision, inversion_mode(s->ctx), s->stream);
   if (e == cudaSuccess) e = cudaEventRecord(L.done, s->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -401,30 +401,39 @@ cudaError_t launch_mode(const TrialParams& p, int mask_words, int precision, boo
                          : launch_one<2, AccExact, false, INV>(p, st);
 }
 
-template <class Acc, int INV>
+template <int MW, class Acc, int INV>
 cudaError_t launch_batch_mode(const TrialParams* d_items, const int64_t* d_warp_begin,
                               int n_items, int64_t total_warps, cudaStream_t st) {
   const int64_t blocks = (total_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks == 0) return cudaSuccess;
-  batch_kernel<2, Acc, INV><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
+  batch_kernel<MW, Acc, INV><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
       d_items, d_warp_begin, n_items, total_warps);
   count_launches(1);
   return cudaGetLastError();
 }
 
+template <class Acc, int INV>
+cudaError_t launch_batch_mw(const TrialParams* d_items, const int64_t* d_warp_begin,
+                            int n_items, int64_t total_warps, int mask_words, cudaStream_t st) {
+  return mask_words == 1
+             ? launch_batch_mode<1, Acc, INV>(d_items, d_warp_begin, n_items, total_warps, st)
+             : launch_batch_mode<2, Acc, INV>(d_items, d_warp_begin, n_items, total_warps, st);
+}
+
 }  // namespace
 
 cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp_begin,
-                               int n_items, int64_t total_warps, int precision, int inversion,
-                               cudaStream_t st) {
+                               int n_items, int64_t total_warps, int mask_words, int precision,
+                               int inversion, cudaStream_t st) {
+  const int mw = mask_words;
   if (precision == 1) {
-    if (inversion == 2) return launch_batch_mode<AccKahan, 2>(d_items, d_warp_begin, n_items, total_warps, st);
-    if (inversion == 1) return launch_batch_mode<AccKahan, 1>(d_items, d_warp_begin, n_items, total_warps, st);
-    return launch_batch_mode<AccKahan, 0>(d_items, d_warp_begin, n_items, total_warps, st);
+    if (inversion == 2) return launch_batch_mw<AccKahan, 2>(d_items, d_warp_begin, n_items, total_warps, mw, st);
+    if (inversion == 1) return launch_batch_mw<AccKahan, 1>(d_items, d_warp_begin, n_items, total_warps, mw, st);
+    return launch_batch_mw<AccKahan, 0>(d_items, d_warp_begin, n_items, total_warps, mw, st);
   }
-  if (inversion == 2) return launch_batch_mode<AccExact, 2>(d_items, d_warp_begin, n_items, total_warps, st);
-  if (inversion == 1) return launch_batch_mode<AccExact, 1>(d_items, d_warp_begin, n_items, total_warps, st);
-  return launch_batch_mode<AccExact, 0>(d_items, d_warp_begin, n_items, total_warps, st);
+  if (inversion == 2) return launch_batch_mw<AccExact, 2>(d_items, d_warp_begin, n_items, total_warps, mw, st);
+  if (inversion == 1) return launch_batch_mw<AccExact, 1>(d_items, d_warp_begin, n_items, total_warps, mw, st);
+  return launch_batch_mw<AccExact, 0>(d_items, d_warp_begin, n_items, total_warps, mw, st);
 }
 
 cudaError_t launch_trial(const TrialParams& p, int mask_words, int precision, int inversion,
