@@ -405,6 +405,45 @@ def run_ours(a):
               "oep_pml": [float(x) for x in oep_p]}
     del ev_out
 
+    # ---- portfolio: three programs of layers over the same ELTs, one call vs one run per layer -
+    rng_pf = np.random.default_rng(5)
+    pf_layers, pf_elts = [], 0
+    for _prog in range(3):
+        for _l in range(3):
+            k = int(rng_pf.integers(3, len(elts) + 1))
+            pick = [elts[i] for i in rng_pf.choice(len(elts), size=k, replace=False)]
+            pf_elts += k
+            pf_layers.append(ctx.add_layer(pick, terms.occ_ret, terms.occ_lim,
+                                           terms.agg_ret * k / len(elts),
+                                           terms.agg_lim * k / len(elts)))
+    pf_rows = {}
+    for n_pf in (n, min(n, 20_000)):
+        pf_out = torch.empty((len(pf_layers), n_pf), dtype=torch.float64, device=dev)
+        ctx.run_portfolio(yet, pf_layers, 0, n_pf, out=pf_out, stream=stream)
+        k_pf = 3
+        ev_b = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(k_pf)]
+        for e0, e1 in ev_b:
+            e0.record(stream)
+            ctx.run_portfolio(yet, pf_layers, 0, n_pf, out=pf_out, stream=stream)
+            e1.record(stream)
+        ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(k_pf)]
+        for e0, e1 in ev_s:
+            e0.record(stream)
+            for i, l in enumerate(pf_layers):
+                ctx.run(yet, l, 0, n_pf, out=pf_out[i], stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pf_rows[str(n_pf)] = {
+            "one_call_ms": statistics.mean(a.elapsed_time(b) for a, b in ev_b),
+            "per_layer_runs_ms": statistics.mean(a.elapsed_time(b) for a, b in ev_s)}
+        del pf_out
+    for l in pf_layers:
+        ctx.free_layer(l)
+    portfolio = {"programs": 3, "layers": len(pf_layers), "elts_per_layer_mean":
+                 pf_elts / len(pf_layers), "by_trials": pf_rows}
+
     # ---- the Newton inversion on the same data (secondary figure) -----------------------------
     ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
     ctx.run(yet, layer, 0, n, out=ylt, stream=stream)
@@ -470,6 +509,7 @@ def run_ours(a):
         "schedules_ms": sched_ms,
         "precision": precision,
         "event_outputs": events,
+        "portfolio": portfolio,
         "uncertified_records": s1["uncertified"],
         "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
                           "tvar": [float(v) for v in tvar]},
