@@ -234,6 +234,8 @@ ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
                       ctx->stream) != cudaSuccess ||
       cudaMalloc(&ctx->d_misc, 4096) != cudaSuccess ||
       cudaMemsetAsync(ctx->d_not_conv, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device) !=
+          cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     ara_destroy(ctx);
@@ -715,6 +717,61 @@ int inversion_mode(const ara_ctx* ctx) {
   return ctx->inversion;
 }
 
+// The end of a run call: nothing more for an asynchronous call; else the YLT back to a host
+// buffer, and ARA_ERR_NOT_CONVERGED if the convergence counter moved during the call.
+static ara_status finish_run(ara_ctx* ctx, void* stream, bool dev_out, double* ylt,
+                             const double* d_ylt, int64_t total, unsigned long long nc_before,
+                             cudaStream_t st) {
+  if (stream) return ARA_OK;
+  if (!dev_out)
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)total,
+                                  cudaMemcpyDeviceToHost, st));
+  unsigned long long nc_after = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
+                                cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (nc_after != nc_before)
+    return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
+                nc_after - nc_before);
+  return ARA_OK;
+}
+
+// Where the net aggregate loss A(s) = min(max(s*unit - AggR, 0), AggL) (binary64, s grid units,
+// s*unit exact) is constant: A = 0 for s <= *zero_max, A = AggL for s >= *full_min.  Both by
+// bisection on the same binary64 expression the kernels evaluate, which is monotone in s.
+static void agg_bounds(double unit, double agg_ret, double agg_lim, unsigned long long* zero_max,
+                       unsigned long long* full_min) {
+  const unsigned long long top = 1ull << 53;  // year sums stay below 2^52 units
+  auto net = [&](unsigned long long s) { return (double)s * unit - agg_ret; };
+  // largest s in [0, top] with net(s) <= 0 (net(0) <= 0 always)
+  unsigned long long lo = 0, hi = top;
+  if (net(top) <= 0.0) {
+    lo = top;
+  } else {
+    while (hi - lo > 1) {
+      const unsigned long long mid = lo + (hi - lo) / 2;
+      if (net(mid) <= 0.0) lo = mid; else hi = mid;
+    }
+  }
+  *zero_max = lo;
+  // smallest s in [0, top] with net(s) >= AggL, or never
+  if (!(net(top) >= agg_lim)) {
+    *full_min = ~0ull;
+    return;
+  }
+  lo = 0;
+  hi = top;
+  if (net(0) >= agg_lim) {
+    *full_min = 0;
+    return;
+  }
+  while (hi - lo > 1) {
+    const unsigned long long mid = lo + (hi - lo) / 2;
+    if (net(mid) >= agg_lim) hi = mid; else lo = mid;
+  }
+  *full_min = hi;
+}
+
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
                         int64_t n, double* d_ylt) {
   TrialParams p;
@@ -743,6 +800,7 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   const int qe = year_grid_exponent((float)L.occ_lim, Y.max_len);
   p.q_scale = std::ldexp(1.0f, -qe);
   p.q_unit = std::ldexp(1.0, qe);
+  agg_bounds(p.q_unit, L.agg_ret, L.agg_lim, &p.agg_zero_max, &p.agg_full_min);
   if (L.band_log2w > 0) {
     for (const auto& v : Y.bands)
       if (v.log2w == L.band_log2w) {
@@ -912,26 +970,49 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   struct Group { int32_t first = 0, count = 0; int64_t units = 0, trials = 0; };
   Group g[4];
   int32_t band_row = 0;
+  unsigned long long nc_before = 0;
+  if (!stream)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
+                                  cudaMemcpyDeviceToHost, st));
+  // a layer whose own grid is many waves deep runs as its own launch (launch parameters in the
+  // constant bank, as ara_run); only small layers share a batched launch, where filling the GPU
+  // matters more than the items' parameters being read from global memory
+  const int64_t big_blocks = 32ll * ctx->sm_count * 4;
+  int32_t n_items = 0;
   for (int32_t k = 0; k < n_layers; ++k) {
     const int32_t i = order[k];
     const LayerDev& L = ctx->layers[layers[i]];
     TrialParams p = make_params(ctx, Y, L, t0, n, d_ylt + (int64_t)i * n);
+    const bool band = group(i) < 2;
+    const int64_t own_blocks = band ? (int64_t)p.n_bands * band_tiles(n) : (n + 7) / 8;
+    if (own_blocks >= big_blocks) {
+      if (band) {
+        p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
+        CUDA_TRY(ctx, launch_band(p, L.mask_words, ctx->cfg.precision, st));
+      } else {
+        CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision, inversion_mode(ctx),
+                                   false, st));
+      }
+      continue;
+    }
+    const int32_t kk = n_items++;
     Group& G = g[group(i)];
-    if (G.count == 0) G.first = k;
-    if (group(i) < 2) {
+    if (G.count == 0) G.first = kk;
+    if (band) {
       p.tiles = (int32_t)band_tiles(n);
       p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
-      begin[n_layers + k] = G.units;
-      begin[2 * (size_t)n_layers + k] = G.trials;
+      begin[n_layers + kk] = G.units;
+      begin[2 * (size_t)n_layers + kk] = G.trials;
       G.units += (int64_t)p.n_bands * p.tiles;
       G.trials += n;
     } else {
-      begin[k] = G.units;
+      begin[kk] = G.units;
       G.units += n;
     }
     G.count++;
-    items[k] = p;
+    items[kk] = p;
   }
+  if (n_items == 0) return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
   TrialParams* d_items = nullptr;
   int64_t* d_begin = nullptr;
   CUDA_TRY(ctx, mem_alloc(&d_items, n_layers, true, st));
@@ -943,10 +1024,6 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
                                 cudaMemcpyHostToDevice, st));
   CUDA_TRY(ctx, cudaMemcpyAsync(d_begin, begin.data(), sizeof(int64_t) * begin.size(),
                                 cudaMemcpyHostToDevice, st));
-  unsigned long long nc_before = 0;
-  if (!stream)
-    CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
-                                  cudaMemcpyDeviceToHost, st));
   for (int gi = 0; gi < 4; ++gi) {
     const Group& G = g[gi];
     if (G.count == 0) continue;
@@ -959,18 +1036,7 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
       CUDA_TRY(ctx, launch_trial_batch(d_items + G.first, d_begin + G.first, G.count, G.units,
                                        mw, ctx->cfg.precision, inversion_mode(ctx), st));
   }
-  if (stream) return ARA_OK;
-  if (!dev_out)
-    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)total,
-                                  cudaMemcpyDeviceToHost, st));
-  unsigned long long nc_after = 0;
-  CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
-                                cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  if (nc_after != nc_before)
-    return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
-                nc_after - nc_before);
-  return ARA_OK;
+  return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
 }
 
 ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {

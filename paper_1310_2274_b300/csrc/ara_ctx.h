@@ -21,6 +21,7 @@ using ara::YetDev;
 struct ara_ctx {
   ara_config cfg{};
   int device = 0;
+  int sm_count = 148;  // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   std::string detail;
   std::vector<YetDev> yets;

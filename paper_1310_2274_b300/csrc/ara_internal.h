@@ -121,6 +121,9 @@ struct TrialParams {
   // per-occurrence outputs (trial-major only), indexed by occurrence position - offsets[t0]
   float* olt;                // occurrence loss after occurrence terms, or null
   double* inc;               // increment of the year's net aggregate loss, or null
+  // A(S) = min(max(S - AggR, 0), AggL) for S = s grid units is 0 for s <= agg_zero_max and AggL
+  // for s >= agg_full_min (exact bounds of the binary64 formula), so increments there are 0
+  unsigned long long agg_zero_max, agg_full_min;
 };
 
 // Work counters are striped over kStatStripes copies (counter c of stripe s at

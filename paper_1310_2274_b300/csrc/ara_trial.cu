@@ -81,11 +81,18 @@ __device__ __forceinline__ void occurrence_outputs(const TrialParams& P, int64_t
     const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
     if (lane >= d) incl += t;
   }
-  const unsigned long long s1 = carry + incl;
-  const double a1 = fmin(fmax((double)s1 * P.q_unit - P.agg_ret, 0.0), P.agg_lim);
-  const double a0 = fmin(fmax((double)(s1 - un) * P.q_unit - P.agg_ret, 0.0), P.agg_lim);
-  if (in) P.inc[q - q0] = a1 - a0;
+  const unsigned long long s1 = carry + incl, s0 = s1 - un;
   carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+  if (!in) return;
+  // binary64 is slow on this part: below the retention and past the limit A is constant, so the
+  // formula runs only for occurrences that cross into or lie inside the layer
+  double d = 0.0;
+  if (s1 > P.agg_zero_max && s0 < P.agg_full_min) {
+    const double a1 = fmin(fmax((double)s1 * P.q_unit - P.agg_ret, 0.0), P.agg_lim);
+    const double a0 = fmin(fmax((double)s0 * P.q_unit - P.agg_ret, 0.0), P.agg_lim);
+    d = a1 - a0;
+  }
+  P.inc[q - q0] = d;
 }
 
 // The whole of Algorithm 1 for one trial (w-th of the launch item P), run by one warp.

@@ -147,3 +147,36 @@ def test_events_ragged_yet_with_empty_trials(ara, oracle):
     assert np.all(got[0][lens == 0] == 0.0) and np.all(got[1][lens == 0] == 0.0)
     assert empty[2].shape == (0,) and empty[3].shape == (0,)
     np.testing.assert_array_equal(empty[0], np.zeros(3))
+
+
+def test_increments_are_the_formula_on_the_devices_own_sums(ara, staged):
+    # S_k is the exact sum of the occurrence losses on the grid 2^e (e fixed by the longest trial
+    # and OccL so that a year fits in 52 bits); the increments must be A(S_k) - A(S_k - o_k) in
+    # binary64 bit for bit, including the regions where the kernel skips the formula
+    c, w, yet, elts, layer, ref = staged
+    max_len = int(np.diff(w.yet.offsets).max())
+    for agg_ret, agg_lim in [(w.terms.agg_ret, w.terms.agg_lim), (3.0e8 + 0.3, 7.7e7 + 0.1),
+                             (0.0, 1e15), (1e15, 1.0)]:
+        t = synth.Terms(w.terms.occ_ret, w.terms.occ_lim, agg_ret, agg_lim)
+        l2 = c.add_layer(elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+        try:
+            ylt, _, olt, inc = c.run_events(yet, l2, 0, 400, n_occ(w, 0, 400))
+        finally:
+            c.free_layer(l2)
+        e = int(np.ceil(np.log2(float(np.float32(t.occ_lim)) * max_len))) - 52
+        units = np.rint(olt.astype(np.float64) * 2.0 ** -e).astype(np.int64)
+        lens = np.diff(w.yet.offsets[:401])
+        trial = np.repeat(np.arange(400), lens)
+        s1 = np.cumsum(units)
+        first = np.r_[0, np.cumsum(lens)[:-1]]
+        s1 = s1 - np.repeat(np.r_[0, s1][first], lens)  # restart at every trial
+        s0 = s1 - units
+
+        def A(s):
+            return np.minimum(np.maximum(s.astype(np.float64) * 2.0 ** e - agg_ret, 0.0), agg_lim)
+
+        np.testing.assert_array_equal(inc, A(s1) - A(s0))
+        last = np.cumsum(lens) - 1
+        nz = lens > 0
+        np.testing.assert_array_equal(ylt[nz], A(s1[last[nz]]))
+        assert trial.shape == inc.shape
