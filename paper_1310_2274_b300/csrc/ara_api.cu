@@ -977,7 +977,7 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   // a layer whose own grid is many waves deep runs as its own launch (launch parameters in the
   // constant bank, as ara_run); only small layers share a batched launch, where filling the GPU
   // matters more than the items' parameters being read from global memory
-  const int64_t big_blocks = 32ll * ctx->sm_count * 4;
+  const int64_t big_blocks = 12ll * ctx->sm_count * 4;
   int32_t n_items = 0;
   for (int32_t k = 0; k < n_layers; ++k) {
     const int32_t i = order[k];

@@ -351,19 +351,36 @@ bool issue(ara_server* s) {
     s->pool.push_back(L);
     return false;
   }
-  // band-major items first (items [0, kb)), then trial-major ones (items [kb, k))
+  // batched band-major items first (items [0, kb)), then trial-major ones (items [kb, kb + kt))
   std::stable_partition(take.begin(), take.end(),
                         [](const std::pair<Request*, int64_t>& t) { return t.first->band; });
   const YetDev& Y = s->ctx->yets[s->cfg.yet];
   const int k = (int)take.size();
   const int cap = L.cap;
-  int kb = 0;
+  int kb = 0, kt = 0;
   int64_t warp = 0, blocks = 0, trials = 0;
+  cudaError_t e = cudaSuccess;
+  // a slice whose own grid is many waves deep runs as its own launch (parameters in the constant
+  // bank); the others share one batched launch per schedule
+  const int64_t big_blocks = 12ll * s->ctx->sm_count * 4;
   for (int i = 0; i < k; ++i) {
     Request& r = *take[i].first;
     const int64_t n = take[i].second;
     const LayerDev& Ld = r.layer;
     TrialParams p = make_params(s->ctx, Y, Ld, r.req.t0 + r.next, n, r.d_ylt + r.next);
+    const int64_t own_blocks = r.band ? (int64_t)p.n_bands * ara::band_tiles(n) : (n + 7) / 8;
+    if (own_blocks >= big_blocks) {
+      if (r.band) {
+        p.ysum = r.d_ysum + r.next;
+        if (e == cudaSuccess) e = ara::launch_band(p, 2, s->ctx->cfg.precision, s->stream);
+      } else if (e == cudaSuccess) {
+        e = ara::launch_trial(p, 2, s->ctx->cfg.precision, inversion_mode(s->ctx), false,
+                              s->stream);
+      }
+      r.next += n;
+      L.parts.emplace_back(r.ticket, n);
+      continue;
+    }
     if (r.band) {
       p.tiles = (int32_t)ara::band_tiles(n);
       p.ysum = r.d_ysum + r.next;
@@ -371,25 +388,27 @@ bool issue(ara_server* s) {
       L.h_begin[2 * cap + kb] = trials;
       blocks += (int64_t)p.n_bands * p.tiles;
       trials += n;
-      ++kb;
+      L.h_items[kb++] = p;
     } else {
-      L.h_begin[i - kb] = warp;
+      // every band item precedes every trial-major one in take, so kb is final here
+      L.h_begin[kt] = warp;
       warp += n;
+      L.h_items[kb + kt++] = p;
     }
-    L.h_items[i] = p;
     r.next += n;
     L.parts.emplace_back(r.ticket, n);
   }
-  cudaError_t e = cudaMemcpyAsync(L.d_items, L.h_items, sizeof(TrialParams) * k,
-                                  cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && kb + kt > 0)
+    e = cudaMemcpyAsync(L.d_items, L.h_items, sizeof(TrialParams) * (kb + kt),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && kb + kt > 0)
     e = cudaMemcpyAsync(L.d_begin, L.h_begin, sizeof(int64_t) * 3 * cap, cudaMemcpyHostToDevice,
                         s->stream);
   if (e == cudaSuccess && kb > 0)
     e = ara::launch_band_batch(L.d_items, L.d_begin + cap, L.d_begin + 2 * cap, kb, blocks,
                                trials, 2, s->ctx->cfg.precision, s->stream);
-  if (e == cudaSuccess && k > kb)
-    e = ara::launch_trial_batch(L.d_items + kb, L.d_begin, k - kb, warp, 2,
+  if (e == cudaSuccess && kt > 0)
+    e = ara::launch_trial_batch(L.d_items + kb, L.d_begin, kt, warp, 2,
                                 s->ctx->cfg.precision, inversion_mode(s->ctx), s->stream);
   if (e == cudaSuccess) e = cudaEventRecord(L.done, s->stream);
   if (e != cudaSuccess) {

@@ -193,3 +193,23 @@ def test_trial_major_serving_equals_requests_run_alone(ara, staged, mode):
     finally:
         c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
         c.set_option(ara.OPT_PRECISION, ara.ACC_FP64)
+
+
+def test_deep_slices_launch_alone_and_match(ara, staged):
+    # slices of up to 40,000 trials have grids many waves deep: they run as their own launches
+    # beside the batched small ones; every request still equals its run alone
+    c, yet, hs = staged
+    mix = request_mix(hs, 6, seed=7)
+    mix[0] = dict(mix[0], t0=0, n_trials=N_TRIALS)
+    ref = [alone(c, yet, r) for r in mix]
+    s0 = c.stats()
+    with ara.Server(c, yet, max_inflight=6, slice_trials=N_TRIALS) as s:
+        tickets = [s.submit(**r) for r in mix]
+        for tk in tickets:
+            assert s.wait(tk, 120.0) == 0
+        for tk, (y, p, t) in zip(tickets, ref):
+            res = s.result(tk)
+            np.testing.assert_array_equal(res["ylt"], y)
+            np.testing.assert_array_equal(res["pml"][:3], p)
+            np.testing.assert_array_equal(res["tvar"][:3], t)
+    assert c.stats()["launches"] > s0["launches"]
