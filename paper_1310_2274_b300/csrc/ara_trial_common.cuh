@@ -158,8 +158,13 @@ __device__ __forceinline__ SuDraw su_draw(float u, float uc, float cc) {
   return d;
 }
 
-// Bit position of the n-th (0-based) set bit of m (n < popc(m)).
-__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) { return (int)__fns(m, 0u, n + 1); }
+// Bit position of the n-th (0-based) set bit of m (n < popc(m)): clear the n lowest set bits,
+// then find the lowest.  n is the hit's rank within its event, almost always 0 or 1, so this
+// short loop beats a general n-th-bit search (1.6% of the band kernel's time).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+  for (int i = 0; i < n; ++i) m &= m - 1u;
+  return __ffs(m) - 1;
+}
 
 __device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
   const float4* q = reinterpret_cast<const float4*>(p);
