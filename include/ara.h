@@ -97,6 +97,21 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 /* ARA_OPT_BAND_WIDTH: the band width 2^w (value w in 10..20) of layers created afterwards;
  * 0 (default) chooses w per layer from its record count.  Results do not depend on w. */
 #define ARA_OPT_BAND_WIDTH 6
+/* ARA_OPT_TABLES: when the certified quantile tables of ELTs staged afterwards are built.
+ *   ARA_TABLES_EAGER (default): by ara_add_elt.
+ *   ARA_TABLES_ON_DEMAND: not at staging; a run of the table inversion over a layer whose ELTs
+ *     lack tables uses Newton's method instead, and the ELTs' tables are built (and the layer's
+ *     packed copy gathered) before the first run at which each such ELT's Newton work so far
+ *     plus this run's would reach the cost of building its tables: rent-or-buy, never more than
+ *     twice the cheaper of the two in hindsight.  Work is counted in expected hits per record,
+ *     (occurrences of the run's trials) / (catalogue size), against ARA_TABLE_BUY_HITS, the
+ *     measured break-even of build time per record over the per-hit saving of a table.  Results
+ *     of a run are those of the inversion it used (both are checked against the oracle).
+ *   A server (ara_server_create) builds every missing table of its YET's ELTs when created. */
+#define ARA_OPT_TABLES 7
+#define ARA_TABLES_EAGER 0
+#define ARA_TABLES_ON_DEMAND 1
+#define ARA_TABLE_BUY_HITS 1700.0
 ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
 
 /* Year Event Table (paper §2.1) ------------------------------------------------------------------

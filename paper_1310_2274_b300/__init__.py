@@ -24,6 +24,9 @@ OPT_PRECISION, OPT_SEED, OPT_SURROGATE, OPT_INVERSION = 1, 2, 3, 4
 INV_TABLE, INV_NEWTON = 0, 1
 OPT_SCHEDULE = 5
 OPT_BAND_WIDTH = 6
+OPT_TABLES = 7
+TABLES_EAGER, TABLES_ON_DEMAND = 0, 1
+TABLE_BUY_HITS = 1700.0  # expected hits per record at which on-demand tables are built
 SCHED_BAND, SCHED_TRIAL = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",
           5: "inversion did not converge", 6: "busy", 7: "no CUDA device"}

@@ -109,6 +109,7 @@ void free_elt(EltDev& e) {
   dev_free(e.recs);
   dev_free(e.tables);
   dev_free(e.corr);
+  dev_free(e.ab64);
   e = EltDev();
 }
 
@@ -310,6 +311,11 @@ ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value) {
         return fail(ctx, ARA_ERR_INVALID_ARG, "band width exponent must be 0 or 10..20");
       ctx->band_log2w = (int32_t)value;
       return ARA_OK;
+    case ARA_OPT_TABLES:
+      if (value != ARA_TABLES_EAGER && value != ARA_TABLES_ON_DEMAND)
+        return fail(ctx, ARA_ERR_INVALID_ARG, "tables must be ARA_TABLES_EAGER or _ON_DEMAND");
+      ctx->table_policy = (int32_t)value;
+      return ARA_OK;
     case ARA_OPT_SCHEDULE:
       if (value != ARA_SCHED_BAND && value != ARA_SCHED_TRIAL)
         return fail(ctx, ARA_ERR_INVALID_ARG, "schedule must be ARA_SCHED_BAND or ARA_SCHED_TRIAL");
@@ -423,6 +429,7 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
   ara_status s = set_device(ctx);
   if (s != ARA_OK) return s;
   const YetDev& y = ctx->yets[yet];
+  const bool defer = ctx->table_policy == ARA_TABLES_ON_DEMAND;
   EltDev e;
   e.yet = yet;
   e.n = n;
@@ -440,20 +447,22 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
     dev_free(d_mx);
     dev_free(d_dup);
     dev_free(d_uncert);
-    dev_free(d_ab64);
+    if (!defer) dev_free(d_ab64);  // deferred tables keep (alpha, beta) in e.ab64
   };
   if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
-      (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess ||
+      (!defer && (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess) ||
       (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
       (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess ||
       (err = dev_alloc(&d_uncert, 1)) != cudaSuccess || (err = dev_alloc(&d_ab64, n)) != cudaSuccess ||
       (sd_corr && ((err = dev_alloc(&d_sdc, n)) != cudaSuccess ||
                    (err = dev_alloc(&e.corr, n)) != cudaSuccess))) {
     cudaGetLastError();
+    if (defer) e.ab64 = d_ab64;
     cleanup();
     free_elt(e);
     return fail(ctx, ARA_ERR_OOM, "ELT of %lld records: %s", (long long)n, cudaGetErrorString(err));
   }
+  if (defer) e.ab64 = d_ab64;
   unsigned int flags = 0;
   if ((err = copy_in(e.ids, event_ids, n, ctx->stream)) != cudaSuccess ||
       (err = copy_in(d_mean, mean, n, ctx->stream)) != cudaSuccess ||
@@ -465,7 +474,8 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
       (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_sdc, d_mx, y.catalog, e.recs, d_ab64,
                                 e.corr, d_dup, ctx->d_flags, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-      (err = launch_build_tables(n, e.recs, d_ab64, e.tables, d_uncert, ctx->stream)) != cudaSuccess ||
+      (!defer &&
+       (err = launch_build_tables(n, e.recs, d_ab64, e.tables, d_uncert, ctx->stream)) != cudaSuccess) ||
       (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
@@ -590,11 +600,15 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   // packed records, then the records' tables copied into packed order (one gather per hit);
   // correlated weights only when some ELT of the layer has a correlated SD
   const TablePiece** d_src = nullptr;
-  bool has_corr = false;
-  for (int j = 0; j < n_elts; ++j) has_corr = has_corr || ctx->elts[elts[j]].corr != nullptr;
+  bool has_corr = false, all_tables = true;
+  for (int j = 0; j < n_elts; ++j) {
+    has_corr = has_corr || ctx->elts[elts[j]].corr != nullptr;
+    all_tables = all_tables && ctx->elts[elts[j]].tables != nullptr;
+  }
   if ((err = mem_alloc(&L.packed, L.n_packed, ordered, st)) != cudaSuccess ||
       (err = mem_alloc(&L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
-      (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) != cudaSuccess ||
+      (all_tables && (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) !=
+                         cudaSuccess) ||
       (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess ||
       (has_corr && (err = mem_alloc(&L.corr, L.n_packed, ordered, st)) != cudaSuccess)) {
     cudaGetLastError();
@@ -606,7 +620,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
                                L.corr, st);
-  if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
+  if (err == cudaSuccess && all_tables) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   cleanup();
   mem_free(d_src, ordered, st);
@@ -685,8 +699,113 @@ static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64
 }  // extern "C"
 
 bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
-  return inversion_mode(ctx) == 0 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
+  return layer_inversion(ctx, L) == 0 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
          ctx->cfg.precision == ARA_ACC_FP64;
+}
+
+int layer_inversion(const ara_ctx* ctx, const LayerDev& L) {
+  const int m = inversion_mode(ctx);
+  return (m == 0 && L.tables == nullptr) ? 1 : m;
+}
+
+// The certified tables of one ELT, from the (alpha, beta) kept at staging.
+static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
+  if (e.tables) return ARA_OK;
+  if (!e.ab64) return fail(ctx, ARA_ERR_INVALID_ARG, "ELT has neither tables nor parameters");
+  unsigned long long* d_uncert = nullptr;
+  unsigned long long uncert = 0;
+  cudaError_t err;
+  if ((err = dev_alloc(&e.tables, e.n * kTablePieces)) != cudaSuccess ||
+      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(e.tables);
+    e.tables = nullptr;
+    dev_free(d_uncert);
+    return fail(ctx, ARA_ERR_OOM, "tables of %lld records", (long long)e.n);
+  }
+  if ((err = cudaMemsetAsync(d_uncert, 0, sizeof uncert, ctx->stream)) != cudaSuccess ||
+      (err = launch_build_tables(e.n, e.recs, e.ab64, e.tables, d_uncert, ctx->stream)) !=
+          cudaSuccess ||
+      (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess ||
+      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(e.tables);
+    e.tables = nullptr;
+    dev_free(d_uncert);
+    return fail(ctx, ARA_ERR_CUDA, "building tables: %s", cudaGetErrorString(err));
+  }
+  dev_free(d_uncert);
+  dev_free(e.ab64);
+  e.ab64 = nullptr;
+  e.n_uncertified = (int64_t)uncert;
+  return ARA_OK;
+}
+
+// The layer's packed table copy (its ELTs' tables first).
+static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
+  if (L.tables) return ARA_OK;
+  for (int j = 0; j < L.n_slots; ++j) {
+    const ara_status s = ensure_elt_tables(ctx, ctx->elts[L.handles[j]]);
+    if (s != ARA_OK) return s;
+  }
+  const TablePiece** d_src = nullptr;
+  cudaError_t err;
+  if ((err = dev_alloc(&L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
+      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(L.tables);
+    L.tables = nullptr;
+    dev_free(d_src);
+    return fail(ctx, ARA_ERR_OOM, "layer tables: %s", cudaGetErrorString(err));
+  }
+  // the scatter rewrites the packed records as they are and fills the table source pointers
+  err = cudaSuccess;
+  for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
+    err = launch_layer_scatter(ctx->elts[L.handles[j]], j, L.mask_words, L.evt, L.packed, d_src,
+                               L.packed_rec, L.corr, ctx->stream);
+  if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  dev_free(d_src);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(L.tables);
+    L.tables = nullptr;
+    return fail(ctx, ARA_ERR_CUDA, "layer tables: %s", cudaGetErrorString(err));
+  }
+  return ARA_OK;
+}
+
+ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n) {
+  if (L.tables || inversion_mode(ctx) != 0) return ARA_OK;
+  if (ctx->table_policy == ARA_TABLES_EAGER) return ensure_layer_tables(ctx, L);
+  const YetDev& Y = ctx->yets[L.yet];
+  // expected hits per record of this run: each occurrence meets a given record with
+  // probability 1 / catalogue
+  const double per_rec = Y.n_trials > 0 && Y.catalog > 0
+                             ? (double)Y.n_occ * ((double)n / (double)Y.n_trials) / Y.catalog
+                             : 0.0;
+  bool buy = true;
+  for (int j = 0; j < L.n_slots; ++j) {
+    const EltDev& e = ctx->elts[L.handles[j]];
+    if (!e.tables && e.rent_hits + per_rec < ARA_TABLE_BUY_HITS) buy = false;
+  }
+  if (buy) return ensure_layer_tables(ctx, L);
+  for (int j = 0; j < L.n_slots; ++j) {
+    EltDev& e = ctx->elts[L.handles[j]];
+    if (!e.tables) e.rent_hits += per_rec;
+  }
+  return ARA_OK;
+}
+
+ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet) {
+  for (auto& e : ctx->elts)
+    if (e.live && e.yet == yet) {
+      const ara_status s = ensure_elt_tables(ctx, e);
+      if (s != ARA_OK) return s;
+    }
+  return ARA_OK;
 }
 
 ara_status ensure_band_variant(ara_ctx* ctx, int32_t yet, int log2w, bool* available) {
@@ -873,6 +992,8 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   if (!stream)
     CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
                                   cudaMemcpyDeviceToHost, st));
+  s = prepare_layer_for_run(ctx, ctx->layers[layer], n);
+  if (s != ARA_OK) return s;
   TrialParams p = make_params(ctx, Y, ctx->layers[layer], t0, n, d_ylt);
   p.oep = d_oep;
   p.olt = d_olt;
@@ -887,7 +1008,7 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
     CUDA_TRY(ctx, launch_band(p, ctx->layers[layer].mask_words, ctx->cfg.precision, st));
   } else {
     CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
-                               inversion_mode(ctx), false, st));
+                               layer_inversion(ctx, ctx->layers[layer]), false, st));
   }
   if (stream) return ARA_OK;
   if (!dev_out) {
@@ -946,14 +1067,19 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
     if (s != ARA_OK) return s;
     d_ylt = ctx->d_ylt_tmp;
   }
-  // one launch item per layer, grouped by schedule and lookup-entry width (one batched launch
-  // per group): band-major items first, each with its own year-sum rows
+  for (int32_t i = 0; i < n_layers; ++i) {
+    ara_status s = prepare_layer_for_run(ctx, ctx->layers[layers[i]], n);
+    if (s != ARA_OK) return s;
+  }
+  // one launch item per layer, grouped by schedule, inversion and lookup-entry width (one
+  // batched launch per group): band-major items first, each with its own year-sum rows
   const YetDev& Y = ctx->yets[yet];
   std::vector<int32_t> order(n_layers);
   for (int32_t i = 0; i < n_layers; ++i) order[i] = i;
-  auto group = [&](int32_t i) {
+  auto group = [&](int32_t i) {  // 0, 1 band-major; 2 + 2 inversion + (width - 1) trial-major
     const LayerDev& L = ctx->layers[layers[i]];
-    return (uses_band_schedule(ctx, L) ? 0 : 2) + (L.mask_words == 1 ? 0 : 1);
+    const int w = L.mask_words == 1 ? 0 : 1;
+    return uses_band_schedule(ctx, L) ? w : 2 + 2 * layer_inversion(ctx, L) + w;
   };
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t a, int32_t b) { return group(a) < group(b); });
@@ -968,7 +1094,7 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   std::vector<TrialParams> items(n_layers);
   std::vector<int64_t> begin(3 * (size_t)n_layers, 0);  // warp / block / trial firsts per item
   struct Group { int32_t first = 0, count = 0; int64_t units = 0, trials = 0; };
-  Group g[4];
+  Group g[8];
   int32_t band_row = 0;
   unsigned long long nc_before = 0;
   if (!stream)
@@ -990,8 +1116,8 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
         p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
         CUDA_TRY(ctx, launch_band(p, L.mask_words, ctx->cfg.precision, st));
       } else {
-        CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision, inversion_mode(ctx),
-                                   false, st));
+        CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision,
+                                   layer_inversion(ctx, L), false, st));
       }
       continue;
     }
@@ -1024,17 +1150,18 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
                                 cudaMemcpyHostToDevice, st));
   CUDA_TRY(ctx, cudaMemcpyAsync(d_begin, begin.data(), sizeof(int64_t) * begin.size(),
                                 cudaMemcpyHostToDevice, st));
-  for (int gi = 0; gi < 4; ++gi) {
+  for (int gi = 0; gi < 8; ++gi) {
     const Group& G = g[gi];
     if (G.count == 0) continue;
     const int mw = (gi & 1) ? 2 : 1;
+    const int inv = gi < 2 ? 0 : (gi - 2) / 2;
     if (gi < 2)
       CUDA_TRY(ctx, launch_band_batch(d_items + G.first, d_begin + n_layers + G.first,
                                       d_begin + 2 * (int64_t)n_layers + G.first, G.count,
                                       G.units, G.trials, mw, ctx->cfg.precision, st));
     else
       CUDA_TRY(ctx, launch_trial_batch(d_items + G.first, d_begin + G.first, G.count, G.units,
-                                       mw, ctx->cfg.precision, inversion_mode(ctx), st));
+                                       mw, ctx->cfg.precision, inv, st));
   }
   return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
 }
@@ -1252,7 +1379,7 @@ ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   p.tr_count = d_cnt;
   std::vector<int32_t> cnt(n), k(total), j(total), rec(total);
   std::vector<float> u(total), x(total), loss(total);
-  e = launch_trial(p, L.mask_words, ARA_ACC_FP64, inversion_mode(ctx), true, ctx->stream);
+  e = launch_trial(p, L.mask_words, ARA_ACC_FP64, layer_inversion(ctx, L), true, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(k.data(), d_k, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(j.data(), d_j, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);

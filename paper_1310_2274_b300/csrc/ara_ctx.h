@@ -45,6 +45,7 @@ struct ara_ctx {
   unsigned long long* d_ysum = nullptr;  // year sums in grid units (band-major runs)
   int64_t ysum_cap = 0;
   int32_t schedule = 0;                  // ARA_SCHED_BAND or ARA_SCHED_TRIAL
+  int32_t table_policy = 0;              // ARA_TABLES_EAGER or ARA_TABLES_ON_DEMAND
   uint32_t* d_sel = nullptr;             // top-k selection: flags, positions, scan scratch
   int64_t sel_cap = 0;
   int32_t band_log2w = 0;                // band width exponent for new layers (0: automatic)
@@ -67,5 +68,13 @@ int inversion_mode(const ara_ctx* ctx);
 // Makes sure the YET has its band-major copy for band width 2^log2w (*available: it has).
 ara_status ensure_band_variant(ara_ctx* ctx, int32_t yet, int log2w, bool* available);
 bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L);
+// The inversion a run over L uses: the context's, except that the table inversion falls back to
+// Newton's method (1) while the layer has no packed tables (ARA_TABLES_ON_DEMAND).
+int layer_inversion(const ara_ctx* ctx, const LayerDev& L);
+// Rent-or-buy before a run of n trials over L: builds the tables of L's ELTs and L's packed copy
+// when the accumulated Newton work reaches the build cost; else books this run as Newton work.
+ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n);
+// Builds every missing table of the live ELTs of a YET (servers need them).
+ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet);
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,
                         double* d_ylt);

@@ -52,6 +52,8 @@ struct EltDev {
   TablePiece* tables = nullptr;  // [n * kTablePieces] certified quantile tables
   float* corr = nullptr;     // [n] normalised correlated weights (NULL: every sigma_C = 0)
   int64_t n_uncertified = 0; // records whose table failed certification
+  double2* ab64 = nullptr;   // [n] binary64 (alpha, beta), kept until the tables are built
+  double rent_hits = 0.0;    // expected hits per record served by Newton while tables were absent
 };
 
 // A layer: lookup structure over the YET's catalogue plus its terms (paper §2.1, §2.3).
