@@ -27,6 +27,7 @@ OPT_BAND_WIDTH = 6
 OPT_TABLES = 7
 TABLES_EAGER, TABLES_ON_DEMAND = 0, 1
 TABLE_BUY_HITS = 1700.0  # expected hits per record at which on-demand tables are built
+OPT_STREAM_CHUNK = 8
 SCHED_BAND, SCHED_TRIAL = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",
           5: "inversion did not converge", 6: "busy", 7: "no CUDA device"}
@@ -102,6 +103,7 @@ _SIGNATURES = {
     "ara_last_error_detail": ([_P, C.c_char_p, C.c_size_t], C.c_int),
     "ara_set_option": ([_P, _I32, _I64], C.c_int),
     "ara_create_yet": ([_P, _I64, _P, _P, _P, _I32, C.POINTER(_I32)], C.c_int),
+    "ara_create_yet_host": ([_P, _I64, _P, _P, _P, _I32, C.POINTER(_I32)], C.c_int),
     "ara_free_yet": ([_P, _I32], C.c_int),
     "ara_add_elt": ([_P, _I32, _I64, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
     "ara_add_elt_corr": ([_P, _I32, _I64, _P, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
@@ -196,6 +198,7 @@ class Context:
         if st != 0:
             raise AraError(st, "ara_create")
         self._h = h
+        self._host_yets = {}  # host-resident YETs: the arrays the library reads, kept alive
 
     # -- plumbing ------------------------------------------------------------------------------
     @property
@@ -290,8 +293,23 @@ class Context:
                                         agg_ret, agg_lim, C.byref(out)))
         return out.value
 
+    def create_yet_host(self, offsets, event_ids, timestamps, catalog_size: int) -> int:
+        """A YET whose ids and timestamps stay in host memory and are streamed by each run (one
+        pass per staging); the arrays (page-locked for copy/compute overlap, e.g. a pinned
+        torch tensor's numpy view) are referenced, not copied, until free_yet."""
+        off = _np(offsets, np.int64)
+        ids = _np(event_ids, np.int32)
+        ts = _np(timestamps, np.float32)
+        n_trials = int(off.shape[0]) - 1
+        out = _I32(-1)
+        self._check(lib().ara_create_yet_host(self._h, n_trials, _ptr(off), _ptr(ids), _ptr(ts),
+                                              int(catalog_size), C.byref(out)))
+        self._host_yets[out.value] = (off, ids, ts)
+        return out.value
+
     def free_yet(self, yet: int):
         self._check(lib().ara_free_yet(self._h, yet))
+        self._host_yets.pop(yet, None)
 
     def free_elt(self, elt: int):
         self._check(lib().ara_free_elt(self._h, elt))

@@ -273,6 +273,16 @@ void ara_destroy(ara_ctx* ctx) {
   dev_free(ctx->mlp_G);
   dev_free(ctx->mlp_W);
   dev_free(ctx->mlp_bound);
+  for (int b = 0; b < 2; ++b) {
+    dev_free(ctx->d_sids[b]);
+    dev_free(ctx->d_sts[b]);
+    if (ctx->ev_ready[b]) cudaEventDestroy(ctx->ev_ready[b]);
+    if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
+  }
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   cudaGetLastError();
   delete ctx;
@@ -310,6 +320,11 @@ ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value) {
       if (value != 0 && (value < 10 || value > 20))
         return fail(ctx, ARA_ERR_INVALID_ARG, "band width exponent must be 0 or 10..20");
       ctx->band_log2w = (int32_t)value;
+      return ARA_OK;
+    case ARA_OPT_STREAM_CHUNK:
+      if (value < 1024 || value > ((int64_t)1 << 30))
+        return fail(ctx, ARA_ERR_INVALID_ARG, "stream chunk must be 1024 .. 2^30 occurrences");
+      ctx->stream_chunk = value;
       return ARA_OK;
     case ARA_OPT_TABLES:
       if (value != ARA_TABLES_EAGER && value != ARA_TABLES_ON_DEMAND)
@@ -398,6 +413,54 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   }
   y.live = true;
   ctx->yets.push_back(y);
+  *yet_out = (int32_t)ctx->yets.size() - 1;
+  return ARA_OK;
+}
+
+ara_status ara_create_yet_host(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_offsets,
+                               const int32_t* event_ids, const float* timestamps,
+                               int32_t catalog_size, int32_t* yet_out) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!yet_out) return fail(ctx, ARA_ERR_INVALID_ARG, "yet_out is NULL");
+  if (n_trials < 0) return fail(ctx, ARA_ERR_INVALID_ARG, "n_trials < 0");
+  if (catalog_size <= 0) return fail(ctx, ARA_ERR_INVALID_ARG, "catalog_size <= 0");
+  if (!trial_offsets) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets is NULL");
+  if (is_device_ptr(trial_offsets) || (event_ids && is_device_ptr(event_ids)) ||
+      (timestamps && is_device_ptr(timestamps)))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "a host-resident YET takes host arrays");
+  ara_status s = set_device(ctx);
+  if (s != ARA_OK) return s;
+  YetDev y;
+  y.host = true;
+  y.h_off.assign(trial_offsets, trial_offsets + n_trials + 1);
+  if (y.h_off[0] != 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets[0] != 0");
+  int64_t max_len = 0;
+  for (int64_t i = 0; i < n_trials; ++i) {
+    const int64_t len = y.h_off[(size_t)i + 1] - y.h_off[(size_t)i];
+    if (len < 0)
+      return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets decrease at trial %lld", (long long)i);
+    max_len = std::max(max_len, len);
+  }
+  const int64_t n_occ = y.h_off[(size_t)n_trials];
+  if (n_occ > 0 && (!event_ids || !timestamps))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "event_ids or timestamps is NULL");
+  if (n_occ >= ((int64_t)1 << 40)) return fail(ctx, ARA_ERR_INVALID_ARG, "YET too large");
+  y.n_trials = n_trials;
+  y.n_occ = n_occ;
+  y.catalog = catalog_size;
+  y.max_len = max_len;
+  y.h_ids = event_ids;
+  y.h_ts = timestamps;
+  cudaError_t e;
+  if ((e = dev_alloc(&y.offsets, n_trials + 1)) != cudaSuccess ||
+      (e = copy_in(y.offsets, y.h_off.data(), n_trials + 1, ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    free_yet(y);
+    return fail(ctx, ARA_ERR_CUDA, "staging YET offsets: %s", cudaGetErrorString(e));
+  }
+  y.live = true;
+  ctx->yets.push_back(std::move(y));
   *yet_out = (int32_t)ctx->yets.size() - 1;
   return ARA_OK;
 }
@@ -811,6 +874,7 @@ ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet) {
 ara_status ensure_band_variant(ara_ctx* ctx, int32_t yet, int log2w, bool* available) {
   *available = false;
   YetDev& Y = ctx->yets[yet];
+  if (Y.host) return ARA_OK;  // a streamed YET runs trial-major
   if (!band_layout_fits(Y, log2w)) return ARA_OK;
   for (int v = 0; v < kMaxBandVariants; ++v)
     if (Y.bands[v].log2w == log2w) {
@@ -940,6 +1004,71 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
 
 extern "C" {
 
+// A run over a host-resident YET: trials in chunks of whole trials (up to ctx->stream_chunk
+// occurrences), each chunk's ids and timestamps copied on the copy stream into one of two device
+// buffers while the previous chunk is validated and run on st; the run of a chunk skips its work
+// if any chunk so far failed validation.  Outputs are device pointers for trials [t0, t0 + n).
+static ara_status run_streamed(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
+                               int64_t n, double* d_ylt, double* d_oep, float* d_olt,
+                               double* d_inc, cudaStream_t st) {
+  const int64_t cap = std::max<int64_t>(ctx->stream_chunk, Y.max_len);
+  if (cap > ctx->stream_cap) {
+    for (int b = 0; b < 2; ++b) {
+      dev_free(ctx->d_sids[b]);
+      dev_free(ctx->d_sts[b]);
+      ctx->d_sids[b] = nullptr;
+      ctx->d_sts[b] = nullptr;
+    }
+    ctx->stream_cap = 0;
+    for (int b = 0; b < 2; ++b)
+      CUDA_TRY(ctx, dev_alloc(&ctx->d_sids[b], cap));
+    for (int b = 0; b < 2; ++b)
+      CUDA_TRY(ctx, dev_alloc(&ctx->d_sts[b], cap));
+    ctx->stream_cap = cap;
+  }
+  if (!ctx->copy_stream)
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b) {
+    if (!ctx->ev_ready[b])
+      CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_ready[b], cudaEventDisableTiming));
+    if (!ctx->ev_free[b])
+      CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));  // both buffers free once st gets here
+  }
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), st));
+  const int64_t q_first = Y.h_off[(size_t)t0];
+  int k = 0;
+  for (int64_t tb = t0; tb < t0 + n; ++k) {
+    int64_t te = tb + 1;  // whole trials up to cap occurrences (a trial never exceeds cap)
+    while (te < t0 + n && Y.h_off[(size_t)te + 1] - Y.h_off[(size_t)tb] <= cap) ++te;
+    const int64_t ob = Y.h_off[(size_t)tb], len = Y.h_off[(size_t)te] - ob;
+    const int b = k & 1;
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
+    if (len > 0) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sids[b], Y.h_ids + ob, sizeof(int32_t) * (size_t)len,
+                                    cudaMemcpyHostToDevice, ctx->copy_stream));
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sts[b], Y.h_ts + ob, sizeof(float) * (size_t)len,
+                                    cudaMemcpyHostToDevice, ctx->copy_stream));
+    }
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_ready[b], ctx->copy_stream));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_ready[b], 0));
+    CUDA_TRY(ctx, launch_validate_yet_range(ctx->d_sids[b], ctx->d_sts[b], ob, Y.offsets, tb,
+                                            te - tb, Y.catalog, ctx->d_flags, st));
+    TrialParams p = make_params(ctx, Y, L, tb, te - tb, d_ylt + (tb - t0));
+    p.ids = ctx->d_sids[b];
+    p.occ_base = ob;
+    p.abort_flag = ctx->d_flags;
+    p.oep = d_oep ? d_oep + (tb - t0) : nullptr;
+    p.olt = d_olt ? d_olt + (ob - q_first) : nullptr;
+    p.inc = d_inc ? d_inc + (ob - q_first) : nullptr;
+    CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision, layer_inversion(ctx, L),
+                               false, st));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));
+    tb = te;
+  }
+  return ARA_OK;
+}
+
 ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
                           double* ylt, double* oep, float* olt, double* inc, void* stream) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
@@ -953,6 +1082,8 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
       (inc && is_device_ptr(inc) != dev_out))
     return fail(ctx, ARA_ERR_INVALID_ARG, "outputs must all be host or all device memory");
   const bool per_occ = olt != nullptr || inc != nullptr;
+  if (ctx->yets[yet].host && stream)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "runs over a host-resident YET are blocking");
   if (inc && ctx->cfg.precision != ARA_ACC_FP64)
     return fail(ctx, ARA_ERR_INVALID_ARG, "occurrence increments need ARA_ACC_FP64 year sums");
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
@@ -999,7 +1130,10 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   p.olt = d_olt;
   p.inc = d_inc;
   // per-occurrence outputs are written in trial order, so they keep the trial-major schedule
-  if (!per_occ && uses_band_schedule(ctx, ctx->layers[layer])) {
+  if (Y.host) {
+    s = run_streamed(ctx, Y, ctx->layers[layer], t0, n, d_ylt, d_oep, d_olt, d_inc, st);
+    if (s != ARA_OK) return s;
+  } else if (!per_occ && uses_band_schedule(ctx, ctx->layers[layer])) {
     // year sums (8 B per trial), then the OEP maxima (4 B per trial) in the same scratch
     s = ensure_ysum(ctx, oep ? n + (n + 1) / 2 : n);
     if (s != ARA_OK) return s;
@@ -1025,9 +1159,18 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
                                     cudaMemcpyDeviceToHost, st));
   }
   unsigned long long nc_after = 0;
+  unsigned int yet_flags = 0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
                                 cudaMemcpyDeviceToHost, st));
+  if (Y.host)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&yet_flags, ctx->d_flags, sizeof yet_flags,
+                                  cudaMemcpyDeviceToHost, st));
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (yet_flags)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
+                (yet_flags & 1) ? " event id outside [0, catalog_size)" : "",
+                (yet_flags & 2) ? " timestamps decrease within a trial" : "",
+                (yet_flags & 4) ? " NaN timestamp" : "");
   if (nc_after != nc_before)
     return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
                 nc_after - nc_before);
@@ -1067,6 +1210,8 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
     if (s != ARA_OK) return s;
     d_ylt = ctx->d_ylt_tmp;
   }
+  if (ctx->yets[yet].host)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "a host-resident YET runs one layer per call");
   for (int32_t i = 0; i < n_layers; ++i) {
     ara_status s = prepare_layer_for_run(ctx, ctx->layers[layers[i]], n);
     if (s != ARA_OK) return s;
@@ -1346,6 +1491,8 @@ ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   if (!n_hits || max_hits < 0 || (max_hits > 0 && (!hit_trial || !hit_k || !hit_j || !hit_rec ||
                                                      !hit_u || !hit_x || !hit_loss)) || !ylt)
     return fail(ctx, ARA_ERR_INVALID_ARG, "NULL trace buffer");
+  if (ctx->yets[yet].host)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "tracing needs a device-resident YET");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const YetDev& Y = ctx->yets[yet];
   const LayerDev& L = ctx->layers[layer];

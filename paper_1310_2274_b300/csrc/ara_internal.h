@@ -32,6 +32,12 @@ constexpr int kMaxBands = 512;
 // Year Event Table on the device: trial-major event ids and timestamps (paper §2.1).
 struct YetDev {
   bool live = false;
+  // host-resident YET (ara_create_yet_host): ids and timestamps stay in the caller's memory and
+  // each run streams the trials it needs; offsets are on the device as for a resident YET
+  bool host = false;
+  const int32_t* h_ids = nullptr;
+  const float* h_ts = nullptr;
+  std::vector<int64_t> h_off;  // [n_trials + 1] (host YETs only)
   int64_t n_trials = 0;
   int64_t n_occ = 0;
   int32_t catalog = 0;
@@ -120,6 +126,10 @@ struct TrialParams {
   double* oep;               // [n] or null
   unsigned int* omax;        // [n] binary32 bit patterns of the running maxima (band-major;
                              //     zeroed first; non-negative floats order like their bits)
+  // host-resident YETs: ids holds occurrences [occ_base, ...) of the streamed chunk (0 for a
+  // resident YET); a nonzero *abort_flag (the chunk failed validation) makes warps skip work
+  int64_t occ_base;
+  const unsigned int* abort_flag;
   // per-occurrence outputs (trial-major only), indexed by occurrence position - offsets[t0]
   float* olt;                // occurrence loss after occurrence terms, or null
   double* inc;               // increment of the year's net aggregate loss, or null
@@ -139,6 +149,10 @@ int64_t launches_so_far();
 
 // ---- launchers (each returns the launch's cudaError_t) ---------------------------------------
 cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st);
+// the same for trials [t_begin, t_begin + n) whose occurrences [occ_base, ...) are in ids/ts
+cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64_t occ_base,
+                                      const int64_t* offsets, int64_t t_begin, int64_t n,
+                                      int32_t catalog, unsigned int* d_flags, cudaStream_t st);
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
                                const double* sd, const double* sdc, const double* mx,
                                int32_t catalog, BetaRec* recs, double2* ab64, float* corr,

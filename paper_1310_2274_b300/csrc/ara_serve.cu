@@ -453,6 +453,7 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
   *out = nullptr;
   if (cfg->yet < 0 || cfg->yet >= (int32_t)ctx->yets.size() || !ctx->yets[cfg->yet].live)
     return ARA_ERR_BAD_HANDLE;
+  if (ctx->yets[cfg->yet].host) return ARA_ERR_INVALID_ARG;  // a server keeps its YET resident
   if (cfg->slice_trials < 1 || cfg->max_batch_trials < cfg->slice_trials || cfg->max_inflight < 1)
     return ARA_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARA_ERR_CUDA;

@@ -30,15 +30,17 @@ inline unsigned grid_for(int64_t n, int per_block = kThreads) {
 
 // ---- YET validation (warp per trial) ----------------------------------------------------------
 // flags bit 0: id out of range; bit 1: timestamp decreases within a trial; bit 2: NaN timestamp.
+// Trials [t_begin, t_begin + n_trials); ids/ts hold occurrences from occ_base on.
 __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float* __restrict__ ts,
-                                    const int64_t* __restrict__ off, int64_t n_trials,
-                                    int32_t catalog, unsigned int* flags) {
+                                    int64_t occ_base, const int64_t* __restrict__ off,
+                                    int64_t t_begin, int64_t n_trials, int32_t catalog,
+                                    unsigned int* flags) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned int f = 0;
-  for (int64_t i = warp; i < n_trials; i += nwarps) {
-    const int64_t beg = off[i], end = off[i + 1];
+  for (int64_t i = t_begin + warp; i < t_begin + n_trials; i += nwarps) {
+    const int64_t beg = off[i] - occ_base, end = off[i + 1] - occ_base;
     for (int64_t q = beg + lane; q < end; q += 32) {
       const int32_t e = ids[q];
       if (e < 0 || e >= catalog) f |= 1u;
@@ -273,15 +275,21 @@ std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
-cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st) {
-  if (y.n_trials == 0) return cudaSuccess;
-  int64_t warps = y.n_trials;
-  int64_t blocks = (warps * 32 + kThreads - 1) / kThreads;
+cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64_t occ_base,
+                                      const int64_t* offsets, int64_t t_begin, int64_t n,
+                                      int32_t catalog, unsigned int* d_flags, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n * 32 + kThreads - 1) / kThreads;
   if (blocks > 148 * 64) blocks = 148 * 64;
-  validate_yet_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(y.ids, y.ts, y.offsets, y.n_trials,
-                                                              y.catalog, d_flags);
+  validate_yet_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(ids, ts, occ_base, offsets, t_begin,
+                                                              n, catalog, d_flags);
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st) {
+  return launch_validate_yet_range(y.ids, y.ts, 0, y.offsets, 0, y.n_trials, y.catalog, d_flags,
+                                   st);
 }
 
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,

@@ -104,6 +104,8 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
   constexpr bool TABLE = INV == 0;
   constexpr bool SURR = INV == 2;
   const int64_t trial = P.t0 + w;
+  if (P.abort_flag != nullptr && *reinterpret_cast<const volatile unsigned int*>(P.abort_flag))
+    return;  // the streamed chunk holding this trial failed validation
   const int64_t beg = P.offsets[trial];
   const int64_t end = P.offsets[trial + 1];
 
@@ -129,7 +131,8 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
       en.base = 0;
       en.m0 = 0;
       if constexpr (MW == 2) en.m1 = 0;
-      if (q < end) en = Entry<MW>::load(P.evt, ld_stream_s32(P.ids + q, pol.stream), pol.keep);
+      if (q < end)
+        en = Entry<MW>::load(P.evt, ld_stream_s32(P.ids + (q - P.occ_base), pol.stream), pol.keep);
       const int cnt = en.count();
       int incl = cnt;
 #pragma unroll

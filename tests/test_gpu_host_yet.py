@@ -1,0 +1,119 @@
+"""Host-resident YETs: runs stream the trials they need from host memory in chunks (copy stream,
+two device buffers) while earlier chunks are validated and run.  Results must equal the
+device-resident YET's trial-major runs bit for bit, for any trial range, chunk size and output
+set; invalid chunks are reported after the run without any of their trials being computed."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1310_2274_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N = 3000
+
+
+def pinned(a):
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t, t.numpy()
+
+
+@pytest.fixture(scope="module")
+def pair(ara):
+    """The paper-scale layer (2,000,000-event catalogue, 16 ELTs) on 3,000 trials, staged on a
+    resident YET in one context and on a host-resident one (page-locked arrays) in another, so
+    that the ELTs have the same handles (which key their draws) in both."""
+    w = synth.paper(n_trials=N)
+    keep = [pinned(x) for x in (w.yet.offsets, w.yet.event_ids, w.yet.timestamps)]
+    off, ids, ts = (k[1] for k in keep)
+    cr = ara.Context(seed=42)
+    res_yet, _, res_layer = cr.stage_workload(w)
+    ch = ara.Context(seed=42)
+    h_yet = ch.create_yet_host(off, ids, ts, 2_000_000)
+    h_elts = [ch.add_elt(h_yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in w.elts]
+    t = w.terms
+    h_layer = ch.add_layer(h_elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+    cr.set_option(ara.OPT_SCHEDULE, ara.SCHED_TRIAL)
+    yield (cr, ch), w, (res_yet, res_layer), (h_yet, h_layer), keep
+    ch.close()
+    cr.close()
+
+
+def n_occ(w, t0, n):
+    return int(w.yet.offsets[t0 + n] - w.yet.offsets[t0])
+
+
+@pytest.mark.parametrize("chunk", [1 << 26, 1 << 18, 1024])
+def test_streamed_runs_equal_resident_runs(ara, pair, chunk):
+    (cr, ch), w, (ry, rl), (hy, hl), _ = pair
+    ch.set_option(ara.OPT_STREAM_CHUNK, chunk)
+    try:
+        for t0, n in [(0, N), (7, 1500), (N - 1, 1), (1234, 567)]:
+            np.testing.assert_array_equal(ch.run(hy, hl, t0, n), cr.run(ry, rl, t0, n))
+    finally:
+        ch.set_option(ara.OPT_STREAM_CHUNK, 1 << 26)
+
+
+def test_streamed_event_outputs_and_newton(ara, pair):
+    (cr, ch), w, (ry, rl), (hy, hl), _ = pair
+    ch.set_option(ara.OPT_STREAM_CHUNK, 1 << 18)
+    try:
+        for t0, n in [(0, N), (100, 900)]:
+            got = ch.run_events(hy, hl, t0, n, n_occ(w, t0, n))
+            want = cr.run_events(ry, rl, t0, n, n_occ(w, t0, n))
+            for a, b in zip(got, want):
+                np.testing.assert_array_equal(a, b)
+        for c in (cr, ch):
+            c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+        np.testing.assert_array_equal(ch.run(hy, hl, 0, N), cr.run(ry, rl, 0, N))
+    finally:
+        for c in (cr, ch):
+            c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+        ch.set_option(ara.OPT_STREAM_CHUNK, 1 << 26)
+
+
+def test_streamed_run_matches_oracle(ara, oracle, pair):
+    (_, ch), w, _, (hy, hl), _ = pair
+    g = ch.run(hy, hl, 0, 800)
+    o, _ = oracle.run(w.yet, w.elts, w.terms, 42, trials=np.arange(800),
+                      elt_handles=list(range(16)))
+    scale = np.maximum(np.maximum(np.abs(o), w.terms.agg_ret), 1.0)
+    assert np.max(np.abs(g - o) / scale) <= 1e-5
+
+
+def test_invalid_chunks_are_reported(ara):
+    # event ids outside the catalogue in one trial, timestamps out of order in another: the
+    # chunk's validation runs before the chunk, whose trials are then skipped, and the run fails
+    rng = np.random.default_rng(3)
+    lens = np.full(400, 50)
+    off = np.zeros(401, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    ids = rng.integers(0, 10_000, size=int(off[-1]), dtype=np.int32)
+    ts = np.tile(np.linspace(0, 365, 50, dtype=np.float32), 400)
+    elt = synth.make_elt(2_000, 10_000, seed=2)
+    for bad in ("id", "ts"):
+        ids2, ts2 = ids.copy(), ts.copy()
+        if bad == "id":
+            ids2[off[300] + 7] = 10_000
+        else:
+            ts2[off[120] + 3] = -1.0
+        with ara.Context(seed=42) as c:
+            c.set_option(ara.OPT_STREAM_CHUNK, 4096)
+            y = c.create_yet_host(off, ids2, ts2, 10_000)
+            e = c.add_elt(y, elt.event_ids, elt.mean, elt.sd, elt.max_exposure)
+            layer = c.add_layer([e], 0.0, 1e9, 0.0, 1e12)
+            with pytest.raises(ara.AraError) as ex:
+                c.run(y, layer, 0, 400)
+            assert ex.value.status == 1
+            # the context stays usable: a valid range before the bad trial still runs
+            assert c.run(y, layer, 0, 100).shape == (100,)
+
+
+def test_host_yet_restrictions(ara, pair):
+    (_, ch), w, _, (hy, hl), _ = pair
+    with pytest.raises(ara.AraError):
+        ch.run_portfolio(hy, [hl], 0, 10)
+    with pytest.raises(ara.AraError):  # asynchronous calls (a non-default stream)
+        ch.run(hy, hl, 0, 10, out=torch.zeros(10, dtype=torch.float64, device="cuda"),
+               stream=torch.cuda.Stream())
