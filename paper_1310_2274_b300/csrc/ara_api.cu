@@ -1238,7 +1238,11 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   }
   std::vector<TrialParams> items(n_layers);
   std::vector<int64_t> begin(3 * (size_t)n_layers, 0);  // warp / block / trial firsts per item
-  struct Group { int32_t first = 0, count = 0; int64_t units = 0, trials = 0; };
+  struct Group {
+    int32_t first = 0, count = 0;
+    int64_t units = 0, trials = 0;
+    bool corr = false;  // some item carries correlated weights
+  };
   Group g[8];
   int32_t band_row = 0;
   unsigned long long nc_before = 0;
@@ -1281,6 +1285,7 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
       G.units += n;
     }
     G.count++;
+    G.corr = G.corr || p.corr != nullptr;
     items[kk] = p;
   }
   if (n_items == 0) return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
@@ -1303,7 +1308,8 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
     if (gi < 2)
       CUDA_TRY(ctx, launch_band_batch(d_items + G.first, d_begin + n_layers + G.first,
                                       d_begin + 2 * (int64_t)n_layers + G.first, G.count,
-                                      G.units, G.trials, mw, ctx->cfg.precision, st));
+                                      G.units, G.trials, mw, G.corr, ctx->cfg.precision,
+                                      st));
     else
       CUDA_TRY(ctx, launch_trial_batch(d_items + G.first, d_begin + G.first, G.count, G.units,
                                        mw, ctx->cfg.precision, inv, st));

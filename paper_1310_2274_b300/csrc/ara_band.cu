@@ -114,7 +114,10 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, unsigned lo
 
 // Trials [i_rel0, i_rel0 + nt) of the launch item P in band `band`, by one warp: the band-major
 // words of those trials are contiguous, and the warp walks them 128 at a time.
-template <int MW>
+// CORR: the launch may carry correlated weights (paper §3.2; P.corr is still checked, since a
+// batch mixes items); without them the draw is the hit's own uniform and the weight load and
+// combination are compiled out.
+template <int MW, bool CORR>
 __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_t i_rel0, int nt,
                                           int lane, BandWarpSmem& sm) {
   const L2Policies pol = L2Policies::make();
@@ -221,8 +224,10 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
       }
       const bool has = g < r1;
       float loss = 0.f;
+      int seg_start = lane;  // first lane of this hit's event in the round
       if (has) {
         const int nth = g - sm.excl[ev];
+        seg_start = max(lane - nth, 0);
         int slot;
         if constexpr (MW == 1) {
           slot = nth_set_bit(sm.mask[0][ev], nth);
@@ -234,7 +239,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
         const uint32_t pos = sm.base[ev] + (uint32_t)nth;
         const int64_t trial = P.t0 + i_rel0 + sm.t[ev];
         const float u0 = su_uniform_rk(P.rk0, P.rk1, trial, sm.k[ev], P.handles[slot]);
-        const float cc = P.corr != nullptr ? __ldg(P.corr + pos) : 0.0f;
+        const float cc = (CORR && P.corr != nullptr) ? __ldg(P.corr + pos) : 0.0f;
         const SuDraw d =
             su_draw(u0, cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, sm.k[ev]) : 0.5f, cc);
         const float u = d.z;
@@ -255,14 +260,13 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
           loss = pc.mx * ib.x;
         }
       }
-      // segmented inclusive scan: segments are the runs of equal ev
+      // segmented inclusive scan: segments are the runs of equal ev, lanes seg_start .. lane
       const int seg = has ? ev : -1;
       float val = loss;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const float nv = __shfl_up_sync(0xFFFFFFFFu, val, d);
-        const int ns = __shfl_up_sync(0xFFFFFFFFu, seg, d);
-        if (lane >= d && ns == seg) val += nv;
+        if (lane - d >= seg_start) val += nv;
       }
       const int next_seg = __shfl_down_sync(0xFFFFFFFFu, seg, 1);
       if (has && (lane == 31 || next_seg != seg)) sm.lsum[ev] += val;
@@ -324,7 +328,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
   }
 }
 
-template <int MW>
+template <int MW, bool CORR>
 __device__ __forceinline__ void band_block(const TrialParams& P, int64_t local_block,
                                            BandWarpSmem* sms) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -333,17 +337,17 @@ __device__ __forceinline__ void band_block(const TrialParams& P, int64_t local_b
   const int64_t i_rel0 = tile * kTrialsPerBlock + (int64_t)wib * kT;
   const int64_t left = P.n - i_rel0;
   if (left <= 0) return;  // whole warp; no block-wide barrier in this kernel
-  band_warp<MW>(P, band, i_rel0, (int)min((int64_t)kT, left), lane, sms[wib]);
+  band_warp<MW, CORR>(P, band, i_rel0, (int)min((int64_t)kT, left), lane, sms[wib]);
 }
 
 // Table inversion only: 64 registers for 4 blocks of 8 warps per SM, as the trial-major path.
-template <int MW>
+template <int MW, bool CORR>
 __global__ void __launch_bounds__(kBW * 32, 4) band_kernel(const __grid_constant__ TrialParams P) {
   __shared__ BandWarpSmem s_w[kBW];
-  band_block<MW>(P, (int64_t)blockIdx.x, s_w);
+  band_block<MW, CORR>(P, (int64_t)blockIdx.x, s_w);
 }
 
-template <int MW>
+template <int MW, bool CORR>
 __global__ void __launch_bounds__(kBW * 32, 4)
     band_batch_kernel(const TrialParams* __restrict__ items,
                       const int64_t* __restrict__ block_begin, int n_items) {
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(kBW * 32, 4)
     const int mid = (lo + hi + 1) >> 1;
     if (block_begin[mid] <= b) lo = mid; else hi = mid - 1;
   }
-  band_block<MW>(items[lo], b - block_begin[lo], s_w);
+  band_block<MW, CORR>(items[lo], b - block_begin[lo], s_w);
 }
 
 // Year losses from the exact year sums: S = units x 2^e, then the aggregate terms.
@@ -396,7 +400,10 @@ cudaError_t launch_band_t(const TrialParams& p0, cudaStream_t st) {
     e = cudaMemsetAsync(p.omax, 0, sizeof(unsigned int) * (size_t)p.n, st);
     if (e != cudaSuccess) return e;
   }
-  band_kernel<MW><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
+  if (p.corr != nullptr)
+    band_kernel<MW, true><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
+  else
+    band_kernel<MW, false><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
   count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -499,17 +506,23 @@ cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cud
 
 cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block_begin,
                               const int64_t* d_trial_begin, int n_items, int64_t total_blocks,
-                              int64_t total_trials, int mask_words, int precision,
+                              int64_t total_trials, int mask_words, bool corr, int precision,
                               cudaStream_t st) {
   if (precision != 0) return cudaErrorInvalidValue;
   if (total_blocks <= 0) return cudaSuccess;
   if (total_blocks > 0x7FFFFFFFll) return cudaErrorInvalidConfiguration;
-  if (mask_words == 1)
-    band_batch_kernel<1><<<(unsigned)total_blocks, kBW * 32, 0, st>>>(d_items, d_block_begin,
-                                                                     n_items);
-  else
-    band_batch_kernel<2><<<(unsigned)total_blocks, kBW * 32, 0, st>>>(d_items, d_block_begin,
-                                                                     n_items);
+  const dim3 grid((unsigned)total_blocks), block(kBW * 32);
+  if (mask_words == 1) {
+    if (corr)
+      band_batch_kernel<1, true><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+    else
+      band_batch_kernel<1, false><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+  } else {
+    if (corr)
+      band_batch_kernel<2, true><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+    else
+      band_batch_kernel<2, false><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+  }
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

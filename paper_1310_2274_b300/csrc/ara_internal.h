@@ -196,9 +196,10 @@ cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cud
 // many items in one launch (serving slices, portfolio layers), all with mask_words-word lookup
 // entries: items with their band fields set (tiles = band_tiles(n), ysum zeroed); block_begin[i]
 // = first block of item i (n_bands * tiles blocks each), trial_begin[i] = its first trial
+// corr: some item carries correlated weights
 cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block_begin,
                               const int64_t* d_trial_begin, int n_items, int64_t total_blocks,
-                              int64_t total_trials, int mask_words, int precision,
+                              int64_t total_trials, int mask_words, bool corr, int precision,
                               cudaStream_t st);
 // warp_begin[i] = first warp of item i (one warp per trial)
 cudaError_t launch_trial_batch(const TrialParams* d_items, const int64_t* d_warp_begin,

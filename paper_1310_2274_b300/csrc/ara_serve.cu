@@ -359,6 +359,7 @@ bool issue(ara_server* s) {
   const int cap = L.cap;
   int kb = 0, kt = 0;
   int64_t warp = 0, blocks = 0, trials = 0;
+  bool band_corr = false;  // some batched band item carries correlated weights
   cudaError_t e = cudaSuccess;
   // a slice whose own grid is many waves deep runs as its own launch (parameters in the constant
   // bank); the others share one batched launch per schedule
@@ -388,6 +389,7 @@ bool issue(ara_server* s) {
       L.h_begin[2 * cap + kb] = trials;
       blocks += (int64_t)p.n_bands * p.tiles;
       trials += n;
+      band_corr = band_corr || p.corr != nullptr;
       L.h_items[kb++] = p;
     } else {
       // every band item precedes every trial-major one in take, so kb is final here
@@ -406,7 +408,7 @@ bool issue(ara_server* s) {
                         s->stream);
   if (e == cudaSuccess && kb > 0)
     e = ara::launch_band_batch(L.d_items, L.d_begin + cap, L.d_begin + 2 * cap, kb, blocks,
-                               trials, 2, s->ctx->cfg.precision, s->stream);
+                               trials, 2, band_corr, s->ctx->cfg.precision, s->stream);
   if (e == cudaSuccess && kt > 0)
     e = ara::launch_trial_batch(L.d_items + kb, L.d_begin, kt, warp, 2,
                                 s->ctx->cfg.precision, inversion_mode(s->ctx), s->stream);

@@ -178,8 +178,10 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
       float loss = 0.f, u = 0.f, x = __int_as_float(0x7FC00000), mx = 0.f;
       float surr_z[3] = {0.f, 0.f, 0.f};
       bool net = false;
+      int seg_start = lane;  // first lane of this hit's event in the round
       if (has) {
         const int nth = g - excl[ev];
+        seg_start = max(lane - nth, 0);
         if constexpr (MW == 1) {
           slot = nth_set_bit(s_maskw[0][ev], nth);
         } else {
@@ -267,14 +269,14 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
           P.tr_loss[o] = loss;
         }
       }
-      // segmented inclusive scan over lanes: segments are the runs of equal ev
+      // segmented inclusive scan over lanes: segments are the runs of equal ev, lanes
+      // seg_start .. lane
       const int seg = has ? ev : -1;
       float val = loss;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const float nv = __shfl_up_sync(0xFFFFFFFFu, val, d);
-        const int ns = __shfl_up_sync(0xFFFFFFFFu, seg, d);
-        if (lane >= d && ns == seg) val += nv;
+        if (lane - d >= seg_start) val += nv;
       }
       const int next_seg = __shfl_down_sync(0xFFFFFFFFu, seg, 1);
       const bool tail = has && (lane == 31 || next_seg != seg);
