@@ -1,0 +1,173 @@
+// ara_host.h -- host-side helpers shared by the C-ABI implementation files: error detail,
+// pointer kinds, plain and stream-ordered device allocation, grow-only context scratch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "../../include/ara.h"
+#include "ara_ctx.h"
+#include "ara_internal.h"
+
+namespace ara {
+inline ara_status fail(ara_ctx* c, ara_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->detail = buf;
+  }
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess) {                                                                  \
+      cudaGetLastError();                                                                     \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA, "%s: %s", \
+                  #call, cudaGetErrorString(_e));                                             \
+    }                                                                                         \
+  } while (0)
+
+inline bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dev_alloc(T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)n);
+}
+
+inline void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Allocation either plain (cudaMalloc/cudaFree, which waits for the device) or stream-ordered
+// on st (cudaMallocAsync/cudaFreeAsync from the device's memory pool, which never blocks the host:
+// the serving loop builds and frees layers while launches run).
+template <class T>
+cudaError_t mem_alloc(T** p, int64_t n, bool ordered, cudaStream_t st) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  const size_t bytes = sizeof(T) * (size_t)n;
+  return ordered ? cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st)
+                 : cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+inline void mem_free(const void* p, bool ordered, cudaStream_t st) {
+  if (!p) return;
+  if (ordered) cudaFreeAsync(const_cast<void*>(p), st);
+  else cudaFree(const_cast<void*>(p));
+}
+
+// A stream-ordered temporary freed when the call returns, on whichever path.
+struct OrderedTemp {
+  void* p;
+  cudaStream_t st;
+  ~OrderedTemp() { mem_free(p, true, st); }
+};
+
+// Copies n elements from a host or device pointer into device memory on the stream.
+template <class T>
+cudaError_t copy_in(T* dst, const T* src, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, st);
+}
+
+inline void free_yet(YetDev& y) {
+  for (auto& v : y.bands) free_band_variant(v);
+  dev_free(y.ids);
+  dev_free(y.ts);
+  dev_free(y.offsets);
+  y = YetDev();
+}
+inline void free_elt(EltDev& e) {
+  dev_free(e.ids);
+  dev_free(e.recs);
+  dev_free(e.tables);
+  dev_free(e.corr);
+  dev_free(e.ab64);
+  e = EltDev();
+}
+
+inline ara_status set_device(ara_ctx* c) {
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  return ARA_OK;
+}
+
+inline ara_status ensure_ylt_tmp(ara_ctx* c, int64_t n) {
+  if (n <= c->ylt_tmp_cap) return ARA_OK;
+  dev_free(c->d_ylt_tmp);
+  c->d_ylt_tmp = nullptr;
+  c->ylt_tmp_cap = 0;
+  CUDA_TRY(c, dev_alloc(&c->d_ylt_tmp, n));
+  c->ylt_tmp_cap = n;
+  return ARA_OK;
+}
+
+inline ara_status ensure_ysum(ara_ctx* c, int64_t n) {
+  if (n <= c->ysum_cap) return ARA_OK;
+  dev_free(c->d_ysum);
+  c->d_ysum = nullptr;
+  c->ysum_cap = 0;
+  CUDA_TRY(c, dev_alloc(&c->d_ysum, n));
+  c->ysum_cap = n;
+  return ARA_OK;
+}
+
+inline ara_status ensure_sort(ara_ctx* c, int64_t n) {
+  SortScratch& s = c->sort;
+  const int64_t tiles = sort_tiles(n);
+  const int64_t hist_n = 256 * tiles;
+  if (n > s.cap) {
+    for (int b = 0; b < 2; ++b) {
+      dev_free(s.keys[b]);
+      dev_free(s.vals[b]);
+      s.keys[b] = nullptr;
+      s.vals[b] = nullptr;
+    }
+    s.cap = 0;
+    for (int b = 0; b < 2; ++b) {
+      CUDA_TRY(c, dev_alloc(&s.keys[b], n));
+      CUDA_TRY(c, dev_alloc(&s.vals[b], n));
+    }
+    s.cap = n;
+  }
+  if (hist_n > s.hist_cap) {
+    dev_free(s.hist);
+    dev_free(s.scan_tmp);
+    s.hist = nullptr;
+    s.scan_tmp = nullptr;
+    s.hist_cap = 0;
+    CUDA_TRY(c, dev_alloc(&s.hist, hist_n));
+    s.scan_cap = scan_tmp_words(hist_n);
+    CUDA_TRY(c, dev_alloc(&s.scan_tmp, s.scan_cap));
+    s.hist_cap = hist_n;
+  }
+  if (!s.digit_flags) CUDA_TRY(c, dev_alloc(&s.digit_flags, 4));
+  return ARA_OK;
+}
+
+inline int64_t tail_count(int64_t n, double rp) {
+  const double q = (double)n / rp;
+  const double r = nearbyint(q);
+  int64_t k = (fabs(q - r) <= 1e-9 * fmax(1.0, q)) ? (int64_t)r : (int64_t)ceil(q);
+  if (k < 1) k = 1;
+  if (k > n) k = n;
+  return k;
+}
+
+}  // namespace ara

@@ -1,0 +1,715 @@
+// ara_run.cu -- runs of Algorithm 1 through the C ABI: argument checks, the table policy,
+// launch parameters, resident and streamed runs, event-level outputs, portfolios, counters,
+// and the verification trace.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/ara.h"
+#include "ara_ctx.h"
+#include "ara_host.h"
+#include "ara_internal.h"
+#include "ara_philox.cuh"
+
+using namespace ara;
+
+// ---- run ------------------------------------------------------------------------------------
+static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n) {
+  if (yet < 0 || yet >= (int32_t)ctx->yets.size() || !ctx->yets[yet].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad YET handle %d", yet);
+  if (layer < 0 || layer >= (int32_t)ctx->layers.size() || !ctx->layers[layer].live)
+    return fail(ctx, ARA_ERR_BAD_HANDLE, "bad layer handle %d", layer);
+  const LayerDev& L = ctx->layers[layer];
+  if (L.yet != yet) return fail(ctx, ARA_ERR_INVALID_ARG, "layer belongs to another YET");
+  for (int j = 0; j < L.n_slots; ++j)
+    if (!ctx->elts[L.handles[j]].live)
+      return fail(ctx, ARA_ERR_BAD_HANDLE, "layer uses freed ELT %d", L.handles[j]);
+  if (t0 < 0 || n < 0 || t0 + n > ctx->yets[yet].n_trials)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "trial range [%lld, %lld) outside the YET",
+                (long long)t0, (long long)(t0 + n));
+  return ARA_OK;
+}
+
+bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
+  return layer_inversion(ctx, L) == 0 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
+         ctx->cfg.precision == ARA_ACC_FP64;
+}
+
+int layer_inversion(const ara_ctx* ctx, const LayerDev& L) {
+  const int m = inversion_mode(ctx);
+  return (m == 0 && L.tables == nullptr) ? 1 : m;
+}
+
+// The certified tables of one ELT, from the (alpha, beta) kept at staging.
+static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
+  if (e.tables) return ARA_OK;
+  if (!e.ab64) return fail(ctx, ARA_ERR_INVALID_ARG, "ELT has neither tables nor parameters");
+  unsigned long long* d_uncert = nullptr;
+  unsigned long long uncert = 0;
+  cudaError_t err;
+  if ((err = dev_alloc(&e.tables, e.n * kTablePieces)) != cudaSuccess ||
+      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(e.tables);
+    e.tables = nullptr;
+    dev_free(d_uncert);
+    return fail(ctx, ARA_ERR_OOM, "tables of %lld records", (long long)e.n);
+  }
+  if ((err = cudaMemsetAsync(d_uncert, 0, sizeof uncert, ctx->stream)) != cudaSuccess ||
+      (err = launch_build_tables(e.n, e.recs, e.ab64, e.tables, d_uncert, ctx->stream)) !=
+          cudaSuccess ||
+      (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess ||
+      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(e.tables);
+    e.tables = nullptr;
+    dev_free(d_uncert);
+    return fail(ctx, ARA_ERR_CUDA, "building tables: %s", cudaGetErrorString(err));
+  }
+  dev_free(d_uncert);
+  dev_free(e.ab64);
+  e.ab64 = nullptr;
+  e.n_uncertified = (int64_t)uncert;
+  return ARA_OK;
+}
+
+// The layer's packed table copy (its ELTs' tables first).
+static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
+  if (L.tables) return ARA_OK;
+  for (int j = 0; j < L.n_slots; ++j) {
+    const ara_status s = ensure_elt_tables(ctx, ctx->elts[L.handles[j]]);
+    if (s != ARA_OK) return s;
+  }
+  const TablePiece** d_src = nullptr;
+  cudaError_t err;
+  if ((err = dev_alloc(&L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
+      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(L.tables);
+    L.tables = nullptr;
+    dev_free(d_src);
+    return fail(ctx, ARA_ERR_OOM, "layer tables: %s", cudaGetErrorString(err));
+  }
+  // the scatter rewrites the packed records as they are and fills the table source pointers
+  err = cudaSuccess;
+  for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
+    err = launch_layer_scatter(ctx->elts[L.handles[j]], j, L.mask_words, L.evt, L.packed, d_src,
+                               L.packed_rec, L.corr, ctx->stream);
+  if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  dev_free(d_src);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(L.tables);
+    L.tables = nullptr;
+    return fail(ctx, ARA_ERR_CUDA, "layer tables: %s", cudaGetErrorString(err));
+  }
+  return ARA_OK;
+}
+
+ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n) {
+  if (L.tables || inversion_mode(ctx) != 0) return ARA_OK;
+  if (ctx->table_policy == ARA_TABLES_EAGER) return ensure_layer_tables(ctx, L);
+  const YetDev& Y = ctx->yets[L.yet];
+  // expected hits per record of this run: each occurrence meets a given record with
+  // probability 1 / catalogue
+  const double per_rec = Y.n_trials > 0 && Y.catalog > 0
+                             ? (double)Y.n_occ * ((double)n / (double)Y.n_trials) / Y.catalog
+                             : 0.0;
+  bool buy = true;
+  for (int j = 0; j < L.n_slots; ++j) {
+    const EltDev& e = ctx->elts[L.handles[j]];
+    if (!e.tables && e.rent_hits + per_rec < ARA_TABLE_BUY_HITS) buy = false;
+  }
+  if (buy) return ensure_layer_tables(ctx, L);
+  for (int j = 0; j < L.n_slots; ++j) {
+    EltDev& e = ctx->elts[L.handles[j]];
+    if (!e.tables) e.rent_hits += per_rec;
+  }
+  return ARA_OK;
+}
+
+ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet) {
+  for (auto& e : ctx->elts)
+    if (e.live && e.yet == yet) {
+      const ara_status s = ensure_elt_tables(ctx, e);
+      if (s != ARA_OK) return s;
+    }
+  return ARA_OK;
+}
+
+ara_status ensure_band_variant(ara_ctx* ctx, int32_t yet, int log2w, bool* available) {
+  *available = false;
+  YetDev& Y = ctx->yets[yet];
+  if (Y.host) return ARA_OK;  // a streamed YET runs trial-major
+  if (!band_layout_fits(Y, log2w)) return ARA_OK;
+  for (int v = 0; v < kMaxBandVariants; ++v)
+    if (Y.bands[v].log2w == log2w) {
+      *available = true;
+      return ARA_OK;
+    }
+  for (int v = 0; v < kMaxBandVariants; ++v)
+    if (Y.bands[v].log2w == 0) {
+      const cudaError_t err = build_band_variant(Y, log2w, Y.bands[v], ctx->stream);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA,
+                    "band-major YET copy: %s", cudaGetErrorString(err));
+      }
+      *available = true;
+      return ARA_OK;
+    }
+  return ARA_OK;  // every slot taken: the layer runs trial-major
+}
+
+int inversion_mode(const ara_ctx* ctx) {
+  if (ctx->cfg.use_surrogate && ctx->mlp_ready) return 2;
+  return ctx->inversion;
+}
+
+// The end of a run call: nothing more for an asynchronous call; else the YLT back to a host
+// buffer, and ARA_ERR_NOT_CONVERGED if the convergence counter moved during the call.
+static ara_status finish_run(ara_ctx* ctx, void* stream, bool dev_out, double* ylt,
+                             const double* d_ylt, int64_t total, unsigned long long nc_before,
+                             cudaStream_t st) {
+  if (stream) return ARA_OK;
+  if (!dev_out)
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)total,
+                                  cudaMemcpyDeviceToHost, st));
+  unsigned long long nc_after = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
+                                cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (nc_after != nc_before)
+    return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
+                nc_after - nc_before);
+  return ARA_OK;
+}
+
+// Where the net aggregate loss A(s) = min(max(s*unit - AggR, 0), AggL) (binary64, s grid units,
+// s*unit exact) is constant: A = 0 for s <= *zero_max, A = AggL for s >= *full_min.  Both by
+// bisection on the same binary64 expression the kernels evaluate, which is monotone in s.
+static void agg_bounds(double unit, double agg_ret, double agg_lim, unsigned long long* zero_max,
+                       unsigned long long* full_min) {
+  const unsigned long long top = 1ull << 53;  // year sums stay below 2^52 units
+  auto net = [&](unsigned long long s) { return (double)s * unit - agg_ret; };
+  // largest s in [0, top] with net(s) <= 0 (net(0) <= 0 always)
+  unsigned long long lo = 0, hi = top;
+  if (net(top) <= 0.0) {
+    lo = top;
+  } else {
+    while (hi - lo > 1) {
+      const unsigned long long mid = lo + (hi - lo) / 2;
+      if (net(mid) <= 0.0) lo = mid; else hi = mid;
+    }
+  }
+  *zero_max = lo;
+  // smallest s in [0, top] with net(s) >= AggL, or never
+  if (!(net(top) >= agg_lim)) {
+    *full_min = ~0ull;
+    return;
+  }
+  lo = 0;
+  hi = top;
+  if (net(0) >= agg_lim) {
+    *full_min = 0;
+    return;
+  }
+  while (hi - lo > 1) {
+    const unsigned long long mid = lo + (hi - lo) / 2;
+    if (net(mid) >= agg_lim) hi = mid; else lo = mid;
+  }
+  *full_min = hi;
+}
+
+TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
+                        int64_t n, double* d_ylt) {
+  TrialParams p;
+  memset(&p, 0, sizeof p);
+  p.ids = Y.ids;
+  p.offsets = Y.offsets;
+  p.evt = L.evt;
+  p.recs = L.packed;
+  p.tables = L.tables;
+  p.corr = L.corr;
+  p.rec_idx = L.packed_rec;
+  for (int j = 0; j < kMaxLayerElts; ++j) p.handles[j] = L.handles[j];
+  p.n_slots = L.n_slots;
+  p.occ_ret = (float)L.occ_ret;
+  p.occ_lim = (float)L.occ_lim;
+  p.agg_ret = L.agg_ret;
+  p.agg_lim = L.agg_lim;
+  p.seed = ctx->cfg.seed;
+  ara::philox_round_keys(p.seed, p.rk0, p.rk1);
+  p.t0 = t0;
+  p.n = n;
+  p.ylt = d_ylt;
+  p.not_conv = ctx->d_not_conv;
+  p.stats = ctx->d_stats;
+  p.yet_n = Y.n_trials;
+  const int qe = year_grid_exponent((float)L.occ_lim, Y.max_len);
+  p.q_scale = std::ldexp(1.0f, -qe);
+  p.q_unit = std::ldexp(1.0, qe);
+  agg_bounds(p.q_unit, L.agg_ret, L.agg_lim, &p.agg_zero_max, &p.agg_full_min);
+  if (L.band_log2w > 0) {
+    for (const auto& v : Y.bands)
+      if (v.log2w == L.band_log2w) {
+        p.bocc = v.occ;
+        p.boff = v.off;
+        p.log2w = v.log2w;
+        p.kbits = v.kbits;
+        p.n_bands = v.n_bands;
+      }
+  }
+  if (ctx->cfg.use_surrogate && ctx->mlp_ready) {
+    p.mlp = &ctx->mlp_W->fwd;
+    p.mlp_bound = ctx->mlp_bound;
+    p.mlp_eps = ctx->mlp_eps;
+  }
+  return p;
+}
+
+extern "C" {
+
+// A run over a host-resident YET: trials in chunks of whole trials (up to ctx->stream_chunk
+// occurrences), each chunk's ids and timestamps copied on the copy stream into one of two device
+// buffers while the previous chunk is validated and run on st; the run of a chunk skips its work
+// if any chunk so far failed validation.  Outputs are device pointers for trials [t0, t0 + n).
+static ara_status run_streamed(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
+                               int64_t n, double* d_ylt, double* d_oep, float* d_olt,
+                               double* d_inc, cudaStream_t st) {
+  const int64_t cap = std::max<int64_t>(ctx->stream_chunk, Y.max_len);
+  if (cap > ctx->stream_cap) {
+    for (int b = 0; b < 2; ++b) {
+      dev_free(ctx->d_sids[b]);
+      dev_free(ctx->d_sts[b]);
+      ctx->d_sids[b] = nullptr;
+      ctx->d_sts[b] = nullptr;
+    }
+    ctx->stream_cap = 0;
+    for (int b = 0; b < 2; ++b)
+      CUDA_TRY(ctx, dev_alloc(&ctx->d_sids[b], cap));
+    for (int b = 0; b < 2; ++b)
+      CUDA_TRY(ctx, dev_alloc(&ctx->d_sts[b], cap));
+    ctx->stream_cap = cap;
+  }
+  if (!ctx->copy_stream)
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b) {
+    if (!ctx->ev_ready[b])
+      CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_ready[b], cudaEventDisableTiming));
+    if (!ctx->ev_free[b])
+      CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));  // both buffers free once st gets here
+  }
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), st));
+  const int64_t q_first = Y.h_off[(size_t)t0];
+  int k = 0;
+  for (int64_t tb = t0; tb < t0 + n; ++k) {
+    int64_t te = tb + 1;  // whole trials up to cap occurrences (a trial never exceeds cap)
+    while (te < t0 + n && Y.h_off[(size_t)te + 1] - Y.h_off[(size_t)tb] <= cap) ++te;
+    const int64_t ob = Y.h_off[(size_t)tb], len = Y.h_off[(size_t)te] - ob;
+    const int b = k & 1;
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
+    if (len > 0) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sids[b], Y.h_ids + ob, sizeof(int32_t) * (size_t)len,
+                                    cudaMemcpyHostToDevice, ctx->copy_stream));
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sts[b], Y.h_ts + ob, sizeof(float) * (size_t)len,
+                                    cudaMemcpyHostToDevice, ctx->copy_stream));
+    }
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_ready[b], ctx->copy_stream));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_ready[b], 0));
+    CUDA_TRY(ctx, launch_validate_yet_range(ctx->d_sids[b], ctx->d_sts[b], ob, Y.offsets, tb,
+                                            te - tb, Y.catalog, ctx->d_flags, st));
+    TrialParams p = make_params(ctx, Y, L, tb, te - tb, d_ylt + (tb - t0));
+    p.ids = ctx->d_sids[b];
+    p.occ_base = ob;
+    p.abort_flag = ctx->d_flags;
+    p.oep = d_oep ? d_oep + (tb - t0) : nullptr;
+    p.olt = d_olt ? d_olt + (ob - q_first) : nullptr;
+    p.inc = d_inc ? d_inc + (ob - q_first) : nullptr;
+    CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision, layer_inversion(ctx, L),
+                               false, st));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));
+    tb = te;
+  }
+  return ARA_OK;
+}
+
+ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                          double* ylt, double* oep, float* olt, double* inc, void* stream) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  ara_status s = check_run_args(ctx, yet, layer, t0, n);
+  if (s != ARA_OK) return s;
+  if (n > 0 && !ylt) return fail(ctx, ARA_ERR_INVALID_ARG, "ylt is NULL");
+  if (n == 0) return ARA_OK;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const bool dev_out = is_device_ptr(ylt);
+  if ((oep && is_device_ptr(oep) != dev_out) || (olt && is_device_ptr(olt) != dev_out) ||
+      (inc && is_device_ptr(inc) != dev_out))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "outputs must all be host or all device memory");
+  const bool per_occ = olt != nullptr || inc != nullptr;
+  if (ctx->yets[yet].host && stream)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "runs over a host-resident YET are blocking");
+  if (inc && ctx->cfg.precision != ARA_ACC_FP64)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "occurrence increments need ARA_ACC_FP64 year sums");
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  if (stream && !dev_out)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need device outputs");
+  const YetDev& Y = ctx->yets[yet];
+  double* d_ylt = ylt;
+  double* d_oep = oep;
+  float* d_olt = olt;
+  double* d_inc = inc;
+  int64_t n_occ = 0;
+  OrderedTemp tmp_olt{nullptr, st}, tmp_inc{nullptr, st};  // host outputs' device staging
+  if (!dev_out) {
+    s = ensure_ylt_tmp(ctx, oep ? 2 * n : n);
+    if (s != ARA_OK) return s;
+    d_ylt = ctx->d_ylt_tmp;
+    d_oep = oep ? ctx->d_ylt_tmp + n : nullptr;
+    if (per_occ) {
+      int64_t ends[2];
+      CUDA_TRY(ctx, cudaMemcpyAsync(&ends[0], Y.offsets + t0, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(ctx, cudaMemcpyAsync(&ends[1], Y.offsets + t0 + n, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(ctx, cudaStreamSynchronize(st));
+      n_occ = ends[1] - ends[0];
+      if (olt) {
+        CUDA_TRY(ctx, mem_alloc(&d_olt, n_occ, true, st));
+        tmp_olt.p = d_olt;
+      }
+      if (inc) {
+        CUDA_TRY(ctx, mem_alloc(&d_inc, n_occ, true, st));
+        tmp_inc.p = d_inc;
+      }
+    }
+  }
+  unsigned long long nc_before = 0;
+  if (!stream)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
+                                  cudaMemcpyDeviceToHost, st));
+  s = prepare_layer_for_run(ctx, ctx->layers[layer], n);
+  if (s != ARA_OK) return s;
+  TrialParams p = make_params(ctx, Y, ctx->layers[layer], t0, n, d_ylt);
+  p.oep = d_oep;
+  p.olt = d_olt;
+  p.inc = d_inc;
+  // per-occurrence outputs are written in trial order, so they keep the trial-major schedule
+  if (Y.host) {
+    s = run_streamed(ctx, Y, ctx->layers[layer], t0, n, d_ylt, d_oep, d_olt, d_inc, st);
+    if (s != ARA_OK) return s;
+  } else if (!per_occ && uses_band_schedule(ctx, ctx->layers[layer])) {
+    // year sums (8 B per trial), then the OEP maxima (4 B per trial) in the same scratch
+    s = ensure_ysum(ctx, oep ? n + (n + 1) / 2 : n);
+    if (s != ARA_OK) return s;
+    p.ysum = ctx->d_ysum;
+    p.omax = oep ? reinterpret_cast<unsigned int*>(ctx->d_ysum + n) : nullptr;
+    CUDA_TRY(ctx, launch_band(p, ctx->layers[layer].mask_words, ctx->cfg.precision, st));
+  } else {
+    CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
+                               layer_inversion(ctx, ctx->layers[layer]), false, st));
+  }
+  if (stream) return ARA_OK;
+  if (!dev_out) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                                  st));
+    if (oep)
+      CUDA_TRY(ctx, cudaMemcpyAsync(oep, d_oep, sizeof(double) * (size_t)n,
+                                    cudaMemcpyDeviceToHost, st));
+    if (olt && n_occ > 0)
+      CUDA_TRY(ctx, cudaMemcpyAsync(olt, d_olt, sizeof(float) * (size_t)n_occ,
+                                    cudaMemcpyDeviceToHost, st));
+    if (inc && n_occ > 0)
+      CUDA_TRY(ctx, cudaMemcpyAsync(inc, d_inc, sizeof(double) * (size_t)n_occ,
+                                    cudaMemcpyDeviceToHost, st));
+  }
+  unsigned long long nc_after = 0;
+  unsigned int yet_flags = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
+                                cudaMemcpyDeviceToHost, st));
+  if (Y.host)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&yet_flags, ctx->d_flags, sizeof yet_flags,
+                                  cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (yet_flags)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
+                (yet_flags & 1) ? " event id outside [0, catalog_size)" : "",
+                (yet_flags & 2) ? " timestamps decrease within a trial" : "",
+                (yet_flags & 4) ? " NaN timestamp" : "");
+  if (nc_after != nc_before)
+    return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
+                nc_after - nc_before);
+  return ARA_OK;
+}
+
+ara_status ara_run_ep(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                      double* ylt, double* oep, void* stream) {
+  return ara_run_events(ctx, yet, layer, t0, n, ylt, oep, nullptr, nullptr, stream);
+}
+
+ara_status ara_run(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n, double* ylt,
+                   void* stream) {
+  return ara_run_events(ctx, yet, layer, t0, n, ylt, nullptr, nullptr, nullptr, stream);
+}
+
+ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, int32_t n_layers,
+                             int64_t t0, int64_t n, double* ylt, void* stream) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (n_layers < 0 || (n_layers > 0 && !layers))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "bad layer list");
+  for (int32_t i = 0; i < n_layers; ++i) {
+    const ara_status s = check_run_args(ctx, yet, layers[i], t0, n);
+    if (s != ARA_OK) return s;
+  }
+  if (n == 0 || n_layers == 0) return ARA_OK;
+  if (!ylt) return fail(ctx, ARA_ERR_INVALID_ARG, "ylt is NULL");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const bool dev_out = is_device_ptr(ylt);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  if (stream && !dev_out)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "asynchronous runs need a device ylt");
+  const int64_t total = (int64_t)n_layers * n;
+  double* d_ylt = ylt;
+  if (!dev_out) {
+    ara_status s = ensure_ylt_tmp(ctx, total);
+    if (s != ARA_OK) return s;
+    d_ylt = ctx->d_ylt_tmp;
+  }
+  if (ctx->yets[yet].host)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "a host-resident YET runs one layer per call");
+  for (int32_t i = 0; i < n_layers; ++i) {
+    ara_status s = prepare_layer_for_run(ctx, ctx->layers[layers[i]], n);
+    if (s != ARA_OK) return s;
+  }
+  // one launch item per layer, grouped by schedule, inversion and lookup-entry width (one
+  // batched launch per group): band-major items first, each with its own year-sum rows
+  const YetDev& Y = ctx->yets[yet];
+  std::vector<int32_t> order(n_layers);
+  for (int32_t i = 0; i < n_layers; ++i) order[i] = i;
+  auto group = [&](int32_t i) {  // 0, 1 band-major; 2 + 2 inversion + (width - 1) trial-major
+    const LayerDev& L = ctx->layers[layers[i]];
+    const int w = L.mask_words == 1 ? 0 : 1;
+    return uses_band_schedule(ctx, L) ? w : 2 + 2 * layer_inversion(ctx, L) + w;
+  };
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return group(a) < group(b); });
+  int32_t n_band = 0;
+  for (int32_t i = 0; i < n_layers; ++i) n_band += group(i) < 2 ? 1 : 0;
+  if (n_band > 0) {
+    ara_status s = ensure_ysum(ctx, (int64_t)n_band * n);
+    if (s != ARA_OK) return s;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ysum, 0,
+                                  sizeof(unsigned long long) * (size_t)n_band * (size_t)n, st));
+  }
+  std::vector<TrialParams> items(n_layers);
+  std::vector<int64_t> begin(3 * (size_t)n_layers, 0);  // warp / block / trial firsts per item
+  struct Group {
+    int32_t first = 0, count = 0;
+    int64_t units = 0, trials = 0;
+    bool corr = false;  // some item carries correlated weights
+  };
+  Group g[8];
+  int32_t band_row = 0;
+  unsigned long long nc_before = 0;
+  if (!stream)
+    CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
+                                  cudaMemcpyDeviceToHost, st));
+  // a layer whose own grid is many waves deep runs as its own launch (launch parameters in the
+  // constant bank, as ara_run); only small layers share a batched launch, where filling the GPU
+  // matters more than the items' parameters being read from global memory
+  const int64_t big_blocks = 12ll * ctx->sm_count * 4;
+  int32_t n_items = 0;
+  for (int32_t k = 0; k < n_layers; ++k) {
+    const int32_t i = order[k];
+    const LayerDev& L = ctx->layers[layers[i]];
+    TrialParams p = make_params(ctx, Y, L, t0, n, d_ylt + (int64_t)i * n);
+    const bool band = group(i) < 2;
+    const int64_t own_blocks = band ? (int64_t)p.n_bands * band_tiles(n) : (n + 7) / 8;
+    if (own_blocks >= big_blocks) {
+      if (band) {
+        p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
+        CUDA_TRY(ctx, launch_band(p, L.mask_words, ctx->cfg.precision, st));
+      } else {
+        CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision,
+                                   layer_inversion(ctx, L), false, st));
+      }
+      continue;
+    }
+    const int32_t kk = n_items++;
+    Group& G = g[group(i)];
+    if (G.count == 0) G.first = kk;
+    if (band) {
+      p.tiles = (int32_t)band_tiles(n);
+      p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
+      begin[n_layers + kk] = G.units;
+      begin[2 * (size_t)n_layers + kk] = G.trials;
+      G.units += (int64_t)p.n_bands * p.tiles;
+      G.trials += n;
+    } else {
+      begin[kk] = G.units;
+      G.units += n;
+    }
+    G.count++;
+    G.corr = G.corr || p.corr != nullptr;
+    items[kk] = p;
+  }
+  if (n_items == 0) return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
+  TrialParams* d_items = nullptr;
+  int64_t* d_begin = nullptr;
+  CUDA_TRY(ctx, mem_alloc(&d_items, n_layers, true, st));
+  OrderedTemp tmp_items{d_items, st};
+  CUDA_TRY(ctx, mem_alloc(&d_begin, 3 * (int64_t)n_layers, true, st));
+  OrderedTemp tmp_begin{d_begin, st};
+  // pageable sources: each copy has read its source when the call returns
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_items, items.data(), sizeof(TrialParams) * (size_t)n_layers,
+                                cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_begin, begin.data(), sizeof(int64_t) * begin.size(),
+                                cudaMemcpyHostToDevice, st));
+  for (int gi = 0; gi < 8; ++gi) {
+    const Group& G = g[gi];
+    if (G.count == 0) continue;
+    const int mw = (gi & 1) ? 2 : 1;
+    const int inv = gi < 2 ? 0 : (gi - 2) / 2;
+    if (gi < 2)
+      CUDA_TRY(ctx, launch_band_batch(d_items + G.first, d_begin + n_layers + G.first,
+                                      d_begin + 2 * (int64_t)n_layers + G.first, G.count,
+                                      G.units, G.trials, mw, G.corr, ctx->cfg.precision,
+                                      st));
+    else
+      CUDA_TRY(ctx, launch_trial_batch(d_items + G.first, d_begin + G.first, G.count, G.units,
+                                       mw, ctx->cfg.precision, inv, st));
+  }
+  return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
+}
+
+ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {
+  if (!ctx || !out) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaDeviceSynchronize());
+  unsigned long long raw[kStatCounters * kStatStripes], v[kStatCounters] = {}, nc = 0;
+  CUDA_TRY(ctx, cudaMemcpy(raw, ctx->d_stats, sizeof raw, cudaMemcpyDeviceToHost));
+  for (int c = 0; c < kStatCounters; ++c)
+    for (int s = 0; s < kStatStripes; ++s) v[c] += raw[c * kStatStripes + s];
+  CUDA_TRY(ctx, cudaMemcpy(&nc, ctx->d_not_conv, sizeof nc, cudaMemcpyDeviceToHost));
+  out[0] = (int64_t)v[0];
+  out[1] = (int64_t)v[1];
+  out[2] = (int64_t)v[2];
+  out[3] = (int64_t)nc;
+  out[4] = (int64_t)v[3];
+  out[5] = launches_so_far();
+  out[6] = (int64_t)v[4];
+  int64_t unc = 0;
+  for (const auto& e : ctx->elts)
+    if (e.live) unc += e.n_uncertified;
+  out[7] = unc;
+  out[8] = (int64_t)v[5];
+  return ARA_OK;
+}
+
+ara_status ara_set_stream(ara_ctx* ctx, void* stream) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return ARA_OK;
+}
+
+ara_status ara_not_converged(ara_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return ARA_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  CUDA_TRY(ctx, cudaDeviceSynchronize());
+  unsigned long long v = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&v, ctx->d_not_conv, sizeof v, cudaMemcpyDeviceToHost));
+  *count = (int64_t)v;
+  return ARA_OK;
+}
+
+ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, int64_t n,
+                          int64_t max_hits, int32_t* hit_trial, int32_t* hit_k, int32_t* hit_j,
+                          int32_t* hit_rec, float* hit_u, float* hit_x, float* hit_loss,
+                          double* ylt, int64_t* n_hits) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  ara_status s = check_run_args(ctx, yet, layer, t0, n);
+  if (s != ARA_OK) return s;
+  if (!n_hits || max_hits < 0 || (max_hits > 0 && (!hit_trial || !hit_k || !hit_j || !hit_rec ||
+                                                     !hit_u || !hit_x || !hit_loss)) || !ylt)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "NULL trace buffer");
+  if (ctx->yets[yet].host)
+    return fail(ctx, ARA_ERR_INVALID_ARG, "tracing needs a device-resident YET");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const YetDev& Y = ctx->yets[yet];
+  const LayerDev& L = ctx->layers[layer];
+  const int64_t cap = std::max<int64_t>(1, Y.max_len * L.n_slots);
+  const int64_t total = n * cap;
+  if (total > ((int64_t)1 << 27)) return fail(ctx, ARA_ERR_INVALID_ARG, "trace too large");
+  if (n == 0) {
+    *n_hits = 0;
+    return ARA_OK;
+  }
+  int32_t *d_k = nullptr, *d_j = nullptr, *d_rec = nullptr, *d_cnt = nullptr;
+  float *d_u = nullptr, *d_x = nullptr, *d_loss = nullptr;
+  double* d_ylt = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(d_k); dev_free(d_j); dev_free(d_rec); dev_free(d_cnt);
+    dev_free(d_u); dev_free(d_x); dev_free(d_loss); dev_free(d_ylt);
+  };
+  cudaError_t e;
+  if ((e = dev_alloc(&d_k, total)) != cudaSuccess || (e = dev_alloc(&d_j, total)) != cudaSuccess ||
+      (e = dev_alloc(&d_rec, total)) != cudaSuccess || (e = dev_alloc(&d_cnt, n)) != cudaSuccess ||
+      (e = dev_alloc(&d_u, total)) != cudaSuccess || (e = dev_alloc(&d_x, total)) != cudaSuccess ||
+      (e = dev_alloc(&d_loss, total)) != cudaSuccess || (e = dev_alloc(&d_ylt, n)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, ARA_ERR_OOM, "trace buffers: %s", cudaGetErrorString(e));
+  }
+  TrialParams p = make_params(ctx, Y, L, t0, n, d_ylt);
+  p.trace_cap = cap;
+  p.tr_k = d_k; p.tr_j = d_j; p.tr_rec = d_rec; p.tr_u = d_u; p.tr_x = d_x; p.tr_loss = d_loss;
+  p.tr_count = d_cnt;
+  std::vector<int32_t> cnt(n), k(total), j(total), rec(total);
+  std::vector<float> u(total), x(total), loss(total);
+  e = launch_trial(p, L.mask_words, ARA_ACC_FP64, layer_inversion(ctx, L), true, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(k.data(), d_k, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(j.data(), d_j, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rec.data(), d_rec, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u.data(), d_u, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x.data(), d_x, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loss.data(), d_loss, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, ARA_ERR_CUDA, "trace: %s", cudaGetErrorString(e));
+  }
+  int64_t h = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    for (int32_t q = 0; q < cnt[t] && q < cap; ++q) {
+      if (h < max_hits) {
+        const int64_t o = t * cap + q;
+        hit_trial[h] = (int32_t)t;
+        hit_k[h] = k[o];
+        hit_j[h] = j[o];
+        hit_rec[h] = rec[o];
+        hit_u[h] = u[o];
+        hit_x[h] = x[o];
+        hit_loss[h] = loss[o];
+      }
+      ++h;
+    }
+  }
+  *n_hits = h;
+  return ARA_OK;
+}
+
+}  // extern "C"
