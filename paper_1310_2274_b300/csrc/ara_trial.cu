@@ -95,8 +95,10 @@ __device__ __forceinline__ void occurrence_outputs(const TrialParams& P, int64_t
   P.inc[q - q0] = d;
 }
 
-// The whole of Algorithm 1 for one trial (w-th of the launch item P), run by one warp.
-template <int MW, class Acc, bool TRACE, int INV>
+// The whole of Algorithm 1 for one trial (w-th of the launch item P), run by one warp.  CORR:
+// the item may carry correlated weights (paper §3.2; P.corr is still checked); without them the
+// weight load and the combination are compiled out.
+template <int MW, class Acc, bool TRACE, int INV, bool CORR>
 __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, int lane, int wib,
                                               int32_t* excl, uint32_t* sbase,
                                               uint32_t (*s_maskw)[kChunk], float* lsum,
@@ -194,7 +196,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
         bool sd0 = false, use_table = false;
         TablePiece pc;
         float tau = 0.f;
-        const float cc = P.corr != nullptr ? __ldg(P.corr + pos) : 0.0f;
+        const float cc = (CORR && P.corr != nullptr) ? __ldg(P.corr + pos) : 0.0f;
         if constexpr (TABLE) {
           // the piece index depends on the draw alone: draw first, then one 32-byte load
           const SuDraw d = su_draw(su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]),
@@ -331,7 +333,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
 // INV: 0 certified tables (Newton fallback), 1 Newton, 2 learned surrogate (Newton fallback).
 // The table path is latency bound on its two dependent loads per hit (record header, then table
 // piece), so it is held to 64 registers for 4 blocks (32 warps) per SM.
-template <int MW, class Acc, bool TRACE, int INV>
+template <int MW, class Acc, bool TRACE, int INV, bool CORR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 ? 3 : 1))
     trial_kernel(const __grid_constant__ TrialParams P) {
   __shared__ int32_t s_excl[kWarpsPerBlock][kChunk];
@@ -349,8 +351,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 
   const int wib = threadIdx.x >> 5;
   const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
   if (w >= P.n) return;  // whole warp leaves together; no block-wide barrier follows
-  process_trial<MW, Acc, TRACE, INV>(P, w, lane, wib, s_excl[wib], s_base[wib], s_mask[wib],
-                                     s_lsum[wib], &s_mlp[0]);
+  process_trial<MW, Acc, TRACE, INV, CORR>(P, w, lane, wib, s_excl[wib], s_base[wib],
+                                           s_mask[wib], s_lsum[wib], &s_mlp[0]);
 }
 
 // One launch over many work items (serving: slices of different requests, each with its own
@@ -379,11 +381,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 
     const int mid = (lo + hi + 1) >> 1;
     if (warp_begin[mid] <= w) lo = mid; else hi = mid - 1;
   }
-  process_trial<MW, Acc, false, INV>(items[lo], w - warp_begin[lo], lane, wib, s_excl[wib],
-                                     s_base[wib], s_mask[wib], s_lsum[wib], &s_mlp[0]);
+  process_trial<MW, Acc, false, INV, true>(items[lo], w - warp_begin[lo], lane, wib,
+                                           s_excl[wib], s_base[wib], s_mask[wib], s_lsum[wib],
+                                           &s_mlp[0]);
 }
 
-template <int MW, class Acc, bool TRACE, int INV>
+template <int MW, class Acc, bool TRACE, int INV, bool CORR = true>
 cudaError_t launch_one(const TrialParams& p, cudaStream_t st) {
   const int64_t blocks = (p.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks == 0) return cudaSuccess;
@@ -392,7 +395,7 @@ cudaError_t launch_one(const TrialParams& p, cudaStream_t st) {
   cfg.blockDim = dim3(kWarpsPerBlock * 32);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, trial_kernel<MW, Acc, TRACE, INV>, p);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, trial_kernel<MW, Acc, TRACE, INV, CORR>, p);
   count_launches(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -408,6 +411,12 @@ cudaError_t launch_mode(const TrialParams& p, int mask_words, int precision, boo
   if (precision == 1) {
     return mask_words == 1 ? launch_one<1, AccKahan, false, INV>(p, st)
                            : launch_one<2, AccKahan, false, INV>(p, st);
+  }
+  // the common case (exact sums, no weights, no surrogate) compiled without the weight path
+  if constexpr (INV != 2) {
+    if (p.corr == nullptr)
+      return mask_words == 1 ? launch_one<1, AccExact, false, INV, false>(p, st)
+                             : launch_one<2, AccExact, false, INV, false>(p, st);
   }
   return mask_words == 1 ? launch_one<1, AccExact, false, INV>(p, st)
                          : launch_one<2, AccExact, false, INV>(p, st);
