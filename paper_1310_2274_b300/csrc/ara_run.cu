@@ -368,8 +368,11 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   float* d_olt = olt;
   double* d_inc = inc;
   int64_t n_occ = 0;
-  OrderedTemp tmp_olt{nullptr, st}, tmp_inc{nullptr, st};  // host outputs' device staging
-  if (!dev_out) {
+  OrderedTemp tmp_olt{nullptr, st}, tmp_inc{nullptr, st};  // staged outputs' device memory
+  // host outputs are staged on the device; so are all outputs of a streamed run, which are
+  // handed over only once every chunk has passed validation
+  const bool staged = !dev_out || Y.host;
+  if (staged) {
     s = ensure_ylt_tmp(ctx, oep ? 2 * n : n);
     if (s != ARA_OK) return s;
     d_ylt = ctx->d_ylt_tmp;
@@ -418,32 +421,33 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
                                layer_inversion(ctx, ctx->layers[layer]), false, st));
   }
   if (stream) return ARA_OK;
-  if (!dev_out) {
-    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
-                                  st));
-    if (oep)
-      CUDA_TRY(ctx, cudaMemcpyAsync(oep, d_oep, sizeof(double) * (size_t)n,
-                                    cudaMemcpyDeviceToHost, st));
-    if (olt && n_occ > 0)
-      CUDA_TRY(ctx, cudaMemcpyAsync(olt, d_olt, sizeof(float) * (size_t)n_occ,
-                                    cudaMemcpyDeviceToHost, st));
-    if (inc && n_occ > 0)
-      CUDA_TRY(ctx, cudaMemcpyAsync(inc, d_inc, sizeof(double) * (size_t)n_occ,
-                                    cudaMemcpyDeviceToHost, st));
-  }
   unsigned long long nc_after = 0;
   unsigned int yet_flags = 0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&nc_after, ctx->d_not_conv, sizeof nc_after,
                                 cudaMemcpyDeviceToHost, st));
-  if (Y.host)
+  if (Y.host) {
     CUDA_TRY(ctx, cudaMemcpyAsync(&yet_flags, ctx->d_flags, sizeof yet_flags,
                                   cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (yet_flags)  // nothing is written to the caller's outputs
+      return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
+                  (yet_flags & 1) ? " event id outside [0, catalog_size)" : "",
+                  (yet_flags & 2) ? " timestamps decrease within a trial" : "",
+                  (yet_flags & 4) ? " NaN timestamp" : "");
+  }
+  if (staged) {  // to host or device outputs alike
+    CUDA_TRY(ctx, cudaMemcpyAsync(ylt, d_ylt, sizeof(double) * (size_t)n, cudaMemcpyDefault, st));
+    if (oep)
+      CUDA_TRY(ctx, cudaMemcpyAsync(oep, d_oep, sizeof(double) * (size_t)n, cudaMemcpyDefault,
+                                    st));
+    if (olt && n_occ > 0)
+      CUDA_TRY(ctx, cudaMemcpyAsync(olt, d_olt, sizeof(float) * (size_t)n_occ, cudaMemcpyDefault,
+                                    st));
+    if (inc && n_occ > 0)
+      CUDA_TRY(ctx, cudaMemcpyAsync(inc, d_inc, sizeof(double) * (size_t)n_occ,
+                                    cudaMemcpyDefault, st));
+  }
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  if (yet_flags)
-    return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
-                (yet_flags & 1) ? " event id outside [0, catalog_size)" : "",
-                (yet_flags & 2) ? " timestamps decrease within a trial" : "",
-                (yet_flags & 4) ? " NaN timestamp" : "");
   if (nc_after != nc_before)
     return fail(ctx, ARA_ERR_NOT_CONVERGED, "%llu inversions hit the iteration cap",
                 nc_after - nc_before);

@@ -103,9 +103,11 @@ def test_invalid_chunks_are_reported(ara):
             y = c.create_yet_host(off, ids2, ts2, 10_000)
             e = c.add_elt(y, elt.event_ids, elt.mean, elt.sd, elt.max_exposure)
             layer = c.add_layer([e], 0.0, 1e9, 0.0, 1e12)
+            out = np.full(400, -7.0)
             with pytest.raises(ara.AraError) as ex:
-                c.run(y, layer, 0, 400)
+                c.run(y, layer, 0, 400, out=out)
             assert ex.value.status == 1
+            assert np.all(out == -7.0)  # outputs are written only on success
             # the context stays usable: a valid range before the bad trial still runs
             assert c.run(y, layer, 0, 100).shape == (100,)
 
