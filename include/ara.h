@@ -113,7 +113,7 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_TABLES_ON_DEMAND 1
 #define ARA_TABLE_BUY_HITS 1700.0
 /* ARA_OPT_STREAM_CHUNK: occurrences per copied chunk of a host-resident YET's runs (1024 .. 2^30;
- * default 2^26, two buffers of 8 bytes per occurrence on the device; a chunk always holds whole
+ * default 2^26, two buffers of 4 bytes per occurrence on the device; a chunk always holds whole
  * trials, so it grows to the longest trial if needed). */
 #define ARA_OPT_STREAM_CHUNK 8
 ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
@@ -124,18 +124,22 @@ ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
  * nondecreasing (an empty trial is allowed).  Event ids must lie in [0, catalog_size).
  * Rejected with ARA_ERR_INVALID_ARG: n_trials < 0, catalog_size <= 0, bad offsets, an id out of
  * range, a timestamp below its predecessor in the same trial, a NaN timestamp.
- * Device copy: int32 ids and float32 timestamps, trial-major; 8 bytes per occurrence. */
+ * Device copy: int32 ids, trial-major, 4 bytes per occurrence.  Runs never read timestamps: host
+ * ones are checked on host threads while the ids are copied and are not stored; device ones are
+ * copied and checked on the device (4 more bytes per occurrence). */
 ARA_API ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_offsets,
                                   const int32_t* event_ids, const float* timestamps,
                                   int32_t catalog_size, int32_t* yet_out);
 /* Host-resident YET for single passes: the same arrays and checks as ara_create_yet, but only
  * trial_offsets is copied (to the device, 8 B per trial); event_ids and timestamps stay in the
  * caller's host memory, which must stay valid and unchanged until ara_free_yet.  Each ara_run /
- * ara_run_ep / ara_run_events over it (blocking; stream must be NULL) copies the trials it needs
- * in chunks of whole trials (ARA_OPT_STREAM_CHUNK) on a copy stream into two device buffers
- * used in turn, while the previous chunk is validated (ids in range, timestamps in order: else
- * ARA_ERR_INVALID_ARG after the run) and run trial-major on the compute stream, so the PCIe copy
- * of a pass overlaps its computation.  Page-locked host memory (cudaHostAlloc, or registered)
+ * ara_run_ep / ara_run_events over it (blocking; stream must be NULL) copies the event ids of
+ * the trials it needs in chunks of whole trials (ARA_OPT_STREAM_CHUNK) on a copy stream into two
+ * device buffers used in turn, while the previous chunk's ids are checked and the chunk is run
+ * trial-major on the compute stream, so the PCIe copy of a pass overlaps its computation.  The
+ * timestamps never cross: the first run checks them on host threads meanwhile.  An id out of
+ * range or a timestamp out of order makes the run return ARA_ERR_INVALID_ARG without writing
+ * its outputs.  Page-locked host memory (cudaHostAlloc, or registered)
  * gives the overlap; pageable memory still works, with staged copies.  Layers over it run
  * trial-major; ara_run_portfolio, ara_trace_hits and servers need a device-resident YET
  * (ARA_ERR_INVALID_ARG).  A second pass copies the YET again: keep a YET that several passes

@@ -11,6 +11,7 @@
 #include <new>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ara.h"
@@ -31,6 +32,43 @@ void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st) {
 }
 
 void free_layer(LayerDev& l) { free_layer_on(l, false, nullptr); }
+
+namespace ara {
+
+unsigned int validate_timestamps_host(const int64_t* off, const float* ts, int64_t n_trials) {
+  const int64_t n_occ = off[n_trials];
+  // parts of at least 4M occurrences, cut at trial boundaries, one host thread each
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(hw, n_occ >> 22));
+  std::vector<int64_t> cut((size_t)parts + 1, n_trials);
+  cut[0] = 0;
+  for (int64_t k = 1; k < parts; ++k) {
+    const int64_t target = n_occ / parts * k;
+    cut[(size_t)k] = std::upper_bound(off, off + n_trials + 1, target) - off - 1;
+  }
+  std::vector<unsigned int> flags((size_t)parts, 0u);
+  auto check = [&](int64_t k) {
+    unsigned int f = 0;
+    for (int64_t i = cut[(size_t)k]; i < cut[(size_t)k + 1]; ++i) {
+      // branch-free OR reductions over the trial, which the compiler vectorises
+      const int64_t b = off[i], e = off[i + 1];
+      int nan = 0, dec = 0;
+      for (int64_t q = b; q < e; ++q) nan |= (ts[q] != ts[q]);
+      for (int64_t q = b + 1; q < e; ++q) dec |= (ts[q] < ts[q - 1]);
+      f |= (nan ? 4u : 0u) | (dec ? 2u : 0u);
+    }
+    flags[(size_t)k] = f;
+  };
+  std::vector<std::thread> pool;
+  for (int64_t k = 1; k < parts; ++k) pool.emplace_back(check, k);
+  check(0);
+  for (auto& th : pool) th.join();
+  unsigned int f = 0;
+  for (unsigned int x : flags) f |= x;
+  return f;
+}
+
+}  // namespace ara
 
 extern "C" {
 
@@ -114,7 +152,6 @@ void ara_destroy(ara_ctx* ctx) {
   dev_free(ctx->mlp_bound);
   for (int b = 0; b < 2; ++b) {
     dev_free(ctx->d_sids[b]);
-    dev_free(ctx->d_sts[b]);
     if (ctx->ev_ready[b]) cudaEventDestroy(ctx->ev_ready[b]);
     if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
   }
@@ -218,31 +255,44 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   y.n_occ = n_occ;
   y.catalog = catalog_size;
   y.max_len = max_len;
+  // the runs never read timestamps: host ones are checked on host threads while the ids cross
+  // to the device, and only device ones are staged (and checked by the kernel)
+  const bool ts_on_host = n_occ > 0 && !is_device_ptr(timestamps);
   cudaError_t e;
-  if ((e = dev_alloc(&y.ids, n_occ)) != cudaSuccess || (e = dev_alloc(&y.ts, n_occ)) != cudaSuccess ||
+  if ((e = dev_alloc(&y.ids, n_occ)) != cudaSuccess ||
+      (!ts_on_host && (e = dev_alloc(&y.ts, n_occ)) != cudaSuccess) ||
       (e = dev_alloc(&y.offsets, n_trials + 1)) != cudaSuccess) {
     cudaGetLastError();
     free_yet(y);
     return fail(ctx, ARA_ERR_OOM, "YET of %lld occurrences: %s", (long long)n_occ,
                 cudaGetErrorString(e));
   }
+  unsigned int host_flags = 0;
+  std::thread ts_check;
+  if (ts_on_host)
+    ts_check = std::thread(
+        [&]() { host_flags = validate_timestamps_host(off.data(), timestamps, n_trials); });
   if ((e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess ||
-      (e = copy_in(y.ts, timestamps, n_occ, ctx->stream)) != cudaSuccess ||
+      (!ts_on_host && (e = copy_in(y.ts, timestamps, n_occ, ctx->stream)) != cudaSuccess) ||
       (e = copy_in(y.offsets, off.data(), n_trials + 1, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
       (e = launch_validate_yet(y, ctx->d_flags, ctx->stream)) != cudaSuccess) {
     cudaGetLastError();
+    if (ts_check.joinable()) ts_check.join();
+    cudaStreamSynchronize(ctx->stream);
     free_yet(y);
     return fail(ctx, ARA_ERR_CUDA, "staging YET: %s", cudaGetErrorString(e));
   }
   unsigned int flags = 0;
-  if ((e = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
-                           ctx->stream)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+  e = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (ts_check.joinable()) ts_check.join();
+  if (e != cudaSuccess) {
     cudaGetLastError();
     free_yet(y);
     return fail(ctx, ARA_ERR_CUDA, "staging YET: %s", cudaGetErrorString(e));
   }
+  flags |= host_flags;
   if (flags) {
     free_yet(y);
     return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",

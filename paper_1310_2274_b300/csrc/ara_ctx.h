@@ -48,13 +48,12 @@ struct ara_ctx {
   int32_t table_policy = 0;              // ARA_TABLES_EAGER or ARA_TABLES_ON_DEMAND
   uint32_t* d_sel = nullptr;             // top-k selection: flags, positions, scan scratch
   int64_t sel_cap = 0;
-  // streamed runs over host-resident YETs: a copy stream, two device buffers of ids and
-  // timestamps filled in turn, and the events that hand each buffer between the streams
+  // streamed runs over host-resident YETs: a copy stream, two device buffers of ids filled in
+  // turn, and the events that hand each buffer between the streams
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_ready[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
   int32_t* d_sids[2] = {nullptr, nullptr};
-  float* d_sts[2] = {nullptr, nullptr};
   int64_t stream_cap = 0;
   int64_t stream_chunk = (int64_t)1 << 26;  // ARA_OPT_STREAM_CHUNK
   int32_t band_log2w = 0;                // band width exponent for new layers (0: automatic)

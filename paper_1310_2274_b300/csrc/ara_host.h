@@ -170,4 +170,8 @@ inline int64_t tail_count(int64_t n, double rp) {
   return k;
 }
 
+// Timestamps of a host YET checked on host threads: bit 1 if they decrease within a trial, bit 2
+// if one is NaN (the flags of the device check).  off: n_trials + 1 host offsets.
+unsigned int validate_timestamps_host(const int64_t* off, const float* ts, int64_t n_trials);
+
 }  // namespace ara

@@ -38,6 +38,7 @@ struct YetDev {
   const int32_t* h_ids = nullptr;
   const float* h_ts = nullptr;
   std::vector<int64_t> h_off;  // [n_trials + 1] (host YETs only)
+  bool ts_checked = false;     // host YETs: timestamps validated (by the first run)
   int64_t n_trials = 0;
   int64_t n_occ = 0;
   int32_t catalog = 0;

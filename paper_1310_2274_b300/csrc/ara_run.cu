@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "../../include/ara.h"
@@ -278,9 +279,10 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
 extern "C" {
 
 // A run over a host-resident YET: trials in chunks of whole trials (up to ctx->stream_chunk
-// occurrences), each chunk's ids and timestamps copied on the copy stream into one of two device
-// buffers while the previous chunk is validated and run on st; the run of a chunk skips its work
-// if any chunk so far failed validation.  Outputs are device pointers for trials [t0, t0 + n).
+// occurrences), each chunk's ids copied on the copy stream into one of two device buffers while
+// the previous chunk's ids are checked and the chunk run on st; the run of a chunk skips its work
+// if any chunk so far failed the check.  (Timestamps never cross: the caller checks them on host
+// threads.)  Outputs are device pointers for trials [t0, t0 + n).
 static ara_status run_streamed(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
                                int64_t n, double* d_ylt, double* d_oep, float* d_olt,
                                double* d_inc, cudaStream_t st) {
@@ -288,15 +290,11 @@ static ara_status run_streamed(ara_ctx* ctx, const YetDev& Y, const LayerDev& L,
   if (cap > ctx->stream_cap) {
     for (int b = 0; b < 2; ++b) {
       dev_free(ctx->d_sids[b]);
-      dev_free(ctx->d_sts[b]);
       ctx->d_sids[b] = nullptr;
-      ctx->d_sts[b] = nullptr;
     }
     ctx->stream_cap = 0;
     for (int b = 0; b < 2; ++b)
       CUDA_TRY(ctx, dev_alloc(&ctx->d_sids[b], cap));
-    for (int b = 0; b < 2; ++b)
-      CUDA_TRY(ctx, dev_alloc(&ctx->d_sts[b], cap));
     ctx->stream_cap = cap;
   }
   if (!ctx->copy_stream)
@@ -317,16 +315,13 @@ static ara_status run_streamed(ara_ctx* ctx, const YetDev& Y, const LayerDev& L,
     const int64_t ob = Y.h_off[(size_t)tb], len = Y.h_off[(size_t)te] - ob;
     const int b = k & 1;
     CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
-    if (len > 0) {
+    if (len > 0)
       CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sids[b], Y.h_ids + ob, sizeof(int32_t) * (size_t)len,
                                     cudaMemcpyHostToDevice, ctx->copy_stream));
-      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sts[b], Y.h_ts + ob, sizeof(float) * (size_t)len,
-                                    cudaMemcpyHostToDevice, ctx->copy_stream));
-    }
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev_ready[b], ctx->copy_stream));
     CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_ready[b], 0));
-    CUDA_TRY(ctx, launch_validate_yet_range(ctx->d_sids[b], ctx->d_sts[b], ob, Y.offsets, tb,
-                                            te - tb, Y.catalog, ctx->d_flags, st));
+    CUDA_TRY(ctx, launch_validate_yet_range(ctx->d_sids[b], nullptr, ob, Y.offsets, tb, te - tb,
+                                            Y.catalog, ctx->d_flags, st));
     TrialParams p = make_params(ctx, Y, L, tb, te - tb, d_ylt + (tb - t0));
     p.ids = ctx->d_sids[b];
     p.occ_base = ob;
@@ -406,6 +401,18 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   p.olt = d_olt;
   p.inc = d_inc;
   // per-occurrence outputs are written in trial order, so they keep the trial-major schedule
+  // a host YET's timestamps are checked once, on host threads, while its first run streams
+  unsigned int ts_flags = 0;
+  std::thread ts_check;
+  if (Y.host && !Y.ts_checked && Y.n_occ > 0)
+    ts_check = std::thread(
+        [&]() { ts_flags = validate_timestamps_host(Y.h_off.data(), Y.h_ts, Y.n_trials); });
+  struct Joiner {
+    std::thread& t;
+    ~Joiner() {
+      if (t.joinable()) t.join();
+    }
+  } joiner{ts_check};
   if (Y.host) {
     s = run_streamed(ctx, Y, ctx->layers[layer], t0, n, d_ylt, d_oep, d_olt, d_inc, st);
     if (s != ARA_OK) return s;
@@ -429,6 +436,11 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
     CUDA_TRY(ctx, cudaMemcpyAsync(&yet_flags, ctx->d_flags, sizeof yet_flags,
                                   cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (ts_check.joinable()) {
+      ts_check.join();
+      yet_flags |= ts_flags;
+      if (ts_flags == 0) ctx->yets[yet].ts_checked = true;
+    }
     if (yet_flags)  // nothing is written to the caller's outputs
       return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
                   (yet_flags & 1) ? " event id outside [0, catalog_size)" : "",

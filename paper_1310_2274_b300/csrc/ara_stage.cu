@@ -30,7 +30,7 @@ inline unsigned grid_for(int64_t n, int per_block = kThreads) {
 
 // ---- YET validation (warp per trial) ----------------------------------------------------------
 // flags bit 0: id out of range; bit 1: timestamp decreases within a trial; bit 2: NaN timestamp.
-// Trials [t_begin, t_begin + n_trials); ids/ts hold occurrences from occ_base on.
+// Trials [t_begin, t_begin + n_trials); ids/ts hold occurrences from occ_base on (ts may be null).
 __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float* __restrict__ ts,
                                     int64_t occ_base, const int64_t* __restrict__ off,
                                     int64_t t_begin, int64_t n_trials, int32_t catalog,
@@ -44,9 +44,11 @@ __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float
     for (int64_t q = beg + lane; q < end; q += 32) {
       const int32_t e = ids[q];
       if (e < 0 || e >= catalog) f |= 1u;
-      const float t = ts[q];
-      if (t != t) f |= 4u;
-      if (q > beg && t < ts[q - 1]) f |= 2u;
+      if (ts != nullptr) {  // null: the timestamps are checked on the host
+        const float t = ts[q];
+        if (t != t) f |= 4u;
+        if (q > beg && t < ts[q - 1]) f |= 2u;
+      }
     }
   }
   f = __reduce_or_sync(0xFFFFFFFFu, f);

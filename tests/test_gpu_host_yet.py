@@ -83,8 +83,9 @@ def test_streamed_run_matches_oracle(ara, oracle, pair):
 
 
 def test_invalid_chunks_are_reported(ara):
-    # event ids outside the catalogue in one trial, timestamps out of order in another: the
-    # chunk's validation runs before the chunk, whose trials are then skipped, and the run fails
+    # event ids outside the catalogue in one trial (checked per chunk on the device before the
+    # chunk, whose trials are then skipped), timestamps out of order in another (checked on host
+    # threads during the run): the run fails and writes nothing
     rng = np.random.default_rng(3)
     lens = np.full(400, 50)
     off = np.zeros(401, dtype=np.int64)
@@ -108,8 +109,13 @@ def test_invalid_chunks_are_reported(ara):
                 c.run(y, layer, 0, 400, out=out)
             assert ex.value.status == 1
             assert np.all(out == -7.0)  # outputs are written only on success
-            # the context stays usable: a valid range before the bad trial still runs
-            assert c.run(y, layer, 0, 100).shape == (100,)
+            if bad == "id":
+                # ids are checked chunk by chunk on the device: a range before the bad trial runs
+                assert c.run(y, layer, 0, 100).shape == (100,)
+            else:
+                # timestamps are checked for the whole YET on host threads: every run fails
+                with pytest.raises(ara.AraError):
+                    c.run(y, layer, 0, 100)
 
 
 def test_host_yet_restrictions(ara, pair):

@@ -90,3 +90,31 @@ def test_server_builds_deferred_tables(ara):
         _, d = delta(c, lambda: c.run(y, layer, 0, 5_000))
         assert d["table_evals"] > 0.99 * d["hits"]
         np.testing.assert_array_equal(c.run(y, layer, 0, 5_000), got)
+
+
+def test_portfolio_mixes_tables_and_newton(ara):
+    # one layer over ELTs whose tables exist, one over deferred ELTs: the portfolio groups them
+    # by inversion and each row equals its layer run alone
+    yet_h, elts_h, terms = workload(3_000, 100)
+    with ara.Context(seed=42) as c:
+        y = c.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, yet_h.catalog_size)
+        eager = [c.add_elt(y, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h[:2]]
+        c.set_option(ara.OPT_TABLES, ara.TABLES_ON_DEMAND)
+        lazy = c.add_elt(y, elts_h[2].event_ids, elts_h[2].mean, elts_h[2].sd,
+                         elts_h[2].max_exposure)
+        l_table = c.add_layer(eager, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+        l_newton = c.add_layer([eager[0], lazy], terms.occ_ret, terms.occ_lim, terms.agg_ret,
+                               terms.agg_lim)
+        m, d = delta(c, lambda: c.run_portfolio(y, [l_table, l_newton], 0, 3_000))
+        assert d["table_evals"] > 0 and d["inversions"] > 0
+        np.testing.assert_array_equal(m[0], c.run(y, l_table, 0, 3_000))
+        np.testing.assert_array_equal(m[1], c.run(y, l_newton, 0, 3_000))
+
+
+def test_option_values_are_checked(ara):
+    with ara.Context(seed=42) as c:
+        for opt, bad in [(ara.OPT_TABLES, 2), (ara.OPT_TABLES, -1), (ara.OPT_STREAM_CHUNK, 1000),
+                         (ara.OPT_STREAM_CHUNK, (1 << 30) + 1)]:
+            with pytest.raises(ara.AraError) as e:
+                c.set_option(opt, bad)
+            assert e.value.status == 1
