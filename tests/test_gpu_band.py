@@ -198,3 +198,38 @@ def test_oep_ragged_yet_and_newton_path(ara, oracle):
         assert np.max(np.abs(e - o_e) / scale) <= YLT_TOL
         assert np.all(e[lens == 0] == 0.0)
     assert np.count_nonzero(o_e) > 100
+
+
+def test_dense_64_elt_layer_splits_events_and_overflows_the_hit_map(ara, oracle):
+    # the widest layer (64 ELTs) over a 300-event catalogue that every ELT covers in full: each
+    # occurrence meets 64 records, so an event's hits span two rounds (split 32 hits from its
+    # first) and a chunk's 8,192 hits overflow the 512-entry hit map (events found by search);
+    # trials of 0, 1, 129 and 3,000 events
+    rng = np.random.default_rng(13)
+    lens = np.array([0, 1, 129, 3000, 7, 0, 260, 1])
+    offsets = np.zeros(lens.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    ids = rng.integers(0, 300, size=int(offsets[-1]), dtype=np.int32)
+    yet_h = synth.Yet(offsets, ids, np.zeros(ids.shape[0], np.float32), 300)
+    elts_h = []
+    for s in range(64):
+        e = synth.make_elt(300, 300, seed=500 + s)
+        elts_h.append(e)
+    assert all(e.n == 300 for e in elts_h)
+    terms = synth.Terms(1e6, 5e8, 1e8, 1e12)
+    n = lens.size
+    with ara.Context(seed=42) as c:
+        yet = c.create_yet(yet_h.offsets, yet_h.event_ids, yet_h.timestamps, 300)
+        elts = [c.add_elt(yet, e.event_ids, e.mean, e.sd, e.max_exposure) for e in elts_h]
+        c.set_option(ara.OPT_BAND_WIDTH, 11)  # one band holds the whole catalogue
+        layer = c.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+        gb, db = run_sched(ara, c, yet, layer, ara.SCHED_BAND, 0, n)
+        gt, dt = run_sched(ara, c, yet, layer, ara.SCHED_TRIAL, 0, n)
+    assert db["launches"] == 2 and dt["launches"] == 1  # band kernel + finalisation; trial kernel
+    assert db["hits"] == dt["hits"] == 64 * int(offsets[-1])
+    np.testing.assert_array_equal(gb, gt)
+    o, nc = oracle.run(yet_h, elts_h, terms, 42, elt_handles=elts)
+    assert nc == 0
+    scale = np.maximum(np.maximum(np.abs(o), terms.agg_ret), 1.0)
+    assert np.max(np.abs(gb - o) / scale) <= YLT_TOL
+    assert np.all(gb[lens == 0] == 0.0) and np.count_nonzero(gb) >= 4
