@@ -56,10 +56,11 @@ BYTES_PER_OCCURRENCE = 4.0
 BYTES_PER_TABLE_EVAL = 32.0
 BYTES_PER_TRIAL = 8.0
 
-# Device-counted FP32 work of the Newton inversion (the device algorithm's own trip counts):
-#   continued-fraction term 14.25 ops; Newton iteration 17 ops + 4 calls; per inversion 14 + 2.
+# Device-counted FP32 work of the Newton-Halley inversion (the device algorithm's own trip
+# counts): continued-fraction term 14.25 ops; iteration 17 ops + 4 calls for the Newton step and
+# 10 for Halley's correction; per inversion 14 + 2.
 FLOP_PER_CF_TERM = 14.25
-FLOP_PER_NEWTON = 17.0 + 4.0
+FLOP_PER_NEWTON = 17.0 + 4.0 + 10.0
 FLOP_PER_INVERSION = 14.0 + 2.0
 
 
