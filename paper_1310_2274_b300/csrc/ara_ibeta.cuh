@@ -87,8 +87,9 @@ ARA_HD float ara_pow2_scale_of(float s) {
 
 // K(a,b,x) = 1/(1 + d1/(1 + d2/(...))) of DLMF 8.17.22 by the Wallis recurrence on the
 // division-free equivalent fraction T = 1 + alpha_1/(beta_1 + alpha_2/(beta_2 + ...)), K = 1/T.
-// Converges quickly for x < (a+1)/(a+b+2).  Returns K; *terms counts recurrence steps.
-ARA_HD float ara_beta_cf(float a, float b, float x, int* terms) {
+// Converges quickly for x < (a+1)/(a+b+2).  Returns K once two estimates 4 terms apart agree to
+// tol (relative); *terms counts recurrence steps.
+ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e-7f) {
   const float apb = a + b;
   // T_n = A_n / B_n.  A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1.
   float Am2 = 1.0f, Am1 = 1.0f, Bm2 = 0.0f, Bm1 = 1.0f;
@@ -115,7 +116,7 @@ ARA_HD float ara_beta_cf(float a, float b, float x, int* terms) {
     Am1 *= sc; Am2 *= sc; Bm1 *= sc; Bm2 *= sc;
     if (((n + 1) & 3) == 0 || n + 2 > kCfMaxTerms) {
       res = Bm1 / Am1;
-      if (fabsf(res - prev) <= 1.2e-7f * fabsf(res)) { n += 2; break; }
+      if (fabsf(res - prev) <= tol * fabsf(res)) { n += 2; break; }
       prev = res;
     }
   }
@@ -190,7 +191,9 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
   // Below e^-69 ~ 1e-30 the loss max_l * x is far under every term of a year loss.
   if (!(t > -69.0f)) { r.x = flip ? 1.0f : 0.0f; r.t = t; return r; }
 
-  // ---- Newton iterations in t ---------------------------------------------------------------
+  // ---- Newton-Halley iterations in t --------------------------------------------------------
+  // The first iteration starts ~1e-2 from the root, so its continued fraction is summed only
+  // to 1e-4; the iterations after it (one of which must end the loop) to binary32 accuracy.
   const float thr = (a + 1.0f) / (s + 2.0f);
   bool done = false;
   int it = 0;
@@ -206,12 +209,13 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
     const float E = L0 + a * lnrx + b * lnry;
     float G, dG;
     if (x < thr) {
-      const float K = ara_beta_cf(a, b, x, &r.cf_terms);
+      const float K = ara_beta_cf(a, b, x, &r.cf_terms, it == 0 ? 1.0e-4f : 1.2e-7f);
       G = E + logf(K) - lna - lnp;
       dG = a / (y * K);
     } else {
       const float P = expf(E);
-      const float J = P * ara_beta_cf(b, a, y, &r.cf_terms) / b;  // I_{1-x}(b,a)
+      const float J =  // I_{1-x}(b,a)
+          P * ara_beta_cf(b, a, y, &r.cf_terms, it == 0 ? 1.0e-4f : 1.2e-7f) / b;
       G = log1pf(-J) - lnp;
       dG = P / (y * (1.0f - J));
     }
@@ -227,7 +231,7 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
     const float step = fabsf(tn - t);
     t = tn;
     x = expf(t);
-    if (step <= 3.0e-4f) { done = true; ++it; break; }
+    if (it > 0 && step <= 3.0e-4f) { done = true; ++it; break; }
     if (!(t > -69.0f)) { done = true; ++it; x = 0.0f; break; }
   }
   r.iters = it;
