@@ -44,7 +44,7 @@ def test_rent_then_buy(ara, oracle):
     with ara.Context(seed=42) as c:
         c.set_option(ara.OPT_TABLES, ara.TABLES_ON_DEMAND)
         y, hs, layer = stage(ara, c, yet_h, elts_h, terms)
-        buy_run = int(np.ceil(ara.TABLE_BUY_HITS / 200.0))  # 9th run: 8 x 200 + 200 >= 1700
+        buy_run = int(np.ceil(ara.TABLE_BUY_HITS / 200.0))  # the first k with 200 k >= threshold
         for r in range(1, buy_run + 2):
             g, d = delta(c, lambda: c.run(y, layer, 0, n))
             if r < buy_run:
@@ -59,14 +59,15 @@ def test_rent_then_buy(ara, oracle):
 
 
 def test_large_run_buys_at_once_and_partial_ranges_rent(ara):
-    yet_h, elts_h, terms = workload(20_000, 1000)  # 2,000 expected hits per record
+    yet_h, elts_h, terms = workload(20_000, 1200)  # 2,400 expected hits per record
     with ara.Context(seed=42) as c:
         c.set_option(ara.OPT_TABLES, ara.TABLES_ON_DEMAND)
         y, hs, layer = stage(ara, c, yet_h, elts_h, terms)
-        # a tenth of the trials: 200 per record, rented
+        assert 240 < ara.TABLE_BUY_HITS <= 2_400
+        # a tenth of the trials: 240 per record, rented
         _, d = delta(c, lambda: c.run(y, layer, 0, 2_000))
         assert d["table_evals"] == 0
-        # the rest: 200 + 1,800 >= 1,700, bought before the run
+        # the rest: 240 + 2,160 reaches the threshold, bought before the run
         _, d = delta(c, lambda: c.run(y, layer, 2_000, 18_000))
         assert d["table_evals"] > 0.99 * d["hits"]
         # a new layer over the same ELTs reuses their tables at once
