@@ -445,6 +445,28 @@ def run_ours(a):
     portfolio = {"programs": 3, "layers": len(pf_layers), "elts_per_layer_mean":
                  pf_elts / len(pf_layers), "by_trials": pf_rows}
 
+    # ---- where the time goes (the paper's split of lookup and secondary uncertainty, §5): the
+    # same layer with every SD zero, so each hit is looked up, drawn and loaded but not inverted
+    z_elts = [ctx.add_elt(yet, e.event_ids, e.mean, np.zeros(e.n), e.max_exposure)
+              for e in elts_h]
+    z_layer = ctx.add_layer(z_elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
+    ctx.run(yet, z_layer, 0, n, out=ylt, stream=stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(max(3, min(10, a.steps)))]
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.run(yet, z_layer, 0, n, out=ylt, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sd0_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    ctx.free_layer(z_layer)
+    for e in z_elts:
+        ctx.free_elt(e)
+    time_split = {"sd0_ms": sd0_ms, "full_ms": kern_ms,
+                  "inversion_share": 1.0 - sd0_ms / kern_ms,
+                  "note": "sd0: lookups, draws, piece loads, event sums and terms without the "
+                          "table evaluation; the rest of the full run is the inversion"}
+
     # ---- correlated standard deviations (paper §3.1-3.2) on the same YET ----------------------
     # each record's SD split into independent and correlated parts: the occurrence's shared
     # uniform enters every hit through Phi^-1, a linear combination and Phi
@@ -538,6 +560,7 @@ def run_ours(a):
         "event_outputs": events,
         "portfolio": portfolio,
         "correlated_sd": correlated,
+        "time_split": time_split,
         "uncertified_records": s1["uncertified"],
         "risk_measures": {"rps": rps, "pml": [float(v) for v in pml],
                           "tvar": [float(v) for v in tvar]},
