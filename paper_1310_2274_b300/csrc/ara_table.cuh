@@ -21,40 +21,119 @@ namespace ara {
 
 constexpr double kTableTol = 1e-6;
 
-// K = 1/(1 + d1/(1 + ...)) of DLMF 8.17.22 in binary64 by the Wallis recurrence of the
+// ---- double-float arithmetic -------------------------------------------------------------------
+// A value hi + lo of two binary32 numbers (|lo| <= ulp(hi)/2, ~48 significant bits): the FP64 pipe
+// of this part is 1/64 of the FP32 one, so the build's continued fraction runs in pairs of
+// binary32 (Dekker's and Knuth's error-free sum and product, the product through an FMA).  The
+// additions and products are the round-to-nearest intrinsics on the device, so that the compiler
+// never fuses them into FMAs, which would break the error-free transformations.
+struct DF {
+  float hi, lo;
+};
+#ifdef __CUDA_ARCH__
+ARA_HD float df_add_rn(float a, float b) { return __fadd_rn(a, b); }
+ARA_HD float df_sub_rn(float a, float b) { return __fsub_rn(a, b); }
+ARA_HD float df_mul_rn(float a, float b) { return __fmul_rn(a, b); }
+#else
+ARA_HD float df_add_rn(float a, float b) { return a + b; }
+ARA_HD float df_sub_rn(float a, float b) { return a - b; }
+ARA_HD float df_mul_rn(float a, float b) { return a * b; }
+#endif
+ARA_HD DF df_from(double d) {
+  DF r;
+  r.hi = (float)d;
+  r.lo = (float)(d - (double)r.hi);
+  return r;
+}
+ARA_HD double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+// s + e with |s| >= |e| (or s = 0), renormalised
+ARA_HD DF df_quick(float s, float e) {
+  DF r;
+  r.hi = df_add_rn(s, e);
+  r.lo = df_sub_rn(e, df_sub_rn(r.hi, s));
+  return r;
+}
+ARA_HD DF df_add(DF a, DF b) {
+  const float s = df_add_rn(a.hi, b.hi);
+  const float bb = df_sub_rn(s, a.hi);
+  float e = df_add_rn(df_sub_rn(a.hi, df_sub_rn(s, bb)), df_sub_rn(b.hi, bb));
+  e = df_add_rn(e, df_add_rn(a.lo, b.lo));
+  return df_quick(s, e);
+}
+ARA_HD DF df_add_f(DF a, float b) {
+  const float s = df_add_rn(a.hi, b);
+  const float bb = df_sub_rn(s, a.hi);
+  float e = df_add_rn(df_sub_rn(a.hi, df_sub_rn(s, bb)), df_sub_rn(b, bb));
+  e = df_add_rn(e, a.lo);
+  return df_quick(s, e);
+}
+ARA_HD DF df_neg(DF a) {
+  a.hi = -a.hi;
+  a.lo = -a.lo;
+  return a;
+}
+ARA_HD DF df_mul(DF a, DF b) {
+  const float p = df_mul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+ARA_HD DF df_mul_f(DF a, float b) {
+  const float p = df_mul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return df_quick(p, e);
+}
+ARA_HD DF df_scale(DF a, float s) {  // s a power of two: exact
+  a.hi *= s;
+  a.lo *= s;
+  return a;
+}
+
+// K = 1/(1 + d1/(1 + ...)) of DLMF 8.17.22 in double-float by the Wallis recurrence of the
 // division-free equivalent fraction (numerators -(a+b)x, -(a+m)(a+b+m)x, m(b-m)x; denominators
-// a+n), rescaled by powers of two every step pair.
-ARA_HD double ara_beta_cf_f64(double a, double b, double x) {
-  const double apb = a + b;
-  double Am2 = 1.0, Am1 = 1.0, Bm2 = 0.0, Bm1 = 1.0, pA = 1.0, pB = 1.0;
+// a+n), rescaled by a power of two every step pair.  Converged when B/A moved by at most 1e-10
+// relative since the previous pair, tested without a division: |B pA - pB A| <= 1e-10 |B pA|
+// (pA, pB: the previous pair at the same scale).  The knots need L to ~1e-9 (pieces fit to ~1e-8,
+// certified to 1e-6).
+ARA_HD double ara_beta_cf_f64(double a64, double b64, double x64) {
+  const DF a = df_from(a64), b = df_from(b64), x = df_from(x64);
+  const DF apb = df_add(a, b);
+  DF Am2 = {1.0f, 0.0f}, Am1 = {1.0f, 0.0f}, Bm2 = {0.0f, 0.0f}, Bm1 = {1.0f, 0.0f};
+  DF pA = Am1, pB = Bm1;
   for (int n = 1; n < 4000; n += 2) {
-    const double m = 0.5 * (double)(n - 1);
-    const double al_odd = (n == 1) ? -apb * x : -(a + m) * (apb + m) * x;
-    const double be_odd = a + (double)n;
-    double A = be_odd * Am1 + al_odd * Am2;
-    double B = be_odd * Bm1 + al_odd * Bm2;
+    const float m = 0.5f * (float)(n - 1);  // exact
+    const DF al_odd = (n == 1) ? df_neg(df_mul(apb, x))
+                               : df_neg(df_mul(df_mul(df_add_f(a, m), df_add_f(apb, m)), x));
+    const DF be_odd = df_add_f(a, (float)n);
+    DF A = df_add(df_mul(be_odd, Am1), df_mul(al_odd, Am2));
+    DF B = df_add(df_mul(be_odd, Bm1), df_mul(al_odd, Bm2));
     Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
-    const double m2 = m + 1.0;
-    const double al_even = m2 * (b - m2) * x;
-    const double be_even = a + (double)(n + 1);
-    A = be_even * Am1 + al_even * Am2;
-    B = be_even * Bm1 + al_even * Bm2;
+    const float m2 = m + 1.0f;
+    const DF al_even = df_mul(df_mul_f(df_add_f(b, -m2), m2), x);
+    const DF be_even = df_add_f(a, (float)(n + 1));
+    A = df_add(df_mul(be_even, Am1), df_mul(al_even, Am2));
+    B = df_add(df_mul(be_even, Bm1), df_mul(al_even, Bm2));
     Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
-    // converged when B/A moved by at most 1e-10 relative since the previous pair, tested without
-    // a division: |B pA - pB A| <= 1e-10 |B pA| (pA, pB: the previous pair at the same scale).
-    // The knots need L to ~1e-9 (pieces fit to ~1e-8, certified to 1e-6); a tighter test only
-    // adds binary64 terms, the bound of the build (1e-15 took 13% longer, same tables)
-    const bool done = fabs(Bm1 * pA - pB * Am1) <= 1e-10 * fabs(Bm1 * pA);
-    if (((n >> 1) & 3) == 3) {  // a pair grows A, B by about (a+n)^2: rescale every 4th pair
-      int e;
-      frexp(Am1, &e);
-      Am1 = ldexp(Am1, -e); Am2 = ldexp(Am2, -e); Bm1 = ldexp(Bm1, -e); Bm2 = ldexp(Bm2, -e);
+    const DF lhs = df_mul(Bm1, pA);
+    const DF d = df_add(lhs, df_neg(df_mul(pB, Am1)));
+    const bool done = fabsf(d.hi) <= 1e-10f * fabsf(lhs.hi);
+    // a pair grows A, B by about (a+n)^2: rescale every pair to stay inside binary32's range
+    if (Am1.hi != 0.0f && isfinite(Am1.hi)) {
+      const float sc = ara_pow2_scale_of(Am1.hi);
+      Am1 = df_scale(Am1, sc); Am2 = df_scale(Am2, sc);
+      Bm1 = df_scale(Bm1, sc); Bm2 = df_scale(Bm2, sc);
     }
     pA = Am1;
     pB = Bm1;
     if (done) break;
   }
-  return Bm1 / Am1;
+  // K = B / A: a binary32 quotient corrected by the double-float remainder
+  const float q1 = Bm1.hi / Am1.hi;
+  const DF r = df_add(Bm1, df_neg(df_mul_f(Am1, q1)));
+  const float q2 = r.hi / Am1.hi;
+  return (double)q1 + (double)q2;
 }
 
 // ln I_x(a,b) for x = e^r (DLMF 8.17.22; past (a+1)/(a+b+2) through DLMF 8.17.4); lna = ln a.
