@@ -111,7 +111,7 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_OPT_TABLES 7
 #define ARA_TABLES_EAGER 0
 #define ARA_TABLES_ON_DEMAND 1
-#define ARA_TABLE_BUY_HITS 1200.0
+#define ARA_TABLE_BUY_HITS 2100.0
 /* ARA_OPT_STREAM_CHUNK: occurrences per copied chunk of a host-resident YET's runs (1024 .. 2^30;
  * default 2^26, two buffers of 4 bytes per occurrence on the device; a chunk always holds whole
  * trials, so it grows to the longest trial if needed). */

@@ -28,6 +28,7 @@ void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st) {
   mem_free(l.packed, ordered, st);
   mem_free(l.packed_rec, ordered, st);
   mem_free(l.corr, ordered, st);
+  mem_free(l.starts, ordered, st);
   l = LayerDev();
 }
 
@@ -402,6 +403,7 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
     if (!defer) dev_free(d_ab64);  // deferred tables keep (alpha, beta) in e.ab64
   };
   if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
+      (err = dev_alloc(&e.starts, n * kStartFloats)) != cudaSuccess ||
       (!defer && (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess) ||
       (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
       (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess ||
@@ -425,6 +427,7 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
       (err = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
       (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_sdc, d_mx, y.catalog, e.recs, d_ab64,
                                 e.corr, d_dup, ctx->d_flags, ctx->stream)) != cudaSuccess ||
+      (err = launch_build_starts(n, e.recs, e.starts, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
       (!defer &&
        (err = launch_build_tables(n, e.recs, d_ab64, e.tables, d_uncert, ctx->stream)) != cudaSuccess) ||
@@ -478,7 +481,7 @@ ara_status ara_free_elt(ara_ctx* ctx, int32_t elt) {
 ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
                            double occ_lim, double agg_ret, double agg_lim, bool wide,
                            cudaStream_t st, bool may_build_band, bool ordered,
-                           LayerDev* out) {
+                           LayerDev* out, bool starts) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
   if (!out || !elts) return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
   if (n_elts < 1 || n_elts > kMaxLayerElts)
@@ -552,17 +555,20 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   // packed records, then the records' tables copied into packed order (one gather per hit);
   // correlated weights only when some ELT of the layer has a correlated SD
   const TablePiece** d_src = nullptr;
-  bool has_corr = false, all_tables = true;
+  bool has_corr = false, all_tables = true, all_starts = starts;
   for (int j = 0; j < n_elts; ++j) {
     has_corr = has_corr || ctx->elts[elts[j]].corr != nullptr;
     all_tables = all_tables && ctx->elts[elts[j]].tables != nullptr;
+    all_starts = all_starts && ctx->elts[elts[j]].starts != nullptr;
   }
   if ((err = mem_alloc(&L.packed, L.n_packed, ordered, st)) != cudaSuccess ||
       (err = mem_alloc(&L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
       (all_tables && (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) !=
                          cudaSuccess) ||
       (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess ||
-      (has_corr && (err = mem_alloc(&L.corr, L.n_packed, ordered, st)) != cudaSuccess)) {
+      (has_corr && (err = mem_alloc(&L.corr, L.n_packed, ordered, st)) != cudaSuccess) ||
+      (all_starts &&
+       (err = mem_alloc(&L.starts, L.n_packed * kStartFloats, ordered, st)) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
     mem_free(d_src, ordered, st);
@@ -571,7 +577,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
-                               L.corr, st);
+                               L.corr, L.starts, st);
   if (err == cudaSuccess && all_tables) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   cleanup();

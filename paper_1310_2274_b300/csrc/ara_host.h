@@ -100,6 +100,7 @@ inline void free_elt(EltDev& e) {
   dev_free(e.tables);
   dev_free(e.corr);
   dev_free(e.ab64);
+  dev_free(e.starts);
   e = EltDev();
 }
 

@@ -42,9 +42,21 @@ using std::isfinite;
 struct float4 {
   float x, y, z, w;
 };
+struct float2 {
+  float x, y;
+};
 #endif
 
 namespace ara {
+ARA_HD float ara_bits_to_float(int i) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(i);
+#else
+  float f;
+  memcpy(&f, &i, 4);
+  return f;
+#endif
+}
 ARA_HD float4 ara_make_float4(float x, float y, float z, float w) {
   float4 v;
   v.x = x; v.y = y; v.z = z; v.w = w;
@@ -156,7 +168,10 @@ struct BetaRec {
 // The tail is chosen per record: if u > p0 the root lies above the mean, and the symmetric
 // problem I_y(b,a) = 1 - u (exact on the uniform grid) is solved for y = 1 - x instead, so the
 // unknown solved for is always below the mean of its distribution.
-ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
+// start_logit: an estimate of ln(x / (1 - x)) accurate to ~1e-4 (a start table's value), or
+// anything not below 1e29 to use the analytic start.  From a good start the first iteration sums
+// its continued fraction fully and may end the loop.
+ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u, float start_logit = 1e30f) {
   IbetaResult r;
   r.iters = 0;
   r.cf_terms = 0;
@@ -187,13 +202,17 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
                         (lam + 5.0f / 6.0f - 2.0f / (3.0f * h));
     t = lna - logf(a + b * expf(2.0f * w));
   }
+  const bool good = start_logit < 1e29f;  // false for NaN too
+  if (good) t = flip ? -log1pf(expf(start_logit)) : -log1pf(expf(-start_logit));
   t = fminf(t, lnx0);  // the root is below the mean
   // Below e^-69 ~ 1e-30 the loss max_l * x is far under every term of a year loss.
   if (!(t > -69.0f)) { r.x = flip ? 1.0f : 0.0f; r.t = t; return r; }
 
   // ---- Newton-Halley iterations in t --------------------------------------------------------
-  // The first iteration starts ~1e-2 from the root, so its continued fraction is summed only
-  // to 1e-4; the iterations after it (one of which must end the loop) to binary32 accuracy.
+  // From the analytic start (~1e-2 from the root) the first iteration's continued fraction is
+  // summed only to 1e-4 and cannot end the loop; later iterations (and every one from a start
+  // table's estimate) are summed to binary32 accuracy.
+  const float cf_first = good ? 1.2e-7f : 1.0e-4f;
   const float thr = (a + 1.0f) / (s + 2.0f);
   bool done = false;
   int it = 0;
@@ -209,13 +228,13 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
     const float E = L0 + a * lnrx + b * lnry;
     float G, dG;
     if (x < thr) {
-      const float K = ara_beta_cf(a, b, x, &r.cf_terms, it == 0 ? 1.0e-4f : 1.2e-7f);
+      const float K = ara_beta_cf(a, b, x, &r.cf_terms, it == 0 ? cf_first : 1.2e-7f);
       G = E + logf(K) - lna - lnp;
       dG = a / (y * K);
     } else {
       const float P = expf(E);
       const float J =  // I_{1-x}(b,a)
-          P * ara_beta_cf(b, a, y, &r.cf_terms, it == 0 ? 1.0e-4f : 1.2e-7f) / b;
+          P * ara_beta_cf(b, a, y, &r.cf_terms, it == 0 ? cf_first : 1.2e-7f) / b;
       G = log1pf(-J) - lnp;
       dG = P / (y * (1.0f - J));
     }
@@ -231,7 +250,7 @@ ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u) {
     const float step = fabsf(tn - t);
     t = tn;
     x = expf(t);
-    if (it > 0 && step <= 3.0e-4f) { done = true; ++it; break; }
+    if ((it > 0 || good) && step <= 3.0e-4f) { done = true; ++it; break; }
     if (!(t > -69.0f)) { done = true; ++it; x = 0.0f; break; }
   }
   r.iters = it;
@@ -270,6 +289,42 @@ struct TablePiece {
   float mx;       // the record's loss scale (the mean itself for a sd = 0 record)
   uint32_t flag;  // kPiece*
 };
+
+// ---- start tables for the Newton-Halley inversion ---------------------------------------------
+// Where a record's certified table does not exist (tables on demand, before they pay off) the
+// inversion starts from a coarse table built in binary32 when the ELT is staged: the same
+// coordinate z, 16 pieces of width 4 kTableH, a cubic Hermite of the log-odds L from L and
+// dL/dz at the knots (16 bytes a piece, 256 bytes a record).  It is not certified: it is only a
+// start (~2e-6 from the root in ln x on average, 1.4e-4 at worst over the ELT value law, so a
+// single Halley step lands within ~1e-11), and a piece whose knots failed holds NaN, which sends
+// the inversion back to its analytic start.
+constexpr int kStartPieces = 16;
+constexpr int kStartCoefs = 6;                      // quintic Hermite: L, L', L'' at both knots
+constexpr int kStartFloats = kStartPieces * kStartCoefs;
+constexpr float kStartInvH = kTableInvH * 0.25f;  // 1 / (4 kTableH)
+
+// Estimated log-odds of the quantile of u from a record's start table (NaN where none).
+ARA_HD float ara_start_logit(const float* st, float u) {
+  const bool lower = u < 0.5f;
+  const float q = lower ? u : 1.0f - u;
+#ifdef __CUDA_ARCH__
+  const float t = sqrtf(-1.38629436f * __log2f(q));
+#else
+  const float t = sqrtf(-2.0f * logf(q));
+#endif
+  const float z = lower ? t - kTableTm : kTableTm - t;
+  const float pos = fminf(fmaxf((z + kTableZ) * kStartInvH, 0.0f), (float)kStartPieces);
+  const int k = pos < (float)(kStartPieces - 1) ? (int)pos : kStartPieces - 1;
+  const float tau = pos - (float)k;
+  const float2* c2 = reinterpret_cast<const float2*>(st + k * kStartCoefs);
+#ifdef __CUDA_ARCH__
+  const float2 c01 = __ldg(c2), c23 = __ldg(c2 + 1), c45 = __ldg(c2 + 2);
+#else
+  const float2 c01 = c2[0], c23 = c2[1], c45 = c2[2];
+#endif
+  return c01.x +
+         tau * (c01.y + tau * (c23.x + tau * (c23.y + tau * (c45.x + tau * c45.y))));
+}
 static_assert(sizeof(TablePiece) == 32, "a table piece is one 32-byte sector");
 
 ARA_HD float ara_exp2_fast(float r) {

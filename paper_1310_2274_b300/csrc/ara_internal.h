@@ -59,6 +59,7 @@ struct EltDev {
   TablePiece* tables = nullptr;  // [n * kTablePieces] certified quantile tables
   float* corr = nullptr;     // [n] normalised correlated weights (NULL: every sigma_C = 0)
   int64_t n_uncertified = 0; // records whose table failed certification
+  float* starts = nullptr;   // [n * kStartFloats] start tables of the Newton-Halley inversion
   double2* ab64 = nullptr;   // [n] binary64 (alpha, beta), kept until the tables are built
   double rent_hits = 0.0;    // expected hits per record served by Newton while tables were absent
 };
@@ -76,6 +77,7 @@ struct LayerDev {
   uint32_t* evt = nullptr;         // [catalog * (1 + mask_words)] entries, padded to 2 or 4 words
   BetaRec* packed = nullptr;       // [n_packed]
   TablePiece* tables = nullptr;    // [n_packed * kTablePieces] the records' tables, same order
+  float* starts = nullptr;         // [n_packed * kStartFloats] the records' start tables
   uint32_t* packed_rec = nullptr;  // [n_packed] caller record index (verification)
   float* corr = nullptr;           // [n_packed] correlated weights (NULL: none in the layer)
   int64_t n_packed = 0;
@@ -90,6 +92,7 @@ struct TrialParams {
   const BetaRec* recs;
   const TablePiece* tables;  // the layer's tables, kTablePieces per packed record
   const float* corr;         // packed correlated weights (paper §3.2), NULL when all are zero
+  const float* starts;       // packed start tables of the Newton-Halley inversion, or NULL
   const uint32_t* rec_idx;
   int32_t handles[kMaxLayerElts];
   int32_t n_slots;
@@ -167,10 +170,13 @@ cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t
 int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, int mask_words,
                                int64_t catalog, uint32_t* d_evt, cudaStream_t st);
+// packed_starts (optional): the records' start tables in packed order
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
-                                 float* packed_corr, cudaStream_t st);
+                                 float* packed_corr, float* packed_starts, cudaStream_t st);
+// starts[n * kStartFloats]: the records' start tables of the Newton-Halley inversion
+cudaError_t launch_build_starts(int64_t n, const BetaRec* recs, float* starts, cudaStream_t st);
 // ab64[n]: each record's (alpha, beta) in binary64, as written by launch_prepare_elt.
 cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
                                 TablePiece* tables, unsigned long long* d_uncertified,

@@ -101,7 +101,7 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   err = cudaSuccess;
   for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[L.handles[j]], j, L.mask_words, L.evt, L.packed, d_src,
-                               L.packed_rec, L.corr, ctx->stream);
+                               L.packed_rec, L.corr, nullptr, ctx->stream);
   if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   dev_free(d_src);
@@ -114,7 +114,46 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   return ARA_OK;
 }
 
+// The layer's packed start tables (its ELTs' own, built at staging), for runs that invert by
+// Newton-Halley steps.
+static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
+  if (L.starts) return ARA_OK;
+  for (int j = 0; j < L.n_slots; ++j)
+    if (!ctx->elts[L.handles[j]].starts) return ARA_OK;  // (not expected) analytic starts
+  const TablePiece** d_src = nullptr;
+  cudaError_t err;
+  if ((err = dev_alloc(&L.starts, L.n_packed * kStartFloats)) != cudaSuccess ||
+      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(L.starts);
+    L.starts = nullptr;
+    dev_free(d_src);
+    return fail(ctx, ARA_ERR_OOM, "layer start tables: %s", cudaGetErrorString(err));
+  }
+  err = cudaSuccess;
+  for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
+    err = launch_layer_scatter(ctx->elts[L.handles[j]], j, L.mask_words, L.evt, L.packed, d_src,
+                               L.packed_rec, L.corr, L.starts, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  dev_free(d_src);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(L.starts);
+    L.starts = nullptr;
+    return fail(ctx, ARA_ERR_CUDA, "layer start tables: %s", cudaGetErrorString(err));
+  }
+  return ARA_OK;
+}
+
+static ara_status rent_or_buy(ara_ctx* ctx, LayerDev& L, int64_t n);
+
 ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n) {
+  const ara_status s = rent_or_buy(ctx, L, n);
+  if (s != ARA_OK) return s;
+  return layer_inversion(ctx, L) == 1 ? ensure_layer_starts(ctx, L) : ARA_OK;
+}
+
+static ara_status rent_or_buy(ara_ctx* ctx, LayerDev& L, int64_t n) {
   if (L.tables || inversion_mode(ctx) != 0) return ARA_OK;
   if (ctx->table_policy == ARA_TABLES_EAGER) return ensure_layer_tables(ctx, L);
   const YetDev& Y = ctx->yets[L.yet];
@@ -239,6 +278,7 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   p.recs = L.packed;
   p.tables = L.tables;
   p.corr = L.corr;
+  p.starts = L.starts;
   p.rec_idx = L.packed_rec;
   for (int j = 0; j < kMaxLayerElts; ++j) p.handles[j] = L.handles[j];
   p.n_slots = L.n_slots;

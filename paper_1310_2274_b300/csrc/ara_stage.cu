@@ -164,7 +164,8 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
                                      int mask_words, const uint32_t* __restrict__ evt,
                                      BetaRec* packed, const TablePiece** table_src,
                                      uint32_t* packed_rec, const float* __restrict__ corr,
-                                     float* packed_corr) {
+                                     float* packed_corr, const float* __restrict__ starts,
+                                     float* packed_starts) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t e = ids[r];
@@ -183,6 +184,12 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
   table_src[base + rank] = tables + r * kTablePieces;
   if (packed_corr) packed_corr[base + rank] = corr ? corr[r] : 0.0f;
   packed_rec[base + rank] = (uint32_t)r;
+  if (packed_starts && starts) {  // 384 bytes as 8-byte words
+    const float2* src = reinterpret_cast<const float2*>(starts + r * kStartFloats);
+    float2* dst = reinterpret_cast<float2*>(packed_starts + (int64_t)(base + rank) * kStartFloats);
+#pragma unroll 8
+    for (int k = 0; k < kStartFloats / 2; ++k) dst[k] = src[k];
+  }
 }
 
 // ---- exclusive scan of uint32 (three passes: block sums, scan of sums, block scans) ----------
@@ -345,11 +352,12 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
-                                 float* packed_corr, cudaStream_t st) {
+                                 float* packed_corr, float* packed_starts, cudaStream_t st) {
   if (e.n == 0) return cudaSuccess;
   layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, e.tables, slot,
                                                            mask_words, d_evt, packed, table_src,
-                                                           packed_rec, e.corr, packed_corr);
+                                                           packed_rec, e.corr, packed_corr,
+                                                           e.starts, packed_starts);
   count_launches(1);
   return cudaGetLastError();
 }

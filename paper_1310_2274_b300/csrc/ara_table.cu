@@ -23,6 +23,12 @@ __global__ void build_tables_kernel(int64_t n, const BetaRec* __restrict__ recs,
   if (!ok) atomicAdd(n_uncertified, 1ull);
 }
 
+__global__ void build_starts_kernel(int64_t n, const BetaRec* __restrict__ recs, float* starts) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  ara_build_start_record(recs[r], starts + r * kStartFloats);
+}
+
 // Layer copy of the tables in packed order: one warp per packed record, 2 KB each.
 __global__ void gather_tables_kernel(int64_t n, const TablePiece* const* __restrict__ src,
                                      TablePiece* __restrict__ dst) {
@@ -45,6 +51,15 @@ cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* a
   const int threads = 128;
   build_tables_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
       n, recs, ab64, tables, d_uncertified);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_starts(int64_t n, const BetaRec* recs, float* starts, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 128;
+  build_starts_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(n, recs,
+                                                                                  starts);
   count_launches(1);
   return cudaGetLastError();
 }

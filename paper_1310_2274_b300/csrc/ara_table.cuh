@@ -329,4 +329,74 @@ ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, Ta
   *ok_out = ok;
 }
 
+// Fills a record's start table (kStartPieces quintics of the log-odds in tau, kStartCoefs
+// floats each, see ara_start_logit) from binary32 inversions at the knots
+// z_i = -kTableZ + 4 i kTableH: the lower tail through the record, the upper through the swapped
+// record at q = 1 - u, so that u near 1 keeps its precision; the derivatives in z are those of
+// logit_knot (L'' taken on each piece's own side of the median).  Pieces with a failed knot are
+// NaN.
+ARA_HD void ara_build_start_record(const BetaRec& br, float* st) {
+  if (!(br.a > 0.0f)) {  // sd = 0: never inverted
+    for (int k = 0; k < kStartFloats; ++k) st[k] = 0.0f;
+    return;
+  }
+  BetaRec sw;
+  sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
+  sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
+  const float lnB = br.a * br.lnx0 + br.b * br.lny0 - br.L0;
+  const float H = 4.0f * kTableH;
+  float L[kStartPieces + 1], D[kStartPieces + 1], X[kStartPieces + 1], Y[kStartPieces + 1];
+  bool ok[kStartPieces + 1];
+  for (int i = 0; i <= kStartPieces; ++i) {
+    const float z = -kTableZ + (float)i * H;
+    const float t = kTableTm + fabsf(z);
+    const float lnq = -0.5f * t * t;
+    const float q = expf(lnq);
+    float lnx, ln1mx;
+    bool conv;
+    if (z >= 0.0f) {  // lower tail: u = q
+      const IbetaResult r = ara_inv_beta(br, q);
+      conv = r.converged;
+      if (q > br.p0) { ln1mx = r.t; lnx = log1pf(-expf(r.t)); }
+      else { lnx = r.t; ln1mx = log1pf(-expf(r.t)); }
+    } else {  // upper tail: 1 - x ~ Beta(b, a) at probability q
+      const IbetaResult r = ara_inv_beta(sw, q);
+      conv = r.converged;
+      if (q > sw.p0) { lnx = r.t; ln1mx = log1pf(-expf(r.t)); }
+      else { ln1mx = r.t; lnx = log1pf(-expf(r.t)); }
+    }
+    L[i] = lnx - ln1mx;
+    D[i] = -t * expf(lnq + lnB - br.a * lnx - br.b * ln1mx);
+    X[i] = expf(lnx);
+    Y[i] = expf(ln1mx);
+    ok[i] = conv && isfinite(L[i]) && isfinite(D[i]);
+  }
+  for (int k = 0; k < kStartPieces; ++k) {
+    float* c = st + k * kStartCoefs;
+    if (!(ok[k] && ok[k + 1])) {
+      for (int j = 0; j < kStartCoefs; ++j) c[j] = ara_bits_to_float(0x7FC00000);
+      continue;
+    }
+    // L'' = L'^2 (b x - a (1-x)) - s (t^2 - 1) L' / t, s the piece's side of the median
+    const float s = k < kStartPieces / 2 ? -1.0f : 1.0f;
+    float E[2];
+    for (int e = 0; e < 2; ++e) {
+      const int i = k + e;
+      const float t = kTableTm + fabsf(-kTableZ + (float)i * H);
+      E[e] = D[i] * D[i] * (br.b * X[i] - br.a * Y[i]) - s * (t * t - 1.0f) * D[i] / t;
+    }
+    c[0] = L[k];
+    c[1] = H * D[k];
+    c[2] = 0.5f * H * H * E[0];
+    const float A = L[k + 1] - (c[0] + c[1] + c[2]);
+    const float B = H * D[k + 1] - (c[1] + 2.0f * c[2]);
+    const float C = H * H * E[1] - 2.0f * c[2];
+    c[3] = 10.0f * A - 4.0f * B + 0.5f * C;
+    c[4] = -15.0f * A + 7.0f * B - C;
+    c[5] = 6.0f * A - 3.0f * B + 0.5f * C;
+    if (!(isfinite(c[3]) && isfinite(c[4]) && isfinite(c[5])))
+      for (int j = 0; j < kStartCoefs; ++j) c[j] = ara_bits_to_float(0x7FC00000);
+  }
+}
+
 }  // namespace ara

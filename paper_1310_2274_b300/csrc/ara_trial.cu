@@ -239,7 +239,11 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
             n_tab += 1u;
           } else {
             const IbetaResult ib =
-                INV == 1 ? ara_inv_beta(rec, u) : newton_fallback(P.recs + pos, u);
+                INV == 1 ? ara_inv_beta(rec, u,
+                                        P.starts != nullptr
+                                            ? ara_start_logit(P.starts + (size_t)pos * kStartFloats, u)
+                                            : 1e30f)
+                         : newton_fallback(P.recs + pos, u);
             x = ib.x;
             nc += ib.converged ? 0u : 1u;
             n_inv += 1u;
