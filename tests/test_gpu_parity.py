@@ -336,3 +336,22 @@ def test_top_k_and_shard_risk_measures(ctx, oracle):
     np.testing.assert_allclose(gt, ot, rtol=1e-12)
     with pytest.raises(Exception):
         ctx.risk_measures_n(cand[:10], n, rps)  # too few candidates for the 1-in-10 tail
+
+
+def test_start_tables_give_one_halley_step(ara, oracle):
+    # Newton-Halley inversions over the paper-scale ELTs start from the per-record start tables:
+    # about one iteration per inversion, results within the YLT tolerance of the oracle
+    w = synth.paper(n_trials=600)
+    with ara.Context(seed=42) as c:
+        yet, elts, layer = c.stage_workload(w)
+        c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+        s0 = c.stats()
+        g = c.run(yet, layer, 0, 600)
+        s1 = c.stats()
+    d = {k: s1[k] - s0[k] for k in s0}
+    assert d["inversions"] > 0.99 * d["hits"]
+    assert d["newton"] <= 1.01 * d["inversions"]
+    o, nc = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=elts)
+    assert nc == 0
+    worst, _ = ylt_close(g, o, w.terms)
+    assert worst <= YLT_TOL
