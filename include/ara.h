@@ -74,7 +74,11 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
  *   ARA_INV_TABLE (default): each record's quantile function, tabulated when its ELT is staged
  *     (32 quintic pieces per tail in t = sqrt(-2 ln u), certified at every piece's midpoint to
  *     1e-6 relative in x against the Newton inversion); records failing certification use Newton;
- *   ARA_INV_NEWTON: Newton's method in ln x on the continued fraction for every hit. */
+ *   ARA_INV_NEWTON: Halley's method (Newton's step with the free second derivative) in ln x on
+ *     the continued fraction for every hit, started from the record's start table (16 binary32
+ *     quintic pieces of the log-odds, built when the ELT is staged, 384 bytes per record), one
+ *     step in almost every case; also used by runs over ELTs whose certified tables are deferred
+ *     (ARA_OPT_TABLES). */
 #define ARA_OPT_PRECISION 1
 #define ARA_OPT_SEED 2
 #define ARA_OPT_SURROGATE 3
@@ -157,7 +161,8 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
  * (primary uncertainty only).  Values are staged in FP64 once: alpha, beta (moment matching with
  * the sigma_beta_max clamp of §3.3, sigma_beta set to sigma_beta_max (1 - 2^-20) when above it)
  * and the constants of the inversion, then stored as binary32 (32 bytes per record); the record's
- * certified quantile table is built at the same time (2 KB per record, see ARA_OPT_INVERSION).
+ * certified quantile table is built at the same time (2 KB per record, see ARA_OPT_INVERSION;
+ * deferred under ARA_TABLES_ON_DEMAND), and its start table (384 bytes per record).
  * The handle number keys the record's uniforms: Philox4x32-10 counter (k, i_lo, elt/4, i_hi),
  * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i. */
 ARA_API ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
