@@ -29,7 +29,10 @@ namespace ara {
 
 namespace {
 
-constexpr int kBW = 8;               // warps per block
+// Warps per block.  The warps of a block share nothing but its slot on the SM, which is freed
+// only when the slowest of them ends; with work per trial tile uneven, 2-warp blocks (16 per SM)
+// waste least of it (8-warp blocks took 14.36 ms, 4-warp 14.01, 2-warp 13.83, 1-warp 14.24).
+constexpr int kBW = 2;
 constexpr int kT = 32;               // trials per warp
 constexpr int kV = 4;                // positions per lane per chunk
 constexpr int kCh = 32 * kV;         // positions per chunk
@@ -340,15 +343,16 @@ __device__ __forceinline__ void band_block(const TrialParams& P, int64_t local_b
   band_warp<MW, CORR>(P, band, i_rel0, (int)min((int64_t)kT, left), lane, sms[wib]);
 }
 
-// Table inversion only: 64 registers for 4 blocks of 8 warps per SM, as the trial-major path.
+// Table inversion only: 64 registers for 32 warps per SM (16 blocks of 2), as the trial-major
+// path.
 template <int MW, bool CORR>
-__global__ void __launch_bounds__(kBW * 32, 4) band_kernel(const __grid_constant__ TrialParams P) {
+__global__ void __launch_bounds__(kBW * 32, 32 / kBW) band_kernel(const __grid_constant__ TrialParams P) {
   __shared__ BandWarpSmem s_w[kBW];
   band_block<MW, CORR>(P, (int64_t)blockIdx.x, s_w);
 }
 
 template <int MW, bool CORR>
-__global__ void __launch_bounds__(kBW * 32, 4)
+__global__ void __launch_bounds__(kBW * 32, 32 / kBW)
     band_batch_kernel(const TrialParams* __restrict__ items,
                       const int64_t* __restrict__ block_begin, int n_items) {
   __shared__ BandWarpSmem s_w[kBW];

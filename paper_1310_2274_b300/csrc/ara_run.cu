@@ -581,15 +581,16 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   // a layer whose own grid is many waves deep runs as its own launch (launch parameters in the
   // constant bank, as ara_run); only small layers share a batched launch, where filling the GPU
   // matters more than the items' parameters being read from global memory
-  const int64_t big_blocks = 12ll * ctx->sm_count * 4;
+  const int64_t big_warps = 12ll * ctx->sm_count * 32;  // 12 waves of 32 resident warps per SM
   int32_t n_items = 0;
   for (int32_t k = 0; k < n_layers; ++k) {
     const int32_t i = order[k];
     const LayerDev& L = ctx->layers[layers[i]];
     TrialParams p = make_params(ctx, Y, L, t0, n, d_ylt + (int64_t)i * n);
     const bool band = group(i) < 2;
-    const int64_t own_blocks = band ? (int64_t)p.n_bands * band_tiles(n) : (n + 7) / 8;
-    if (own_blocks >= big_blocks) {
+    // band-major: a warp per 32 trials per band; trial-major: a warp per trial
+    const int64_t own_warps = band ? (int64_t)p.n_bands * ((n + 31) / 32) : n;
+    if (own_warps >= big_warps) {
       if (band) {
         p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
         CUDA_TRY(ctx, launch_band(p, L.mask_words, ctx->cfg.precision, st));

@@ -365,14 +365,14 @@ bool issue(ara_server* s) {
   cudaError_t e = cudaSuccess;
   // a slice whose own grid is many waves deep runs as its own launch (parameters in the constant
   // bank); the others share one batched launch per schedule
-  const int64_t big_blocks = 12ll * s->ctx->sm_count * 4;
+  const int64_t big_warps = 12ll * s->ctx->sm_count * 32;  // 12 waves of 32 resident warps per SM
   for (int i = 0; i < k; ++i) {
     Request& r = *take[i].first;
     const int64_t n = take[i].second;
     const LayerDev& Ld = r.layer;
     TrialParams p = make_params(s->ctx, Y, Ld, r.req.t0 + r.next, n, r.d_ylt + r.next);
-    const int64_t own_blocks = r.band ? (int64_t)p.n_bands * ara::band_tiles(n) : (n + 7) / 8;
-    if (own_blocks >= big_blocks) {
+    const int64_t own_warps = r.band ? (int64_t)p.n_bands * ((n + 31) / 32) : n;
+    if (own_warps >= big_warps) {
       if (r.band) {
         p.ysum = r.d_ysum + r.next;
         if (e == cudaSuccess) e = ara::launch_band(p, 2, s->ctx->cfg.precision, s->stream);
