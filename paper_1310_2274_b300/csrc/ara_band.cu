@@ -425,17 +425,19 @@ int year_grid_exponent(float occ_lim, int64_t max_len) {
   return (int)std::ceil(std::log2(top)) - 52;
 }
 
-// Band width for a layer: the largest power of two (2^11 .. 2^19, odd exponents only, so a YET
+// Band width for a layer: the largest power of four (2^12 .. 2^18; even exponents only, so a YET
 // needs few band-major copies) for which one band's lookup entries (16 B per event), record
 // headers (16 B per record) and the part of the records' tables a band pass touches (about
-// 1.25 KB of the 2 KB per record at paper-scale hit rates) stay within 40 MB of L2.
+// 1.25 KB of the 2 KB per record at paper-scale hit rates) stay within 80 MB of the 126 MB L2.
+// (At the paper-scale layer: 2^15 events, 38 MB, took 13.86 ms; 2^16, 77 MB, 13.37 ms; 2^17,
+// 154 MB, 14.15 ms.)
 int choose_band_log2w(int64_t catalog, int64_t n_packed) {
   const double per_event = 16.0 + (double)n_packed / (double)catalog * (16.0 + 1280.0);
-  int best = 11;
-  for (int l = 11; l <= 19; l += 2)
-    if ((double)((int64_t)1 << l) * per_event <= 40.0 * 1024 * 1024) best = l;
+  int best = 12;
+  for (int l = 12; l <= 18; l += 2)
+    if ((double)((int64_t)1 << l) * per_event <= 80.0 * 1024 * 1024) best = l;
   // a band wider than the catalogue gains nothing: use the smallest width that covers it
-  for (int l = 11; l <= best; l += 2)
+  for (int l = 12; l <= best; l += 2)
     if (((int64_t)1 << l) >= catalog) return l;
   return best;
 }

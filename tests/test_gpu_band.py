@@ -1,7 +1,7 @@
 """Band-major schedule of the table path against the trial-major one and the FP64 oracle.
 
-The workload has the paper's 2,000,000-event catalogue and 16 ELTs, so a layer is cut into 62
-bands of 32,768 events, on 3,000 trials (oracle-checkable).  Both schedules make the same hits,
+The workload has the paper's 2,000,000-event catalogue and 16 ELTs, so a layer is cut into 31
+bands of 65,536 events, on 3,000 trials (oracle-checkable).  Both schedules make the same hits,
 uniforms and table evaluations, sum each event's ELT losses the same way and sum years exactly
 (integer grid units), so their year losses are identical bit for bit.
 """
