@@ -117,8 +117,8 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_TABLES_ON_DEMAND 1
 #define ARA_TABLE_BUY_HITS 2100.0
 /* ARA_OPT_STREAM_CHUNK: occurrences per copied chunk of a host-resident YET's runs (1024 .. 2^30;
- * default 2^26, two buffers of 4 bytes per occurrence on the device; a chunk always holds whole
- * trials, so it grows to the longest trial if needed). */
+ * default 2^26, a ring of four buffers of 4 bytes per occurrence on the device; a chunk always
+ * holds whole trials, so it grows to the longest trial if needed). */
 #define ARA_OPT_STREAM_CHUNK 8
 ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
 
@@ -138,10 +138,14 @@ ARA_API ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t*
  * trial_offsets is copied (to the device, 8 B per trial); event_ids and timestamps stay in the
  * caller's host memory, which must stay valid and unchanged until ara_free_yet.  Each ara_run /
  * ara_run_ep / ara_run_events over it (blocking; stream must be NULL) copies the event ids of
- * the trials it needs in chunks of whole trials (ARA_OPT_STREAM_CHUNK) on a copy stream into two
- * device buffers used in turn, while the previous chunk's ids are checked and the chunk is run
- * trial-major on the compute stream, so the PCIe copy of a pass overlaps its computation.  The
- * timestamps never cross: the first run checks them on host threads meanwhile.  An id out of
+ * the trials it needs in chunks of whole trials (ARA_OPT_STREAM_CHUNK) on a copy stream into a
+ * ring of four device buffers, while earlier chunks' ids are checked and the chunks are run
+ * trial-major on the compute stream, so the PCIe copy of a pass overlaps its computation.  This
+ * call already starts the copies of the first four chunks of a run over all trials (nothing
+ * waits for them), so they cross while the caller stages ELTs and layers; a first run that
+ * starts at trial 0 with the same chunk size uses them, any other call that needs the ring
+ * drops them, and ara_free_yet waits for them.  The timestamps never cross: the first run
+ * checks them on host threads meanwhile.  An id out of
  * range or a timestamp out of order makes the run return ARA_ERR_INVALID_ARG without writing
  * its outputs.  Page-locked host memory (cudaHostAlloc, or registered)
  * gives the overlap; pageable memory still works, with staged copies.  Layers over it run

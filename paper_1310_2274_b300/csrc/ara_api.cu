@@ -34,42 +34,6 @@ void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st) {
 
 void free_layer(LayerDev& l) { free_layer_on(l, false, nullptr); }
 
-namespace ara {
-
-unsigned int validate_timestamps_host(const int64_t* off, const float* ts, int64_t n_trials) {
-  const int64_t n_occ = off[n_trials];
-  // parts of at least 4M occurrences, cut at trial boundaries, one host thread each
-  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-  const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(hw, n_occ >> 22));
-  std::vector<int64_t> cut((size_t)parts + 1, n_trials);
-  cut[0] = 0;
-  for (int64_t k = 1; k < parts; ++k) {
-    const int64_t target = n_occ / parts * k;
-    cut[(size_t)k] = std::upper_bound(off, off + n_trials + 1, target) - off - 1;
-  }
-  std::vector<unsigned int> flags((size_t)parts, 0u);
-  auto check = [&](int64_t k) {
-    unsigned int f = 0;
-    for (int64_t i = cut[(size_t)k]; i < cut[(size_t)k + 1]; ++i) {
-      // branch-free OR reductions over the trial, which the compiler vectorises
-      const int64_t b = off[i], e = off[i + 1];
-      int nan = 0, dec = 0;
-      for (int64_t q = b; q < e; ++q) nan |= (ts[q] != ts[q]);
-      for (int64_t q = b + 1; q < e; ++q) dec |= (ts[q] < ts[q - 1]);
-      f |= (nan ? 4u : 0u) | (dec ? 2u : 0u);
-    }
-    flags[(size_t)k] = f;
-  };
-  std::vector<std::thread> pool;
-  for (int64_t k = 1; k < parts; ++k) pool.emplace_back(check, k);
-  check(0);
-  for (auto& th : pool) th.join();
-  unsigned int f = 0;
-  for (unsigned int x : flags) f |= x;
-  return f;
-}
-
-}  // namespace ara
 
 extern "C" {
 
@@ -151,15 +115,14 @@ void ara_destroy(ara_ctx* ctx) {
   dev_free(ctx->mlp_G);
   dev_free(ctx->mlp_W);
   dev_free(ctx->mlp_bound);
-  for (int b = 0; b < 2; ++b) {
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+  for (int b = 0; b < kStreamBufs; ++b) {
     dev_free(ctx->d_sids[b]);
     if (ctx->ev_ready[b]) cudaEventDestroy(ctx->ev_ready[b]);
     if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
   }
-  if (ctx->copy_stream) {
-    cudaStreamSynchronize(ctx->copy_stream);
-    cudaStreamDestroy(ctx->copy_stream);
-  }
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  dev_free(ctx->d_scratch);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   cudaGetLastError();
   delete ctx;
@@ -352,6 +315,8 @@ ara_status ara_create_yet_host(ara_ctx* ctx, int64_t n_trials, const int64_t* tr
   y.live = true;
   ctx->yets.push_back(std::move(y));
   *yet_out = (int32_t)ctx->yets.size() - 1;
+  // the first run's leading chunks cross PCIe while the caller stages ELTs and layers
+  prefetch_stream(ctx, *yet_out);
   return ARA_OK;
 }
 
@@ -363,6 +328,12 @@ ara_status ara_free_yet(ara_ctx* ctx, int32_t yet) {
     if (e.live && e.yet == yet) return fail(ctx, ARA_ERR_INVALID_ARG, "YET still has ELTs");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->yets[yet].host && ctx->copy_stream) {
+    // copies of its ids (ahead of a run, or of a run that stopped on an error) end before the
+    // caller may release the arrays
+    if (ctx->pf_yet == yet) ctx->pf_yet = -1;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->copy_stream));
+  }
   free_yet(ctx->yets[yet]);
   return ARA_OK;
 }
@@ -392,41 +363,54 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
   double2* d_ab64 = nullptr;
   unsigned long long uncert = 0;
   cudaError_t err;
-  auto cleanup = [&]() {
-    cudaStreamSynchronize(ctx->stream);
-    dev_free(d_mean);
-    dev_free(d_sd);
-    dev_free(d_sdc);
-    dev_free(d_mx);
-    dev_free(d_dup);
-    dev_free(d_uncert);
-    if (!defer) dev_free(d_ab64);  // deferred tables keep (alpha, beta) in e.ab64
-  };
+  // the input copies, duplicate marks and (alpha, beta) of eagerly built tables are staging
+  // scratch; deferred tables keep (alpha, beta) in e.ab64
+  auto cleanup = [&]() { cudaStreamSynchronize(ctx->stream); };
+  const size_t scratch = scratch_bytes<double>(n) * (sd_corr ? 4 : 3) +
+                         scratch_bytes<unsigned int>(y.catalog) +
+                         scratch_bytes<unsigned long long>(1) +
+                         (defer ? 0 : scratch_bytes<double2>(n));
   if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
       (err = dev_alloc(&e.starts, n * kStartFloats)) != cudaSuccess ||
       (!defer && (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess) ||
-      (err = dev_alloc(&d_mean, n)) != cudaSuccess || (err = dev_alloc(&d_sd, n)) != cudaSuccess ||
-      (err = dev_alloc(&d_mx, n)) != cudaSuccess || (err = dev_alloc(&d_dup, y.catalog)) != cudaSuccess ||
-      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess || (err = dev_alloc(&d_ab64, n)) != cudaSuccess ||
-      (sd_corr && ((err = dev_alloc(&d_sdc, n)) != cudaSuccess ||
-                   (err = dev_alloc(&e.corr, n)) != cudaSuccess))) {
+      (defer && (err = dev_alloc(&e.ab64, n)) != cudaSuccess) ||
+      (sd_corr && (err = dev_alloc(&e.corr, n)) != cudaSuccess) ||
+      (err = ensure_scratch(ctx, scratch)) != cudaSuccess) {
     cudaGetLastError();
-    if (defer) e.ab64 = d_ab64;
     cleanup();
     free_elt(e);
     return fail(ctx, ARA_ERR_OOM, "ELT of %lld records: %s", (long long)n, cudaGetErrorString(err));
   }
-  if (defer) e.ab64 = d_ab64;
+  ScratchCarver sc{ctx->d_scratch};
+  d_mean = sc.take<double>(n);
+  d_sd = sc.take<double>(n);
+  d_mx = sc.take<double>(n);
+  if (sd_corr) d_sdc = sc.take<double>(n);
+  d_dup = sc.take<unsigned int>(y.catalog);
+  d_uncert = sc.take<unsigned long long>(1);
+  d_ab64 = defer ? e.ab64 : sc.take<double2>(n);
+  // inputs the device can read where they are (device memory, mapped page-locked host memory)
+  // are read in place by the staging kernel, which also writes the ids' device copy; the others
+  // are copied first.  (Reads over PCIe by the kernel do not queue behind other copies, such as
+  // the ids a host-resident YET copies ahead.)
+  const int32_t* r_ids = device_readable(event_ids);
+  const double* r_mean = device_readable(mean);
+  const double* r_sd = device_readable(sd);
+  const double* r_sdc = sd_corr ? device_readable(sd_corr) : nullptr;
+  const double* r_mx = device_readable(max_exposure);
   unsigned int flags = 0;
-  if ((err = copy_in(e.ids, event_ids, n, ctx->stream)) != cudaSuccess ||
-      (err = copy_in(d_mean, mean, n, ctx->stream)) != cudaSuccess ||
-      (err = copy_in(d_sd, sd, n, ctx->stream)) != cudaSuccess ||
-      (sd_corr && (err = copy_in(d_sdc, sd_corr, n, ctx->stream)) != cudaSuccess) ||
-      (err = copy_in(d_mx, max_exposure, n, ctx->stream)) != cudaSuccess ||
+  if ((!r_ids && (err = copy_in(e.ids, event_ids, n, ctx->stream)) != cudaSuccess) ||
+      (!r_mean && (err = copy_in(d_mean, mean, n, ctx->stream)) != cudaSuccess) ||
+      (!r_sd && (err = copy_in(d_sd, sd, n, ctx->stream)) != cudaSuccess) ||
+      (sd_corr && !r_sdc && (err = copy_in(d_sdc, sd_corr, n, ctx->stream)) != cudaSuccess) ||
+      (!r_mx && (err = copy_in(d_mx, max_exposure, n, ctx->stream)) != cudaSuccess) ||
       (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
-      (err = launch_prepare_elt(n, e.ids, d_mean, d_sd, d_sdc, d_mx, y.catalog, e.recs, d_ab64,
-                                e.corr, d_dup, ctx->d_flags, ctx->stream)) != cudaSuccess ||
+      (err = launch_prepare_elt(n, r_ids ? r_ids : e.ids, r_ids ? e.ids : nullptr,
+                                r_mean ? r_mean : d_mean, r_sd ? r_sd : d_sd,
+                                sd_corr ? (r_sdc ? r_sdc : d_sdc) : nullptr, r_mx ? r_mx : d_mx,
+                                y.catalog, e.recs, d_ab64, e.corr, d_dup, ctx->d_flags,
+                                ctx->stream)) != cudaSuccess ||
       (err = launch_build_starts(n, e.recs, e.starts, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
       (!defer &&
@@ -517,17 +501,42 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   uint32_t *d_mask = nullptr, *d_cnt = nullptr, *d_base = nullptr, *d_tmp = nullptr;
   const int64_t tmp_words = scan_tmp_words(C);
   cudaError_t err;
+  const TablePiece** d_src = nullptr;
+  // temporaries: stream-ordered ones on a serving stream, else staging scratch (the table source
+  // pointers sized for every record of the layer's ELTs, which bounds the packed count)
   auto cleanup = [&]() {
-    if (!ordered) cudaStreamSynchronize(st);
+    if (!ordered) {
+      cudaStreamSynchronize(st);
+      return;
+    }
     mem_free(d_mask, ordered, st);
     mem_free(d_cnt, ordered, st);
     mem_free(d_base, ordered, st);
     mem_free(d_tmp, ordered, st);
+    mem_free(d_src, ordered, st);
   };
   const int64_t evt_words = C * (MW == 1 ? 2 : 4);
-  if ((err = mem_alloc(&d_mask, C * MW, ordered, st)) != cudaSuccess || (err = mem_alloc(&d_cnt, C, ordered, st)) != cudaSuccess ||
-      (err = mem_alloc(&d_base, C, ordered, st)) != cudaSuccess || (err = mem_alloc(&d_tmp, tmp_words, ordered, st)) != cudaSuccess ||
-      (err = mem_alloc(&L.evt, evt_words, ordered, st)) != cudaSuccess) {
+  if (ordered) {
+    err = mem_alloc(&d_mask, C * MW, ordered, st);
+    if (err == cudaSuccess) err = mem_alloc(&d_cnt, C, ordered, st);
+    if (err == cudaSuccess) err = mem_alloc(&d_base, C, ordered, st);
+    if (err == cudaSuccess) err = mem_alloc(&d_tmp, tmp_words, ordered, st);
+  } else {
+    int64_t records = 0;
+    for (int j = 0; j < n_elts; ++j) records += ctx->elts[elts[j]].n;
+    err = ensure_scratch(ctx, scratch_bytes<uint32_t>(C * MW) + 2 * scratch_bytes<uint32_t>(C) +
+                                  scratch_bytes<uint32_t>(tmp_words) +
+                                  scratch_bytes<const TablePiece*>(records));
+    if (err == cudaSuccess) {
+      ScratchCarver sc{ctx->d_scratch};
+      d_mask = sc.take<uint32_t>(C * MW);
+      d_cnt = sc.take<uint32_t>(C);
+      d_base = sc.take<uint32_t>(C);
+      d_tmp = sc.take<uint32_t>(tmp_words);
+      d_src = sc.take<const TablePiece*>(records);
+    }
+  }
+  if (err != cudaSuccess || (err = mem_alloc(&L.evt, evt_words, ordered, st)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     free_layer_on(L, ordered, st);
@@ -554,7 +563,6 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   L.n_packed = (int64_t)last[0] + (int64_t)last[1];
   // packed records, then the records' tables copied into packed order (one gather per hit);
   // correlated weights only when some ELT of the layer has a correlated SD
-  const TablePiece** d_src = nullptr;
   bool has_corr = false, all_tables = true, all_starts = starts;
   for (int j = 0; j < n_elts; ++j) {
     has_corr = has_corr || ctx->elts[elts[j]].corr != nullptr;
@@ -565,13 +573,12 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
       (err = mem_alloc(&L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
       (all_tables && (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) !=
                          cudaSuccess) ||
-      (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess ||
+      (ordered && (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess) ||
       (has_corr && (err = mem_alloc(&L.corr, L.n_packed, ordered, st)) != cudaSuccess) ||
       (all_starts &&
        (err = mem_alloc(&L.starts, L.n_packed * kStartFloats, ordered, st)) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
-    mem_free(d_src, ordered, st);
     free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_OOM, "layer records and tables: %s", cudaGetErrorString(err));
   }
@@ -581,7 +588,6 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   if (err == cudaSuccess && all_tables) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   cleanup();
-  mem_free(d_src, ordered, st);
   if (err != cudaSuccess) {
     cudaGetLastError();
     free_layer_on(L, ordered, st);

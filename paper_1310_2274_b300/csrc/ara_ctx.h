@@ -18,6 +18,10 @@ using ara::SortScratch;
 using ara::TrialParams;
 using ara::YetDev;
 
+// Device buffers of event ids a streamed run cycles through (the first ones are filled ahead by
+// ara_create_yet_host).
+constexpr int kStreamBufs = 4;
+
 struct ara_ctx {
   ara_config cfg{};
   int device = 0;
@@ -48,14 +52,23 @@ struct ara_ctx {
   int32_t table_policy = 0;              // ARA_TABLES_EAGER or ARA_TABLES_ON_DEMAND
   uint32_t* d_sel = nullptr;             // top-k selection: flags, positions, scan scratch
   int64_t sel_cap = 0;
-  // streamed runs over host-resident YETs: a copy stream, two device buffers of ids filled in
-  // turn, and the events that hand each buffer between the streams
+  // streamed runs over host-resident YETs: a copy stream, a ring of device buffers of ids filled
+  // in turn, and the events that hand each buffer between the streams
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_ready[2] = {nullptr, nullptr};
-  cudaEvent_t ev_free[2] = {nullptr, nullptr};
-  int32_t* d_sids[2] = {nullptr, nullptr};
+  cudaEvent_t ev_ready[kStreamBufs] = {};
+  cudaEvent_t ev_free[kStreamBufs] = {};
+  int32_t* d_sids[kStreamBufs] = {};
   int64_t stream_cap = 0;
   int64_t stream_chunk = (int64_t)1 << 26;  // ARA_OPT_STREAM_CHUNK
+  // chunks of a host YET's first run copied ahead by ara_create_yet_host: the YET, the chunk
+  // size they were cut with and each one's trial range (buffer k holds chunk k)
+  int32_t pf_yet = -1;
+  int32_t pf_count = 0;
+  int64_t pf_cap = 0;
+  int64_t pf_tb[kStreamBufs] = {}, pf_te[kStreamBufs] = {};
+  // staging scratch (grow-only, see ensure_scratch)
+  char* d_scratch = nullptr;
+  size_t scratch_cap = 0;
   int32_t band_log2w = 0;                // band width exponent for new layers (0: automatic)
   void* d_misc = nullptr;  // small staging area for tail sums
 };
@@ -89,3 +102,11 @@ ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n);
 ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet);
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,
                         double* d_ylt);
+// The stream ring with buffers of at least cap ids, the copy stream and the hand-over events.
+ara_status ensure_stream_ring(ara_ctx* ctx, int64_t cap);
+// End of the streamed chunk that starts at trial tb: whole trials up to cap occurrences (a trial
+// never exceeds cap), ending at `end` at the latest.
+int64_t stream_chunk_end(const YetDev& Y, int64_t tb, int64_t end, int64_t cap);
+// Copies the first chunks of a run over all trials of host YET `yet` into the stream ring ahead
+// of that run, on the copy stream (nothing is waited for; a failure leaves nothing copied ahead).
+void prefetch_stream(ara_ctx* ctx, int32_t yet);

@@ -44,6 +44,21 @@ inline bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// An address through which kernels can read caller memory in place: device and managed memory as
+// they are, page-locked host memory mapped into the device's address space by its device alias;
+// nullptr for pageable host memory (which must be copied first).
+template <class T>
+const T* device_readable(const T* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<const T*>(a.devicePointer);
+  return nullptr;
+}
+
 template <class T>
 cudaError_t dev_alloc(T** p, int64_t n) {
   *p = nullptr;
@@ -117,6 +132,38 @@ inline ara_status ensure_ylt_tmp(ara_ctx* c, int64_t n) {
   CUDA_TRY(c, dev_alloc(&c->d_ylt_tmp, n));
   c->ylt_tmp_cap = n;
   return ARA_OK;
+}
+
+// Staging scratch: the temporaries of the staging calls (ELT and layer builds, table and start
+// table packing) are carved from one device buffer the context keeps until ara_destroy (grown,
+// never shrunk), so these calls free nothing: a cudaFree waits for the whole device, the copy
+// stream included, and would hold staging back behind the ids a host-resident YET copies ahead.
+// Each staging call synchronises its stream before it returns, so the buffer is idle between
+// calls.  Pieces start on 256-byte boundaries.
+template <class T>
+constexpr size_t scratch_bytes(int64_t n) {
+  return (sizeof(T) * (size_t)(n > 0 ? n : 1) + 255) / 256 * 256;
+}
+
+struct ScratchCarver {
+  char* cur;
+  template <class T>
+  T* take(int64_t n) {
+    T* p = reinterpret_cast<T*>(cur);
+    cur += scratch_bytes<T>(n);
+    return p;
+  }
+};
+
+inline cudaError_t ensure_scratch(ara_ctx* c, size_t bytes) {
+  if (bytes <= c->scratch_cap) return cudaSuccess;
+  dev_free(c->d_scratch);
+  c->d_scratch = nullptr;
+  c->scratch_cap = 0;
+  const size_t cap = bytes > ((size_t)64 << 20) ? bytes : ((size_t)64 << 20);
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_scratch), cap);
+  if (e == cudaSuccess) c->scratch_cap = cap;
+  return e;
 }
 
 inline ara_status ensure_ysum(ara_ctx* c, int64_t n) {

@@ -157,10 +157,13 @@ cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStre
 cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64_t occ_base,
                                       const int64_t* offsets, int64_t t_begin, int64_t n,
                                       int32_t catalog, unsigned int* d_flags, cudaStream_t st);
-cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
-                               const double* sd, const double* sdc, const double* mx,
-                               int32_t catalog, BetaRec* recs, double2* ab64, float* corr,
-                               unsigned int* d_dup, unsigned int* d_flags, cudaStream_t st);
+// Checks and converts an ELT's records (ids, mean, sd, optional correlated sd, max exposure, all
+// device-readable) into recs / ab64 / corr; ids_out (nullable) receives a copy of the ids.
+cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
+                               const double* mean, const double* sd, const double* sdc,
+                               const double* mx, int32_t catalog, BetaRec* recs, double2* ab64,
+                               float* corr, unsigned int* d_dup, unsigned int* d_flags,
+                               cudaStream_t st);
 cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
                               cudaStream_t st);
 cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,

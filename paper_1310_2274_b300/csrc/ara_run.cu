@@ -49,17 +49,17 @@ int layer_inversion(const ara_ctx* ctx, const LayerDev& L) {
 static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
   if (e.tables) return ARA_OK;
   if (!e.ab64) return fail(ctx, ARA_ERR_INVALID_ARG, "ELT has neither tables nor parameters");
-  unsigned long long* d_uncert = nullptr;
+  unsigned long long* d_uncert = nullptr;  // staging scratch
   unsigned long long uncert = 0;
   cudaError_t err;
   if ((err = dev_alloc(&e.tables, e.n * kTablePieces)) != cudaSuccess ||
-      (err = dev_alloc(&d_uncert, 1)) != cudaSuccess) {
+      (err = ensure_scratch(ctx, scratch_bytes<unsigned long long>(1))) != cudaSuccess) {
     cudaGetLastError();
     dev_free(e.tables);
     e.tables = nullptr;
-    dev_free(d_uncert);
     return fail(ctx, ARA_ERR_OOM, "tables of %lld records", (long long)e.n);
   }
+  d_uncert = reinterpret_cast<unsigned long long*>(ctx->d_scratch);
   if ((err = cudaMemsetAsync(d_uncert, 0, sizeof uncert, ctx->stream)) != cudaSuccess ||
       (err = launch_build_tables(e.n, e.recs, e.ab64, e.tables, d_uncert, ctx->stream)) !=
           cudaSuccess ||
@@ -70,10 +70,8 @@ static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
     cudaStreamSynchronize(ctx->stream);
     dev_free(e.tables);
     e.tables = nullptr;
-    dev_free(d_uncert);
     return fail(ctx, ARA_ERR_CUDA, "building tables: %s", cudaGetErrorString(err));
   }
-  dev_free(d_uncert);
   dev_free(e.ab64);
   e.ab64 = nullptr;
   e.n_uncertified = (int64_t)uncert;
@@ -87,16 +85,16 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
     const ara_status s = ensure_elt_tables(ctx, ctx->elts[L.handles[j]]);
     if (s != ARA_OK) return s;
   }
-  const TablePiece** d_src = nullptr;
+  const TablePiece** d_src = nullptr;  // staging scratch
   cudaError_t err;
   if ((err = dev_alloc(&L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
-      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
+      (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed))) != cudaSuccess) {
     cudaGetLastError();
     dev_free(L.tables);
     L.tables = nullptr;
-    dev_free(d_src);
     return fail(ctx, ARA_ERR_OOM, "layer tables: %s", cudaGetErrorString(err));
   }
+  d_src = reinterpret_cast<const TablePiece**>(ctx->d_scratch);
   // the scatter rewrites the packed records as they are and fills the table source pointers
   err = cudaSuccess;
   for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
@@ -104,9 +102,9 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
                                L.packed_rec, L.corr, nullptr, ctx->stream);
   if (err == cudaSuccess) err = launch_gather_tables(L.n_packed, d_src, L.tables, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
-  dev_free(d_src);
   if (err != cudaSuccess) {
     cudaGetLastError();
+    cudaStreamSynchronize(ctx->stream);
     dev_free(L.tables);
     L.tables = nullptr;
     return fail(ctx, ARA_ERR_CUDA, "layer tables: %s", cudaGetErrorString(err));
@@ -120,24 +118,24 @@ static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
   if (L.starts) return ARA_OK;
   for (int j = 0; j < L.n_slots; ++j)
     if (!ctx->elts[L.handles[j]].starts) return ARA_OK;  // (not expected) analytic starts
-  const TablePiece** d_src = nullptr;
+  const TablePiece** d_src = nullptr;  // staging scratch
   cudaError_t err;
   if ((err = dev_alloc(&L.starts, L.n_packed * kStartFloats)) != cudaSuccess ||
-      (err = dev_alloc(&d_src, L.n_packed)) != cudaSuccess) {
+      (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed))) != cudaSuccess) {
     cudaGetLastError();
     dev_free(L.starts);
     L.starts = nullptr;
-    dev_free(d_src);
     return fail(ctx, ARA_ERR_OOM, "layer start tables: %s", cudaGetErrorString(err));
   }
+  d_src = reinterpret_cast<const TablePiece**>(ctx->d_scratch);
   err = cudaSuccess;
   for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[L.handles[j]], j, L.mask_words, L.evt, L.packed, d_src,
                                L.packed_rec, L.corr, L.starts, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
-  dev_free(d_src);
   if (err != cudaSuccess) {
     cudaGetLastError();
+    cudaStreamSynchronize(ctx->stream);
     dev_free(L.starts);
     L.starts = nullptr;
     return fail(ctx, ARA_ERR_CUDA, "layer start tables: %s", cudaGetErrorString(err));
@@ -316,49 +314,107 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   return p;
 }
 
-extern "C" {
-
-// A run over a host-resident YET: trials in chunks of whole trials (up to ctx->stream_chunk
-// occurrences), each chunk's ids copied on the copy stream into one of two device buffers while
-// the previous chunk's ids are checked and the chunk run on st; the run of a chunk skips its work
-// if any chunk so far failed the check.  (Timestamps never cross: the caller checks them on host
-// threads.)  Outputs are device pointers for trials [t0, t0 + n).
-static ara_status run_streamed(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0,
-                               int64_t n, double* d_ylt, double* d_oep, float* d_olt,
-                               double* d_inc, cudaStream_t st) {
-  const int64_t cap = std::max<int64_t>(ctx->stream_chunk, Y.max_len);
+ara_status ensure_stream_ring(ara_ctx* ctx, int64_t cap) {
   if (cap > ctx->stream_cap) {
-    for (int b = 0; b < 2; ++b) {
+    ctx->pf_yet = -1;
+    if (ctx->copy_stream) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->copy_stream));
+    for (int b = 0; b < kStreamBufs; ++b) {
       dev_free(ctx->d_sids[b]);
       ctx->d_sids[b] = nullptr;
     }
     ctx->stream_cap = 0;
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kStreamBufs; ++b)
       CUDA_TRY(ctx, dev_alloc(&ctx->d_sids[b], cap));
     ctx->stream_cap = cap;
   }
   if (!ctx->copy_stream)
     CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kStreamBufs; ++b) {
     if (!ctx->ev_ready[b])
       CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_ready[b], cudaEventDisableTiming));
     if (!ctx->ev_free[b])
       CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming));
-    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));  // both buffers free once st gets here
   }
+  return ARA_OK;
+}
+
+int64_t stream_chunk_end(const YetDev& Y, int64_t tb, int64_t end, int64_t cap) {
+  int64_t te = tb + 1;
+  while (te < end && Y.h_off[(size_t)te + 1] - Y.h_off[(size_t)tb] <= cap) ++te;
+  return te;
+}
+
+void prefetch_stream(ara_ctx* ctx, int32_t yet) {
+  const YetDev& Y = ctx->yets[yet];
+  ctx->pf_yet = -1;
+  ctx->pf_count = 0;
+  if (Y.n_occ == 0) return;
+  const std::string detail = ctx->detail;  // a failure here is not the caller's error
+  const int64_t cap = std::max<int64_t>(ctx->stream_chunk, Y.max_len);
+  if (ensure_stream_ring(ctx, cap) != ARA_OK) {
+    cudaGetLastError();
+    ctx->detail = detail;
+    return;
+  }
+  // copies of at most 2^21 ids (8 MB, ~0.15 ms of PCIe): the caller's staging copies, issued
+  // meanwhile on the compute stream, wait behind one piece at most
+  constexpr int64_t kPiece = (int64_t)1 << 21;
+  int k = 0;
+  for (int64_t tb = 0; tb < Y.n_trials && k < kStreamBufs; ++k) {
+    const int64_t te = stream_chunk_end(Y, tb, Y.n_trials, cap);
+    const int64_t ob = Y.h_off[(size_t)tb], len = Y.h_off[(size_t)te] - ob;
+    bool ok = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[k], 0) == cudaSuccess;
+    for (int64_t q = 0; ok && q < len; q += kPiece)
+      ok = cudaMemcpyAsync(ctx->d_sids[k] + q, Y.h_ids + ob + q,
+                           sizeof(int32_t) * (size_t)std::min(kPiece, len - q),
+                           cudaMemcpyHostToDevice, ctx->copy_stream) == cudaSuccess;
+    if (!ok || cudaEventRecord(ctx->ev_ready[k], ctx->copy_stream) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(ctx->copy_stream);
+      return;
+    }
+    ctx->pf_tb[k] = tb;
+    ctx->pf_te[k] = te;
+    tb = te;
+  }
+  ctx->pf_count = k;
+  ctx->pf_cap = cap;
+  ctx->pf_yet = yet;
+}
+
+extern "C" {
+
+// A run over a host-resident YET: trials in chunks of whole trials (up to ctx->stream_chunk
+// occurrences), each chunk's ids copied on the copy stream into the next buffer of the ring while
+// earlier chunks are checked and run on st; the run of a chunk skips its work if any chunk so far
+// failed the check.  Chunks that ara_create_yet_host copied ahead are used as they are when this
+// run starts at trial 0 (the ring then holds chunk k in buffer k).  (Timestamps never cross: the
+// caller checks them on host threads.)  Outputs are device pointers for trials [t0, t0 + n).
+static ara_status run_streamed(ara_ctx* ctx, int32_t yet, const LayerDev& L, int64_t t0,
+                               int64_t n, double* d_ylt, double* d_oep, float* d_olt,
+                               double* d_inc, cudaStream_t st) {
+  const YetDev& Y = ctx->yets[yet];
+  const int64_t cap = std::max<int64_t>(ctx->stream_chunk, Y.max_len);
+  const int n_ahead = (ctx->pf_yet == yet && ctx->pf_cap == cap && t0 == 0) ? ctx->pf_count : 0;
+  ctx->pf_yet = -1;  // the ring is this run's from here on
+  ara_status s = ensure_stream_ring(ctx, cap);
+  if (s != ARA_OK) return s;
+  for (int b = 0; b < kStreamBufs; ++b)
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));  // every buffer free once st gets here
   CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), st));
   const int64_t q_first = Y.h_off[(size_t)t0];
   int k = 0;
   for (int64_t tb = t0; tb < t0 + n; ++k) {
-    int64_t te = tb + 1;  // whole trials up to cap occurrences (a trial never exceeds cap)
-    while (te < t0 + n && Y.h_off[(size_t)te + 1] - Y.h_off[(size_t)tb] <= cap) ++te;
+    const int64_t te = stream_chunk_end(Y, tb, t0 + n, cap);
     const int64_t ob = Y.h_off[(size_t)tb], len = Y.h_off[(size_t)te] - ob;
-    const int b = k & 1;
-    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
-    if (len > 0)
-      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sids[b], Y.h_ids + ob, sizeof(int32_t) * (size_t)len,
-                                    cudaMemcpyHostToDevice, ctx->copy_stream));
-    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_ready[b], ctx->copy_stream));
+    const int b = k % kStreamBufs;
+    if (!(k < n_ahead && ctx->pf_tb[k] == tb && ctx->pf_te[k] == te)) {
+      CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
+      if (len > 0)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_sids[b], Y.h_ids + ob, sizeof(int32_t) * (size_t)len,
+                                      cudaMemcpyHostToDevice, ctx->copy_stream));
+      CUDA_TRY(ctx, cudaEventRecord(ctx->ev_ready[b], ctx->copy_stream));
+    }
     CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_ready[b], 0));
     CUDA_TRY(ctx, launch_validate_yet_range(ctx->d_sids[b], nullptr, ob, Y.offsets, tb, te - tb,
                                             Y.catalog, ctx->d_flags, st));
@@ -441,12 +497,11 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   p.olt = d_olt;
   p.inc = d_inc;
   // per-occurrence outputs are written in trial order, so they keep the trial-major schedule
-  // a host YET's timestamps are checked once, on host threads, while its first run streams
+  // a host YET's timestamps are checked once, on host threads, while its first run streams;
+  // the check starts once every copy and launch of the run is queued (its threads would
+  // otherwise hold the cores the queueing thread needs)
   unsigned int ts_flags = 0;
   std::thread ts_check;
-  if (Y.host && !Y.ts_checked && Y.n_occ > 0)
-    ts_check = std::thread(
-        [&]() { ts_flags = validate_timestamps_host(Y.h_off.data(), Y.h_ts, Y.n_trials); });
   struct Joiner {
     std::thread& t;
     ~Joiner() {
@@ -454,8 +509,11 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
     }
   } joiner{ts_check};
   if (Y.host) {
-    s = run_streamed(ctx, Y, ctx->layers[layer], t0, n, d_ylt, d_oep, d_olt, d_inc, st);
+    s = run_streamed(ctx, yet, ctx->layers[layer], t0, n, d_ylt, d_oep, d_olt, d_inc, st);
     if (s != ARA_OK) return s;
+    if (!Y.ts_checked && Y.n_occ > 0)
+      ts_check = std::thread(
+          [&]() { ts_flags = validate_timestamps_host(Y.h_off.data(), Y.h_ts, Y.n_trials); });
   } else if (!per_occ && uses_band_schedule(ctx, ctx->layers[layer])) {
     // year sums (8 B per trial), then the OEP maxima (4 B per trial) in the same scratch
     s = ensure_ysum(ctx, oep ? n + (n + 1) / 2 : n);

@@ -68,6 +68,7 @@ __device__ double betainc_f64(double a, double b, double x) {
 // sdc (NULL: zero) is the correlated SD of paper §3.1: sigma = sd + sdc feeds the moments and
 // corr[r] receives the normalised correlated weight of §3.2, (sdc/sigma) / |(sd, sdc)/sigma|.
 __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
+                                   int32_t* __restrict__ ids_out,
                                    const double* __restrict__ mean, const double* __restrict__ sd,
                                    const double* __restrict__ sdc, const double* __restrict__ mx,
                                    int32_t catalog, BetaRec* __restrict__ recs,
@@ -77,6 +78,7 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
   if (r >= n) return;
   unsigned int f = 0;
   const int32_t e = ids[r];
+  if (ids_out) ids_out[r] = e;
   if (e < 0 || e >= catalog) {
     f |= 8u;
   } else if (atomicAdd(&dup[e], 1u) != 0u) {
@@ -301,13 +303,14 @@ cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStre
                                    st);
 }
 
-cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, const double* mean,
-                               const double* sd, const double* sdc, const double* mx,
-                               int32_t catalog, BetaRec* recs, double2* ab64, float* corr,
-                               unsigned int* d_dup, unsigned int* d_flags, cudaStream_t st) {
+cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
+                               const double* mean, const double* sd, const double* sdc,
+                               const double* mx, int32_t catalog, BetaRec* recs, double2* ab64,
+                               float* corr, unsigned int* d_dup, unsigned int* d_flags,
+                               cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, mean, sd, sdc, mx, catalog, recs,
-                                                       ab64, corr, d_dup, d_flags);
+  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, ids_out, mean, sd, sdc, mx,
+                                                       catalog, recs, ab64, corr, d_dup, d_flags);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
 """Host-resident YETs: runs stream the trials they need from host memory in chunks (copy stream,
-two device buffers) while earlier chunks are validated and run.  Results must equal the
+a ring of device buffers, the first chunks copied ahead when the YET is created) while earlier
+chunks are validated and run.  Results must equal the
 device-resident YET's trial-major runs bit for bit, for any trial range, chunk size and output
 set; invalid chunks are reported after the run without any of their trials being computed."""
 
@@ -125,3 +126,76 @@ def test_host_yet_restrictions(ara, pair):
     with pytest.raises(ara.AraError):  # asynchronous calls (a non-default stream)
         ch.run(hy, hl, 0, 10, out=torch.zeros(10, dtype=torch.float64, device="cuda"),
                stream=torch.cuda.Stream())
+
+
+def staged_host(ara, w, keep, chunk):
+    """A fresh context (ELT handles 0..15, as in the resident one) with a host-resident YET
+    created under the given chunk size, so its first chunks are copied ahead."""
+    off, ids, ts = (k[1] for k in keep)
+    c = ara.Context(seed=42)
+    c.set_option(ara.OPT_STREAM_CHUNK, chunk)
+    y = c.create_yet_host(off, ids, ts, 2_000_000)
+    elts = [c.add_elt(y, e.event_ids, e.mean, e.sd, e.max_exposure) for e in w.elts]
+    t = w.terms
+    return c, y, c.add_layer(elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+
+
+@pytest.mark.parametrize("first", [(0, N), (0, 300), (5, N - 5), (0, 1)])
+def test_chunks_copied_ahead(ara, pair, first):
+    # chunks of 2^18 occurrences (~262 trials): the ring of buffers wraps several times; the first
+    # run uses the chunks copied ahead when it starts at trial 0 (all of them, or only the first
+    # when it ends inside the second), none otherwise; later runs stream everything
+    (cr, _), w, (ry, rl), _, keep = pair
+    c, y, layer = staged_host(ara, w, keep, 1 << 18)
+    try:
+        t0, n = first
+        np.testing.assert_array_equal(c.run(y, layer, t0, n), cr.run(ry, rl, t0, n))
+        np.testing.assert_array_equal(c.run(y, layer, 0, N), cr.run(ry, rl, 0, N))
+    finally:
+        c.close()
+
+
+def test_copied_ahead_chunks_of_another_yet(ara, pair):
+    # two host YETs created back to back: the second one's chunks are in the ring, so the run over
+    # the first streams all of its own; the second's run then finds its chunks gone and streams
+    # too; a YET freed before any run waits for its copies
+    (cr, _), w, (ry, rl), _, keep = pair
+    off, ids, ts = (k[1] for k in keep)
+    c, y, layer = staged_host(ara, w, keep, 1 << 18)
+    try:
+        y2 = c.create_yet_host(off, ids, ts, 2_000_000)
+        np.testing.assert_array_equal(c.run(y, layer, 0, N), cr.run(ry, rl, 0, N))
+        c.free_yet(y2)
+        y3 = c.create_yet_host(off, ids, ts, 2_000_000)
+        c.free_yet(y3)
+        np.testing.assert_array_equal(c.run(y, layer, 0, 700), cr.run(ry, rl, 0, 700))
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("kind", ["pinned", "cuda"])
+def test_elt_inputs_read_in_place(ara, pair, kind):
+    # ELT arrays in page-locked host memory or on the device are read in place by the staging
+    # kernel (pageable ones are copied first, as in the resident context): the same records give
+    # bit-identical runs, and a bad record read in place is still rejected
+    (cr, _), w, (ry, rl), _, _ = pair
+
+    def conv(a, dt):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+        return t.pin_memory() if kind == "pinned" else t.cuda()
+
+    def arrays(e, ids=None):
+        return (conv(e.event_ids if ids is None else ids, np.int32), conv(e.mean, np.float64),
+                conv(e.sd, np.float64), conv(e.max_exposure, np.float64))
+
+    with ara.Context(seed=42) as c:
+        c.set_option(ara.OPT_SCHEDULE, ara.SCHED_TRIAL)
+        y = c.create_yet(w.yet.offsets, w.yet.event_ids, w.yet.timestamps, 2_000_000)
+        elts = [c.add_elt(y, *arrays(e)) for e in w.elts]
+        t = w.terms
+        layer = c.add_layer(elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+        np.testing.assert_array_equal(c.run(y, layer, 0, 500), cr.run(ry, rl, 0, 500))
+        dup = w.elts[0].event_ids.copy()
+        dup[5] = dup[4]
+        with pytest.raises(ara.AraError, match="duplicate"):
+            c.add_elt(y, *arrays(w.elts[0], dup))
