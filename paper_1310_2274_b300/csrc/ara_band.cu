@@ -255,7 +255,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
         } else if (pc.flag == kPieceMean) {
           loss = pc.mx;  // sd = 0: the mean (primary uncertainty only)
         } else {
-          const IbetaResult ib = newton_fallback(P.recs + pos, u);
+          const IbetaResult ib = newton_fallback<false>(P.recs + pos, u);
           nc += ib.converged ? 0u : 1u;
           n_inv += 1u;
           n_it += (unsigned)ib.iters;

@@ -34,7 +34,11 @@ namespace ara {
 
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+// Warps per block: 2 where a block's warps run independent trials (its slot on the SM is freed
+// only when its slowest warp ends, so small blocks waste least of it), 8 for the surrogate path,
+// whose blocks first load the network's weights into shared memory.
+template <int INV>
+constexpr int kWPB = INV == 2 ? 8 : 2;
 constexpr int kV = 4;             // occurrences per lane per chunk
 constexpr int kChunk = 32 * kV;   // occurrences per chunk
 
@@ -243,7 +247,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
                                         P.starts != nullptr
                                             ? ara_start_logit(P.starts + (size_t)pos * kStartFloats, u)
                                             : 1e30f)
-                         : newton_fallback(P.recs + pos, u);
+                         : newton_fallback<INV == 2>(P.recs + pos, u);
             x = ib.x;
             nc += ib.converged ? 0u : 1u;
             n_inv += 1u;
@@ -336,15 +340,16 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
 
 // INV: 0 certified tables (Newton fallback), 1 Newton, 2 learned surrogate (Newton fallback).
 // The table and Newton paths are latency bound (dependent loads per hit; the serial continued
-// fraction), so they are held to 64 registers for 4 blocks (32 warps) per SM (the Newton path
-// runs 4% faster so than at 3 blocks with 85 registers).
+// fraction), so they are held to 64 registers for 32 resident warps per SM (the Newton path
+// runs 4% faster so than at 24 warps with 85 registers).
 template <int MW, class Acc, bool TRACE, int INV, bool CORR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 2 ? 1 : 4)
+__global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 2 ? 8 : 32) / kWPB<INV>)
     trial_kernel(const __grid_constant__ TrialParams P) {
-  __shared__ int32_t s_excl[kWarpsPerBlock][kChunk];
-  __shared__ uint32_t s_base[kWarpsPerBlock][kChunk];
-  __shared__ uint32_t s_mask[kWarpsPerBlock][MW][kChunk];
-  __shared__ float s_lsum[kWarpsPerBlock][kChunk];
+  constexpr int W = kWPB<INV>;
+  __shared__ int32_t s_excl[W][kChunk];
+  __shared__ uint32_t s_base[W][kChunk];
+  __shared__ uint32_t s_mask[W][MW][kChunk];
+  __shared__ float s_lsum[W][kChunk];
   __shared__ __align__(16) MlpSmem s_mlp[1];
   if constexpr (INV == 2) {  // network weights, once per block, before any warp may leave
     const uint4* src = reinterpret_cast<const uint4*>(P.mlp);
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 2 ? 1 : 4)
   }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+  const int64_t w = (int64_t)blockIdx.x * W + wib;
   if (w >= P.n) return;  // whole warp leaves together; no block-wide barrier follows
   process_trial<MW, Acc, TRACE, INV, CORR>(P, w, lane, wib, s_excl[wib], s_base[wib],
                                            s_mask[wib], s_lsum[wib], &s_mlp[0]);
@@ -363,13 +368,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 2 ? 1 : 4)
 // One launch over many work items (serving: slices of different requests, each with its own
 // layer and YLT): warp w runs trial w - warp_begin[i] of the item i with warp_begin[i] <= w.
 template <int MW, class Acc, int INV>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 ? 3 : 1))
+__global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 0 ? 32 : (INV == 1 ? 24 : 8)) / kWPB<INV>)
     batch_kernel(const TrialParams* __restrict__ items, const int64_t* __restrict__ warp_begin,
                  int n_items, int64_t total_warps) {
-  __shared__ int32_t s_excl[kWarpsPerBlock][kChunk];
-  __shared__ uint32_t s_base[kWarpsPerBlock][kChunk];
-  __shared__ uint32_t s_mask[kWarpsPerBlock][MW][kChunk];
-  __shared__ float s_lsum[kWarpsPerBlock][kChunk];
+  constexpr int W = kWPB<INV>;
+  __shared__ int32_t s_excl[W][kChunk];
+  __shared__ uint32_t s_base[W][kChunk];
+  __shared__ uint32_t s_mask[W][MW][kChunk];
+  __shared__ float s_lsum[W][kChunk];
   __shared__ __align__(16) MlpSmem s_mlp[1];
   if constexpr (INV == 2) {
     const uint4* src = reinterpret_cast<const uint4*>(items[0].mlp);
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 
   }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+  const int64_t w = (int64_t)blockIdx.x * W + wib;
   if (w >= total_warps) return;
   int lo = 0, hi = n_items - 1;
   while (lo < hi) {  // largest item whose first warp is <= w
@@ -393,11 +399,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, INV == 0 ? 4 : (INV == 1 
 
 template <int MW, class Acc, bool TRACE, int INV, bool CORR = true>
 cudaError_t launch_one(const TrialParams& p, cudaStream_t st) {
-  const int64_t blocks = (p.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t blocks = (p.n + kWPB<INV> - 1) / kWPB<INV>;
   if (blocks == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
-  cfg.blockDim = dim3(kWarpsPerBlock * 32);
+  cfg.blockDim = dim3(kWPB<INV> * 32);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, trial_kernel<MW, Acc, TRACE, INV, CORR>, p);
@@ -430,9 +436,9 @@ cudaError_t launch_mode(const TrialParams& p, int mask_words, int precision, boo
 template <int MW, class Acc, int INV>
 cudaError_t launch_batch_mode(const TrialParams* d_items, const int64_t* d_warp_begin,
                               int n_items, int64_t total_warps, cudaStream_t st) {
-  const int64_t blocks = (total_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t blocks = (total_warps + kWPB<INV> - 1) / kWPB<INV>;
   if (blocks == 0) return cudaSuccess;
-  batch_kernel<MW, Acc, INV><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
+  batch_kernel<MW, Acc, INV><<<(unsigned)blocks, kWPB<INV> * 32, 0, st>>>(
       d_items, d_warp_begin, n_items, total_warps);
   count_launches(1);
   return cudaGetLastError();

@@ -177,10 +177,12 @@ __device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
 }
 
 
-// The Newton inversion for the rare record whose table failed certification, kept out of line
-// so that its registers do not weigh on the table path.
+// The Newton inversion for the rare record whose table failed certification (and for the
+// surrogate's rejected cells), kept out of line so that its registers do not weigh on the table
+// path; ONE_CF as for ara_inv_beta.
+template <bool ONE_CF>
 __device__ __noinline__ IbetaResult newton_fallback(const BetaRec* p, float u) {
-  return ara_inv_beta(load_rec(p), u);
+  return ara_inv_beta<ONE_CF>(load_rec(p), u);
 }
 
 }  // namespace
