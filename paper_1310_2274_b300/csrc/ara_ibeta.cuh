@@ -100,13 +100,14 @@ ARA_HD float ara_pow2_scale_of(float s) {
 // K(a,b,x) = 1/(1 + d1/(1 + d2/(...))) of DLMF 8.17.22 by the Wallis recurrence on the
 // division-free equivalent fraction T = 1 + alpha_1/(beta_1 + alpha_2/(beta_2 + ...)), K = 1/T.
 // Converges quickly for x < (a+1)/(a+b+2).  Returns K once two estimates 4 terms apart agree to
-// tol (relative); *terms counts recurrence steps.
+// tol (relative); *terms counts recurrence steps.  The test compares the estimates B/A and
+// pB/pA cross-multiplied, |B pA - pB A| <= tol |B pA| (A and pA are rescaled into [1, 2)), so
+// the one division is the final K.
 ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e-7f) {
   const float apb = a + b;
   // T_n = A_n / B_n.  A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1.
   float Am2 = 1.0f, Am1 = 1.0f, Bm2 = 0.0f, Bm1 = 1.0f;
-  float prev = 1.0f;
-  float res = 1.0f;
+  float pA = 1.0f, pB = 1.0f;  // the estimate last tested, as the pair (A, B)
   int n = 1;
   for (; n <= kCfMaxTerms; n += 2) {
     // odd step n = 2m+1: alpha = -(a+m)(a+b+m) x  (alpha_1 = -(a+b) x: the a cancels)
@@ -127,13 +128,14 @@ ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e
     const float sc = ara_pow2_scale_of(Am1);
     Am1 *= sc; Am2 *= sc; Bm1 *= sc; Bm2 *= sc;
     if (((n + 1) & 3) == 0 || n + 2 > kCfMaxTerms) {
-      res = Bm1 / Am1;
-      if (fabsf(res - prev) <= tol * fabsf(res)) { n += 2; break; }
-      prev = res;
+      const float cur = Bm1 * pA;
+      if (fabsf(fmaf(-pB, Am1, cur)) <= tol * fabsf(cur)) { n += 2; break; }
+      pA = Am1;
+      pB = Bm1;
     }
   }
   if (terms) *terms += n - 1;
-  return res;
+  return Bm1 / Am1;
 }
 
 // Normal quantile for the upper tail probability q in (0, 1/2]: the deviate t with
