@@ -168,7 +168,10 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
  * certified quantile table is built at the same time (2 KB per record, see ARA_OPT_INVERSION;
  * deferred under ARA_TABLES_ON_DEMAND), and its start table (384 bytes per record).
  * The handle number keys the record's uniforms: Philox4x32-10 counter (k, i_lo, elt/4, i_hi),
- * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i. */
+ * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i.  The arrays may be host or
+ * device memory; device memory and page-locked host memory mapped into the device's address
+ * space are read in place by the staging kernel, pageable host memory is copied first.  The call
+ * returns once the records are checked (blocking). */
 ARA_API ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
                                const double* mean, const double* sd, const double* max_exposure,
                                int32_t* elt_out);
