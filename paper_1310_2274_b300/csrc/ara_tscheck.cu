@@ -1,9 +1,11 @@
 // ara_tscheck.cu -- the host-side check of a host-resident YET's timestamps (§2.1: each trial's
 // occurrences in nondecreasing time order), run on host threads while the event ids cross PCIe.
 // It reads every timestamp once; on a CPU with AVX2 eight at a time (compared with their
-// predecessors through an overlapping load), else with the scalar loop.
-#include <immintrin.h>
+// predecessors through an overlapping load), else (or on other CPUs) with the scalar loop.
 #include <stdint.h>
+#if defined(__x86_64__)
+#include <immintrin.h>
+#endif
 
 #include <algorithm>
 #include <thread>
@@ -26,6 +28,7 @@ unsigned int check_trials_scalar(const int64_t* off, const float* ts, int64_t a,
   return f;
 }
 
+#if defined(__x86_64__)
 __attribute__((target("avx2"))) unsigned int check_trials_avx2(const int64_t* off,
                                                                const float* ts, int64_t a,
                                                                int64_t b) {
@@ -51,6 +54,8 @@ __attribute__((target("avx2"))) unsigned int check_trials_avx2(const int64_t* of
   return (any_nan ? 4u : 0u) | (any_dec ? 2u : 0u);
 }
 
+#endif
+
 }  // namespace
 
 unsigned int validate_timestamps_host(const int64_t* off, const float* ts, int64_t n_trials);
@@ -67,11 +72,19 @@ unsigned int validate_timestamps_host(const int64_t* off, const float* ts, int64
     const int64_t target = n_occ / parts * k;
     cut[(size_t)k] = std::upper_bound(off, off + n_trials + 1, target) - off - 1;
   }
+#if defined(__x86_64__)
   static const bool avx2 = __builtin_cpu_supports("avx2");
+#endif
   std::vector<unsigned int> flags((size_t)parts, 0u);
   auto check = [&](int64_t k) {
     const int64_t a = cut[(size_t)k], b = cut[(size_t)k + 1];
-    flags[(size_t)k] = avx2 ? check_trials_avx2(off, ts, a, b) : check_trials_scalar(off, ts, a, b);
+#if defined(__x86_64__)
+    if (avx2) {
+      flags[(size_t)k] = check_trials_avx2(off, ts, a, b);
+      return;
+    }
+#endif
+    flags[(size_t)k] = check_trials_scalar(off, ts, a, b);
   };
   std::vector<std::thread> pool;
   for (int64_t k = 1; k < parts; ++k) pool.emplace_back(check, k);
