@@ -593,19 +593,16 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_CUDA, "layer records: %s", cudaGetErrorString(err));
   }
-  // band-major copy of the YET at this layer's band width (built once per width)
+  // band-major copy of the YET at this layer's band width (one per width and YET): used if it
+  // exists, else made at the first run that takes the band schedule (a single pass that inverts
+  // by Newton's method never needs it)
   const int log2w = ctx->band_log2w > 0 ? ctx->band_log2w : choose_band_log2w(C, L.n_packed);
   bool banded = false;
-  if (may_build_band) {
-    const ara_status bs = ensure_band_variant(ctx, yet, log2w, &banded);
-    if (bs != ARA_OK) {
-      free_layer_on(L, ordered, st);
-      return bs;
-    }
-  } else {
-    for (const auto& v : ctx->yets[yet].bands) banded = banded || v.log2w == log2w;
-  }
-  if (banded) L.band_log2w = log2w;
+  for (const auto& v : ctx->yets[yet].bands) banded = banded || v.log2w == log2w;
+  if (banded)
+    L.band_log2w = log2w;
+  else if (may_build_band)
+    L.band_want = log2w;
   L.live = true;
   *out = L;
   return ARA_OK;

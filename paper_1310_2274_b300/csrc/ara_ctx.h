@@ -97,7 +97,9 @@ bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L);
 int layer_inversion(const ara_ctx* ctx, const LayerDev& L);
 // Rent-or-buy before a run of n trials over L: builds the tables of L's ELTs and L's packed copy
 // when the accumulated Newton work reaches the build cost; else books this run as Newton work.
-ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n);
+// With band_ok, a run that takes the band schedule first makes the layer's band-major YET copy
+// if it is still wanted.
+ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n, bool band_ok);
 // Builds every missing table of the live ELTs of a YET (servers need them).
 ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet);
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,

@@ -82,6 +82,8 @@ struct LayerDev {
   float* corr = nullptr;           // [n_packed] correlated weights (NULL: none in the layer)
   int64_t n_packed = 0;
   int32_t band_log2w = 0;          // band width of the band-major schedule (0: trial-major only)
+  int32_t band_want = 0;           // width chosen at build whose band-major YET copy is made at
+                                   // the first run that takes the band schedule (0: none)
 };
 
 // Parameters of one trial-kernel launch.

@@ -145,9 +145,17 @@ static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
 
 static ara_status rent_or_buy(ara_ctx* ctx, LayerDev& L, int64_t n);
 
-ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n) {
-  const ara_status s = rent_or_buy(ctx, L, n);
+ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n, bool band_ok) {
+  ara_status s = rent_or_buy(ctx, L, n);
   if (s != ARA_OK) return s;
+  if (band_ok && L.band_want > 0 && L.band_log2w == 0 && layer_inversion(ctx, L) == 0 &&
+      ctx->schedule == ARA_SCHED_BAND && ctx->cfg.precision == ARA_ACC_FP64) {
+    bool banded = false;
+    s = ensure_band_variant(ctx, L.yet, L.band_want, &banded);
+    if (s != ARA_OK) return s;
+    if (banded) L.band_log2w = L.band_want;
+    L.band_want = 0;
+  }
   return layer_inversion(ctx, L) == 1 ? ensure_layer_starts(ctx, L) : ARA_OK;
 }
 
@@ -490,7 +498,7 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
   if (!stream)
     CUDA_TRY(ctx, cudaMemcpyAsync(&nc_before, ctx->d_not_conv, sizeof nc_before,
                                   cudaMemcpyDeviceToHost, st));
-  s = prepare_layer_for_run(ctx, ctx->layers[layer], n);
+  s = prepare_layer_for_run(ctx, ctx->layers[layer], n, !per_occ);
   if (s != ARA_OK) return s;
   TrialParams p = make_params(ctx, Y, ctx->layers[layer], t0, n, d_ylt);
   p.oep = d_oep;
@@ -600,7 +608,7 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   if (ctx->yets[yet].host)
     return fail(ctx, ARA_ERR_INVALID_ARG, "a host-resident YET runs one layer per call");
   for (int32_t i = 0; i < n_layers; ++i) {
-    ara_status s = prepare_layer_for_run(ctx, ctx->layers[layers[i]], n);
+    ara_status s = prepare_layer_for_run(ctx, ctx->layers[layers[i]], n, true);
     if (s != ARA_OK) return s;
   }
   // one launch item per layer, grouped by schedule, inversion and lookup-entry width (one

@@ -55,6 +55,7 @@ def test_portfolio_equals_layers_run_alone(ara, staged, schedule):
     layers = build_layers(c, pf)
     c.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND if schedule == "band" else ara.SCHED_TRIAL)
     try:
+        c.run_portfolio(yet, layers, 0, 1)  # makes the layers' band-major YET copies first
         s0 = c.stats()
         m = c.run_portfolio(yet, layers, 0, N)
         s1 = c.stats()
