@@ -87,10 +87,10 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_INV_NEWTON 1
 /* ARA_OPT_SCHEDULE (value ARA_SCHED_*), for the table inversion:
  *   ARA_SCHED_BAND (default): the catalogue is cut into bands of 2^w events (w chosen per layer
- *     so that one band's lookup entries, record headers and tables fit in L2); ara_add_layer
- *     builds a band-major copy of the YET's event ids for that w once (4 bytes per occurrence
- *     plus 4 per (band, trial)), and ara_run visits the work band by band, each band's year sums
- *     kept apart and combined in band order;
+ *     so that one band's lookup entries, record headers and tables fit in L2); the layer's first
+ *     run that takes this schedule makes a band-major copy of the YET's event ids for that w,
+ *     once per w and YET (4 bytes per occurrence plus 4 per (band, trial)), and ara_run visits
+ *     the work band by band, each band's year sums kept apart and combined in band order;
  *   ARA_SCHED_TRIAL: one warp per trial over its events in order (also used by the Newton and
  *     surrogate inversions, and by layers whose YET cannot be banded: more than 2^32
  *     occurrences, trials longer than 2^(32-w) events, or more than 512 bands).
