@@ -586,6 +586,11 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
                                L.corr, L.starts, st);
   if (err == cudaSuccess && all_tables) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
+  // the largest event-loss bound sizes the grid of the exact year sums (d_cnt is free by now)
+  unsigned int ev_bits = 0u;
+  if (err == cudaSuccess) err = launch_layer_event_bound(L.evt, MW, C, L.packed, d_cnt, st);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&ev_bits, d_cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   cleanup();
   if (err != cudaSuccess) {
@@ -593,6 +598,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     free_layer_on(L, ordered, st);
     return fail(ctx, ARA_ERR_CUDA, "layer records: %s", cudaGetErrorString(err));
   }
+  memcpy(&L.ev_bound, &ev_bits, sizeof(float));
   // band-major copy of the YET at this layer's band width (one per width and YET): used if it
   // exists, else made at the first run that takes the band schedule (a single pass that inverts
   // by Newton's method never needs it)

@@ -418,11 +418,21 @@ cudaError_t launch_band_t(const TrialParams& p0, cudaStream_t st) {
 
 }  // namespace
 
-int year_grid_exponent(float occ_lim, int64_t max_len) {
-  // the largest possible year sum, max_len x OccL, must fit in 2^52 units; never finer than 2^-52
-  const double top = (double)occ_lim * (double)std::max<int64_t>(1, max_len);
-  if (!(top > 1.0)) return -52;
-  return (int)std::ceil(std::log2(top)) - 52;
+int year_grid_exponent(double o_max, int64_t max_len) {
+  // the largest possible year sum, max_len x o_max, must fit in 2^62 units, so that the 64-bit
+  // integer sum (at most half a unit of rounding per occurrence on top) never wraps; the finest
+  // grid is 2^-100, far below any binary32 occurrence result that matters
+  const double top = o_max * (double)std::max<int64_t>(1, max_len);
+  if (!(top > 0.0)) return -62;
+  return std::max(-100, (int)std::ceil(std::log2(top)) - 62);
+}
+
+double occurrence_bound(float ev_bound, double occ_ret, double occ_lim) {
+  // an event's binary32 loss sum exceeds the exact sum of its records' bounds by at most 64
+  // roundings (2^-18 relative); OccR and OccL are rounded to binary32, and l - OccR once more
+  const double l = (double)ev_bound * (1.0 + 0x1p-16);
+  const double o = std::max(0.0, l - occ_ret * (1.0 - 0x1p-20)) * (1.0 + 0x1p-20);
+  return std::min(o, occ_lim * (1.0 + 0x1p-20));
 }
 
 // Band width for a layer: the largest power of four (2^12 .. 2^18; even exponents only, so a YET

@@ -99,43 +99,69 @@ ARA_HD float ara_pow2_scale_of(float s) {
 
 // K(a,b,x) = 1/(1 + d1/(1 + d2/(...))) of DLMF 8.17.22 by the Wallis recurrence on the
 // division-free equivalent fraction T = 1 + alpha_1/(beta_1 + alpha_2/(beta_2 + ...)), K = 1/T.
-// Converges quickly for x < (a+1)/(a+b+2).  Returns K once two estimates 4 terms apart agree to
-// tol (relative); *terms counts recurrence steps.  The test compares the estimates B/A and
-// pB/pA cross-multiplied, |B pA - pB A| <= tol |B pA| (A and pA are rescaled into [1, 2)), so
-// the one division is the final K.
+// Converges quickly for x < (a+1)/(a+b+2).  The fraction is summed in blocks of four terms: after
+// each block two estimates four terms apart are compared, B/A against pB/pA cross-multiplied,
+// |B pA - pB A| <= tol |B pA| (A and pA are rescaled into [1, 2)), so the one division is the
+// final K.  CfState holds the recurrence between blocks, so a lane can sum one fraction block by
+// block and take up another's when it is done (the batched inversion of the kernels).
+struct CfState {
+  float a, b, x, apb;
+  float Am2, Am1, Bm2, Bm1;  // T_n = A_n / B_n; A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1
+  float pA, pB;              // the estimate last tested, as the pair (A, B)
+  int n;                     // index of the next (odd) term
+};
+
+ARA_HD void ara_cf_init(CfState& c, float a, float b, float x) {
+  c.a = a; c.b = b; c.x = x; c.apb = a + b;
+  c.Am2 = 1.0f; c.Am1 = 1.0f; c.Bm2 = 0.0f; c.Bm1 = 1.0f;
+  c.pA = 1.0f; c.pB = 1.0f;
+  c.n = 1;
+}
+
+// Terms n (odd) and n+1, then the exact power-of-two rescale.
+ARA_HD void ara_cf_pair(CfState& c, int n) {
+  // odd step n = 2m+1: alpha = -(a+m)(a+b+m) x  (alpha_1 = -(a+b) x: the a cancels)
+  const float m = 0.5f * (float)(n - 1);
+  const float al_odd = (n == 1) ? -c.apb * c.x : -(c.a + m) * (c.apb + m) * c.x;
+  const float be_odd = c.a + (float)n;
+  float A = be_odd * c.Am1 + al_odd * c.Am2;
+  float B = be_odd * c.Bm1 + al_odd * c.Bm2;
+  c.Am2 = c.Am1; c.Bm2 = c.Bm1; c.Am1 = A; c.Bm1 = B;
+  // even step n+1 = 2(m+1): alpha = (m+1)(b-m-1) x
+  const float m2 = m + 1.0f;
+  const float al_even = m2 * (c.b - m2) * c.x;
+  const float be_even = c.a + (float)(n + 1);
+  A = be_even * c.Am1 + al_even * c.Am2;
+  B = be_even * c.Bm1 + al_even * c.Bm2;
+  c.Am2 = c.Am1; c.Bm2 = c.Bm1; c.Am1 = A; c.Bm1 = B;
+  // exact power-of-two rescale keeps the recurrence inside binary32 range
+  const float sc = ara_pow2_scale_of(c.Am1);
+  c.Am1 *= sc; c.Am2 *= sc; c.Bm1 *= sc; c.Bm2 *= sc;
+}
+
+// Four more terms and the convergence test: true once the fraction has converged or reached
+// kCfMaxTerms terms; c.n - 1 is then the number of terms summed.
+ARA_HD bool ara_cf_block(CfState& c, float tol) {
+  ara_cf_pair(c, c.n);
+  ara_cf_pair(c, c.n + 2);
+  c.n += 4;
+  const float cur = c.Bm1 * c.pA;
+  if (fabsf(fmaf(-c.pB, c.Am1, cur)) <= tol * fabsf(cur)) return true;
+  c.pA = c.Am1;
+  c.pB = c.Bm1;
+  return c.n > kCfMaxTerms;
+}
+
+ARA_HD float ara_cf_value(const CfState& c) { return c.Bm1 / c.Am1; }
+
+// The whole fraction for one lane; *terms is increased by the number of terms summed.
 ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e-7f) {
-  const float apb = a + b;
-  // T_n = A_n / B_n.  A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1.
-  float Am2 = 1.0f, Am1 = 1.0f, Bm2 = 0.0f, Bm1 = 1.0f;
-  float pA = 1.0f, pB = 1.0f;  // the estimate last tested, as the pair (A, B)
-  int n = 1;
-  for (; n <= kCfMaxTerms; n += 2) {
-    // odd step n = 2m+1: alpha = -(a+m)(a+b+m) x  (alpha_1 = -(a+b) x: the a cancels)
-    const float m = 0.5f * (float)(n - 1);
-    const float al_odd = (n == 1) ? -apb * x : -(a + m) * (apb + m) * x;
-    const float be_odd = a + (float)n;
-    float A = be_odd * Am1 + al_odd * Am2;
-    float B = be_odd * Bm1 + al_odd * Bm2;
-    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
-    // even step n+1 = 2(m+1): alpha = (m+1)(b-m-1) x
-    const float m2 = m + 1.0f;
-    const float al_even = m2 * (b - m2) * x;
-    const float be_even = a + (float)(n + 1);
-    A = be_even * Am1 + al_even * Am2;
-    B = be_even * Bm1 + al_even * Bm2;
-    Am2 = Am1; Bm2 = Bm1; Am1 = A; Bm1 = B;
-    // exact power-of-two rescale keeps the recurrence inside binary32 range
-    const float sc = ara_pow2_scale_of(Am1);
-    Am1 *= sc; Am2 *= sc; Bm1 *= sc; Bm2 *= sc;
-    if (((n + 1) & 3) == 0 || n + 2 > kCfMaxTerms) {
-      const float cur = Bm1 * pA;
-      if (fabsf(fmaf(-pB, Am1, cur)) <= tol * fabsf(cur)) { n += 2; break; }
-      pA = Am1;
-      pB = Bm1;
-    }
+  CfState c;
+  ara_cf_init(c, a, b, x);
+  while (!ara_cf_block(c, tol)) {
   }
-  if (terms) *terms += n - 1;
-  return Bm1 / Am1;
+  if (terms) *terms += c.n - 1;
+  return ara_cf_value(c);
 }
 
 // Normal quantile for the upper tail probability q in (0, 1/2]: the deviate t with
@@ -160,6 +186,174 @@ struct BetaRec {
   float p0, lnx0, lny0, lns;
 };
 
+// The state of one inversion between the pieces of a Halley iteration (the one-lane inversion
+// below runs them in a loop; the batched inversion of the kernels runs the continued fraction of
+// many inversions in between).
+struct HalleyState {
+  float a, b, s, lnx0, lny0, L0, lna, lnp, thr;  // of the tail solved (swapped when u > p0)
+  float t, x;                                    // current iterate, t = ln x
+  bool flip, good;                               // tail swapped; start from a table's estimate
+};
+
+// Start of the inversion.  Returns false when it is already done (r holds the result): the
+// start lies below e^-69, where the loss max_l x is far under every term of a year loss.
+ARA_HD bool ara_halley_setup(const BetaRec& rec, float u, float start_logit, HalleyState& h,
+                             IbetaResult& r) {
+  r.iters = 0;
+  r.cf_terms = 0;
+  r.converged = true;
+  r.t = 0.0f;
+  h.flip = u > rec.p0;
+  const float p = h.flip ? 1.0f - u : u;
+  h.a = h.flip ? rec.b : rec.a;
+  h.b = h.flip ? rec.a : rec.b;
+  h.lnx0 = h.flip ? rec.lny0 : rec.lnx0;
+  h.lny0 = h.flip ? rec.lnx0 : rec.lny0;
+  h.L0 = rec.L0;
+  h.s = h.a + h.b;
+  h.lna = h.lnx0 + rec.lns;
+  h.lnp = logf(p);
+  const float a = h.a, b = h.b;
+
+  // small-x limit of DLMF 8.17.22 (K -> 1, y -> 1): ln p = L0 + a ln(x/x0) - b ln y0 - ln a
+  float t = h.lnx0 + (h.lnp + h.lna - h.L0 + b * h.lny0) / a;
+  if (a > 1.0f && b > 1.0f) {
+    // A&S 26.5.22: x ~ a / (a + b e^{2w}), with yp the upper-tail normal deviate of p.
+    const float yp = ara_norm_upper_quantile(fminf(p, 0.5f));
+    const float ypl = p > 0.5f ? -ara_norm_upper_quantile(1.0f - p) : yp;
+    const float lam = (ypl * ypl - 3.0f) / 6.0f;
+    const float hh = 2.0f / (1.0f / (2.0f * a - 1.0f) + 1.0f / (2.0f * b - 1.0f));
+    const float w = ypl * sqrtf(fmaxf(hh + lam, 0.0f)) / hh -
+                    (1.0f / (2.0f * b - 1.0f) - 1.0f / (2.0f * a - 1.0f)) *
+                        (lam + 5.0f / 6.0f - 2.0f / (3.0f * hh));
+    t = h.lna - logf(a + b * expf(2.0f * w));
+  }
+  h.good = start_logit < 1e29f;  // false for NaN too
+  if (h.good) {
+    // a table's estimate below e^-69 ends the inversion only if the analytic start (exact in
+    // that limit) agrees: start tables are not certified, and on shapes far outside the ELT
+    // value law (a, b near 1e-6 under the sd clamp of §3.3) they can be far off
+    const float ts = h.flip ? -log1pf(expf(start_logit)) : -log1pf(expf(-start_logit));
+    if (ts > -69.0f) t = ts; else h.good = false;
+  }
+  t = fminf(t, h.lnx0);  // the root is below the mean
+  h.thr = (a + 1.0f) / (h.s + 2.0f);
+  h.t = t;
+  if (!(t > -69.0f)) {  // below e^-69 ~ 1e-30
+    r.x = h.flip ? 1.0f : 0.0f;
+    r.t = t;
+    return false;
+  }
+  h.x = expf(t);
+  return true;
+}
+
+// The part of a Halley iteration before the continued fraction: E = ln(x^a y^b / B(a,b)) and the
+// fraction to sum, K(a,b,x) below the threshold x = (a+1)/(a+b+2) (I_x = P K / a), else K(b,a,y)
+// (the complement I_y(b,a) = P K / b).
+struct HalleyPre {
+  float y, E;
+  bool lower;
+  float ca, cb, cx;  // arguments of the continued fraction
+};
+
+ARA_HD HalleyPre ara_halley_pre(const HalleyState& h) {
+  HalleyPre q;
+  const float x = h.x;
+  q.y = 1.0f - x;
+  // E = L0 + a ln(x/x0) + b ln(y/y0), w = (x - x0)(a + b)
+  const float w = fmaf(x, h.s, -h.a);
+  const float rx = w / h.a;   // x/x0 - 1
+  const float ry = -w / h.b;  // y/y0 - 1
+  const float lnrx = rx > -0.5f ? log1pf(rx) : h.t - h.lnx0;
+  const float lnry = ry > -0.5f ? log1pf(ry) : logf(q.y) - h.lny0;
+  q.E = h.L0 + h.a * lnrx + h.b * lnry;
+  q.lower = x < h.thr;
+  q.ca = q.lower ? h.a : h.b;
+  q.cb = q.lower ? h.b : h.a;
+  q.cx = q.lower ? x : q.y;
+  return q;
+}
+
+// The part after it: G = ln I_x - ln p, G' and Halley's step in t.  Returns true when the
+// iteration `it` (0-based) ends the inversion.
+ARA_HD bool ara_halley_post(HalleyState& h, const HalleyPre& q, float K, int it) {
+  const float a = h.a, b = h.b, x = h.x, y = q.y;
+  float G, dG;
+  if (q.lower) {
+    G = q.E + logf(K) - h.lna - h.lnp;
+    dG = a / (y * K);
+  } else {
+    const float P = expf(q.E);
+    const float J = P * K / b;  // I_{1-x}(b,a)
+    G = log1pf(-J) - h.lnp;
+    dG = P / (y * (1.0f - J));
+  }
+  // Where I_x is nearly flat in t (G' below 1e-3: a shape parameter far below the paper's
+  // value law, e.g. the sd clamp of §3.3, which gives a, b near 1e-6) the binary32 residual's
+  // rounding noise (a few units of 2^-24 times the exponent E, |E| ~ 15 there) moves the
+  // Newton step by far more than 3e-4 and the steps never settle; there the iteration ends
+  // once the residual is at that noise, x then being the exact quantile of a uniform within a
+  // few 1e-6 of u (a backward-error stop).
+  if (dG < 1e-3f && fabsf(G) <= 2.4e-7f * (2.0f + fabsf(q.E))) return true;
+  // Halley's correction of the Newton step dn = G/G': the second derivative is free, since
+  // G' = x f(x) / I_x gives G'' = G' (a - (b-1) x/y - G'); the step converges cubically, so
+  // a step of 3e-4 leaves an error near 1e-11 in t.  Far from the root (|dn c| large) the
+  // plain Newton step is taken.
+  const float dn = G / dG;
+  const float c = 0.5f * (a - (b - 1.0f) * x / y - dG);
+  const float den = 1.0f - dn * c;
+  float tn = h.t - ((den > 0.5f && den < 2.0f) ? dn / den : dn);
+  if (!(tn < 0.0f)) tn = 0.5f * h.t;  // a step past x = 1 is halved toward it
+  const float step = fabsf(tn - h.t);
+  h.t = tn;
+  h.x = expf(tn);
+  if ((it > 0 || h.good) && step <= 3.0e-4f) return true;
+  if (!(tn > -69.0f)) {
+    h.x = 0.0f;
+    return true;
+  }
+  return false;
+}
+
+ARA_HD void ara_halley_result(const HalleyState& h, int iters, bool done, IbetaResult& r) {
+  r.iters = iters;
+  r.converged = done;
+  r.t = h.t;
+  r.x = h.flip ? 1.0f - h.x : h.x;
+}
+
+// Iterations it0, it0 + 1, ... of an inversion set up by ara_halley_setup, to the end; r.cf_terms
+// is increased by the terms summed.  From the analytic start (~1e-2 from the root) the first
+// iteration's continued fraction is summed only to 1e-4 and cannot end the loop; later
+// iterations (and every one from a start table's estimate) are summed to binary32 accuracy.
+// ONE_CF: evaluate the continued fraction in one loop whichever side of the threshold x lies on
+// (lanes of a warp on different sides share it; 16% faster where most hits invert this way), or
+// in a loop per side (fewer registers, for the out-of-line fallback of the table paths).  Both
+// give the same result bit for bit.
+template <bool ONE_CF>
+ARA_HD void ara_halley_iterate(HalleyState& h, int it0, IbetaResult& r) {
+  const float cf_first = h.good ? 1.2e-7f : 1.0e-4f;
+  bool done = false;
+  int it = it0;
+  for (; it < kIbetaMaxIter; ++it) {
+    const HalleyPre q = ara_halley_pre(h);
+    const float tol = it == 0 ? cf_first : 1.2e-7f;
+    float K;
+    if constexpr (ONE_CF)
+      K = ara_beta_cf(q.ca, q.cb, q.cx, &r.cf_terms, tol);
+    else
+      K = q.lower ? ara_beta_cf(h.a, h.b, h.x, &r.cf_terms, tol)
+                  : ara_beta_cf(h.b, h.a, q.y, &r.cf_terms, tol);
+    if (ara_halley_post(h, q, K, it)) {
+      done = true;
+      ++it;
+      break;
+    }
+  }
+  ara_halley_result(h, it, done, r);
+}
+
 // Solve I_x(a,b) = u for x, x in [0,1].
 //
 // Halley's method on G(t) = ln I_{e^t}(a,b) - ln p in t = ln x.  Below the threshold
@@ -171,106 +365,15 @@ struct BetaRec {
 // problem I_y(b,a) = 1 - u (exact on the uniform grid) is solved for y = 1 - x instead, so the
 // unknown solved for is always below the mean of its distribution.
 // start_logit: an estimate of ln(x / (1 - x)) accurate to ~1e-4 (a start table's value), or
-// anything not below 1e29 to use the analytic start.  From a good start the first iteration sums
-// its continued fraction fully and may end the loop.
-// ONE_CF: evaluate the continued fraction in one loop whichever side of the threshold x lies on
-// (lanes of a warp on different sides share it; 16% faster where most hits invert this way), or
-// in a loop per side (fewer registers, for the out-of-line fallback of the table paths).  Both
-// give the same result bit for bit.
+// anything not below 1e29 to use the analytic start (the small-x limit of DLMF 8.17.22 or, for
+// a, b > 1, the normal approximation of A&S 26.5.22).  From a good start the first iteration
+// sums its continued fraction fully and may end the loop.
 template <bool ONE_CF = true>
 ARA_HD IbetaResult ara_inv_beta(const BetaRec& rec, float u, float start_logit = 1e30f) {
   IbetaResult r;
-  r.iters = 0;
-  r.cf_terms = 0;
-  r.converged = true;
-  r.t = 0.0f;
-  const bool flip = u > rec.p0;
-  const float p = flip ? 1.0f - u : u;
-  const float a = flip ? rec.b : rec.a;
-  const float b = flip ? rec.a : rec.b;
-  const float lnx0 = flip ? rec.lny0 : rec.lnx0;
-  const float lny0 = flip ? rec.lnx0 : rec.lny0;
-  const float L0 = rec.L0;
-  const float s = a + b;
-  const float lna = lnx0 + rec.lns;
-  const float lnp = logf(p);
-
-  // ---- start --------------------------------------------------------------------------------
-  // small-x limit of DLMF 8.17.22 (K -> 1, y -> 1): ln p = L0 + a ln(x/x0) - b ln y0 - ln a
-  float t = lnx0 + (lnp + lna - L0 + b * lny0) / a;
-  if (a > 1.0f && b > 1.0f) {
-    // A&S 26.5.22: x ~ a / (a + b e^{2w}), with yp the upper-tail normal deviate of p.
-    const float yp = ara_norm_upper_quantile(fminf(p, 0.5f));
-    const float ypl = p > 0.5f ? -ara_norm_upper_quantile(1.0f - p) : yp;
-    const float lam = (ypl * ypl - 3.0f) / 6.0f;
-    const float h = 2.0f / (1.0f / (2.0f * a - 1.0f) + 1.0f / (2.0f * b - 1.0f));
-    const float w = ypl * sqrtf(fmaxf(h + lam, 0.0f)) / h -
-                    (1.0f / (2.0f * b - 1.0f) - 1.0f / (2.0f * a - 1.0f)) *
-                        (lam + 5.0f / 6.0f - 2.0f / (3.0f * h));
-    t = lna - logf(a + b * expf(2.0f * w));
-  }
-  const bool good = start_logit < 1e29f;  // false for NaN too
-  if (good) t = flip ? -log1pf(expf(start_logit)) : -log1pf(expf(-start_logit));
-  t = fminf(t, lnx0);  // the root is below the mean
-  // Below e^-69 ~ 1e-30 the loss max_l * x is far under every term of a year loss.
-  if (!(t > -69.0f)) { r.x = flip ? 1.0f : 0.0f; r.t = t; return r; }
-
-  // ---- Newton-Halley iterations in t --------------------------------------------------------
-  // From the analytic start (~1e-2 from the root) the first iteration's continued fraction is
-  // summed only to 1e-4 and cannot end the loop; later iterations (and every one from a start
-  // table's estimate) are summed to binary32 accuracy.
-  const float cf_first = good ? 1.2e-7f : 1.0e-4f;
-  const float thr = (a + 1.0f) / (s + 2.0f);
-  bool done = false;
-  int it = 0;
-  float x = expf(t);
-  for (; it < kIbetaMaxIter; ++it) {
-    const float y = 1.0f - x;
-    // E = ln(x^a y^b / B(a,b)) = L0 + a ln(x/x0) + b ln(y/y0), w = (x - x0)(a + b)
-    const float w = fmaf(x, s, -a);
-    const float rx = w / a;   // x/x0 - 1
-    const float ry = -w / b;  // y/y0 - 1
-    const float lnrx = rx > -0.5f ? log1pf(rx) : t - lnx0;
-    const float lnry = ry > -0.5f ? log1pf(ry) : logf(y) - lny0;
-    const float E = L0 + a * lnrx + b * lnry;
-    // below the threshold K(a,b,x) gives I_x = P K / a, above it K(b,a,y) gives the complement
-    // I_y(b,a) = P K / b
-    const bool lower = x < thr;
-    const float tol = it == 0 ? cf_first : 1.2e-7f;
-    float K;
-    if constexpr (ONE_CF)
-      K = ara_beta_cf(lower ? a : b, lower ? b : a, lower ? x : y, &r.cf_terms, tol);
-    else
-      K = lower ? ara_beta_cf(a, b, x, &r.cf_terms, tol) : ara_beta_cf(b, a, y, &r.cf_terms, tol);
-    float G, dG;
-    if (lower) {
-      G = E + logf(K) - lna - lnp;
-      dG = a / (y * K);
-    } else {
-      const float P = expf(E);
-      const float J = P * K / b;  // I_{1-x}(b,a)
-      G = log1pf(-J) - lnp;
-      dG = P / (y * (1.0f - J));
-    }
-    // Halley's correction of the Newton step dn = G/G': the second derivative is free, since
-    // G' = x f(x) / I_x gives G'' = G' (a - (b-1) x/y - G'); the step converges cubically, so
-    // a step of 3e-4 leaves an error near 1e-11 in t.  Far from the root (|dn c| large) the
-    // plain Newton step is taken.
-    const float dn = G / dG;
-    const float c = 0.5f * (a - (b - 1.0f) * x / y - dG);
-    const float den = 1.0f - dn * c;
-    float tn = t - ((den > 0.5f && den < 2.0f) ? dn / den : dn);
-    if (!(tn < 0.0f)) tn = 0.5f * t;  // a step past x = 1 is halved toward it
-    const float step = fabsf(tn - t);
-    t = tn;
-    x = expf(t);
-    if ((it > 0 || good) && step <= 3.0e-4f) { done = true; ++it; break; }
-    if (!(t > -69.0f)) { done = true; ++it; x = 0.0f; break; }
-  }
-  r.iters = it;
-  r.converged = done;
-  r.t = t;
-  r.x = flip ? 1.0f - x : x;
+  HalleyState h;
+  if (!ara_halley_setup(rec, u, start_logit, h, r)) return r;
+  ara_halley_iterate<ONE_CF>(h, 0, r);
   return r;
 }
 

@@ -84,6 +84,7 @@ struct LayerDev {
   int32_t band_log2w = 0;          // band width of the band-major schedule (0: trial-major only)
   int32_t band_want = 0;           // width chosen at build whose band-major YET copy is made at
                                    // the first run that takes the band schedule (0: none)
+  float ev_bound = 0.f;            // largest event-loss bound (sizes the year-sum grid)
 };
 
 // Parameters of one trial-kernel launch.
@@ -180,6 +181,11 @@ cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
                                  float* packed_corr, float* packed_starts, cudaStream_t st);
+// *d_bound = binary32 bits of the layer's largest event-loss bound (sum over an event's records
+// of max_l, or the mean where sd = 0), rounded up; 0 for a layer without records
+cudaError_t launch_layer_event_bound(const uint32_t* d_evt, int mask_words, int64_t catalog,
+                                     const BetaRec* packed, unsigned int* d_bound,
+                                     cudaStream_t st);
 // starts[n * kStartFloats]: the records' start tables of the Newton-Halley inversion
 cudaError_t launch_build_starts(int64_t n, const BetaRec* recs, float* starts, cudaStream_t st);
 // ab64[n]: each record's (alpha, beta) in binary64, as written by launch_prepare_elt.
@@ -201,8 +207,11 @@ bool band_layout_fits(const YetDev& y, int log2w);
 cudaError_t build_band_variant(const YetDev& y, int log2w, BandedYet& out, cudaStream_t st);
 void free_band_variant(BandedYet& v);
 int64_t band_tiles(int64_t n);
-// exponent e of the year-sum grid for trials of at most max_len occurrences under OccL
-int year_grid_exponent(float occ_lim, int64_t max_len);
+// exponent e of the year-sum grid for trials of at most max_len occurrences, each at most o_max
+int year_grid_exponent(double o_max, int64_t max_len);
+// the largest occurrence result o = min(max(l - OccR, 0), OccL) the kernels can produce when no
+// event loss l exceeds ev_bound (binary32 rounding of the sums and of OccR included)
+double occurrence_bound(float ev_bound, double occ_ret, double occ_lim);
 // band kernel + per-trial finalisation over p.t0 .. p.t0 + p.n; p.ysum holds n words (zeroed here)
 cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cudaStream_t st);
 // many items in one launch (serving slices, portfolio layers), all with mask_words-word lookup

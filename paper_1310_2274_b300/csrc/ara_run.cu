@@ -243,7 +243,7 @@ static ara_status finish_run(ara_ctx* ctx, void* stream, bool dev_out, double* y
 // bisection on the same binary64 expression the kernels evaluate, which is monotone in s.
 static void agg_bounds(double unit, double agg_ret, double agg_lim, unsigned long long* zero_max,
                        unsigned long long* full_min) {
-  const unsigned long long top = 1ull << 53;  // year sums stay below 2^52 units
+  const unsigned long long top = 1ull << 63;  // year sums stay below 2^62 + max_len / 2 units
   auto net = [&](unsigned long long s) { return (double)s * unit - agg_ret; };
   // largest s in [0, top] with net(s) <= 0 (net(0) <= 0 always)
   unsigned long long lo = 0, hi = top;
@@ -300,7 +300,7 @@ TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_
   p.not_conv = ctx->d_not_conv;
   p.stats = ctx->d_stats;
   p.yet_n = Y.n_trials;
-  const int qe = year_grid_exponent((float)L.occ_lim, Y.max_len);
+  const int qe = year_grid_exponent(occurrence_bound(L.ev_bound, L.occ_ret, L.occ_lim), Y.max_len);
   p.q_scale = std::ldexp(1.0f, -qe);
   p.q_unit = std::ldexp(1.0, qe);
   agg_bounds(p.q_unit, L.agg_ret, L.agg_lim, &p.agg_zero_max, &p.agg_full_min);

@@ -194,6 +194,35 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
   }
 }
 
+// The largest loss an event of the layer can bring before occurrence terms: over catalogue events,
+// the sum of the event's records' loss bounds (the support bound max_l with sd > 0, the mean with
+// sd = 0: packed[].mx holds exactly that), summed in binary64 and rounded up to binary32; the
+// warp's maximum goes to *bound as an integer maximum of non-negative binary32 patterns.  It sizes
+// the grid of the exact year sums (paper §2.3: o <= min(OccL, max(l - OccR, 0))).
+__global__ void layer_event_bound_kernel(const uint32_t* __restrict__ evt, int mask_words,
+                                         int64_t catalog, const BetaRec* __restrict__ packed,
+                                         unsigned int* bound) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned int b = 0u;
+  if (e < catalog) {
+    uint32_t base, cnt;
+    if (mask_words == 1) {
+      const uint2 v = reinterpret_cast<const uint2*>(evt)[e];
+      base = v.x;
+      cnt = __popc(v.y);
+    } else {
+      const uint4 v = reinterpret_cast<const uint4*>(evt)[e];
+      base = v.x;
+      cnt = __popc(v.y) + __popc(v.z);
+    }
+    double s = 0.0;
+    for (uint32_t r = 0; r < cnt; ++r) s += (double)packed[base + r].mx;
+    b = __float_as_uint(__double2float_ru(s));
+  }
+  b = __reduce_max_sync(0xFFFFFFFFu, b);
+  if ((threadIdx.x & 31) == 0 && b != 0u) atomicMax(bound, b);
+}
+
 // ---- exclusive scan of uint32 (three passes: block sums, scan of sums, block scans) ----------
 constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 8;  // per thread
@@ -361,6 +390,17 @@ cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                                            mask_words, d_evt, packed, table_src,
                                                            packed_rec, e.corr, packed_corr,
                                                            e.starts, packed_starts);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_event_bound(const uint32_t* d_evt, int mask_words, int64_t catalog,
+                                     const BetaRec* packed, unsigned int* d_bound,
+                                     cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_bound, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess || catalog == 0) return e;
+  layer_event_bound_kernel<<<grid_for(catalog), kThreads, 0, st>>>(d_evt, mask_words, catalog,
+                                                                   packed, d_bound);
   count_launches(1);
   return cudaGetLastError();
 }

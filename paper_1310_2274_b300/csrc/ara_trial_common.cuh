@@ -15,9 +15,11 @@ namespace {
 // occurrence's result; warp_reduce() combines the 32 lanes; value() is the year sum S.
 //
 // AccExact (ARA_ACC_FP64): each binary32 occurrence result is rounded to a multiple of the
-// item's grid unit 2^e (e chosen per launch so that max trial length x OccL fits in 2^52 units)
-// and summed exactly in 64-bit integers; S = units x 2^e is then exact in binary64.  The sum is
-// independent of the order and grouping of the additions, so every schedule gives the same S.
+// item's grid unit 2^e and summed exactly in 64-bit integers.  e is chosen per launch so that the
+// longest trial times the largest occurrence result the layer's records allow (the sum of an
+// event's loss bounds less OccR, at most OccL) fits in 2^62 units; S = units x 2^e is rounded
+// once to binary64.  The integer sum is independent of the order and grouping of the additions,
+// so every schedule gives the same S.
 struct AccExact {
   unsigned long long s = 0;
   float qs = 1.0f;    // 2^-e

@@ -52,3 +52,47 @@ def test_host_timestamp_check():
     cases, wrong, flagged = (int(v) for v in out)
     assert cases == 400 and wrong == 0
     assert 250 <= flagged <= 300  # three kinds in four plant a NaN or a decrease
+
+
+# (mean, sd, max): sd above the largest a beta distribution with mean/max allows, so paper §3.3's
+# clamp applies and alpha, beta come out near 1e-6
+CLAMPED = [(1.0, 1.0, 1.5), (1000.0, 1500.0, 2000.0), (5e5, 9e5, 1.1e6), (1.0, 1.5, 2.5),
+           (3e5, 6e5, 4e5)]
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs a host C++ compiler")
+def test_clamped_records_invert_to_a_valid_quantile(oracle):
+    """On clamped records the quantile is a near-step function: all but a few 1e-5 of the uniform
+    grid maps to x within 1e-5 of 0 or 1, and in the narrow band between, x is extremely sensitive
+    to the binary32 evaluation of I_x.  Every inversion must converge (no iteration cap), agree
+    with the FP64 oracle within 1e-5 wherever the problem is well conditioned, and elsewhere be
+    the exact quantile of a uniform within 5e-6 of u (backward error), checked by the oracle's
+    I_x in binary64."""
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "clamp_check")
+        subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC, "-o", exe,
+                        os.path.join(HERE, "clamp_check.cpp")], check=True)
+        for mean, sd, mx in CLAMPED:
+            rc, a_o, b_o = oracle.beta_moments(mean, sd, mx)
+            assert rc == 1  # the oracle clamps too
+            out = subprocess.run([exe, repr(mean), repr(sd), repr(mx), "509"], check=True,
+                                 capture_output=True, text=True).stdout.splitlines()
+            a, b, _ = out[0].split()
+            a, b = float(a), float(b)
+            assert a == pytest.approx(a_o, rel=1e-12) and b == pytest.approx(b_o, rel=1e-12)
+            assert a < 2e-6 and b < 2e-6
+            rows = [line.split() for line in out[1:]]
+            assert len(rows) == 16_481 + 6_001
+            n_sensitive = 0
+            for u_s, xn_s, xs_s, cn, cs in rows:
+                assert cn == "1" and cs == "1", (mean, u_s)
+                u = float(u_s)
+                xo, st = oracle.betaincinv(a, b, u)
+                assert st == 0
+                for x in (float(xn_s), float(xs_s)):
+                    assert 0.0 <= x <= 1.0
+                    if abs(x - xo) <= 1e-5:
+                        continue
+                    n_sensitive += 1
+                    assert abs(oracle.betainc(a, b, x) - u) <= 5e-6, (mean, u, x, xo)
+            assert 0 < n_sensitive <= 400  # the window holds the band, a few 1e-5 of u
