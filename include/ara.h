@@ -303,7 +303,9 @@ typedef struct {
   double gen_ms, train_ms, cert_ms;
   double cells_accepted;          /* fraction of certification cells with error <= eps          */
   double err_median, err_p99;     /* over cells: recorded |x_net - x|                            */
-  int64_t bad_targets;            /* tuples whose exact inversion reported non-convergence       */
+  int64_t bad_targets;            /* training tuples and certification points whose exact        */
+                                  /* inversion reported non-convergence (such a point rejects     */
+                                  /* its cell)                                                    */
 } ara_surrogate_report;
 ARA_API ara_status ara_train_surrogate(ara_ctx* ctx, const ara_surrogate_config* cfg,
                                        ara_surrogate_report* report);
@@ -349,8 +351,9 @@ ARA_API ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int6
  *   stream       cudaStream_t (NULL = the legacy default stream); the call is asynchronous and
  *                the outputs are valid once the stream has passed it.
  * Scratch is a fixed device array inside the library (about 29 MB, held by every GPU that loads
- * the library until the process exits).  The first call on a device looks up that array's device
- * address (make it before any stream capture).  Calls share the array: calls whose work overlaps
+ * the library until the process exits).  Every call looks up that array's device address on the
+ * current device; the first call on a device also loads the library's device code there (make it
+ * before any stream capture).  Calls share the array: calls whose work overlaps
  * on the GPU race and must not be made.  A YLT holding NaN yields NaN outputs.
  * Returns ARA_ERR_INVALID_ARG for a size above the maximum, host pointers or a bad return
  * period; ARA_ERR_CUDA if a launch fails; ARA_ERR_NO_DEVICE without a current device. */

@@ -364,11 +364,13 @@ __global__ void cert_points_kernel(int64_t n_cells, int samples, uint64_t seed, 
   u = fmin(fmax(u, 0x1p-24), 1.0 - 0x1p-24);
   const float uf = (float)(ldexp(2.0 * floor(ldexp(u, 23)) + 1.0, -24));
   double lnx, ln1mx;
-  if (!ara_exact_quantile_logs(a, b, uf, &lnx, &ln1mx)) atomicAdd(bad, 1u);
+  const bool ok = ara_exact_quantile_logs(a, b, uf, &lnx, &ln1mx);
+  if (!ok) atomicAdd(bad, 1u);
   Z[3 * i + 0] = (float)((log(a) - kLnCenter) / kLnHalf);
   Z[3 * i + 1] = (float)((log(b) - kLnCenter) / kLnHalf);
   Z[3 * i + 2] = (logf(uf) - log1pf(-uf)) / kLogitScale;
-  X[i] = (float)exp(lnx);
+  // no reference where the exact inversion failed: NaN makes the cell's bound 1 (rejected)
+  X[i] = ok ? (float)exp(lnx) : __int_as_float(0x7FC00000);
 }
 
 __global__ void cert_reduce_kernel(int64_t n_cells, int samples, const float* X, const float* Y,

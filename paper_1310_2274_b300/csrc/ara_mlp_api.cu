@@ -94,8 +94,11 @@ ara_status mlp_certify(ara_ctx* ctx, int samples, uint64_t seed, ara_surrogate_r
     return fail(ctx, ARA_ERR_CUDA, "surrogate certification: %s", cudaGetErrorString(e));
   }
   std::vector<float> b(kCertCells);
+  unsigned int n_bad = 0;
   e = cudaMemcpyAsync(b.data(), ctx->mlp_bound, sizeof(float) * kCertCells, cudaMemcpyDeviceToHost,
                       ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&n_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   cleanup();
   if (e != cudaSuccess) return fail(ctx, ARA_ERR_CUDA, "surrogate certification: %s", cudaGetErrorString(e));
@@ -105,6 +108,7 @@ ara_status mlp_certify(ara_ctx* ctx, int samples, uint64_t seed, ara_surrogate_r
     rep->cells_accepted = (double)acc / (double)kCertCells;
     rep->err_median = percentile(b, 0.5);
     rep->err_p99 = percentile(b, 0.99);
+    rep->bad_targets += n_bad;
   }
   return ARA_OK;
 }
@@ -235,7 +239,7 @@ ara_status ara_train_surrogate(ara_ctx* ctx, const ara_surrogate_config* cfg,
   }
   rep.loss_first = a / w;
   rep.loss_last = z / w;
-  rep.bad_targets = hbad;
+  rep.bad_targets += hbad;  // plus the certification points counted by mlp_certify
   cleanup();
   if (report) *report = rep;
   return ARA_OK;

@@ -17,8 +17,6 @@
 #include <math.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "../../include/ara.h"
 #include "ara_internal.h"
 
@@ -42,25 +40,15 @@ constexpr size_t kScratchBytes = kOffFlags + 256;
 
 static __device__ __align__(256) unsigned char g_risk_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_risk_scratch on the current device, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, never a device address.
+// Device address of g_risk_scratch on the current device.  In host code the array's name is only
+// a host-side stand-in, never a device address.  The address is looked up on every call, not
+// cached: a cudaDeviceReset (or any other teardown of the device's primary context) reloads the
+// module, and an address kept from before it would point at freed memory.
 cudaError_t scratch_for_current_device(unsigned char** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_risk_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_risk_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
