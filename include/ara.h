@@ -85,16 +85,18 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_OPT_INVERSION 4
 #define ARA_INV_TABLE 0
 #define ARA_INV_NEWTON 1
-/* ARA_OPT_SCHEDULE (value ARA_SCHED_*), for the table inversion:
+/* ARA_OPT_SCHEDULE (value ARA_SCHED_*):
  *   ARA_SCHED_BAND (default): the catalogue is cut into bands of 2^w events (w chosen per layer
  *     so that one band's lookup entries, record headers and tables fit in L2); the layer's first
- *     run that takes this schedule makes a band-major copy of the YET's event ids for that w,
+ *     run with the table inversion makes a band-major copy of the YET's event ids for that w,
  *     once per w and YET (4 bytes per occurrence plus 4 per (band, trial)), and ara_run visits
- *     the work band by band, each band's year sums kept apart and combined in band order;
- *   ARA_SCHED_TRIAL: one warp per trial over its events in order (also used by the Newton and
- *     surrogate inversions, and by layers whose YET cannot be banded: more than 2^32
- *     occurrences, trials longer than 2^(32-w) events, or more than 512 bands).
- * Both give the same hits, uniforms and losses; year sums differ only in summation order. */
+ *     the work band by band, each band's year sums kept apart and combined exactly.  A run with
+ *     the Newton-Halley inversion takes this schedule too where that copy exists already (it
+ *     never makes one: a single pass gains far less than the copy costs);
+ *   ARA_SCHED_TRIAL: one warp per trial over its events in order (also used by the surrogate
+ *     inversion, by per-occurrence outputs, and by layers whose YET cannot be banded: more than
+ *     2^32 occurrences, trials longer than 2^(32-w) events, or more than 512 bands).
+ * Both give the same hits, uniforms, losses and year losses, bit for bit. */
 #define ARA_OPT_SCHEDULE 5
 #define ARA_SCHED_BAND 0
 #define ARA_SCHED_TRIAL 1
@@ -326,7 +328,9 @@ ARA_API ara_status ara_mlp_grad(ara_ctx* ctx, const float* params, const float* 
                                 const float* t, int64_t n, float* grad, double* loss);
 
 /* Verification ------------------------------------------------------------------------------------
- * Re-runs trials [t0, t0+n) with the same device code as ara_run, additionally listing every
+ * Re-runs trials [t0, t0+n) with the same device code as ara_run (trial-major, after the same
+ * preparation of the layer: tables or start tables as a run of these trials would build them),
+ * additionally listing every
  * (trial, event, ELT) hit in event order, then layer order: the trial offset from t0, the event
  * position k within its trial, the layer slot j, the record index in the caller's ELT order, the
  * uniform u, the beta quantile x (NaN for a sigma = 0 record) and the loss.  Host arrays of
@@ -432,7 +436,8 @@ ARA_API ara_status ara_server_result(ara_server* s, int64_t ticket, ara_request_
 ARA_API ara_status ara_server_release(ara_server* s, int64_t ticket);
 ARA_API ara_status ara_server_get_stats(ara_server* s, ara_server_stats* out);
 /* Stops the worker after the launches in flight, frees the server's memory and gives the context
- * back its own stream.  Requests not yet finished are dropped.  NULL-safe. */
+ * back the stream and the inversion options (ARA_OPT_SURROGATE, ARA_OPT_INVERSION) it had before
+ * ara_server_create.  Requests not yet finished are dropped.  NULL-safe. */
 ARA_API void ara_server_destroy(ara_server* s);
 
 /* Synchronises the context's stream. */

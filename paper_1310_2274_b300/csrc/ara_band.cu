@@ -120,7 +120,33 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, unsigned lo
 // CORR: the launch may carry correlated weights (paper §3.2; P.corr is still checked, since a
 // batch mixes items); without them the draw is the hit's own uniform and the weight load and
 // combination are compiled out.
-template <int MW, bool CORR>
+// The 32-byte record and the 24-byte start-table piece of a hit under the evict-last policy:
+// while a band is processed its records and start tables are reused from L2.
+__device__ __forceinline__ BetaRec load_rec_keep(const BetaRec* p, unsigned long long keep) {
+  const uint4 a = ld_keep_u4(reinterpret_cast<const uint4*>(p), keep);
+  const uint4 b = ld_keep_u4(reinterpret_cast<const uint4*>(p) + 1, keep);
+  BetaRec r;
+  r.a = __uint_as_float(a.x); r.b = __uint_as_float(a.y);
+  r.mx = __uint_as_float(a.z); r.L0 = __uint_as_float(a.w);
+  r.p0 = __uint_as_float(b.x); r.lnx0 = __uint_as_float(b.y);
+  r.lny0 = __uint_as_float(b.z); r.lns = __uint_as_float(b.w);
+  return r;
+}
+
+__device__ __forceinline__ float start_logit_keep(const float* st, float u,
+                                                  unsigned long long keep) {
+  float tau;
+  const int k = ara_start_piece(u, &tau);
+  const uint2* c2 = reinterpret_cast<const uint2*>(st + k * kStartCoefs);
+  const uint2 a = ld_keep_u2(c2, keep), b = ld_keep_u2(c2 + 1, keep), c = ld_keep_u2(c2 + 2, keep);
+  return ara_start_poly(make_float2(__uint_as_float(a.x), __uint_as_float(a.y)),
+                        make_float2(__uint_as_float(b.x), __uint_as_float(b.y)),
+                        make_float2(__uint_as_float(c.x), __uint_as_float(c.y)), tau);
+}
+
+// INV: 0 certified tables (Newton-Halley fallback for uncertified records), 1 Newton-Halley from
+// the start tables, records and start tables kept in L2 like the table pieces.
+template <int MW, bool CORR, int INV>
 __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_t i_rel0, int nt,
                                           int lane, BandWarpSmem& sm) {
   const L2Policies pol = L2Policies::make();
@@ -246,6 +272,20 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
         const SuDraw d =
             su_draw(u0, cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, sm.k[ev]) : 0.5f, cc);
         const float u = d.z;
+        if constexpr (INV == 1) {
+          const BetaRec rec = load_rec_keep(P.recs + pos, pol.keep);
+          if (!(rec.a > 0.f)) {
+            loss = rec.mx;  // sd = 0: the mean (primary uncertainty only)
+          } else {
+            const float sl = start_logit_keep(P.starts + (size_t)pos * kStartFloats, u, pol.keep);
+            const IbetaResult ib = ara_inv_beta<true>(rec, u, sl);
+            nc += ib.converged ? 0u : 1u;
+            n_inv += 1u;
+            n_it += (unsigned)ib.iters;
+            n_cf += (unsigned)ib.cf_terms;
+            loss = rec.mx * ib.x;
+          }
+        } else {
         float tau;
         const int kp = ara_table_piece_q(d.lower, d.q, &tau);
         const TablePiece pc = ara_load_piece<true>(P.tables + (size_t)pos * kTablePieces, kp);
@@ -261,6 +301,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
           n_it += (unsigned)ib.iters;
           n_cf += (unsigned)ib.cf_terms;
           loss = pc.mx * ib.x;
+        }
         }
       }
       // segmented inclusive scan: segments are the runs of equal ev, lanes seg_start .. lane
@@ -331,7 +372,7 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
   }
 }
 
-template <int MW, bool CORR>
+template <int MW, bool CORR, int INV>
 __device__ __forceinline__ void band_block(const TrialParams& P, int64_t local_block,
                                            BandWarpSmem* sms) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -340,19 +381,22 @@ __device__ __forceinline__ void band_block(const TrialParams& P, int64_t local_b
   const int64_t i_rel0 = tile * kTrialsPerBlock + (int64_t)wib * kT;
   const int64_t left = P.n - i_rel0;
   if (left <= 0) return;  // whole warp; no block-wide barrier in this kernel
-  band_warp<MW, CORR>(P, band, i_rel0, (int)min((int64_t)kT, left), lane, sms[wib]);
+  band_warp<MW, CORR, INV>(P, band, i_rel0, (int)min((int64_t)kT, left), lane, sms[wib]);
 }
 
-// Table inversion only: 64 registers for 32 warps per SM (16 blocks of 2), as the trial-major
-// path.
-template <int MW, bool CORR>
-__global__ void __launch_bounds__(kBW * 32, 32 / kBW) band_kernel(const __grid_constant__ TrialParams P) {
+// 64 registers for 32 warps per SM (16 blocks of 2), as the trial-major path.
+template <int INV>
+constexpr int kBandBlocksPerSM = 32 / kBW;
+
+template <int MW, bool CORR, int INV>
+__global__ void __launch_bounds__(kBW * 32, kBandBlocksPerSM<INV>)
+    band_kernel(const __grid_constant__ TrialParams P) {
   __shared__ BandWarpSmem s_w[kBW];
-  band_block<MW, CORR>(P, (int64_t)blockIdx.x, s_w);
+  band_block<MW, CORR, INV>(P, (int64_t)blockIdx.x, s_w);
 }
 
-template <int MW, bool CORR>
-__global__ void __launch_bounds__(kBW * 32, 32 / kBW)
+template <int MW, bool CORR, int INV>
+__global__ void __launch_bounds__(kBW * 32, kBandBlocksPerSM<INV>)
     band_batch_kernel(const TrialParams* __restrict__ items,
                       const int64_t* __restrict__ block_begin, int n_items) {
   __shared__ BandWarpSmem s_w[kBW];
@@ -362,7 +406,7 @@ __global__ void __launch_bounds__(kBW * 32, 32 / kBW)
     const int mid = (lo + hi + 1) >> 1;
     if (block_begin[mid] <= b) lo = mid; else hi = mid - 1;
   }
-  band_block<MW, CORR>(items[lo], b - block_begin[lo], s_w);
+  band_block<MW, CORR, INV>(items[lo], b - block_begin[lo], s_w);
 }
 
 // Year losses from the exact year sums: S = units x 2^e, then the aggregate terms.
@@ -390,7 +434,7 @@ __global__ void band_finalize_batch_kernel(const TrialParams* __restrict__ items
   finalize_one(items[lo], g - trial_begin[lo]);
 }
 
-template <int MW>
+template <int MW, int INV>
 cudaError_t launch_band_t(const TrialParams& p0, cudaStream_t st) {
   TrialParams p = p0;
   p.tiles = (int32_t)band_tiles(p.n);
@@ -405,9 +449,9 @@ cudaError_t launch_band_t(const TrialParams& p0, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   if (p.corr != nullptr)
-    band_kernel<MW, true><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
+    band_kernel<MW, true, INV><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
   else
-    band_kernel<MW, false><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
+    band_kernel<MW, false, INV><<<(unsigned)blocks, kBW * 32, 0, st>>>(p);
   count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -515,9 +559,15 @@ cudaError_t build_band_variant(const YetDev& y, int log2w, BandedYet& out, cudaS
   return cudaSuccess;
 }
 
-cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cudaStream_t st) {
+cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, int inversion,
+                        cudaStream_t st) {
   if (precision != 0) return cudaErrorInvalidValue;  // exact year sums only
-  return mask_words == 1 ? launch_band_t<1>(p, st) : launch_band_t<2>(p, st);
+  if (inversion == 1) {
+    if (p.starts == nullptr) return cudaErrorInvalidValue;
+    return mask_words == 1 ? launch_band_t<1, 1>(p, st) : launch_band_t<2, 1>(p, st);
+  }
+  if (inversion != 0) return cudaErrorInvalidValue;
+  return mask_words == 1 ? launch_band_t<1, 0>(p, st) : launch_band_t<2, 0>(p, st);
 }
 
 cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block_begin,
@@ -530,14 +580,14 @@ cudaError_t launch_band_batch(const TrialParams* d_items, const int64_t* d_block
   const dim3 grid((unsigned)total_blocks), block(kBW * 32);
   if (mask_words == 1) {
     if (corr)
-      band_batch_kernel<1, true><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+      band_batch_kernel<1, true, 0><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
     else
-      band_batch_kernel<1, false><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+      band_batch_kernel<1, false, 0><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
   } else {
     if (corr)
-      band_batch_kernel<2, true><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+      band_batch_kernel<2, true, 0><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
     else
-      band_batch_kernel<2, false><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
+      band_batch_kernel<2, false, 0><<<grid, block, 0, st>>>(d_items, d_block_begin, n_items);
   }
   count_launches(1);
   cudaError_t e = cudaGetLastError();

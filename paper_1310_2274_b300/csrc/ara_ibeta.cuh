@@ -108,42 +108,45 @@ struct CfState {
   float a, b, x, apb;
   float Am2, Am1, Bm2, Bm1;  // T_n = A_n / B_n; A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1
   float pA, pB;              // the estimate last tested, as the pair (A, B)
-  int n;                     // index of the next (odd) term
+  float m;                   // the next pair holds terms 2m+1 and 2m+2 (an exact small integer)
+  int n;                     // index of the next (odd) term, 2m+1
 };
 
 ARA_HD void ara_cf_init(CfState& c, float a, float b, float x) {
   c.a = a; c.b = b; c.x = x; c.apb = a + b;
   c.Am2 = 1.0f; c.Am1 = 1.0f; c.Bm2 = 0.0f; c.Bm1 = 1.0f;
   c.pA = 1.0f; c.pB = 1.0f;
+  c.m = 0.0f;
   c.n = 1;
 }
 
-// Terms n (odd) and n+1, then the exact power-of-two rescale.
-ARA_HD void ara_cf_pair(CfState& c, int n) {
-  // odd step n = 2m+1: alpha = -(a+m)(a+b+m) x  (alpha_1 = -(a+b) x: the a cancels)
-  const float m = 0.5f * (float)(n - 1);
-  const float al_odd = (n == 1) ? -c.apb * c.x : -(c.a + m) * (c.apb + m) * c.x;
-  const float be_odd = c.a + (float)n;
+// Terms 2m+1 and 2m+2, then the exact power-of-two rescale.
+ARA_HD void ara_cf_pair(CfState& c) {
+  // odd step 2m+1: alpha = -(a+m)(a+b+m) x  (alpha_1 = -(a+b) x: the a cancels)
+  const float m = c.m;
+  const float al_odd = (m == 0.0f) ? -c.apb * c.x : -(c.a + m) * (c.apb + m) * c.x;
+  const float be_odd = c.a + fmaf(2.0f, m, 1.0f);  // a + (2m+1), the integer exact
   float A = be_odd * c.Am1 + al_odd * c.Am2;
   float B = be_odd * c.Bm1 + al_odd * c.Bm2;
   c.Am2 = c.Am1; c.Bm2 = c.Bm1; c.Am1 = A; c.Bm1 = B;
-  // even step n+1 = 2(m+1): alpha = (m+1)(b-m-1) x
+  // even step 2(m+1): alpha = (m+1)(b-m-1) x
   const float m2 = m + 1.0f;
   const float al_even = m2 * (c.b - m2) * c.x;
-  const float be_even = c.a + (float)(n + 1);
+  const float be_even = c.a + 2.0f * m2;
   A = be_even * c.Am1 + al_even * c.Am2;
   B = be_even * c.Bm1 + al_even * c.Bm2;
   c.Am2 = c.Am1; c.Bm2 = c.Bm1; c.Am1 = A; c.Bm1 = B;
   // exact power-of-two rescale keeps the recurrence inside binary32 range
   const float sc = ara_pow2_scale_of(c.Am1);
   c.Am1 *= sc; c.Am2 *= sc; c.Bm1 *= sc; c.Bm2 *= sc;
+  c.m = m2;
 }
 
 // Four more terms and the convergence test: true once the fraction has converged or reached
 // kCfMaxTerms terms; c.n - 1 is then the number of terms summed.
 ARA_HD bool ara_cf_block(CfState& c, float tol) {
-  ara_cf_pair(c, c.n);
-  ara_cf_pair(c, c.n + 2);
+  ara_cf_pair(c);
+  ara_cf_pair(c);
   c.n += 4;
   const float cur = c.Bm1 * c.pA;
   if (fabsf(fmaf(-c.pB, c.Am1, cur)) <= tol * fabsf(cur)) return true;
@@ -197,12 +200,8 @@ struct HalleyState {
 
 // Start of the inversion.  Returns false when it is already done (r holds the result): the
 // start lies below e^-69, where the loss max_l x is far under every term of a year loss.
-ARA_HD bool ara_halley_setup(const BetaRec& rec, float u, float start_logit, HalleyState& h,
-                             IbetaResult& r) {
-  r.iters = 0;
-  r.cf_terms = 0;
-  r.converged = true;
-  r.t = 0.0f;
+// The fields of the state that depend on the record and u alone; returns p (u or 1 - u).
+ARA_HD float ara_halley_fields(const BetaRec& rec, float u, HalleyState& h) {
   h.flip = u > rec.p0;
   const float p = h.flip ? 1.0f - u : u;
   h.a = h.flip ? rec.b : rec.a;
@@ -213,31 +212,50 @@ ARA_HD bool ara_halley_setup(const BetaRec& rec, float u, float start_logit, Hal
   h.s = h.a + h.b;
   h.lna = h.lnx0 + rec.lns;
   h.lnp = logf(p);
+  h.thr = (h.a + 1.0f) / (h.s + 2.0f);
+  return p;
+}
+
+ARA_HD bool ara_halley_setup(const BetaRec& rec, float u, float start_logit, HalleyState& h,
+                             IbetaResult& r) {
+  r.iters = 0;
+  r.cf_terms = 0;
+  r.converged = true;
+  r.t = 0.0f;
+  const float p = ara_halley_fields(rec, u, h);
   const float a = h.a, b = h.b;
 
-  // small-x limit of DLMF 8.17.22 (K -> 1, y -> 1): ln p = L0 + a ln(x/x0) - b ln y0 - ln a
-  float t = h.lnx0 + (h.lnp + h.lna - h.L0 + b * h.lny0) / a;
-  if (a > 1.0f && b > 1.0f) {
-    // A&S 26.5.22: x ~ a / (a + b e^{2w}), with yp the upper-tail normal deviate of p.
-    const float yp = ara_norm_upper_quantile(fminf(p, 0.5f));
-    const float ypl = p > 0.5f ? -ara_norm_upper_quantile(1.0f - p) : yp;
-    const float lam = (ypl * ypl - 3.0f) / 6.0f;
-    const float hh = 2.0f / (1.0f / (2.0f * a - 1.0f) + 1.0f / (2.0f * b - 1.0f));
-    const float w = ypl * sqrtf(fmaxf(hh + lam, 0.0f)) / hh -
-                    (1.0f / (2.0f * b - 1.0f) - 1.0f / (2.0f * a - 1.0f)) *
-                        (lam + 5.0f / 6.0f - 2.0f / (3.0f * hh));
-    t = h.lna - logf(a + b * expf(2.0f * w));
-  }
+  // a start table's estimate of the log-odds L, as t = ln x = -ln(1 + e^-L) of the tail solved
+  // (a start only: the fast exponential and logarithm are ample).  An estimate below e^-69 ends
+  // the inversion only if the analytic start (exact in that limit) agrees: start tables are not
+  // certified, and on shapes far outside the ELT value law (a, b near 1e-6 under the sd clamp
+  // of §3.3) they can be far off.
+  float t = 0.0f;
   h.good = start_logit < 1e29f;  // false for NaN too
   if (h.good) {
-    // a table's estimate below e^-69 ends the inversion only if the analytic start (exact in
-    // that limit) agrees: start tables are not certified, and on shapes far outside the ELT
-    // value law (a, b near 1e-6 under the sd clamp of §3.3) they can be far off
-    const float ts = h.flip ? -log1pf(expf(start_logit)) : -log1pf(expf(-start_logit));
-    if (ts > -69.0f) t = ts; else h.good = false;
+#ifdef __CUDA_ARCH__
+    t = -__logf(1.0f + __expf(h.flip ? start_logit : -start_logit));
+#else
+    t = -std::log(1.0f + std::exp(h.flip ? start_logit : -start_logit));
+#endif
+    h.good = t > -69.0f;
+  }
+  if (!h.good) {
+    // small-x limit of DLMF 8.17.22 (K -> 1, y -> 1): ln p = L0 + a ln(x/x0) - b ln y0 - ln a
+    t = h.lnx0 + (h.lnp + h.lna - h.L0 + b * h.lny0) / a;
+    if (a > 1.0f && b > 1.0f) {
+      // A&S 26.5.22: x ~ a / (a + b e^{2w}), with yp the upper-tail normal deviate of p.
+      const float yp = ara_norm_upper_quantile(fminf(p, 0.5f));
+      const float ypl = p > 0.5f ? -ara_norm_upper_quantile(1.0f - p) : yp;
+      const float lam = (ypl * ypl - 3.0f) / 6.0f;
+      const float hh = 2.0f / (1.0f / (2.0f * a - 1.0f) + 1.0f / (2.0f * b - 1.0f));
+      const float w = ypl * sqrtf(fmaxf(hh + lam, 0.0f)) / hh -
+                      (1.0f / (2.0f * b - 1.0f) - 1.0f / (2.0f * a - 1.0f)) *
+                          (lam + 5.0f / 6.0f - 2.0f / (3.0f * hh));
+      t = h.lna - logf(a + b * expf(2.0f * w));
+    }
   }
   t = fminf(t, h.lnx0);  // the root is below the mean
-  h.thr = (a + 1.0f) / (h.s + 2.0f);
   h.t = t;
   if (!(t > -69.0f)) {  // below e^-69 ~ 1e-30
     r.x = h.flip ? 1.0f : 0.0f;
@@ -277,17 +295,27 @@ ARA_HD HalleyPre ara_halley_pre(const HalleyState& h) {
 
 // The part after it: G = ln I_x - ln p, G' and Halley's step in t.  Returns true when the
 // iteration `it` (0-based) ends the inversion.
+// The residual G is the function value and keeps IEEE arithmetic; G' and Halley's correction
+// only shape the step toward the root, so their quotients take the fast division (ara_fdiv).
+ARA_HD float ara_fdiv(float n, float d) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(n, d);
+#else
+  return n / d;
+#endif
+}
+
 ARA_HD bool ara_halley_post(HalleyState& h, const HalleyPre& q, float K, int it) {
   const float a = h.a, b = h.b, x = h.x, y = q.y;
   float G, dG;
   if (q.lower) {
     G = q.E + logf(K) - h.lna - h.lnp;
-    dG = a / (y * K);
+    dG = ara_fdiv(a, y * K);
   } else {
     const float P = expf(q.E);
     const float J = P * K / b;  // I_{1-x}(b,a)
     G = log1pf(-J) - h.lnp;
-    dG = P / (y * (1.0f - J));
+    dG = ara_fdiv(P, y * (1.0f - J));
   }
   // Where I_x is nearly flat in t (G' below 1e-3: a shape parameter far below the paper's
   // value law, e.g. the sd clamp of §3.3, which gives a, b near 1e-6) the binary32 residual's
@@ -300,10 +328,10 @@ ARA_HD bool ara_halley_post(HalleyState& h, const HalleyPre& q, float K, int it)
   // G' = x f(x) / I_x gives G'' = G' (a - (b-1) x/y - G'); the step converges cubically, so
   // a step of 3e-4 leaves an error near 1e-11 in t.  Far from the root (|dn c| large) the
   // plain Newton step is taken.
-  const float dn = G / dG;
-  const float c = 0.5f * (a - (b - 1.0f) * x / y - dG);
+  const float dn = ara_fdiv(G, dG);
+  const float c = 0.5f * (a - (b - 1.0f) * ara_fdiv(x, y) - dG);
   const float den = 1.0f - dn * c;
-  float tn = h.t - ((den > 0.5f && den < 2.0f) ? dn / den : dn);
+  float tn = h.t - ((den > 0.5f && den < 2.0f) ? ara_fdiv(dn, den) : dn);
   if (!(tn < 0.0f)) tn = 0.5f * h.t;  // a step past x = 1 is halved toward it
   const float step = fabsf(tn - h.t);
   h.t = tn;
@@ -420,8 +448,8 @@ constexpr int kStartCoefs = 6;                      // quintic Hermite: L, L', L
 constexpr int kStartFloats = kStartPieces * kStartCoefs;
 constexpr float kStartInvH = kTableInvH * 0.25f;  // 1 / (4 kTableH)
 
-// Estimated log-odds of the quantile of u from a record's start table (NaN where none).
-ARA_HD float ara_start_logit(const float* st, float u) {
+// Piece and local coordinate of u in a start table.
+ARA_HD int ara_start_piece(float u, float* tau) {
   const bool lower = u < 0.5f;
   const float q = lower ? u : 1.0f - u;
 #ifdef __CUDA_ARCH__
@@ -432,15 +460,28 @@ ARA_HD float ara_start_logit(const float* st, float u) {
   const float z = lower ? t - kTableTm : kTableTm - t;
   const float pos = fminf(fmaxf((z + kTableZ) * kStartInvH, 0.0f), (float)kStartPieces);
   const int k = pos < (float)(kStartPieces - 1) ? (int)pos : kStartPieces - 1;
-  const float tau = pos - (float)k;
+  *tau = pos - (float)k;
+  return k;
+}
+
+// The piece's quintic at tau, by Horner with explicit FMAs: every caller, whatever load brought
+// the coefficients, gets the same bits.
+ARA_HD float ara_start_poly(float2 c01, float2 c23, float2 c45, float tau) {
+  return fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, fmaf(tau, c45.y, c45.x), c23.y), c23.x), c01.y),
+              c01.x);
+}
+
+// Estimated log-odds of the quantile of u from a record's start table (NaN where none).
+ARA_HD float ara_start_logit(const float* st, float u) {
+  float tau;
+  const int k = ara_start_piece(u, &tau);
   const float2* c2 = reinterpret_cast<const float2*>(st + k * kStartCoefs);
 #ifdef __CUDA_ARCH__
   const float2 c01 = __ldg(c2), c23 = __ldg(c2 + 1), c45 = __ldg(c2 + 2);
 #else
   const float2 c01 = c2[0], c23 = c2[1], c45 = c2[2];
 #endif
-  return c01.x +
-         tau * (c01.y + tau * (c23.x + tau * (c23.y + tau * (c45.x + tau * c45.y))));
+  return ara_start_poly(c01, c23, c45, tau);
 }
 static_assert(sizeof(TablePiece) == 32, "a table piece is one 32-byte sector");
 

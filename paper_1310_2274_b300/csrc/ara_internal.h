@@ -213,7 +213,9 @@ int year_grid_exponent(double o_max, int64_t max_len);
 // event loss l exceeds ev_bound (binary32 rounding of the sums and of OccR included)
 double occurrence_bound(float ev_bound, double occ_ret, double occ_lim);
 // band kernel + per-trial finalisation over p.t0 .. p.t0 + p.n; p.ysum holds n words (zeroed here)
-cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, cudaStream_t st);
+// inversion: 0 certified tables, 1 Newton-Halley from the layer's start tables (p.starts set)
+cudaError_t launch_band(const TrialParams& p, int mask_words, int precision, int inversion,
+                        cudaStream_t st);
 // many items in one launch (serving slices, portfolio layers), all with mask_words-word lookup
 // entries: items with their band fields set (tiles = band_tiles(n), ysum zeroed); block_begin[i]
 // = first block of item i (n_bands * tiles blocks each), trial_begin[i] = its first trial

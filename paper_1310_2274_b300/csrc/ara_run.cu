@@ -40,6 +40,14 @@ bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
          ctx->cfg.precision == ARA_ACC_FP64;
 }
 
+// A single-layer run takes the band schedule for the Newton-Halley inversion too, where the YET's
+// band-major copy exists already (made for the table inversion: a Newton pass alone gains ~1 ms
+// from it, far less than the copy costs).
+static bool run_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
+  return layer_inversion(ctx, L) <= 1 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
+         ctx->cfg.precision == ARA_ACC_FP64;
+}
+
 int layer_inversion(const ara_ctx* ctx, const LayerDev& L) {
   const int m = inversion_mode(ctx);
   return (m == 0 && L.tables == nullptr) ? 1 : m;
@@ -522,13 +530,14 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
     if (!Y.ts_checked && Y.n_occ > 0)
       ts_check = std::thread(
           [&]() { ts_flags = validate_timestamps_host(Y.h_off.data(), Y.h_ts, Y.n_trials); });
-  } else if (!per_occ && uses_band_schedule(ctx, ctx->layers[layer])) {
+  } else if (!per_occ && run_band_schedule(ctx, ctx->layers[layer])) {
     // year sums (8 B per trial), then the OEP maxima (4 B per trial) in the same scratch
     s = ensure_ysum(ctx, oep ? n + (n + 1) / 2 : n);
     if (s != ARA_OK) return s;
     p.ysum = ctx->d_ysum;
     p.omax = oep ? reinterpret_cast<unsigned int*>(ctx->d_ysum + n) : nullptr;
-    CUDA_TRY(ctx, launch_band(p, ctx->layers[layer].mask_words, ctx->cfg.precision, st));
+    CUDA_TRY(ctx, launch_band(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
+                              layer_inversion(ctx, ctx->layers[layer]), st));
   } else {
     CUDA_TRY(ctx, launch_trial(p, ctx->layers[layer].mask_words, ctx->cfg.precision,
                                layer_inversion(ctx, ctx->layers[layer]), false, st));
@@ -659,7 +668,7 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
     if (own_warps >= big_warps) {
       if (band) {
         p.ysum = ctx->d_ysum + (int64_t)band_row++ * n;
-        CUDA_TRY(ctx, launch_band(p, L.mask_words, ctx->cfg.precision, st));
+        CUDA_TRY(ctx, launch_band(p, L.mask_words, ctx->cfg.precision, 0, st));
       } else {
         CUDA_TRY(ctx, launch_trial(p, L.mask_words, ctx->cfg.precision,
                                    layer_inversion(ctx, L), false, st));
@@ -769,7 +778,7 @@ ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
     return fail(ctx, ARA_ERR_INVALID_ARG, "tracing needs a device-resident YET");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const YetDev& Y = ctx->yets[yet];
-  const LayerDev& L = ctx->layers[layer];
+  LayerDev& L = ctx->layers[layer];
   const int64_t cap = std::max<int64_t>(1, Y.max_len * L.n_slots);
   const int64_t total = n * cap;
   if (total > ((int64_t)1 << 27)) return fail(ctx, ARA_ERR_INVALID_ARG, "trace too large");
@@ -777,6 +786,10 @@ ara_status ara_trace_hits(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
     *n_hits = 0;
     return ARA_OK;
   }
+  // the layer as a run of these trials would see it (tables or start tables), so that the trace
+  // reproduces the run's year losses bit for bit
+  s = prepare_layer_for_run(ctx, L, n, false);
+  if (s != ARA_OK) return s;
   int32_t *d_k = nullptr, *d_j = nullptr, *d_rec = nullptr, *d_cnt = nullptr;
   float *d_u = nullptr, *d_x = nullptr, *d_loss = nullptr;
   double* d_ylt = nullptr;

@@ -106,6 +106,11 @@ struct ara_server {
   SortScratch sort;  // the server's own ordering buffers
   int64_t* d_k = nullptr;
   double *d_pml = nullptr, *d_tvar = nullptr;
+  // the context's stream and inversion options before the server took it over (restored when
+  // the server is destroyed)
+  cudaStream_t saved_stream = nullptr;
+  int32_t saved_surrogate = 0, saved_inversion = 0;
+  bool saved = false;
 };
 
 namespace {
@@ -375,7 +380,7 @@ bool issue(ara_server* s) {
     if (own_warps >= big_warps) {
       if (r.band) {
         p.ysum = r.d_ysum + r.next;
-        if (e == cudaSuccess) e = ara::launch_band(p, 2, s->ctx->cfg.precision, s->stream);
+        if (e == cudaSuccess) e = ara::launch_band(p, 2, s->ctx->cfg.precision, 0, s->stream);
       } else if (e == cudaSuccess) {
         e = ara::launch_trial(p, 2, s->ctx->cfg.precision, inversion_mode(s->ctx), false,
                               s->stream);
@@ -499,6 +504,10 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
   s->budget = cfg->hbm_budget > 0 ? cfg->hbm_budget
                                   : std::max<int64_t>(0, (int64_t)free_b - ((int64_t)4 << 30));
   // the server owns the context's device work while it runs
+  s->saved_stream = ctx->stream;
+  s->saved_surrogate = ctx->cfg.use_surrogate;
+  s->saved_inversion = ctx->inversion;
+  s->saved = true;
   ara_set_stream(ctx, s->stream);
   if (cfg->use_surrogate) {
     if (ara_set_option(ctx, ARA_OPT_SURROGATE, 1) != ARA_OK) {
@@ -694,7 +703,15 @@ void ara_server_destroy(ara_server* s) {
   if (s->d_k) cudaFree(s->d_k);
   if (s->d_pml) cudaFree(s->d_pml);
   if (s->d_tvar) cudaFree(s->d_tvar);
-  if (s->ctx) ara_set_stream(s->ctx, nullptr);
+  if (s->ctx) {
+    if (s->saved) {  // the context as it was before the server
+      ara_set_stream(s->ctx, s->saved_stream == s->ctx->own_stream ? nullptr : s->saved_stream);
+      s->ctx->cfg.use_surrogate = s->saved_surrogate;
+      s->ctx->inversion = s->saved_inversion;
+    } else {
+      ara_set_stream(s->ctx, nullptr);
+    }
+  }
   for (cudaStream_t st : {s->stream, s->fin_stream, s->build_stream}) {
     if (!st) continue;
     cudaStreamSynchronize(st);
