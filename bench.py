@@ -384,8 +384,38 @@ def run_ours(a):
     run_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in run_ev)
     value = world * evals / (step_ms * 1e-3)
     d = {k: (s1[k] - s0[k]) / a.steps for k in s0}
-    ylt_cold = ylt.cpu().numpy().copy()
+    ylt_cold = ylt.cpu().numpy().copy()  # the last timed step's YLT (its ELT handles: cold_handles)
     pml_cold, tvar_cold = [float(v) for v in pml], [float(v) for v in tvar]
+
+    # where a step's time goes, by API call (host clock, each call followed by a synchronise;
+    # outside the timed region)
+    def phases():
+        out = {}
+
+        def tick(name, t0):
+            torch.cuda.synchronize(dev)
+            out[name] = out.get(name, 0.0) + (time.perf_counter() - t0) * 1e3
+            return time.perf_counter()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        yet_p = ctx.create_yet(off_d, ids_d, ts_d, 2_000_000)
+        t = tick("create_yet", t)
+        elts_p = [ctx.add_elt(yet_p, *v) for v in elts_d]
+        t = tick("add_elt_x16", t)
+        layer_p = ctx.add_layer(elts_p, terms.occ_ret, terms.occ_lim, terms.agg_ret,
+                                terms.agg_lim)
+        t = tick("add_layer", t)
+        ctx.run(yet_p, layer_p, 0, n, out=ylt, stream=stream)
+        t = tick("run", t)
+        risk(ylt)
+        t = tick("risk_measures", t)
+        ctx.free_layer(layer_p)
+        for e in elts_p:
+            ctx.free_elt(e)
+        ctx.free_yet(yet_p)
+        tick("frees", t)
+        return out
+    step_phases = phases()
 
     # ---- a persistent staging of the same data for the other legs -----------------------------
     yet = ctx.create_yet(off_d, ids_d, ts_d, 2_000_000)
@@ -616,7 +646,8 @@ def run_ours(a):
                          "(device arrays: records, start tables) + ara_add_layer + ara_run + "
                          "ara_risk_measures + frees; tables on demand (this single pass runs "
                          "Newton-Halley)",
-                 "run_ms": run_ms, "per_launch": {k: d[k] for k in ("hits", "inversions",
+                 "run_ms": run_ms, "phases_ms": step_phases,
+                 "per_launch": {k: d[k] for k in ("hits", "inversions",
                                                                     "newton", "cf_terms")},
                  "risk_measures": {"rps": rps, "pml": pml_cold, "tvar": tvar_cold}},
         "repricing": repricing,

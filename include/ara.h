@@ -130,9 +130,11 @@ ARA_API ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value);
  * nondecreasing (an empty trial is allowed).  Event ids must lie in [0, catalog_size).
  * Rejected with ARA_ERR_INVALID_ARG: n_trials < 0, catalog_size <= 0, bad offsets, an id out of
  * range, a timestamp below its predecessor in the same trial, a NaN timestamp.
- * Device copy: int32 ids, trial-major, 4 bytes per occurrence.  Runs never read timestamps: host
- * ones are checked on host threads while the ids are copied and are not stored; device ones are
- * copied and checked on the device (4 more bytes per occurrence). */
+ * Device copy: int32 ids, trial-major, 4 bytes per occurrence.  Runs never read timestamps, so
+ * they are checked and not stored: host ones on host threads while the ids are copied, device
+ * ones where they are, on the device.  The context's device memory (YETs, ELTs, layers) comes
+ * from a memory pool of its own that keeps up to 32 GiB of freed memory for later staging (it is
+ * handed back when an allocation would otherwise fail, and at ara_destroy). */
 ARA_API ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_offsets,
                                   const int32_t* event_ids, const float* timestamps,
                                   int32_t catalog_size, int32_t* yet_out);

@@ -22,17 +22,17 @@
 
 using namespace ara;
 
-void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st) {
-  mem_free(l.evt, ordered, st);
-  mem_free(l.tables, ordered, st);
-  mem_free(l.packed, ordered, st);
-  mem_free(l.packed_rec, ordered, st);
-  mem_free(l.corr, ordered, st);
-  mem_free(l.starts, ordered, st);
+void free_layer_on(ara_ctx* c, LayerDev& l, bool ordered, cudaStream_t st) {
+  mem_free(c, l.evt, ordered, st);
+  mem_free(c, l.tables, ordered, st);
+  mem_free(c, l.packed, ordered, st);
+  mem_free(c, l.packed_rec, ordered, st);
+  mem_free(c, l.corr, ordered, st);
+  mem_free(c, l.starts, ordered, st);
   l = LayerDev();
 }
 
-void free_layer(LayerDev& l) { free_layer_on(l, false, nullptr); }
+void free_layer(ara_ctx* c, LayerDev& l) { free_layer_on(c, l, false, nullptr); }
 
 
 extern "C" {
@@ -84,6 +84,20 @@ ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
     ara_destroy(ctx);
     return ARA_ERR_CUDA;
   }
+  {  // the pool of object memory (obj_alloc), keeping up to kPoolKeepBytes of freed memory
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    uint64_t keep = kPoolKeepBytes;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      ara_destroy(ctx);
+      return ARA_ERR_CUDA;
+    }
+  }
   *out = ctx;
   return ARA_OK;
 }
@@ -91,10 +105,16 @@ ara_status ara_create(const ara_config* cfg, ara_ctx** out) {
 void ara_destroy(ara_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (auto& y : ctx->yets) free_yet(y);
-  for (auto& e : ctx->elts) free_elt(e);
-  for (auto& l : ctx->layers) free_layer(l);
+  cudaDeviceSynchronize();
+  if (ctx->own_stream) ctx->stream = ctx->own_stream;  // a caller's stream may be gone by now
+  if (ctx->pool) {
+    for (auto& y : ctx->yets) free_yet(ctx, y);
+    for (auto& e : ctx->elts) free_elt(ctx, e);
+    for (auto& l : ctx->layers) free_layer(ctx, l);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaMemPoolDestroy(ctx->pool);
+    ctx->pool = nullptr;
+  }
   for (int b = 0; b < 2; ++b) {
     dev_free(ctx->sort.keys[b]);
     dev_free(ctx->sort.vals[b]);
@@ -219,15 +239,14 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   y.n_occ = n_occ;
   y.catalog = catalog_size;
   y.max_len = max_len;
-  // the runs never read timestamps: host ones are checked on host threads while the ids cross
-  // to the device, and only device ones are staged (and checked by the kernel)
+  // the runs never read timestamps, so they are checked and not kept: host ones on host threads
+  // while the ids cross to the device, device ones where they are, by the validation kernel
   const bool ts_on_host = n_occ > 0 && !is_device_ptr(timestamps);
   cudaError_t e;
-  if ((e = dev_alloc(&y.ids, n_occ)) != cudaSuccess ||
-      (!ts_on_host && (e = dev_alloc(&y.ts, n_occ)) != cudaSuccess) ||
-      (e = dev_alloc(&y.offsets, n_trials + 1)) != cudaSuccess) {
+  if ((e = obj_alloc(ctx, &y.ids, n_occ)) != cudaSuccess ||
+      (e = obj_alloc(ctx, &y.offsets, n_trials + 1)) != cudaSuccess) {
     cudaGetLastError();
-    free_yet(y);
+    free_yet(ctx, y);
     return fail(ctx, ARA_ERR_OOM, "YET of %lld occurrences: %s", (long long)n_occ,
                 cudaGetErrorString(e));
   }
@@ -236,15 +255,18 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   if (ts_on_host)
     ts_check = std::thread(
         [&]() { host_flags = validate_timestamps_host(off.data(), timestamps, n_trials); });
+  // device offsets are copied where they are (the host copy above served the checks)
+  const int64_t* off_src = is_device_ptr(trial_offsets) ? trial_offsets : off.data();
   if ((e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess ||
-      (!ts_on_host && (e = copy_in(y.ts, timestamps, n_occ, ctx->stream)) != cudaSuccess) ||
-      (e = copy_in(y.offsets, off.data(), n_trials + 1, ctx->stream)) != cudaSuccess ||
+      (e = copy_in(y.offsets, off_src, n_trials + 1, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
-      (e = launch_validate_yet(y, ctx->d_flags, ctx->stream)) != cudaSuccess) {
+      (e = launch_validate_yet_range(y.ids, ts_on_host ? nullptr : timestamps, 0, y.offsets, 0,
+                                     n_trials, catalog_size, ctx->d_flags, ctx->stream)) !=
+          cudaSuccess) {
     cudaGetLastError();
     if (ts_check.joinable()) ts_check.join();
     cudaStreamSynchronize(ctx->stream);
-    free_yet(y);
+    free_yet(ctx, y);
     return fail(ctx, ARA_ERR_CUDA, "staging YET: %s", cudaGetErrorString(e));
   }
   unsigned int flags = 0;
@@ -253,12 +275,12 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   if (ts_check.joinable()) ts_check.join();
   if (e != cudaSuccess) {
     cudaGetLastError();
-    free_yet(y);
+    free_yet(ctx, y);
     return fail(ctx, ARA_ERR_CUDA, "staging YET: %s", cudaGetErrorString(e));
   }
   flags |= host_flags;
   if (flags) {
-    free_yet(y);
+    free_yet(ctx, y);
     return fail(ctx, ARA_ERR_INVALID_ARG, "YET rejected:%s%s%s",
                 (flags & 1) ? " event id outside [0, catalog_size)" : "",
                 (flags & 2) ? " timestamps decrease within a trial" : "",
@@ -305,11 +327,11 @@ ara_status ara_create_yet_host(ara_ctx* ctx, int64_t n_trials, const int64_t* tr
   y.h_ids = event_ids;
   y.h_ts = timestamps;
   cudaError_t e;
-  if ((e = dev_alloc(&y.offsets, n_trials + 1)) != cudaSuccess ||
+  if ((e = obj_alloc(ctx, &y.offsets, n_trials + 1)) != cudaSuccess ||
       (e = copy_in(y.offsets, y.h_off.data(), n_trials + 1, ctx->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
     cudaGetLastError();
-    free_yet(y);
+    free_yet(ctx, y);
     return fail(ctx, ARA_ERR_CUDA, "staging YET offsets: %s", cudaGetErrorString(e));
   }
   y.live = true;
@@ -327,14 +349,14 @@ ara_status ara_free_yet(ara_ctx* ctx, int32_t yet) {
   for (auto& e : ctx->elts)
     if (e.live && e.yet == yet) return fail(ctx, ARA_ERR_INVALID_ARG, "YET still has ELTs");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaDeviceSynchronize());  // no stream may still read the YET
   if (ctx->yets[yet].host && ctx->copy_stream) {
     // copies of its ids (ahead of a run, or of a run that stopped on an error) end before the
     // caller may release the arrays
     if (ctx->pf_yet == yet) ctx->pf_yet = -1;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->copy_stream));
   }
-  free_yet(ctx->yets[yet]);
+  free_yet(ctx, ctx->yets[yet]);
   return ARA_OK;
 }
 
@@ -370,15 +392,16 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
                          scratch_bytes<unsigned int>(y.catalog) +
                          scratch_bytes<unsigned long long>(1) +
                          (defer ? 0 : scratch_bytes<double2>(n));
-  if ((err = dev_alloc(&e.ids, n)) != cudaSuccess || (err = dev_alloc(&e.recs, n)) != cudaSuccess ||
-      (err = dev_alloc(&e.starts, n * kStartFloats)) != cudaSuccess ||
-      (!defer && (err = dev_alloc(&e.tables, n * kTablePieces)) != cudaSuccess) ||
-      (defer && (err = dev_alloc(&e.ab64, n)) != cudaSuccess) ||
-      (sd_corr && (err = dev_alloc(&e.corr, n)) != cudaSuccess) ||
+  if ((err = obj_alloc(ctx, &e.ids, n)) != cudaSuccess ||
+      (err = obj_alloc(ctx, &e.recs, n)) != cudaSuccess ||
+      (err = obj_alloc(ctx, &e.starts, n * kStartFloats)) != cudaSuccess ||
+      (!defer && (err = obj_alloc(ctx, &e.tables, n * kTablePieces)) != cudaSuccess) ||
+      (defer && (err = obj_alloc(ctx, &e.ab64, n)) != cudaSuccess) ||
+      (sd_corr && (err = obj_alloc(ctx, &e.corr, n)) != cudaSuccess) ||
       (err = ensure_scratch(ctx, scratch)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    free_elt(e);
+    free_elt(ctx, e);
     return fail(ctx, ARA_ERR_OOM, "ELT of %lld records: %s", (long long)n, cudaGetErrorString(err));
   }
   ScratchCarver sc{ctx->d_scratch};
@@ -422,12 +445,12 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
       (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    free_elt(e);
+    free_elt(ctx, e);
     return fail(ctx, ARA_ERR_CUDA, "staging ELT: %s", cudaGetErrorString(err));
   }
   cleanup();
   if (flags) {
-    free_elt(e);
+    free_elt(ctx, e);
     return fail(ctx, ARA_ERR_INVALID_ARG, "ELT rejected:%s%s%s%s",
                 (flags & 8) ? " event id outside the catalogue" : "",
                 (flags & 16) ? " mean <= 0, an sd < 0 or non-finite value" : "",
@@ -452,8 +475,8 @@ ara_status ara_free_elt(ara_ctx* ctx, int32_t elt) {
   if (elt < 0 || elt >= (int32_t)ctx->elts.size() || !ctx->elts[elt].live)
     return fail(ctx, ARA_ERR_BAD_HANDLE, "bad ELT handle %d", elt);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  free_elt(ctx->elts[elt]);
+  CUDA_TRY(ctx, cudaDeviceSynchronize());  // no stream may still read the ELT
+  free_elt(ctx, ctx->elts[elt]);
   return ARA_OK;
 }
 
@@ -509,18 +532,18 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
       cudaStreamSynchronize(st);
       return;
     }
-    mem_free(d_mask, ordered, st);
-    mem_free(d_cnt, ordered, st);
-    mem_free(d_base, ordered, st);
-    mem_free(d_tmp, ordered, st);
-    mem_free(d_src, ordered, st);
+    mem_free(ctx, d_mask, ordered, st);
+    mem_free(ctx, d_cnt, ordered, st);
+    mem_free(ctx, d_base, ordered, st);
+    mem_free(ctx, d_tmp, ordered, st);
+    mem_free(ctx, d_src, ordered, st);
   };
   const int64_t evt_words = C * (MW == 1 ? 2 : 4);
   if (ordered) {
-    err = mem_alloc(&d_mask, C * MW, ordered, st);
-    if (err == cudaSuccess) err = mem_alloc(&d_cnt, C, ordered, st);
-    if (err == cudaSuccess) err = mem_alloc(&d_base, C, ordered, st);
-    if (err == cudaSuccess) err = mem_alloc(&d_tmp, tmp_words, ordered, st);
+    err = mem_alloc(ctx, &d_mask, C * MW, ordered, st);
+    if (err == cudaSuccess) err = mem_alloc(ctx, &d_cnt, C, ordered, st);
+    if (err == cudaSuccess) err = mem_alloc(ctx, &d_base, C, ordered, st);
+    if (err == cudaSuccess) err = mem_alloc(ctx, &d_tmp, tmp_words, ordered, st);
   } else {
     int64_t records = 0;
     for (int j = 0; j < n_elts; ++j) records += ctx->elts[elts[j]].n;
@@ -536,10 +559,10 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
       d_src = sc.take<const TablePiece*>(records);
     }
   }
-  if (err != cudaSuccess || (err = mem_alloc(&L.evt, evt_words, ordered, st)) != cudaSuccess) {
+  if (err != cudaSuccess || (err = mem_alloc(ctx, &L.evt, evt_words, ordered, st)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    free_layer_on(L, ordered, st);
+    free_layer_on(ctx, L, ordered, st);
     return fail(ctx, ARA_ERR_OOM, "layer index: %s", cudaGetErrorString(err));
   }
   uint32_t last[2] = {0, 0};
@@ -557,7 +580,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   if (err != cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    free_layer_on(L, ordered, st);
+    free_layer_on(ctx, L, ordered, st);
     return fail(ctx, ARA_ERR_CUDA, "layer index: %s", cudaGetErrorString(err));
   }
   L.n_packed = (int64_t)last[0] + (int64_t)last[1];
@@ -569,17 +592,17 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     all_tables = all_tables && ctx->elts[elts[j]].tables != nullptr;
     all_starts = all_starts && ctx->elts[elts[j]].starts != nullptr;
   }
-  if ((err = mem_alloc(&L.packed, L.n_packed, ordered, st)) != cudaSuccess ||
-      (err = mem_alloc(&L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
-      (all_tables && (err = mem_alloc(&L.tables, L.n_packed * kTablePieces, ordered, st)) !=
+  if ((err = mem_alloc(ctx, &L.packed, L.n_packed, ordered, st)) != cudaSuccess ||
+      (err = mem_alloc(ctx, &L.packed_rec, L.n_packed, ordered, st)) != cudaSuccess ||
+      (all_tables && (err = mem_alloc(ctx, &L.tables, L.n_packed * kTablePieces, ordered, st)) !=
                          cudaSuccess) ||
-      (ordered && (err = mem_alloc(&d_src, L.n_packed, ordered, st)) != cudaSuccess) ||
-      (has_corr && (err = mem_alloc(&L.corr, L.n_packed, ordered, st)) != cudaSuccess) ||
+      (ordered && (err = mem_alloc(ctx, &d_src, L.n_packed, ordered, st)) != cudaSuccess) ||
+      (has_corr && (err = mem_alloc(ctx, &L.corr, L.n_packed, ordered, st)) != cudaSuccess) ||
       (all_starts &&
-       (err = mem_alloc(&L.starts, L.n_packed * kStartFloats, ordered, st)) != cudaSuccess)) {
+       (err = mem_alloc(ctx, &L.starts, L.n_packed * kStartFloats, ordered, st)) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
-    free_layer_on(L, ordered, st);
+    free_layer_on(ctx, L, ordered, st);
     return fail(ctx, ARA_ERR_OOM, "layer records and tables: %s", cudaGetErrorString(err));
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
@@ -595,7 +618,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   cleanup();
   if (err != cudaSuccess) {
     cudaGetLastError();
-    free_layer_on(L, ordered, st);
+    free_layer_on(ctx, L, ordered, st);
     return fail(ctx, ARA_ERR_CUDA, "layer records: %s", cudaGetErrorString(err));
   }
   memcpy(&L.ev_bound, &ev_bits, sizeof(float));
@@ -641,8 +664,8 @@ ara_status ara_free_layer(ara_ctx* ctx, int32_t layer) {
   if (layer < 0 || layer >= (int32_t)ctx->layers.size() || !ctx->layers[layer].live)
     return fail(ctx, ARA_ERR_BAD_HANDLE, "bad layer handle %d", layer);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  free_layer(ctx->layers[layer]);
+  CUDA_TRY(ctx, cudaDeviceSynchronize());  // no stream may still read the layer
+  free_layer(ctx, ctx->layers[layer]);
   return ARA_OK;
 }
 

@@ -71,20 +71,22 @@ struct ara_ctx {
   size_t scratch_cap = 0;
   int32_t band_log2w = 0;                // band width exponent for new layers (0: automatic)
   void* d_misc = nullptr;  // small staging area for tail sums
+  // the device memory of YETs, ELTs and layers (see obj_alloc)
+  cudaMemPool_t pool = nullptr;
 };
 
 // Internal entry points shared between the API and the serving loop.
 // Builds a layer into *out (not registered in ctx->layers) with its device work on st; with
 // may_build_band false an absent band-major YET copy leaves the layer trial-major; with ordered
-// true its memory is stream-ordered on st (free it with free_layer_on(..., true, stream)); with
+// true its memory is stream-ordered on st (free it with free_layer_on(ctx, ..., true, stream)); with
 // starts true the ELTs' start tables are packed too (runs that invert by Newton-Halley steps;
 // otherwise the first such run packs them).
 ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
                            double occ_lim, double agg_ret, double agg_lim, bool wide,
                            cudaStream_t st, bool may_build_band, bool ordered, LayerDev* out,
                            bool starts = false);
-void free_layer(LayerDev& l);
-void free_layer_on(LayerDev& l, bool ordered, cudaStream_t st);
+void free_layer(ara_ctx* ctx, LayerDev& l);
+void free_layer_on(ara_ctx* ctx, LayerDev& l, bool ordered, cudaStream_t st);
 ara_status ara_add_layer_impl(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, double occ_ret,
                               double occ_lim, double agg_ret, double agg_lim, bool wide,
                               int32_t* layer_out);

@@ -70,29 +70,57 @@ inline void dev_free(void* p) {
   if (p) cudaFree(p);
 }
 
-// Allocation either plain (cudaMalloc/cudaFree, which waits for the device) or stream-ordered
-// on st (cudaMallocAsync/cudaFreeAsync from the device's memory pool, which never blocks the host:
-// the serving loop builds and frees layers while launches run).
+// Object memory: the device buffers of YETs, ELTs and layers come from the context's own
+// memory pool, stream-ordered on its stream, and go back to it when freed.  The pool keeps up to
+// kPoolKeepBytes of freed memory for the next staging: an analysis stages and frees ~10 GB in
+// ~80 buffers, and a cudaMalloc / cudaFree pair of a multi-GB buffer costs milliseconds (cudaFree
+// also waits for the whole device).  A buffer is freed only once no stream can still read it:
+// the ara_free_* calls synchronise the device first, staging's own error paths free after
+// synchronising the context's stream, the only one their work was on.
+constexpr uint64_t kPoolKeepBytes = (uint64_t)32 << 30;
+
 template <class T>
-cudaError_t mem_alloc(T** p, int64_t n, bool ordered, cudaStream_t st) {
+cudaError_t obj_alloc(ara_ctx* c, T** p, int64_t n) {
   *p = nullptr;
   if (n <= 0) n = 1;
   const size_t bytes = sizeof(T) * (size_t)n;
-  return ordered ? cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st)
-                 : cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, c->pool, c->stream);
+  if (e == cudaErrorMemoryAllocation) {  // hand back what the pool keeps, then try again
+    cudaGetLastError();
+    cudaStreamSynchronize(c->stream);
+    cudaMemPoolTrimTo(c->pool, 0);
+    e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, c->pool, c->stream);
+  }
+  return e;
 }
 
-inline void mem_free(const void* p, bool ordered, cudaStream_t st) {
+inline void obj_free(ara_ctx* c, const void* p) {
+  if (p) cudaFreeAsync(const_cast<void*>(p), c->stream);
+}
+
+// Layer memory: object memory, or stream-ordered on st from the device's default pool (ordered:
+// the serving loop builds and frees request layers while launches run, and never blocks).
+template <class T>
+cudaError_t mem_alloc(ara_ctx* c, T** p, int64_t n, bool ordered, cudaStream_t st) {
+  if (!ordered) return obj_alloc(c, p, n);
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * (size_t)n, st);
+}
+
+inline void mem_free(ara_ctx* c, const void* p, bool ordered, cudaStream_t st) {
   if (!p) return;
   if (ordered) cudaFreeAsync(const_cast<void*>(p), st);
-  else cudaFree(const_cast<void*>(p));
+  else obj_free(c, p);
 }
 
 // A stream-ordered temporary freed when the call returns, on whichever path.
 struct OrderedTemp {
   void* p;
   cudaStream_t st;
-  ~OrderedTemp() { mem_free(p, true, st); }
+  ~OrderedTemp() {
+    if (p) cudaFreeAsync(p, st);
+  }
 };
 
 // Copies n elements from a host or device pointer into device memory on the stream.
@@ -102,20 +130,19 @@ cudaError_t copy_in(T* dst, const T* src, int64_t n, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, st);
 }
 
-inline void free_yet(YetDev& y) {
+inline void free_yet(ara_ctx* c, YetDev& y) {
   for (auto& v : y.bands) free_band_variant(v);
-  dev_free(y.ids);
-  dev_free(y.ts);
-  dev_free(y.offsets);
+  obj_free(c, y.ids);
+  obj_free(c, y.offsets);
   y = YetDev();
 }
-inline void free_elt(EltDev& e) {
-  dev_free(e.ids);
-  dev_free(e.recs);
-  dev_free(e.tables);
-  dev_free(e.corr);
-  dev_free(e.ab64);
-  dev_free(e.starts);
+inline void free_elt(ara_ctx* c, EltDev& e) {
+  obj_free(c, e.ids);
+  obj_free(c, e.recs);
+  obj_free(c, e.tables);
+  obj_free(c, e.corr);
+  obj_free(c, e.ab64);
+  obj_free(c, e.starts);
   e = EltDev();
 }
 

@@ -43,8 +43,7 @@ struct YetDev {
   int64_t n_occ = 0;
   int32_t catalog = 0;
   int64_t max_len = 0;       // longest trial
-  int32_t* ids = nullptr;    // [n_occ]
-  float* ts = nullptr;       // [n_occ]
+  int32_t* ids = nullptr;    // [n_occ] (timestamps are checked at staging and not kept)
   int64_t* offsets = nullptr;  // [n_trials + 1]
   BandedYet bands[kMaxBandVariants];  // band-major copies, built on demand per band width
 };
@@ -155,8 +154,9 @@ void count_launches(int64_t n);
 int64_t launches_so_far();
 
 // ---- launchers (each returns the launch's cudaError_t) ---------------------------------------
-cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st);
-// the same for trials [t_begin, t_begin + n) whose occurrences [occ_base, ...) are in ids/ts
+// Checks of a YET's trials [t_begin, t_begin + n) whose occurrences [occ_base, ...) are in
+// ids / ts (ts may be null: timestamps checked elsewhere): flags bit 0 an id out of range, bit 1
+// a decreasing timestamp, bit 2 a NaN timestamp
 cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64_t occ_base,
                                       const int64_t* offsets, int64_t t_begin, int64_t n,
                                       int32_t catalog, unsigned int* d_flags, cudaStream_t st);

@@ -60,10 +60,10 @@ static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
   unsigned long long* d_uncert = nullptr;  // staging scratch
   unsigned long long uncert = 0;
   cudaError_t err;
-  if ((err = dev_alloc(&e.tables, e.n * kTablePieces)) != cudaSuccess ||
+  if ((err = obj_alloc(ctx, &e.tables, e.n * kTablePieces)) != cudaSuccess ||
       (err = ensure_scratch(ctx, scratch_bytes<unsigned long long>(1))) != cudaSuccess) {
     cudaGetLastError();
-    dev_free(e.tables);
+    obj_free(ctx, e.tables);
     e.tables = nullptr;
     return fail(ctx, ARA_ERR_OOM, "tables of %lld records", (long long)e.n);
   }
@@ -76,11 +76,11 @@ static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
       (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamSynchronize(ctx->stream);
-    dev_free(e.tables);
+    obj_free(ctx, e.tables);
     e.tables = nullptr;
     return fail(ctx, ARA_ERR_CUDA, "building tables: %s", cudaGetErrorString(err));
   }
-  dev_free(e.ab64);
+  obj_free(ctx, e.ab64);
   e.ab64 = nullptr;
   e.n_uncertified = (int64_t)uncert;
   return ARA_OK;
@@ -95,10 +95,10 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   }
   const TablePiece** d_src = nullptr;  // staging scratch
   cudaError_t err;
-  if ((err = dev_alloc(&L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
+  if ((err = obj_alloc(ctx, &L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
       (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed))) != cudaSuccess) {
     cudaGetLastError();
-    dev_free(L.tables);
+    obj_free(ctx, L.tables);
     L.tables = nullptr;
     return fail(ctx, ARA_ERR_OOM, "layer tables: %s", cudaGetErrorString(err));
   }
@@ -113,7 +113,7 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   if (err != cudaSuccess) {
     cudaGetLastError();
     cudaStreamSynchronize(ctx->stream);
-    dev_free(L.tables);
+    obj_free(ctx, L.tables);
     L.tables = nullptr;
     return fail(ctx, ARA_ERR_CUDA, "layer tables: %s", cudaGetErrorString(err));
   }
@@ -128,10 +128,10 @@ static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
     if (!ctx->elts[L.handles[j]].starts) return ARA_OK;  // (not expected) analytic starts
   const TablePiece** d_src = nullptr;  // staging scratch
   cudaError_t err;
-  if ((err = dev_alloc(&L.starts, L.n_packed * kStartFloats)) != cudaSuccess ||
+  if ((err = obj_alloc(ctx, &L.starts, L.n_packed * kStartFloats)) != cudaSuccess ||
       (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed))) != cudaSuccess) {
     cudaGetLastError();
-    dev_free(L.starts);
+    obj_free(ctx, L.starts);
     L.starts = nullptr;
     return fail(ctx, ARA_ERR_OOM, "layer start tables: %s", cudaGetErrorString(err));
   }
@@ -144,7 +144,7 @@ static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
   if (err != cudaSuccess) {
     cudaGetLastError();
     cudaStreamSynchronize(ctx->stream);
-    dev_free(L.starts);
+    obj_free(ctx, L.starts);
     L.starts = nullptr;
     return fail(ctx, ARA_ERR_CUDA, "layer start tables: %s", cudaGetErrorString(err));
   }
@@ -493,11 +493,11 @@ ara_status ara_run_events(ara_ctx* ctx, int32_t yet, int32_t layer, int64_t t0, 
       CUDA_TRY(ctx, cudaStreamSynchronize(st));
       n_occ = ends[1] - ends[0];
       if (olt) {
-        CUDA_TRY(ctx, mem_alloc(&d_olt, n_occ, true, st));
+        CUDA_TRY(ctx, mem_alloc(ctx, &d_olt, n_occ, true, st));
         tmp_olt.p = d_olt;
       }
       if (inc) {
-        CUDA_TRY(ctx, mem_alloc(&d_inc, n_occ, true, st));
+        CUDA_TRY(ctx, mem_alloc(ctx, &d_inc, n_occ, true, st));
         tmp_inc.p = d_inc;
       }
     }
@@ -696,9 +696,9 @@ ara_status ara_run_portfolio(ara_ctx* ctx, int32_t yet, const int32_t* layers, i
   if (n_items == 0) return finish_run(ctx, stream, dev_out, ylt, d_ylt, total, nc_before, st);
   TrialParams* d_items = nullptr;
   int64_t* d_begin = nullptr;
-  CUDA_TRY(ctx, mem_alloc(&d_items, n_layers, true, st));
+  CUDA_TRY(ctx, mem_alloc(ctx, &d_items, n_layers, true, st));
   OrderedTemp tmp_items{d_items, st};
-  CUDA_TRY(ctx, mem_alloc(&d_begin, 3 * (int64_t)n_layers, true, st));
+  CUDA_TRY(ctx, mem_alloc(ctx, &d_begin, 3 * (int64_t)n_layers, true, st));
   OrderedTemp tmp_begin{d_begin, st};
   // pageable sources: each copy has read its source when the call returns
   CUDA_TRY(ctx, cudaMemcpyAsync(d_items, items.data(), sizeof(TrialParams) * (size_t)n_layers,

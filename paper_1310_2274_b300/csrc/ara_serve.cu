@@ -235,7 +235,7 @@ void builder_loop(ara_server* s) {
       s->retired.pop_front();
       lk.unlock();
       // the request's launches and copies are complete: stream-ordered frees, no host wait
-      if (f.has_layer) free_layer_on(f.layer, true, s->build_stream);
+      if (f.has_layer) free_layer_on(s->ctx, f.layer, true, s->build_stream);
       if (f.d_ylt) cudaFreeAsync(f.d_ylt, s->build_stream);
       if (f.d_ysum) cudaFreeAsync(f.d_ysum, s->build_stream);
       cudaGetLastError();
@@ -679,7 +679,7 @@ void ara_server_destroy(ara_server* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (auto& kv : s->reqs) retire(s, *kv.second);
   for (auto& f : s->retired) {
-    if (f.has_layer) free_layer_on(f.layer, true, s->build_stream);
+    if (f.has_layer) free_layer_on(s->ctx, f.layer, true, s->build_stream);
     if (f.d_ylt) cudaFreeAsync(f.d_ylt, s->build_stream);
     if (f.d_ysum) cudaFreeAsync(f.d_ysum, s->build_stream);
   }

@@ -327,11 +327,6 @@ cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate_yet(const YetDev& y, unsigned int* d_flags, cudaStream_t st) {
-  return launch_validate_yet_range(y.ids, y.ts, 0, y.offsets, 0, y.n_trials, y.catalog, d_flags,
-                                   st);
-}
-
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
                                const double* mean, const double* sd, const double* sdc,
                                const double* mx, int32_t catalog, BetaRec* recs, double2* ab64,
