@@ -218,19 +218,37 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   if (!trial_offsets) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets is NULL");
   ara_status s = set_device(ctx);
   if (s != ARA_OK) return s;
-  // offsets are validated on the host (n_trials + 1 values)
-  std::vector<int64_t> off((size_t)n_trials + 1);
-  CUDA_TRY(ctx, cudaMemcpy(off.data(), trial_offsets, sizeof(int64_t) * off.size(),
-                           cudaMemcpyDefault));
-  if (off[0] != 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets[0] != 0");
-  int64_t max_len = 0;
-  for (int64_t i = 0; i < n_trials; ++i) {
-    const int64_t len = off[(size_t)i + 1] - off[(size_t)i];
-    if (len < 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets decrease at trial %lld",
-                             (long long)i);
-    if (len > max_len) max_len = len;
+  // offsets: checked on the device where they and the timestamps are there (the host keeps no
+  // copy then), else on the host
+  const bool dev_path = is_device_ptr(trial_offsets) && (!timestamps || is_device_ptr(timestamps));
+  std::vector<int64_t> off;
+  int64_t max_len = 0, n_occ = 0;
+  if (dev_path) {
+    OffsetCheck oc;
+    CUDA_TRY(ctx, launch_check_offsets(trial_offsets, n_trials,
+                                       reinterpret_cast<OffsetCheck*>(ctx->d_misc), ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(&oc, ctx->d_misc, sizeof oc, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (oc.first != 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets[0] != 0");
+    if (oc.first_decrease >= 0)
+      return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets decrease at trial %lld",
+                  (long long)oc.first_decrease);
+    max_len = oc.max_len;
+    n_occ = oc.last;
+  } else {
+    off.resize((size_t)n_trials + 1);
+    CUDA_TRY(ctx, cudaMemcpy(off.data(), trial_offsets, sizeof(int64_t) * off.size(),
+                             cudaMemcpyDefault));
+    if (off[0] != 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets[0] != 0");
+    for (int64_t i = 0; i < n_trials; ++i) {
+      const int64_t len = off[(size_t)i + 1] - off[(size_t)i];
+      if (len < 0) return fail(ctx, ARA_ERR_INVALID_ARG, "trial_offsets decrease at trial %lld",
+                               (long long)i);
+      if (len > max_len) max_len = len;
+    }
+    n_occ = off[(size_t)n_trials];
   }
-  const int64_t n_occ = off[(size_t)n_trials];
   if (n_occ > 0 && (!event_ids || !timestamps))
     return fail(ctx, ARA_ERR_INVALID_ARG, "event_ids or timestamps is NULL");
   if (n_occ >= ((int64_t)1 << 40)) return fail(ctx, ARA_ERR_INVALID_ARG, "YET too large");
@@ -255,8 +273,8 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   if (ts_on_host)
     ts_check = std::thread(
         [&]() { host_flags = validate_timestamps_host(off.data(), timestamps, n_trials); });
-  // device offsets are copied where they are (the host copy above served the checks)
-  const int64_t* off_src = is_device_ptr(trial_offsets) ? trial_offsets : off.data();
+  // device offsets are copied where they are
+  const int64_t* off_src = dev_path ? trial_offsets : off.data();
   if ((e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess ||
       (e = copy_in(y.offsets, off_src, n_trials + 1, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
@@ -525,6 +543,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   const int64_t tmp_words = scan_tmp_words(C);
   cudaError_t err;
   const TablePiece** d_src = nullptr;
+  const float** d_ssrc = nullptr;  // start-table sources (layers packed with start tables)
   // temporaries: stream-ordered ones on a serving stream, else staging scratch (the table source
   // pointers sized for every record of the layer's ELTs, which bounds the packed count)
   auto cleanup = [&]() {
@@ -537,6 +556,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     mem_free(ctx, d_base, ordered, st);
     mem_free(ctx, d_tmp, ordered, st);
     mem_free(ctx, d_src, ordered, st);
+    mem_free(ctx, d_ssrc, ordered, st);
   };
   const int64_t evt_words = C * (MW == 1 ? 2 : 4);
   if (ordered) {
@@ -549,7 +569,8 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
     for (int j = 0; j < n_elts; ++j) records += ctx->elts[elts[j]].n;
     err = ensure_scratch(ctx, scratch_bytes<uint32_t>(C * MW) + 2 * scratch_bytes<uint32_t>(C) +
                                   scratch_bytes<uint32_t>(tmp_words) +
-                                  scratch_bytes<const TablePiece*>(records));
+                                  scratch_bytes<const TablePiece*>(records) +
+                                  (starts ? scratch_bytes<const float*>(records) : 0));
     if (err == cudaSuccess) {
       ScratchCarver sc{ctx->d_scratch};
       d_mask = sc.take<uint32_t>(C * MW);
@@ -557,6 +578,7 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
       d_base = sc.take<uint32_t>(C);
       d_tmp = sc.take<uint32_t>(tmp_words);
       d_src = sc.take<const TablePiece*>(records);
+      if (starts) d_ssrc = sc.take<const float*>(records);
     }
   }
   if (err != cudaSuccess || (err = mem_alloc(ctx, &L.evt, evt_words, ordered, st)) != cudaSuccess) {
@@ -599,7 +621,9 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
       (ordered && (err = mem_alloc(ctx, &d_src, L.n_packed, ordered, st)) != cudaSuccess) ||
       (has_corr && (err = mem_alloc(ctx, &L.corr, L.n_packed, ordered, st)) != cudaSuccess) ||
       (all_starts &&
-       (err = mem_alloc(ctx, &L.starts, L.n_packed * kStartFloats, ordered, st)) != cudaSuccess)) {
+       (err = mem_alloc(ctx, &L.starts, L.n_packed * kStartFloats, ordered, st)) != cudaSuccess) ||
+      (all_starts && ordered && (err = mem_alloc(ctx, &d_ssrc, L.n_packed, ordered, st)) !=
+                                    cudaSuccess)) {
     cudaGetLastError();
     cleanup();
     free_layer_on(ctx, L, ordered, st);
@@ -607,8 +631,10 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   }
   for (int j = 0; j < n_elts && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[elts[j]], j, MW, L.evt, L.packed, d_src, L.packed_rec,
-                               L.corr, L.starts, st);
+                               L.corr, all_starts ? d_ssrc : nullptr, st);
   if (err == cudaSuccess && all_tables) err = launch_gather_tables(L.n_packed, d_src, L.tables, st);
+  if (err == cudaSuccess && all_starts)
+    err = launch_gather_starts(L.n_packed, d_ssrc, L.starts, st);
   // the largest event-loss bound sizes the grid of the exact year sums (d_cnt is free by now)
   unsigned int ev_bits = 0u;
   if (err == cudaSuccess) err = launch_layer_event_bound(L.evt, MW, C, L.packed, d_cnt, st);

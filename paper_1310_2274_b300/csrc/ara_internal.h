@@ -154,6 +154,14 @@ void count_launches(int64_t n);
 int64_t launches_so_far();
 
 // ---- launchers (each returns the launch's cudaError_t) ---------------------------------------
+// Trial offsets checked on the device: off[0], the first trial whose offset decreases (-1:
+// none), the longest trial and off[n_trials].
+struct OffsetCheck {
+  int64_t first, first_decrease, max_len, last;
+};
+// *out (device, 32 bytes) receives the check of off[0 .. n_trials]
+cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, OffsetCheck* out,
+                                 cudaStream_t st);
 // Checks of a YET's trials [t_begin, t_begin + n) whose occurrences [occ_base, ...) are in
 // ids / ts (ts may be null: timestamps checked elsewhere): flags bit 0 an id out of range, bit 1
 // a decreasing timestamp, bit 2 a NaN timestamp
@@ -176,11 +184,11 @@ cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t
 int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, int mask_words,
                                int64_t catalog, uint32_t* d_evt, cudaStream_t st);
-// packed_starts (optional): the records' start tables in packed order
+// start_src (optional): each packed record's start table in its ELT, for launch_gather_starts
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
-                                 float* packed_corr, float* packed_starts, cudaStream_t st);
+                                 float* packed_corr, const float** start_src, cudaStream_t st);
 // *d_bound = binary32 bits of the layer's largest event-loss bound (sum over an event's records
 // of max_l, or the mean where sd = 0), rounded up; 0 for a layer without records
 cudaError_t launch_layer_event_bound(const uint32_t* d_evt, int mask_words, int64_t catalog,
@@ -192,6 +200,8 @@ cudaError_t launch_build_starts(int64_t n, const BetaRec* recs, float* starts, c
 cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
                                 TablePiece* tables, unsigned long long* d_uncertified,
                                 cudaStream_t st);
+// dst[i * kStartFloats ...] = the start table at d_src[i], for the n packed records of a layer
+cudaError_t launch_gather_starts(int64_t n, const float* const* d_src, float* dst, cudaStream_t st);
 // dst[i * kTablePieces ...] = the table at d_src[i], for the n packed records of a layer
 cudaError_t launch_gather_tables(int64_t n, const TablePiece* const* d_src, TablePiece* dst,
                                  cudaStream_t st);

@@ -126,20 +126,24 @@ static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
   if (L.starts) return ARA_OK;
   for (int j = 0; j < L.n_slots; ++j)
     if (!ctx->elts[L.handles[j]].starts) return ARA_OK;  // (not expected) analytic starts
-  const TablePiece** d_src = nullptr;  // staging scratch
   cudaError_t err;
   if ((err = obj_alloc(ctx, &L.starts, L.n_packed * kStartFloats)) != cudaSuccess ||
-      (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed))) != cudaSuccess) {
+      (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed) +
+                                     scratch_bytes<const float*>(L.n_packed))) != cudaSuccess) {
     cudaGetLastError();
     obj_free(ctx, L.starts);
     L.starts = nullptr;
     return fail(ctx, ARA_ERR_OOM, "layer start tables: %s", cudaGetErrorString(err));
   }
-  d_src = reinterpret_cast<const TablePiece**>(ctx->d_scratch);
+  // staging scratch: the table and start-table source of each packed record
+  ScratchCarver sc{ctx->d_scratch};
+  const TablePiece** d_src = sc.take<const TablePiece*>(L.n_packed);
+  const float** d_ssrc = sc.take<const float*>(L.n_packed);
   err = cudaSuccess;
   for (int j = 0; j < L.n_slots && err == cudaSuccess; ++j)
     err = launch_layer_scatter(ctx->elts[L.handles[j]], j, L.mask_words, L.evt, L.packed, d_src,
-                               L.packed_rec, L.corr, L.starts, ctx->stream);
+                               L.packed_rec, L.corr, d_ssrc, ctx->stream);
+  if (err == cudaSuccess) err = launch_gather_starts(L.n_packed, d_ssrc, L.starts, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   if (err != cudaSuccess) {
     cudaGetLastError();

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "ara_internal.h"
@@ -53,6 +54,43 @@ __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float
   }
   f = __reduce_or_sync(0xFFFFFFFFu, f);
   if (lane == 0 && f) atomicOr(flags, f);
+}
+
+// Offsets: the longest trial by a maximum, the first decrease by a minimum over trial indices
+// (both as 64-bit integer atomics on fields set by check_offsets_init).
+__global__ void check_offsets_init(const int64_t* __restrict__ off, int64_t n_trials,
+                                   OffsetCheck* out) {
+  out->first = off[0];
+  out->first_decrease = INT64_MAX;
+  out->max_len = 0;
+  out->last = off[n_trials];
+}
+
+__global__ void check_offsets_kernel(const int64_t* __restrict__ off, int64_t n_trials,
+                                     OffsetCheck* out) {
+  int64_t len_max = 0, dec = INT64_MAX;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_trials;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = off[i + 1] - off[i];
+    if (len > len_max) len_max = len;
+    if (len < 0 && i < dec) dec = i;
+  }
+  // lengths and indices are non-negative here, so unsigned maxima and minima order them
+  unsigned long long lm = (unsigned long long)len_max, dm = (unsigned long long)dec;
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    lm = max(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, d));
+    dm = min(dm, __shfl_xor_sync(0xFFFFFFFFu, dm, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lm) atomicMax(reinterpret_cast<unsigned long long*>(&out->max_len), lm);
+    if (dm != (unsigned long long)INT64_MAX)
+      atomicMin(reinterpret_cast<unsigned long long*>(&out->first_decrease), dm);
+  }
+}
+
+__global__ void check_offsets_fini(OffsetCheck* out) {
+  if (out->first_decrease == INT64_MAX) out->first_decrease = -1;
 }
 
 // ---- ELT record preparation (FP64, once per record) --------------------------------------------
@@ -167,7 +205,7 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
                                      BetaRec* packed, const TablePiece** table_src,
                                      uint32_t* packed_rec, const float* __restrict__ corr,
                                      float* packed_corr, const float* __restrict__ starts,
-                                     float* packed_starts) {
+                                     const float** start_src) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t e = ids[r];
@@ -186,12 +224,7 @@ __global__ void layer_scatter_kernel(int64_t n, const int32_t* __restrict__ ids,
   table_src[base + rank] = tables + r * kTablePieces;
   if (packed_corr) packed_corr[base + rank] = corr ? corr[r] : 0.0f;
   packed_rec[base + rank] = (uint32_t)r;
-  if (packed_starts && starts) {  // 384 bytes as 8-byte words
-    const float2* src = reinterpret_cast<const float2*>(starts + r * kStartFloats);
-    float2* dst = reinterpret_cast<float2*>(packed_starts + (int64_t)(base + rank) * kStartFloats);
-#pragma unroll 8
-    for (int k = 0; k < kStartFloats / 2; ++k) dst[k] = src[k];
-  }
+  if (start_src) start_src[base + rank] = starts + r * kStartFloats;  // copied by gather_starts
 }
 
 // The largest loss an event of the layer can bring before occurrence terms: over catalogue events,
@@ -327,6 +360,18 @@ cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64
   return cudaGetLastError();
 }
 
+cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, OffsetCheck* out,
+                                 cudaStream_t st) {
+  check_offsets_init<<<1, 1, 0, st>>>(off, n_trials, out);
+  if (n_trials > 0) {
+    const int64_t blocks = std::min<int64_t>((n_trials + kThreads - 1) / kThreads, 148 * 8);
+    check_offsets_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(off, n_trials, out);
+  }
+  check_offsets_fini<<<1, 1, 0, st>>>(out);
+  count_launches(n_trials > 0 ? 3 : 2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
                                const double* mean, const double* sd, const double* sdc,
                                const double* mx, int32_t catalog, BetaRec* recs, double2* ab64,
@@ -379,12 +424,12 @@ cudaError_t launch_layer_index(const uint32_t* d_mask, const uint32_t* d_base, i
 cudaError_t launch_layer_scatter(const EltDev& e, int slot, int mask_words,
                                  const uint32_t* d_evt, BetaRec* packed,
                                  const TablePiece** table_src, uint32_t* packed_rec,
-                                 float* packed_corr, float* packed_starts, cudaStream_t st) {
+                                 float* packed_corr, const float** start_src, cudaStream_t st) {
   if (e.n == 0) return cudaSuccess;
   layer_scatter_kernel<<<grid_for(e.n), kThreads, 0, st>>>(e.n, e.ids, e.recs, e.tables, slot,
                                                            mask_words, d_evt, packed, table_src,
                                                            packed_rec, e.corr, packed_corr,
-                                                           e.starts, packed_starts);
+                                                           e.starts, start_src);
   count_launches(1);
   return cudaGetLastError();
 }

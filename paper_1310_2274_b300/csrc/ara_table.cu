@@ -42,7 +42,31 @@ __global__ void gather_tables_kernel(int64_t n, const TablePiece* const* __restr
     d[i * 32 + lane] = s[i * 32 + lane];
 }
 
+// Layer copy of the start tables in packed order: one thread per 16 bytes, 24 per record, so the
+// warp's stores are contiguous.
+__global__ void gather_starts_kernel(int64_t n, const float* const* __restrict__ src,
+                                     float* __restrict__ dst) {
+  constexpr int kParts = kStartFloats * (int)sizeof(float) / 16;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kParts) return;
+  const int64_t w = i / kParts;
+  const int part = (int)(i - w * kParts);
+  reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src[w])[part];
+}
+static_assert(kStartFloats * sizeof(float) % 16 == 0, "start tables copy in 16-byte parts");
+
 }  // namespace
+
+cudaError_t launch_gather_starts(int64_t n, const float* const* d_src, float* dst,
+                                 cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t total = n * (kStartFloats * (int64_t)sizeof(float) / 16);
+  gather_starts_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(n, d_src,
+                                                                                       dst);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
                                 TablePiece* tables, unsigned long long* d_uncertified,

@@ -38,3 +38,55 @@ def test_scratch_growth_keeps_staging_exact(ara, oracle):
     want, _ = oracle.run(yet, [big], terms, 42, trials=np.arange(N), elt_handles=[1])
     scale = np.maximum(np.maximum(np.abs(want), terms.agg_ret), 1.0)
     assert np.max(np.abs(got - want) / scale) <= 1e-5
+
+
+def test_device_resident_yet_checked_on_the_device(ara):
+    """A YET whose arrays are in device memory is checked there (offsets by a kernel, timestamps
+    where they are, never copied): bad offsets, ids and timestamps are rejected, and a valid one
+    runs exactly as the same YET staged from host arrays (the same handles)."""
+    import torch
+
+    w = synth.tiny(300)
+    y = w.yet
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    with ara.Context(seed=42) as ctx:
+        h = ctx.create_yet(y.offsets, y.event_ids, y.timestamps, y.catalog_size)
+        d = ctx.create_yet(dev(y.offsets), dev(y.event_ids), dev(y.timestamps), y.catalog_size)
+        e_h = ctx.add_elt(h, *(getattr(w.elts[0], f) for f in ("event_ids", "mean", "sd",
+                                                                "max_exposure")))
+        e_d = ctx.add_elt(d, *(getattr(w.elts[0], f) for f in ("event_ids", "mean", "sd",
+                                                                "max_exposure")))
+        assert (e_h, e_d) == (0, 1)
+        t = w.terms
+        l_d = ctx.add_layer([e_d], t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+        # the uniforms are keyed by the ELT handle: compare with a context of host arrays in
+        # which the same ELT also has handle 1
+        got_d = ctx.run(d, l_d, 0, 300)
+        with ara.Context(seed=42) as ref:
+            rh = ref.create_yet(y.offsets, y.event_ids, y.timestamps, y.catalog_size)
+            ref.add_elt(rh, *(getattr(w.elts[0], f) for f in ("event_ids", "mean", "sd",
+                                                               "max_exposure")))
+            r1 = ref.add_elt(rh, *(getattr(w.elts[0], f) for f in ("event_ids", "mean", "sd",
+                                                                    "max_exposure")))
+            rl = ref.add_layer([r1], t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+            np.testing.assert_array_equal(got_d, ref.run(rh, rl, 0, 300))
+        # rejections, each with the caller's arrays on the device
+        bad_off = y.offsets.copy()
+        bad_off[7], bad_off[8] = bad_off[8], bad_off[7]  # trial 7 ends before it starts
+        with pytest.raises(ara.AraError, match="decrease at trial 7"):
+            ctx.create_yet(dev(bad_off), dev(y.event_ids), dev(y.timestamps), y.catalog_size)
+        first = y.offsets.copy() + 1
+        with pytest.raises(ara.AraError, match=r"trial_offsets\[0\] != 0"):
+            ctx.create_yet(dev(first), dev(y.event_ids), dev(y.timestamps), y.catalog_size)
+        ids = y.event_ids.copy()
+        ids[1234] = y.catalog_size
+        with pytest.raises(ara.AraError, match="event id outside"):
+            ctx.create_yet(dev(y.offsets), dev(ids), dev(y.timestamps), y.catalog_size)
+        ts = y.timestamps.copy()
+        ts[int(y.offsets[5]) + 3] = -1.0  # below its predecessor in trial 5
+        with pytest.raises(ara.AraError, match="timestamps decrease"):
+            ctx.create_yet(dev(y.offsets), dev(y.event_ids), dev(ts), y.catalog_size)
+        ts = y.timestamps.copy()
+        ts[int(y.offsets[9])] = np.nan
+        with pytest.raises(ara.AraError, match="NaN timestamp"):
+            ctx.create_yet(dev(y.offsets), dev(y.event_ids), dev(ts), y.catalog_size)
