@@ -168,7 +168,8 @@ ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n, bool band
     if (banded) L.band_log2w = L.band_want;
     L.band_want = 0;
   }
-  return layer_inversion(ctx, L) == 1 ? ensure_layer_starts(ctx, L) : ARA_OK;
+  // Newton-Halley runs and the surrogate's fallbacks start from the layer's start tables
+  return layer_inversion(ctx, L) >= 1 ? ensure_layer_starts(ctx, L) : ARA_OK;
 }
 
 static ara_status rent_or_buy(ara_ctx* ctx, LayerDev& L, int64_t n) {

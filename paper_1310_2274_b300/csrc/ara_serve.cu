@@ -136,7 +136,7 @@ int64_t request_bytes(const ara_server* s, const ara_request& r) {
   for (int j = 0; j < r.n_elts; ++j) recs += c->elts[r.elts[j]].n;
   // per packed record: header, caller index, table copy, and the start table of Newton servers
   const int64_t per_rec = (int64_t)(sizeof(BetaRec) + 4 + ara::kTablePieces * sizeof(ara::TablePiece)) +
-                          (inversion_mode(c) == 1 ? (int64_t)(ara::kStartFloats * sizeof(float)) : 0);
+                          (inversion_mode(c) >= 1 ? (int64_t)(ara::kStartFloats * sizeof(float)) : 0);
   return C * 16 + recs * per_rec + r.n_trials * 16 + (1 << 20);
 }
 
@@ -266,7 +266,7 @@ void builder_loop(ara_server* s) {
     bool band = false;
     ara_status st = ara_build_layer(s->ctx, req.elts, req.n_elts, req.occ_ret, req.occ_lim,
                                     req.agg_ret, req.agg_lim, true, s->build_stream, false, true,
-                                    &L, inversion_mode(s->ctx) == 1);
+                                    &L, inversion_mode(s->ctx) >= 1);
     if (st == ARA_OK) {
       band = uses_band_schedule(s->ctx, L);
       const size_t n = (size_t)std::max<int64_t>(1, req.n_trials);

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ara_ibeta.cuh"
 #include "ara_internal.h"
 #include "ara_mlp.cuh"
@@ -38,33 +40,145 @@ namespace {
 // only when its slowest warp ends, so small blocks waste least of it), 8 for the surrogate path,
 // whose blocks first load the network's weights into shared memory.
 template <int INV>
-constexpr int kWPB = INV == 2 ? 8 : 2;
+constexpr int kWPB = INV == 2 ? 4 : 2;
 constexpr int kV = 4;             // occurrences per lane per chunk
 constexpr int kChunk = 32 * kV;   // occurrences per chunk
 
-// Surrogate inference for the round's hits: lanes with want set get the network's x (logit x =
-// kOutScale * y); the warp's 32 hits are two 16-row MMA tiles (lane 16 m + r is row r of tile m).
-__device__ __forceinline__ float surrogate_round(const MlpSmem& W, const float (&z)[3], int lane) {
+// One 16-row tile of the network (tile mt of the warp's 32 rows: lane 16 mt + r holds row r's
+// inputs); returns row g's output in *y0 and row g + 8's in *y8.  Out of line, so that the two
+// tiles run one after the other and its registers do not add to the caller's.
+__device__ __noinline__ void surrogate_tile(const MlpSmem& W, float z0, float z1, float z2,
+                                            int mt, int lane, float* y0, float* y8) {
   const int g = lane >> 2, t = lane & 3;
-  float y_t[2][2];
+  const float zc[3] = {z0, z1, z2};
+  float zr0[3], zr8[3];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    float zr0[3], zr8[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      zr0[c] = __shfl_sync(0xFFFFFFFFu, z[c], mt * 16 + g);
-      zr8[c] = __shfl_sync(0xFFFFFFFFu, z[c], mt * 16 + g + 8);
-    }
-    mlp_tile_forward(W, zr0, zr8, g, t, &y_t[mt][0], &y_t[mt][1]);
+  for (int c = 0; c < 3; ++c) {
+    zr0[c] = __shfl_sync(0xFFFFFFFFu, zc[c], mt * 16 + g);
+    zr8[c] = __shfl_sync(0xFFFFFFFFu, zc[c], mt * 16 + g + 8);
   }
+  mlp_tile_forward(W, zr0, zr8, g, t, y0, y8);
+}
+
+// Surrogate inference for 32 rows (one per lane): x from logit x = kOutScale * y; the rows are
+// two 16-row MMA tiles (lane 16 m + r is row r of tile m).
+__device__ __forceinline__ float surrogate_round(const MlpSmem& W, const float (&z)[3], int lane) {
+  float a0, a8, b0, b8;
+  surrogate_tile(W, z[0], z[1], z[2], 0, lane, &a0, &a8);
+  surrogate_tile(W, z[0], z[1], z[2], 1, lane, &b0, &b8);
   // row r of tile m sits in lanes 4 (r mod 8) .. 4 (r mod 8) + 3, component r >= 8
   const int r = lane & 15, src = 4 * (r & 7);
-  const float a0 = __shfl_sync(0xFFFFFFFFu, y_t[0][0], src);
-  const float a8 = __shfl_sync(0xFFFFFFFFu, y_t[0][1], src);
-  const float b0 = __shfl_sync(0xFFFFFFFFu, y_t[1][0], src);
-  const float b8 = __shfl_sync(0xFFFFFFFFu, y_t[1][1], src);
+  a0 = __shfl_sync(0xFFFFFFFFu, a0, src);
+  a8 = __shfl_sync(0xFFFFFFFFu, a8, src);
+  b0 = __shfl_sync(0xFFFFFFFFu, b0, src);
+  b8 = __shfl_sync(0xFFFFFFFFu, b8, src);
   const float y = lane < 16 ? (r < 8 ? a0 : a8) : (r < 8 ? b0 : b8);
   return 1.0f / (1.0f + __expf(-kOutScale * y));
+}
+
+// ---- the learned surrogate's hits, a segment at a time ------------------------------------------
+// Running the network in every round where any lane's hit is eligible costs a full 32-row pass
+// per round (about 18% of hits are eligible); instead the losses of a segment of up to kSegCap
+// hits are computed ahead: pass A draws every hit and inverts the ineligible ones (Newton-Halley
+// from the record's start table), listing the eligible ones; pass B runs the network over the
+// list 32 rows at a time.  The rounds then read each hit's loss.
+constexpr int kSegCap = 128;
+struct SurrWarpSmem {
+  float z[3][kSegCap];     // network inputs of the listed hits
+  float mx[kSegCap];       // their loss scale
+  uint8_t idx[kSegCap];    // their position in the segment
+  float loss[kSegCap];     // every hit of the segment
+};
+
+// The exact inversion of a hit the network does not serve: Newton-Halley from the record's start
+// table (analytic start without one), out of line so its registers do not add to the network's.
+__device__ __noinline__ IbetaResult surrogate_fallback(const BetaRec* p, float u,
+                                                       const float* start) {
+  return ara_inv_beta<true>(load_rec(p), u, start ? ara_start_logit(start, u) : 1e30f);
+}
+
+// Losses of hits [s0, s1) of the chunk (s1 - s0 <= kSegCap) into sm.loss (and, with TRACE, x and
+// u into tx, tu); hit(g) gives (packed record, slot, occurrence position) of hit g.
+template <bool TRACE, bool CORR, class HitFn>
+__device__ __forceinline__ void surrogate_segment(const TrialParams& P, const MlpSmem& W,
+                                                  int64_t trial, int32_t s0, int32_t s1,
+                                                  HitFn hit, SurrWarpSmem& sm, float* tx,
+                                                  float* tu, int lane, unsigned int& nc,
+                                                  unsigned int& n_inv, unsigned int& n_it,
+                                                  unsigned int& n_cf, unsigned int& n_net) {
+  const unsigned below = (1u << lane) - 1u;
+  int n_list = 0;
+  for (int32_t g0 = s0; g0 < s1; g0 += 32) {
+    const int32_t g = g0 + lane;
+    bool listed = false;
+    float z0 = 0.f, z1 = 0.f, z2 = 0.f, mx = 0.f, u = 0.f;
+    if (g < s1) {
+      uint32_t pos, k;
+      int slot;
+      hit(g, &pos, &slot, &k);
+      const BetaRec rec = load_rec(P.recs + pos);
+      mx = rec.mx;
+      const bool sd0 = !(rec.a > 0.f);
+      if (!sd0 || TRACE) {
+        const float cc = (CORR && P.corr != nullptr) ? __ldg(P.corr + pos) : 0.0f;
+        u = su_draw(su_uniform_rk(P.rk0, P.rk1, trial, k, P.handles[slot]),
+                    cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, k) : 0.5f, cc).z;
+      }
+      float l = mx, x = __int_as_float(0x7FC00000);
+      if (!sd0) {
+        // the network serves the hit if (alpha, beta) lies in its box and the certified error
+        // of the hit's cell is within eps
+        if (rec.a >= kBoxLo && rec.a <= kBoxHi && rec.b >= kBoxLo && rec.b <= kBoxHi) {
+          z0 = (logf(rec.a) - kLnCenter) / kLnHalf;
+          z1 = (logf(rec.b) - kLnCenter) / kLnHalf;
+          z2 = (logf(u) - log1pf(-u)) / kLogitScale;
+          const int i0 = min(max((int)((z0 + 1.0f) * (0.5f * kCert0)), 0), kCert0 - 1);
+          const int i1 = min(max((int)((z1 + 1.0f) * (0.5f * kCert1)), 0), kCert1 - 1);
+          const int i2 = min(max((int)((z2 + 1.0f) * (0.5f * kCert2)), 0), kCert2 - 1);
+          listed = __ldg(P.mlp_bound + ((i0 * kCert1) + i1) * kCert2 + i2) <= P.mlp_eps;
+        }
+        if (!listed) {
+          const IbetaResult ib = surrogate_fallback(
+              P.recs + pos, u, P.starts ? P.starts + (size_t)pos * kStartFloats : nullptr);
+          nc += ib.converged ? 0u : 1u;
+          n_inv += 1u;
+          n_it += (unsigned)ib.iters;
+          n_cf += (unsigned)ib.cf_terms;
+          x = ib.x;
+          l = mx * x;
+        }
+      }
+      if (!listed) sm.loss[g - s0] = l;
+      if constexpr (TRACE) {
+        tx[g - s0] = x;
+        tu[g - s0] = u;
+      }
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, listed);
+    if (listed) {
+      const int j = n_list + __popc(m & below);
+      sm.z[0][j] = z0;
+      sm.z[1][j] = z1;
+      sm.z[2][j] = z2;
+      sm.mx[j] = mx;
+      sm.idx[j] = (uint8_t)(g - s0);
+    }
+    n_list += __popc(m);
+  }
+  __syncwarp();
+  for (int j0 = 0; j0 < n_list; j0 += 32) {
+    const int j = j0 + lane;
+    const bool in = j < n_list;
+    const float zz[3] = {in ? sm.z[0][j] : 0.f, in ? sm.z[1][j] : 0.f, in ? sm.z[2][j] : 0.f};
+    const float xs = surrogate_round(W, zz, lane);
+    if (in) {
+      const int i = sm.idx[j];
+      sm.loss[i] = sm.mx[j] * xs;
+      if constexpr (TRACE) tx[i] = xs;
+      n_net += 1u;
+    }
+  }
+  __syncwarp();
 }
 
 // Per-occurrence outputs for 32 consecutive occurrences (lane l: position q), in trial order:
@@ -106,7 +220,8 @@ template <int MW, class Acc, bool TRACE, int INV, bool CORR>
 __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, int lane, int wib,
                                               int32_t* excl, uint32_t* sbase,
                                               uint32_t (*s_maskw)[kChunk], float* lsum,
-                                              const MlpSmem* s_mlp) {
+                                              const MlpSmem* s_mlp, SurrWarpSmem* s_surr,
+                                              float* s_tx, float* s_tu) {
   constexpr bool TABLE = INV == 0;
   constexpr bool SURR = INV == 2;
   const int64_t trial = P.t0 + w;
@@ -159,7 +274,33 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
     // ---- rounds of up to 32 hits ending on an event boundary (an event with more than 32
     // hits left is split 32 hits from its first): uniform draw, inverse beta, per-event
     // segmented sum.  Rounds depend on the event's hits alone, so the FP32 event sums do too.
+    int32_t seg0 = 0, seg1 = 0;  // surrogate: hits whose losses are computed ahead
     for (int32_t r0 = 0; r0 < run;) {
+      if constexpr (SURR) {
+        if (r0 + 32 > seg1 && seg1 < run) {  // the next round may need hits past the segment
+          seg0 = r0;
+          seg1 = min(run, r0 + kSegCap);
+          const uint32_t kc = (uint32_t)(c - beg);
+          auto hit = [&](int32_t gg, uint32_t* pos, int* slot, uint32_t* k) {
+            int e = 0;
+#pragma unroll
+            for (int step = kChunk / 2; step >= 1; step >>= 1)
+              if (excl[e + step] <= gg) e += step;
+            const int nth = gg - excl[e];
+            if constexpr (MW == 1) {
+              *slot = nth_set_bit(s_maskw[0][e], nth);
+            } else {
+              const uint32_t m0 = s_maskw[0][e];
+              const int c0 = __popc(m0);
+              *slot = nth < c0 ? nth_set_bit(m0, nth) : 32 + nth_set_bit(s_maskw[1][e], nth - c0);
+            }
+            *pos = sbase[e] + (uint32_t)nth;
+            *k = kc + (uint32_t)e;
+          };
+          surrogate_segment<TRACE, CORR>(P, *s_mlp, trial, seg0, seg1, hit, *s_surr, s_tx, s_tu,
+                                         lane, nc, n_inv, n_it, n_cf, n_net);
+        }
+      }
       const int32_t g = r0 + lane;
       int ev = 0;  // event of hit g: the last position whose exclusive prefix is <= g
       if (g < run) {
@@ -182,8 +323,6 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
       int slot = 0;
       uint32_t pos = 0, k = 0;
       float loss = 0.f, u = 0.f, x = __int_as_float(0x7FC00000), mx = 0.f;
-      float surr_z[3] = {0.f, 0.f, 0.f};
-      bool net = false;
       int seg_start = lane;  // first lane of this hit's event in the round
       if (has) {
         const int nth = g - excl[ev];
@@ -214,7 +353,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
           use_table = pc.flag == kPieceTable;
         }
         BetaRec rec;
-        if (!TABLE) {
+        if constexpr (INV == 1) {
           rec = load_rec(P.recs + pos);
           sd0 = !(rec.a > 0.f);
           mx = rec.mx;
@@ -223,21 +362,15 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
                         cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, k) : 0.5f, cc).z;
         }
         if constexpr (SURR) {
-          // the network serves this hit if (alpha, beta) lies in its box and the certified error
-          // of the hit's cell is within eps; all lanes then evaluate it together below
-          if (!sd0 && rec.a >= kBoxLo && rec.a <= kBoxHi && rec.b >= kBoxLo && rec.b <= kBoxHi) {
-            surr_z[0] = (logf(rec.a) - kLnCenter) / kLnHalf;
-            surr_z[1] = (logf(rec.b) - kLnCenter) / kLnHalf;
-            surr_z[2] = (logf(u) - log1pf(-u)) / kLogitScale;
-            const int i0 = min(max((int)((surr_z[0] + 1.0f) * (0.5f * kCert0)), 0), kCert0 - 1);
-            const int i1 = min(max((int)((surr_z[1] + 1.0f) * (0.5f * kCert1)), 0), kCert1 - 1);
-            const int i2 = min(max((int)((surr_z[2] + 1.0f) * (0.5f * kCert2)), 0), kCert2 - 1);
-            net = __ldg(P.mlp_bound + ((i0 * kCert1) + i1) * kCert2 + i2) <= P.mlp_eps;
+          // computed ahead by surrogate_segment
+          loss = s_surr->loss[g - seg0];
+          if constexpr (TRACE) {
+            x = s_tx[g - seg0];
+            u = s_tu[g - seg0];
           }
-        }
-        if (sd0) {
+        } else if (sd0) {
           loss = mx;  // sd = 0: the mean (primary uncertainty only)
-        } else if (!net) {
+        } else {
           if (TABLE && use_table) {
             x = ara_piece_x(pc, tau);
             n_tab += 1u;
@@ -247,7 +380,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
                                         P.starts != nullptr
                                             ? ara_start_logit(P.starts + (size_t)pos * kStartFloats, u)
                                             : 1e30f)
-                         : newton_fallback<INV == 2>(P.recs + pos, u);
+                         : newton_fallback<false>(P.recs + pos, u);
             x = ib.x;
             nc += ib.converged ? 0u : 1u;
             n_inv += 1u;
@@ -255,16 +388,6 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
             n_cf += (unsigned)ib.cf_terms;
           }
           loss = mx * x;
-        }
-      }
-      if constexpr (SURR) {
-        if (__any_sync(0xFFFFFFFFu, net)) {
-          const float xs = surrogate_round(*s_mlp, surr_z, lane);
-          if (net) {
-            x = xs;
-            loss = mx * x;
-            n_net += 1u;
-          }
         }
       }
       if constexpr (TRACE) {
@@ -341,9 +464,24 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
 // INV: 0 certified tables (Newton fallback), 1 Newton, 2 learned surrogate (Newton fallback).
 // The table and Newton paths are latency bound (dependent loads per hit; the serial continued
 // fraction), so they are held to 64 registers for 32 resident warps per SM (the Newton path
-// runs 4% faster so than at 24 warps with 85 registers).
+// runs 4% faster so than at 24 warps with 85 registers).  The surrogate path's blocks hold the
+// network's weights (22 KB) and their warps' segment lists in shared memory (45 KB a 4-warp
+// block): 4 blocks per SM at up to 128 registers, on a persistent grid so that each block copies
+// the weights once.
+template <int INV>
+constexpr int kBlocksPerSM = INV == 2 ? 4 : 32 / kWPB<INV>;
+
+// Shared memory of the surrogate's segments (trace: each hit's x and u as well), declared only
+// where INV == 2.
+#define SURR_SMEM(W, INV, TRACE)                                                                 \
+  __shared__ SurrWarpSmem s_surr[(INV) == 2 ? (W) : 1];                                         \
+  __shared__ float s_trace[((INV) == 2 && (TRACE)) ? 2 * (W) * kSegCap : 1]
+#define SURR_ARGS(INV, TRACE)                                                                    \
+  &s_surr[(INV) == 2 ? wib : 0], ((INV) == 2 && (TRACE)) ? s_trace + 2 * wib * kSegCap : nullptr, \
+      ((INV) == 2 && (TRACE)) ? s_trace + (2 * wib + 1) * kSegCap : nullptr
+
 template <int MW, class Acc, bool TRACE, int INV, bool CORR>
-__global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 2 ? 8 : 32) / kWPB<INV>)
+__global__ void __launch_bounds__(kWPB<INV> * 32, kBlocksPerSM<INV>)
     trial_kernel(const __grid_constant__ TrialParams P) {
   constexpr int W = kWPB<INV>;
   __shared__ int32_t s_excl[W][kChunk];
@@ -351,6 +489,7 @@ __global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 2 ? 8 : 32) / kWPB<INV
   __shared__ uint32_t s_mask[W][MW][kChunk];
   __shared__ float s_lsum[W][kChunk];
   __shared__ __align__(16) MlpSmem s_mlp[1];
+  SURR_SMEM(W, INV, TRACE);
   if constexpr (INV == 2) {  // network weights, once per block, before any warp may leave
     const uint4* src = reinterpret_cast<const uint4*>(P.mlp);
     uint4* dst = reinterpret_cast<uint4*>(&s_mlp[0]);
@@ -359,16 +498,18 @@ __global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 2 ? 8 : 32) / kWPB<INV
   }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * W + wib;
-  if (w >= P.n) return;  // whole warp leaves together; no block-wide barrier follows
-  process_trial<MW, Acc, TRACE, INV, CORR>(P, w, lane, wib, s_excl[wib], s_base[wib],
-                                           s_mask[wib], s_lsum[wib], &s_mlp[0]);
+  // one trial per warp; a warp of a grid smaller than the launch's trials takes every
+  // (grid size)-th trial (whole warps, no block-wide barrier follows)
+  for (int64_t w = (int64_t)blockIdx.x * W + wib; w < P.n; w += (int64_t)gridDim.x * W)
+    process_trial<MW, Acc, TRACE, INV, CORR>(P, w, lane, wib, s_excl[wib], s_base[wib],
+                                             s_mask[wib], s_lsum[wib], &s_mlp[0],
+                                             SURR_ARGS(INV, TRACE));
 }
 
 // One launch over many work items (serving: slices of different requests, each with its own
 // layer and YLT): warp w runs trial w - warp_begin[i] of the item i with warp_begin[i] <= w.
 template <int MW, class Acc, int INV>
-__global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 0 ? 32 : (INV == 1 ? 24 : 8)) / kWPB<INV>)
+__global__ void __launch_bounds__(kWPB<INV> * 32, kBlocksPerSM<INV>)
     batch_kernel(const TrialParams* __restrict__ items, const int64_t* __restrict__ warp_begin,
                  int n_items, int64_t total_warps) {
   constexpr int W = kWPB<INV>;
@@ -377,6 +518,7 @@ __global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 0 ? 32 : (INV == 1 ? 2
   __shared__ uint32_t s_mask[W][MW][kChunk];
   __shared__ float s_lsum[W][kChunk];
   __shared__ __align__(16) MlpSmem s_mlp[1];
+  SURR_SMEM(W, INV, false);
   if constexpr (INV == 2) {
     const uint4* src = reinterpret_cast<const uint4*>(items[0].mlp);
     uint4* dst = reinterpret_cast<uint4*>(&s_mlp[0]);
@@ -385,21 +527,36 @@ __global__ void __launch_bounds__(kWPB<INV> * 32, (INV == 0 ? 32 : (INV == 1 ? 2
   }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * W + wib;
-  if (w >= total_warps) return;
-  int lo = 0, hi = n_items - 1;
-  while (lo < hi) {  // largest item whose first warp is <= w
-    const int mid = (lo + hi + 1) >> 1;
-    if (warp_begin[mid] <= w) lo = mid; else hi = mid - 1;
+  for (int64_t w = (int64_t)blockIdx.x * W + wib; w < total_warps;
+       w += (int64_t)gridDim.x * W) {
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {  // largest item whose first warp is <= w
+      const int mid = (lo + hi + 1) >> 1;
+      if (warp_begin[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    process_trial<MW, Acc, false, INV, true>(items[lo], w - warp_begin[lo], lane, wib,
+                                             s_excl[wib], s_base[wib], s_mask[wib],
+                                             s_lsum[wib], &s_mlp[0], SURR_ARGS(INV, false));
   }
-  process_trial<MW, Acc, false, INV, true>(items[lo], w - warp_begin[lo], lane, wib,
-                                           s_excl[wib], s_base[wib], s_mask[wib], s_lsum[wib],
-                                           &s_mlp[0]);
+}
+
+// Blocks of a launch over n warps: one warp per trial, or for the surrogate path at most
+// kBlocksPerSM resident blocks per SM (a persistent grid).
+template <int INV>
+int64_t trial_blocks(int64_t n_warps) {
+  int64_t blocks = (n_warps + kWPB<INV> - 1) / kWPB<INV>;
+  if constexpr (INV == 2) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = std::min<int64_t>(blocks, (int64_t)sms * kBlocksPerSM<INV>);
+  }
+  return blocks;
 }
 
 template <int MW, class Acc, bool TRACE, int INV, bool CORR = true>
 cudaError_t launch_one(const TrialParams& p, cudaStream_t st) {
-  const int64_t blocks = (p.n + kWPB<INV> - 1) / kWPB<INV>;
+  const int64_t blocks = trial_blocks<INV>(p.n);
   if (blocks == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
@@ -436,7 +593,7 @@ cudaError_t launch_mode(const TrialParams& p, int mask_words, int precision, boo
 template <int MW, class Acc, int INV>
 cudaError_t launch_batch_mode(const TrialParams* d_items, const int64_t* d_warp_begin,
                               int n_items, int64_t total_warps, cudaStream_t st) {
-  const int64_t blocks = (total_warps + kWPB<INV> - 1) / kWPB<INV>;
+  const int64_t blocks = trial_blocks<INV>(total_warps);
   if (blocks == 0) return cudaSuccess;
   batch_kernel<MW, Acc, INV><<<(unsigned)blocks, kWPB<INV> * 32, 0, st>>>(
       d_items, d_warp_begin, n_items, total_warps);

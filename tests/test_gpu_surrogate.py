@@ -1,6 +1,8 @@
 """The learned surrogate of InvCDF_beta: tensor-core forward and backward kernels against the FP64
-reference network (oracle/mlp.py), training on the GPU, certification, and its use inside the run
-with exact Newton fallback, measured against the FP64 oracle and against the method without it.
+reference network (oracle/mlp.py) and, element by element, against the same network with the
+kernels' rounding points (tests/mlp_emulation.py), training on the GPU on 5e7 exact tuples,
+certification, and its use inside the run with exact fallback, measured against the FP64 oracle
+and against the method without it.
 """
 
 import time
@@ -8,6 +10,7 @@ import time
 import numpy as np
 import pytest
 
+import mlp_emulation as emu
 from oracle import mlp as ref
 from paper_1310_2274_b300 import synth
 
@@ -30,35 +33,44 @@ def batch():
 
 def test_forward_matches_reference_network(ara, batch):
     z, _, _ = batch
-    p = ref.init_params(7)
+    p = emu.scaled_params(7)
     with ara.Context() as c:
-        y = c.mlp_eval(z, params=p)
+        y = c.mlp_eval(z, params=p).astype(np.float64)
+    # element by element against the kernels' arithmetic (BF16 rounding points), within the
+    # bound the hardware tanh's error can reach
+    want, bound = emu.bounds(p, z)
+    assert np.all(np.abs(y - want) <= bound), np.max(np.abs(y - want) / bound)
+    assert np.abs(want).max() > 1.0  # outputs of a trained network's size
+    # and close to the binary64 network throughout
     yr, _ = ref.forward(p, z)
-    # BF16 weights and activations against binary64 throughout
     assert rel_l2(y, yr) <= 2e-2
-    assert np.corrcoef(y, yr)[0, 1] >= 0.999
 
 
 def test_gradient_matches_reference_network(ara, batch):
     z, x, t = batch
-    p = ref.init_params(7)
+    p = emu.scaled_params(7)
     with ara.Context() as c:
         loss, g = c.mlp_grad(p, z, x, t)
-    lr_, gr = ref.loss_grad(p, z, x, t)
-    assert abs(loss - lr_) <= 2e-2 * abs(lr_)
-    parts_g, parts_r = ref.unpack(g.astype(np.float64)), ref.unpack(gr)
+    (_, want_loss, want), bound = emu.bounds(p, z, x, t)
+    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
+    g = g.astype(np.float64)
+    bad = np.abs(g - want) > bound
     names = ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"]
-    for name, a, b in zip(names, parts_g, parts_r):
-        a, b = a.reshape(-1), b.reshape(-1)
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
-        assert cos >= 0.995, (name, cos)
-        assert rel_l2(a, b) <= 8e-2, (name, rel_l2(a, b))
+    for name, gb, wb, bb in zip(names, ref.unpack(g), ref.unpack(want), ref.unpack(bound)):
+        assert np.all(np.abs(gb - wb) <= bb), (name, float(np.max(np.abs(gb - wb) / bb)))
+    assert not bad.any()
+    # and near the binary64 network's gradient, parameter block by block: the BF16 rounding of
+    # the layer gradients before their sums over the batch (which cancel) moves a block by up to
+    # ~8% at this weight scale, as the emulation above, rounding at the same points, shows
+    _, gr = ref.loss_grad(p, z, x, t)
+    for name, a, b in zip(names, ref.unpack(g), ref.unpack(gr)):
+        assert rel_l2(a.reshape(-1), b.reshape(-1)) <= 0.15, name
 
 
 @pytest.fixture(scope="module")
 def trained(ara):
     c = ara.Context(seed=42)
-    rep = c.train_surrogate(n_samples=8_000_000, steps=30_000, batch=8192, lr=3e-3,
+    rep = c.train_surrogate(n_samples=50_000_000, steps=30_000, batch=8192, lr=3e-3,
                             lr_final=3e-5, eps=5e-4, cert_samples=16, seed=3)
     yield c, rep
     c.close()
@@ -120,25 +132,49 @@ def test_surrogate_run_against_oracle_and_gain(ara, oracle, trained):
           f"({fallback / hits:.1%})")
 
 
-def test_surrogate_gain_over_newton_on_paper_sample(ara, trained):
-    # what the network gains over the method without it: the same run with Newton everywhere
-    # against the surrogate with Newton fallback, on 20,000 trials of the paper-scale layer
+def test_surrogate_cost_against_newton_on_paper_sample(ara, trained):
+    """What the network gains over the method without it, on 20,000 trials of the paper-scale
+    layer: it replaces the inversions of the hits it serves (a certified share of them, the rest
+    falling back to Newton-Halley), at PML within 1e-3 of the exact form; and what it costs.  The
+    run cannot be faster than the bookkeeping every form pays (the same layer with every SD zero)
+    plus its fallbacks' share of the Newton-Halley inversion time, which is the bound that keeps
+    this network (82% fallback on this law) slower than the plain form."""
     c, _ = trained
     w = synth.paper(n_trials=20_000)
     yet, elts, layer = c.stage_workload(w)
-    times = {}
-    for mode in ("newton", "surrogate"):
+    z_elts = [c.add_elt(yet, e.event_ids, e.mean, np.zeros(e.n), e.max_exposure) for e in w.elts]
+    t = w.terms
+    z_layer = c.add_layer(z_elts, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+
+    def timed(lay, surrogate):
         c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
-        c.set_option(ara.OPT_SURROGATE, 1 if mode == "surrogate" else 0)
-        c.run(yet, layer, 0, w.yet.n_trials)  # warm
-        t = time.perf_counter()
-        y = c.run(yet, layer, 0, w.yet.n_trials)
-        times[mode] = (time.perf_counter() - t, y)
-    c.set_option(ara.OPT_SURROGATE, 0)
-    c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
-    (tn, yn), (ts, ys) = times["newton"], times["surrogate"]
+        c.set_option(ara.OPT_SURROGATE, 1 if surrogate else 0)
+        c.set_option(ara.OPT_SCHEDULE, ara.SCHED_TRIAL)
+        try:
+            c.run(yet, lay, 0, w.yet.n_trials)  # warm (and the layer's start tables)
+            s0 = c.stats()
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                y = c.run(yet, lay, 0, w.yet.n_trials)
+                ts.append(time.perf_counter() - t0)
+            s1 = c.stats()
+        finally:
+            c.set_option(ara.OPT_SURROGATE, 0)
+            c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+            c.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND)
+        return sorted(ts)[1], y, {k: (s1[k] - s0[k]) / 3 for k in s0}
+
+    tn, yn, _ = timed(layer, False)
+    ts, ys, ds = timed(layer, True)
+    t0, _, _ = timed(z_layer, False)
+    net, fb = ds["surrogate_evals"], ds["inversions"]
+    share = fb / (net + fb)
     pn, _ = c.risk_measures(yn, w.rps)
     ps, _ = c.risk_measures(ys, w.rps)
-    print(f"paper-scale 20k trials: Newton {tn * 1e3:.2f} ms, surrogate {ts * 1e3:.2f} ms, "
-          f"PML rel diff {np.max(np.abs(ps - pn) / pn):.2e}")
+    print(f"paper-scale 20k trials: Newton-Halley {tn * 1e3:.2f} ms, surrogate {ts * 1e3:.2f} ms "
+          f"(speed-up {tn / ts:.2f}), bookkeeping {t0 * 1e3:.2f} ms, network evaluations {net:.0f}, "
+          f"fallback share {share:.1%}, PML rel diff {np.max(np.abs(ps - pn) / pn):.2e}")
+    assert net > 0 and 0.0 < share < 1.0
     assert np.max(np.abs(ps - pn) / pn) <= 1e-3
+    assert ts >= t0 + 0.8 * share * (tn - t0)  # the bound stated above holds on this run
