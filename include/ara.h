@@ -170,7 +170,7 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
  * the sigma_beta_max clamp of §3.3, sigma_beta set to sigma_beta_max (1 - 2^-20) when above it)
  * and the constants of the inversion, then stored as binary32 (32 bytes per record); the record's
  * certified quantile table is built at the same time (2 KB per record, see ARA_OPT_INVERSION;
- * deferred under ARA_TABLES_ON_DEMAND), and its start table (384 bytes per record).
+ * deferred under ARA_TABLES_ON_DEMAND), and its start table (512 bytes per record).
  * The handle number keys the record's uniforms: Philox4x32-10 counter (k, i_lo, elt/4, i_hi),
  * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i.  The arrays may be host or
  * device memory; device memory and page-locked host memory mapped into the device's address

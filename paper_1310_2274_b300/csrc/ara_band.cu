@@ -120,30 +120,6 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, unsigned lo
 // CORR: the launch may carry correlated weights (paper §3.2; P.corr is still checked, since a
 // batch mixes items); without them the draw is the hit's own uniform and the weight load and
 // combination are compiled out.
-// The 32-byte record and the 24-byte start-table piece of a hit under the evict-last policy:
-// while a band is processed its records and start tables are reused from L2.
-__device__ __forceinline__ BetaRec load_rec_keep(const BetaRec* p, unsigned long long keep) {
-  const uint4 a = ld_keep_u4(reinterpret_cast<const uint4*>(p), keep);
-  const uint4 b = ld_keep_u4(reinterpret_cast<const uint4*>(p) + 1, keep);
-  BetaRec r;
-  r.a = __uint_as_float(a.x); r.b = __uint_as_float(a.y);
-  r.mx = __uint_as_float(a.z); r.L0 = __uint_as_float(a.w);
-  r.p0 = __uint_as_float(b.x); r.lnx0 = __uint_as_float(b.y);
-  r.lny0 = __uint_as_float(b.z); r.lns = __uint_as_float(b.w);
-  return r;
-}
-
-__device__ __forceinline__ float start_logit_keep(const float* st, float u,
-                                                  unsigned long long keep) {
-  float tau;
-  const int k = ara_start_piece(u, &tau);
-  const uint2* c2 = reinterpret_cast<const uint2*>(st + k * kStartCoefs);
-  const uint2 a = ld_keep_u2(c2, keep), b = ld_keep_u2(c2 + 1, keep), c = ld_keep_u2(c2 + 2, keep);
-  return ara_start_poly(make_float2(__uint_as_float(a.x), __uint_as_float(a.y)),
-                        make_float2(__uint_as_float(b.x), __uint_as_float(b.y)),
-                        make_float2(__uint_as_float(c.x), __uint_as_float(c.y)), tau);
-}
-
 // INV: 0 certified tables (Newton-Halley fallback for uncertified records), 1 Newton-Halley from
 // the start tables, records and start tables kept in L2 like the table pieces.
 template <int MW, bool CORR, int INV>
@@ -273,11 +249,11 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
             su_draw(u0, cc > 0.0f ? su_uniform_corr_rk(P.rk0, P.rk1, trial, sm.k[ev]) : 0.5f, cc);
         const float u = d.z;
         if constexpr (INV == 1) {
-          const BetaRec rec = load_rec_keep(P.recs + pos, pol.keep);
+          const BetaRec rec = load_rec_policy(P.recs + pos, pol.keep);
           if (!(rec.a > 0.f)) {
             loss = rec.mx;  // sd = 0: the mean (primary uncertainty only)
           } else {
-            const float sl = start_logit_keep(P.starts + (size_t)pos * kStartFloats, u, pol.keep);
+            const float sl = start_logit_policy(P.starts + (size_t)pos * kStartFloats, u, pol.keep);
             const IbetaResult ib = ara_inv_beta<true>(rec, u, sl);
             nc += ib.converged ? 0u : 1u;
             n_inv += 1u;

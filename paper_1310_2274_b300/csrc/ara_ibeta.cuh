@@ -438,14 +438,16 @@ struct TablePiece {
 // ---- start tables for the Newton-Halley inversion ---------------------------------------------
 // Where a record's certified table does not exist (tables on demand, before they pay off) the
 // inversion starts from a coarse table built in binary32 when the ELT is staged: the same
-// coordinate z, 16 pieces of width 4 kTableH, a cubic Hermite of the log-odds L from L and
-// dL/dz at the knots (16 bytes a piece, 256 bytes a record).  It is not certified: it is only a
-// start (~2e-6 from the root in ln x on average, 1.4e-4 at worst over the ELT value law, so a
-// single Halley step lands within ~1e-11), and a piece whose knots failed holds NaN, which sends
-// the inversion back to its analytic start.
+// coordinate z, 16 pieces of width 4 kTableH, a quintic Hermite of the log-odds L from L, dL/dz
+// and d2L/dz2 at the knots.  A piece's six coefficients are padded to one 32-byte sector (512
+// bytes a record), so a hit reads one sector of it.  It is not certified: it is only a start
+// (~2e-6 from the root in ln x on average, 1.7e-4 at worst over the ELT value law, so a single
+// Halley step lands within ~1e-11), and a piece whose knots failed holds NaN, which sends the
+// inversion back to its analytic start.
 constexpr int kStartPieces = 16;
 constexpr int kStartCoefs = 6;                      // quintic Hermite: L, L', L'' at both knots
-constexpr int kStartFloats = kStartPieces * kStartCoefs;
+constexpr int kStartStride = 8;                     // floats a piece takes: one 32-byte sector
+constexpr int kStartFloats = kStartPieces * kStartStride;
 constexpr float kStartInvH = kTableInvH * 0.25f;  // 1 / (4 kTableH)
 
 // Piece and local coordinate of u in a start table.
@@ -475,7 +477,7 @@ ARA_HD float ara_start_poly(float2 c01, float2 c23, float2 c45, float tau) {
 ARA_HD float ara_start_logit(const float* st, float u) {
   float tau;
   const int k = ara_start_piece(u, &tau);
-  const float2* c2 = reinterpret_cast<const float2*>(st + k * kStartCoefs);
+  const float2* c2 = reinterpret_cast<const float2*>(st + k * kStartStride);
 #ifdef __CUDA_ARCH__
   const float2 c01 = __ldg(c2), c23 = __ldg(c2 + 1), c45 = __ldg(c2 + 2);
 #else

@@ -372,7 +372,8 @@ ARA_HD void ara_build_start_record(const BetaRec& br, float* st) {
     ok[i] = conv && isfinite(L[i]) && isfinite(D[i]);
   }
   for (int k = 0; k < kStartPieces; ++k) {
-    float* c = st + k * kStartCoefs;
+    float* c = st + k * kStartStride;
+    c[6] = c[7] = 0.0f;  // padding of the piece's sector
     if (!(ok[k] && ok[k + 1])) {
       for (int j = 0; j < kStartCoefs; ++j) c[j] = ara_bits_to_float(0x7FC00000);
       continue;

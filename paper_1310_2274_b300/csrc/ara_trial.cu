@@ -354,7 +354,7 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
         }
         BetaRec rec;
         if constexpr (INV == 1) {
-          rec = load_rec(P.recs + pos);
+          rec = load_rec_policy(P.recs + pos, pol.keep);
           sd0 = !(rec.a > 0.f);
           mx = rec.mx;
           if (!sd0 || TRACE)
@@ -378,7 +378,8 @@ __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, i
             const IbetaResult ib =
                 INV == 1 ? ara_inv_beta(rec, u,
                                         P.starts != nullptr
-                                            ? ara_start_logit(P.starts + (size_t)pos * kStartFloats, u)
+                                            ? start_logit_policy(P.starts + (size_t)pos *
+                                                                     kStartFloats, u, pol.stream)
                                             : 1e30f)
                          : newton_fallback<false>(P.recs + pos, u);
             x = ib.x;

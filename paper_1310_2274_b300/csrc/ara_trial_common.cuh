@@ -93,13 +93,13 @@ __device__ __forceinline__ int32_t ld_stream_s32(const int32_t* p, unsigned long
                : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ uint2 ld_keep_u2(const uint2* p, unsigned long long pol) {
+__device__ __forceinline__ uint2 ld_pol_u2(const uint2* p, unsigned long long pol) {
   uint2 v;
   asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
                : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ uint4 ld_keep_u4(const uint4* p, unsigned long long pol) {
+__device__ __forceinline__ uint4 ld_pol_u4(const uint4* p, unsigned long long pol) {
   uint4 v;
   asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
@@ -113,7 +113,7 @@ struct Entry<1> {
   uint32_t base;
   uint32_t m0;
   __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
-    const uint2 v = ld_keep_u2(reinterpret_cast<const uint2*>(evt) + e, pol);
+    const uint2 v = ld_pol_u2(reinterpret_cast<const uint2*>(evt) + e, pol);
     Entry r;
     r.base = v.x;
     r.m0 = v.y;
@@ -126,7 +126,7 @@ struct Entry<2> {
   uint32_t base;
   uint32_t m0, m1;
   __device__ static Entry load(const uint32_t* evt, int32_t e, unsigned long long pol) {
-    const uint4 v = ld_keep_u4(reinterpret_cast<const uint4*>(evt) + e, pol);
+    const uint4 v = ld_pol_u4(reinterpret_cast<const uint4*>(evt) + e, pol);
     Entry r;
     r.base = v.x;
     r.m0 = v.y;
@@ -178,6 +178,34 @@ __device__ __forceinline__ BetaRec load_rec(const BetaRec* p) {
   return r;
 }
 
+
+// A hit's 32-byte record and its start-table piece (one 32-byte sector) under an L2 policy:
+// evict-last for records, which both schedules reuse from L2 (57 MB at paper scale); the band
+// schedule keeps its band's start tables too, the trial-major schedule streams them (919 MB
+// swept at random).
+__device__ __forceinline__ BetaRec load_rec_policy(const BetaRec* p, unsigned long long pol) {
+  const uint4 a = ld_pol_u4(reinterpret_cast<const uint4*>(p), pol);
+  const uint4 b = ld_pol_u4(reinterpret_cast<const uint4*>(p) + 1, pol);
+  BetaRec r;
+  r.a = __uint_as_float(a.x); r.b = __uint_as_float(a.y);
+  r.mx = __uint_as_float(a.z); r.L0 = __uint_as_float(a.w);
+  r.p0 = __uint_as_float(b.x); r.lnx0 = __uint_as_float(b.y);
+  r.lny0 = __uint_as_float(b.z); r.lns = __uint_as_float(b.w);
+  return r;
+}
+
+// ara_start_logit with the piece loaded under the policy pol.
+__device__ __forceinline__ float start_logit_policy(const float* st, float u,
+                                                    unsigned long long pol) {
+  float tau;
+  const int k = ara_start_piece(u, &tau);
+  const uint4* c4 = reinterpret_cast<const uint4*>(st + k * kStartStride);
+  const uint4 a = ld_pol_u4(c4, pol);
+  const uint2 b = ld_pol_u2(reinterpret_cast<const uint2*>(c4 + 1), pol);
+  return ara_start_poly(make_float2(__uint_as_float(a.x), __uint_as_float(a.y)),
+                        make_float2(__uint_as_float(a.z), __uint_as_float(a.w)),
+                        make_float2(__uint_as_float(b.x), __uint_as_float(b.y)), tau);
+}
 
 // The Newton inversion for the rare record whose table failed certification (and for the
 // surrogate's rejected cells), kept out of line so that its registers do not weigh on the table
