@@ -95,12 +95,6 @@ __global__ void check_offsets_fini(OffsetCheck* out) {
 
 // ---- ELT record preparation (FP64, once per record) --------------------------------------------
 
-// I_x(a,b) in binary64 (DLMF 8.17.22, with the symmetry DLMF 8.17.4 past (a+1)/(a+b+2)).
-__device__ double betainc_f64(double a, double b, double x) {
-  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
-  return exp(ara_ln_betainc_f64(a, b, log(x), lnB));
-}
-
 // flags bit 3: id out of range; bit 4: mean <= 0 or an SD < 0 or non-finite; bit 5: max <= mean
 // with sd > 0; dup[e] counts records per event (a count above one is a duplicate, bit 6).
 // sdc (NULL: zero) is the correlated SD of paper §3.1: sigma = sd + sdc feeds the moments and
@@ -147,17 +141,9 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
       const double rr = sig_max / sig_b;
       const double k = rr * rr - 1.0;
       const double a = mu_b * k, b = (1.0 - mu_b) * k;
-      const double s = a + b;
-      const double lnx0 = log(a / s), lny0 = log(b / s);
-      const double lnB = lgamma(a) + lgamma(b) - lgamma(s);
-      rec.a = (float)a;
-      rec.b = (float)b;
+      double lnB;
+      rec = ara_beta_rec_f64(a, b, &lnB);  // p0 from the same ln B(a,b): one set of lgamma calls
       rec.mx = (float)m;
-      rec.L0 = (float)(a * lnx0 + b * lny0 - lnB);
-      rec.p0 = (float)betainc_f64(a, b, a / s);
-      rec.lnx0 = (float)lnx0;
-      rec.lny0 = (float)lny0;
-      rec.lns = (float)log(s);
       ab = make_double2(a, b);
       if (!(rec.a > 0.f) || !(rec.b > 0.f)) f |= 16u;  // alpha or beta outside binary32 range
     }
