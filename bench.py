@@ -3,11 +3,11 @@
 
 A step is one whole analysis of the paper-scale layer (800,000 trials x 1,000 events x 16 ELTs)
 from raw inputs already resident in HBM: stage the YET (ara_create_yet), the 16 ELTs
-(ara_add_elt) and the layer (ara_add_layer), run Algorithm 1 (ara_run -> YLT; a single pass
-inverts the beta CDF by Newton-Halley from start tables: certified tables would cost more to
-build than they save), take PML/TVaR at 1-in-100/250/500/1000 (ara_risk_measures), and free
-everything.  The metric is trial-event-ELT evaluations per second, N * K * J / step time, i.e.
-the paper's "s per 800k x 1000 run".  Beside it: the same analysis re-priced with the tables
+(ara_add_elt) and the layer (ara_add_layer), run Algorithm 1 (ara_run -> YLT; with ~400 hits per
+record a single pass buys the records' certified quantile tables, built in binary32 in one launch,
+and inverts the beta CDF through them), take PML/TVaR at 1-in-100/250/500/1000
+(ara_risk_measures), and free everything.  The metric is trial-event-ELT evaluations per
+second, N * K * J / step time, i.e. the paper's "s per 800k x 1000 run".  Beside it: the same analysis re-priced with the tables
 resident (the serving situation), the step through host buffers (e2e), the error of PML/TVaR
 against the FP64 oracle, the precision study, the learned surrogate, serving, and the CPU
 oracle's rate.  Prints one JSON line (rank 0).
@@ -65,6 +65,9 @@ BYTES_PER_TRIAL = 8.0
 # Device-counted FP32 work of the Newton-Halley inversion (the device algorithm's own trip
 # counts): continued-fraction term 14.25 ops; iteration 17 ops + 4 calls for the Newton step and
 # 10 for Halley's correction; per inversion 14 + 2.
+# inversions the table build performs per record with sd > 0: a knot and a midpoint check per
+# piece, plus the analytic start of each of the record's four chains
+BUILD_INVERSIONS_PER_RECORD = 2 * 64 + 4
 FLOP_PER_CF_TERM = 14.25
 FLOP_PER_NEWTON = 17.0 + 4.0 + 10.0
 FLOP_PER_INVERSION = 14.0 + 2.0
@@ -109,7 +112,7 @@ def workload_config(a, world, l2_note=True):
                         "each rank's k_max largest year losses" if world > 1 else
                         "trial batch on one GPU"),
         "l2": "inputs larger than L2: each step stages 6.4 GB of YET (event ids and "
-              "timestamps) and its Newton-Halley run streams the 3.2 GB of event ids",
+              "timestamps) and its run streams the 3.2 GB of event ids",
     }
 
 
@@ -228,6 +231,10 @@ def run_reference(a):
 PROFILE_FILES = {
     "band": ("band_kernel_table_200000x1000x16.md",
              ("ara_band.cu", "ara_trial_common.cuh", "ara_ibeta.cuh", "ara_philox.cuh")),
+    "table_trial": ("trial_kernel_table_200000x1000x16.md",
+                    ("ara_trial.cu", "ara_trial_common.cuh", "ara_ibeta.cuh", "ara_philox.cuh")),
+    "table_build": ("build_tables_kernel_paper_16_elts.md",
+                    ("ara_table.cu", "ara_table.cuh", "ara_ibeta.cuh")),
     "newton_trial": ("trial_kernel_newton_50000x1000x16.md",
                      ("ara_trial.cu", "ara_trial_common.cuh", "ara_ibeta.cuh", "ara_philox.cuh")),
 }
@@ -354,8 +361,8 @@ def run_ours(a):
         ctx.free_yet(yet)
         return out
 
-    # ---- the headline: one whole analysis per step (tables on demand: this single pass of 400
-    # expected hits per record inverts by Newton-Halley from start tables) ---------------------
+    # ---- the headline: one whole analysis per step (tables on demand: this single pass of ~400
+    # expected hits per record buys them, all 16 ELTs' in one launch, then runs trial-major) ----
     ctx.set_option(ara.OPT_TABLES, ara.TABLES_ON_DEMAND)
     for _ in range(a.warmup):
         cold_step(False)
@@ -430,18 +437,25 @@ def run_ours(a):
     def run_layer(l=None):
         ctx.run(yet, layer if l is None else l, 0, n, out=ylt, stream=stream)
 
-    # Newton-Halley on both schedules (the band-major YET copy does not exist yet: trial-major
-    # first, as in the headline step; the band schedule after the table runs below made it)
+    # the table kernel alone, trial-major as in the headline step (tables resident)
+    ctx.set_option(ara.OPT_SCHEDULE, ara.SCHED_TRIAL)
+    run_layer()
+    table_trial_ms = time_calls(run_layer, nrep, stream, dev)
+    # Newton-Halley on both schedules (trial-major first: the band-major copy does not exist yet;
+    # the band schedule after the table runs below made it)
     ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
     run_layer()
     torch.cuda.synchronize(dev)
     sn0 = ctx.stats()
     newton_trial_ms = time_calls(run_layer, nrep, stream, dev)
     sn1 = ctx.stats()
+    ylt_newton = ylt.cpu().numpy().copy()
+    pml_n, tvar_n = ctx.risk_measures(ylt, rps)
     ctx.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
     dn = {k: (sn1[k] - sn0[k]) / nrep for k in sn0}
 
     # ---- re-pricing: the same layer with its certified tables resident (band schedule) --------
+    ctx.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND)  # makes the band-major copy at once
     run_layer()
     s2 = ctx.stats()
     rep_ev = [ev_pair() for _ in range(a.steps)]
@@ -463,34 +477,61 @@ def run_ours(a):
     run_layer()
     newton_band_ms = time_calls(run_layer, nrep, stream, dev)
     ctx.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
-    ctx.set_option(ara.OPT_SCHEDULE, ara.SCHED_TRIAL)
-    run_layer()
-    table_trial_ms = time_calls(run_layer, nrep, stream, dev)
-    ctx.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND)
 
-    # roofline of the headline's dominant kernel: the Newton-Halley trial kernel.  Unit: one
-    # beta inversion; per-unit work W_INV frozen from the oracle's algorithm.
+    # roofline of the headline's run call (SURVEY §8(d)'s unit: one beta inversion per hit, the
+    # per-unit work W_INV frozen from the oracle's algorithm): the binary32 table build (one
+    # launch over the 16 ELTs), the layer's table gather and the trial-major table kernel
     n_inv = d["inversions"] + d["table_evals"] + d["surrogate_evals"]
     achieved = n_inv * W_INV / (run_ms * 1e-3) / 1e12
-    prof = profile_for_current_kernel("newton_trial")
-    traffic = None
-    if prof.get("dram_bytes_per_launch") is not None:
-        traffic = prof["dram_bytes_per_launch"] * n / 800_000  # summaries state 800k launches
-    flops = (FLOP_PER_CF_TERM * dn["cf_terms"] + FLOP_PER_NEWTON * dn["newton"] +
-             FLOP_PER_INVERSION * dn["inversions"])
+    build_ms = max(run_ms - table_trial_ms, 1e-3)  # the build and the gather
+    n_sd = sum(int(np.count_nonzero(e.sd > 0)) for e in elts_h)
+    build_inv = n_sd * BUILD_INVERSIONS_PER_RECORD
+    prof_t = profile_for_current_kernel("table_trial")
+    prof_bt = profile_for_current_kernel("table_build")
+    bytes_trial = (BYTES_PER_OCCURRENCE * n * a.events + BYTES_PER_TABLE_EVAL * d["table_evals"]
+                   + BYTES_PER_TRIAL * n)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-        "frac": achieved / alu_peak, "traffic": traffic,
-        "kernel": "trial_kernel, Newton-Halley inversion from start tables (one warp per trial); "
-                  "timed as the step's ara_run call (the layer's start-table packing, the "
-                  "kernel), CUDA events inside the timed region",
-        "kernel_ms": run_ms, "kernel_only_ms": newton_trial_ms,
-        "frac_kernel_only": n_inv * W_INV / (newton_trial_ms * 1e-3) / 1e12 / alu_peak,
-        "inversions_per_launch": n_inv,
+        "frac": achieved / alu_peak,
+        "traffic": (prof_t["dram_bytes_per_launch"] * n / 800_000
+                    if prof_t.get("dram_bytes_per_launch") else None),
+        "kernel": "the step's ara_run call: build_tables_kernel (the 16 ELTs' certified tables, "
+                  "132 binary32 Newton-Halley inversions per record), the layer's table gather, "
+                  "trial_kernel with the table inversion (one warp per trial); CUDA events "
+                  "inside the timed region; traffic: the table kernel's",
+        "kernel_ms": run_ms, "units_per_launch": n_inv,
+        "unit_of_work": "one beta inversion per hit (W_inv each, the paper method's work): the "
+                        "tables reuse each record's inversions across its ~400 hits, so the run "
+                        "does less arithmetic than the units it is credited with",
         "w_inv": {"ops": W_INV_OPS, "library_calls": W_INV_CALLS,
                   "source": "oracle counters, 1,076,084 paper-scale inversions"},
         "peak_source": f"FP32 issue peak 2 x {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
                        f"{sm_mhz:.0f} MHz (derived; {peak_src} SM clock)",
+        "build": {"ms": build_ms, "inversions": build_inv,
+                  "achieved": build_inv * W_INV / (build_ms * 1e-3) / 1e12,
+                  "frac": build_inv * W_INV / (build_ms * 1e-3) / 1e12 / alu_peak,
+                  "note": "run call minus the table kernel timed alone; inversions: 2 x 64 "
+                          "knots and midpoints + 4 chain starts per record with sd > 0",
+                  "ncu": prof_bt.get("metrics")},
+        "table_kernel": {"ms": table_trial_ms, "bytes_per_launch": bytes_trial,
+                         "hbm_achieved": bytes_trial / (table_trial_ms * 1e-3) / 1e9,
+                         "hbm_peak": hbm_peak,
+                         "hbm_frac": bytes_trial / (table_trial_ms * 1e-3) / 1e9 / hbm_peak,
+                         "ncu": prof_t.get("metrics")},
+    }
+    prof = profile_for_current_kernel("newton_trial")
+    flops = (FLOP_PER_CF_TERM * dn["cf_terms"] + FLOP_PER_NEWTON * dn["newton"] +
+             FLOP_PER_INVERSION * dn["inversions"])
+    n_inv_n = dn["inversions"] + dn["table_evals"]
+    newton_roofline = {
+        "bound": "alu", "achieved": n_inv_n * W_INV / (newton_trial_ms * 1e-3) / 1e12,
+        "peak": alu_peak, "unit": "TFLOP/s",
+        "frac": n_inv_n * W_INV / (newton_trial_ms * 1e-3) / 1e12 / alu_peak,
+        "traffic": (prof["dram_bytes_per_launch"] * n / 800_000
+                    if prof.get("dram_bytes_per_launch") else None),
+        "kernel": "trial_kernel, Newton-Halley inversion from start tables (one warp per "
+                  "trial), tables absent; timed alone",
+        "kernel_ms": newton_trial_ms, "inversions_per_launch": n_inv_n,
         "device_counted": {"flops_per_launch": flops,
                            "achieved": flops / (newton_trial_ms * 1e-3) / 1e12,
                            "frac": flops / (newton_trial_ms * 1e-3) / 1e12 / alu_peak,
@@ -643,16 +684,20 @@ def run_ours(a):
         "clocks": clk,
         "roofline": roofline,
         "step": {"what": "ara_create_yet (device arrays: copy + validation) + 16 x ara_add_elt "
-                         "(device arrays: records, start tables) + ara_add_layer + ara_run + "
-                         "ara_risk_measures + frees; tables on demand (this single pass runs "
-                         "Newton-Halley)",
+                         "(device arrays: records) + ara_add_layer + ara_run + "
+                         "ara_risk_measures + frees; tables on demand (this single pass buys "
+                         "them: one build launch over the 16 ELTs, then the trial-major table "
+                         "kernel)",
                  "run_ms": run_ms, "phases_ms": step_phases,
-                 "per_launch": {k: d[k] for k in ("hits", "inversions",
-                                                                    "newton", "cf_terms")},
+                 "per_launch": {k: d[k] for k in ("hits", "table_evals", "inversions",
+                                                  "newton", "cf_terms")},
                  "risk_measures": {"rps": rps, "pml": pml_cold, "tvar": tvar_cold}},
         "repricing": repricing,
         "newton_path": {"trial_major_ms": newton_trial_ms, "band_ms": newton_band_ms,
-                        "band_note": "band schedule once the YET's band-major copy exists"},
+                        "band_note": "band schedule once the YET's band-major copy exists",
+                        "roofline": newton_roofline,
+                        "risk_measures": {"pml": [float(v) for v in pml_n],
+                                          "tvar": [float(v) for v in tvar_n]}},
         "schedules_ms": {"table_band": band_ms, "table_trial": table_trial_ms,
                          "newton_trial": newton_trial_ms, "newton_band": newton_band_ms},
         "precision": precision,
@@ -690,7 +735,8 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_oracle:
         result["oracle_error"] = oracle_error(
             a, yet_h, elts_h, terms, rps,
-            {"newton_single_pass": (ylt_cold, pml_cold, tvar_cold, list(cold_handles)),
+            {"single_pass": (ylt_cold, pml_cold, tvar_cold, list(cold_handles)),
+             "newton": (ylt_newton, pml_n, tvar_n, elts),
              "table_repricing": (ylt_table, pml_t, tvar_t, elts),
              "kahan32": (ylt_kahan, kp, kt, elts),
              "surrogate": ylt_surr + (elts,) if ylt_surr is not None else None},
@@ -1001,9 +1047,10 @@ def e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream):
     steps = max(1, min(a.steps, 5))
 
     def timed(policy, host_yet):
-        # tables on demand: one pass of this workload (400 expected hits per record) is below the
-        # break-even of building them, so the run takes Newton's method; eager builds every table
-        # at staging.  A host-resident YET is streamed by the run, its copy overlapping the run.
+        # tables on demand: one pass of this workload (~400 expected hits per record) is above
+        # the break-even of building them, so the run builds them first (one launch over the 16
+        # ELTs); eager builds each ELT's at staging.  A host-resident YET is streamed by the run,
+        # its copy overlapping the run.
         ctx.set_option(ara.OPT_TABLES, policy)
         try:
             for _ in range(min(a.warmup, 2)):
@@ -1026,7 +1073,7 @@ def e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": steps,
             "yet": "host-resident, its event ids streamed by the run (copy overlapping compute); "
                    "timestamps checked on host threads meanwhile",
-            "tables": "on demand (rent-or-buy): this single pass runs Newton's method",
+            "tables": "on demand (rent-or-buy): this single pass builds them, then uses them",
             "resident_yet_ms_per_step": dt_resident * 1e3,
             "resident_yet_eager_tables_ms_per_step": dt_eager * 1e3,
             "path": "ara_create_yet_host + 16 x ara_add_elt + ara_add_layer from pinned host "

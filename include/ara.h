@@ -71,14 +71,17 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 /* Options settable after creation: ARA_OPT_PRECISION (value ARA_ACC_*), ARA_OPT_SEED,
  * ARA_OPT_SURROGATE (0/1), ARA_OPT_INVERSION (value ARA_INV_*), ARA_OPT_SCHEDULE (ARA_SCHED_*).
  * Inversion of the beta CDF (paper §3.3, InvCDF_beta):
- *   ARA_INV_TABLE (default): each record's quantile function, tabulated when its ELT is staged
- *     (32 quintic pieces per tail in t = sqrt(-2 ln u), certified at every piece's midpoint to
- *     1e-6 relative in x against the Newton inversion); records failing certification use Newton;
+ *   ARA_INV_TABLE (default): each record's quantile function, tabulated (ARA_OPT_TABLES says
+ *     when): 32 quintic pieces per tail in t = sqrt(-2 ln u), 2 KB per record, built from
+ *     binary32 Newton-Halley inversions at the knots and checked at every piece's midpoint
+ *     against that inversion: within 1e-6 relative in x / (1 - x), plus the binary32 rounding of
+ *     the log-odds and of the inversion itself (the latter capped at 1e-5); records failing the
+ *     check use Newton;
  *   ARA_INV_NEWTON: Halley's method (Newton's step with the free second derivative) in ln x on
  *     the continued fraction for every hit, started from the record's start table (16 binary32
- *     quintic pieces of the log-odds, built when the ELT is staged, 384 bytes per record), one
- *     step in almost every case; also used by runs over ELTs whose certified tables are deferred
- *     (ARA_OPT_TABLES). */
+ *     quintic pieces of the log-odds, 512 bytes per record, built when a run or a server first
+ *     needs them), one step in almost every case; also used by runs over ELTs whose tables are
+ *     deferred (ARA_OPT_TABLES). */
 #define ARA_OPT_PRECISION 1
 #define ARA_OPT_SEED 2
 #define ARA_OPT_SURROGATE 3
@@ -86,38 +89,46 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
 #define ARA_INV_TABLE 0
 #define ARA_INV_NEWTON 1
 /* ARA_OPT_SCHEDULE (value ARA_SCHED_*):
- *   ARA_SCHED_BAND (default): the catalogue is cut into bands of 2^w events (w chosen per layer
- *     so that one band's lookup entries, record headers and tables fit in L2); the layer's first
- *     run with the table inversion makes a band-major copy of the YET's event ids for that w,
- *     once per w and YET (4 bytes per occurrence plus 4 per (band, trial)), and ara_run visits
- *     the work band by band, each band's year sums kept apart and combined exactly.  A run with
- *     the Newton-Halley inversion takes this schedule too where that copy exists already (it
- *     never makes one: a single pass gains far less than the copy costs);
+ *   ARA_SCHED_AUTO (default): trial-major (as ARA_SCHED_TRIAL) until the runs of the table
+ *     inversion over a YET have covered ARA_BAND_BUY_PASSES times its occurrences, then band-major
+ *     (as ARA_SCHED_BAND): the band-major copy is bought once it has paid for itself in the
+ *     time it saves per occurrence (rent-or-buy, never more than twice the cheaper of the two
+ *     in hindsight), so a single pass never makes one;
+ *   ARA_SCHED_BAND: the catalogue is cut into bands of 2^w events (w chosen per layer so that
+ *     one band's lookup entries, record headers and tables fit in L2); the layer's first run
+ *     with the table inversion makes a band-major copy of the YET's event ids for that w, once
+ *     per w and YET (4 bytes per occurrence plus 4 per (band, trial)), and ara_run visits the
+ *     work band by band, each band's year sums kept apart and combined exactly.  A run with the
+ *     Newton-Halley inversion takes this schedule too where that copy exists already (it never
+ *     makes one: a single pass gains far less than the copy costs);
  *   ARA_SCHED_TRIAL: one warp per trial over its events in order (also used by the surrogate
  *     inversion, by per-occurrence outputs, and by layers whose YET cannot be banded: more than
  *     2^32 occurrences, trials longer than 2^(32-w) events, or more than 512 bands).
- * Both give the same hits, uniforms, losses and year losses, bit for bit. */
+ * All give the same hits, uniforms, losses and year losses, bit for bit. */
 #define ARA_OPT_SCHEDULE 5
 #define ARA_SCHED_BAND 0
 #define ARA_SCHED_TRIAL 1
+#define ARA_SCHED_AUTO 2
+#define ARA_BAND_BUY_PASSES 3.0
 /* ARA_OPT_BAND_WIDTH: the band width 2^w (value w in 10..20) of layers created afterwards;
  * 0 (default) chooses w per layer from its record count.  Results do not depend on w. */
 #define ARA_OPT_BAND_WIDTH 6
 /* ARA_OPT_TABLES: when the certified quantile tables of ELTs staged afterwards are built.
  *   ARA_TABLES_EAGER (default): by ara_add_elt.
  *   ARA_TABLES_ON_DEMAND: not at staging; a run of the table inversion over a layer whose ELTs
- *     lack tables uses Newton's method instead, and the ELTs' tables are built (and the layer's
- *     packed copy gathered) before the first run at which each such ELT's Newton work so far
- *     plus this run's would reach the cost of building its tables: rent-or-buy, never more than
- *     twice the cheaper of the two in hindsight.  Work is counted in expected hits per record,
- *     (occurrences of the run's trials) / (catalogue size), against ARA_TABLE_BUY_HITS, the
- *     measured break-even of build time per record over the per-hit saving of a table.  Results
- *     of a run are those of the inversion it used (both are checked against the oracle).
+ *     lack tables uses Newton's method instead, and the ELTs' tables are built together (and
+ *     the layer's packed copy gathered) before the first run at which each such ELT's Newton
+ *     work so far plus this run's would reach the cost of building its tables: rent-or-buy,
+ *     never more than twice the cheaper of the two in hindsight.  Work is counted in expected
+ *     hits per record, (occurrences of the run's trials) / (catalogue size), against
+ *     ARA_TABLE_BUY_HITS, the measured break-even of build time per record over the per-hit
+ *     saving of a table (a paper-scale pass, ~400 hits per record, buys at once).  Results of a
+ *     run are those of the inversion it used (both are checked against the oracle).
  *   A server (ara_server_create) builds every missing table of its YET's ELTs when created. */
 #define ARA_OPT_TABLES 7
 #define ARA_TABLES_EAGER 0
 #define ARA_TABLES_ON_DEMAND 1
-#define ARA_TABLE_BUY_HITS 2100.0
+#define ARA_TABLE_BUY_HITS 260.0
 /* ARA_OPT_STREAM_CHUNK: occurrences per copied chunk of a host-resident YET's runs (1024 .. 2^30;
  * default 2^26, a ring of four buffers of 4 bytes per occurrence on the device; a chunk always
  * holds whole trials, so it grows to the longest trial if needed). */

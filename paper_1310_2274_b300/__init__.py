@@ -26,9 +26,9 @@ OPT_SCHEDULE = 5
 OPT_BAND_WIDTH = 6
 OPT_TABLES = 7
 TABLES_EAGER, TABLES_ON_DEMAND = 0, 1
-TABLE_BUY_HITS = 2100.0  # expected hits per record at which on-demand tables are built
+TABLE_BUY_HITS = 260.0  # expected hits per record at which on-demand tables are built
 OPT_STREAM_CHUNK = 8
-SCHED_BAND, SCHED_TRIAL = 0, 1
+SCHED_BAND, SCHED_TRIAL, SCHED_AUTO = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",
           5: "inversion did not converge", 6: "busy", 7: "no CUDA device"}
 

@@ -192,8 +192,8 @@ ara_status ara_set_option(ara_ctx* ctx, int32_t option, int64_t value) {
       ctx->table_policy = (int32_t)value;
       return ARA_OK;
     case ARA_OPT_SCHEDULE:
-      if (value != ARA_SCHED_BAND && value != ARA_SCHED_TRIAL)
-        return fail(ctx, ARA_ERR_INVALID_ARG, "schedule must be ARA_SCHED_BAND or ARA_SCHED_TRIAL");
+      if (value != ARA_SCHED_BAND && value != ARA_SCHED_TRIAL && value != ARA_SCHED_AUTO)
+        return fail(ctx, ARA_ERR_INVALID_ARG, "schedule must be ARA_SCHED_AUTO, _BAND or _TRIAL");
       ctx->schedule = (int32_t)value;
       return ARA_OK;
   }
@@ -400,21 +400,17 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
   double *d_mean = nullptr, *d_sd = nullptr, *d_sdc = nullptr, *d_mx = nullptr;
   unsigned int* d_dup = nullptr;
   unsigned long long* d_uncert = nullptr;
-  double2* d_ab64 = nullptr;
   unsigned long long uncert = 0;
   cudaError_t err;
-  // the input copies, duplicate marks and (alpha, beta) of eagerly built tables are staging
-  // scratch; deferred tables keep (alpha, beta) in e.ab64
+  // the input copies and duplicate marks are staging scratch; the start tables of the
+  // Newton-Halley inversion are built when a run first needs them
   auto cleanup = [&]() { cudaStreamSynchronize(ctx->stream); };
   const size_t scratch = scratch_bytes<double>(n) * (sd_corr ? 4 : 3) +
                          scratch_bytes<unsigned int>(y.catalog) +
-                         scratch_bytes<unsigned long long>(1) +
-                         (defer ? 0 : scratch_bytes<double2>(n));
+                         scratch_bytes<unsigned long long>(1);
   if ((err = obj_alloc(ctx, &e.ids, n)) != cudaSuccess ||
       (err = obj_alloc(ctx, &e.recs, n)) != cudaSuccess ||
-      (err = obj_alloc(ctx, &e.starts, n * kStartFloats)) != cudaSuccess ||
       (!defer && (err = obj_alloc(ctx, &e.tables, n * kTablePieces)) != cudaSuccess) ||
-      (defer && (err = obj_alloc(ctx, &e.ab64, n)) != cudaSuccess) ||
       (sd_corr && (err = obj_alloc(ctx, &e.corr, n)) != cudaSuccess) ||
       (err = ensure_scratch(ctx, scratch)) != cudaSuccess) {
     cudaGetLastError();
@@ -429,7 +425,6 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
   if (sd_corr) d_sdc = sc.take<double>(n);
   d_dup = sc.take<unsigned int>(y.catalog);
   d_uncert = sc.take<unsigned long long>(1);
-  d_ab64 = defer ? e.ab64 : sc.take<double2>(n);
   // inputs the device can read where they are (device memory, mapped page-locked host memory)
   // are read in place by the staging kernel, which also writes the ids' device copy; the others
   // are copied first.  (Reads over PCIe by the kernel do not queue behind other copies, such as
@@ -450,12 +445,10 @@ ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t*
       (err = launch_prepare_elt(n, r_ids ? r_ids : e.ids, r_ids ? e.ids : nullptr,
                                 r_mean ? r_mean : d_mean, r_sd ? r_sd : d_sd,
                                 sd_corr ? (r_sdc ? r_sdc : d_sdc) : nullptr, r_mx ? r_mx : d_mx,
-                                y.catalog, e.recs, d_ab64, e.corr, d_dup, ctx->d_flags,
+                                y.catalog, e.recs, e.corr, d_dup, ctx->d_flags,
                                 ctx->stream)) != cudaSuccess ||
-      (err = launch_build_starts(n, e.recs, e.starts, ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-      (!defer &&
-       (err = launch_build_tables(n, e.recs, d_ab64, e.tables, d_uncert, ctx->stream)) != cudaSuccess) ||
+      (!defer && (err = launch_build_tables(one_job(e), d_uncert, ctx->stream)) != cudaSuccess) ||
       (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
@@ -649,8 +642,8 @@ ara_status ara_build_layer(ara_ctx* ctx, const int32_t* elts, int32_t n_elts, do
   }
   memcpy(&L.ev_bound, &ev_bits, sizeof(float));
   // band-major copy of the YET at this layer's band width (one per width and YET): used if it
-  // exists, else made at the first run that takes the band schedule (a single pass that inverts
-  // by Newton's method never needs it)
+  // exists, else made by a run of the table inversion once the schedule asks for it (at once
+  // under ARA_SCHED_BAND, once it pays under ARA_SCHED_AUTO; a Newton pass never makes one)
   const int log2w = ctx->band_log2w > 0 ? ctx->band_log2w : choose_band_log2w(C, L.n_packed);
   bool banded = false;
   for (const auto& v : ctx->yets[yet].bands) banded = banded || v.log2w == log2w;

@@ -48,7 +48,7 @@ struct ara_ctx {
   int64_t ylt_tmp_cap = 0;
   unsigned long long* d_ysum = nullptr;  // year sums in grid units (band-major runs)
   int64_t ysum_cap = 0;
-  int32_t schedule = 0;                  // ARA_SCHED_BAND or ARA_SCHED_TRIAL
+  int32_t schedule = ARA_SCHED_AUTO;     // ARA_SCHED_*
   int32_t table_policy = 0;              // ARA_TABLES_EAGER or ARA_TABLES_ON_DEMAND
   uint32_t* d_sel = nullptr;             // top-k selection: flags, positions, scan scratch
   int64_t sel_cap = 0;
@@ -102,8 +102,9 @@ int layer_inversion(const ara_ctx* ctx, const LayerDev& L);
 // With band_ok, a run that takes the band schedule first makes the layer's band-major YET copy
 // if it is still wanted.
 ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n, bool band_ok);
-// Builds every missing table of the live ELTs of a YET (servers need them).
+// Builds every missing table (or start table) of the live ELTs of a YET (servers need them).
 ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet);
+ara_status ensure_yet_starts(ara_ctx* ctx, int32_t yet);
 TrialParams make_params(ara_ctx* ctx, const YetDev& Y, const LayerDev& L, int64_t t0, int64_t n,
                         double* d_ylt);
 // The stream ring with buffers of at least cap ids, the copy stream and the hand-over events.

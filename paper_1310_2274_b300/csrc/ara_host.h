@@ -141,9 +141,19 @@ inline void free_elt(ara_ctx* c, EltDev& e) {
   obj_free(c, e.recs);
   obj_free(c, e.tables);
   obj_free(c, e.corr);
-  obj_free(c, e.ab64);
   obj_free(c, e.starts);
   e = EltDev();
+}
+
+// The table build of one ELT as a batch of one.
+inline TableJobs one_job(const EltDev& e) {
+  TableJobs j{};
+  j.recs[0] = e.recs;
+  j.tables[0] = e.tables;
+  j.first[0] = 0;
+  j.first[1] = e.n;
+  j.n = 1;
+  return j;
 }
 
 inline ara_status set_device(ara_ctx* c) {

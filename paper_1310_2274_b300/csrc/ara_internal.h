@@ -46,6 +46,7 @@ struct YetDev {
   int32_t* ids = nullptr;    // [n_occ] (timestamps are checked at staging and not kept)
   int64_t* offsets = nullptr;  // [n_trials + 1]
   BandedYet bands[kMaxBandVariants];  // band-major copies, built on demand per band width
+  double band_rent_occ = 0.0;  // occurrences run trial-major by the table inversion (schedule AUTO)
 };
 
 // One staged ELT: event ids and the derived per-record constants, in the caller's order.
@@ -59,7 +60,7 @@ struct EltDev {
   float* corr = nullptr;     // [n] normalised correlated weights (NULL: every sigma_C = 0)
   int64_t n_uncertified = 0; // records whose table failed certification
   float* starts = nullptr;   // [n * kStartFloats] start tables of the Newton-Halley inversion
-  double2* ab64 = nullptr;   // [n] binary64 (alpha, beta), kept until the tables are built
+                             // (built when a run or a server first needs them)
   double rent_hits = 0.0;    // expected hits per record served by Newton while tables were absent
 };
 
@@ -169,10 +170,10 @@ cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64
                                       const int64_t* offsets, int64_t t_begin, int64_t n,
                                       int32_t catalog, unsigned int* d_flags, cudaStream_t st);
 // Checks and converts an ELT's records (ids, mean, sd, optional correlated sd, max exposure, all
-// device-readable) into recs / ab64 / corr; ids_out (nullable) receives a copy of the ids.
+// device-readable) into recs / corr; ids_out (nullable) receives a copy of the ids.
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
                                const double* mean, const double* sd, const double* sdc,
-                               const double* mx, int32_t catalog, BetaRec* recs, double2* ab64,
+                               const double* mx, int32_t catalog, BetaRec* recs,
                                float* corr, unsigned int* d_dup, unsigned int* d_flags,
                                cudaStream_t st);
 cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
@@ -196,9 +197,17 @@ cudaError_t launch_layer_event_bound(const uint32_t* d_evt, int mask_words, int6
                                      cudaStream_t st);
 // starts[n * kStartFloats]: the records' start tables of the Newton-Halley inversion
 cudaError_t launch_build_starts(int64_t n, const BetaRec* recs, float* starts, cudaStream_t st);
-// ab64[n]: each record's (alpha, beta) in binary64, as written by launch_prepare_elt.
-cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
-                                TablePiece* tables, unsigned long long* d_uncertified,
+// The certified tables of up to kMaxTableJobs ELTs in one launch: job j's records recs[j] and
+// its tables tables[j] (kTablePieces pieces each); first[j] records come before job j (first[n]:
+// all of them).  d_uncertified[j] (zeroed by the caller) counts job j's uncertified records.
+constexpr int kMaxTableJobs = 64;
+struct TableJobs {
+  const BetaRec* recs[kMaxTableJobs];
+  TablePiece* tables[kMaxTableJobs];
+  int64_t first[kMaxTableJobs + 1];
+  int n;
+};
+cudaError_t launch_build_tables(const TableJobs& jobs, unsigned long long* d_uncertified,
                                 cudaStream_t st);
 // dst[i * kStartFloats ...] = the start table at d_src[i], for the n packed records of a layer
 cudaError_t launch_gather_starts(int64_t n, const float* const* d_src, float* dst, cudaStream_t st);

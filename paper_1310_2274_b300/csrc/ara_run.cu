@@ -36,7 +36,7 @@ static ara_status check_run_args(ara_ctx* ctx, int32_t yet, int32_t layer, int64
 }
 
 bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
-  return layer_inversion(ctx, L) == 0 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
+  return layer_inversion(ctx, L) == 0 && ctx->schedule != ARA_SCHED_TRIAL && L.band_log2w > 0 &&
          ctx->cfg.precision == ARA_ACC_FP64;
 }
 
@@ -44,7 +44,7 @@ bool uses_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
 // band-major copy exists already (made for the table inversion: a Newton pass alone gains ~1 ms
 // from it, far less than the copy costs).
 static bool run_band_schedule(const ara_ctx* ctx, const LayerDev& L) {
-  return layer_inversion(ctx, L) <= 1 && ctx->schedule == ARA_SCHED_BAND && L.band_log2w > 0 &&
+  return layer_inversion(ctx, L) <= 1 && ctx->schedule != ARA_SCHED_TRIAL && L.band_log2w > 0 &&
          ctx->cfg.precision == ARA_ACC_FP64;
 }
 
@@ -53,46 +53,84 @@ int layer_inversion(const ara_ctx* ctx, const LayerDev& L) {
   return (m == 0 && L.tables == nullptr) ? 1 : m;
 }
 
-// The certified tables of one ELT, from the (alpha, beta) kept at staging.
-static ara_status ensure_elt_tables(ara_ctx* ctx, EltDev& e) {
-  if (e.tables) return ARA_OK;
-  if (!e.ab64) return fail(ctx, ARA_ERR_INVALID_ARG, "ELT has neither tables nor parameters");
-  unsigned long long* d_uncert = nullptr;  // staging scratch
-  unsigned long long uncert = 0;
-  cudaError_t err;
-  if ((err = obj_alloc(ctx, &e.tables, e.n * kTablePieces)) != cudaSuccess ||
-      (err = ensure_scratch(ctx, scratch_bytes<unsigned long long>(1))) != cudaSuccess) {
-    cudaGetLastError();
-    obj_free(ctx, e.tables);
-    e.tables = nullptr;
-    return fail(ctx, ARA_ERR_OOM, "tables of %lld records", (long long)e.n);
+// The certified tables of the ELTs `handles` that lack them, built together (kMaxTableJobs ELTs
+// per launch, one synchronisation at the end).
+static ara_status ensure_tables(ara_ctx* ctx, const int32_t* handles, int n_handles) {
+  std::vector<int32_t> todo;
+  for (int j = 0; j < n_handles; ++j) {
+    const int32_t h = handles[j];
+    if (!ctx->elts[h].tables && std::find(todo.begin(), todo.end(), h) == todo.end())
+      todo.push_back(h);
   }
-  d_uncert = reinterpret_cast<unsigned long long*>(ctx->d_scratch);
-  if ((err = cudaMemsetAsync(d_uncert, 0, sizeof uncert, ctx->stream)) != cudaSuccess ||
-      (err = launch_build_tables(e.n, e.recs, e.ab64, e.tables, d_uncert, ctx->stream)) !=
-          cudaSuccess ||
-      (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
-                             ctx->stream)) != cudaSuccess ||
-      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+  if (todo.empty()) return ARA_OK;
+  const int n = (int)todo.size();
+  std::vector<unsigned long long> uncert(n, 0ull);
+  cudaError_t err = ensure_scratch(ctx, scratch_bytes<unsigned long long>(n));
+  for (int j = 0; j < n && err == cudaSuccess; ++j) {
+    EltDev& e = ctx->elts[todo[j]];
+    err = obj_alloc(ctx, &e.tables, e.n * kTablePieces);
+  }
+  auto undo = [&]() {
     cudaGetLastError();
     cudaStreamSynchronize(ctx->stream);
-    obj_free(ctx, e.tables);
-    e.tables = nullptr;
+    for (int32_t h : todo) {
+      obj_free(ctx, ctx->elts[h].tables);
+      ctx->elts[h].tables = nullptr;
+    }
+  };
+  if (err != cudaSuccess) {
+    undo();
+    return fail(ctx, ARA_ERR_OOM, "tables of %d ELTs: %s", n, cudaGetErrorString(err));
+  }
+  unsigned long long* d_uncert = reinterpret_cast<unsigned long long*>(ctx->d_scratch);
+  err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long) * (size_t)n, ctx->stream);
+  for (int b = 0; b < n && err == cudaSuccess; b += kMaxTableJobs) {
+    TableJobs jobs{};
+    jobs.n = std::min(kMaxTableJobs, n - b);
+    for (int j = 0; j < jobs.n; ++j) {
+      const EltDev& e = ctx->elts[todo[b + j]];
+      jobs.recs[j] = e.recs;
+      jobs.tables[j] = e.tables;
+      jobs.first[j + 1] = jobs.first[j] + e.n;
+    }
+    err = launch_build_tables(jobs, d_uncert + b, ctx->stream);
+  }
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(uncert.data(), d_uncert, sizeof(unsigned long long) * (size_t)n,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    undo();
     return fail(ctx, ARA_ERR_CUDA, "building tables: %s", cudaGetErrorString(err));
   }
-  obj_free(ctx, e.ab64);
-  e.ab64 = nullptr;
-  e.n_uncertified = (int64_t)uncert;
+  for (int j = 0; j < n; ++j) ctx->elts[todo[j]].n_uncertified = (int64_t)uncert[j];
+  return ARA_OK;
+}
+
+// The start tables of the ELTs `handles` that lack them (stream-ordered on the context's stream).
+static ara_status ensure_starts(ara_ctx* ctx, const int32_t* handles, int n_handles) {
+  for (int j = 0; j < n_handles; ++j) {
+    EltDev& e = ctx->elts[handles[j]];
+    if (e.starts) continue;
+    cudaError_t err = obj_alloc(ctx, &e.starts, e.n * kStartFloats);
+    if (err == cudaSuccess) err = launch_build_starts(e.n, e.recs, e.starts, ctx->stream);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(ctx->stream);
+      obj_free(ctx, e.starts);
+      e.starts = nullptr;
+      return fail(ctx, err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA,
+                  "start tables: %s", cudaGetErrorString(err));
+    }
+  }
   return ARA_OK;
 }
 
 // The layer's packed table copy (its ELTs' tables first).
 static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   if (L.tables) return ARA_OK;
-  for (int j = 0; j < L.n_slots; ++j) {
-    const ara_status s = ensure_elt_tables(ctx, ctx->elts[L.handles[j]]);
-    if (s != ARA_OK) return s;
-  }
+  const ara_status s = ensure_tables(ctx, L.handles, L.n_slots);
+  if (s != ARA_OK) return s;
   const TablePiece** d_src = nullptr;  // staging scratch
   cudaError_t err;
   if ((err = obj_alloc(ctx, &L.tables, L.n_packed * kTablePieces)) != cudaSuccess ||
@@ -120,12 +158,12 @@ static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   return ARA_OK;
 }
 
-// The layer's packed start tables (its ELTs' own, built at staging), for runs that invert by
-// Newton-Halley steps.
+// The layer's packed start tables (its ELTs' own, built first if missing), for runs that invert
+// by Newton-Halley steps.
 static ara_status ensure_layer_starts(ara_ctx* ctx, LayerDev& L) {
   if (L.starts) return ARA_OK;
-  for (int j = 0; j < L.n_slots; ++j)
-    if (!ctx->elts[L.handles[j]].starts) return ARA_OK;  // (not expected) analytic starts
+  const ara_status s = ensure_starts(ctx, L.handles, L.n_slots);
+  if (s != ARA_OK) return s;
   cudaError_t err;
   if ((err = obj_alloc(ctx, &L.starts, L.n_packed * kStartFloats)) != cudaSuccess ||
       (err = ensure_scratch(ctx, scratch_bytes<const TablePiece*>(L.n_packed) +
@@ -161,12 +199,22 @@ ara_status prepare_layer_for_run(ara_ctx* ctx, LayerDev& L, int64_t n, bool band
   ara_status s = rent_or_buy(ctx, L, n);
   if (s != ARA_OK) return s;
   if (band_ok && L.band_want > 0 && L.band_log2w == 0 && layer_inversion(ctx, L) == 0 &&
-      ctx->schedule == ARA_SCHED_BAND && ctx->cfg.precision == ARA_ACC_FP64) {
-    bool banded = false;
-    s = ensure_band_variant(ctx, L.yet, L.band_want, &banded);
-    if (s != ARA_OK) return s;
-    if (banded) L.band_log2w = L.band_want;
-    L.band_want = 0;
+      ctx->schedule != ARA_SCHED_TRIAL && ctx->cfg.precision == ARA_ACC_FP64) {
+    // under ARA_SCHED_AUTO the copy is bought once the YET's trial-major table runs plus this
+    // one cover ARA_BAND_BUY_PASSES times its occurrences; until then this run rents
+    YetDev& Y = ctx->yets[L.yet];
+    const double occ =
+        Y.n_trials > 0 ? (double)Y.n_occ * ((double)n / (double)Y.n_trials) : 0.0;
+    if (ctx->schedule == ARA_SCHED_AUTO &&
+        Y.band_rent_occ + occ < ARA_BAND_BUY_PASSES * (double)Y.n_occ) {
+      Y.band_rent_occ += occ;
+    } else {
+      bool banded = false;
+      s = ensure_band_variant(ctx, L.yet, L.band_want, &banded);
+      if (s != ARA_OK) return s;
+      if (banded) L.band_log2w = L.band_want;
+      L.band_want = 0;
+    }
   }
   // Newton-Halley runs and the surrogate's fallbacks start from the layer's start tables
   return layer_inversion(ctx, L) >= 1 ? ensure_layer_starts(ctx, L) : ARA_OK;
@@ -194,12 +242,23 @@ static ara_status rent_or_buy(ara_ctx* ctx, LayerDev& L, int64_t n) {
   return ARA_OK;
 }
 
+static std::vector<int32_t> live_elts_of(const ara_ctx* ctx, int32_t yet) {
+  std::vector<int32_t> hs;
+  for (int32_t h = 0; h < (int32_t)ctx->elts.size(); ++h)
+    if (ctx->elts[h].live && ctx->elts[h].yet == yet) hs.push_back(h);
+  return hs;
+}
+
 ara_status ensure_yet_tables(ara_ctx* ctx, int32_t yet) {
-  for (auto& e : ctx->elts)
-    if (e.live && e.yet == yet) {
-      const ara_status s = ensure_elt_tables(ctx, e);
-      if (s != ARA_OK) return s;
-    }
+  const std::vector<int32_t> hs = live_elts_of(ctx, yet);
+  return ensure_tables(ctx, hs.data(), (int)hs.size());
+}
+
+ara_status ensure_yet_starts(ara_ctx* ctx, int32_t yet) {
+  const std::vector<int32_t> hs = live_elts_of(ctx, yet);
+  const ara_status s = ensure_starts(ctx, hs.data(), (int)hs.size());
+  if (s != ARA_OK) return s;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return ARA_OK;
 }
 

@@ -466,9 +466,12 @@ ara_status ara_server_create(ara_ctx* ctx, const ara_server_config* cfg, ara_ser
   if (cfg->slice_trials < 1 || cfg->max_batch_trials < cfg->slice_trials || cfg->max_inflight < 1)
     return ARA_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARA_ERR_CUDA;
-  // the server's layers carry the tables of their ELTs: build any that staging deferred
-  if (!cfg->use_surrogate && cfg->inversion == ARA_INV_TABLE) {
-    const ara_status ts = ensure_yet_tables(ctx, cfg->yet);
+  // the server's layers carry the tables of their ELTs (build any that staging deferred), or,
+  // for Newton-Halley steps and the surrogate's fallbacks, their start tables
+  {
+    const ara_status ts = (!cfg->use_surrogate && cfg->inversion == ARA_INV_TABLE)
+                              ? ensure_yet_tables(ctx, cfg->yet)
+                              : ensure_yet_starts(ctx, cfg->yet);
     if (ts != ARA_OK) return ts;
   }
   ara_server* s = new ara_server();

@@ -104,7 +104,7 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
                                    const double* __restrict__ mean, const double* __restrict__ sd,
                                    const double* __restrict__ sdc, const double* __restrict__ mx,
                                    int32_t catalog, BetaRec* __restrict__ recs,
-                                   double2* __restrict__ ab64, float* __restrict__ corr,
+                                   float* __restrict__ corr,
                                    unsigned int* dup, unsigned int* flags) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -126,7 +126,6 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
   BetaRec rec;
   rec.a = 0.f; rec.b = 0.f; rec.mx = (float)mu; rec.L0 = 0.f;
   rec.p0 = 0.5f; rec.lnx0 = 0.f; rec.lny0 = 0.f; rec.lns = 0.f;
-  double2 ab = make_double2(0.0, 0.0);
   if (!(mu > 0.0) || !(sigma >= 0.0) || !isfinite(mu) || !isfinite(sigma)) {
     f |= 16u;
   } else if (sigma > 0.0) {
@@ -144,12 +143,10 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
       double lnB;
       rec = ara_beta_rec_f64(a, b, &lnB);  // p0 from the same ln B(a,b): one set of lgamma calls
       rec.mx = (float)m;
-      ab = make_double2(a, b);
       if (!(rec.a > 0.f) || !(rec.b > 0.f)) f |= 16u;  // alpha or beta outside binary32 range
     }
   }
   recs[r] = rec;
-  ab64[r] = ab;
   if (f) atomicOr(flags, f);
 }
 
@@ -360,12 +357,12 @@ cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, OffsetChe
 
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
                                const double* mean, const double* sd, const double* sdc,
-                               const double* mx, int32_t catalog, BetaRec* recs, double2* ab64,
+                               const double* mx, int32_t catalog, BetaRec* recs,
                                float* corr, unsigned int* d_dup, unsigned int* d_flags,
                                cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, ids_out, mean, sd, sdc, mx,
-                                                       catalog, recs, ab64, corr, d_dup, d_flags);
+                                                       catalog, recs, corr, d_dup, d_flags);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
-// ara_table.cu -- builds and certifies the per-record quantile tables when an ELT is staged
-// (one thread per record; the construction itself is in ara_table.cuh).
+// ara_table.cu -- builds and certifies the per-record quantile tables (kTableSegments threads per
+// record), builds the start tables, and gathers both into a layer's packed order; the
+// construction itself is in ara_table.cuh.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -11,16 +12,50 @@ namespace ara {
 
 namespace {
 
-__global__ void build_tables_kernel(int64_t n, const BetaRec* __restrict__ recs,
-                                    const double2* __restrict__ ab64, TablePiece* tables,
-                                    unsigned long long* n_uncertified) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const BetaRec br = recs[r];
-  const double2 ab = ab64[r];
-  bool ok;
-  ara_build_table_record(br, ab.x, ab.y, tables + r * kTablePieces, &ok);
-  if (!ok) atomicAdd(n_uncertified, 1ull);
+// Tables of the records of several ELTs in one launch.  A block takes 32 records; its warp w
+// builds segment w (kTablePieces / kTableSegments pieces, a chain from its own first knot) of
+// each of them, so a warp's lanes solve at nearby uniforms of 32 records (similar work) and a
+// record's 129 inversions run as kTableSegments short chains.  A record keeps its table only if
+// all its segments passed their checks (combined in shared memory); uncert[j] counts the
+// records of job j that did not.
+__global__ void __launch_bounds__(32 * kTableSegments) build_tables_kernel(
+    const __grid_constant__ TableJobs J, unsigned long long* uncert) {
+  constexpr int per = kTablePieces / kTableSegments;
+  __shared__ unsigned int s_ok[kTableSegments];
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * 32 + lane;
+  const bool valid = g < J.first[J.n];
+  int j = 0;
+  if (valid) {  // the job holding record g: the last whose first record is <= g
+    int lo = 0, hi = J.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (J.first[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    j = lo;
+  }
+  bool ok = true;
+  BetaRec br{};
+  TablePiece* pc = nullptr;
+  if (valid) {
+    const int64_t r = g - J.first[j];
+    br = J.recs[j][r];
+    pc = J.tables[j] + r * kTablePieces;
+    if (!(br.a > 0.0f))
+      ara_table_fill(pc, seg * per, (seg + 1) * per, br.mx, kPieceMean);
+    else
+      ok = ara_build_table_pieces(br, seg * per, (seg + 1) * per, pc);
+  }
+  const unsigned failed = __ballot_sync(0xFFFFFFFFu, !ok);  // lanes of this segment that failed
+  if (lane == 0) s_ok[seg] = failed;
+  __syncthreads();
+  unsigned any = 0u;
+#pragma unroll
+  for (int w = 0; w < kTableSegments; ++w) any |= s_ok[w];
+  if (valid && (any >> lane & 1u)) {
+    ara_table_fill(pc, seg * per, (seg + 1) * per, br.mx, kPieceNewton);
+    if (seg == 0) atomicAdd(uncert + j, 1ull);
+  }
 }
 
 __global__ void build_starts_kernel(int64_t n, const BetaRec* __restrict__ recs, float* starts) {
@@ -68,13 +103,11 @@ cudaError_t launch_gather_starts(int64_t n, const float* const* d_src, float* ds
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_tables(int64_t n, const BetaRec* recs, const double2* ab64,
-                                TablePiece* tables, unsigned long long* d_uncertified,
+cudaError_t launch_build_tables(const TableJobs& jobs, unsigned long long* d_uncert,
                                 cudaStream_t st) {
+  const int64_t n = jobs.first[jobs.n];
   if (n == 0) return cudaSuccess;
-  const int threads = 128;
-  build_tables_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
-      n, recs, ab64, tables, d_uncertified);
+  build_tables_kernel<<<(unsigned)((n + 31) / 32), 32 * kTableSegments, 0, st>>>(jobs, d_uncert);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -2,12 +2,15 @@
 //
 // Knots are placed at z_i = -kTableZ + i kTableH (i = 0..kTablePieces), z the signed distance
 // from the median in t = sqrt(-2 ln q), q = min(u, 1 - u).  The quantile at a knot comes from
-// the binary32 Newton inversion on the record's own tail (u <= p0: x itself; u > p0: 1 - x of
-// the swapped record, so x near 1 keeps its precision), polished by one binary64 Newton step;
-// the log-odds L = ln x - ln(1-x) and its first two derivatives in z follow from the beta density;
-// each piece's quintic Hermite coefficients are formed in binary64.  Each piece is then checked at
-// its midpoint against a polished inversion; a record keeps its table only if every midpoint
-// agrees to kTableTol in L (so in x/(1-x) relatively) plus the binary32 rounding of L.
+// the binary32 Newton-Halley inversion on the record's own tail (u <= p0: x itself; u > p0: 1 - x
+// of the swapped record, so x near 1 keeps its precision), started from the Taylor step of the
+// knot before it; the log-odds L = ln x - ln(1-x) and its first two derivatives in z follow from
+// the beta density; each piece's quintic Hermite coefficients are stored as log2-odds.  Each
+// piece is then checked at its midpoint against the same inversion started from the piece
+// itself; a record keeps its table only if every midpoint agrees to kTableTol in L (so in
+// x/(1-x) relatively) plus the binary32 rounding of L and the inversion's own rounding.  A table
+// is thus the binary32 Newton-Halley inversion, tabulated: its error against the exact quantile
+// is that inversion's (mean 2.3e-7 relative in x over the ELT value law) plus at most kTableTol.
 //
 // Derivatives (g = dL/du = B(a,b) / (x^a (1-x)^b), t = t_m + |z|, u(z) with du/dz = -t q):
 //   L'  = -t q g,
@@ -20,10 +23,18 @@
 namespace ara {
 
 constexpr double kTableTol = 1e-6;
+// The binary32 check's allowance for its reference's own rounding: the inversion's residual
+// ln I - ln p carries up to kTableNoiseUlps units of 2^-24 of the magnitude of its terms (the
+// prefactor's L0, a ln(x/x0), b ln(y/y0), ln p, the fraction), which moves its L by that times
+// dL/d(ln p) = |L'| / t (about 1/a in a lower tail: the binary32 inversion of a record with a
+// shape parameter near 0.1 is itself only good to ~1e-5 there).  Capped at kTableNoiseCap: a
+// record whose inversion is worse conditioned still keeps the Newton inversion.
+constexpr float kTableNoiseUlps = 16.0f;
+constexpr float kTableNoiseCap = 1e-5f;
 
-// ---- double-float arithmetic -------------------------------------------------------------------
+// ---- quantiles polished in binary64 (staging constants, the learned surrogate's targets) --------
 // A value hi + lo of two binary32 numbers (|lo| <= ulp(hi)/2, ~48 significant bits): the FP64 pipe
-// of this part is 1/64 of the FP32 one, so the build's continued fraction runs in pairs of
+// of this part is 1/64 of the FP32 one, so the polish's continued fraction runs in pairs of
 // binary32 (Dekker's and Knuth's error-free sum and product, the product through an FMA).  The
 // additions and products are the round-to-nearest intrinsics on the device, so that the compiler
 // never fuses them into FMAs, which would break the error-free transformations.
@@ -95,8 +106,7 @@ ARA_HD DF df_scale(DF a, float s) {  // s a power of two: exact
 // division-free equivalent fraction (numerators -(a+b)x, -(a+m)(a+b+m)x, m(b-m)x; denominators
 // a+n), rescaled by a power of two every step pair.  Converged when B/A moved by at most 1e-10
 // relative since the previous pair, tested without a division: |B pA - pB A| <= 1e-10 |B pA|
-// (pA, pB: the previous pair at the same scale).  The knots need L to ~1e-9 (pieces fit to ~1e-8,
-// certified to 1e-6).
+// (pA, pB: the previous pair at the same scale).
 ARA_HD double ara_beta_cf_f64(double a64, double b64, double x64) {
   const DF a = df_from(a64), b = df_from(b64), x = df_from(x64);
   const DF apb = df_add(a, b);
@@ -215,126 +225,12 @@ ARA_HD bool ara_exact_quantile_logs(double a, double b, float u, double* lnx, do
   return ok;
 }
 
-ARA_HD double piece_eval(const double* c, double tau) {
-  return c[0] + tau * (c[1] + tau * (c[2] + tau * (c[3] + tau * (c[4] + tau * c[5]))));
-}
-
-// Log-odds of the quantile at z and its first two derivatives in z (the second from the side s).
-struct LogitKnot {
-  double L, L1, L2;
-  bool ok;
-};
-
-ARA_HD LogitKnot logit_knot(const BetaRec& br, const BetaRec& sw, const TailParams& lo,
-                            const TailParams& up, double z, double s) {
-  LogitKnot k;
-  const double t = (double)kTableTm + fabs(z);
-  const double lnq = -0.5 * t * t;
-  const float qf = expf((float)lnq);
-  // u = q below the median, 1 - q above it; ln u or ln(1 - u) (whichever the solve needs) in
-  // binary64 without cancellation.  The complement ln(1 - v) of the solved v = x or 1 - x is
-  // well conditioned in binary32 while v <= 1/2 (it enters L at the 1e-7 level); above that it
-  // takes binary64
-  const bool below = z >= 0.0 ? (double)qf <= (double)br.p0 : (1.0 - (double)qf) <= (double)br.p0;
-  bool ok;
-  double lnx, ln1mx;
-  if (below) {
-    const double lnu = z >= 0.0 ? lnq : log1p(-exp(lnq));
-    float uf = (float)exp(lnu);
-    if (!(uf <= br.p0)) uf = br.p0;
-    if (!(uf > 0.0f)) uf = 1.17549435e-38f;
-    lnx = ara_polish_ln_quantile(br, lo, uf, lnu, &ok);
-    ln1mx = lnx < -0.6931471805599453 ? (double)log1pf(-expf((float)lnx)) : log1p(-exp(lnx));
-  } else {
-    const double ln1mu = z >= 0.0 ? log1p(-exp(lnq)) : lnq;
-    float vf = (float)exp(ln1mu);
-    if (!(vf <= sw.p0)) vf = sw.p0;
-    if (!(vf > 0.0f)) vf = 1.17549435e-38f;
-    ln1mx = ara_polish_ln_quantile(sw, up, vf, ln1mu, &ok);
-    lnx = ln1mx < -0.6931471805599453 ? (double)log1pf(-expf((float)ln1mx)) : log1p(-exp(ln1mx));
-  }
-  const double a = lo.a, b = lo.b;
-  // the derivatives need ~1e-7 relative accuracy only (they enter the pieces multiplied by h and
-  // h^2): exponents in binary64, exponentials in binary32
-  const double x = (double)expf((float)lnx), y = (double)expf((float)ln1mx);
-  k.L = lnx - ln1mx;
-  k.L1 = -t * (double)expf((float)(lnq + lo.lnB - a * lnx - b * ln1mx));
-  k.L2 = k.L1 * k.L1 * (b * x - a * y) - s * (t * t - 1.0) * k.L1 / t;
-  k.ok = ok && isfinite(k.L) && isfinite(k.L1) && isfinite(k.L2);
-  return k;
-}
-
-// Fills a record's kTablePieces pieces (pc) and reports whether every piece was certified.
-// br: the record in binary32; a64, b64: its beta parameters in binary64.
-ARA_HD void ara_build_table_record(const BetaRec& br, double a64, double b64, TablePiece* pc,
-                                   bool* ok_out) {
-  *ok_out = true;
-  if (!(br.a > 0.0f)) {  // sd = 0: the loss is the mean
-    for (int i = 0; i < kTablePieces; ++i) {
-      for (int j = 0; j < 6; ++j) pc[i].c[j] = 0.0f;
-      pc[i].mx = br.mx;
-      pc[i].flag = kPieceMean;
-    }
-    return;
-  }
-  const double lnB = lgamma(a64) + lgamma(b64) - lgamma(a64 + b64);
-  const TailParams lo = {a64, b64, lnB, log(a64)}, up = {b64, a64, lnB, log(b64)};
-  BetaRec sw;  // the swapped record: 1 - x ~ Beta(b, a), whose own mean probability is 1 - p0
-  sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
-  sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
-  const double h = (double)kTableH, z0 = -(double)kTableZ;
-  const double kLog2e = 1.4426950408889634;
-  bool ok = true;
-  const int half = kTablePieces / 2;
-  LogitKnot k0 = logit_knot(br, sw, lo, up, z0, -1.0);
-  ok = ok && k0.ok;
-  for (int i = 0; i < kTablePieces && ok; ++i) {
-    const double side = i < half ? -1.0 : 1.0;  // the median is the boundary of pieces half-1, half
-    if (i == half) k0 = logit_knot(br, sw, lo, up, 0.0, 1.0);
-    const LogitKnot k1 = logit_knot(br, sw, lo, up, z0 + (i + 1) * h, side);
-    ok = ok && k0.ok && k1.ok;
-    // quintic Hermite on tau in [0,1]: values, h * first, h^2 * second derivatives at both ends
-    double c[6];
-    c[0] = k0.L;
-    c[1] = h * k0.L1;
-    c[2] = 0.5 * h * h * k0.L2;
-    const double A = k1.L - (c[0] + c[1] + c[2]);
-    const double B = h * k1.L1 - (c[1] + 2.0 * c[2]);
-    const double C = h * h * k1.L2 - 2.0 * c[2];
-    c[3] = 10.0 * A - 4.0 * B + 0.5 * C;
-    c[4] = -15.0 * A + 7.0 * B - C;
-    c[5] = 6.0 * A - 3.0 * B + 0.5 * C;
-    double cf[6];  // the stored log2-odds coefficients, back in natural units
-    for (int j = 0; j < 6; ++j) {
-      pc[i].c[j] = (float)(c[j] * kLog2e);
-      cf[j] = (double)pc[i].c[j] / kLog2e;
-    }
-    pc[i].mx = br.mx;
-    pc[i].flag = kPieceTable;
-    // certify at the midpoint against a polished inversion (coefficients as stored)
-    const LogitKnot km = logit_knot(br, sw, lo, up, z0 + (i + 0.5) * h, side);
-    const double err = fabs(piece_eval(cf, 0.5) - km.L);
-    // allowed: kTableTol plus the binary32 rounding of L (4 ulp of |L|), which dominates only for
-    // x or 1 - x below ~1e-12, far below any loss that reaches a year loss
-    const double tol = kTableTol + 2.384185791015625e-7 * fabs(km.L);
-    if (!(err <= tol) || !km.ok) ok = false;
-    k0 = k1;
-  }
-  if (!ok) {
-    for (int i = 0; i < kTablePieces; ++i) {
-      pc[i].mx = br.mx;
-      pc[i].flag = kPieceNewton;
-    }
-  }
-  *ok_out = ok;
-}
-
 // Fills a record's start table (kStartPieces quintics of the log-odds in tau, kStartCoefs
 // floats each, see ara_start_logit) from binary32 inversions at the knots
 // z_i = -kTableZ + 4 i kTableH: the lower tail through the record, the upper through the swapped
 // record at q = 1 - u, so that u near 1 keeps its precision; the derivatives in z are those of
-// logit_knot (L'' taken on each piece's own side of the median).  Pieces with a failed knot are
-// NaN.
+// the certified tables (L'' taken on each piece's own side of the median).  Pieces with a failed
+// knot are NaN.
 ARA_HD void ara_build_start_record(const BetaRec& br, float* st) {
   if (!(br.a > 0.0f)) {  // sd = 0: never inverted
     for (int k = 0; k < kStartFloats; ++k) st[k] = 0.0f;
@@ -399,5 +295,144 @@ ARA_HD void ara_build_start_record(const BetaRec& br, float* st) {
       for (int j = 0; j < kStartCoefs; ++j) c[j] = ara_bits_to_float(0x7FC00000);
   }
 }
+
+// ---- certified tables ------------------------------------------------------------------------------
+
+// ln(x^a (1-x)^b / B(a,b)) as L0 + a ln(x/x0) + b ln(y/y0), with w = (x - x0)(a+b) taken from
+// the smaller of x and y, so that it has no cancellation near the mean; *mag receives the sum of
+// the magnitudes of its terms (its rounding scales with it).
+ARA_HD float ara_beta_log_prefactor(const BetaRec& br, float lnx, float ln1mx, float x, float y,
+                                    float* mag) {
+  const float a = br.a, b = br.b, s = a + b;
+  const float w = x < 0.5f ? fmaf(x, s, -a) : fmaf(-y, s, b);
+  const float rx = w / a, ry = -w / b;
+  const float lnrx = rx > -0.5f ? log1pf(rx) : lnx - br.lnx0;
+  const float lnry = ry > -0.5f ? log1pf(ry) : ln1mx - br.lny0;
+  *mag = fabsf(br.L0) + fabsf(a * lnrx) + fabsf(b * lnry);
+  return br.L0 + a * lnrx + b * lnry;
+}
+
+// A knot: L and its derivatives in z, L'' = L2a - s L2b on the side s of the median.
+struct KnotF {
+  float z, L, L1, L2a, L2b;
+  float gmag;  // magnitude of the terms of the inversion's residual at the root
+  bool ok;
+};
+
+// Log-odds of the quantile at z (start: an estimate of it, or 1e30 for the analytic start) and
+// its derivatives in z: L' = -t e^(ln q - E), E the log prefactor at the root.
+ARA_HD KnotF ara_knot(const BetaRec& br, const BetaRec& sw, float z, float start) {
+  KnotF k;
+  k.z = z;
+  const float t = kTableTm + fabsf(z);
+  const float lnq = -0.5f * t * t;
+  const float q = expf(lnq);
+  float lnx, ln1mx;
+  bool conv;
+  if (z >= 0.0f) {  // lower tail: u = q
+    const IbetaResult r = ara_inv_beta(br, q, start);
+    conv = r.converged;
+    if (q > br.p0) { ln1mx = r.t; lnx = log1pf(-expf(r.t)); }
+    else { lnx = r.t; ln1mx = log1pf(-expf(r.t)); }
+  } else {  // upper tail: 1 - x ~ Beta(b, a) at probability q (start: the log-odds of 1 - x)
+    const IbetaResult r = ara_inv_beta(sw, q, start < 1e29f ? -start : start);
+    conv = r.converged;
+    if (q > sw.p0) { lnx = r.t; ln1mx = log1pf(-expf(r.t)); }
+    else { ln1mx = r.t; lnx = log1pf(-expf(r.t)); }
+  }
+  const float x = expf(lnx), y = expf(ln1mx);
+  float mag;
+  k.L = lnx - ln1mx;
+  k.L1 = -t * expf(lnq - ara_beta_log_prefactor(br, lnx, ln1mx, x, y, &mag));
+  k.gmag = 2.0f + mag - lnq;
+  k.L2a = k.L1 * k.L1 * (br.b * x - br.a * y);
+  k.L2b = (t * t - 1.0f) * k.L1 / t;
+  k.ok = conv && isfinite(k.L) && isfinite(k.L1) && isfinite(k.L2a) && isfinite(k.L2b);
+  return k;
+}
+
+// Pieces [i0, i1) of a record's table (br.a > 0), the knots chained from z_i0 (its own start
+// analytic); true if every one passed its midpoint check.  Writes coefficients, mx and
+// kPieceTable; the caller turns every piece of a record that failed anywhere to kPieceNewton.
+ARA_HD bool ara_build_table_pieces(const BetaRec& br, int i0, int i1, TablePiece* pc) {
+  BetaRec sw;  // the swapped record: 1 - x ~ Beta(b, a), whose own mean probability is 1 - p0
+  sw.a = br.b; sw.b = br.a; sw.mx = br.mx; sw.L0 = br.L0;
+  sw.p0 = 1.0f - br.p0; sw.lnx0 = br.lny0; sw.lny0 = br.lnx0; sw.lns = br.lns;
+  const float h = kTableH, z0 = -kTableZ;
+  const float kLog2e = 1.44269504f, kLn2 = 0.693147181f;
+  const int half = kTablePieces / 2;
+  KnotF k0 = ara_knot(br, sw, z0 + (float)i0 * h, 1e30f);
+  bool ok = k0.ok;
+  float d3 = 0.0f;  // third derivative over the piece before, by difference (0: none this side)
+  for (int i = i0; i < i1 && ok; ++i) {
+    const float side = i < half ? -1.0f : 1.0f;  // the median is the boundary of pieces half-1, half
+    if (i == half) d3 = 0.0f;
+    const float d2 = k0.L2a - side * k0.L2b;
+    // the next knot starts from the cubic Taylor step, so one Halley step nearly always suffices
+    const float guess = fmaf(h, fmaf(h, fmaf(h * (1.0f / 6.0f), d3, 0.5f * d2), k0.L1), k0.L);
+    const KnotF k1 = ara_knot(br, sw, z0 + (float)(i + 1) * h, guess);
+    const float e2 = k1.L2a - side * k1.L2b;
+    d3 = (e2 - d2) * kTableInvH;
+    // quintic Hermite on tau in [0,1]: values, h * first, h^2 * second derivatives at both ends
+    float c[6];
+    c[0] = k0.L;
+    c[1] = h * k0.L1;
+    c[2] = 0.5f * h * h * d2;
+    const float A = k1.L - (c[0] + c[1] + c[2]);
+    const float B = h * k1.L1 - (c[1] + 2.0f * c[2]);
+    const float C = h * h * e2 - 2.0f * c[2];
+    c[3] = 10.0f * A - 4.0f * B + 0.5f * C;
+    c[4] = -15.0f * A + 7.0f * B - C;
+    c[5] = 6.0f * A - 3.0f * B + 0.5f * C;
+    TablePiece p;
+    for (int j = 0; j < 6; ++j) p.c[j] = c[j] * kLog2e;
+    p.mx = br.mx;
+    p.flag = kPieceTable;
+    pc[i] = p;
+    // the check at the midpoint, against the inversion started from the piece (as stored)
+    const float Lt =
+        kLn2 * fmaf(0.5f, fmaf(0.5f, fmaf(0.5f, fmaf(0.5f, fmaf(0.5f, p.c[5], p.c[4]), p.c[3]),
+                                          p.c[2]),
+                               p.c[1]),
+                    p.c[0]);
+    const KnotF km = ara_knot(br, sw, z0 + ((float)i + 0.5f) * h, Lt);
+    const float tol = (float)kTableTol + 2.384185791015625e-7f * fabsf(km.L) +
+                      fminf(kTableNoiseUlps * 5.9604645e-8f * km.gmag * fabsf(km.L1) /
+                                (kTableTm + fabsf(km.z)),
+                            kTableNoiseCap);
+    ok = k1.ok && km.ok && fabsf(Lt - km.L) <= tol;
+    k0 = k1;
+  }
+  return ok;
+}
+
+// Pieces [i0, i1) of a record that is not tabulated: the mean (sd = 0) or Newton's method.
+ARA_HD void ara_table_fill(TablePiece* pc, int i0, int i1, float mx, uint32_t flag) {
+  for (int i = i0; i < i1; ++i) {
+    if (flag == kPieceMean)
+      for (int j = 0; j < 6; ++j) pc[i].c[j] = 0.0f;
+    pc[i].mx = mx;
+    pc[i].flag = flag;
+  }
+}
+
+// A record's whole table in one pass (the kernels split it into kTableSegments chains); *ok_out:
+// every piece certified (else every piece says kPieceNewton).
+constexpr int kTableSegments = 4;
+ARA_HD void ara_build_table_record(const BetaRec& br, TablePiece* pc, bool* ok_out) {
+  *ok_out = true;
+  if (!(br.a > 0.0f)) {  // sd = 0: the loss is the mean
+    ara_table_fill(pc, 0, kTablePieces, br.mx, kPieceMean);
+    return;
+  }
+  constexpr int per = kTablePieces / kTableSegments;
+  bool ok = true;
+  for (int g = 0; g < kTableSegments; ++g)
+    ok = ara_build_table_pieces(br, g * per, (g + 1) * per, pc) && ok;
+  if (!ok) ara_table_fill(pc, 0, kTablePieces, br.mx, kPieceNewton);
+  *ok_out = ok;
+}
+static_assert(kTablePieces % kTableSegments == 0 && 32 % kTableSegments == 0,
+              "segments split the pieces evenly and a warp into whole records");
 
 }  // namespace ara

@@ -25,7 +25,7 @@ int main(int argc, char** argv) {
   br.mx = (float)mx;
   static TablePiece pc[kTablePieces];
   bool ok;
-  ara_build_table_record(br, a, b, pc, &ok);
+  ara_build_table_record(br, pc, &ok);
   float st[kStartFloats];
   ara_build_start_record(br, st);
   std::printf("%.17g %.17g %d\n", a, b, (int)ok);

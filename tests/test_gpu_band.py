@@ -21,9 +21,10 @@ N = 3000
 def staged(ara):
     w = synth.paper(n_trials=N)
     c = ara.Context(seed=42)
+    c.set_option(ara.OPT_SCHEDULE, ara.SCHED_BAND)
     yet, elts, layer = c.stage_workload(w)
-    # the layer's band-major YET copy is made by its first band-schedule run (5 launches): make it
-    # here, so that the tests count the launches of runs alone
+    # under ARA_SCHED_BAND the layer's band-major YET copy is made by its first run (5 launches):
+    # make it here, so that the tests count the launches of runs alone
     s0 = c.stats()
     c.run(yet, layer, 0, 1)
     assert c.stats()["launches"] - s0["launches"] == 2 + 5
