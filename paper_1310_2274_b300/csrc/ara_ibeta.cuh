@@ -27,9 +27,11 @@
 #ifndef ARA_HD
 #ifdef __CUDACC__
 #define ARA_HD __host__ __device__ __forceinline__
+#define ARA_HD_CALL static __host__ __device__ __noinline__
 #else
 #include <cmath>
 #define ARA_HD inline
+#define ARA_HD_CALL static inline
 #endif
 #endif
 
@@ -522,7 +524,8 @@ ARA_HD int ara_table_piece(float u, float* tau) {
 
 // One 32-byte load of piece k of the record whose table starts at rec.  KEEP chooses the L2
 // policy: evict-last when pieces are reused while cached (band-major schedule), evict-first when
-// the tables are swept at random (trial-major schedule).
+// the tables are swept at random (trial-major schedule).  A miss fills 64 bytes, not the default
+// 128: a random 32-byte gather then reads half as much from DRAM.
 template <bool KEEP>
 ARA_HD TablePiece ara_load_piece(const TablePiece* rec, int k) {
   TablePiece pc;
@@ -531,13 +534,13 @@ ARA_HD TablePiece ara_load_piece(const TablePiece* rec, int k) {
   const TablePiece* p = rec + k;
   if constexpr (KEEP) {
     asm volatile(
-        "ld.global.nc.L1::no_allocate.L2::evict_last.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        "ld.global.nc.L1::no_allocate.L2::evict_last.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
           "=r"(w[7])
         : "l"(p));
   } else {
     asm volatile(
-        "ld.global.nc.L1::no_allocate.L2::evict_first.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        "ld.global.nc.L1::no_allocate.L2::evict_first.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
           "=r"(w[7])
         : "l"(p));

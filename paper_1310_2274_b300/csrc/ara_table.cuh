@@ -320,8 +320,9 @@ struct KnotF {
 };
 
 // Log-odds of the quantile at z (start: an estimate of it, or 1e30 for the analytic start) and
-// its derivatives in z: L' = -t e^(ln q - E), E the log prefactor at the root.
-ARA_HD KnotF ara_knot(const BetaRec& br, const BetaRec& sw, float z, float start) {
+// its derivatives in z: L' = -t e^(ln q - E), E the log prefactor at the root.  Out of line: the
+// build's three call sites then share one copy of the inversion (instruction-cache footprint).
+ARA_HD_CALL KnotF ara_knot(const BetaRec& br, const BetaRec& sw, float z, float start) {
   KnotF k;
   k.z = z;
   const float t = kTableTm + fabsf(z);

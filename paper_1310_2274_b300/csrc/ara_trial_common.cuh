@@ -93,15 +93,17 @@ __device__ __forceinline__ int32_t ld_stream_s32(const int32_t* p, unsigned long
                : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+// Gathers of 8 or 16 bytes at random addresses (index entries, records, start pieces), with an L2
+// policy; a miss fills 64 bytes rather than the default 128.
 __device__ __forceinline__ uint2 ld_pol_u2(const uint2* p, unsigned long long pol) {
   uint2 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+  asm volatile("ld.global.nc.L2::cache_hint.L2::64B.v2.u32 {%0,%1}, [%2], %3;"
                : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ uint4 ld_pol_u4(const uint4* p, unsigned long long pol) {
   uint4 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+  asm volatile("ld.global.nc.L2::cache_hint.L2::64B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
   return v;
 }
