@@ -273,14 +273,16 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   if (ts_on_host)
     ts_check = std::thread(
         [&]() { host_flags = validate_timestamps_host(off.data(), timestamps, n_trials); });
-  // device offsets are copied where they are
+  // device offsets are copied where they are; ids the device can read are copied by the
+  // validation kernel as it checks them (one pass over them), others first
   const int64_t* off_src = dev_path ? trial_offsets : off.data();
-  if ((e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess ||
+  const int32_t* r_ids = n_occ > 0 ? device_readable(event_ids) : nullptr;
+  if ((!r_ids && (e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess) ||
       (e = copy_in(y.offsets, off_src, n_trials + 1, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
-      (e = launch_validate_yet_range(y.ids, ts_on_host ? nullptr : timestamps, 0, y.offsets, 0,
-                                     n_trials, catalog_size, ctx->d_flags, ctx->stream)) !=
-          cudaSuccess) {
+      (e = launch_validate_yet_range(r_ids ? r_ids : y.ids, ts_on_host ? nullptr : timestamps, 0,
+                                     y.offsets, 0, n_trials, catalog_size, ctx->d_flags,
+                                     ctx->stream, r_ids ? y.ids : nullptr)) != cudaSuccess) {
     cudaGetLastError();
     if (ts_check.joinable()) ts_check.join();
     cudaStreamSynchronize(ctx->stream);

@@ -165,10 +165,12 @@ cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, OffsetChe
                                  cudaStream_t st);
 // Checks of a YET's trials [t_begin, t_begin + n) whose occurrences [occ_base, ...) are in
 // ids / ts (ts may be null: timestamps checked elsewhere): flags bit 0 an id out of range, bit 1
-// a decreasing timestamp, bit 2 a NaN timestamp
+// a decreasing timestamp, bit 2 a NaN timestamp; ids_out (nullable) receives a copy of the ids
+// checked
 cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64_t occ_base,
                                       const int64_t* offsets, int64_t t_begin, int64_t n,
-                                      int32_t catalog, unsigned int* d_flags, cudaStream_t st);
+                                      int32_t catalog, unsigned int* d_flags, cudaStream_t st,
+                                      int32_t* ids_out = nullptr);
 // Checks and converts an ELT's records (ids, mean, sd, optional correlated sd, max exposure, all
 // device-readable) into recs / corr; ids_out (nullable) receives a copy of the ids.
 cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,

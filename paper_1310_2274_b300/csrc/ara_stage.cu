@@ -35,7 +35,7 @@ inline unsigned grid_for(int64_t n, int per_block = kThreads) {
 __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float* __restrict__ ts,
                                     int64_t occ_base, const int64_t* __restrict__ off,
                                     int64_t t_begin, int64_t n_trials, int32_t catalog,
-                                    unsigned int* flags) {
+                                    unsigned int* flags, int32_t* __restrict__ ids_out) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -44,6 +44,7 @@ __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float
     const int64_t beg = off[i] - occ_base, end = off[i + 1] - occ_base;
     for (int64_t q = beg + lane; q < end; q += 32) {
       const int32_t e = ids[q];
+      if (ids_out != nullptr) ids_out[q] = e;  // the YET's device copy, made in the same pass
       if (e < 0 || e >= catalog) f |= 1u;
       if (ts != nullptr) {  // null: the timestamps are checked on the host
         const float t = ts[q];
@@ -140,8 +141,7 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
       const double rr = sig_max / sig_b;
       const double k = rr * rr - 1.0;
       const double a = mu_b * k, b = (1.0 - mu_b) * k;
-      double lnB;
-      rec = ara_beta_rec_f64(a, b, &lnB);  // p0 from the same ln B(a,b): one set of lgamma calls
+      rec = ara_beta_rec_staged(a, b);
       rec.mx = (float)m;
       if (!(rec.a > 0.f) || !(rec.b > 0.f)) f |= 16u;  // alpha or beta outside binary32 range
     }
@@ -333,12 +333,13 @@ int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64_t occ_base,
                                       const int64_t* offsets, int64_t t_begin, int64_t n,
-                                      int32_t catalog, unsigned int* d_flags, cudaStream_t st) {
+                                      int32_t catalog, unsigned int* d_flags, cudaStream_t st,
+                                      int32_t* ids_out) {
   if (n == 0) return cudaSuccess;
   int64_t blocks = (n * 32 + kThreads - 1) / kThreads;
   if (blocks > 148 * 64) blocks = 148 * 64;
   validate_yet_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(ids, ts, occ_base, offsets, t_begin,
-                                                              n, catalog, d_flags);
+                                                              n, catalog, d_flags, ids_out);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -203,6 +203,24 @@ ARA_HD BetaRec ara_beta_rec_f64(double a, double b, double* lnB_out) {
   return r;
 }
 
+// The record staged for an ELT: the constants of ara_beta_rec_f64, except p0 = I_{x0}(a,b), which
+// only picks the tail an inversion solves and is taken in binary32: at the mean the prefactor is
+// e^{L0} exactly, so p0 = e^{L0} K(a,b,x0) / a (x0 below the fraction's threshold when a <= b),
+// else 1 - e^{L0} K(b,a,y0) / b.  Within ~1e-7 of the binary64 value over the ELT value law.
+ARA_HD BetaRec ara_beta_rec_staged(double a, double b) {
+  const double s = a + b;
+  const double lnx0 = log(a / s), lny0 = log(b / s);
+  const double lnB = lgamma(a) + lgamma(b) - lgamma(s);
+  BetaRec r;
+  r.a = (float)a; r.b = (float)b; r.mx = 1.0f;
+  r.L0 = (float)(a * lnx0 + b * lny0 - lnB);
+  r.lnx0 = (float)lnx0; r.lny0 = (float)lny0; r.lns = (float)log(s);
+  const float P = expf(r.L0);
+  r.p0 = r.a <= r.b ? P * ara_beta_cf(r.a, r.b, expf(r.lnx0), nullptr) / r.a
+                    : 1.0f - P * ara_beta_cf(r.b, r.a, expf(r.lny0), nullptr) / r.b;
+  return r;
+}
+
 // ln x and ln(1 - x) of InvCDF_beta(u; a, b) for binary64 a, b, polished in binary64 (training
 // targets and certification references of the learned surrogate).
 ARA_HD bool ara_exact_quantile_logs(double a, double b, float u, double* lnx, double* ln1mx) {
