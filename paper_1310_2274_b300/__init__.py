@@ -27,6 +27,7 @@ OPT_BAND_WIDTH = 6
 OPT_TABLES = 7
 TABLES_EAGER, TABLES_ON_DEMAND = 0, 1
 TABLE_BUY_HITS = 260.0  # expected hits per record at which on-demand tables are built
+BAND_BUY_PASSES = 3.0  # YET passes after which ARA_SCHED_AUTO makes the band-major copy
 OPT_STREAM_CHUNK = 8
 SCHED_BAND, SCHED_TRIAL, SCHED_AUTO = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "bad handle", 3: "out of memory", 4: "CUDA error",

@@ -67,3 +67,19 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(P, "_lib", None)
     with pytest.raises(ImportError):
         P.lib()
+
+
+def test_binding_constants_match_the_header():
+    """The binding's option values and thresholds are the header's #defines."""
+    import paper_1310_2274_b300 as ara
+
+    text = open(HEADER).read()
+    defs = {m.group(1): m.group(2) for m in re.finditer(r"#define\s+ARA_(\w+)\s+([\d.]+)\b", text)}
+    pairs = {"OPT_SCHEDULE": ara.OPT_SCHEDULE, "SCHED_BAND": ara.SCHED_BAND,
+             "SCHED_TRIAL": ara.SCHED_TRIAL, "SCHED_AUTO": ara.SCHED_AUTO,
+             "OPT_TABLES": ara.OPT_TABLES, "TABLES_EAGER": ara.TABLES_EAGER,
+             "TABLES_ON_DEMAND": ara.TABLES_ON_DEMAND, "OPT_BAND_WIDTH": ara.OPT_BAND_WIDTH,
+             "OPT_STREAM_CHUNK": ara.OPT_STREAM_CHUNK, "TABLE_BUY_HITS": ara.TABLE_BUY_HITS,
+             "BAND_BUY_PASSES": ara.BAND_BUY_PASSES}
+    for name, value in pairs.items():
+        assert float(defs[name]) == float(value), name

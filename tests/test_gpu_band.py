@@ -240,3 +240,33 @@ def test_dense_64_elt_layer_splits_events_and_overflows_the_hit_map(ara, oracle)
     scale = np.maximum(np.maximum(np.abs(o), terms.agg_ret), 1.0)
     assert np.max(np.abs(gb - o) / scale) <= YLT_TOL
     assert np.all(gb[lens == 0] == 0.0) and np.count_nonzero(gb) >= 4
+
+
+def test_auto_schedule_buys_the_band_copy_once_it_pays(ara):
+    """ARA_SCHED_AUTO (the default) runs trial-major (one launch) until the YET's table runs
+    reach ARA_BAND_BUY_PASSES passes of its occurrences, then makes the band-major copy (5
+    launches) and runs band-major (band kernel and finalisation) from then on; every run gives
+    the same year losses, bit for bit."""
+    w = synth.paper(n_trials=N)
+    with ara.Context(seed=42) as c:
+        yet, elts, layer = c.stage_workload(w)
+        launches, ylts = [], []
+        for _ in range(5):
+            s0 = c.stats()["launches"]
+            ylts.append(c.run(yet, layer, 0, N))
+            launches.append(c.stats()["launches"] - s0)
+        # whole-YET runs: passes 1 and 2 rent, the third reaches 3 passes and buys
+        assert ara.BAND_BUY_PASSES == 3.0
+        assert launches == [1, 1, 5 + 2, 2, 2], launches
+        for y in ylts[1:]:
+            np.testing.assert_array_equal(y, ylts[0])
+        # runs over part of the trials count their share of the occurrences
+        c2 = ara.Context(seed=42)
+        yet2, elts2, layer2 = c2.stage_workload(w)
+        got = []
+        for _ in range(6):
+            s0 = c2.stats()["launches"]
+            c2.run(yet2, layer2, 0, N // 2)
+            got.append(c2.stats()["launches"] - s0)
+        c2.close()
+        assert got == [1, 1, 1, 1, 1, 5 + 2], got

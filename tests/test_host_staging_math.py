@@ -1,8 +1,9 @@
-"""Staging arithmetic compiled for the host from the device headers: the table build's
-double-float sum and product keep ~48 bits, the continued fraction of DLMF 8.17.22 that polishes
-every knot agrees with a long-double evaluation of the same recurrence to within its 1e-10
-stopping rule, and the start tables of the Newton-Halley inversion estimate the root to within
-the 3e-4 that lets one Halley step end it.  The host check of a host-resident YET's timestamps
+"""Staging arithmetic compiled for the host from the device headers: the double-float sum and
+product keep ~48 bits, the continued fraction of DLMF 8.17.22 behind the binary64-polished
+quantiles agrees with a long-double evaluation of the same recurrence to within its 1e-10
+stopping rule, the certified tables err like the binary32 inversion they are checked against, and
+the start tables of the Newton-Halley inversion estimate the root to within the 3e-4 that lets one
+Halley step end it.  The host check of a host-resident YET's timestamps
 (vectorised where the CPU has AVX2) flags exactly what the plain definition flags."""
 
 import os
@@ -96,3 +97,26 @@ def test_clamped_records_invert_to_a_valid_quantile(oracle):
                     n_sensitive += 1
                     assert abs(oracle.betainc(a, b, x) - u) <= 5e-6, (mean, u, x, xo)
             assert 0 < n_sensitive <= 400  # the window holds the band, a few 1e-5 of u
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs a host C++ compiler")
+def test_binary32_tables_against_polished_quantiles():
+    """The tables a run builds (binary32 knots, checked against the binary32 inversion) certify
+    every record of the ELT value law and err like that inversion: over records staged as
+    ara_add_elt stages them, x against the binary64-polished quantile, relatively, down to
+    x = 1e-12."""
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "table_check")
+        subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC, "-o", exe,
+                        os.path.join(HERE, "table_check.cpp")], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    n_rec, certified = int(out[0]), int(out[1])
+    worst_t, mean_t, worst_n, mean_n, worst_t4, worst_n4 = (float(v) for v in out[2:])
+    assert n_rec == 1500 and certified == n_rec
+    # the check admits 1e-6 in L plus the inversion's own rounding (capped at 1e-5) and 4 units
+    # of the binary32 rounding of L (which dominates for tiny x); on average the tables sit within
+    # a few 1e-7 of the exact quantile, as the inversion does
+    assert worst_t <= 2.5e-5 and mean_t <= 1e-6
+    assert worst_n <= 1e-5 and mean_n <= 5e-7
+    # where losses matter (x >= 1e-4), both within 1e-5
+    assert worst_t4 <= 1e-5 and worst_n4 <= 1e-5
