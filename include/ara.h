@@ -122,7 +122,9 @@ ARA_API ara_status ara_last_error_detail(const ara_ctx* ctx, char* buf, size_t n
  *     never more than twice the cheaper of the two in hindsight.  Work is counted in expected
  *     hits per record, (occurrences of the run's trials) / (catalogue size), against
  *     ARA_TABLE_BUY_HITS, the measured break-even of build time per record over the per-hit
- *     saving of a table (a paper-scale pass, ~400 hits per record, buys at once).  Results of a
+ *     saving of a table (a paper-scale pass, ~400 hits per record, buys at once).  A layer none
+ *     of whose ELTs has tables yet gets them built straight into its own packed order (the ELTs
+ *     keep none and go on renting for other layers).  Results of a
  *     run are those of the inversion it used (both are checked against the oracle).
  *   A server (ara_server_create) builds every missing table of its YET's ELTs when created. */
 #define ARA_OPT_TABLES 7
@@ -263,7 +265,8 @@ ARA_API ara_status ara_not_converged(ara_ctx* ctx, int64_t* count);
  * out[0] Newton inversions, out[1] Newton iterations, out[2] continued-fraction terms,
  * out[3] inversions that hit the iteration cap, out[4] hits (ELT records met, sigma = 0 ones
  * included), out[5] kernel launches issued by the library in this process (all contexts),
- * out[6] table evaluations, out[7] records of live ELTs whose table failed certification,
+ * out[6] table evaluations, out[7] records whose table failed certification (those of live ELTs,
+ * and of live layers whose tables were built for the layer alone),
  * out[8] surrogate evaluations.  They state the algorithmic work of a launch. */
 ARA_API ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]);
 

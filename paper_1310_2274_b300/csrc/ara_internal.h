@@ -81,6 +81,8 @@ struct LayerDev {
   uint32_t* packed_rec = nullptr;  // [n_packed] caller record index (verification)
   float* corr = nullptr;           // [n_packed] correlated weights (NULL: none in the layer)
   int64_t n_packed = 0;
+  bool own_tables = false;         // tables built in place (the ELTs had none)
+  int64_t n_uncertified = 0;       // records of tables built for the layer alone that failed
   int32_t band_log2w = 0;          // band width of the band-major schedule (0: trial-major only)
   int32_t band_want = 0;           // width chosen at build whose band-major YET copy is made at
                                    // the first run that takes the band schedule (0: none)
@@ -211,6 +213,13 @@ struct TableJobs {
 };
 cudaError_t launch_build_tables(const TableJobs& jobs, unsigned long long* d_uncertified,
                                 cudaStream_t st);
+// elt_tables[n * kTablePieces] = the tables of the n records (ids) of the ELT in slot `slot` of a
+// layer whose tables (layer_tables, packed order, lookup entries evt) were built in place;
+// *d_uncertified (zeroed by the caller) += the records among them whose table failed.
+cudaError_t launch_unpack_tables(int64_t n, const int32_t* ids, int slot, int mask_words,
+                                 const uint32_t* evt, const TablePiece* layer_tables,
+                                 TablePiece* elt_tables, unsigned long long* d_uncertified,
+                                 cudaStream_t st);
 // dst[i * kStartFloats ...] = the start table at d_src[i], for the n packed records of a layer
 cudaError_t launch_gather_starts(int64_t n, const float* const* d_src, float* dst, cudaStream_t st);
 // dst[i * kTablePieces ...] = the table at d_src[i], for the n packed records of a layer

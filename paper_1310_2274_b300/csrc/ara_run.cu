@@ -53,6 +53,24 @@ int layer_inversion(const ara_ctx* ctx, const LayerDev& L) {
   return (m == 0 && L.tables == nullptr) ? 1 : m;
 }
 
+// A live layer whose in-place tables cover ELT h (its slot in *slot), or null.
+static const LayerDev* layer_holding_tables(const ara_ctx* ctx, int32_t h, int* slot) {
+  for (const auto& l : ctx->layers) {
+    if (!l.live || !l.own_tables || !l.tables) continue;
+    for (int j = 0; j < l.n_slots; ++j)
+      if (l.handles[j] == h) {
+        *slot = j;
+        return &l;
+      }
+  }
+  return nullptr;
+}
+
+static bool tables_available(const ara_ctx* ctx, int32_t h) {
+  int slot;
+  return ctx->elts[h].tables != nullptr || layer_holding_tables(ctx, h, &slot) != nullptr;
+}
+
 // The certified tables of the ELTs `handles` that lack them, built together (kMaxTableJobs ELTs
 // per launch, one synchronisation at the end).
 static ara_status ensure_tables(ara_ctx* ctx, const int32_t* handles, int n_handles) {
@@ -62,6 +80,40 @@ static ara_status ensure_tables(ara_ctx* ctx, const int32_t* handles, int n_hand
     if (!ctx->elts[h].tables && std::find(todo.begin(), todo.end(), h) == todo.end())
       todo.push_back(h);
   }
+  if (todo.empty()) return ARA_OK;
+  // an ELT whose records a live layer holds tables for (built in place) takes a copy of them
+  std::vector<int32_t> rest;
+  for (int32_t h : todo) {
+    int slot = -1;
+    const LayerDev* src = layer_holding_tables(ctx, h, &slot);
+    if (!src) {
+      rest.push_back(h);
+      continue;
+    }
+    EltDev& e = ctx->elts[h];
+    unsigned long long uncert = 0;
+    cudaError_t err = obj_alloc(ctx, &e.tables, e.n * kTablePieces);
+    if (err == cudaSuccess) err = ensure_scratch(ctx, scratch_bytes<unsigned long long>(1));
+    unsigned long long* d_uncert = reinterpret_cast<unsigned long long*>(ctx->d_scratch);
+    if (err == cudaSuccess) err = cudaMemsetAsync(d_uncert, 0, sizeof uncert, ctx->stream);
+    if (err == cudaSuccess)
+      err = launch_unpack_tables(e.n, e.ids, slot, src->mask_words, src->evt, src->tables,
+                                 e.tables, d_uncert, ctx->stream);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(ctx->stream);
+      obj_free(ctx, e.tables);
+      e.tables = nullptr;
+      return fail(ctx, err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA,
+                  "tables from a layer: %s", cudaGetErrorString(err));
+    }
+    e.n_uncertified = (int64_t)uncert;
+  }
+  todo.swap(rest);
   if (todo.empty()) return ARA_OK;
   const int n = (int)todo.size();
   std::vector<unsigned long long> uncert(n, 0ull);
@@ -126,9 +178,49 @@ static ara_status ensure_starts(ara_ctx* ctx, const int32_t* handles, int n_hand
   return ARA_OK;
 }
 
-// The layer's packed table copy (its ELTs' tables first).
+// A layer's tables built straight into its packed order from its packed records (none of its
+// ELTs has tables yet): the ELTs' own copies and the gather are skipped; their rent-or-buy goes
+// on for other layers.
+static ara_status build_layer_tables(ara_ctx* ctx, LayerDev& L) {
+  unsigned long long uncert = 0;
+  cudaError_t err = obj_alloc(ctx, &L.tables, L.n_packed * kTablePieces);
+  if (err == cudaSuccess) err = ensure_scratch(ctx, scratch_bytes<unsigned long long>(1));
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    obj_free(ctx, L.tables);
+    L.tables = nullptr;
+    return fail(ctx, ARA_ERR_OOM, "layer tables: %s", cudaGetErrorString(err));
+  }
+  unsigned long long* d_uncert = reinterpret_cast<unsigned long long*>(ctx->d_scratch);
+  TableJobs jobs{};
+  jobs.n = 1;
+  jobs.recs[0] = L.packed;
+  jobs.tables[0] = L.tables;
+  jobs.first[1] = L.n_packed;
+  err = cudaMemsetAsync(d_uncert, 0, sizeof uncert, ctx->stream);
+  if (err == cudaSuccess) err = launch_build_tables(jobs, d_uncert, ctx->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(ctx->stream);
+    obj_free(ctx, L.tables);
+    L.tables = nullptr;
+    return fail(ctx, ARA_ERR_CUDA, "building layer tables: %s", cudaGetErrorString(err));
+  }
+  L.n_uncertified = (int64_t)uncert;
+  L.own_tables = true;
+  return ARA_OK;
+}
+
+// The layer's packed table copy: built in place when none of its ELTs has tables, else gathered
+// from theirs (those missing built first).
 static ara_status ensure_layer_tables(ara_ctx* ctx, LayerDev& L) {
   if (L.tables) return ARA_OK;
+  bool none = true;
+  for (int j = 0; j < L.n_slots; ++j) none = none && !tables_available(ctx, L.handles[j]);
+  if (none) return build_layer_tables(ctx, L);
   const ara_status s = ensure_tables(ctx, L.handles, L.n_slots);
   if (s != ARA_OK) return s;
   const TablePiece** d_src = nullptr;  // staging scratch
@@ -232,7 +324,8 @@ static ara_status rent_or_buy(ara_ctx* ctx, LayerDev& L, int64_t n) {
   bool buy = true;
   for (int j = 0; j < L.n_slots; ++j) {
     const EltDev& e = ctx->elts[L.handles[j]];
-    if (!e.tables && e.rent_hits + per_rec < ARA_TABLE_BUY_HITS) buy = false;
+    if (!tables_available(ctx, L.handles[j]) && e.rent_hits + per_rec < ARA_TABLE_BUY_HITS)
+      buy = false;
   }
   if (buy) return ensure_layer_tables(ctx, L);
   for (int j = 0; j < L.n_slots; ++j) {
@@ -805,6 +898,8 @@ ara_status ara_get_stats(ara_ctx* ctx, int64_t out[9]) {
   int64_t unc = 0;
   for (const auto& e : ctx->elts)
     if (e.live) unc += e.n_uncertified;
+  for (const auto& l : ctx->layers)
+    if (l.live) unc += l.n_uncertified;
   out[7] = unc;
   out[8] = (int64_t)v[5];
   return ARA_OK;

@@ -90,6 +90,39 @@ __global__ void gather_starts_kernel(int64_t n, const float* const* __restrict__
 }
 static_assert(kStartFloats * sizeof(float) % 16 == 0, "start tables copy in 16-byte parts");
 
+// An ELT's tables copied out of a layer whose tables were built in its packed order: record r of
+// the ELT in slot `slot` sits at packed position base(e) + (rank of the slot among e's mask bits),
+// e its event.  One thread per 16 bytes, kParts per record; uncert counts the ELT's records whose
+// table failed certification.
+__global__ void unpack_tables_kernel(int64_t n, const int32_t* __restrict__ ids, int slot,
+                                     int mask_words, const uint32_t* __restrict__ evt,
+                                     const TablePiece* __restrict__ layer_tables,
+                                     TablePiece* __restrict__ elt_tables,
+                                     unsigned long long* uncert) {
+  constexpr int kParts = kTablePieces * (int)sizeof(TablePiece) / 16;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kParts) return;
+  const int64_t r = i / kParts;
+  const int part = (int)(i - r * kParts);
+  const int64_t e = ids[r];
+  uint32_t base, rank;
+  if (mask_words == 1) {
+    const uint2 v = reinterpret_cast<const uint2*>(evt)[e];
+    base = v.x;
+    rank = __popc(v.y & ((1u << slot) - 1u));
+  } else {
+    const uint4 v = reinterpret_cast<const uint4*>(evt)[e];
+    base = v.x;
+    const uint64_t m = ((uint64_t)v.z << 32) | v.y;
+    rank = __popcll(m & ((1ull << slot) - 1ull));
+  }
+  const uint4* src =
+      reinterpret_cast<const uint4*>(layer_tables + (int64_t)(base + rank) * kTablePieces);
+  const uint4 v = src[part];
+  reinterpret_cast<uint4*>(elt_tables + r * kTablePieces)[part] = v;
+  if (part == kParts - 1 && v.w == kPieceNewton) atomicAdd(uncert, 1ull);  // piece 63's flag
+}
+
 }  // namespace
 
 cudaError_t launch_gather_starts(int64_t n, const float* const* d_src, float* dst,
@@ -117,6 +150,19 @@ cudaError_t launch_build_starts(int64_t n, const BetaRec* recs, float* starts, c
   const int threads = 128;
   build_starts_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(n, recs,
                                                                                   starts);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_tables(int64_t n, const int32_t* ids, int slot, int mask_words,
+                                 const uint32_t* evt, const TablePiece* layer_tables,
+                                 TablePiece* elt_tables, unsigned long long* d_uncertified,
+                                 cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t total = n * (kTablePieces * (int64_t)sizeof(TablePiece) / 16);
+  unpack_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
+      n, ids, slot, mask_words, evt, layer_tables, elt_tables, d_uncertified);
   count_launches(1);
   return cudaGetLastError();
 }
