@@ -120,3 +120,18 @@ def test_binary32_tables_against_polished_quantiles():
     assert worst_n <= 1e-5 and mean_n <= 5e-7
     # where losses matter (x >= 1e-4), both within 1e-5
     assert worst_t4 <= 1e-5 and worst_n4 <= 1e-5
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs a host C++ compiler")
+def test_staging_lngamma_against_the_c_library():
+    """The staging's branch-free ln Gamma (shift by 8, Stirling's series through B_12) agrees with
+    lgamma to ~1e-14 of max(1, |ln Gamma|), and ln B(a, b) over the ELT value law to 1e-12: far
+    below the binary32 rounding of the constants it feeds."""
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "lngamma_check")
+        subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC, "-o", exe,
+                        os.path.join(HERE, "lngamma_check.cpp")], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    worst, worst_b = float(out[0]), float(out[1])
+    assert worst <= 5e-14
+    assert worst_b <= 1e-12
