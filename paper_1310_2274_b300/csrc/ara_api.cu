@@ -273,10 +273,11 @@ ara_status ara_create_yet(ara_ctx* ctx, int64_t n_trials, const int64_t* trial_o
   if (ts_on_host)
     ts_check = std::thread(
         [&]() { host_flags = validate_timestamps_host(off.data(), timestamps, n_trials); });
-  // device offsets are copied where they are; ids the device can read are copied by the
-  // validation kernel as it checks them (one pass over them), others first
+  // device offsets are copied where they are; ids in device memory are copied by the validation
+  // kernel as it checks them (one pass over them); host ones, even page-locked, by one bulk copy
+  // first (the kernel's scattered reads would cross PCIe slower than the copy engine)
   const int64_t* off_src = dev_path ? trial_offsets : off.data();
-  const int32_t* r_ids = n_occ > 0 ? device_readable(event_ids) : nullptr;
+  const int32_t* r_ids = n_occ > 0 && is_device_ptr(event_ids) ? event_ids : nullptr;
   if ((!r_ids && (e = copy_in(y.ids, event_ids, n_occ, ctx->stream)) != cudaSuccess) ||
       (e = copy_in(y.offsets, off_src, n_trials + 1, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
