@@ -3,14 +3,14 @@
 
 A step is one whole analysis of the paper-scale layer (800,000 trials x 1,000 events x 16 ELTs)
 from raw inputs already resident in HBM: stage the YET (ara_create_yet), the 16 ELTs
-(ara_add_elt) and the layer (ara_add_layer), run Algorithm 1 (ara_run -> YLT; with ~400 hits per
-record a single pass buys the records' certified quantile tables, built in binary32 in one launch,
-and inverts the beta CDF through them), take PML/TVaR at 1-in-100/250/500/1000
-(ara_risk_measures), and free everything.  The metric is trial-event-ELT evaluations per
-second, N * K * J / step time, i.e. the paper's "s per 800k x 1000 run".  Beside it: the same analysis re-priced with the tables
-resident (the serving situation), the step through host buffers (e2e), the error of PML/TVaR
-against the FP64 oracle, the precision study, the learned surrogate, serving, and the CPU
-oracle's rate.  Prints one JSON line (rank 0).
+(ara_add_elts: one call, one check) and the layer (ara_add_layer), run Algorithm 1 (ara_run ->
+YLT; with ~400 hits per record a single pass buys the records' certified quantile tables, built in
+binary32 in one launch, and inverts the beta CDF through them), take PML/TVaR at 1-in-100/250/500/
+1000 (ara_risk_measures), and free everything.  The metric is trial-event-ELT evaluations per
+second, N * K * J / step time, i.e. the paper's "s per 800k x 1000 run".  Beside it: the same
+analysis re-priced with the tables resident (the serving situation), the step through host
+buffers (e2e), the error of PML/TVaR against the FP64 oracle, the precision study, the learned
+surrogate, serving, and the CPU oracle's rate.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -344,7 +344,7 @@ def run_ours(a):
 
     def cold_step(timed):
         yet = ctx.create_yet(off_d, ids_d, ts_d, 2_000_000)
-        elts = [ctx.add_elt(yet, *v) for v in elts_d]
+        elts = ctx.add_elts(yet, elts_d)
         cold_handles[:] = elts  # the uniforms are keyed by the ELT handles (the oracle needs them)
         layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
         if timed:
@@ -407,8 +407,8 @@ def run_ours(a):
         t = time.perf_counter()
         yet_p = ctx.create_yet(off_d, ids_d, ts_d, 2_000_000)
         t = tick("create_yet", t)
-        elts_p = [ctx.add_elt(yet_p, *v) for v in elts_d]
-        t = tick("add_elt_x16", t)
+        elts_p = ctx.add_elts(yet_p, elts_d)
+        t = tick("add_elts_16", t)
         layer_p = ctx.add_layer(elts_p, terms.occ_ret, terms.occ_lim, terms.agg_ret,
                                 terms.agg_lim)
         t = tick("add_layer", t)
@@ -428,7 +428,7 @@ def run_ours(a):
     yet = ctx.create_yet(off_d, ids_d, ts_d, 2_000_000)
     t_st = time.perf_counter()
     ctx.set_option(ara.OPT_TABLES, ara.TABLES_EAGER)  # certified tables built at staging
-    elts = [ctx.add_elt(yet, *v) for v in elts_d]
+    elts = ctx.add_elts(yet, elts_d)
     torch.cuda.synchronize(dev)
     tables_build_s = time.perf_counter() - t_st
     layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
@@ -683,11 +683,11 @@ def run_ours(a):
         "gpu_launches": int(s1["launches"] - s0["launches"]),
         "clocks": clk,
         "roofline": roofline,
-        "step": {"what": "ara_create_yet (device arrays: copy + validation) + 16 x ara_add_elt "
-                         "(device arrays: records) + ara_add_layer + ara_run + "
+        "step": {"what": "ara_create_yet (device arrays: copy + validation) + ara_add_elts (16 "
+                         "ELTs from device arrays, one check) + ara_add_layer + ara_run + "
                          "ara_risk_measures + frees; tables on demand (this single pass buys "
-                         "them: one build launch over the 16 ELTs, then the trial-major table "
-                         "kernel)",
+                         "them: one build launch over the layer's records, then the trial-major "
+                         "table kernel)",
                  "run_ms": run_ms, "phases_ms": step_phases,
                  "per_launch": {k: d[k] for k in ("hits", "table_evals", "inversions",
                                                   "newton", "cf_terms")},
@@ -1034,7 +1034,7 @@ def e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream):
     def step(host_yet):
         make = ctx.create_yet_host if host_yet else ctx.create_yet
         yet = make(off, ids, ts, 2_000_000)
-        elts = [ctx.add_elt(yet, *(v[1] for v in p)) for p in elt_p]
+        elts = ctx.add_elts(yet, [tuple(v[1] for v in p) for p in elt_p])
         layer = ctx.add_layer(elts, terms.occ_ret, terms.occ_lim, terms.agg_ret, terms.agg_lim)
         ctx.run(yet, layer, 0, a.trials, out=ylt)
         pml, tvar = ctx.risk_measures(ylt, rps)
@@ -1076,7 +1076,7 @@ def e2e(a, ara, ctx, yet_h, elts_h, terms, rps, dev, stream):
             "tables": "on demand (rent-or-buy): this single pass builds them, then uses them",
             "resident_yet_ms_per_step": dt_resident * 1e3,
             "resident_yet_eager_tables_ms_per_step": dt_eager * 1e3,
-            "path": "ara_create_yet_host + 16 x ara_add_elt + ara_add_layer from pinned host "
+            "path": "ara_create_yet_host + ara_add_elts (16 ELTs) + ara_add_layer from pinned host "
                     "memory, ara_run into a host YLT, ara_risk_measures, frees"}
 
 

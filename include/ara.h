@@ -183,7 +183,8 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
  * the sigma_beta_max clamp of §3.3, sigma_beta set to sigma_beta_max (1 - 2^-20) when above it)
  * and the constants of the inversion, then stored as binary32 (32 bytes per record); the record's
  * certified quantile table is built at the same time (2 KB per record, see ARA_OPT_INVERSION;
- * deferred under ARA_TABLES_ON_DEMAND), and its start table (512 bytes per record).
+ * deferred under ARA_TABLES_ON_DEMAND); its start table (512 bytes per record) when a
+ * Newton-Halley run first needs it.
  * The handle number keys the record's uniforms: Philox4x32-10 counter (k, i_lo, elt/4, i_hi),
  * key (seed_lo, seed_hi), word elt mod 4, for occurrence k of trial i.  The arrays may be host or
  * device memory; device memory and page-locked host memory mapped into the device's address
@@ -192,6 +193,16 @@ ARA_API ara_status ara_free_yet(ara_ctx* ctx, int32_t yet);
 ARA_API ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
                                const double* mean, const double* sd, const double* max_exposure,
                                int32_t* elt_out);
+/* Several ELTs of one YET staged together, each as ara_add_elt_corr stages it: ELT j has n[j]
+ * records in event_ids[j], mean[j], sd[j] (sigma_I), sd_corr[j] (sigma_C; sd_corr itself or any
+ * entry NULL: all zero) and max_exposure[j].  Their staging is queued back to back and checked
+ * once at the end (one synchronisation for all of them), and under ARA_TABLES_EAGER their tables
+ * are built in one launch.  Handles go to elts_out[0 .. n_elts) in order.  All or nothing: if an
+ * ELT is rejected none is added, and the error detail names the first rejected ELT. */
+ARA_API ara_status ara_add_elts(ara_ctx* ctx, int32_t yet, int32_t n_elts, const int64_t* n,
+                                const int32_t* const* event_ids, const double* const* mean,
+                                const double* const* sd, const double* const* sd_corr,
+                                const double* const* max_exposure, int32_t* elts_out);
 /* The same with the two standard deviations of paper §3.1: sd_indep (sigma_I) and sd_corr
  * (sigma_C, NULL = all zero), both >= 0.  sigma = sigma_I + sigma_C feeds the moments (§3.2 step
  * 1).  A hit's uniform follows §3.2 steps 2-5: the hit's own Philox uniform above plays

@@ -108,6 +108,7 @@ _SIGNATURES = {
     "ara_free_yet": ([_P, _I32], C.c_int),
     "ara_add_elt": ([_P, _I32, _I64, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
     "ara_add_elt_corr": ([_P, _I32, _I64, _P, _P, _P, _P, _P, C.POINTER(_I32)], C.c_int),
+    "ara_add_elts": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "ara_free_elt": ([_P, _I32], C.c_int),
     "ara_add_layer": ([_P, _P, _I32, _D, _D, _D, _D, C.POINTER(_I32)], C.c_int),
     "ara_free_layer": ([_P, _I32], C.c_int),
@@ -285,6 +286,23 @@ class Context:
                                                _ptr(mu), _ptr(s), _ptr(sc), _ptr(mx),
                                                C.byref(out)))
         return out.value
+
+    def add_elts(self, yet: int, elts) -> list:
+        """Stage several ELTs at once (one check for all of them; all or none are added).  elts:
+        a sequence of (event_ids, mean, sd, max_exposure) or (..., sd_corr) tuples."""
+        arrs = []
+        for e in elts:
+            ids, mu, s, mx = (_np(e[0], np.int32), _np(e[1], np.float64), _np(e[2], np.float64),
+                              _np(e[3], np.float64))
+            sc = _np(e[4], np.float64) if len(e) > 4 and e[4] is not None else None
+            arrs.append((ids, mu, s, mx, sc))
+        k = len(arrs)
+        n = np.array([int(a[0].shape[0]) for a in arrs], dtype=np.int64)
+        col = lambda i: (C.c_void_p * max(k, 1))(*[_ptr(a[i]) for a in arrs])  # noqa: E731
+        out = np.full(max(k, 1), -1, dtype=np.int32)
+        self._check(lib().ara_add_elts(self._h, yet, k, _ptr(n), col(0), col(1), col(2), col(4),
+                                       col(3), _ptr(out)))
+        return [int(v) for v in out[:k]]
 
     def add_layer(self, elts, occ_ret: float, occ_lim: float, agg_ret: float,
                   agg_lim: float) -> int:

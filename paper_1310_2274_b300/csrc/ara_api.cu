@@ -382,100 +382,148 @@ ara_status ara_free_yet(ara_ctx* ctx, int32_t yet) {
 }
 
 // ---- ELT ------------------------------------------------------------------------------------
-ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
-                            const double* mean, const double* sd_indep, const double* sd_corr,
-                            const double* max_exposure, int32_t* elt_out) {
-  const double* sd = sd_indep;
+ara_status ara_add_elts(ara_ctx* ctx, int32_t yet, int32_t n_elts, const int64_t* n,
+                        const int32_t* const* event_ids, const double* const* mean,
+                        const double* const* sd, const double* const* sd_corr,
+                        const double* const* max_exposure, int32_t* elts_out) {
   if (!ctx) return ARA_ERR_INVALID_ARG;
-  if (!elt_out) return fail(ctx, ARA_ERR_INVALID_ARG, "elt_out is NULL");
+  if (n_elts < 0) return fail(ctx, ARA_ERR_INVALID_ARG, "n_elts < 0");
+  if (n_elts > 0 && (!elts_out || !n || !event_ids || !mean || !sd || !max_exposure))
+    return fail(ctx, ARA_ERR_INVALID_ARG, "NULL argument");
   if (yet < 0 || yet >= (int32_t)ctx->yets.size() || !ctx->yets[yet].live)
     return fail(ctx, ARA_ERR_BAD_HANDLE, "bad YET handle %d", yet);
-  if (n < 0 || n >= ((int64_t)1 << 31)) return fail(ctx, ARA_ERR_INVALID_ARG, "bad record count");
-  if (n > 0 && (!event_ids || !mean || !sd || !max_exposure))
-    return fail(ctx, ARA_ERR_INVALID_ARG, "NULL ELT array");
+  for (int32_t j = 0; j < n_elts; ++j) {
+    if (n[j] < 0 || n[j] >= ((int64_t)1 << 31))
+      return fail(ctx, ARA_ERR_INVALID_ARG, "bad record count of ELT %d", j);
+    if (n[j] > 0 && (!event_ids[j] || !mean[j] || !sd[j] || !max_exposure[j]))
+      return fail(ctx, ARA_ERR_INVALID_ARG, "NULL array of ELT %d", j);
+  }
+  if (n_elts == 0) return ARA_OK;
   ara_status s = set_device(ctx);
   if (s != ARA_OK) return s;
   const YetDev& y = ctx->yets[yet];
   const bool defer = ctx->table_policy == ARA_TABLES_ON_DEMAND;
-  EltDev e;
-  e.yet = yet;
-  e.n = n;
-  double *d_mean = nullptr, *d_sd = nullptr, *d_sdc = nullptr, *d_mx = nullptr;
-  unsigned int* d_dup = nullptr;
-  unsigned long long* d_uncert = nullptr;
-  unsigned long long uncert = 0;
-  cudaError_t err;
-  // the input copies and duplicate marks are staging scratch; the start tables of the
-  // Newton-Halley inversion are built when a run first needs them
-  auto cleanup = [&]() { cudaStreamSynchronize(ctx->stream); };
-  const size_t scratch = scratch_bytes<double>(n) * (sd_corr ? 4 : 3) +
-                         scratch_bytes<unsigned int>(y.catalog) +
-                         scratch_bytes<unsigned long long>(1);
-  if ((err = obj_alloc(ctx, &e.ids, n)) != cudaSuccess ||
-      (err = obj_alloc(ctx, &e.recs, n)) != cudaSuccess ||
-      (!defer && (err = obj_alloc(ctx, &e.tables, n * kTablePieces)) != cudaSuccess) ||
-      (sd_corr && (err = obj_alloc(ctx, &e.corr, n)) != cudaSuccess) ||
-      (err = ensure_scratch(ctx, scratch)) != cudaSuccess) {
+  auto sdc_of = [&](int32_t j) { return sd_corr ? sd_corr[j] : nullptr; };
+  // staging scratch: each ELT's check flags and uncertified count, the duplicate marks, and the
+  // input copies of the largest ELT (reused ELT after ELT: the stream orders them); sized once,
+  // before any work is queued
+  size_t temps = 0;
+  for (int32_t j = 0; j < n_elts; ++j)
+    temps = std::max(temps, scratch_bytes<double>(n[j]) * (sdc_of(j) ? 4 : 3));
+  const size_t scratch = scratch_bytes<unsigned int>(n_elts) +
+                         scratch_bytes<unsigned long long>(n_elts) +
+                         scratch_bytes<unsigned int>(y.catalog) + temps;
+  std::vector<EltDev> es((size_t)n_elts);
+  auto undo = [&]() {
     cudaGetLastError();
-    cleanup();
-    free_elt(ctx, e);
-    return fail(ctx, ARA_ERR_OOM, "ELT of %lld records: %s", (long long)n, cudaGetErrorString(err));
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& e : es) free_elt(ctx, e);
+  };
+  cudaError_t err = cudaSuccess;
+  for (int32_t j = 0; j < n_elts && err == cudaSuccess; ++j) {
+    EltDev& e = es[(size_t)j];
+    e.yet = yet;
+    e.n = n[j];
+    if ((err = obj_alloc(ctx, &e.ids, e.n)) == cudaSuccess &&
+        (err = obj_alloc(ctx, &e.recs, e.n)) == cudaSuccess &&
+        (defer || (err = obj_alloc(ctx, &e.tables, e.n * kTablePieces)) == cudaSuccess) && sdc_of(j))
+      err = obj_alloc(ctx, &e.corr, e.n);
+  }
+  if (err == cudaSuccess) err = ensure_scratch(ctx, scratch);
+  if (err != cudaSuccess) {
+    undo();
+    return fail(ctx, ARA_ERR_OOM, "%d ELTs: %s", n_elts, cudaGetErrorString(err));
   }
   ScratchCarver sc{ctx->d_scratch};
-  d_mean = sc.take<double>(n);
-  d_sd = sc.take<double>(n);
-  d_mx = sc.take<double>(n);
-  if (sd_corr) d_sdc = sc.take<double>(n);
-  d_dup = sc.take<unsigned int>(y.catalog);
-  d_uncert = sc.take<unsigned long long>(1);
-  // inputs the device can read where they are (device memory, mapped page-locked host memory)
-  // are read in place by the staging kernel, which also writes the ids' device copy; the others
-  // are copied first.  (Reads over PCIe by the kernel do not queue behind other copies, such as
-  // the ids a host-resident YET copies ahead.)
-  const int32_t* r_ids = device_readable(event_ids);
-  const double* r_mean = device_readable(mean);
-  const double* r_sd = device_readable(sd);
-  const double* r_sdc = sd_corr ? device_readable(sd_corr) : nullptr;
-  const double* r_mx = device_readable(max_exposure);
-  unsigned int flags = 0;
-  if ((!r_ids && (err = copy_in(e.ids, event_ids, n, ctx->stream)) != cudaSuccess) ||
-      (!r_mean && (err = copy_in(d_mean, mean, n, ctx->stream)) != cudaSuccess) ||
-      (!r_sd && (err = copy_in(d_sd, sd, n, ctx->stream)) != cudaSuccess) ||
-      (sd_corr && !r_sdc && (err = copy_in(d_sdc, sd_corr, n, ctx->stream)) != cudaSuccess) ||
-      (!r_mx && (err = copy_in(d_mx, max_exposure, n, ctx->stream)) != cudaSuccess) ||
-      (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog, ctx->stream)) != cudaSuccess ||
-      (err = cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned int), ctx->stream)) != cudaSuccess ||
-      (err = launch_prepare_elt(n, r_ids ? r_ids : e.ids, r_ids ? e.ids : nullptr,
-                                r_mean ? r_mean : d_mean, r_sd ? r_sd : d_sd,
-                                sd_corr ? (r_sdc ? r_sdc : d_sdc) : nullptr, r_mx ? r_mx : d_mx,
-                                y.catalog, e.recs, e.corr, d_dup, ctx->d_flags,
-                                ctx->stream)) != cudaSuccess ||
-      (err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-      (!defer && (err = launch_build_tables(one_job(e), d_uncert, ctx->stream)) != cudaSuccess) ||
-      (err = cudaMemcpyAsync(&uncert, d_uncert, sizeof uncert, cudaMemcpyDeviceToHost,
-                             ctx->stream)) != cudaSuccess ||
-      (err = cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost,
-                             ctx->stream)) != cudaSuccess ||
-      (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
-    cudaGetLastError();
-    cleanup();
-    free_elt(ctx, e);
-    return fail(ctx, ARA_ERR_CUDA, "staging ELT: %s", cudaGetErrorString(err));
+  unsigned int* d_flags = sc.take<unsigned int>(n_elts);
+  unsigned long long* d_uncert = sc.take<unsigned long long>(n_elts);
+  unsigned int* d_dup = sc.take<unsigned int>(y.catalog);
+  std::vector<unsigned int> flags((size_t)n_elts, 0u);
+  std::vector<unsigned long long> uncert((size_t)n_elts, 0ull);
+  err = cudaMemsetAsync(d_flags, 0, sizeof(unsigned int) * (size_t)n_elts, ctx->stream);
+  if (err == cudaSuccess)
+    err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long) * (size_t)n_elts, ctx->stream);
+  for (int32_t j = 0; j < n_elts && err == cudaSuccess; ++j) {
+    EltDev& e = es[(size_t)j];
+    const int64_t nj = e.n;
+    ScratchCarver tc = sc;
+    double* d_mean = tc.take<double>(nj);
+    double* d_sd = tc.take<double>(nj);
+    double* d_mx = tc.take<double>(nj);
+    double* d_sdc = sdc_of(j) ? tc.take<double>(nj) : nullptr;
+    // inputs the device can read where they are (device memory, mapped page-locked host memory)
+    // are read in place by the staging kernel, which also writes the ids' device copy; the others
+    // are copied first.  (Reads over PCIe by the kernel do not queue behind other copies, such as
+    // the ids a host-resident YET copies ahead.)
+    const int32_t* r_ids = device_readable(event_ids[j]);
+    const double* r_mean = device_readable(mean[j]);
+    const double* r_sd = device_readable(sd[j]);
+    const double* r_sdc = sdc_of(j) ? device_readable(sdc_of(j)) : nullptr;
+    const double* r_mx = device_readable(max_exposure[j]);
+    if ((!r_ids && (err = copy_in(e.ids, event_ids[j], nj, ctx->stream)) != cudaSuccess) ||
+        (!r_mean && (err = copy_in(d_mean, mean[j], nj, ctx->stream)) != cudaSuccess) ||
+        (!r_sd && (err = copy_in(d_sd, sd[j], nj, ctx->stream)) != cudaSuccess) ||
+        (sdc_of(j) && !r_sdc && (err = copy_in(d_sdc, sdc_of(j), nj, ctx->stream)) != cudaSuccess) ||
+        (!r_mx && (err = copy_in(d_mx, max_exposure[j], nj, ctx->stream)) != cudaSuccess) ||
+        (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog,
+                               ctx->stream)) != cudaSuccess)
+      break;
+    err = launch_prepare_elt(nj, r_ids ? r_ids : e.ids, r_ids ? e.ids : nullptr,
+                             r_mean ? r_mean : d_mean, r_sd ? r_sd : d_sd,
+                             sdc_of(j) ? (r_sdc ? r_sdc : d_sdc) : nullptr, r_mx ? r_mx : d_mx,
+                             y.catalog, e.recs, e.corr, d_dup, d_flags + j, ctx->stream);
   }
-  cleanup();
-  if (flags) {
-    free_elt(ctx, e);
-    return fail(ctx, ARA_ERR_INVALID_ARG, "ELT rejected:%s%s%s%s",
-                (flags & 8) ? " event id outside the catalogue" : "",
-                (flags & 16) ? " mean <= 0, an sd < 0 or non-finite value" : "",
-                (flags & 32) ? " max_exposure <= mean with sd > 0" : "",
-                (flags & 64) ? " duplicate event id" : "");
+  // tables at staging (ARA_TABLES_EAGER): all the ELTs' in one launch (kMaxTableJobs a launch)
+  for (int32_t b = 0; !defer && b < n_elts && err == cudaSuccess; b += kMaxTableJobs) {
+    TableJobs jobs{};
+    jobs.n = std::min(kMaxTableJobs, n_elts - b);
+    for (int k = 0; k < jobs.n; ++k) {
+      const EltDev& e = es[(size_t)(b + k)];
+      jobs.recs[k] = e.recs;
+      jobs.tables[k] = e.tables;
+      jobs.first[k + 1] = jobs.first[k] + e.n;
+    }
+    err = launch_build_tables(jobs, d_uncert + b, ctx->stream);
   }
-  e.n_uncertified = (int64_t)uncert;
-  e.live = true;
-  ctx->elts.push_back(e);
-  *elt_out = (int32_t)ctx->elts.size() - 1;
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(flags.data(), d_flags, sizeof(unsigned int) * (size_t)n_elts,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(uncert.data(), d_uncert, sizeof(unsigned long long) * (size_t)n_elts,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    const ara_status st = err == cudaErrorMemoryAllocation ? ARA_ERR_OOM : ARA_ERR_CUDA;
+    undo();
+    return fail(ctx, st, "staging ELTs: %s", cudaGetErrorString(err));
+  }
+  for (int32_t j = 0; j < n_elts; ++j)
+    if (flags[(size_t)j]) {
+      const unsigned int f = flags[(size_t)j];
+      undo();
+      return fail(ctx, ARA_ERR_INVALID_ARG, "ELT %d rejected:%s%s%s%s", j,
+                  (f & 8) ? " event id outside the catalogue" : "",
+                  (f & 16) ? " mean <= 0, an sd < 0 or non-finite value" : "",
+                  (f & 32) ? " max_exposure <= mean with sd > 0" : "",
+                  (f & 64) ? " duplicate event id" : "");
+    }
+  for (int32_t j = 0; j < n_elts; ++j) {
+    EltDev& e = es[(size_t)j];
+    e.n_uncertified = (int64_t)uncert[(size_t)j];
+    e.live = true;
+    ctx->elts.push_back(e);
+    elts_out[j] = (int32_t)ctx->elts.size() - 1;
+  }
   return ARA_OK;
+}
+
+ara_status ara_add_elt_corr(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,
+                            const double* mean, const double* sd_indep, const double* sd_corr,
+                            const double* max_exposure, int32_t* elt_out) {
+  if (!ctx) return ARA_ERR_INVALID_ARG;
+  if (!elt_out) return fail(ctx, ARA_ERR_INVALID_ARG, "elt_out is NULL");
+  return ara_add_elts(ctx, yet, 1, &n, &event_ids, &mean, &sd_indep, &sd_corr, &max_exposure,
+                      elt_out);
 }
 
 ara_status ara_add_elt(ara_ctx* ctx, int32_t yet, int64_t n, const int32_t* event_ids,

@@ -90,3 +90,38 @@ def test_device_resident_yet_checked_on_the_device(ara):
         ts[int(y.offsets[9])] = np.nan
         with pytest.raises(ara.AraError, match="NaN timestamp"):
             ctx.create_yet(dev(y.offsets), dev(y.event_ids), dev(ts), y.catalog_size)
+
+
+def test_add_elts_stages_like_add_elt_and_is_all_or_nothing(ara):
+    """ara_add_elts stages several ELTs with one check: the records, tables and uniforms are those
+    of one ara_add_elt per ELT (same handles, same year losses bit for bit, with and without
+    correlated SDs); a batch with a rejected ELT adds none and names it."""
+    w = synth.tiny(400)
+    y = w.yet
+    e0 = w.elts[0]
+    e1 = synth.make_elt(1_500, y.catalog_size, seed=21)
+    e2 = synth.split_sd(synth.make_elt(1_000, y.catalog_size, seed=22), seed=22)
+    t = w.terms
+    tup = lambda e: (e.event_ids, e.mean, e.sd, e.max_exposure)  # noqa: E731
+    for policy in (ara.TABLES_EAGER, ara.TABLES_ON_DEMAND):
+        with ara.Context(seed=42) as a, ara.Context(seed=42) as b:
+            a.set_option(ara.OPT_TABLES, policy)
+            b.set_option(ara.OPT_TABLES, policy)
+            ya = a.create_yet(y.offsets, y.event_ids, y.timestamps, y.catalog_size)
+            yb = b.create_yet(y.offsets, y.event_ids, y.timestamps, y.catalog_size)
+            ha = a.add_elts(ya, [tup(e0), tup(e1), tup(e2) + (e2.sd_corr,)])
+            hb = [b.add_elt(yb, *tup(e0)), b.add_elt(yb, *tup(e1)),
+                  b.add_elt(yb, *tup(e2), sd_corr=e2.sd_corr)]
+            assert ha == hb == [0, 1, 2]
+            la = a.add_layer(ha, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+            lb = b.add_layer(hb, t.occ_ret, t.occ_lim, t.agg_ret, t.agg_lim)
+            ga, gb = a.run(ya, la, 0, 400), b.run(yb, lb, 0, 400)
+            np.testing.assert_array_equal(ga, gb)
+            assert np.count_nonzero(ga) > 100
+            assert a.stats()["uncertified"] == b.stats()["uncertified"]
+            # a batch whose second ELT repeats an event id: rejected as a whole
+            bad = e1.event_ids.copy()
+            bad[7] = bad[3]
+            with pytest.raises(ara.AraError, match="ELT 1 rejected: duplicate event id"):
+                a.add_elts(ya, [tup(e0), (bad, e1.mean, e1.sd, e1.max_exposure), tup(e2)])
+            assert a.add_elt(ya, *tup(e0)) == 3  # nothing of the failed batch was added
