@@ -405,11 +405,15 @@ ara_status ara_add_elts(ara_ctx* ctx, int32_t yet, int32_t n_elts, const int64_t
   const bool defer = ctx->table_policy == ARA_TABLES_ON_DEMAND;
   auto sdc_of = [&](int32_t j) { return sd_corr ? sd_corr[j] : nullptr; };
   // staging scratch: each ELT's check flags and uncertified count, the duplicate marks, and the
-  // input copies of the largest ELT (reused ELT after ELT: the stream orders them); sized once,
-  // before any work is queued
+  // input copies of the largest batch of kMaxPrepJobs ELTs (reused batch after batch: the stream
+  // orders them); sized once, before any work is queued
   size_t temps = 0;
-  for (int32_t j = 0; j < n_elts; ++j)
-    temps = std::max(temps, scratch_bytes<double>(n[j]) * (sdc_of(j) ? 4 : 3));
+  for (int32_t b = 0; b < n_elts; b += kMaxPrepJobs) {
+    size_t t = 0;
+    for (int32_t j = b; j < std::min(n_elts, b + kMaxPrepJobs); ++j)
+      t += scratch_bytes<double>(n[j]) * (sdc_of(j) ? 4 : 3);
+    temps = std::max(temps, t);
+  }
   const size_t scratch = scratch_bytes<unsigned int>(n_elts) +
                          scratch_bytes<unsigned long long>(n_elts) +
                          scratch_bytes<unsigned int>(y.catalog) + temps;
@@ -443,35 +447,49 @@ ara_status ara_add_elts(ara_ctx* ctx, int32_t yet, int32_t n_elts, const int64_t
   err = cudaMemsetAsync(d_flags, 0, sizeof(unsigned int) * (size_t)n_elts, ctx->stream);
   if (err == cudaSuccess)
     err = cudaMemsetAsync(d_uncert, 0, sizeof(unsigned long long) * (size_t)n_elts, ctx->stream);
-  for (int32_t j = 0; j < n_elts && err == cudaSuccess; ++j) {
-    EltDev& e = es[(size_t)j];
-    const int64_t nj = e.n;
+  // the records of each batch of kMaxPrepJobs ELTs checked and converted in one launch
+  for (int32_t b = 0; b < n_elts && err == cudaSuccess; b += kMaxPrepJobs) {
+    PrepJobs jobs{};
+    jobs.n = std::min(kMaxPrepJobs, n_elts - b);
     ScratchCarver tc = sc;
-    double* d_mean = tc.take<double>(nj);
-    double* d_sd = tc.take<double>(nj);
-    double* d_mx = tc.take<double>(nj);
-    double* d_sdc = sdc_of(j) ? tc.take<double>(nj) : nullptr;
-    // inputs the device can read where they are (device memory, mapped page-locked host memory)
-    // are read in place by the staging kernel, which also writes the ids' device copy; the others
-    // are copied first.  (Reads over PCIe by the kernel do not queue behind other copies, such as
-    // the ids a host-resident YET copies ahead.)
-    const int32_t* r_ids = device_readable(event_ids[j]);
-    const double* r_mean = device_readable(mean[j]);
-    const double* r_sd = device_readable(sd[j]);
-    const double* r_sdc = sdc_of(j) ? device_readable(sdc_of(j)) : nullptr;
-    const double* r_mx = device_readable(max_exposure[j]);
-    if ((!r_ids && (err = copy_in(e.ids, event_ids[j], nj, ctx->stream)) != cudaSuccess) ||
-        (!r_mean && (err = copy_in(d_mean, mean[j], nj, ctx->stream)) != cudaSuccess) ||
-        (!r_sd && (err = copy_in(d_sd, sd[j], nj, ctx->stream)) != cudaSuccess) ||
-        (sdc_of(j) && !r_sdc && (err = copy_in(d_sdc, sdc_of(j), nj, ctx->stream)) != cudaSuccess) ||
-        (!r_mx && (err = copy_in(d_mx, max_exposure[j], nj, ctx->stream)) != cudaSuccess) ||
-        (err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog,
-                               ctx->stream)) != cudaSuccess)
-      break;
-    err = launch_prepare_elt(nj, r_ids ? r_ids : e.ids, r_ids ? e.ids : nullptr,
-                             r_mean ? r_mean : d_mean, r_sd ? r_sd : d_sd,
-                             sdc_of(j) ? (r_sdc ? r_sdc : d_sdc) : nullptr, r_mx ? r_mx : d_mx,
-                             y.catalog, e.recs, e.corr, d_dup, d_flags + j, ctx->stream);
+    for (int k = 0; k < jobs.n && err == cudaSuccess; ++k) {
+      const int32_t j = b + k;
+      EltDev& e = es[(size_t)j];
+      const int64_t nj = e.n;
+      double* d_mean = tc.take<double>(nj);
+      double* d_sd = tc.take<double>(nj);
+      double* d_mx = tc.take<double>(nj);
+      double* d_sdc = sdc_of(j) ? tc.take<double>(nj) : nullptr;
+      // inputs the device can read where they are (device memory, mapped page-locked host
+      // memory) are read in place by the staging kernel, which also writes the ids' device copy;
+      // the others are copied first.  (Reads over PCIe by the kernel do not queue behind other
+      // copies, such as the ids a host-resident YET copies ahead.)
+      const int32_t* r_ids = device_readable(event_ids[j]);
+      const double* r_mean = device_readable(mean[j]);
+      const double* r_sd = device_readable(sd[j]);
+      const double* r_sdc = sdc_of(j) ? device_readable(sdc_of(j)) : nullptr;
+      const double* r_mx = device_readable(max_exposure[j]);
+      if ((!r_ids && (err = copy_in(e.ids, event_ids[j], nj, ctx->stream)) != cudaSuccess) ||
+          (!r_mean && (err = copy_in(d_mean, mean[j], nj, ctx->stream)) != cudaSuccess) ||
+          (!r_sd && (err = copy_in(d_sd, sd[j], nj, ctx->stream)) != cudaSuccess) ||
+          (sdc_of(j) && !r_sdc &&
+           (err = copy_in(d_sdc, sdc_of(j), nj, ctx->stream)) != cudaSuccess) ||
+          (!r_mx && (err = copy_in(d_mx, max_exposure[j], nj, ctx->stream)) != cudaSuccess))
+        break;
+      jobs.ids[k] = r_ids ? r_ids : e.ids;
+      jobs.ids_out[k] = r_ids ? e.ids : nullptr;
+      jobs.mean[k] = r_mean ? r_mean : d_mean;
+      jobs.sd[k] = r_sd ? r_sd : d_sd;
+      jobs.sdc[k] = sdc_of(j) ? (r_sdc ? r_sdc : d_sdc) : nullptr;
+      jobs.mx[k] = r_mx ? r_mx : d_mx;
+      jobs.recs[k] = e.recs;
+      jobs.corr[k] = e.corr;
+      jobs.first[k + 1] = jobs.first[k] + nj;
+    }
+    if (err == cudaSuccess)
+      err = cudaMemsetAsync(d_dup, 0, sizeof(unsigned int) * (size_t)y.catalog, ctx->stream);
+    if (err == cudaSuccess)
+      err = launch_prepare_elts(jobs, y.catalog, d_dup, d_flags + b, ctx->stream);
   }
   // tables at staging (ARA_TABLES_EAGER): all the ELTs' in one launch (kMaxTableJobs a launch)
   for (int32_t b = 0; !defer && b < n_elts && err == cudaSuccess; b += kMaxTableJobs) {

@@ -173,13 +173,26 @@ cudaError_t launch_validate_yet_range(const int32_t* ids, const float* ts, int64
                                       const int64_t* offsets, int64_t t_begin, int64_t n,
                                       int32_t catalog, unsigned int* d_flags, cudaStream_t st,
                                       int32_t* ids_out = nullptr);
-// Checks and converts an ELT's records (ids, mean, sd, optional correlated sd, max exposure, all
-// device-readable) into recs / corr; ids_out (nullable) receives a copy of the ids.
-cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
-                               const double* mean, const double* sd, const double* sdc,
-                               const double* mx, int32_t catalog, BetaRec* recs,
-                               float* corr, unsigned int* d_dup, unsigned int* d_flags,
-                               cudaStream_t st);
+// Checks and converts the records of up to kMaxPrepJobs ELTs in one launch: job j's ids, mean,
+// sd, optional correlated sd (sdc[j] NULL: zero) and max exposure (all device-readable) into
+// recs[j] / corr[j] (corr[j] NULL: none); ids_out[j] (nullable) receives a copy of the ids.
+// first[j] records come before job j (first[n]: all).  d_dup[catalog] (zeroed by the caller)
+// marks events per job; d_flags[j] (zeroed) receives job j's rejection flags.
+constexpr int kMaxPrepJobs = 32;
+struct PrepJobs {
+  const int32_t* ids[kMaxPrepJobs];
+  int32_t* ids_out[kMaxPrepJobs];
+  const double* mean[kMaxPrepJobs];
+  const double* sd[kMaxPrepJobs];
+  const double* sdc[kMaxPrepJobs];
+  const double* mx[kMaxPrepJobs];
+  BetaRec* recs[kMaxPrepJobs];
+  float* corr[kMaxPrepJobs];
+  int64_t first[kMaxPrepJobs + 1];
+  int n;
+};
+cudaError_t launch_prepare_elts(const PrepJobs& jobs, int32_t catalog, unsigned int* d_dup,
+                               unsigned int* d_flags, cudaStream_t st);
 cudaError_t launch_layer_mask(const EltDev& e, int slot, int mask_words, uint32_t* d_mask,
                               cudaStream_t st);
 cudaError_t launch_layer_counts(const uint32_t* d_mask, int mask_words, int64_t catalog,

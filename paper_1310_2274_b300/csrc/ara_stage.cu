@@ -96,32 +96,28 @@ __global__ void check_offsets_fini(OffsetCheck* out) {
 
 // ---- ELT record preparation (FP64, once per record) --------------------------------------------
 
-// flags bit 3: id out of range; bit 4: mean <= 0 or an SD < 0 or non-finite; bit 5: max <= mean
-// with sd > 0; dup[e] counts records per event (a count above one is a duplicate, bit 6).
-// sdc (NULL: zero) is the correlated SD of paper §3.1: sigma = sd + sdc feeds the moments and
-// corr[r] receives the normalised correlated weight of §3.2, (sdc/sigma) / |(sd, sdc)/sigma|.
-__global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
-                                   int32_t* __restrict__ ids_out,
-                                   const double* __restrict__ mean, const double* __restrict__ sd,
-                                   const double* __restrict__ sdc, const double* __restrict__ mx,
-                                   int32_t catalog, BetaRec* __restrict__ recs,
-                                   float* __restrict__ corr,
-                                   unsigned int* dup, unsigned int* flags) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+// One record of an ELT (job j of a launch): flags bit 3: id out of range; bit 4: mean <= 0 or an
+// SD < 0 or non-finite; bit 5: max <= mean with sd > 0; bit 6: a duplicate event id (bit j of
+// dup[e] marks event e as met in job j).  sdc (NULL: zero) is the correlated SD of paper §3.1:
+// sigma = sd + sdc feeds the moments and corr[r] receives the normalised correlated weight of
+// §3.2, (sdc/sigma) / |(sd, sdc)/sigma|.
+__device__ __forceinline__ unsigned int prepare_record(const PrepJobs& J, int j, int64_t r,
+                                                       int32_t catalog, unsigned int* dup) {
   unsigned int f = 0;
-  const int32_t e = ids[r];
-  if (ids_out) ids_out[r] = e;
+  const int32_t e = J.ids[j][r];
+  if (J.ids_out[j]) J.ids_out[j][r] = e;
+  const unsigned int bit = 1u << j;
   if (e < 0 || e >= catalog) {
     f |= 8u;
-  } else if (atomicAdd(&dup[e], 1u) != 0u) {
+  } else if (atomicOr(&dup[e], bit) & bit) {
     f |= 64u;
   }
-  const double sd_i = sd[r], sd_c = sdc ? sdc[r] : 0.0;
-  const double mu = mean[r], sigma = sd_i + sd_c, m = mx[r];
-  if (corr) {  // paper §3.2 steps 3-4: weights sd_i/sigma, sd_c/sigma, normalised
+  const double* sdc = J.sdc[j];
+  const double sd_i = J.sd[j][r], sd_c = sdc ? sdc[r] : 0.0;
+  const double mu = J.mean[j][r], sigma = sd_i + sd_c, m = J.mx[j][r];
+  if (J.corr[j]) {  // paper §3.2 steps 3-4: weights sd_i/sigma, sd_c/sigma, normalised
     const double wi = sigma > 0.0 ? sd_i / sigma : 1.0, wc = sigma > 0.0 ? sd_c / sigma : 0.0;
-    corr[r] = (float)(wc / sqrt(wi * wi + wc * wc));
+    J.corr[j][r] = (float)(wc / sqrt(wi * wi + wc * wc));
   }
   if (!(sd_i >= 0.0) || !(sd_c >= 0.0)) f |= 16u;
   BetaRec rec;
@@ -146,8 +142,23 @@ __global__ void prepare_elt_kernel(int64_t n, const int32_t* __restrict__ ids,
       if (!(rec.a > 0.f) || !(rec.b > 0.f)) f |= 16u;  // alpha or beta outside binary32 range
     }
   }
-  recs[r] = rec;
-  if (f) atomicOr(flags, f);
+  J.recs[j][r] = rec;
+  return f;
+}
+
+// The records of up to kMaxPrepJobs ELTs in one launch (thread per record); flags[j] collects
+// job j's flags.
+__global__ void prepare_elts_kernel(const __grid_constant__ PrepJobs J, int32_t catalog,
+                                    unsigned int* dup, unsigned int* flags) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= J.first[J.n]) return;
+  int lo = 0, hi = J.n - 1;
+  while (lo < hi) {  // the job holding record g: the last whose first record is <= g
+    const int mid = (lo + hi + 1) >> 1;
+    if (J.first[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const unsigned int f = prepare_record(J, lo, g - J.first[lo], catalog, dup);
+  if (f) atomicOr(flags + lo, f);
 }
 
 // ---- layer lookup structure ----------------------------------------------------------------------
@@ -356,14 +367,11 @@ cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, OffsetChe
   return cudaGetLastError();
 }
 
-cudaError_t launch_prepare_elt(int64_t n, const int32_t* ids, int32_t* ids_out,
-                               const double* mean, const double* sd, const double* sdc,
-                               const double* mx, int32_t catalog, BetaRec* recs,
-                               float* corr, unsigned int* d_dup, unsigned int* d_flags,
-                               cudaStream_t st) {
+cudaError_t launch_prepare_elts(const PrepJobs& jobs, int32_t catalog, unsigned int* d_dup,
+                               unsigned int* d_flags, cudaStream_t st) {
+  const int64_t n = jobs.first[jobs.n];
   if (n == 0) return cudaSuccess;
-  prepare_elt_kernel<<<grid_for(n), kThreads, 0, st>>>(n, ids, ids_out, mean, sd, sdc, mx,
-                                                       catalog, recs, corr, d_dup, d_flags);
+  prepare_elts_kernel<<<grid_for(n), kThreads, 0, st>>>(jobs, catalog, d_dup, d_flags);
   count_launches(1);
   return cudaGetLastError();
 }
