@@ -36,6 +36,7 @@
 #endif
 
 #include <stdint.h>
+#include <string.h>
 
 #ifndef __CUDACC__
 #include <cmath>
@@ -99,6 +100,67 @@ ARA_HD float ara_pow2_scale_of(float s) {
   return r;
 }
 
+// Two binary32 values in one 64-bit register, (lo, hi): the recurrence advances its numerator
+// and denominator together by the paired FP32 instructions (fma.rn.f32x2, mul.rn.f32x2), each
+// element rounded as its scalar operation.
+struct F2 {
+  unsigned long long v;
+};
+ARA_HD F2 f2_make(float lo, float hi) {
+  F2 r;
+#ifdef __CUDA_ARCH__
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+#else
+  uint32_t a, b;
+  memcpy(&a, &lo, 4);
+  memcpy(&b, &hi, 4);
+  r.v = ((unsigned long long)b << 32) | a;
+#endif
+  return r;
+}
+ARA_HD float f2_lo(F2 p) {
+#ifdef __CUDA_ARCH__
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p.v));
+  return lo;
+#else
+  const uint32_t a = (uint32_t)p.v;
+  float f;
+  memcpy(&f, &a, 4);
+  return f;
+#endif
+}
+ARA_HD float f2_hi(F2 p) {
+#ifdef __CUDA_ARCH__
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p.v));
+  return hi;
+#else
+  const uint32_t b = (uint32_t)(p.v >> 32);
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+ARA_HD F2 f2_fma(F2 a, F2 b, F2 c) {
+#ifdef __CUDA_ARCH__
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+#else
+  return f2_make(fmaf(f2_lo(a), f2_lo(b), f2_lo(c)), fmaf(f2_hi(a), f2_hi(b), f2_hi(c)));
+#endif
+}
+ARA_HD F2 f2_mul(F2 a, F2 b) {
+#ifdef __CUDA_ARCH__
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+#else
+  return f2_make(f2_lo(a) * f2_lo(b), f2_hi(a) * f2_hi(b));
+#endif
+}
+
 // K(a,b,x) = 1/(1 + d1/(1 + d2/(...))) of DLMF 8.17.22 by the Wallis recurrence on the
 // division-free equivalent fraction T = 1 + alpha_1/(beta_1 + alpha_2/(beta_2 + ...)), K = 1/T.
 // Converges quickly for x < (a+1)/(a+b+2).  The fraction is summed in blocks of four terms: after
@@ -108,7 +170,8 @@ ARA_HD float ara_pow2_scale_of(float s) {
 // block and take up another's when it is done (the batched inversion of the kernels).
 struct CfState {
   float a, b, x, apb;
-  float Am2, Am1, Bm2, Bm1;  // T_n = A_n / B_n; A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1
+  F2 P1, P2;                 // (A_{n-1}, B_{n-1}), (A_{n-2}, B_{n-2}); T_n = A_n / B_n;
+                             // A_{-1} = 1, A_0 = 1; B_{-1} = 0, B_0 = 1
   float pA, pB;              // the estimate last tested, as the pair (A, B)
   float m;                   // the next pair holds terms 2m+1 and 2m+2 (an exact small integer)
   int n;                     // index of the next (odd) term, 2m+1
@@ -116,7 +179,8 @@ struct CfState {
 
 ARA_HD void ara_cf_init(CfState& c, float a, float b, float x) {
   c.a = a; c.b = b; c.x = x; c.apb = a + b;
-  c.Am2 = 1.0f; c.Am1 = 1.0f; c.Bm2 = 0.0f; c.Bm1 = 1.0f;
+  c.P2 = f2_make(1.0f, 0.0f);
+  c.P1 = f2_make(1.0f, 1.0f);
   c.pA = 1.0f; c.pB = 1.0f;
   c.m = 0.0f;
   c.n = 1;
@@ -128,19 +192,21 @@ ARA_HD void ara_cf_pair(CfState& c) {
   const float m = c.m;
   const float al_odd = (m == 0.0f) ? -c.apb * c.x : -(c.a + m) * (c.apb + m) * c.x;
   const float be_odd = c.a + fmaf(2.0f, m, 1.0f);  // a + (2m+1), the integer exact
-  float A = be_odd * c.Am1 + al_odd * c.Am2;
-  float B = be_odd * c.Bm1 + al_odd * c.Bm2;
-  c.Am2 = c.Am1; c.Bm2 = c.Bm1; c.Am1 = A; c.Bm1 = B;
+  F2 N = f2_fma(f2_make(be_odd, be_odd), c.P1, f2_mul(f2_make(al_odd, al_odd), c.P2));
+  c.P2 = c.P1;
+  c.P1 = N;
   // even step 2(m+1): alpha = (m+1)(b-m-1) x
   const float m2 = m + 1.0f;
   const float al_even = m2 * (c.b - m2) * c.x;
   const float be_even = c.a + 2.0f * m2;
-  A = be_even * c.Am1 + al_even * c.Am2;
-  B = be_even * c.Bm1 + al_even * c.Bm2;
-  c.Am2 = c.Am1; c.Bm2 = c.Bm1; c.Am1 = A; c.Bm1 = B;
+  N = f2_fma(f2_make(be_even, be_even), c.P1, f2_mul(f2_make(al_even, al_even), c.P2));
+  c.P2 = c.P1;
+  c.P1 = N;
   // exact power-of-two rescale keeps the recurrence inside binary32 range
-  const float sc = ara_pow2_scale_of(c.Am1);
-  c.Am1 *= sc; c.Am2 *= sc; c.Bm1 *= sc; c.Bm2 *= sc;
+  const float sc = ara_pow2_scale_of(f2_lo(c.P1));
+  const F2 s2 = f2_make(sc, sc);
+  c.P1 = f2_mul(c.P1, s2);
+  c.P2 = f2_mul(c.P2, s2);
   c.m = m2;
 }
 
@@ -150,14 +216,15 @@ ARA_HD bool ara_cf_block(CfState& c, float tol) {
   ara_cf_pair(c);
   ara_cf_pair(c);
   c.n += 4;
-  const float cur = c.Bm1 * c.pA;
-  if (fabsf(fmaf(-c.pB, c.Am1, cur)) <= tol * fabsf(cur)) return true;
-  c.pA = c.Am1;
-  c.pB = c.Bm1;
+  const float A = f2_lo(c.P1), B = f2_hi(c.P1);
+  const float cur = B * c.pA;
+  if (fabsf(fmaf(-c.pB, A, cur)) <= tol * fabsf(cur)) return true;
+  c.pA = A;
+  c.pB = B;
   return c.n > kCfMaxTerms;
 }
 
-ARA_HD float ara_cf_value(const CfState& c) { return c.Bm1 / c.Am1; }
+ARA_HD float ara_cf_value(const CfState& c) { return f2_hi(c.P1) / f2_lo(c.P1); }
 
 // The whole fraction for one lane; *terms is increased by the number of terms summed.
 ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e-7f) {
