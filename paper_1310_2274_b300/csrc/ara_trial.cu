@@ -41,8 +41,13 @@ namespace {
 // whose blocks first load the network's weights into shared memory.
 template <int INV>
 constexpr int kWPB = INV == 2 ? 4 : 2;
-constexpr int kV = 4;             // occurrences per lane per chunk
-constexpr int kChunk = 32 * kV;   // occurrences per chunk
+// Occurrences per lane per chunk: 8 (the 8 index lookups a lane issues together hide each
+// other's latency); 4 where the surrogate's network and segments already fill a block's shared
+// memory.
+template <int INV>
+constexpr int kVOf = INV == 2 ? 4 : 8;
+template <int INV>
+constexpr int kChunkOf = 32 * kVOf<INV>;  // occurrences per chunk
 
 // One 16-row tile of the network (tile mt of the warp's 32 rows: lane 16 mt + r holds row r's
 // inputs); returns row g's output in *y0 and row g + 8's in *y8.  Out of line, so that the two
@@ -219,10 +224,11 @@ __device__ __forceinline__ void occurrence_outputs(const TrialParams& P, int64_t
 template <int MW, class Acc, bool TRACE, int INV, bool CORR>
 __device__ __forceinline__ void process_trial(const TrialParams& P, int64_t w, int lane, int wib,
                                               int32_t* excl, uint32_t* sbase,
-                                              uint32_t (*s_maskw)[kChunk], float* lsum,
+                                              uint32_t (*s_maskw)[kChunkOf<INV>], float* lsum,
                                               const MlpSmem* s_mlp, SurrWarpSmem* s_surr,
                                               float* s_tx, float* s_tu) {
   constexpr bool TABLE = INV == 0;
+  constexpr int kV = kVOf<INV>, kChunk = kChunkOf<INV>;
   constexpr bool SURR = INV == 2;
   const int64_t trial = P.t0 + w;
   if (P.abort_flag != nullptr && *reinterpret_cast<const volatile unsigned int*>(P.abort_flag))
@@ -485,10 +491,10 @@ template <int MW, class Acc, bool TRACE, int INV, bool CORR>
 __global__ void __launch_bounds__(kWPB<INV> * 32, kBlocksPerSM<INV>)
     trial_kernel(const __grid_constant__ TrialParams P) {
   constexpr int W = kWPB<INV>;
-  __shared__ int32_t s_excl[W][kChunk];
-  __shared__ uint32_t s_base[W][kChunk];
-  __shared__ uint32_t s_mask[W][MW][kChunk];
-  __shared__ float s_lsum[W][kChunk];
+  __shared__ int32_t s_excl[W][kChunkOf<INV>];
+  __shared__ uint32_t s_base[W][kChunkOf<INV>];
+  __shared__ uint32_t s_mask[W][MW][kChunkOf<INV>];
+  __shared__ float s_lsum[W][kChunkOf<INV>];
   __shared__ __align__(16) MlpSmem s_mlp[1];
   SURR_SMEM(W, INV, TRACE);
   if constexpr (INV == 2) {  // network weights, once per block, before any warp may leave
@@ -514,10 +520,10 @@ __global__ void __launch_bounds__(kWPB<INV> * 32, kBlocksPerSM<INV>)
     batch_kernel(const TrialParams* __restrict__ items, const int64_t* __restrict__ warp_begin,
                  int n_items, int64_t total_warps) {
   constexpr int W = kWPB<INV>;
-  __shared__ int32_t s_excl[W][kChunk];
-  __shared__ uint32_t s_base[W][kChunk];
-  __shared__ uint32_t s_mask[W][MW][kChunk];
-  __shared__ float s_lsum[W][kChunk];
+  __shared__ int32_t s_excl[W][kChunkOf<INV>];
+  __shared__ uint32_t s_base[W][kChunkOf<INV>];
+  __shared__ uint32_t s_mask[W][MW][kChunkOf<INV>];
+  __shared__ float s_lsum[W][kChunkOf<INV>];
   __shared__ __align__(16) MlpSmem s_mlp[1];
   SURR_SMEM(W, INV, false);
   if constexpr (INV == 2) {
