@@ -165,8 +165,11 @@ ARA_HD F2 f2_mul(F2 a, F2 b) {
 // division-free equivalent fraction T = 1 + alpha_1/(beta_1 + alpha_2/(beta_2 + ...)), K = 1/T.
 // Converges quickly for x < (a+1)/(a+b+2).  The fraction is summed in blocks of four terms: after
 // each block two estimates four terms apart are compared, B/A against pB/pA cross-multiplied,
-// |B pA - pB A| <= tol |B pA| (A and pA are rescaled into [1, 2)), so the one division is the
-// final K.  CfState holds the recurrence between blocks, so a lane can sum one fraction block by
+// |B pA - pB A| <= max(tol |B pA|, tol_g |A pA|) (A and pA are rescaled into [1, 2)), so the one
+// division is the final K.  The first bound is a relative error tol in K; the second, with
+// tol_g = tol a / y, is a relative error in K of tol a / (y K) = tol G', where G' = dlnI/dlnx is
+// the inverse beta's sensitivity (below): either stops the fraction once its error moves the
+// root's ln x by at most tol.  CfState holds the recurrence between blocks, so a lane can sum one fraction block by
 // block and take up another's when it is done (the batched inversion of the kernels).
 struct CfState {
   float a, b, x, apb;
@@ -212,13 +215,13 @@ ARA_HD void ara_cf_pair(CfState& c) {
 
 // Four more terms and the convergence test: true once the fraction has converged or reached
 // kCfMaxTerms terms; c.n - 1 is then the number of terms summed.
-ARA_HD bool ara_cf_block(CfState& c, float tol) {
+ARA_HD bool ara_cf_block(CfState& c, float tol, float tol_g = 0.0f) {
   ara_cf_pair(c);
   ara_cf_pair(c);
   c.n += 4;
   const float A = f2_lo(c.P1), B = f2_hi(c.P1);
   const float cur = B * c.pA;
-  if (fabsf(fmaf(-c.pB, A, cur)) <= tol * fabsf(cur)) return true;
+  if (fabsf(fmaf(-c.pB, A, cur)) <= fmaxf(tol * fabsf(cur), tol_g * fabsf(A * c.pA))) return true;
   c.pA = A;
   c.pB = B;
   return c.n > kCfMaxTerms;
@@ -227,10 +230,11 @@ ARA_HD bool ara_cf_block(CfState& c, float tol) {
 ARA_HD float ara_cf_value(const CfState& c) { return f2_hi(c.P1) / f2_lo(c.P1); }
 
 // The whole fraction for one lane; *terms is increased by the number of terms summed.
-ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e-7f) {
+ARA_HD float ara_beta_cf(float a, float b, float x, int* terms, float tol = 1.2e-7f,
+                         float tol_g = 0.0f) {
   CfState c;
   ara_cf_init(c, a, b, x);
-  while (!ara_cf_block(c, tol)) {
+  while (!ara_cf_block(c, tol, tol_g)) {
   }
   if (terms) *terms += c.n - 1;
   return ara_cf_value(c);
@@ -423,7 +427,10 @@ ARA_HD void ara_halley_result(const HalleyState& h, int iters, bool done, IbetaR
 // Iterations it0, it0 + 1, ... of an inversion set up by ara_halley_setup, to the end; r.cf_terms
 // is increased by the terms summed.  From the analytic start (~1e-2 from the root) the first
 // iteration's continued fraction is summed only to 1e-4 and cannot end the loop; later
-// iterations (and every one from a start table's estimate) are summed to binary32 accuracy.
+// iterations (and every one from a start table's estimate) are summed to binary32 accuracy: a
+// relative error of 1.2e-7 in K, or one that moves ln x by at most 1.2e-7 where I_x is steeper
+// than x (G' = a / (y K) > 1 below the threshold: a > 1, most of the ELT value law); above the
+// threshold G' involves the complement and the plain relative bound is kept.
 // ONE_CF: evaluate the continued fraction in one loop whichever side of the threshold x lies on
 // (lanes of a warp on different sides share it; 16% faster where most hits invert this way), or
 // in a loop per side (fewer registers, for the out-of-line fallback of the table paths).  Both
@@ -436,11 +443,12 @@ ARA_HD void ara_halley_iterate(HalleyState& h, int it0, IbetaResult& r) {
   for (; it < kIbetaMaxIter; ++it) {
     const HalleyPre q = ara_halley_pre(h);
     const float tol = it == 0 ? cf_first : 1.2e-7f;
+    const float tol_g = q.lower ? tol * ara_fdiv(h.a, q.y) : 0.0f;
     float K;
     if constexpr (ONE_CF)
-      K = ara_beta_cf(q.ca, q.cb, q.cx, &r.cf_terms, tol);
+      K = ara_beta_cf(q.ca, q.cb, q.cx, &r.cf_terms, tol, tol_g);
     else
-      K = q.lower ? ara_beta_cf(h.a, h.b, h.x, &r.cf_terms, tol)
+      K = q.lower ? ara_beta_cf(h.a, h.b, h.x, &r.cf_terms, tol, tol_g)
                   : ara_beta_cf(h.b, h.a, q.y, &r.cf_terms, tol);
     if (ara_halley_post(h, q, K, it)) {
       done = true;
