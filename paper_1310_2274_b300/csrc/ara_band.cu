@@ -99,9 +99,9 @@ struct BandWarpSmem {
   int32_t excl[kCh];          // hits before each position (chunk order)
   uint32_t base[kCh];         // record base of each position's event
   uint32_t mask[2][kCh];
-  float lsum[kCh];            // the event's summed loss
+  alignas(16) float lsum[kCh];  // the event's summed loss
   uint32_t k[kCh];            // occurrence position in its trial
-  uint8_t t[kCh];             // warp-local trial of each position
+  alignas(4) uint8_t t[kCh];  // warp-local trial of each position
   uint8_t hitev[kHitCap];     // position of each of the chunk's hits (when they fit)
   uint32_t off[kT + 1];       // segment starts of the warp's trials in this band
   unsigned long long ys[kT];  // year-sum units gathered by the warp
@@ -296,7 +296,12 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
     n_hit += (lane == 0) ? (unsigned)run : 0u;
 
     // ---- occurrence terms; exact year-sum units gathered per trial ----------------------------
-    // lane l takes the chunk's positions 4l .. 4l+3, which mostly belong to one trial
+    // lane l takes the chunk's positions 4l .. 4l+3, which mostly belong to one trial; their
+    // event losses and trials come in one 16-byte and one 4-byte shared load
+    static_assert(kV == 4, "a lane's positions are one float4 of lsum and one word of t");
+    const float4 l4 = *reinterpret_cast<const float4*>(&sm.lsum[kV * lane]);
+    const uint32_t t4 = *reinterpret_cast<const uint32_t*>(&sm.t[kV * lane]);
+    const float lv[kV] = {l4.x, l4.y, l4.z, l4.w};
     unsigned long long acc = 0;
     float om = 0.f;
     int tc = -1;
@@ -304,8 +309,8 @@ __device__ __forceinline__ void band_warp(const TrialParams& P, int band, int64_
     for (int j = 0; j < kV; ++j) {
       const int p = kV * lane + j;
       if (c + (uint32_t)p < end) {
-        const int t = sm.t[p];
-        const float o = fminf(fmaxf(sm.lsum[p] - P.occ_ret, 0.f), P.occ_lim);
+        const int t = (int)((t4 >> (8 * j)) & 0xFFu);
+        const float o = fminf(fmaxf(lv[j] - P.occ_ret, 0.f), P.occ_lim);
         if (t != tc) {
           if (tc >= 0) {
             atomicAdd(&sm.ys[tc], acc);

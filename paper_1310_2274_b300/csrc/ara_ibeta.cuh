@@ -120,9 +120,7 @@ ARA_HD F2 f2_make(float lo, float hi) {
 }
 ARA_HD float f2_lo(F2 p) {
 #ifdef __CUDA_ARCH__
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p.v));
-  return lo;
+  return __uint_as_float((uint32_t)p.v);
 #else
   const uint32_t a = (uint32_t)p.v;
   float f;
@@ -132,9 +130,7 @@ ARA_HD float f2_lo(F2 p) {
 }
 ARA_HD float f2_hi(F2 p) {
 #ifdef __CUDA_ARCH__
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p.v));
-  return hi;
+  return __uint_as_float((uint32_t)(p.v >> 32));
 #else
   const uint32_t b = (uint32_t)(p.v >> 32);
   float f;
@@ -166,10 +162,9 @@ ARA_HD F2 f2_mul(F2 a, F2 b) {
 // Converges quickly for x < (a+1)/(a+b+2).  The fraction is summed in blocks of four terms: after
 // each block two estimates four terms apart are compared, B/A against pB/pA cross-multiplied,
 // |B pA - pB A| <= max(tol |B pA|, tol_g |A pA|) (A and pA are rescaled into [1, 2)), so the one
-// division is the final K.  The first bound is a relative error tol in K; the second, with
-// tol_g = tol a / y, is a relative error in K of tol a / (y K) = tol G', where G' = dlnI/dlnx is
-// the inverse beta's sensitivity (below): either stops the fraction once its error moves the
-// root's ln x by at most tol.  CfState holds the recurrence between blocks, so a lane can sum one fraction block by
+// division is the final K.  The first bound is a relative error tol in K; the second is a
+// relative error tol_g / K in K, which the inversion below sets so that the fraction stops once
+// its error moves the root's ln x by at most tol.  CfState holds the recurrence between blocks, so a lane can sum one fraction block by
 // block and take up another's when it is done (the batched inversion of the kernels).
 struct CfState {
   float a, b, x, apb;
@@ -271,6 +266,15 @@ struct HalleyState {
   bool flip, good;                               // tail swapped; start from a table's estimate
 };
 
+// The fast division (about 2 ulp), for quotients that only steer the iteration.
+ARA_HD float ara_fdiv(float n, float d) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(n, d);
+#else
+  return n / d;
+#endif
+}
+
 // Start of the inversion.  Returns false when it is already done (r holds the result): the
 // start lies below e^-69, where the loss max_l x is far under every term of a year loss.
 // The fields of the state that depend on the record and u alone; returns p (u or 1 - u).
@@ -285,7 +289,7 @@ ARA_HD float ara_halley_fields(const BetaRec& rec, float u, HalleyState& h) {
   h.s = h.a + h.b;
   h.lna = h.lnx0 + rec.lns;
   h.lnp = logf(p);
-  h.thr = (h.a + 1.0f) / (h.s + 2.0f);
+  h.thr = ara_fdiv(h.a + 1.0f, h.s + 2.0f);  // chooses the fraction's side; either side is exact
   return p;
 }
 
@@ -370,14 +374,6 @@ ARA_HD HalleyPre ara_halley_pre(const HalleyState& h) {
 // iteration `it` (0-based) ends the inversion.
 // The residual G is the function value and keeps IEEE arithmetic; G' and Halley's correction
 // only shape the step toward the root, so their quotients take the fast division (ara_fdiv).
-ARA_HD float ara_fdiv(float n, float d) {
-#ifdef __CUDA_ARCH__
-  return __fdividef(n, d);
-#else
-  return n / d;
-#endif
-}
-
 ARA_HD bool ara_halley_post(HalleyState& h, const HalleyPre& q, float K, int it) {
   const float a = h.a, b = h.b, x = h.x, y = q.y;
   float G, dG;
@@ -428,9 +424,11 @@ ARA_HD void ara_halley_result(const HalleyState& h, int iters, bool done, IbetaR
 // is increased by the terms summed.  From the analytic start (~1e-2 from the root) the first
 // iteration's continued fraction is summed only to 1e-4 and cannot end the loop; later
 // iterations (and every one from a start table's estimate) are summed to binary32 accuracy: a
-// relative error of 1.2e-7 in K, or one that moves ln x by at most 1.2e-7 where I_x is steeper
-// than x (G' = a / (y K) > 1 below the threshold: a > 1, most of the ELT value law); above the
-// threshold G' involves the complement and the plain relative bound is kept.
+// relative error of 1.2e-7 in K, or one that moves ln x by at most 1.2e-7, whichever is looser.
+// A relative error e in the fraction K(c, d, z) moves t = ln x by e y K / c on either side of the
+// threshold (c = a below it, where G = E + ln K - ln a - ln p and G' = a / (y K); c = b above it,
+// where G = ln(1 - J) - ln p with J = P K / b and G' = P / (y (1 - J))), so the second bound is
+// tol_g = tol c / y, capped at 1e-4 so that the first-order step stays valid.
 // ONE_CF: evaluate the continued fraction in one loop whichever side of the threshold x lies on
 // (lanes of a warp on different sides share it; 16% faster where most hits invert this way), or
 // in a loop per side (fewer registers, for the out-of-line fallback of the table paths).  Both
@@ -443,13 +441,13 @@ ARA_HD void ara_halley_iterate(HalleyState& h, int it0, IbetaResult& r) {
   for (; it < kIbetaMaxIter; ++it) {
     const HalleyPre q = ara_halley_pre(h);
     const float tol = it == 0 ? cf_first : 1.2e-7f;
-    const float tol_g = q.lower ? tol * ara_fdiv(h.a, q.y) : 0.0f;
+    const float tol_g = fminf(tol * ara_fdiv(q.ca, q.y), 1e-4f);
     float K;
     if constexpr (ONE_CF)
       K = ara_beta_cf(q.ca, q.cb, q.cx, &r.cf_terms, tol, tol_g);
     else
       K = q.lower ? ara_beta_cf(h.a, h.b, h.x, &r.cf_terms, tol, tol_g)
-                  : ara_beta_cf(h.b, h.a, q.y, &r.cf_terms, tol);
+                  : ara_beta_cf(h.b, h.a, q.y, &r.cf_terms, tol, tol_g);
     if (ara_halley_post(h, q, K, it)) {
       done = true;
       ++it;
@@ -532,7 +530,10 @@ ARA_HD int ara_start_piece(float u, float* tau) {
   const bool lower = u < 0.5f;
   const float q = lower ? u : 1.0f - u;
 #ifdef __CUDA_ARCH__
-  const float t = sqrtf(-1.38629436f * __log2f(q));
+  // the hardware base-2 logarithm and square root (q >= 2^-24 is normal): ample for a start
+  float lg, t;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(q));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(-1.38629436f * lg));
 #else
   const float t = sqrtf(-2.0f * logf(q));
 #endif
