@@ -756,6 +756,12 @@ def run_ours(a):
     return 0
 
 
+# accepted error of the surrogate (relative to a record's mean loss), and the other values the
+# tiny workload is run at
+SURROGATE_EPS = 5e-4
+EPS_SWEEP = (2.5e-4, 1e-3, 2e-3)
+
+
 def surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, newton_ms):
     """Trains the surrogate on 5e7 exact tuples (the GPU's own kernels), then runs the
     paper-scale layer with it (network inside its certified cells, Newton-Halley elsewhere)
@@ -767,7 +773,7 @@ def surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, newton_ms):
 
     t = time.perf_counter()
     rep = ctx.train_surrogate(n_samples=50_000_000, steps=30_000, batch=8192, lr=3e-3,
-                              lr_final=3e-5, eps=5e-4, cert_samples=16, seed=3)
+                              lr_final=3e-5, eps=SURROGATE_EPS, cert_samples=16, seed=3)
     train_s = time.perf_counter() - t
     run = lambda: ctx.run(yet, layer, 0, a.trials, out=ylt, stream=stream)  # noqa: E731
     ctx.set_option(ara.OPT_SURROGATE, 1)
@@ -779,10 +785,20 @@ def surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, newton_ms):
         s1 = ctx.stats()
         y_s = ylt.cpu().numpy().copy()
         sp, st = ctx.risk_measures(ylt, list(synth.RPS_PAPER))
-        # the tiny workload (one ELT of 2,000 records), surrogate and plain, against the oracle
+        # the tiny workload (one ELT of 2,000 records), surrogate and plain, against the oracle;
+        # the surrogate also at other accepted errors eps (the cell table is kept)
         w = synth.tiny()
         ty, te, tl = ctx.stage_workload(w)
         g_s = ctx.run(ty, tl, 0, w.yet.n_trials)
+        sweep = {}
+        for eps in EPS_SWEEP:
+            ctx.set_surrogate_eps(eps)
+            e0 = ctx.stats()
+            g_e = ctx.run(ty, tl, 0, w.yet.n_trials)
+            e1 = ctx.stats()
+            sweep[eps] = (g_e, e1["surrogate_evals"] - e0["surrogate_evals"],
+                          e1["inversions"] - e0["inversions"])
+        ctx.set_surrogate_eps(SURROGATE_EPS)
         ctx.set_option(ara.OPT_SURROGATE, 0)
         ctx.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
         g_n = ctx.run(ty, tl, 0, w.yet.n_trials)
@@ -791,13 +807,18 @@ def surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, newton_ms):
         ctx.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
     o, _ = oracle.run(w.yet, w.elts, w.terms, 42, elt_handles=te)
     op, ot = oracle.risk(o, w.rps)
-    tiny = {}
-    for name, g in (("surrogate", g_s), ("newton", g_n)):
+
+    def errors(g):
         gp, gt = ctx.risk_measures(g, w.rps)
         scale = np.maximum(np.maximum(np.abs(o), w.terms.agg_ret), 1.0)
-        tiny[name] = {"ylt_max_err": float(np.max(np.abs(g - o) / scale)),
-                      "pml_rel_err": [abs(float(x) / float(y) - 1.0) for x, y in zip(gp, op)],
-                      "tvar_rel_err": [abs(float(x) / float(y) - 1.0) for x, y in zip(gt, ot)]}
+        return {"ylt_max_err": float(np.max(np.abs(g - o) / scale)),
+                "pml_rel_err": [abs(float(x) / float(y) - 1.0) for x, y in zip(gp, op)],
+                "tvar_rel_err": [abs(float(x) / float(y) - 1.0) for x, y in zip(gt, ot)]}
+
+    tiny = {name: errors(g) for name, g in (("surrogate", g_s), ("newton", g_n))}
+    tiny["surrogate_eps_sweep"] = [
+        dict(eps=eps, fallback_rate=fb / max(1, net + fb), **errors(g))
+        for eps, (g, net, fb) in sweep.items()]
     ctx.free_layer(tl)
     for e in te:
         ctx.free_elt(e)
@@ -807,7 +828,10 @@ def surrogate_leg(a, ara, ctx, yet, layer, ylt, stream, dev, newton_ms):
     return {"kernel_ms": ms, "newton_ms": newton_ms, "speedup_vs_newton": newton_ms / ms,
             "network_evals": net, "fallback_rate": fb / max(1, net + fb),
             "cells_accepted": rep["cells_accepted"], "train_s": train_s,
-            "train": {"tuples": 50_000_000, "steps": 30_000, "batch": 8192, "eps": 5e-4,
+            "eps": SURROGATE_EPS,
+            "eps_meaning": "a hit is served where its cell's certified error in x is <= eps x "
+                           "mu_beta: each served loss within eps of the record's mean loss",
+            "train": {"tuples": 50_000_000, "steps": 30_000, "batch": 8192, "eps": SURROGATE_EPS,
                       "gen_ms": rep["gen_ms"], "train_ms": rep["train_ms"],
                       "cert_ms": rep["cert_ms"], "bad_targets": rep["bad_targets"]},
             "tiny_vs_oracle": tiny, "_ylt": (y_s, sp, st)}

@@ -315,22 +315,26 @@ ARA_API ara_status ara_risk_measures_n(ara_ctx* ctx, const double* values, int64
  * tuples generated by the exact inversion (polished in binary64); then certified: on a 32 x 32 x 64
  * grid of cells over the normalised inputs, each cell's largest |x_net - x| over its corners and
  * cert_samples - 8 further points is recorded.  With ARA_OPT_SURROGATE = 1, ara_run uses the
- * network for a hit only inside the box and where its cell's recorded error is <= eps; every other
- * hit falls back to the exact Newton inversion. */
+ * network for a hit only inside the box and where its cell's recorded error is <= eps * mu_beta,
+ * mu_beta = alpha / (alpha + beta) being the record's mean loss over its maximum exposure: a served
+ * loss is then within eps times the record's mean loss, and a year's sum of served losses within
+ * eps of its expected value.  Every other hit falls back to the exact Newton inversion. */
 typedef struct {
   int64_t n_samples;    /* training tuples generated (e.g. 50,000,000)                       */
   int64_t steps;        /* Adam steps                                                          */
   int32_t batch;        /* rows per step, a multiple of 128                                    */
   int32_t cert_samples; /* points per certification cell (>= 8)                                */
   float lr, lr_final;   /* cosine schedule from lr to lr_final                                 */
-  float eps;            /* accepted absolute error in x per cell                               */
+  float eps;            /* accepted error: a cell serves a record when its error in x is     */
+                        /* <= eps * mu_beta (eps relative to the record's mean loss)         */
   float reserved;
   uint64_t seed;        /* stream of the training tuples and of the initial weights            */
 } ara_surrogate_config;
 typedef struct {
   double loss_first, loss_last;   /* mean loss of the first and last 1% of steps                */
   double gen_ms, train_ms, cert_ms;
-  double cells_accepted;          /* fraction of certification cells with error <= eps          */
+  double cells_accepted;          /* fraction of certification cells with error <= eps, i.e.    */
+                                  /* usable by records of mu_beta = 1 (fewer serve a smaller one) */
   double err_median, err_p99;     /* over cells: recorded |x_net - x|                            */
   int64_t bad_targets;            /* training tuples and certification points whose exact        */
                                   /* inversion reported non-convergence (such a point rejects     */
@@ -342,7 +346,8 @@ ARA_API ara_status ara_train_surrogate(ara_ctx* ctx, const ara_surrogate_config*
  * most cap bytes (*bytes receives the size needed); load replaces the context's surrogate. */
 ARA_API ara_status ara_save_surrogate(ara_ctx* ctx, void* blob, size_t cap, size_t* bytes);
 ARA_API ara_status ara_load_surrogate(ara_ctx* ctx, const void* blob, size_t bytes);
-/* Sets the accepted error eps of the loaded surrogate (the cell table is kept). */
+/* Sets the accepted error eps (relative to a record's mean loss, as above) of the loaded surrogate
+ * (the cell table is kept). */
 ARA_API ara_status ara_set_surrogate_eps(ara_ctx* ctx, float eps);
 /* Network evaluation and gradient with caller parameters (host FP32 vector of 8,641 in the order
  * W1[64,3], b1, W2[64,64], b2, W3[64,64], b3, W4[64], b4; NULL = the context's trained network):

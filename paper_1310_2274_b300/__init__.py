@@ -460,8 +460,8 @@ class Context:
         return {k: v[:m] for k, v in bufs.items()}, ylt
 
     # -- learned surrogate ---------------------------------------------------------------------
-    def train_surrogate(self, n_samples=50_000_000, steps=20_000, batch=8192, lr=3e-3,
-                        lr_final=3e-5, eps=2e-3, cert_samples=24, seed=3) -> dict:
+    def train_surrogate(self, n_samples=50_000_000, steps=30_000, batch=8192, lr=3e-3,
+                        lr_final=3e-5, eps=5e-4, cert_samples=16, seed=3) -> dict:
         cfg = SurrogateConfig(int(n_samples), int(steps), int(batch), int(cert_samples),
                               float(lr), float(lr_final), float(eps), 0.0, int(seed))
         rep = SurrogateReport()

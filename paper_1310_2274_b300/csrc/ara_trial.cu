@@ -132,7 +132,10 @@ __device__ __forceinline__ void surrogate_segment(const TrialParams& P, const Ml
       float l = mx, x = __int_as_float(0x7FC00000);
       if (!sd0) {
         // the network serves the hit if (alpha, beta) lies in its box and the certified error
-        // of the hit's cell is within eps
+        // in x of the hit's cell is within eps * mu_beta (mu_beta = alpha / (alpha + beta), the
+        // record's mean over its maximum exposure): the served loss mx * x is then within eps
+        // times the record's mean loss, so a year's sum of served losses is within eps of its
+        // expectation whatever the hits' x
         if (rec.a >= kBoxLo && rec.a <= kBoxHi && rec.b >= kBoxLo && rec.b <= kBoxHi) {
           z0 = (logf(rec.a) - kLnCenter) / kLnHalf;
           z1 = (logf(rec.b) - kLnCenter) / kLnHalf;
@@ -140,7 +143,8 @@ __device__ __forceinline__ void surrogate_segment(const TrialParams& P, const Ml
           const int i0 = min(max((int)((z0 + 1.0f) * (0.5f * kCert0)), 0), kCert0 - 1);
           const int i1 = min(max((int)((z1 + 1.0f) * (0.5f * kCert1)), 0), kCert1 - 1);
           const int i2 = min(max((int)((z2 + 1.0f) * (0.5f * kCert2)), 0), kCert2 - 1);
-          listed = __ldg(P.mlp_bound + ((i0 * kCert1) + i1) * kCert2 + i2) <= P.mlp_eps;
+          const float mu = rec.a / (rec.a + rec.b);
+          listed = __ldg(P.mlp_bound + ((i0 * kCert1) + i1) * kCert2 + i2) <= P.mlp_eps * mu;
         }
         if (!listed) {
           const IbetaResult ib = surrogate_fallback(

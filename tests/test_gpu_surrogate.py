@@ -132,6 +132,47 @@ def test_surrogate_run_against_oracle_and_gain(ara, oracle, trained):
           f"({fallback / hits:.1%})")
 
 
+def test_served_losses_within_eps_of_mean_loss(ara, oracle, trained):
+    """A hit is served by the network only where its cell's certified error in x is at most
+    eps * mu_beta (mu_beta = mean / max exposure of the hit's record), so each served loss is
+    within eps of the record's mean loss and a year's sum within eps of its expected value.  The
+    cell error is the largest over the cell's sampled points, not a proof: per year the summed
+    loss errors must stay within 2 eps of the year's summed mean losses, hit by hit against the
+    FP64 oracle's quantiles."""
+    c, _ = trained
+    w = synth.tiny()
+    yet, elts, layer = c.stage_workload(w)
+    eps = 5e-4
+    c.set_surrogate_eps(eps)
+    c.set_option(ara.OPT_INVERSION, ara.INV_NEWTON)
+    c.set_option(ara.OPT_SURROGATE, 1)
+    try:
+        s0 = c.stats()
+        gh, _ = c.trace(yet, layer, 0, w.yet.n_trials)
+        s1 = c.stats()
+    finally:
+        c.set_option(ara.OPT_SURROGATE, 0)
+        c.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
+    oh, _ = oracle.trace(w.yet, w.elts, w.terms, 42, np.arange(w.yet.n_trials), elt_handles=elts)
+    np.testing.assert_array_equal(gh["trial"], oh["trial"])
+    np.testing.assert_array_equal(gh["rec"], oh["rec"])
+    e = w.elts[0]
+    rec = oh["rec"]
+    mean, mx = e.mean[rec], e.max_exposure[rec]
+    err = np.abs(gh["x"].astype(np.float64) - oh["x"]) * mx  # loss error of every hit
+    served = err > 1e-5 * mx  # the exact fallback is within 1e-5 in x
+    assert s1["surrogate_evals"] - s0["surrogate_evals"] > 0 and served.any()
+    per_hit = err / (eps * mean)
+    yr_err = np.bincount(oh["trial"], weights=err, minlength=w.yet.n_trials)
+    yr_mean = np.bincount(oh["trial"], weights=mean, minlength=w.yet.n_trials)
+    has = yr_mean > 0
+    yr = yr_err[has] / (eps * yr_mean[has])
+    print(f"served {served.mean():.1%} of hits; loss error / (eps x mean): per hit max "
+          f"{per_hit.max():.3f}, p99 {np.quantile(per_hit[served], 0.99):.3f}; per year max "
+          f"{yr.max():.3f}")
+    assert yr.max() <= 2.0
+
+
 def test_surrogate_cost_against_newton_on_paper_sample(ara, trained):
     """What the network gains over the method without it, on 20,000 trials of the paper-scale
     layer: it replaces the inversions of the hits it serves (a certified share of them, the rest
