@@ -179,7 +179,7 @@ def test_surrogate_cost_against_newton_on_paper_sample(ara, trained):
     falling back to Newton-Halley), at PML within 1e-3 of the exact form; and what it costs.  The
     run cannot be faster than the bookkeeping every form pays (the same layer with every SD zero)
     plus its fallbacks' share of the Newton-Halley inversion time, which is the bound that keeps
-    this network (82% fallback on this law) slower than the plain form."""
+    this network (most hits fall back on this law) slower than the plain form."""
     c, _ = trained
     w = synth.paper(n_trials=20_000)
     yet, elts, layer = c.stage_workload(w)
