@@ -7,15 +7,16 @@
 //   S = sum of o over the year;  YLT[trial] = min(max(S - AggR, 0), AggL)
 //
 // Schedule (designed for SIMT on sm_103a, not the paper's thread-per-trial):
-//   * A warp walks its trial in chunks of 128 occurrences; lane l reads occurrences
-//     c + 32v + l (v = 0..3), so each of the four id loads is one coalesced 128-byte line.
+//   * A warp walks its trial in chunks of 256 occurrences (128 on the surrogate path); lane l
+//     reads occurrences c + 32v + l (v = 0..7, or 0..3), so each id load is one coalesced
+//     128-byte line.
 //   * Each occurrence reads its 8/16-byte lookup entry (record base + ELT mask); hits are counted
 //     with popc and laid out in event order by a warp scan, giving the chunk's hit list.
 //   * The hit list is processed in rounds of up to 32 hits, one hit per lane, so the inversion
 //     (the time sink) runs with nearly every lane busy however sparse the hits are; a round ends
-//     on an event boundary, so an event's ELT losses are summed the same way in every schedule.  A lane finds its hit's event
-//     by binary search of the chunk's hit prefix in shared memory and its ELT by the n-th set bit
-//     of the mask.
+//     on an event boundary, so an event's ELT losses are summed the same way in every schedule.
+//     A lane finds its hit's event by binary search of the chunk's hit prefix in shared memory
+//     and its ELT by the n-th set bit of the mask.
 //   * An event's losses (contiguous in the hit list) are summed by a segmented warp scan; the
 //     tail lane adds the segment to the event's shared accumulator.  The order is fixed by the
 //     data, so results do not depend on the launch configuration.
@@ -37,7 +38,7 @@ namespace ara {
 namespace {
 
 // Warps per block: 2 where a block's warps run independent trials (its slot on the SM is freed
-// only when its slowest warp ends, so small blocks waste least of it), 8 for the surrogate path,
+// only when its slowest warp ends, so small blocks waste least of it), 4 for the surrogate path,
 // whose blocks first load the network's weights into shared memory.
 template <int INV>
 constexpr int kWPB = INV == 2 ? 4 : 2;
@@ -83,7 +84,7 @@ __device__ __forceinline__ float surrogate_round(const MlpSmem& W, const float (
 
 // ---- the learned surrogate's hits, a segment at a time ------------------------------------------
 // Running the network in every round where any lane's hit is eligible costs a full 32-row pass
-// per round (about 18% of hits are eligible); instead the losses of a segment of up to kSegCap
+// per round (a minority of hits is eligible); instead the losses of a segment of up to kSegCap
 // hits are computed ahead: pass A draws every hit and inverts the ineligible ones (Newton-Halley
 // from the record's start table), listing the eligible ones; pass B runs the network over the
 // list 32 rows at a time.  The rounds then read each hit's loss.
