@@ -311,6 +311,8 @@ ARA_API ara_status ara_risk_measures_n(ara_ctx* ctx, const double* values, int64
 /* Learned surrogate of InvCDF_beta ----------------------------------------------------------------
  * A 3 -> 64 -> 64 -> 64 -> 1 SiLU network (BF16 weights, FP32 accumulation, tensor-core MMA) maps
  * (ln alpha, ln beta, logit u), normalised over the box alpha, beta in [0.1, 50], to logit x.
+ * Training rounds inputs and activations to BF16; evaluation, certification and ara_run carry
+ * them as hi + lo BF16 pairs (about 16 significant bits).
  * Trained on the GPU by this library's own forward/backward/Adam kernels on (alpha, beta, u, x)
  * tuples generated by the exact inversion (polished in binary64); then certified: on a 32 x 32 x 64
  * grid of cells over the normalised inputs, each cell's largest |x_net - x| over its corners and

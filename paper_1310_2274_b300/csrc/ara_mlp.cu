@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) fwd_bwd_kernel(
     float pre1[8][4], pre2[8][4], pre3[8][4];
     uint32_t h1[4][4], h2[4][4];
     float y0, y8;
-    mlp_tile_forward(W, zr0, zr8, g, t, &y0, &y8, pre1, pre2, pre3, h1, h2, nullptr);
+    mlp_tile_forward_train(W, zr0, zr8, g, t, &y0, &y8, pre1, pre2, pre3, h1, h2, nullptr);
     // dL/dy for rows g and g + 8
     float dy[2];
 #pragma unroll
@@ -289,7 +289,8 @@ __global__ void pack_kernel(const float* __restrict__ P, MlpDevWeights* Wd) {
   for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < kH * kLd;
        i += blockDim.x * gridDim.x) {
     const int r = i / kLd, c = i % kLd;
-    if (c < 24) F.w1[r][c] = c < 3 ? __float2bfloat16_rn(P[kOffW1 + r * 3 + c]) : zero;
+    // W1 in columns 0..2 and, for the lo parts of the inference inputs, again in 3..5
+    if (c < 24) F.w1[r][c] = c < 6 ? __float2bfloat16_rn(P[kOffW1 + r * 3 + c % 3]) : zero;
     F.w2[r][c] = c < kH ? __float2bfloat16_rn(P[kOffW2 + r * kH + c]) : zero;
     F.w3[r][c] = c < kH ? __float2bfloat16_rn(P[kOffW3 + r * kH + c]) : zero;
     Bw.w2t[r][c] = c < kH ? __float2bfloat16_rn(P[kOffW2 + c * kH + r]) : zero;

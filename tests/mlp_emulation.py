@@ -1,10 +1,12 @@
 """The surrogate network as the tensor-core kernels compute it, in binary64 with their rounding
 points (test infrastructure: the GPU tests compare the kernels with it element by element).
 
-Rounding points of the kernels: inputs z, the weights of the three hidden layers, the layer-1 and
-layer-2 activations and the back-propagated layer gradients dZ are BF16 (round to nearest even);
-accumulation, biases, the layer-3 activations, the output layer, the loss and the bias
-gradients are FP32.  SiLU is z(1 + tanh(z/2))/2 with the hardware tanh, whose error (about 2^-11
+Rounding points of the training kernels: inputs z, the weights of the three hidden layers, the
+layer-1 and layer-2 activations and the back-propagated layer gradients dZ are BF16 (round to
+nearest even); accumulation, biases, the layer-3 activations, the output layer, the loss and the
+bias gradients are FP32.  The inference kernels (evaluation, certification, the trial kernel)
+carry inputs and layer-1/2 activations as FP32 values split into hi = bf16(v) and
+lo = bf16(v - hi) (split=True).  SiLU is z(1 + tanh(z/2))/2 with the hardware tanh, whose error (about 2^-11
 relative) the comparison cannot reproduce: element-wise bounds are drawn instead from repeated
 emulations with tanh perturbed by a relative 2^-10 (which also moves the BF16 roundings it can
 flip), see bounds().
@@ -23,8 +25,16 @@ def bf16(x):
     return r.view(np.float32).astype(np.float64)
 
 
-def emulate(p, z, x=None, t=None, tanh_err=0.0, rng=None):
-    """y (and, with x and t, the loss and the gradient) of the kernels' arithmetic."""
+def split(v):
+    """hi + lo of the inference kernels: the FP32 value v as bf16(v) + bf16(v - bf16(v))."""
+    v = np.asarray(v, dtype=np.float32).astype(np.float64)
+    hi = bf16(v)
+    return hi + bf16(v - hi)
+
+
+def emulate(p, z, x=None, t=None, tanh_err=0.0, rng=None, split_ops=False):
+    """y (and, with x and t, the loss and the gradient) of the kernels' arithmetic; split_ops:
+    the inference kernels' hi + lo operands."""
     W1, b1, W2, b2, W3, b3, W4, b4 = ref.unpack(p)
 
     def tanh(v):
@@ -40,11 +50,12 @@ def emulate(p, z, x=None, t=None, tanh_err=0.0, rng=None):
         s = 0.5 * (1.0 + tanh(0.5 * a))
         return s * (1.0 + a * (1.0 - s))
 
-    zq, W1q, W2q, W3q = bf16(z), bf16(W1), bf16(W2), bf16(W3)
+    act = split if split_ops else bf16
+    zq, W1q, W2q, W3q = act(z), bf16(W1), bf16(W2), bf16(W3)
     a1 = zq @ W1q.T + b1
-    h1 = bf16(silu(a1))
+    h1 = act(silu(a1))
     a2 = h1 @ W2q.T + b2
-    h2 = bf16(silu(a2))
+    h2 = act(silu(a2))
     a3 = h2 @ W3q.T + b3
     h3 = silu(a3)
     y = h3 @ W4[0] + b4[0]
@@ -72,13 +83,15 @@ def emulate(p, z, x=None, t=None, tanh_err=0.0, rng=None):
 def bounds(p, z, x=None, t=None, samples=30, seed=0):
     """The emulation and element-wise bounds: twice the largest deviation over `samples`
     emulations with tanh perturbed by 2^-10, plus a floor for FP32 accumulation (1e-5 of |y|; for
-    the gradient 2e-4 of the largest entry of each parameter block)."""
+    the gradient 2e-4 of the largest entry of each parameter block).  Without x: the inference
+    kernels' forward pass; with x and t: the training kernels' forward and backward passes."""
     rng = np.random.default_rng(seed)
-    base = emulate(p, z, x, t)
+    base = emulate(p, z, x, t, split_ops=x is None)
     if x is None:
         dev = np.zeros_like(base)
         for _ in range(samples):
-            dev = np.maximum(dev, np.abs(emulate(p, z, tanh_err=2.0 ** -10, rng=rng) - base))
+            dev = np.maximum(dev, np.abs(emulate(p, z, tanh_err=2.0 ** -10, rng=rng,
+                                                 split_ops=True) - base))
         return base, 2.0 * dev + 1e-5 * (1.0 + np.abs(base))
     y0, _, g0 = base
     dev = np.zeros_like(g0)
