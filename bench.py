@@ -478,7 +478,7 @@ def run_ours(a):
     newton_band_ms = time_calls(run_layer, nrep, stream, dev)
     ctx.set_option(ara.OPT_INVERSION, ara.INV_TABLE)
 
-    # roofline of the headline's run call (SURVEY §8(d)'s unit: one beta inversion per hit, the
+    # roofline of the headline's run call (unit of work: one beta inversion per hit, the
     # per-unit work W_INV frozen from the oracle's algorithm): the binary32 table build (one
     # launch over the 16 ELTs), the layer's table gather and the trial-major table kernel
     n_inv = d["inversions"] + d["table_evals"] + d["surrogate_evals"]
