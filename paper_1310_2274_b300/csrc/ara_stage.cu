@@ -42,6 +42,8 @@ __global__ void validate_yet_kernel(const int32_t* __restrict__ ids, const float
   unsigned int f = 0;
   for (int64_t i = t_begin + warp; i < t_begin + n_trials; i += nwarps) {
     const int64_t beg = off[i] - occ_base, end = off[i + 1] - occ_base;
+    // unrolled by 4: a lane keeps four groups of loads in flight (a memory-bound pass)
+#pragma unroll 4
     for (int64_t q = beg + lane; q < end; q += 32) {
       const int32_t e = ids[q];
       if (ids_out != nullptr) ids_out[q] = e;  // the YET's device copy, made in the same pass
